@@ -1,0 +1,72 @@
+"""The synthetic input generator: RMAT graphs and seed sets (CPU)."""
+import numpy as np
+
+from paper_2009_09103_gb300 import inputs
+
+
+def _check_csr(g, wmax):
+    V = g.V
+    off = g.off.astype(np.int64)
+    assert off[0] == 0 and off[-1] == g.E and np.all(np.diff(off) >= 0)
+    src = np.repeat(np.arange(V, dtype=np.int64), np.diff(off))
+    col = g.col.astype(np.int64)
+    assert np.all(col < V)
+    assert not np.any(src == col), "self-loop"
+    # rows strictly ascending (sorted, no duplicates)
+    same_row = src[1:] == src[:-1]
+    assert np.all(col[1:][same_row] > col[:-1][same_row])
+    # symmetric with equal weights both ways
+    fwd = src * V + col
+    rev = col * V + src
+    order = np.argsort(rev)
+    assert np.array_equal(np.sort(fwd), rev[order])
+    pos = np.searchsorted(fwd, rev)
+    assert np.array_equal(g.w[pos], g.w)
+    assert g.w.min() >= 1 and g.w.max() <= wmax
+
+
+def test_rmat_small_is_valid_csr():
+    g = inputs.rmat_csr(10, 8, 37, seed=3)
+    _check_csr(g, 37)
+    deg = np.diff(g.off)
+    assert deg.max() > 8 * deg.mean()          # power-law: hubs well above the mean
+    assert g.E > 0.7 * 2 * 8 * g.V              # few duplicates at this scale
+
+
+def test_rmat_deterministic_and_seed_dependent():
+    a = inputs.rmat_csr(9, 4, 10, seed=1)
+    b = inputs.rmat_csr(9, 4, 10, seed=1, threads=3)
+    c = inputs.rmat_csr(9, 4, 10, seed=2)
+    assert np.array_equal(a.off, b.off) and np.array_equal(a.col, b.col) and np.array_equal(a.w, b.w)
+    assert not np.array_equal(a.col, c.col)
+
+
+def test_rmat_hubs_are_spread_over_ids():
+    g = inputs.rmat_csr(12, 16, 100, seed=12)
+    deg = np.diff(g.off)
+    top = np.argsort(deg)[-16:]
+    assert top.max() > g.V // 4   # the label permutation moved hubs away from low ids
+
+
+def test_workload_sample_s12_shape():
+    wl = inputs.workload_sample_s12()
+    _check_csr(wl.graph, 100)
+    assert wl.graph.V == 4096 and wl.graph.E <= 131072
+    assert len(wl.seeds) == 256 and wl.seeds.max() < 4096
+    assert wl.fanout == [10, 5]
+
+
+def test_seed_sets():
+    sizes = inputs.loguniform_sizes(4096, 6.0, 7.0, seed=24, stream=4)
+    assert sizes.min() >= 64 and sizes.max() < 8192
+    # log-uniform: about half the instances below 2^9.5
+    frac = np.mean(sizes < 2 ** 9.5)
+    assert 0.45 < frac < 0.55
+    seeds, offs = inputs.distinct_seeds(sizes[:50], 1 << 16, seed=1)
+    for i in range(50):
+        s = seeds[offs[i]:offs[i + 1]]
+        assert len(np.unique(s)) == len(s) == sizes[i]
+        assert s.max() < (1 << 16)
+    u = inputs.uniform_vertices(100000, 1000, seed=9)
+    counts = np.bincount(u, minlength=1000)
+    assert counts.min() > 50 and counts.max() < 160

@@ -1,0 +1,420 @@
+"""Pins of the oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle (oracle/csaw_ref.c) against something other than
+itself: the paper's worked examples (Fig. 1(b), Fig. 5), Philox known-answer
+vectors, exact enumeration of the selection law (Theorem 1 with the integer
+mapping), closed forms (stationary law of a weighted walk), special cases that
+reduce to a textbook routine (fanout "all" is breadth-first search), and
+hand-computed node2vec transition tables (Sec. II-A).
+"""
+import os
+
+import numpy as np
+import pytest
+from scipy import stats
+from scipy.sparse import csr_matrix
+from scipy.sparse.csgraph import shortest_path
+
+import oracle
+from paper_2009_09103_gb300 import inputs
+from conftest import GOLDEN, read_kv
+
+TWO64 = 1 << 64
+P_MIN = 1e-4  # chi-square acceptance; inputs are seeded so each test is deterministic
+
+
+def chi2_pvalue(counts, probs):
+    counts = np.asarray(counts, dtype=np.float64)
+    probs = np.asarray(probs, dtype=np.float64)
+    n = counts.sum()
+    exp = probs * n
+    # merge bins with small expectation into one
+    small = exp < 5
+    if small.any():
+        counts = np.append(counts[~small], counts[small].sum())
+        exp = np.append(exp[~small], exp[small].sum())
+        if exp[-1] == 0:
+            assert counts[-1] == 0
+            counts, exp = counts[:-1], exp[:-1]
+    if len(exp) < 2:
+        return 1.0
+    return stats.chisquare(counts, exp * counts.sum() / exp.sum()).pvalue
+
+
+# ---------------------------------------------------------------- Philox
+def test_philox_known_answer_vectors():
+    rows = []
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                rows.append([int(x, 16) for x in line.split()])
+    assert len(rows) == 3
+    for r in rows:
+        out = oracle.philox4x32_10(r[0:4], r[4:6])
+        assert [int(x) for x in out] == r[6:10]
+
+
+def test_draw_word_layout():
+    # key = (lo32(seed), hi32(seed)), counter = (attempt, vertex, layer, instance),
+    # r = out1 << 32 | out0
+    seed = 0x0123456789ABCDEF
+    out = oracle.philox4x32_10([7, 11, 13, 17], [seed & 0xFFFFFFFF, seed >> 32])
+    assert oracle.draw(seed, 7, 11, 13, 17) == (int(out[1]) << 32) | int(out[0])
+
+
+def test_draw_bits_are_uniform():
+    # statistical sanity: each of the 64 bits of r is set about half the time
+    n = 20000
+    r = np.array([oracle.draw(1, a, 5, 0, 0) for a in range(n)], dtype=np.uint64)
+    for bit in (0, 17, 31, 32, 50, 63):
+        ones = int(((r >> np.uint64(bit)) & np.uint64(1)).sum())
+        assert abs(ones - n / 2) < 5 * np.sqrt(n / 4)
+
+
+# ---------------------------------------------------------------- scaling r -> [0, T)
+def test_scale_exact_for_powers_of_two_and_extremes():
+    for k in (1, 2, 7, 32, 63):
+        for r in (0, 1, 12345678901234567, TWO64 - 1, 1 << 63):
+            assert oracle.scale(r, 1 << k) == r >> (64 - k)
+    for T in (1, 3, 15, 10**12 + 7, TWO64 - 1):
+        assert oracle.scale(0, T) == 0
+        assert oracle.scale(TWO64 - 1, T) == T - 1
+
+
+def test_scale_preimage_sizes():
+    # x has exactly ceil((x+1) 2^64 / T) - ceil(x 2^64 / T) preimages: check the
+    # boundary draws land on each side of every boundary.
+    for T in (3, 15, 1000003):
+        for x in (0, 1, T // 2, T - 1):
+            lo = -(-x * TWO64 // T)            # smallest r with scale(r) >= x
+            assert oracle.scale(lo, T) == x
+            if lo > 0:
+                assert oracle.scale(lo - 1, T) == x - 1
+
+
+# ---------------------------------------------------------------- paper examples
+NAMES = ["v5", "v7", "v9", "v10", "v11"]
+
+
+def test_fig1b_inverse_transform_sampling():
+    g = read_kv("paper_its_examples.txt")
+    b = [int(x) for x in g["biases"]]
+    prefix = [int(x) for x in g["prefix_with_leading_zero"]]
+    assert list(np.cumsum(b)) == prefix[1:]
+    T = prefix[-1]
+    assert np.allclose(np.array(prefix) / T, [float(x) for x in g["ctps"]], atol=0.005)
+    r = int(float(g["its_draw"][0]) * TWO64)
+    assert NAMES[oracle.select_given_draws(b, 1, [r])[0]] == g["its_pick"][0]
+    # every x in [0, T) selects the candidate whose interval [S_m, S_m+1) holds x
+    for x in range(T):
+        r = -(-x * TWO64 // T)
+        pick = int(oracle.select_given_draws(b, 1, [r])[0])
+        assert prefix[pick] <= x < prefix[pick + 1]
+
+
+def test_fig5_updated_sampling_and_collision():
+    g = read_kv("paper_its_examples.txt")
+    b = [int(x) for x in g["biases"]]
+    r_v7 = int(float(g["its_draw"][0]) * TWO64)
+    r2 = int(float(g["updated_draw"][0]) * TWO64)
+    # updated sampling from the second attempt on: v7 then v10
+    picks = oracle.select_given_draws(b, 2, [r_v7, r2], attempt_cap=1)
+    assert [NAMES[i] for i in picks] == ["v7", g["updated_pick"][0]]
+    # the paper's updated prefix sums
+    rem = [int(x) for x in g["updated_remaining_biases"]]
+    assert [0] + list(np.cumsum(rem)) == [int(x) for x in g["updated_prefix"]]
+    # repeated sampling: 0.58 hits v7's region again, so two draws are not enough
+    assert oracle.select_given_draws(b, 2, [r_v7, r2], attempt_cap=1024) is None
+    r3 = int(0.9 * TWO64)  # 0.9 * 15 = 13.5 -> v11
+    picks = oracle.select_given_draws(b, 2, [r_v7, r2, r3], attempt_cap=1024)
+    assert [NAMES[i] for i in picks] == ["v7", "v11"]
+
+
+def _fig1_graph():
+    """v8 with neighbours v5, v7, v9, v10, v11 of degrees 3, 6, 2, 2, 2
+    (Fig. 1(a) caption); padding vertices 12.. give them those degrees."""
+    und = [(8, 5), (8, 7), (8, 9), (8, 10), (8, 11)]
+    nxt = 12
+    for v, extra in ((5, 2), (7, 5), (9, 1), (10, 1), (11, 1)):
+        for _ in range(extra):
+            und.append((v, nxt))
+            nxt += 1
+    edges = und + [(b, a) for a, b in und]
+    return inputs.csr_from_edges(nxt, edges)
+
+
+def test_fig1_neighbour_degree_bias_law():
+    g = _fig1_graph()
+    assert list(g.col[g.off[8]:g.off[9]]) == [5, 7, 9, 10, 11]
+    n = 30000
+    counts = {5: 0, 7: 0, 9: 0, 10: 0, 11: 0}
+    for inst in range(n):
+        counts[int(oracle.select(g, 8, 1, "neighbor_degree", 99, 0, inst)[0])] += 1
+    p = chi2_pvalue([counts[v] for v in (5, 7, 9, 10, 11)], np.array([3, 6, 2, 2, 2]) / 15)
+    assert p > P_MIN
+
+
+# ---------------------------------------------------------------- hand-worked two-neighbour case
+def test_two_neighbour_weights_1_3():
+    b = [1, 3]
+    rng = np.random.default_rng(5)
+    for top in range(4):
+        for _ in range(8):
+            low = int(rng.integers(0, 1 << 62))
+            r = (top << 62) | low          # x = floor(4 r / 2^64) = top
+            assert int(oracle.select_given_draws(b, 1, [r])[0]) == (0 if top == 0 else 1)
+    # k >= 2: both, CSR order, no draws used
+    assert list(oracle.select_given_draws(b, 2, [])) == [0, 1]
+    assert list(oracle.select_given_draws(b, 5, [])) == [0, 1]
+    # frequency through the full keyed path: P(nbr 0) = 1/4
+    g = inputs.csr_from_edges(3, [(0, 1), (0, 2)], weights=[1, 3])
+    n = 40000
+    c1 = sum(int(oracle.select(g, 0, 1, "edge_weight", 7, 0, i)[0]) == 2 for i in range(n))  # vertex 2 = nbr 1
+    assert chi2_pvalue([n - c1, c1], [0.25, 0.75]) > P_MIN
+
+
+def test_zero_bias_never_drawn_and_take_all_positive():
+    b = [0, 5, 0, 0, 2, 0]
+    rng = np.random.default_rng(3)
+    draws = [int(x) for x in rng.integers(0, 2**63, size=200, dtype=np.uint64)]
+    for k in (1,):
+        for r in draws:
+            assert int(oracle.select_given_draws(b, k, [r])[0]) in (1, 4)
+    # two positive candidates <= k: take them in CSR order
+    assert list(oracle.select_given_draws(b, 2, [])) == [1, 4]
+    assert list(oracle.select_given_draws(b, oracle.FANOUT_ALL, [])) == [1, 4]
+    assert len(oracle.select_given_draws([0, 0, 0], 2, [])) == 0
+
+
+# ---------------------------------------------------------------- exact selection law by enumeration
+def _attempt_probs(b):
+    """Exact probability that one attempt lands on each candidate, under
+    x = floor(r T / 2^64) with r uniform on [0, 2^64)."""
+    S = np.cumsum([0] + list(b)).tolist()
+    T = S[-1]
+    q = []
+    for i in range(len(b)):
+        lo = -(-S[i] * TWO64 // T)
+        hi = -(-S[i + 1] * TWO64 // T)
+        q.append((hi - lo) / TWO64)
+    return q
+
+
+def _tuple_probs(b, k):
+    """Law of the ordered k-tuple of first distinct hits (Theorem 1 applied
+    repeatedly): prod_t q_jt / (1 - sum_{s<t} q_js)."""
+    q = _attempt_probs(b)
+    out = {}
+
+    def rec(prefix, p, used):
+        if len(prefix) == k:
+            out[tuple(prefix)] = p
+            return
+        for j in range(len(b)):
+            if q[j] > 0 and j not in prefix:
+                rec(prefix + [j], p * q[j] / (1.0 - used), used + q[j])
+    rec([], 1.0, 0.0)
+    return out
+
+
+@pytest.mark.parametrize("b,k,cap", [
+    ([1, 3], 1, 1024),
+    ([5, 1, 1, 2], 2, 1024),
+    ([7, 1, 3, 2, 1], 3, 1024),
+    ([2, 9, 1, 4, 4, 1], 3, 1024),
+    ([7, 1, 3, 2, 1], 3, 0),       # updated sampling from the first attempt
+    ([2, 9, 1, 4, 4, 1], 2, 1),    # switch after one attempt
+])
+def test_selection_law_matches_enumeration(b, k, cap):
+    d = len(b)
+    edges = [(0, j + 1) for j in range(d)]
+    g = inputs.csr_from_edges(d + 1, edges, weights=b)
+    probs = _tuple_probs(b, k)
+    keys = sorted(probs)
+    index = {t: i for i, t in enumerate(keys)}
+    counts = np.zeros(len(keys))
+    n = 30000
+    for inst in range(n):
+        picks = oracle.select(g, 0, k, "edge_weight", 2024, 1, inst, attempt_cap=cap)
+        t = tuple(int(u) - 1 for u in picks)
+        assert len(set(t)) == k
+        counts[index[t]] += 1
+    assert chi2_pvalue(counts, [probs[t] for t in keys]) > P_MIN
+
+
+# ---------------------------------------------------------------- walks
+def _ring_with_chords(n=64, seed=1):
+    rng = np.random.default_rng(seed)
+    und = {}
+    for v in range(n):
+        und[(v, (v + 1) % n)] = int(rng.integers(1, 10))
+    und[(0, 2)] = 5      # a triangle 0-1-2 makes the walk aperiodic
+    for _ in range(40):
+        a, c = (int(x) for x in rng.integers(0, n, 2))
+        if a != c:
+            und[(min(a, c), max(a, c))] = int(rng.integers(1, 10))
+    edges, ws = [], []
+    seen = set()
+    for (a, c), w in und.items():
+        key = (min(a, c), max(a, c))
+        if key in seen:
+            continue
+        seen.add(key)
+        edges += [(a, c), (c, a)]
+        ws += [w, w]
+    return inputs.csr_from_edges(n, edges, ws)
+
+
+def test_weighted_walk_stationary_law():
+    # A long weighted walk on a connected non-bipartite undirected graph visits
+    # v with frequency W(v) / sum W, W(v) = sum of the weights at v.
+    g = _ring_with_chords()
+    V = g.V
+    W = np.array([g.w[g.off[v]:g.off[v + 1]].sum() for v in range(V)], dtype=np.float64)
+    pi = W / W.sum()
+    starts = inputs.uniform_vertices(8000, V, 5)
+    path = oracle.walk(g, starts, 600, "edge_weight", 11)
+    visits = np.bincount(path[:, 100:].ravel(), minlength=V) / path[:, 100:].size
+    assert 0.5 * np.abs(visits - pi).sum() < 0.01
+
+
+def test_uniform_walk_on_cycle_is_symmetric():
+    n = 16
+    edges = [(v, (v + 1) % n) for v in range(n)] + [((v + 1) % n, v) for v in range(n)]
+    g = inputs.csr_from_edges(n, edges)
+    path = oracle.walk(g, np.zeros(20000, dtype=np.uint32), 1, "uniform", 3)
+    right = int((path[:, 1] == 1).sum())
+    assert chi2_pvalue([right, 20000 - right], [0.5, 0.5]) > P_MIN
+    # equal weights behave as uniform: identical paths (biases scale by a constant)
+    g2 = inputs.csr_from_edges(n, edges, weights=[7] * len(edges))
+    assert np.array_equal(oracle.walk(g2, np.arange(n), 30, "edge_weight", 9),
+                          oracle.walk(g, np.arange(n), 30, "uniform", 9))
+
+
+def test_walk_dead_end_and_zero_weights():
+    # 0 -> 1 -> 2, 2 has no out-edge; 3 -> 4 only with weight 0
+    g = inputs.csr_from_edges(5, [(0, 1), (1, 2), (3, 4)], weights=[1, 1, 0])
+    p = oracle.walk(g, [0, 3, 2], 4, "edge_weight", 1)
+    N = oracle.NONE
+    assert p[0].tolist() == [0, 1, 2, N, N]
+    assert p[1].tolist() == [3, N, N, N, N]
+    assert p[2].tolist() == [2, N, N, N, N]
+
+
+def test_node2vec_hand_computed_transitions():
+    # triangle 0-1-2 plus pendant 3 on 0; w(0,3) = 3, others 1.
+    # From 1 the first step is by weight: 0 or 2 with 1/2 each.
+    # At 0 having come from 1: u=1 is prev (x1), u=2 is adjacent to 1 (x2),
+    # u=3 is not (x4): biases 1*1, 1*2, 3*4 -> (1, 2, 12) / 15.
+    # At 2 having come from 1: u=0 adjacent to 1 (x2), u=1 is prev (x1): (2, 1)/3.
+    und = [(0, 1, 1), (0, 2, 1), (1, 2, 1), (0, 3, 3)]
+    edges = [(a, b) for a, b, _ in und] + [(b, a) for a, b, _ in und]
+    ws = [w for *_, w in und] * 2
+    g = inputs.csr_from_edges(4, edges, ws)
+    n = 30000
+    path = oracle.walk(g, np.ones(n, dtype=np.uint32), 2, "node2vec", 17, mult=(1, 2, 4))
+    first = path[:, 1]
+    assert chi2_pvalue([(first == 0).sum(), (first == 2).sum()], [0.5, 0.5]) > P_MIN
+    at0 = path[first == 0, 2]
+    assert chi2_pvalue([(at0 == 1).sum(), (at0 == 2).sum(), (at0 == 3).sum()],
+                       np.array([1, 2, 12]) / 15) > P_MIN
+    at2 = path[first == 2, 2]
+    assert chi2_pvalue([(at2 == 0).sum(), (at2 == 1).sum()], np.array([2, 1]) / 3) > P_MIN
+
+
+def test_node2vec_equal_multipliers_equal_weighted_walk():
+    # Scaling every bias by c leaves every pick unchanged:
+    # floor(floor(r cT / 2^64) / c) = floor(r T / 2^64) and intervals scale by c.
+    g = inputs.rmat_csr(10, 8, 50, 3)
+    starts = np.arange(g.V, dtype=np.uint32)
+    ref = oracle.walk(g, starts, 12, "edge_weight", 77)
+    assert np.array_equal(oracle.walk(g, starts, 12, "node2vec", 77, mult=(1, 1, 1)), ref)
+    assert np.array_equal(oracle.walk(g, starts, 12, "node2vec", 77, mult=(2, 2, 2)), ref)
+    assert not np.array_equal(oracle.walk(g, starts, 12, "node2vec", 77, mult=(1, 2, 4)), ref)
+
+
+def test_walk_invariants_and_subset_ids():
+    g = inputs.rmat_csr(10, 8, 50, 4)
+    starts = inputs.uniform_vertices(500, g.V, 8)
+    path = oracle.walk(g, starts, 20, "edge_weight", 5)
+    adj = set()
+    for v in range(g.V):
+        for u in g.col[g.off[v]:g.off[v + 1]]:
+            adj.add((v, int(u)))
+    for row in path:
+        for s in range(20):
+            a, c = int(row[s]), int(row[s + 1])
+            if a == oracle.NONE:
+                assert c == oracle.NONE
+            elif c != oracle.NONE:
+                assert (a, c) in adj
+            else:
+                assert g.off[a + 1] == g.off[a]   # sentinel only after a dead end
+    # a subset run with explicit walker ids reproduces those rows exactly
+    ids = np.array([3, 77, 499], dtype=np.uint64)
+    sub = oracle.walk(g, starts[ids.astype(np.int64)], 20, "edge_weight", 5, walker_ids=ids)
+    assert np.array_equal(sub, path[ids.astype(np.int64)])
+
+
+# ---------------------------------------------------------------- layered sampling
+def test_fanout_all_is_breadth_first_search():
+    # With every neighbour taken, the frontier of layer l is BFS level l and
+    # the emitted edges are all edges leaving levels 0 .. depth-1.
+    g = inputs.rmat_csr(9, 4, 10, 6)
+    V = g.V
+    A = csr_matrix((np.ones(g.E), g.col.astype(np.int64), g.off.astype(np.int64)), shape=(V, V))
+    seed_v = int(np.argmax(np.diff(g.off)))
+    dist = shortest_path(A, unweighted=True, indices=[seed_v])[0]
+    depth = 3
+    out = oracle.sample(g, [seed_v], [0, 1], [oracle.FANOUT_ALL] * depth, "edge_weight", 1)
+    for lvl in range(depth + 1):
+        assert out["fsize"][lvl] == int((dist == lvl).sum())
+    for lvl in range(depth):
+        lo, hi = out["edge_off"][lvl], out["edge_off"][lvl + 1]
+        src = out["src"][lo:hi]
+        expect = np.flatnonzero(dist == lvl)
+        assert np.array_equal(np.unique(src), expect)
+        assert hi - lo == int(np.diff(g.off)[expect].sum())
+
+
+def test_sampling_invariants_small_workload():
+    wl = inputs.workload_sample_s12()
+    g = wl.graph
+    out = oracle.sample(g, wl.seeds, wl.inst_offsets, wl.fanout, wl.bias, wl.rng_seed)
+    deg = np.diff(g.off)
+    visited = set(np.unique(wl.seeds).tolist())
+    assert out["fsize"][0] == len(visited)
+    frontier = sorted(visited)
+    for lvl, k in enumerate(wl.fanout):
+        lo, hi = int(out["edge_off"][lvl]), int(out["edge_off"][lvl + 1])
+        src, dst = out["src"][lo:hi], out["dst"][lo:hi]
+        # sources are the frontier in ascending order, each with min(k, d) picks
+        expect_src = np.repeat(np.array(frontier, dtype=np.uint32),
+                               np.minimum(k, deg[np.array(frontier, dtype=np.int64)]).astype(np.int64))
+        assert np.array_equal(src, expect_src)
+        start = 0
+        for v in frontier:
+            n = int(min(k, deg[v]))
+            picks = dst[start:start + n]
+            nb = set(g.col[g.off[v]:g.off[v + 1]].tolist())
+            assert len(set(picks.tolist())) == n and set(picks.tolist()) <= nb
+            start += n
+        nxt = sorted(set(dst.tolist()) - visited)
+        assert out["fsize"][lvl + 1] == len(nxt)
+        visited |= set(nxt)
+        frontier = nxt
+    assert out["edge_off"][-1] > 2000
+
+
+def test_sampling_instances_are_independent():
+    # An instance's output depends only on its own seeds and index.
+    g = inputs.rmat_csr(10, 8, 30, 9)
+    seeds = inputs.uniform_vertices(60, g.V, 4)
+    io = np.array([0, 20, 40, 60], dtype=np.uint64)
+    full = oracle.sample(g, seeds, io, [4, 3], "edge_weight", 5)
+    # instance 1 alone, placed at index 1 with an empty instance 0
+    solo = oracle.sample(g, seeds[20:40], np.array([0, 0, 20], dtype=np.uint64), [4, 3], "edge_weight", 5)
+    for lvl in range(2):
+        a = full["edge_off"][lvl * 3 + 1], full["edge_off"][lvl * 3 + 2]
+        b = solo["edge_off"][lvl * 2 + 1], solo["edge_off"][lvl * 2 + 2]
+        assert np.array_equal(full["dst"][a[0]:a[1]], solo["dst"][b[0]:b[1]])
