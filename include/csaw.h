@@ -1,0 +1,209 @@
+/*
+ * csaw.h -- C ABI of libcsaw: biased neighbour selection for graph sampling
+ * and random walks on one GB300 (sm_103a), after C-SAW (Pandey, Li, Hoisie,
+ * Li, Liu, "C-SAW: A Framework for Graph Sampling and Random Walk on GPUs",
+ * SC20).
+ *
+ * What every call computes (the paper's method, in exact integer form):
+ *   - EdgeBias (Sec. III-C, Eq. 3): each neighbour u of the vertex v being
+ *     expanded gets a uint32 bias b(u): 1 (uniform), the edge weight w(v,u),
+ *     the degree of u, or node2vec's second-order bias (Sec. II-A):
+ *     w(v,u) * m0 if u is the walk's previous vertex t, w(v,u) * m1 if u is a
+ *     neighbour of t, w(v,u) * m2 otherwise; the first step of a walk uses w.
+ *   - Inverse transform sampling (Sec. II-B, Theorem 1, Eq. 1): S[i] is the
+ *     inclusive uint64 prefix sum of the biases in CSR order, T = S[d-1];
+ *     neighbour i owns [S[i-1], S[i]).  Attempt a draws a 64-bit r from
+ *     Philox4x32-10 (key = {lo32(seed), hi32(seed)}, counter = {a, vertex,
+ *     layer or step, instance}, r = out1 << 32 | out0), maps it to
+ *     x = floor(r * T / 2^64) and picks the i whose interval holds x.
+ *   - Selection without replacement (Sec. IV-B): the first k distinct picks
+ *     in attempt order (repeated sampling).  After CSAW_ATTEMPT_CAP attempts
+ *     the remaining picks use updated sampling (the draw is scaled to the
+ *     total of the unpicked biases and searched among them), which ends in at
+ *     most k more attempts and leaves each pick's conditional law unchanged.
+ *     A vertex with at most k neighbours of positive bias takes all of them,
+ *     in CSR order, with no draws.
+ *   - Layered sampling (Sec. III-B, Fig. 2(b); Update, Eq. 4): each frontier
+ *     vertex selects fanout[l] neighbours; every pick is a sampled edge; the
+ *     next frontier is the set of picked vertices not yet visited by that
+ *     instance (traversal sampling never revisits a vertex, Sec. II-A).
+ *   - Random walk (Sec. II-A): one pick per step, with replacement.
+ * Results are bit-exact functions of (graph, arguments, rng_seed): they do
+ * not depend on batching, launch shape or what else runs on the GPU.
+ *
+ * Conventions
+ *   - All calls return csaw_status; none aborts.  On error,
+ *     csaw_last_error() returns a message for the calling thread.
+ *   - mem_kind says where the caller's array arguments live:
+ *     CSAW_MEM_DEVICE: device pointers; the call is asynchronous on `stream`
+ *     (a cudaStream_t, NULL = legacy default stream).
+ *     CSAW_MEM_HOST: host pointers; the call copies inputs to the device,
+ *     runs, copies outputs back and returns when they are in host memory.
+ *   - Invalid vertex / padding value: CSAW_NONE.
+ *   - The library owns the objects it returns until the matching destroy or
+ *     free call; the caller keeps ownership of every buffer it passes.
+ */
+#ifndef CSAW_H
+#define CSAW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CSAW_OK = 0,
+    CSAW_ERR_INVALID = 1,   /* malformed argument or graph */
+    CSAW_ERR_NOMEM = 2,     /* device or host allocation failed, or over budget */
+    CSAW_ERR_CUDA = 3,      /* a CUDA runtime call failed */
+    CSAW_ERR_OVERFLOW = 4,  /* a bias does not fit in 32 bits */
+    CSAW_ERR_TIMEOUT = 5,   /* csaw_poll: not finished within the timeout */
+    CSAW_ERR_ABORTED = 6,   /* request cancelled or server shut down */
+    CSAW_ERR_NOT_FOUND = 7  /* unknown ticket */
+} csaw_status;
+
+typedef enum {
+    CSAW_BIAS_UNIFORM = 0,
+    CSAW_BIAS_EDGE_WEIGHT = 1,
+    CSAW_BIAS_NEIGHBOR_DEGREE = 2,
+    CSAW_BIAS_NODE2VEC = 3
+} csaw_bias_kind;
+
+/* Bias of a call.  n2v_mult = (m0, m1, m2) for CSAW_BIAS_NODE2VEC:
+ * multiplier when the neighbour is the previous vertex, when it is adjacent
+ * to the previous vertex, otherwise.  node2vec's 1/p, 1, 1/q scaled to
+ * integers; p = 2, q = 0.5 gives (1, 2, 4).  Ignored for the other kinds. */
+typedef struct {
+    int32_t kind;
+    uint32_t n2v_mult[3];
+} csaw_bias;
+
+enum { CSAW_MEM_HOST = 0, CSAW_MEM_DEVICE = 1 };
+
+#define CSAW_NONE 0xFFFFFFFFu
+#define CSAW_FANOUT_ALL 0xFFFFFFFFu
+#define CSAW_ATTEMPT_CAP 1024u
+#define CSAW_MAX_DEPTH 16u
+
+typedef struct csaw_graph csaw_graph;
+typedef struct csaw_sample_result csaw_sample_result;
+
+/* ---------------------------------------------------------------- graph */
+
+/* Build a device-resident graph from CSR.  The graph is the input of every
+ * selection (Sec. II-A; all neighbours of a vertex must be present to form
+ * its biases, Sec. I and V-A).
+ *   row_offsets  uint64[n_vertices + 1], row_offsets[0] = 0,
+ *                row_offsets[n_vertices] = n_edges, non-decreasing
+ *   cols         uint32[n_edges]: neighbours of v at
+ *                cols[row_offsets[v] .. row_offsets[v+1]), strictly ascending
+ *                (sorted, no duplicates; node2vec's membership test relies on
+ *                it), every entry < n_vertices
+ *   weights      uint32[n_edges] edge weights, or NULL for all ones
+ *   mem_kind     where the three arrays live (host or device)
+ * The arrays are copied; the caller may free them when the call returns (for
+ * device inputs, once `stream` has reached this call).  Validation runs on
+ * the device and the call waits for it.  Errors: CSAW_ERR_INVALID (any rule
+ * above broken, or a row longer than 2^32 - 1), CSAW_ERR_NOMEM, CSAW_ERR_CUDA. */
+csaw_status csaw_graph_create(const uint64_t* row_offsets, uint32_t n_vertices,
+                              const uint32_t* cols, const uint32_t* weights, uint64_t n_edges,
+                              int mem_kind, void* stream, csaw_graph** out);
+
+/* Release the graph's device memory.  Work still queued on it must have
+ * finished.  NULL is accepted. */
+csaw_status csaw_graph_destroy(csaw_graph* g);
+
+/* Sizes and derived facts of a graph (host values). */
+typedef struct {
+    uint32_t n_vertices;
+    uint64_t n_edges;
+    uint32_t max_degree;
+    uint32_t max_weight;
+    uint64_t device_bytes;   /* device memory the graph holds */
+} csaw_graph_info;
+
+csaw_status csaw_graph_get_info(const csaw_graph* g, csaw_graph_info* out);
+
+/* ---------------------------------------------------------------- walks */
+
+/* Biased random walks (Sec. II-A; static bias: edge weight or neighbour
+ * degree; dynamic bias: node2vec), one pick per step with replacement.
+ *   starts    uint32[n_walkers] start vertices (each < n_vertices)
+ *   length    steps per walker
+ *   path      uint32[n_walkers][length + 1] row-major output;
+ *             path[w][0] = starts[w]; path[w][s+1] is the vertex after step s.
+ *             A walker at a vertex whose biases are all zero (or with no
+ *             neighbour) stops there; the rest of its row is CSAW_NONE.
+ * The draw of walker w at step s uses attempt 0, vertex = its current vertex,
+ * layer = s, instance = w.  Errors: CSAW_ERR_INVALID (bad bias kind, a start
+ * >= n_vertices for host inputs, n_walkers >= 2^32), CSAW_ERR_OVERFLOW
+ * (node2vec: max weight * max multiplier >= 2^32), CSAW_ERR_NOMEM,
+ * CSAW_ERR_CUDA.  With device inputs an out-of-range start is caught on the
+ * device: its row is filled with CSAW_NONE. */
+csaw_status csaw_walk(csaw_graph* g, const uint32_t* starts, uint64_t n_walkers, uint32_t length,
+                      const csaw_bias* bias, uint64_t rng_seed, uint32_t* path, int mem_kind,
+                      void* stream);
+
+/* ---------------------------------------------------------------- sampling */
+
+/* Layered biased neighbour sampling over many independent instances
+ * (Sec. III-B, Fig. 2(b); instances, Sec. IV-A; batched multi-instance
+ * sampling, Sec. V-B).
+ *   seeds         uint32[inst_offsets[n_instances]]: instance i's seeds are
+ *                 seeds[inst_offsets[i] .. inst_offsets[i+1]); duplicates are
+ *                 merged
+ *   inst_offsets  uint64[n_instances + 1], non-decreasing, starting at 0
+ *   depth         number of layers (1 .. CSAW_MAX_DEPTH)
+ *   fanout        uint32[depth] HOST array: picks per frontier vertex at each
+ *                 layer, or CSAW_FANOUT_ALL
+ *   bias          UNIFORM, EDGE_WEIGHT or NEIGHBOR_DEGREE (NODE2VEC needs a
+ *                 walk's previous vertex and is rejected)
+ * The draws of frontier vertex v of instance i at layer l use vertex = v,
+ * layer = l, instance = i.  Output edges are grouped by layer, then instance,
+ * then source vertex ascending; each vertex's picks are in pick order.
+ * seeds/inst_offsets live in mem_kind memory.  The result is returned in *out
+ * and lives on the device; read it with csaw_sample_get_view or copy it with
+ * csaw_sample_copy_edges, release it with csaw_result_free.
+ * Errors: CSAW_ERR_INVALID, CSAW_ERR_NOMEM, CSAW_ERR_CUDA. */
+csaw_status csaw_sample(csaw_graph* g, const uint32_t* seeds, const uint64_t* inst_offsets,
+                        uint32_t n_instances, uint32_t depth, const uint32_t* fanout,
+                        const csaw_bias* bias, uint64_t rng_seed, int mem_kind, void* stream,
+                        csaw_sample_result** out);
+
+typedef struct {
+    uint32_t depth;
+    uint32_t n_instances;
+    uint64_t n_edges;
+    /* host, depth*n_instances + 1 entries: edges of (layer l, instance i) are
+     * [edge_offsets[l*n_instances + i], edge_offsets[l*n_instances + i + 1]) */
+    const uint64_t* edge_offsets;
+    /* host, depth*n_instances entries: frontier size of (layer l, instance i) */
+    const uint64_t* frontier_sizes;
+    const uint32_t* src;   /* device, n_edges: sampled edge sources */
+    const uint32_t* dst;   /* device, n_edges: sampled edge destinations */
+} csaw_sample_view;
+
+/* Wait for the result's stream to reach the end of the sampling call and fill
+ * *view.  The pointers stay valid until csaw_result_free. */
+csaw_status csaw_sample_get_view(csaw_sample_result* r, csaw_sample_view* view);
+
+/* Copy the sampled edges to host arrays of n_edges entries each (waits). */
+csaw_status csaw_sample_copy_edges(csaw_sample_result* r, uint32_t* src, uint32_t* dst);
+
+/* Release a result returned by this library.  NULL is accepted. */
+void csaw_result_free(void* result);
+
+/* ---------------------------------------------------------------- misc */
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* csaw_last_error(void);
+
+/* ABI version: major * 10000 + minor * 100 + patch. */
+uint32_t csaw_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CSAW_H */

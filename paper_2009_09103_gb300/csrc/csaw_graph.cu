@@ -1,0 +1,250 @@
+// csaw_graph.cu -- errors, allocation, and the device-resident CSR graph.
+//
+// The graph is the input every selection reads (Sec. II-A; all neighbours of
+// a vertex must be present to form its biases, Sec. V-A).  It is copied once
+// into HBM and validated there: offsets monotone and ending at E, columns in
+// range, rows strictly ascending.  The degree array and the maximum degree and
+// weight are derived in the same pass.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "csaw_internal.cuh"
+
+namespace csaw {
+
+static thread_local char g_last_error[512] = "";
+
+csaw_status fail(csaw_status st, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+csaw_status cuda_fail(cudaError_t err, const char* what)
+{
+    if (err == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(CSAW_ERR_NOMEM, "%s: %s", what, cudaGetErrorString(err));
+    }
+    return fail(CSAW_ERR_CUDA, "%s: %s", what, cudaGetErrorString(err));
+}
+
+void clear_error() { g_last_error[0] = '\0'; }
+
+csaw_status dalloc(void** p, size_t bytes, cudaStream_t s)
+{
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(p, bytes, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(e == cudaErrorMemoryAllocation ? CSAW_ERR_NOMEM : CSAW_ERR_CUDA,
+                    "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    }
+    return CSAW_OK;
+}
+
+void dfree(void* p, cudaStream_t s)
+{
+    if (p) cudaFreeAsync(p, s);
+}
+
+csaw_status check_bias(const csaw_graph* g, const csaw_bias* bias, bool allow_node2vec, int* kind_out)
+{
+    if (!bias) return fail(CSAW_ERR_INVALID, "bias is NULL");
+    int kind = bias->kind;
+    switch (kind) {
+    case CSAW_BIAS_UNIFORM:
+    case CSAW_BIAS_NEIGHBOR_DEGREE:
+        break;
+    case CSAW_BIAS_EDGE_WEIGHT:
+        if (!g->w) kind = CSAW_BIAS_UNIFORM;   // all weights one: same picks as uniform
+        break;
+    case CSAW_BIAS_NODE2VEC: {
+        if (!allow_node2vec)
+            return fail(CSAW_ERR_INVALID, "node2vec bias needs a walk's previous vertex");
+        uint64_t m = 0;
+        for (int i = 0; i < 3; ++i) m = bias->n2v_mult[i] > m ? bias->n2v_mult[i] : m;
+        if ((uint64_t)g->max_weight * m > 0xFFFFFFFFull)
+            return fail(CSAW_ERR_OVERFLOW,
+                        "node2vec bias max_weight (%u) * max multiplier (%llu) does not fit in 32 bits",
+                        g->max_weight, (unsigned long long)m);
+        break;
+    }
+    default:
+        return fail(CSAW_ERR_INVALID, "unknown bias kind %d", kind);
+    }
+    *kind_out = kind;
+    return CSAW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Validation and derived arrays.  One warp per row; flags collect violations.
+enum : uint32_t {
+    BAD_OFFSET_ORDER = 1u,
+    BAD_COLUMN_RANGE = 2u,
+    BAD_ROW_ORDER = 4u,
+    BAD_ROW_LENGTH = 8u,
+    BAD_ENDS = 16u,
+};
+
+__global__ void validate_kernel(const uint64_t* __restrict__ off, const uint32_t* __restrict__ col,
+                                const uint32_t* __restrict__ w, uint32_t V, uint64_t E,
+                                uint32_t* __restrict__ deg, uint32_t* __restrict__ flags,
+                                uint32_t* __restrict__ max_deg, uint32_t* __restrict__ max_w)
+{
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    uint32_t local_flags = 0, local_maxw = 0, local_maxd = 0;
+    if (warp == 0 && lane == 0) {
+        if (off[0] != 0 || off[V] != E) local_flags |= BAD_ENDS;
+    }
+    for (uint64_t v = warp; v < V; v += nwarps) {
+        const uint64_t beg = off[v], end = off[v + 1];
+        if (end < beg || end > E) {
+            local_flags |= BAD_OFFSET_ORDER;
+            if (lane == 0) deg[v] = 0;
+            continue;
+        }
+        const uint64_t d = end - beg;
+        if (d > 0xFFFFFFFFull) local_flags |= BAD_ROW_LENGTH;
+        if (lane == 0) deg[v] = (uint32_t)(d > 0xFFFFFFFFull ? 0xFFFFFFFFull : d);
+        if (d > local_maxd) local_maxd = (uint32_t)(d > 0xFFFFFFFFull ? 0xFFFFFFFFull : d);
+        for (uint64_t e = beg + lane; e < end; e += 32) {
+            const uint32_t c = col[e];
+            if (c >= V) local_flags |= BAD_COLUMN_RANGE;
+            if (e + 1 < end && col[e + 1] <= c) local_flags |= BAD_ROW_ORDER;
+            if (w) local_maxw = max(local_maxw, w[e]);
+        }
+    }
+    local_flags = __reduce_or_sync(CSAW_FULL_MASK, local_flags);
+    local_maxw = __reduce_max_sync(CSAW_FULL_MASK, local_maxw);
+    local_maxd = __reduce_max_sync(CSAW_FULL_MASK, local_maxd);
+    if (lane == 0) {
+        if (local_flags) atomicOr(flags, local_flags);
+        atomicMax(max_w, local_maxw);
+        atomicMax(max_deg, local_maxd);
+    }
+}
+
+}  // namespace csaw
+
+using namespace csaw;
+
+extern "C" const char* csaw_last_error(void) { return g_last_error; }
+
+extern "C" uint32_t csaw_version(void) { return 10000u; }
+
+extern "C" csaw_status csaw_graph_destroy(csaw_graph* g)
+{
+    clear_error();
+    if (!g) return CSAW_OK;
+    cudaFree(g->off);
+    cudaFree(g->col);
+    cudaFree(g->w);
+    cudaFree(g->deg);
+    delete g;
+    return CSAW_OK;
+}
+
+extern "C" csaw_status csaw_graph_create(const uint64_t* row_offsets, uint32_t n_vertices,
+                                         const uint32_t* cols, const uint32_t* weights,
+                                         uint64_t n_edges, int mem_kind, void* stream,
+                                         csaw_graph** out)
+{
+    clear_error();
+    if (!out) return fail(CSAW_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!row_offsets || (n_edges > 0 && !cols))
+        return fail(CSAW_ERR_INVALID, "row_offsets/cols is NULL");
+    if (n_vertices == 0) return fail(CSAW_ERR_INVALID, "graph has no vertices");
+    if (n_vertices == 0xFFFFFFFFu) return fail(CSAW_ERR_INVALID, "vertex id 0xFFFFFFFF is reserved");
+    if (mem_kind != CSAW_MEM_HOST && mem_kind != CSAW_MEM_DEVICE)
+        return fail(CSAW_ERR_INVALID, "bad mem_kind %d", mem_kind);
+    if (mem_kind == CSAW_MEM_HOST) {
+        if (row_offsets[0] != 0 || row_offsets[n_vertices] != n_edges)
+            return fail(CSAW_ERR_INVALID, "row_offsets must start at 0 and end at n_edges");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    csaw_graph* g = new (std::nothrow) csaw_graph();
+    if (!g) return fail(CSAW_ERR_NOMEM, "host allocation failed");
+    CSAW_CUDA(cudaGetDevice(&g->device));
+    CSAW_CUDA(cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, g->device));
+    {
+        // Keep freed stream-ordered allocations in the device's pool instead of
+        // returning them at every synchronisation: calls reuse their buffers.
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, g->device) == cudaSuccess) {
+            uint64_t keep = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+    }
+    g->V = n_vertices;
+    g->E = n_edges;
+    const size_t off_b = sizeof(uint64_t) * ((size_t)n_vertices + 1);
+    const size_t col_b = sizeof(uint32_t) * (size_t)n_edges;
+    const size_t deg_b = sizeof(uint32_t) * (size_t)n_vertices;
+    cudaError_t e = cudaMalloc(&g->off, off_b);
+    if (e == cudaSuccess) e = cudaMalloc(&g->col, col_b ? col_b : 16);
+    if (e == cudaSuccess && weights) e = cudaMalloc(&g->w, col_b ? col_b : 16);
+    if (e == cudaSuccess) e = cudaMalloc(&g->deg, deg_b);
+    if (e != cudaSuccess) {
+        csaw_graph_destroy(g);
+        return cuda_fail(e, "cudaMalloc(graph)");
+    }
+    g->device_bytes = off_b + col_b + (weights ? col_b : 0) + deg_b;
+    const cudaMemcpyKind kind = mem_kind == CSAW_MEM_HOST ? cudaMemcpyHostToDevice
+                                                          : cudaMemcpyDeviceToDevice;
+    e = cudaMemcpyAsync(g->off, row_offsets, off_b, kind, s);
+    if (e == cudaSuccess && col_b) e = cudaMemcpyAsync(g->col, cols, col_b, kind, s);
+    if (e == cudaSuccess && weights && col_b) e = cudaMemcpyAsync(g->w, weights, col_b, kind, s);
+    uint32_t* d_stat = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&d_stat, 4 * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_stat, 0, 4 * sizeof(uint32_t), s);
+    if (e == cudaSuccess) {
+        const int threads = 256;
+        const uint64_t warps_needed = n_vertices;
+        uint64_t blocks = (warps_needed * 32 + threads - 1) / threads;
+        const uint64_t cap = (uint64_t)g->sm_count * 16;
+        if (blocks > cap) blocks = cap;
+        validate_kernel<<<(unsigned)blocks, threads, 0, s>>>(g->off, g->col, g->w, n_vertices, n_edges,
+                                                             g->deg, d_stat, d_stat + 1, d_stat + 2);
+        e = cudaGetLastError();
+    }
+    uint32_t h_stat[4] = {0, 0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_stat, d_stat, sizeof(h_stat), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_stat);
+    if (e != cudaSuccess) {
+        csaw_graph_destroy(g);
+        return cuda_fail(e, "graph upload/validation");
+    }
+    if (h_stat[0]) {
+        csaw_graph_destroy(g);
+        return fail(CSAW_ERR_INVALID, "invalid CSR (flags 0x%x: 1 offsets, 2 column range, "
+                    "4 row order/duplicates, 8 row length, 16 ends)", h_stat[0]);
+    }
+    g->max_degree = h_stat[1];
+    g->max_weight = weights ? h_stat[2] : 1u;
+    *out = g;
+    return CSAW_OK;
+}
+
+extern "C" csaw_status csaw_graph_get_info(const csaw_graph* g, csaw_graph_info* out)
+{
+    clear_error();
+    if (!g || !out) return fail(CSAW_ERR_INVALID, "NULL argument");
+    out->n_vertices = g->V;
+    out->n_edges = g->E;
+    out->max_degree = g->max_degree;
+    out->max_weight = g->max_weight;
+    out->device_bytes = g->device_bytes;
+    return CSAW_OK;
+}

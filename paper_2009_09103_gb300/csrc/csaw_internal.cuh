@@ -1,0 +1,136 @@
+// csaw_internal.cuh -- shared pieces of libcsaw's CUDA translation units.
+//
+// Device-side random numbers, integer draw mapping, warp collectives, the
+// graph object and error plumbing.  Everything here is written for sm_103a.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "csaw.h"
+
+#define CSAW_FULL_MASK 0xFFFFFFFFu
+
+// ---------------------------------------------------------------------------
+// Graph: CSR resident in HBM (uint64 offsets, uint32 columns and weights) and
+// the derived uint32 degree array used by the neighbour-degree bias.
+struct csaw_graph {
+    uint32_t V = 0;
+    uint64_t E = 0;
+    uint64_t* off = nullptr;   // [V+1]
+    uint32_t* col = nullptr;   // [E], rows strictly ascending
+    uint32_t* w = nullptr;     // [E] or nullptr (all ones)
+    uint32_t* deg = nullptr;   // [V]
+    uint32_t max_degree = 0;
+    uint32_t max_weight = 1;
+    uint64_t device_bytes = 0;
+    int device = 0;
+    int sm_count = 0;
+};
+
+// ---------------------------------------------------------------------------
+// Errors: every entry point returns a csaw_status and leaves a message in a
+// thread-local buffer.
+namespace csaw {
+
+csaw_status fail(csaw_status st, const char* fmt, ...);
+csaw_status cuda_fail(cudaError_t err, const char* what);
+void clear_error();
+
+#define CSAW_CUDA(call)                                                   \
+    do {                                                                  \
+        cudaError_t _e = (call);                                          \
+        if (_e != cudaSuccess) return ::csaw::cuda_fail(_e, #call);       \
+    } while (0)
+
+#define CSAW_TRY(expr)                                                    \
+    do {                                                                  \
+        csaw_status _s = (expr);                                          \
+        if (_s != CSAW_OK) return _s;                                     \
+    } while (0)
+
+// Stream-ordered device allocation (CUDA's pool allocator).
+csaw_status dalloc(void** p, size_t bytes, cudaStream_t s);
+void dfree(void* p, cudaStream_t s);
+
+// Validation of a bias argument against a graph; fills the effective kind
+// (EDGE_WEIGHT on a graph without weights is UNIFORM).
+csaw_status check_bias(const csaw_graph* g, const csaw_bias* bias, bool allow_node2vec,
+                       int* kind_out);
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC11): ten rounds, each two
+// 32x32 -> 64-bit products of counter words 0 and 2 with the round
+// multipliers, the high halves xored with the other counter words and the
+// key; the key advances by the Weyl increments between rounds.
+// Key = {lo32(seed), hi32(seed)}; counter = {attempt, vertex, layer, instance};
+// the 64-bit draw is out1 << 32 | out0.
+__device__ __forceinline__ uint64_t philox_draw(uint32_t k0, uint32_t k1, uint32_t attempt,
+                                                uint32_t vertex, uint32_t layer,
+                                                uint32_t instance)
+{
+    uint32_t c0 = attempt, c1 = vertex, c2 = layer, c3 = instance;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo0 = 0xD2511F53u * c0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t lo1 = 0xCD9E8D57u * c2;
+        c0 = hi1 ^ c1 ^ k0;
+        c1 = lo1;
+        c2 = hi0 ^ c3 ^ k1;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return ((uint64_t)c1 << 32) | (uint64_t)c0;
+}
+
+// x = floor(r * T / 2^64), the draw placed in [0, T).
+__device__ __forceinline__ uint64_t scale_draw(uint64_t r, uint64_t total)
+{
+    return __umul64hi(r, total);
+}
+
+// ---------------------------------------------------------------------------
+// Warp collectives on 64-bit values.
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(CSAW_FULL_MASK, x, o);
+    return x;
+}
+
+__device__ __forceinline__ uint64_t warp_inclusive_scan_u64(uint64_t x, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(CSAW_FULL_MASK, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt()
+{
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Membership of u in the sorted neighbour list col[beg, end) (node2vec's
+// "is u adjacent to the previous vertex").
+__device__ __forceinline__ bool sorted_contains(const uint32_t* __restrict__ col, uint64_t beg,
+                                                uint64_t end, uint32_t u)
+{
+    const uint64_t row_end = end;
+    while (beg < end) {
+        const uint64_t mid = beg + ((end - beg) >> 1);
+        const uint32_t c = __ldg(col + mid);
+        if (c < u) beg = mid + 1; else end = mid;
+    }
+    return beg < row_end && __ldg(col + beg) == u;
+}
+
+}  // namespace csaw

@@ -1,0 +1,176 @@
+"""Walks on the GPU through the C ABI, bit-exact against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2009_09103_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+NONE = 0xFFFFFFFF
+
+
+@pytest.fixture(scope="module")
+def csaw():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2009_09103_gb300 import build
+    build.build()
+    from paper_2009_09103_gb300 import csaw as c
+    return c
+
+
+def gpu_walk(csaw, g, starts, length, bias, seed, mult=(1, 1, 1)):
+    import torch
+    G = csaw.Graph(g.off, g.col, g.w)
+    s = torch.from_numpy(np.asarray(starts, dtype=np.uint32).view(np.int32)).cuda()
+    path = csaw.walk(G, s, length, bias, seed, mult)
+    torch.cuda.synchronize()
+    out = path.cpu().numpy().view(np.uint32)
+    G.close()
+    return out
+
+
+def small_graphs():
+    out = {}
+    und = [(0, 1, 1), (0, 2, 1), (1, 2, 1), (0, 3, 3)]
+    e = [(a, b) for a, b, _ in und] + [(b, a) for a, b, _ in und]
+    out["triangle_pendant"] = inputs.csr_from_edges(4, e, [w for *_, w in und] * 2)
+    out["dead_end_zero_w"] = inputs.csr_from_edges(5, [(0, 1), (1, 2), (3, 4)], [1, 1, 0])
+    out["rmat_s8"] = inputs.rmat_csr(8, 8, 40, 1)
+    out["rmat_s12"] = inputs.rmat_csr(12, 16, 100, 12)
+    return out
+
+
+BIASES = [("uniform", (1, 1, 1)), ("edge_weight", (1, 1, 1)), ("neighbor_degree", (1, 1, 1)),
+          ("node2vec", (1, 2, 4)), ("node2vec", (3, 1, 2))]
+
+
+@pytest.mark.parametrize("gname", ["triangle_pendant", "dead_end_zero_w", "rmat_s8", "rmat_s12"])
+@pytest.mark.parametrize("bias,mult", BIASES)
+def test_walk_bit_exact_small(csaw, gname, bias, mult):
+    g = small_graphs()[gname]
+    starts = np.concatenate([np.arange(g.V, dtype=np.uint32),
+                             inputs.uniform_vertices(300, g.V, 3)])
+    ref = oracle.walk(g, starts, 25, bias, 1234, mult=mult)
+    got = gpu_walk(csaw, g, starts, 25, bias, 1234, mult)
+    assert np.array_equal(got, ref)
+
+
+def test_walk_hubs_many_chunks(csaw):
+    # A star whose centre has more neighbours than fit in one chunk table slot
+    # per round (forces the multi-round-per-chunk path), plus ragged tails.
+    rng = np.random.default_rng(7)
+    for d in (1, 31, 32, 33, 255, 256, 257, 8191, 70001, 300007):
+        edges = [(0, j + 1) for j in range(d)] + [(j + 1, 0) for j in range(d)]
+        w = list(rng.integers(1, 2**20, size=d)) + [1] * d
+        g = inputs.csr_from_edges(d + 1, edges, w)
+        starts = np.zeros(64, dtype=np.uint32)
+        for bias in ("edge_weight", "uniform"):
+            ref = oracle.walk(g, starts, 3, bias, 99)
+            got = gpu_walk(csaw, g, starts, 3, bias, 99)
+            assert np.array_equal(got, ref), (d, bias)
+
+
+def test_walk_host_buffers_match_device(csaw):
+    g = inputs.rmat_csr(12, 16, 100, 12)
+    starts = inputs.uniform_vertices(5000, g.V, 2)
+    G = csaw.Graph(g.off, g.col, g.w)
+    host = csaw.walk(G, starts, 30, "edge_weight", 5)
+    dev = gpu_walk(csaw, g, starts, 30, "edge_weight", 5)
+    assert np.array_equal(host, dev)
+    assert np.array_equal(host, oracle.walk(g, starts, 30, "edge_weight", 5))
+
+
+def test_walk_errors(csaw):
+    g = inputs.rmat_csr(8, 8, 40, 1)
+    G = csaw.Graph(g.off, g.col, g.w)
+    with pytest.raises(csaw.CsawError) as e:
+        csaw.walk(G, np.array([g.V], dtype=np.uint32), 3, "edge_weight", 1)
+    assert e.value.status == csaw.ERR_INVALID
+    with pytest.raises(csaw.CsawError) as e:
+        csaw.walk(G, np.array([0], dtype=np.uint32), 3, "node2vec", 1, mult=(1, 2**30, 4))
+    assert e.value.status == csaw.ERR_OVERFLOW
+    with pytest.raises(csaw.CsawError) as e:
+        csaw.walk(G, np.array([0], dtype=np.uint32), 3, csaw.make_bias(9), 1)
+    assert e.value.status == csaw.ERR_INVALID
+    # malformed CSR: unsorted row
+    with pytest.raises(csaw.CsawError) as e:
+        csaw.Graph(np.array([0, 2, 2], dtype=np.uint64), np.array([1, 0], dtype=np.uint32))
+    assert e.value.status == csaw.ERR_INVALID
+    with pytest.raises(csaw.CsawError) as e:
+        csaw.Graph(np.array([0, 1, 1], dtype=np.uint64), np.array([5], dtype=np.uint32))
+    assert e.value.status == csaw.ERR_INVALID
+    # empty walk is fine
+    assert csaw.walk(G, np.zeros(0, dtype=np.uint32), 3, "edge_weight", 1).shape == (0, 4)
+
+
+def _adjacent_all(torch, g, path_t):
+    """Every consecutive non-sentinel pair is an edge; sentinels only follow
+    dead ends.  Edge keys src<<32|dst are sorted in CSR order."""
+    dev = path_t.device
+    off = torch.from_numpy(g.off.astype(np.int64)).to(dev)
+    col = torch.from_numpy(g.col.astype(np.int64)).to(dev)
+    src = torch.repeat_interleave(torch.arange(g.V, device=dev), off[1:] - off[:-1])
+    keys = (src << 32) | col
+    p = path_t.to(torch.int64) & 0xFFFFFFFF
+    a, b = p[:, :-1], p[:, 1:]
+    real = b != NONE
+    q = ((a << 32) | b)[real]
+    pos = torch.searchsorted(keys, q).clamp(max=keys.numel() - 1)
+    ok_edges = bool((keys[pos] == q).all())
+    # a sentinel after a real vertex only at a dead end (degree 0 for edge weights >= 1)
+    stop = (~real) & (a != NONE)
+    deg = off[1:] - off[:-1]
+    ok_stops = bool((deg[a[stop]] == 0).all())
+    after_none = (a == NONE) & real
+    return ok_edges, ok_stops, not bool(after_none.any())
+
+
+def test_walk_rmat_s20_full_size(csaw):
+    """The weighted-walk workload at full size: RMAT s20 ef16, one walker per
+    vertex, length 80, in the launch configuration the benchmark times.
+    Stratified walker subset bit-exact against the oracle; invariants on all."""
+    import torch
+    wl = inputs.workload_walk_s20()
+    g = wl.graph
+    G = csaw.Graph(g.off, g.col, g.w)
+    s = torch.from_numpy(wl.starts.view(np.int32)).cuda()
+    path = csaw.walk(G, s, wl.length, wl.bias, wl.rng_seed)
+    torch.cuda.synchronize()
+    ok_e, ok_s, ok_n = _adjacent_all(torch, g, path)
+    assert ok_e and ok_s and ok_n
+    # stratified subset: walkers starting at low, mid and hub degrees, plus the ends
+    deg = np.diff(g.off)
+    order = np.argsort(deg, kind="stable")
+    pick = np.unique(np.concatenate([order[:200], order[len(order) // 2: len(order) // 2 + 200],
+                                     order[-300:], np.arange(100), np.arange(g.V - 100, g.V),
+                                     inputs.uniform_vertices(400, g.V, 77).astype(np.int64)]))
+    ids = pick.astype(np.uint64)
+    ref = oracle.walk(g, wl.starts[pick], wl.length, wl.bias, wl.rng_seed, walker_ids=ids)
+    got = path[torch.from_numpy(pick).cuda()].cpu().numpy().view(np.uint32)
+    assert np.array_equal(got, ref)
+    G.close()
+
+
+def test_walk_node2vec_s22_subset(csaw):
+    """node2vec p=2, q=0.5 on RMAT s22 ef32 at full size; stratified subset
+    bit-exact against the oracle."""
+    import torch
+    wl = inputs.workload_node2vec_s22()
+    g = wl.graph
+    G = csaw.Graph(g.off, g.col, g.w)
+    s = torch.from_numpy(wl.starts.view(np.int32)).cuda()
+    path = csaw.walk(G, s, wl.length, wl.bias, wl.rng_seed, wl.n2v_mult)
+    torch.cuda.synchronize()
+    ok_e, ok_s, ok_n = _adjacent_all(torch, g, path)
+    assert ok_e and ok_s and ok_n
+    deg = np.diff(g.off)
+    order = np.argsort(deg, kind="stable")
+    pick = np.unique(np.concatenate([order[-60:], order[len(order) // 2: len(order) // 2 + 60],
+                                     inputs.uniform_vertices(120, g.V, 5).astype(np.int64)]))
+    ref = oracle.walk(g, wl.starts[pick], wl.length, wl.bias, wl.rng_seed, mult=wl.n2v_mult,
+                      walker_ids=pick.astype(np.uint64))
+    got = path[torch.from_numpy(pick).cuda()].cpu().numpy().view(np.uint32)
+    assert np.array_equal(got, ref)
+    G.close()
