@@ -162,9 +162,11 @@ csaw_status csaw_walk(csaw_graph* g, const uint32_t* starts, uint64_t n_walkers,
  * The draws of frontier vertex v of instance i at layer l use vertex = v,
  * layer = l, instance = i.  Output edges are grouped by layer, then instance,
  * then source vertex ascending; each vertex's picks are in pick order.
- * seeds/inst_offsets live in mem_kind memory.  The result is returned in *out
- * and lives on the device; read it with csaw_sample_get_view or copy it with
- * csaw_sample_copy_edges, release it with csaw_result_free.
+ * seeds/inst_offsets live in mem_kind memory.  The call runs the layers on
+ * `stream` and waits on it once per layer (to size the next layer's buffers),
+ * so it returns with the result complete.  The result lives on the device;
+ * read it with csaw_sample_get_view or copy it with csaw_sample_copy_edges,
+ * release it with csaw_result_free.
  * Errors: CSAW_ERR_INVALID, CSAW_ERR_NOMEM, CSAW_ERR_CUDA. */
 csaw_status csaw_sample(csaw_graph* g, const uint32_t* seeds, const uint64_t* inst_offsets,
                         uint32_t n_instances, uint32_t depth, const uint32_t* fanout,
@@ -176,19 +178,25 @@ typedef struct {
     uint32_t n_instances;
     uint64_t n_edges;
     /* host, depth*n_instances + 1 entries: edges of (layer l, instance i) are
-     * [edge_offsets[l*n_instances + i], edge_offsets[l*n_instances + i + 1]) */
+     * [edge_offsets[l*n_instances + i], edge_offsets[l*n_instances + i + 1])
+     * in one numbering that runs over all layers */
     const uint64_t* edge_offsets;
-    /* host, depth*n_instances entries: frontier size of (layer l, instance i) */
+    /* host, depth*n_instances entries: frontier size of (layer l, instance i)
+     * (layer 0 = the instance's distinct seeds) */
     const uint64_t* frontier_sizes;
-    const uint32_t* src;   /* device, n_edges: sampled edge sources */
-    const uint32_t* dst;   /* device, n_edges: sampled edge destinations */
+    /* host arrays of `depth` device pointers.  Layer l's edges are
+     * src[l][j], dst[l][j] for j < edge_offsets[(l+1)*n_instances] -
+     * edge_offsets[l*n_instances], in the order described above. */
+    const uint32_t* const* src;
+    const uint32_t* const* dst;
 } csaw_sample_view;
 
-/* Wait for the result's stream to reach the end of the sampling call and fill
- * *view.  The pointers stay valid until csaw_result_free. */
+/* Fill *view.  csaw_sample returns once its result is complete, so this does
+ * not wait.  The pointers stay valid until csaw_result_free. */
 csaw_status csaw_sample_get_view(csaw_sample_result* r, csaw_sample_view* view);
 
-/* Copy the sampled edges to host arrays of n_edges entries each (waits). */
+/* Copy the sampled edges of all layers, concatenated in layer order, to host
+ * arrays of n_edges entries each.  Synchronous. */
 csaw_status csaw_sample_copy_edges(csaw_sample_result* r, uint32_t* src, uint32_t* dst);
 
 /* Release a result returned by this library.  NULL is accepted. */

@@ -48,7 +48,7 @@ class SampleView(ctypes.Structure):
                 ("n_edges", ctypes.c_uint64),
                 ("edge_offsets", ctypes.POINTER(ctypes.c_uint64)),
                 ("frontier_sizes", ctypes.POINTER(ctypes.c_uint64)),
-                ("src", ctypes.c_void_p), ("dst", ctypes.c_void_p)]
+                ("src", ctypes.POINTER(ctypes.c_void_p)), ("dst", ctypes.POINTER(ctypes.c_void_p))]
 
 
 def lib():
@@ -191,7 +191,7 @@ class SampleResult:
     n_edges: int
     edge_offsets: np.ndarray      # uint64[depth*n_instances+1]
     frontier_sizes: np.ndarray    # uint64[depth*n_instances]
-    src: object                   # device tensor or host array
+    src: object                   # host array (all layers), or list of per-layer device tensors
     dst: object
 
 
@@ -240,9 +240,13 @@ def sample(g: Graph, seeds, inst_offsets, fanout, bias="edge_weight", seed: int 
         dst = np.empty(v.n_edges, dtype=np.uint32)
         _check(L.csaw_sample_copy_edges(out, _ptr(src), _ptr(dst)))
         return SampleResult(v.depth, v.n_instances, v.n_edges, eo, fs, src, dst)
-    import torch
-    res = SampleResult(v.depth, v.n_instances, v.n_edges, eo, fs,
-                       _wrap_device(v.src, v.n_edges, holder), _wrap_device(v.dst, v.n_edges, holder))
+    # per-layer device arrays (torch int32 views of library-owned memory)
+    srcs, dsts = [], []
+    for l in range(v.depth):
+        n_l = int(eo[(l + 1) * v.n_instances] - eo[l * v.n_instances])
+        srcs.append(_wrap_device(v.src[l], n_l, holder))
+        dsts.append(_wrap_device(v.dst[l], n_l, holder))
+    res = SampleResult(v.depth, v.n_instances, v.n_edges, eo, fs, srcs, dsts)
     res._holder = holder
     return res
 

@@ -97,12 +97,13 @@ enum : uint32_t {
 __global__ void validate_kernel(const uint64_t* __restrict__ off, const uint32_t* __restrict__ col,
                                 const uint32_t* __restrict__ w, uint32_t V, uint64_t E,
                                 uint32_t* __restrict__ deg, uint32_t* __restrict__ flags,
-                                uint32_t* __restrict__ max_deg, uint32_t* __restrict__ max_w)
+                                uint32_t* __restrict__ max_deg, uint32_t* __restrict__ max_w,
+                                uint32_t* __restrict__ min_w)
 {
     const int lane = threadIdx.x & 31;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    uint32_t local_flags = 0, local_maxw = 0, local_maxd = 0;
+    uint32_t local_flags = 0, local_maxw = 0, local_maxd = 0, local_minw = 0xFFFFFFFFu;
     if (warp == 0 && lane == 0) {
         if (off[0] != 0 || off[V] != E) local_flags |= BAD_ENDS;
     }
@@ -121,17 +122,35 @@ __global__ void validate_kernel(const uint64_t* __restrict__ off, const uint32_t
             const uint32_t c = col[e];
             if (c >= V) local_flags |= BAD_COLUMN_RANGE;
             if (e + 1 < end && col[e + 1] <= c) local_flags |= BAD_ROW_ORDER;
-            if (w) local_maxw = max(local_maxw, w[e]);
+            if (w) {
+                local_maxw = max(local_maxw, w[e]);
+                local_minw = min(local_minw, w[e]);
+            }
         }
     }
     local_flags = __reduce_or_sync(CSAW_FULL_MASK, local_flags);
     local_maxw = __reduce_max_sync(CSAW_FULL_MASK, local_maxw);
     local_maxd = __reduce_max_sync(CSAW_FULL_MASK, local_maxd);
+    local_minw = __reduce_min_sync(CSAW_FULL_MASK, local_minw);
     if (lane == 0) {
         if (local_flags) atomicOr(flags, local_flags);
         atomicMax(max_w, local_maxw);
         atomicMax(max_deg, local_maxd);
+        atomicMin(min_w, local_minw);
     }
+}
+
+// Whether some edge points at a vertex with no neighbours (a zero
+// neighbour-degree bias).  Runs after validation has filled deg.
+__global__ void zero_target_kernel(const uint32_t* __restrict__ col, const uint32_t* __restrict__ deg,
+                                   uint64_t E, uint32_t* __restrict__ flag)
+{
+    uint32_t found = 0;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
+         e += (uint64_t)gridDim.x * blockDim.x)
+        found |= deg[col[e]] == 0;
+    found = __reduce_or_sync(CSAW_FULL_MASK, found);
+    if ((threadIdx.x & 31) == 0 && found) atomicOr(flag, 1u);
 }
 
 }  // namespace csaw
@@ -175,8 +194,15 @@ extern "C" csaw_status csaw_graph_create(const uint64_t* row_offsets, uint32_t n
     cudaStream_t s = (cudaStream_t)stream;
     csaw_graph* g = new (std::nothrow) csaw_graph();
     if (!g) return fail(CSAW_ERR_NOMEM, "host allocation failed");
-    CSAW_CUDA(cudaGetDevice(&g->device));
-    CSAW_CUDA(cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, g->device));
+    {
+        cudaError_t e0 = cudaGetDevice(&g->device);
+        if (e0 == cudaSuccess)
+            e0 = cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, g->device);
+        if (e0 != cudaSuccess) {
+            delete g;
+            return cuda_fail(e0, "device query");
+        }
+    }
     {
         // Keep freed stream-ordered allocations in the device's pool instead of
         // returning them at every synchronisation: calls reuse their buffers.
@@ -206,8 +232,9 @@ extern "C" csaw_status csaw_graph_create(const uint64_t* row_offsets, uint32_t n
     if (e == cudaSuccess && col_b) e = cudaMemcpyAsync(g->col, cols, col_b, kind, s);
     if (e == cudaSuccess && weights && col_b) e = cudaMemcpyAsync(g->w, weights, col_b, kind, s);
     uint32_t* d_stat = nullptr;
-    if (e == cudaSuccess) e = cudaMalloc(&d_stat, 4 * sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_stat, 0, 4 * sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = cudaMalloc(&d_stat, 8 * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_stat, 0, 8 * sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_stat + 3, 0xFF, sizeof(uint32_t), s);
     if (e == cudaSuccess) {
         const int threads = 256;
         const uint64_t warps_needed = n_vertices;
@@ -215,10 +242,22 @@ extern "C" csaw_status csaw_graph_create(const uint64_t* row_offsets, uint32_t n
         const uint64_t cap = (uint64_t)g->sm_count * 16;
         if (blocks > cap) blocks = cap;
         validate_kernel<<<(unsigned)blocks, threads, 0, s>>>(g->off, g->col, g->w, n_vertices, n_edges,
-                                                             g->deg, d_stat, d_stat + 1, d_stat + 2);
+                                                             g->deg, d_stat, d_stat + 1, d_stat + 2,
+                                                             d_stat + 3);
         e = cudaGetLastError();
     }
-    uint32_t h_stat[4] = {0, 0, 0, 0};
+    uint32_t h_flags = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_flags, d_stat, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && h_flags == 0 && n_edges > 0) {
+        // columns are known to be in range now
+        uint64_t blocks = (n_edges + 255) / 256;
+        const uint64_t cap = (uint64_t)g->sm_count * 16;
+        if (blocks > cap) blocks = cap;
+        zero_target_kernel<<<(unsigned)blocks, 256, 0, s>>>(g->col, g->deg, n_edges, d_stat + 4);
+        e = cudaGetLastError();
+    }
+    uint32_t h_stat[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (e == cudaSuccess) e = cudaMemcpyAsync(h_stat, d_stat, sizeof(h_stat), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(d_stat);
@@ -233,6 +272,8 @@ extern "C" csaw_status csaw_graph_create(const uint64_t* row_offsets, uint32_t n
     }
     g->max_degree = h_stat[1];
     g->max_weight = weights ? h_stat[2] : 1u;
+    g->min_weight = (weights && n_edges > 0) ? h_stat[3] : 1u;
+    g->zero_degree_target = h_stat[4] != 0;
     *out = g;
     return CSAW_OK;
 }

@@ -24,6 +24,8 @@ struct csaw_graph {
     uint32_t* deg = nullptr;   // [V]
     uint32_t max_degree = 0;
     uint32_t max_weight = 1;
+    uint32_t min_weight = 1;            // 0 if some edge weight is zero
+    bool zero_degree_target = false;    // some edge points at a vertex without neighbours
     uint64_t device_bytes = 0;
     int device = 0;
     int sm_count = 0;
@@ -53,6 +55,20 @@ void clear_error();
 // Stream-ordered device allocation (CUDA's pool allocator).
 csaw_status dalloc(void** p, size_t bytes, cudaStream_t s);
 void dfree(void* p, cudaStream_t s);
+
+// Device-wide exclusive scan of n uint32 (n read from *n_dev, n <= n_max):
+// out[i] = in[0] + ... + in[i-1] for i <= n; *total_out (device, optional)
+// receives out[n].  scratch: scan_scratch_bytes(n_max).
+size_t scan_scratch_bytes(uint64_t n_max);
+csaw_status scan_u32(const uint32_t* in, uint64_t* out, const uint64_t* n_dev, uint64_t n_max,
+                     void* scratch, uint64_t* total_out, cudaStream_t s);
+
+// Stable LSD radix sort of n uint64 keys on their low `bits` bits (n read
+// from *n_dev, n <= n_max < 2^32).  keys and alt hold n_max keys; *result is
+// the one holding the sorted keys.  scratch: sort_scratch_bytes(n_max).
+size_t sort_scratch_bytes(uint64_t n_max);
+csaw_status radix_sort_u64(uint64_t* keys, uint64_t* alt, const uint64_t* n_dev, uint64_t n_max,
+                           int bits, int sm_count, void* scratch, cudaStream_t s, uint64_t** result);
 
 // Validation of a bias argument against a graph; fills the effective kind
 // (EDGE_WEIGHT on a graph without weights is UNIFORM).
