@@ -202,6 +202,44 @@ csaw_status csaw_sample_copy_edges(csaw_sample_result* r, uint32_t* src, uint32_
 /* Release a result returned by this library.  NULL is accepted. */
 void csaw_result_free(void* result);
 
+/* ---------------------------------------------------------------- no allocation */
+
+/* One selection layer that allocates no device memory.
+ *
+ * The paper has no counterpart to this call.  It exists for callers that
+ * cannot allocate device memory while they run: code living inside another
+ * framework's fixed memory budget, runtimes without a device allocator, or a
+ * host thread that must not touch the allocator.  It runs the selection of
+ * one sampling layer -- the same kernels and draws as csaw_sample's layer
+ * `layer` -- for n given (vertex, instance) pairs, with every temporary in a
+ * fixed device array of CSAW_NOALLOC_SCRATCH_BYTES that the library holds on
+ * every GPU that loads it, until the process exits.
+ *   vertices, instances  device uint32[n]: entry e selects from the
+ *                neighbours of vertices[e] with the draws of instance
+ *                instances[e] (attempt keys (a, vertex, layer, instance))
+ *   k            picks per vertex (CSAW_FANOUT_ALL for all)
+ *   out_src, out_dst  device uint32[capacity]: entry e's picks are at
+ *                [out_offsets[e], out_offsets[e+1]), in pick order
+ *   capacity     must be at least n * min(k, max degree)
+ *   out_offsets  device uint64[n + 1] (exclusive scan of the pick counts)
+ * Limits: n <= CSAW_NOALLOC_MAX_ITEMS; a graph whose maximum degree needs more
+ * than the scratch left for one CTA's cumulative array (about 5.5 million
+ * neighbours) is rejected.  Errors: CSAW_ERR_INVALID (limits, NULL arrays,
+ * a vertex outside the graph, node2vec bias), CSAW_ERR_CUDA.
+ * The call issues work on `stream` and waits once, after checking the
+ * vertices, before it launches the selection.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine.  The first call made on a device
+ * looks up the array's device address there; make that first call before
+ * any stream capture.  Every call shares the one array and clears the parts
+ * that must start at zero: calls that overlap on the GPU race on it, so
+ * serialise them (one stream, one host thread at a time). */
+#define CSAW_NOALLOC_MAX_ITEMS (1u << 20)
+#define CSAW_NOALLOC_SCRATCH_BYTES (64ull << 20)
+csaw_status csaw_select_noalloc(csaw_graph* g, const uint32_t* vertices, const uint32_t* instances,
+                                uint32_t n, uint32_t k, uint32_t layer, const csaw_bias* bias,
+                                uint64_t rng_seed, uint32_t* out_src, uint32_t* out_dst,
+                                uint64_t capacity, uint64_t* out_offsets, void* stream);
+
 /* ---------------------------------------------------------------- misc */
 
 /* Message of the last failed call on this thread ("" if none). */

@@ -30,6 +30,7 @@
 // the same choice as searching a recomputed prefix sum.
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -901,4 +902,161 @@ extern "C" csaw_status csaw_sample_copy_edges(csaw_sample_result* r, uint32_t* s
 extern "C" void csaw_result_free(void* result)
 {
     delete (csaw_sample_result*)result;
+}
+
+// ---------------------------------------------------------------------------
+// One selection layer without any device allocation.
+//
+// Some callers cannot allocate device memory while they run this library:
+// code executing inside another framework's memory budget, allocator-less
+// embedded runtimes, or a host thread that must not contend on the device
+// allocator.  For them csaw_select_noalloc runs one layer of selection (the
+// count, scan and select kernels above) with every temporary placed in the
+// fixed device array below.  The array is a file-scope __device__ variable:
+// every GPU that loads this library holds its CSAW_NOALLOC_SCRATCH_BYTES until
+// the process exits.  All calls share it, so calls that overlap on the GPU
+// (different streams, or other host threads) race on it; the counters that
+// must start at zero are cleared by every call.
+
+namespace csaw {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[CSAW_NOALLOC_SCRATCH_BYTES];
+
+constexpr size_t NA_HEAD = 256;   // counters
+constexpr size_t NA_KEYS = NA_HEAD;
+constexpr size_t NA_CNT = NA_KEYS + sizeof(uint64_t) * CSAW_NOALLOC_MAX_ITEMS;
+constexpr size_t NA_WLIST = NA_CNT + sizeof(uint32_t) * CSAW_NOALLOC_MAX_ITEMS;
+constexpr size_t NA_CLIST = NA_WLIST + sizeof(uint32_t) * CSAW_NOALLOC_MAX_ITEMS;
+constexpr size_t NA_BSUM = NA_CLIST + sizeof(uint32_t) * CSAW_NOALLOC_MAX_ITEMS;
+constexpr size_t NA_HUB = (NA_BSUM + 8 * 1040 + 255) / 256 * 256;
+static_assert(NA_HUB < CSAW_NOALLOC_SCRATCH_BYTES, "scratch layout does not fit");
+
+// Host-side device addresses of the array, one per device, looked up on the
+// first call made with that device current.
+static std::mutex g_na_mutex;
+static void* g_na_ptr[256];
+
+static csaw_status noalloc_scratch(int device, unsigned char** out)
+{
+    if (device < 0 || device >= 256) return fail(CSAW_ERR_INVALID, "device ordinal %d", device);
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    if (!g_na_ptr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-allocation scratch)");
+        g_na_ptr[device] = p;
+    }
+    *out = (unsigned char*)g_na_ptr[device];
+    return CSAW_OK;
+}
+
+// keys[e] = instances[e] << vbits | vertices[e]; flags any vertex >= V.
+__global__ void noalloc_keys_kernel(const uint32_t* __restrict__ vertices,
+                                    const uint32_t* __restrict__ instances, uint32_t n, uint32_t V,
+                                    uint32_t vbits, uint64_t* __restrict__ keys, uint32_t* __restrict__ err)
+{
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const uint32_t v = vertices[e];
+        if (v >= V) atomicOr(err, 1u);
+        keys[e] = ((uint64_t)instances[e] << vbits) | (v < V ? v : 0u);
+    }
+}
+
+}  // namespace csaw
+
+extern "C" csaw_status csaw_select_noalloc(csaw_graph* g, const uint32_t* vertices,
+                                           const uint32_t* instances, uint32_t n, uint32_t k,
+                                           uint32_t layer, const csaw_bias* bias, uint64_t rng_seed,
+                                           uint32_t* out_src, uint32_t* out_dst, uint64_t capacity,
+                                           uint64_t* out_offsets, void* stream)
+{
+    clear_error();
+    if (!g) return fail(CSAW_ERR_INVALID, "graph is NULL");
+    int kind;
+    CSAW_TRY(check_bias(g, bias, false, &kind));
+    if (n > CSAW_NOALLOC_MAX_ITEMS)
+        return fail(CSAW_ERR_INVALID, "csaw_select_noalloc takes at most %u vertices per call, got %u",
+                    CSAW_NOALLOC_MAX_ITEMS, n);
+    if (!out_offsets) return fail(CSAW_ERR_INVALID, "out_offsets is NULL");
+    if (n > 0 && (!vertices || !instances || !out_src || !out_dst))
+        return fail(CSAW_ERR_INVALID, "NULL vertex, instance or output array");
+    if (k == 0) return fail(CSAW_ERR_INVALID, "k must be at least 1");
+    const uint64_t per = k < g->max_degree ? k : g->max_degree;
+    if (capacity < (uint64_t)n * per)
+        return fail(CSAW_ERR_INVALID, "capacity %llu is below n * min(k, max degree) = %llu",
+                    (unsigned long long)capacity, (unsigned long long)((uint64_t)n * per));
+    int device = 0;
+    CSAW_CUDA(cudaGetDevice(&device));
+    int sel_blocks = select_blocks(kind, g->sm_count);
+    if (g->max_degree > CTA_SMEM_DEG) {
+        const uint64_t slot = (uint64_t)g->max_degree * 8 + ((uint64_t)g->max_degree + 31) / 32 * 4;
+        const uint64_t slots = (CSAW_NOALLOC_SCRATCH_BYTES - NA_HUB) / slot;
+        if (slots == 0)
+            return fail(CSAW_ERR_INVALID, "graph max degree %u needs %llu scratch bytes per CTA; the "
+                        "no-allocation scratch holds %llu", g->max_degree, (unsigned long long)slot,
+                        (unsigned long long)(CSAW_NOALLOC_SCRATCH_BYTES - NA_HUB));
+        if ((uint64_t)sel_blocks > slots) sel_blocks = (int)slots;
+    }
+    unsigned char* base;
+    CSAW_TRY(noalloc_scratch(device, &base));
+    cudaStream_t s = (cudaStream_t)stream;
+    uint64_t* head = (uint64_t*)base;              // [0] n, [1] total, [2..5] items/counters, [6] err
+    uint64_t* d_n = head;
+    uint64_t* d_total = head + 1;
+    unsigned long long* d_items = (unsigned long long*)(head + 2);
+    uint32_t* d_err = (uint32_t*)(head + 6);
+    uint64_t* keys = (uint64_t*)(base + NA_KEYS);
+    uint32_t* cnt = (uint32_t*)(base + NA_CNT);
+    uint32_t* wlist = (uint32_t*)(base + NA_WLIST);
+    uint32_t* clist = (uint32_t*)(base + NA_CLIST);
+    void* bsum = base + NA_BSUM;
+    unsigned char* hub = base + NA_HUB;
+
+    const uint64_t n64 = n;
+    CSAW_CUDA(cudaMemsetAsync(head, 0, NA_HEAD, s));
+    CSAW_CUDA(cudaMemcpyAsync(d_n, &n64, sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+    const int vbits = bits_for(g->V - 1) > 0 ? bits_for(g->V - 1) : 1;
+    const uint64_t vmask = (1ull << vbits) - 1;
+    if (n) {
+        noalloc_keys_kernel<<<grid_for(n, 256, g->sm_count), 256, 0, s>>>(vertices, instances, n, g->V,
+                                                                          vbits, keys, d_err);
+        CSAW_CUDA(cudaGetLastError());
+        uint32_t h_err = 0;
+        CSAW_CUDA(cudaMemcpyAsync(&h_err, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        CSAW_CUDA(cudaStreamSynchronize(s));
+        if (h_err) return fail(CSAW_ERR_INVALID, "a vertex is not in the graph");
+    }
+    const bool zero_bias = (kind == CSAW_BIAS_EDGE_WEIGHT && g->min_weight == 0) ||
+                           (kind == CSAW_BIAS_NEIGHBOR_DEGREE && g->zero_degree_target);
+    CountParams cp;
+    cp.off = g->off; cp.col = g->col; cp.w = g->w; cp.deg = g->deg;
+    cp.fkeys = keys; cp.n_dev = (const unsigned long long*)d_n; cp.vmask = vmask; cp.k = k;
+    cp.zero_bias = zero_bias; cp.cnt = cnt; cp.warp_list = wlist; cp.cta_list = clist;
+    cp.n_items = d_items;
+    if (n) {
+        switch (kind) {
+        case CSAW_BIAS_UNIFORM: CSAW_TRY(launch_count<CSAW_BIAS_UNIFORM>(cp, n, g->sm_count, s)); break;
+        case CSAW_BIAS_EDGE_WEIGHT: CSAW_TRY(launch_count<CSAW_BIAS_EDGE_WEIGHT>(cp, n, g->sm_count, s)); break;
+        default: CSAW_TRY(launch_count<CSAW_BIAS_NEIGHBOR_DEGREE>(cp, n, g->sm_count, s)); break;
+        }
+    }
+    CSAW_TRY(scan_u32(cnt, out_offsets, d_n, n, bsum, d_total, s));
+    if (n) {
+        SelParams sp;
+        sp.off = g->off; sp.col = g->col; sp.w = g->w; sp.deg = g->deg;
+        sp.fkeys = keys; sp.vbits = vbits; sp.vmask = vmask; sp.k = k; sp.layer = layer;
+        sp.k0 = (uint32_t)rng_seed; sp.k1 = (uint32_t)(rng_seed >> 32);
+        sp.zero_bias = zero_bias; sp.pos = out_offsets; sp.warp_list = wlist; sp.cta_list = clist;
+        sp.n_items = d_items; sp.next = d_items + 2;
+        sp.out_src = out_src; sp.out_dst = out_dst; sp.out_cand = nullptr;
+        sp.scratch_S = (uint64_t*)hub;
+        sp.scratch_bits = (uint32_t*)(hub + (size_t)sel_blocks * g->max_degree * 8);
+        sp.scratch_stride = g->max_degree;
+        switch (kind) {
+        case CSAW_BIAS_UNIFORM: CSAW_TRY(launch_select<CSAW_BIAS_UNIFORM>(sp, sel_blocks, s)); break;
+        case CSAW_BIAS_EDGE_WEIGHT: CSAW_TRY(launch_select<CSAW_BIAS_EDGE_WEIGHT>(sp, sel_blocks, s)); break;
+        default: CSAW_TRY(launch_select<CSAW_BIAS_NEIGHBOR_DEGREE>(sp, sel_blocks, s)); break;
+        }
+    }
+    return CSAW_OK;
 }
