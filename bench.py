@@ -56,9 +56,9 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def traffic_record(kernel_src: str):
+def traffic_record(kernel_src: str, workload: str):
     """dram bytes per launch from the committed ncu summary, if it was taken
-    on the current source of the kernel's translation unit."""
+    on the current source of the kernel's translation unit and this workload."""
     p = os.path.join(ROOT, "profiles", "roofline_traffic.json")
     if not os.path.exists(p):
         return None
@@ -67,7 +67,7 @@ def traffic_record(kernel_src: str):
     src = open(os.path.join(ROOT, "paper_2009_09103_gb300", "csrc", kernel_src), "rb").read()
     sha = hashlib.sha256(src).hexdigest()[:16]
     for r in recs:
-        if r.get("source") == kernel_src and r.get("source_sha") == sha:
+        if r.get("source") == kernel_src and r.get("source_sha") == sha and r.get("workload") == workload:
             return r
     return None
 
@@ -135,6 +135,28 @@ def walk_bytes(torch, off_t, path):
     return n_trans, 16 * n_trans + 4 * deg_sum + 4 * n_trans + 4 * n + 4 * n * row + 16 * n_dead
 
 
+def walk_workload(args):
+    from paper_2009_09103_gb300 import inputs
+    if args.workload == "node2vec":
+        if args.scale == 22:
+            return inputs.workload_node2vec_s22()
+        g = inputs.rmat_csr(args.scale, 32, 15, args.scale)
+        return inputs.WalkWorkload(g, np.arange(g.V, dtype=np.uint32), 40, "node2vec", (1, 2, 4), 3)
+    if args.scale == 20:
+        return inputs.workload_walk_s20()
+    g = inputs.rmat_csr(args.scale, 16, 255, args.scale)
+    return inputs.WalkWorkload(g, np.arange(g.V, dtype=np.uint32), 80, "edge_weight", (1, 1, 1), 2)
+
+
+def walk_config(args, wl):
+    g = wl.graph
+    if wl.bias == "node2vec":
+        return (f"node2vec walk p=2 q=0.5 (integer multipliers 1/2/4): RMAT scale {args.scale}, edge factor "
+                f"32, weights uniform [1,15], {g.V:,} walkers (one per vertex), length {wl.length}")
+    return (f"weighted random walk: RMAT scale {args.scale}, edge factor 16, weights uniform [1,255], "
+            f"{g.V:,} walkers (one per vertex), length {wl.length}, edge-weight bias")
+
+
 def run_walk_bench(args, rank, world):
     import torch
     from paper_2009_09103_gb300 import build, csaw, inputs
@@ -143,9 +165,9 @@ def run_walk_bench(args, rank, world):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
     torch.cuda.set_device(dev)
     t0 = time.time()
-    wl = inputs.workload_walk_s20()
+    wl = walk_workload(args)
     g = wl.graph
-    log(f"[bench] graph s20: V={g.V} E={g.E} built in {time.time() - t0:.1f}s")
+    log(f"[bench] {args.workload} graph: V={g.V} E={g.E} built in {time.time() - t0:.1f}s")
     G = csaw.Graph(g.off, g.col, g.w)
     stream = torch.cuda.current_stream()
     starts = torch.from_numpy(wl.starts.view(np.int32)).to(dev)
@@ -155,7 +177,7 @@ def run_walk_bench(args, rank, world):
     seed = wl.rng_seed + rank  # replicas: independent walks per rank
 
     def step():
-        csaw.walk(G, starts, wl.length, wl.bias, seed, path=path, stream=stream)
+        csaw.walk(G, starts, wl.length, wl.bias, seed, wl.n2v_mult, path=path, stream=stream)
 
     for _ in range(args.warmup):
         step()
@@ -194,12 +216,12 @@ def run_walk_bench(args, rank, world):
     h_path = torch.empty((n, wl.length + 1), dtype=torch.int32, pin_memory=True)
     hs = h_starts.numpy().view(np.uint32)
     hp = h_path.numpy().view(np.uint32)
-    csaw.walk(G, hs, wl.length, wl.bias, seed, path=hp, stream=stream)   # warm
+    csaw.walk(G, hs, wl.length, wl.bias, seed, wl.n2v_mult, path=hp, stream=stream)   # warm
     e2e_steps = max(1, min(args.steps, 5))
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     for _ in range(e2e_steps):
-        csaw.walk(G, hs, wl.length, wl.bias, seed, path=hp, stream=stream)
+        csaw.walk(G, hs, wl.length, wl.bias, seed, wl.n2v_mult, path=hp, stream=stream)
     e2e_s = (time.perf_counter() - t1) / e2e_steps
     e2e_ok = bool(np.array_equal(hp, path.cpu().numpy().view(np.uint32)))
     e2e = {"value": n_trans * world / e2e_s, "unit": "edges/s",
@@ -208,8 +230,9 @@ def run_walk_bench(args, rank, world):
 
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / (ms_per_step / 1e3) / 1e9
-    tr = traffic_record("csaw_walk.cu")
-    roofline = {"bound": "hbm", "kernel": "walk_kernel<EDGE_WEIGHT>", "achieved": round(achieved, 1),
+    tr = traffic_record("csaw_walk.cu", f"{args.workload}_s{args.scale}")
+    kname = "walk_kernel<NODE2VEC>" if wl.bias == "node2vec" else "walk_kernel<EDGE_WEIGHT>"
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1),
                 "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
                 "frac": round(achieved / peak, 4),
                 "traffic": tr["traffic_bytes_per_launch"] if tr else None,
@@ -219,9 +242,7 @@ def run_walk_bench(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32 biases / u64 prefix sums", "data": "synthetic (seeded RMAT)",
-        "config": {"workload": "weighted random walk: RMAT scale 20, edge factor 16, weights "
-                               "uniform [1,255], 1,048,576 walkers (one per vertex), length 80, "
-                               "edge-weight bias",
+        "config": {"workload": walk_config(args, wl),
                    "parallelism": "replicas" if world > 1 else "1 GPU",
                    "l2": "flushed (512 MiB write) before every timed step",
                    "sampled_edges_per_step": n_trans},
@@ -247,7 +268,7 @@ def oracle_walk_sample(g, wl, budget_s: float):
         ids = np.linspace(0, n - 1, num=m, dtype=np.int64) + used % 7
         ids = np.unique(np.clip(ids, 0, n - 1))
         t0 = time.perf_counter()
-        p = oracle.walk(g, wl.starts[ids], wl.length, wl.bias, wl.rng_seed,
+        p = oracle.walk(g, wl.starts[ids], wl.length, wl.bias, wl.rng_seed, mult=wl.n2v_mult,
                         walker_ids=ids.astype(np.uint64))
         total_t += time.perf_counter() - t0
         total_e += int((p[:, 1:] != 0xFFFFFFFF).sum())
@@ -260,8 +281,7 @@ def run_reference(args, rank, world):
     """The oracle, as it stands, on the host cores, on bounded samples."""
     if rank != 0:
         return None
-    from paper_2009_09103_gb300 import inputs
-    wl = inputs.workload_walk_s20()
+    wl = walk_workload(args)
     g = wl.graph
     per_step = max(2.0, min(20.0, 60.0 / max(1, args.steps)))
     vals = []
@@ -274,15 +294,13 @@ def run_reference(args, rank, world):
         used_total += used
     value = statistics.mean(vals)
     sample = (f"{used_total // max(1, args.steps)} walkers per step (uniformly spaced over the "
-              f"1,048,576), full length 80, single-threaded oracle")
+              f"{len(wl.starts):,}), full length {wl.length}, single-threaded oracle")
     return {
         "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32 biases / u64 prefix sums", "data": "synthetic (seeded RMAT)",
         "impl": "reference",
-        "config": {"workload": "weighted random walk: RMAT scale 20, edge factor 16, weights "
-                               "uniform [1,255], 1,048,576 walkers (one per vertex), length 80, "
-                               "edge-weight bias"},
+        "config": {"workload": walk_config(args, wl)},
         "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -295,8 +313,13 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--cpu-baseline-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-baseline-seconds", type=float, default=12.0,
+                    help="oracle sample budget; 0 skips the CPU baseline")
+    ap.add_argument("--workload", default="walk", choices=["walk", "node2vec"])
+    ap.add_argument("--scale", type=int, default=None, help="RMAT scale (default: the workload's)")
     args = ap.parse_args()
+    if args.scale is None:
+        args.scale = {"walk": 20, "node2vec": 22}[args.workload]
     rank, world, local = dist_env()
 
     if args.impl == "reference":
@@ -313,11 +336,11 @@ def main():
         torch.cuda.set_device(local)
         torch.distributed.init_process_group("nccl")
     result, (g, wl, n_trans) = run_walk_bench(args, rank, world)
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and args.cpu_baseline_seconds > 0:
         v, used, t = oracle_walk_sample(g, wl, args.cpu_baseline_seconds)
         result["cpu_baseline"] = {"value": v, "unit": "edges/s", "cores": 1, "kind": "oracle",
-                                  "sample": f"{used} walkers (uniformly spaced), length 80, "
-                                            f"{t:.1f} s single-threaded"}
+                                  "sample": f"{used} walkers (uniformly spaced), full length "
+                                            f"{wl.length}, {t:.1f} s single-threaded"}
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:

@@ -217,10 +217,15 @@ extern "C" csaw_status csaw_graph_create(const uint64_t* row_offsets, uint32_t n
     const size_t off_b = sizeof(uint64_t) * ((size_t)n_vertices + 1);
     const size_t col_b = sizeof(uint32_t) * (size_t)n_edges;
     const size_t deg_b = sizeof(uint32_t) * (size_t)n_vertices;
+    // Column and weight arrays carry CSAW_EDGE_PAD zeroed entries past the end so
+    // that 16-byte vector loads of the last row's final group stay inside them.
+    const size_t pad_b = sizeof(uint32_t) * CSAW_EDGE_PAD;
     cudaError_t e = cudaMalloc(&g->off, off_b);
-    if (e == cudaSuccess) e = cudaMalloc(&g->col, col_b ? col_b : 16);
-    if (e == cudaSuccess && weights) e = cudaMalloc(&g->w, col_b ? col_b : 16);
+    if (e == cudaSuccess) e = cudaMalloc(&g->col, col_b + pad_b);
+    if (e == cudaSuccess && weights) e = cudaMalloc(&g->w, col_b + pad_b);
     if (e == cudaSuccess) e = cudaMalloc(&g->deg, deg_b);
+    if (e == cudaSuccess) e = cudaMemsetAsync((char*)g->col + col_b, 0, pad_b, s);
+    if (e == cudaSuccess && weights) e = cudaMemsetAsync((char*)g->w + col_b, 0, pad_b, s);
     if (e != cudaSuccess) {
         csaw_graph_destroy(g);
         return cuda_fail(e, "cudaMalloc(graph)");

@@ -11,6 +11,7 @@
 #include "csaw.h"
 
 #define CSAW_FULL_MASK 0xFFFFFFFFu
+#define CSAW_EDGE_PAD 16   // zeroed uint32 entries after col[] and w[]
 
 // ---------------------------------------------------------------------------
 // Graph: CSR resident in HBM (uint64 offsets, uint32 columns and weights) and

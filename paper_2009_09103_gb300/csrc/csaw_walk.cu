@@ -4,9 +4,13 @@
 // v's neighbour list (Sec. II-B, Eq. 1) with a single draw, so the cumulative
 // bias array never has to be stored: the warp streams the biases once to get
 // the total T (keeping one running prefix per chunk in shared memory), maps
-// the draw to x in [0, T), then rescans only the chunk that holds x with a
-// warp scan to find the first neighbour whose inclusive prefix exceeds x.
-// Rows of at most 256 neighbours stay in registers and need one pass.
+// the draw to x in [0, T), then rescans only the chunk that holds x.  Biases
+// are read as 16-byte groups of four (a round is 4 groups per lane, 512
+// neighbours per warp); a lane sums its sixteen in 32 bits and the warp
+// reduces with one redux.sync when the largest possible bias times 512 stays
+// below 2^32 (64-bit otherwise).  Locating x inside a 128-neighbour tile takes
+// one warp scan of per-lane sums and a four-step search in the hit lane.
+// Rows that fit one round stay in registers and need one pass.
 //
 // Work distribution: a persistent grid; each warp takes the next walker from
 // a global counter and runs all its steps.  The path row is buffered one
@@ -18,9 +22,10 @@ namespace csaw {
 
 constexpr int WALK_THREADS = 256;
 constexpr int WALK_WARPS = WALK_THREADS / 32;
-constexpr int ELEMS = 8;                 // neighbours per lane per round
-constexpr uint32_t ROUND = 32 * ELEMS;   // neighbours per warp per round
-constexpr uint32_t CHUNK_SLOTS = 256;    // chunk prefixes per warp (shared memory)
+constexpr uint32_t TILE = 128;              // neighbours per 16-byte load across the warp
+constexpr int U = 4;                        // tiles per round (four loads in flight per lane)
+constexpr uint32_t ROUND = TILE * U;        // 512 neighbours per round
+constexpr uint32_t CHUNK_SLOTS = 256;       // chunk prefixes per warp (shared memory)
 
 struct WalkParams {
     const uint64_t* __restrict__ off;
@@ -42,104 +47,284 @@ struct PrevCtx {
     uint64_t pbeg, pend; // its neighbour range
 };
 
-// EdgeBias (Eq. 3) of the neighbour at edge index e.
+// Row geometry: biases are read in 16-byte groups aligned to 4 elements, so
+// the row [beg, end) is covered from abeg = beg rounded down to 4.
+struct Row {
+    uint64_t beg, end, abeg;
+    uint32_t d, span;    // span = end - abeg
+    uint32_t lo;         // beg - abeg (0..3): leading elements that are not in the row
+};
+
+// EdgeBias (Eq. 3) of the four neighbours at positions q .. q+3 relative to
+// abeg (q a multiple of 4).  Positions outside [lo, span) get bias 0; only the
+// first and the last group of a row can be partial.
 template <int KIND>
-__device__ __forceinline__ uint32_t edge_bias(const WalkParams& p, uint64_t e, const PrevCtx& c)
+__device__ __forceinline__ void group_bias(const WalkParams& p, const Row& r, uint32_t q,
+                                           const PrevCtx& c, uint32_t (&b)[4])
 {
-    if constexpr (KIND == CSAW_BIAS_UNIFORM) {
-        return 1u;
-    } else if constexpr (KIND == CSAW_BIAS_EDGE_WEIGHT) {
-        return __ldg(p.w + e);
+    b[0] = b[1] = b[2] = b[3] = 0u;
+    if (q >= r.span) return;
+    const bool full = q >= r.lo && q + 4 <= r.span;
+    if constexpr (KIND == CSAW_BIAS_EDGE_WEIGHT) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(p.w + r.abeg) + (q >> 2));
+        b[0] = v.x; b[1] = v.y; b[2] = v.z; b[3] = v.w;
     } else if constexpr (KIND == CSAW_BIAS_NEIGHBOR_DEGREE) {
-        return __ldg(p.deg + __ldg(p.col + e));
-    } else {
-        const uint32_t wt = p.w ? __ldg(p.w + e) : 1u;
-        if (c.prev == CSAW_NONE) return wt;
-        const uint32_t u = __ldg(p.col + e);
-        if (u == c.prev) return wt * p.m0;
-        return sorted_contains(p.col, c.pbeg, c.pend, u) ? wt * p.m1 : wt * p.m2;
-    }
-}
-
-// Biases of one round: lane holds neighbours j = base + 32*u + lane.
-template <int KIND>
-__device__ __forceinline__ void load_round(const WalkParams& p, uint64_t beg, uint32_t d,
-                                           uint32_t base, const PrevCtx& c, int lane,
-                                           uint32_t (&b)[ELEMS])
-{
+        const uint4 u = __ldg(reinterpret_cast<const uint4*>(p.col + r.abeg) + (q >> 2));
+        if (full) {
+            b[0] = __ldg(p.deg + u.x); b[1] = __ldg(p.deg + u.y);
+            b[2] = __ldg(p.deg + u.z); b[3] = __ldg(p.deg + u.w);
+        } else {
+            const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
-    for (int u = 0; u < ELEMS; ++u) {
-        const uint32_t j = base + 32u * u + lane;
-        b[u] = j < d ? edge_bias<KIND>(p, beg + j, c) : 0u;
-    }
-}
-
-// Find, in one round whose biases are b and whose elements start at prefix
-// `before`, the neighbour whose interval holds x.  Returns true and sets
-// *idx (round-relative) if the round holds x.
-__device__ __forceinline__ bool locate_in_round(const uint32_t (&b)[ELEMS], uint64_t& before,
-                                                uint64_t x, int lane, uint32_t* idx)
-{
-#pragma unroll
-    for (int u = 0; u < ELEMS; ++u) {
-        const uint64_t incl = warp_inclusive_scan_u64(b[u], lane);
-        const uint64_t tile = __shfl_sync(CSAW_FULL_MASK, incl, 31);
-        if (before + tile > x) {
-            const uint32_t hit = __ballot_sync(CSAW_FULL_MASK, before + incl > x);
-            *idx = 32u * u + (__ffs(hit) - 1);
-            return true;
+            for (int j = 0; j < 4; ++j)
+                if (q + j >= r.lo && q + j < r.span) b[j] = __ldg(p.deg + uu[j]);
         }
-        before += tile;
+        return;
+    } else {
+        static_assert(KIND != CSAW_BIAS_NODE2VEC, "node2vec biases are formed per tile (n2v_tile_bias)");
     }
-    return false;
+    if (!full) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (q + j < r.lo || q + j >= r.span) b[j] = 0u;
+    }
 }
 
-// One walk step at a vertex with neighbours [beg, beg + d): the inverse
-// transform pick for draw r.  Returns false at a dead end (T == 0).
-template <int KIND>
-__device__ __forceinline__ bool walk_pick(const WalkParams& p, uint64_t beg, uint32_t d,
-                                          const PrevCtx& c, uint64_t r, uint64_t* s_chunk,
-                                          int lane, uint32_t* idx)
+// node2vec biases (Sec. II-A) of one 128-neighbour tile at positions
+// q0 .. q0+127 relative to abeg; lane holds positions q0 + 4*lane .. +3.
+//
+// Membership of a neighbour u in N(prev) is a merge of two sorted lists.  A
+// window of N(prev) is kept staged in this warp's shared buffer: it starts at
+// A = lower_bound(N(prev), smallest id of the tile) and holds up to SEG_SMEM
+// entries.  Tiles come in ascending id order, so the next tile's A is usually
+// found inside the staged window with no global access; the window is
+// reloaded (one coalesced read) only when A moves.  Ids beyond the window's
+// last entry are searched in the rest of N(prev) in global memory.  All lanes
+// call this together, for tiles in ascending order; win = {A, 0} restarts.
+constexpr uint32_t SEG_SMEM = 256;
+
+struct N2vWin {
+    uint64_t A;    // first staged index of N(prev) in col[]
+    uint32_t n;    // staged entries
+};
+
+__device__ __forceinline__ uint64_t lower_bound_col(const uint32_t* __restrict__ col, uint64_t lo,
+                                                    uint64_t hi, uint32_t u)
 {
-    if (d == 0) return false;
+    while (lo < hi) {
+        const uint64_t mid = lo + ((hi - lo) >> 1);
+        if (__ldg(col + mid) < u) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ uint32_t lower_bound_smem(const uint32_t* s, uint32_t n, uint32_t u)
+{
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (s[mid] < u) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void n2v_tile_bias(const WalkParams& p, const Row& r, uint32_t q0,
+                                              const PrevCtx& c, int lane, uint32_t* s_seg,
+                                              N2vWin& win, uint32_t (&b)[4])
+{
+    const uint32_t q = q0 + 4u * lane;
+    b[0] = b[1] = b[2] = b[3] = 0u;
+    uint32_t uu[4] = {0u, 0u, 0u, 0u};
+    bool valid[4] = {false, false, false, false};
+    if (q < r.span) {
+        const uint4 u = __ldg(reinterpret_cast<const uint4*>(p.col + r.abeg) + (q >> 2));
+        uint4 wv = make_uint4(1u, 1u, 1u, 1u);
+        if (p.w) wv = __ldg(reinterpret_cast<const uint4*>(p.w + r.abeg) + (q >> 2));
+        uu[0] = u.x; uu[1] = u.y; uu[2] = u.z; uu[3] = u.w;
+        b[0] = wv.x; b[1] = wv.y; b[2] = wv.z; b[3] = wv.w;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            valid[j] = q + j >= r.lo && q + j < r.span;
+            if (!valid[j]) b[j] = 0u;
+        }
+    }
+    if (c.prev == CSAW_NONE) return;   // first step: the edge weight alone
+    // smallest and largest id of the tile
+    uint32_t mn = 0xFFFFFFFFu, mx = 0u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (valid[j]) { mn = min(mn, uu[j]); mx = max(mx, uu[j]); }
+    mn = __reduce_min_sync(CSAW_FULL_MASK, mn);
+    mx = __reduce_max_sync(CSAW_FULL_MASK, mx);
+    if (mn > mx) return;   // no neighbour of the row in this tile
+    // A = lower_bound(N(prev), mn): inside the staged window when its last
+    // entry is >= mn, else in the rest of N(prev) after the window.
+    uint64_t A;
+    if (win.n > 0 && mn <= s_seg[win.n - 1]) {
+        A = win.A + lower_bound_smem(s_seg, win.n, mn);
+    } else {
+        const uint64_t from = win.n > 0 ? win.A + win.n : c.pbeg;
+        uint64_t a0 = 0;
+        if (lane == 0) a0 = lower_bound_col(p.col, from, c.pend, mn);
+        A = __shfl_sync(CSAW_FULL_MASK, a0, 0);
+    }
+    __syncwarp();
+    if (win.n == 0 || A != win.A) {
+        const uint64_t left = c.pend - A;
+        const uint32_t n = left < SEG_SMEM ? (uint32_t)left : SEG_SMEM;
+        for (uint32_t i = lane; i < n; i += 32) s_seg[i] = __ldg(p.col + A + i);
+        win.A = A;
+        win.n = n;
+        __syncwarp();
+    }
+    const bool to_end = win.A + win.n == c.pend;
+    const uint32_t last = win.n > 0 ? s_seg[win.n - 1] : 0u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (!valid[j]) continue;
+        const uint32_t u = uu[j];
+        uint32_t m;
+        if (u == c.prev) {
+            m = p.m0;
+        } else {
+            bool in;
+            if (to_end || u <= last) {
+                const uint32_t at = lower_bound_smem(s_seg, win.n, u);
+                in = at < win.n && s_seg[at] == u;
+            } else {
+                const uint64_t at = lower_bound_col(p.col, win.A + win.n, c.pend, u);
+                in = at < c.pend && __ldg(p.col + at) == u;
+            }
+            m = in ? p.m1 : p.m2;
+        }
+        b[j] *= m;
+    }
+}
+
+// Sum type of a lane's sixteen biases in one round and of a round's total:
+// 32 bits when max bias * ROUND < 2^32 (NARROW), else 64 bits.
+template <bool WIDE>
+struct Acc;
+template <>
+struct Acc<false> {
+    using T = uint32_t;
+    static __device__ __forceinline__ uint32_t warp_sum(uint32_t x) { return __reduce_add_sync(CSAW_FULL_MASK, x); }
+    static __device__ __forceinline__ uint32_t scan(uint32_t x, int lane)
+    {
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(CSAW_FULL_MASK, x, o);
+            if (lane >= o) x += y;
+        }
+        return x;
+    }
+};
+template <>
+struct Acc<true> {
+    using T = uint64_t;
+    static __device__ __forceinline__ uint64_t warp_sum(uint64_t x) { return warp_sum_u64(x); }
+    static __device__ __forceinline__ uint64_t scan(uint64_t x, int lane) { return warp_inclusive_scan_u64(x, lane); }
+};
+
+// Biases of round `rd` (tiles rd*U .. rd*U+U-1) into b[u][j].
+template <int KIND>
+__device__ __forceinline__ void load_round(const WalkParams& p, const Row& r, uint32_t rd,
+                                           const PrevCtx& c, int lane, uint32_t* s_seg, N2vWin& win,
+                                           uint32_t (&b)[U][4])
+{
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        if constexpr (KIND == CSAW_BIAS_NODE2VEC) n2v_tile_bias(p, r, rd * ROUND + u * TILE, c, lane, s_seg, win, b[u]);
+        else group_bias<KIND>(p, r, rd * ROUND + u * TILE + 4u * lane, c, b[u]);
+    }
+}
+
+// Within round `rd` whose biases are b and which starts at prefix `before`,
+// find the neighbour whose interval holds x (x is known to lie in this
+// round).  Returns its index relative to beg.
+template <bool WIDE>
+__device__ __forceinline__ uint32_t locate_in_round(const Row& r, uint32_t rd, const uint32_t (&b)[U][4],
+                                                    uint64_t before, uint64_t x, int lane)
+{
+    using A = Acc<WIDE>;
+    using T = typename A::T;
+    // tile holding x: the first whose inclusive prefix exceeds x (selected
+    // without dynamic indexing so the biases stay in registers)
+    T st[U];
+    int ut = -1;
+    uint64_t bt = 0, acc = before;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        st[u] = (T)b[u][0] + b[u][1] + b[u][2] + b[u][3];
+        const uint64_t tt = A::warp_sum(st[u]);
+        if (ut < 0 && acc + tt > x) { ut = u; bt = acc; }
+        acc += tt;
+    }
+    T sl = 0;
+    uint32_t b0 = 0, b1 = 0, b2 = 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+        if (u == ut) { sl = st[u]; b0 = b[u][0]; b1 = b[u][1]; b2 = b[u][2]; }
+    const T incl = A::scan(sl, lane);
+    const uint32_t hit = __ballot_sync(CSAW_FULL_MASK, bt + incl > x);
+    const int L = __ffs(hit) - 1;
+    // inside the hit lane's four neighbours: the first whose inclusive prefix exceeds x
+    const uint64_t e0 = bt + incl - sl + b0;
+    const uint64_t e1 = e0 + b1;
+    const uint64_t e2 = e1 + b2;
+    uint32_t j = e0 > x ? 0u : (e1 > x ? 1u : (e2 > x ? 2u : 3u));
+    j = __shfl_sync(CSAW_FULL_MASK, j, L);
+    return rd * ROUND + (uint32_t)ut * TILE + 4u * L + j - r.lo;
+}
+
+// One walk step: the inverse transform pick for draw r over row `row`.
+// Returns false at a dead end (T == 0).
+template <int KIND, bool WIDE>
+__device__ __forceinline__ bool walk_pick(const WalkParams& p, const Row& row, const PrevCtx& c,
+                                          uint64_t r, uint64_t* s_chunk, uint32_t* s_seg, int lane,
+                                          uint32_t* idx)
+{
+    using A = Acc<WIDE>;
+    using T = typename A::T;
+    if (row.d == 0) return false;
     if constexpr (KIND == CSAW_BIAS_UNIFORM) {
-        *idx = (uint32_t)scale_draw(r, d);   // b = 1: S[i] = i + 1, so the pick is x itself
+        *idx = (uint32_t)scale_draw(r, row.d);   // b = 1: S[i] = i + 1, the pick is x itself
         return true;
     }
-    if (d <= ROUND) {
-        uint32_t b[ELEMS];
-        load_round<KIND>(p, beg, d, 0, c, lane, b);
-        uint64_t s = 0;
+    N2vWin win = {0, 0};
+    const uint32_t nrounds = (row.span + ROUND - 1) / ROUND;
+    if (nrounds == 1) {
+        uint32_t b[U][4];
+        load_round<KIND>(p, row, 0, c, lane, s_seg, win, b);
+        T s = 0;
 #pragma unroll
-        for (int u = 0; u < ELEMS; ++u) s += b[u];
-        const uint64_t T = warp_sum_u64(s);
-        if (T == 0) return false;
-        const uint64_t x = scale_draw(r, T);
-        uint64_t before = 0;
-        locate_in_round(b, before, x, lane, idx);
+        for (int u = 0; u < U; ++u) s += (T)b[u][0] + b[u][1] + b[u][2] + b[u][3];
+        const uint64_t total = A::warp_sum(s);
+        if (total == 0) return false;
+        *idx = locate_in_round<WIDE>(row, 0, b, 0, scale_draw(r, total), lane);
         return true;
     }
     // Pass 1: total, with the running prefix stored after every chunk of G rounds.
-    const uint32_t nrounds = (d + ROUND - 1) / ROUND;
     const uint32_t G = (nrounds + CHUNK_SLOTS - 1) / CHUNK_SLOTS;
     const uint32_t nchunks = (nrounds + G - 1) / G;
     uint64_t running = 0;
     for (uint32_t ch = 0; ch < nchunks; ++ch) {
         const uint32_t r_end = min(nrounds, (ch + 1) * G);
-        for (uint32_t rr = ch * G; rr < r_end; ++rr) {
-            uint32_t b[ELEMS];
-            load_round<KIND>(p, beg, d, rr * ROUND, c, lane, b);
-            uint64_t s = 0;
+#pragma unroll 2
+        for (uint32_t rd = ch * G; rd < r_end; ++rd) {
+            uint32_t b[U][4];
+            load_round<KIND>(p, row, rd, c, lane, s_seg, win, b);
+            T s = 0;
 #pragma unroll
-            for (int u = 0; u < ELEMS; ++u) s += b[u];
-            running += warp_sum_u64(s);
+            for (int u = 0; u < U; ++u) s += (T)b[u][0] + b[u][1] + b[u][2] + b[u][3];
+            running += A::warp_sum(s);
         }
         if (lane == 0) s_chunk[ch] = running;
     }
     __syncwarp();
-    const uint64_t T = running;
-    if (T == 0) return false;
-    const uint64_t x = scale_draw(r, T);
+    const uint64_t total = running;
+    if (total == 0) return false;
+    const uint64_t x = scale_draw(r, total);
     // Chunk holding x: the first whose inclusive prefix exceeds x.
     uint32_t ch = 0;
     for (uint32_t base = 0; base < nchunks; base += 32) {
@@ -150,27 +335,43 @@ __device__ __forceinline__ bool walk_pick(const WalkParams& p, uint64_t beg, uin
     }
     uint64_t before = ch > 0 ? s_chunk[ch - 1] : 0;
     __syncwarp();
+    win.n = 0;   // pass 2 restarts the node2vec window at the chunk's first tile
     // Pass 2: rescan that chunk's rounds.
     const uint32_t r_end = min(nrounds, (ch + 1) * G);
-    for (uint32_t rr = ch * G; rr < r_end; ++rr) {
-        uint32_t b[ELEMS];
-        load_round<KIND>(p, beg, d, rr * ROUND, c, lane, b);
-        uint32_t in_round;
-        if (locate_in_round(b, before, x, lane, &in_round)) {
-            *idx = rr * ROUND + in_round;
+    for (uint32_t rd = ch * G; rd < r_end; ++rd) {
+        uint32_t b[U][4];
+        load_round<KIND>(p, row, rd, c, lane, s_seg, win, b);
+        T s = 0;
+#pragma unroll
+        for (int u = 0; u < U; ++u) s += (T)b[u][0] + b[u][1] + b[u][2] + b[u][3];
+        const uint64_t rt = A::warp_sum(s);
+        if (before + rt > x) {
+            *idx = locate_in_round<WIDE>(row, rd, b, before, x, lane);
             return true;
         }
+        before += rt;
     }
-    *idx = d - 1;   // not reached: x < T lies in some chunk
+    *idx = row.d - 1;   // not reached: x < total lies in some round
     return true;
 }
 
-template <int KIND>
-__global__ void __launch_bounds__(WALK_THREADS) walk_kernel(WalkParams p)
+// Resident blocks per SM the register budget is set for: the light biases
+// fit 48 registers, neighbour degree 64, node2vec's membership windows 80.
+template <int KIND, bool WIDE>
+constexpr int walk_min_blocks()
+{
+    return (KIND == CSAW_BIAS_UNIFORM || (KIND == CSAW_BIAS_EDGE_WEIGHT && !WIDE)) ? 5
+           : KIND == CSAW_BIAS_NODE2VEC ? 3 : 4;
+}
+
+template <int KIND, bool WIDE>
+__global__ void __launch_bounds__(WALK_THREADS, (walk_min_blocks<KIND, WIDE>())) walk_kernel(WalkParams p)
 {
     __shared__ uint64_t s_chunk_all[WALK_WARPS][CHUNK_SLOTS];
+    __shared__ uint32_t s_seg_all[KIND == CSAW_BIAS_NODE2VEC ? WALK_WARPS : 1][SEG_SMEM];
     const int lane = threadIdx.x & 31;
     uint64_t* s_chunk = s_chunk_all[threadIdx.x >> 5];
+    uint32_t* s_seg = s_seg_all[KIND == CSAW_BIAS_NODE2VEC ? (threadIdx.x >> 5) : 0];
     const uint64_t row_len = (uint64_t)p.L + 1;
 
     while (true) {
@@ -178,10 +379,10 @@ __global__ void __launch_bounds__(WALK_THREADS) walk_kernel(WalkParams p)
         if (lane == 0) wk = atomicAdd(p.next_walker, 1ull);
         wk = __shfl_sync(CSAW_FULL_MASK, wk, 0);
         if (wk >= p.n) break;
-        uint32_t* row = p.path + wk * row_len;
+        uint32_t* out = p.path + wk * row_len;
         uint32_t cur = __ldg(p.starts + wk);
         if (cur >= p.V) {
-            for (uint64_t t = lane; t < row_len; t += 32) row[t] = CSAW_NONE;
+            for (uint64_t t = lane; t < row_len; t += 32) out[t] = CSAW_NONE;
             continue;
         }
         PrevCtx c;
@@ -190,55 +391,73 @@ __global__ void __launch_bounds__(WALK_THREADS) walk_kernel(WalkParams p)
         uint32_t buf = lane == 0 ? cur : CSAW_NONE;   // entries of the current 32-block
         uint64_t flushed = 0;                         // entries [0, flushed) are in memory
         for (uint32_t s = 0; s < p.L; ++s) {
-            const uint64_t beg = __ldg(p.off + cur);
-            const uint64_t end = __ldg(p.off + cur + 1);
-            const uint32_t d = (uint32_t)(end - beg);
+            Row row;
+            row.beg = __ldg(p.off + cur);
+            row.end = __ldg(p.off + cur + 1);
+            row.abeg = row.beg & ~3ull;
+            row.d = (uint32_t)(row.end - row.beg);
+            row.span = (uint32_t)(row.end - row.abeg);
+            row.lo = (uint32_t)(row.beg - row.abeg);
             const uint64_t r = philox_draw(p.k0, p.k1, 0u, cur, s, (uint32_t)wk);
             uint32_t idx;
-            if (!walk_pick<KIND>(p, beg, d, c, r, s_chunk, lane, &idx)) break;
-            const uint32_t nxt = __ldg(p.col + beg + idx);
+            if (!walk_pick<KIND, WIDE>(p, row, c, r, s_chunk, s_seg, lane, &idx)) break;
+            const uint32_t nxt = __ldg(p.col + row.beg + idx);
             if constexpr (KIND == CSAW_BIAS_NODE2VEC) {
                 c.prev = cur;
-                c.pbeg = beg;
-                c.pend = end;
+                c.pbeg = row.beg;
+                c.pend = row.end;
             }
             cur = nxt;
             const uint64_t t = (uint64_t)s + 1;
             if ((uint32_t)(t & 31) == (uint32_t)lane) buf = cur;
             if ((t & 31) == 31) {
-                row[t - 31 + lane] = buf;
+                out[t - 31 + lane] = buf;
                 buf = CSAW_NONE;
                 flushed = t + 1;
             }
         }
         // Remaining entries: the buffered block, then CSAW_NONE to the end of the row.
         for (uint64_t t = flushed + lane; t < row_len; t += 32)
-            row[t] = (t < flushed + 32) ? buf : CSAW_NONE;
+            out[t] = (t < flushed + 32) ? buf : CSAW_NONE;
     }
 }
 
-static csaw_status launch_walk(int kind, const WalkParams& p, int sm_count, cudaStream_t s)
+template <int KIND, bool WIDE>
+static csaw_status launch_walk_kw(const WalkParams& p, int sm_count, cudaStream_t s)
 {
-    int per_sm = 1;
-    cudaError_t e = cudaSuccess;
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel<KIND, WIDE>,
+                                                                      WALK_THREADS, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "occupancy(walk)");
+        if (per_sm < 1) per_sm = 1;
+    }
+    walk_kernel<KIND, WIDE><<<sm_count * per_sm, WALK_THREADS, 0, s>>>(p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "walk_kernel launch");
+    return CSAW_OK;
+}
+
+// max_bias: an upper bound of any bias of this call; 32-bit round sums when
+// a round of ROUND neighbours cannot reach 2^32.
+static csaw_status launch_walk(int kind, uint64_t max_bias, const WalkParams& p, int sm_count,
+                               cudaStream_t s)
+{
+    const bool wide = max_bias * ROUND >= (1ull << 32);
     switch (kind) {
-#define CSAW_WALK_CASE(K)                                                                      \
-    case K:                                                                                    \
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel<K>, WALK_THREADS, 0); \
-        if (e != cudaSuccess) return cuda_fail(e, "occupancy(walk)");                          \
-        walk_kernel<K><<<sm_count * (per_sm > 0 ? per_sm : 1), WALK_THREADS, 0, s>>>(p);       \
-        break;
-        CSAW_WALK_CASE(CSAW_BIAS_UNIFORM)
-        CSAW_WALK_CASE(CSAW_BIAS_EDGE_WEIGHT)
-        CSAW_WALK_CASE(CSAW_BIAS_NEIGHBOR_DEGREE)
-        CSAW_WALK_CASE(CSAW_BIAS_NODE2VEC)
-#undef CSAW_WALK_CASE
+    case CSAW_BIAS_UNIFORM: return launch_walk_kw<CSAW_BIAS_UNIFORM, false>(p, sm_count, s);
+    case CSAW_BIAS_EDGE_WEIGHT:
+        return wide ? launch_walk_kw<CSAW_BIAS_EDGE_WEIGHT, true>(p, sm_count, s)
+                    : launch_walk_kw<CSAW_BIAS_EDGE_WEIGHT, false>(p, sm_count, s);
+    case CSAW_BIAS_NEIGHBOR_DEGREE:
+        return wide ? launch_walk_kw<CSAW_BIAS_NEIGHBOR_DEGREE, true>(p, sm_count, s)
+                    : launch_walk_kw<CSAW_BIAS_NEIGHBOR_DEGREE, false>(p, sm_count, s);
+    case CSAW_BIAS_NODE2VEC:
+        return wide ? launch_walk_kw<CSAW_BIAS_NODE2VEC, true>(p, sm_count, s)
+                    : launch_walk_kw<CSAW_BIAS_NODE2VEC, false>(p, sm_count, s);
     default:
         return fail(CSAW_ERR_INVALID, "unknown bias kind %d", kind);
     }
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "walk_kernel launch");
-    return CSAW_OK;
 }
 
 }  // namespace csaw
@@ -294,7 +513,15 @@ extern "C" csaw_status csaw_walk(csaw_graph* g, const uint32_t* starts, uint64_t
         p.k0 = (uint32_t)rng_seed; p.k1 = (uint32_t)(rng_seed >> 32);
         p.m0 = bias->n2v_mult[0]; p.m1 = bias->n2v_mult[1]; p.m2 = bias->n2v_mult[2];
         p.next_walker = (unsigned long long*)counter;
-        st = launch_walk(kind, p, g->sm_count, s);
+        uint64_t max_bias = 1;
+        if (kind == CSAW_BIAS_EDGE_WEIGHT) max_bias = g->max_weight;
+        else if (kind == CSAW_BIAS_NEIGHBOR_DEGREE) max_bias = g->max_degree;
+        else if (kind == CSAW_BIAS_NODE2VEC) {
+            uint64_t m = 1;
+            for (int i = 0; i < 3; ++i) m = bias->n2v_mult[i] > m ? bias->n2v_mult[i] : m;
+            max_bias = (uint64_t)g->max_weight * m;
+        }
+        st = launch_walk(kind, max_bias, p, g->sm_count, s);
     }
     dfree(counter, s);
     if (mem_kind == CSAW_MEM_HOST) {

@@ -174,3 +174,30 @@ def test_walk_node2vec_s22_subset(csaw):
     got = path[torch.from_numpy(pick).cuda()].cpu().numpy().view(np.uint32)
     assert np.array_equal(got, ref)
     G.close()
+
+
+@pytest.mark.parametrize("wmax", [2**23 + 5, 2**31])
+def test_walk_wide_sums(csaw, wmax):
+    """Biases large enough that a 512-neighbour round overflows 32 bits take
+    the 64-bit path; results stay bit-exact."""
+    rng = np.random.default_rng(wmax % 97)
+    g0 = inputs.rmat_csr(11, 16, 50, 5)
+    w = rng.integers(wmax // 2, wmax, size=g0.E, dtype=np.uint64).astype(np.uint32)
+    g = inputs.CSRGraph(g0.off, g0.col, w)
+    starts = np.arange(g.V, dtype=np.uint32)
+    assert np.array_equal(gpu_walk(csaw, g, starts, 12, "edge_weight", 3),
+                          oracle.walk(g, starts, 12, "edge_weight", 3))
+    d = 70001
+    edges = [(0, j + 1) for j in range(d)] + [(j + 1, 0) for j in range(d)]
+    ws = list(rng.integers(1, wmax, size=d)) + [1] * d
+    gs = inputs.csr_from_edges(d + 1, edges, ws)
+    z = np.zeros(40, dtype=np.uint32)
+    assert np.array_equal(gpu_walk(csaw, gs, z, 3, "edge_weight", 8), oracle.walk(gs, z, 3, "edge_weight", 8))
+
+
+def test_walk_node2vec_wide_multipliers(csaw):
+    g = inputs.rmat_csr(11, 16, 40, 6)
+    starts = np.arange(g.V, dtype=np.uint32)
+    mult = (1, 2**20, 3)
+    assert np.array_equal(gpu_walk(csaw, g, starts, 10, "node2vec", 4, mult),
+                          oracle.walk(g, starts, 10, "node2vec", 4, mult=mult))
