@@ -88,6 +88,8 @@ enum { CSAW_MEM_HOST = 0, CSAW_MEM_DEVICE = 1 };
 
 typedef struct csaw_graph csaw_graph;
 typedef struct csaw_sample_result csaw_sample_result;
+typedef struct csaw_sample_plan csaw_sample_plan;
+typedef struct csaw_server csaw_server;
 
 /* ---------------------------------------------------------------- graph */
 
@@ -199,8 +201,168 @@ csaw_status csaw_sample_get_view(csaw_sample_result* r, csaw_sample_view* view);
  * arrays of n_edges entries each.  Synchronous. */
 csaw_status csaw_sample_copy_edges(csaw_sample_result* r, uint32_t* src, uint32_t* dst);
 
-/* Release a result returned by this library.  NULL is accepted. */
+/* Release a result returned by this library (a csaw_sample_result or a
+ * csaw_result).  NULL is accepted. */
 void csaw_result_free(void* result);
+
+/* ---------------------------------------------------------------- batched plans */
+
+/* A sample plan: csaw_sample's whole multi-instance, multi-layer pipeline
+ * (the batched multi-instance sampling of Sec. V-B, one frontier queue of
+ * (vertex, instance) entries across all instances) for a fixed instance count,
+ * seed budget, depth, fanout and bias, with every device buffer allocated
+ * once at its upper bound and the pipeline captured into one CUDA graph.
+ * Each run copies a new batch of seeds in and launches the graph: no host
+ * waits, no allocation.  Results are identical to csaw_sample on the same
+ * arguments.
+ * Upper bounds: layer l emits at most |F_l| * min(fanout[l], max degree)
+ * edges; |F_0| <= max_seeds and |F_{l+1}| <= min(edges of layer l,
+ * n_instances * n_vertices).  A plan whose non-last layer may produce 2^32 or
+ * more edges is rejected (CSAW_ERR_INVALID).
+ * Errors: CSAW_ERR_INVALID, CSAW_ERR_NOMEM, CSAW_ERR_CUDA. */
+csaw_status csaw_sample_plan_create(csaw_graph* g, uint32_t n_instances, uint64_t max_seeds,
+                                    uint32_t depth, const uint32_t* fanout, const csaw_bias* bias,
+                                    csaw_sample_plan** out);
+
+/* Run the plan on n_seeds seeds (<= max_seeds) split by inst_offsets
+ * (n_instances + 1 entries, inst_offsets[n_instances] = n_seeds), in host or
+ * device memory per mem_kind; asynchronous on `stream`.  Host inputs are
+ * validated on the host; device inputs are checked on the device and a bad
+ * seed or offset is reported by the next csaw_sample_plan_get_view. */
+csaw_status csaw_sample_plan_run(csaw_sample_plan* p, const uint32_t* seeds, uint64_t n_seeds,
+                                 const uint64_t* inst_offsets, uint64_t rng_seed, int mem_kind,
+                                 void* stream);
+
+/* Wait for the last run and describe its result (same layout as
+ * csaw_sample_view; the device arrays belong to the plan and are overwritten
+ * by its next run). */
+csaw_status csaw_sample_plan_get_view(csaw_sample_plan* p, csaw_sample_view* view);
+
+/* Wait for the last run and copy its edges (all layers, concatenated) to
+ * host arrays of n_edges entries. */
+csaw_status csaw_sample_plan_copy_edges(csaw_sample_plan* p, uint32_t* src, uint32_t* dst);
+
+/* Capacity-based device bytes of the plan's buffers and its selection launch
+ * shape (any pointer may be NULL). */
+csaw_status csaw_sample_plan_get_info(const csaw_sample_plan* p, uint64_t* device_bytes,
+                                      uint32_t* theta_warp, uint32_t* select_blocks);
+
+csaw_status csaw_sample_plan_destroy(csaw_sample_plan* p);
+
+/* ---------------------------------------------------------------- tuning */
+
+/* Launch shape of the selection kernel for one bias kind on one graph.
+ * theta_warp: frontier vertices of degree <= theta_warp (at most 256) are
+ * handled by one warp, larger ones by a CTA (the paper's warp-centric
+ * selection, Sec. IV-A, with a CTA path added for long neighbour lists);
+ * blocks_per_sm: resident CTAs per SM of the persistent grid (0 = as many as
+ * fit).  The shape changes speed only, never results. */
+typedef struct {
+    uint32_t theta_warp;
+    uint32_t blocks_per_sm;
+} csaw_select_tuning;
+
+csaw_status csaw_set_select_tuning(csaw_graph* g, int32_t bias_kind, const csaw_select_tuning* t);
+csaw_status csaw_get_select_tuning(const csaw_graph* g, int32_t bias_kind, csaw_select_tuning* t);
+
+/* Autotuner: times csaw_sample on the given (host) workload for every
+ * theta_warp in {32, 64, 128, 256} and every blocks_per_sm up to the
+ * occupancy limit, keeps the fastest on the graph and returns it in *best. */
+csaw_status csaw_autotune_select(csaw_graph* g, const uint32_t* seeds, const uint64_t* inst_offsets,
+                                 uint32_t n_instances, uint32_t depth, const uint32_t* fanout,
+                                 const csaw_bias* bias, uint64_t rng_seed, void* stream,
+                                 csaw_select_tuning* best);
+
+/* ---------------------------------------------------------------- serving */
+
+/* A request server over one resident graph.  Requests (sampling or walks, in
+ * any mix of sizes) are admitted in arrival order while their device-memory
+ * estimate fits budget_bytes and one of `slots` slots is free; every slot has
+ * its own CUDA stream, so admitted requests run concurrently and their work
+ * overlaps on the GPU.  A request that arrives while others run is admitted as
+ * soon as a slot and enough budget are free.  Each request's draws depend only
+ * on its own arguments and seed, so its result is bit-for-bit the one that
+ * csaw_sample / csaw_walk return for it alone.  The paper has no serving
+ * layer: this runs its selection (Sec. III-IV) for a stream of independent
+ * instances (Sec. IV-A). */
+typedef struct {
+    uint64_t budget_bytes;   /* device bytes that admitted requests may hold at once */
+    uint32_t slots;          /* concurrent requests (1 .. 256) */
+} csaw_server_opts;
+
+enum { CSAW_REQ_SAMPLE = 0, CSAW_REQ_WALK = 1 };
+
+/* A request; all arrays are host memory and are copied by csaw_submit. */
+typedef struct {
+    int32_t kind;                  /* CSAW_REQ_SAMPLE or CSAW_REQ_WALK */
+    csaw_bias bias;
+    uint64_t rng_seed;
+    /* sampling (as csaw_sample) */
+    const uint32_t* seeds;
+    const uint64_t* inst_offsets;
+    uint32_t n_instances;
+    uint32_t depth;
+    const uint32_t* fanout;
+    /* walks (as csaw_walk) */
+    const uint32_t* starts;
+    uint64_t n_walkers;
+    uint32_t length;
+} csaw_request;
+
+/* A finished request: host arrays owned by the result (csaw_result_free). */
+typedef struct {
+    uint32_t tag;                  /* set by the library */
+    int32_t kind;
+    csaw_status status;            /* outcome of the request */
+    /* sampling: layout of csaw_sample_view, edges of all layers concatenated */
+    uint32_t depth;
+    uint32_t n_instances;
+    uint64_t n_edges;
+    uint64_t* edge_offsets;
+    uint64_t* frontier_sizes;
+    uint32_t* src;
+    uint32_t* dst;
+    /* walks: path [n_walkers][length + 1] as csaw_walk */
+    uint64_t n_walkers;
+    uint32_t length;
+    uint32_t* path;
+    /* admission estimate and steady-clock times (ns) */
+    uint64_t device_bytes_estimate;
+    int64_t t_submit_ns, t_admit_ns, t_start_ns, t_finish_ns;
+} csaw_result;
+
+typedef struct {
+    uint32_t pending;
+    uint32_t running;
+    uint64_t bytes_in_use;
+    uint64_t budget_bytes;
+} csaw_server_stats_t;
+
+/* Errors: CSAW_ERR_INVALID, CSAW_ERR_NOMEM, CSAW_ERR_CUDA. */
+csaw_status csaw_server_create(csaw_graph* g, const csaw_server_opts* opts, csaw_server** out);
+
+/* Stops the server: requests not yet admitted finish with CSAW_ERR_ABORTED,
+ * running ones complete; results not yet polled are released.  The graph
+ * must outlive the server. */
+csaw_status csaw_server_destroy(csaw_server* s);
+
+/* Queue a request; *ticket identifies it.  Errors: CSAW_ERR_INVALID (bad
+ * arguments), CSAW_ERR_NOMEM (its estimate exceeds the whole budget),
+ * CSAW_ERR_ABORTED (server shutting down). */
+csaw_status csaw_submit(csaw_server* s, const csaw_request* r, uint64_t* ticket);
+
+/* Wait up to timeout_us (< 0: forever, 0: no wait) for a request.  When it
+ * has finished, *out receives its result (the caller then owns it and the
+ * ticket is retired) and the return value is the request's own status.
+ * Errors: CSAW_ERR_TIMEOUT (not finished; poll again), CSAW_ERR_NOT_FOUND
+ * (unknown or retired ticket), CSAW_ERR_ABORTED (cancelled or shut down). */
+csaw_status csaw_poll(csaw_server* s, uint64_t ticket, int64_t timeout_us, csaw_result** out);
+
+/* Cancel a request that has not been admitted yet; it finishes with
+ * CSAW_ERR_ABORTED.  CSAW_ERR_INVALID if it already started. */
+csaw_status csaw_cancel(csaw_server* s, uint64_t ticket);
+
+csaw_status csaw_server_stats(csaw_server* s, csaw_server_stats_t* out);
 
 /* ---------------------------------------------------------------- no allocation */
 

@@ -43,6 +43,42 @@ class GraphInfo(ctypes.Structure):
                 ("device_bytes", ctypes.c_uint64)]
 
 
+class SelectTuning(ctypes.Structure):
+    _fields_ = [("theta_warp", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32)]
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_uint64), ("slots", ctypes.c_uint32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("bias", Bias), ("rng_seed", ctypes.c_uint64),
+                ("seeds", ctypes.c_void_p), ("inst_offsets", ctypes.c_void_p),
+                ("n_instances", ctypes.c_uint32), ("depth", ctypes.c_uint32), ("fanout", ctypes.c_void_p),
+                ("starts", ctypes.c_void_p), ("n_walkers", ctypes.c_uint64), ("length", ctypes.c_uint32)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint32), ("kind", ctypes.c_int32), ("status", ctypes.c_int),
+                ("depth", ctypes.c_uint32), ("n_instances", ctypes.c_uint32), ("n_edges", ctypes.c_uint64),
+                ("edge_offsets", ctypes.POINTER(ctypes.c_uint64)),
+                ("frontier_sizes", ctypes.POINTER(ctypes.c_uint64)),
+                ("src", ctypes.POINTER(ctypes.c_uint32)), ("dst", ctypes.POINTER(ctypes.c_uint32)),
+                ("n_walkers", ctypes.c_uint64), ("length", ctypes.c_uint32),
+                ("path", ctypes.POINTER(ctypes.c_uint32)),
+                ("device_bytes_estimate", ctypes.c_uint64),
+                ("t_submit_ns", ctypes.c_int64), ("t_admit_ns", ctypes.c_int64),
+                ("t_start_ns", ctypes.c_int64), ("t_finish_ns", ctypes.c_int64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("pending", ctypes.c_uint32), ("running", ctypes.c_uint32),
+                ("bytes_in_use", ctypes.c_uint64), ("budget_bytes", ctypes.c_uint64)]
+
+
+REQ_SAMPLE, REQ_WALK = 0, 1
+
+
 class SampleView(ctypes.Structure):
     _fields_ = [("depth", ctypes.c_uint32), ("n_instances", ctypes.c_uint32),
                 ("n_edges", ctypes.c_uint64),
@@ -73,8 +109,30 @@ def lib():
             L.csaw_sample_copy_edges.argtypes = [P, P, P]
             L.csaw_result_free.argtypes = [P]
             L.csaw_result_free.restype = None
+        PP = ctypes.POINTER(P)
+        L.csaw_sample_plan_create.argtypes = [P, u32, u64, u32, P, ctypes.POINTER(Bias), PP]
+        L.csaw_sample_plan_run.argtypes = [P, P, u64, P, u64, i32, P]
+        L.csaw_sample_plan_get_view.argtypes = [P, ctypes.POINTER(SampleView)]
+        L.csaw_sample_plan_copy_edges.argtypes = [P, P, P]
+        L.csaw_sample_plan_get_info.argtypes = [P, ctypes.POINTER(u64), ctypes.POINTER(u32), ctypes.POINTER(u32)]
+        L.csaw_sample_plan_destroy.argtypes = [P]
+        L.csaw_set_select_tuning.argtypes = [P, ctypes.c_int32, ctypes.POINTER(SelectTuning)]
+        L.csaw_get_select_tuning.argtypes = [P, ctypes.c_int32, ctypes.POINTER(SelectTuning)]
+        L.csaw_autotune_select.argtypes = [P, P, P, u32, u32, P, ctypes.POINTER(Bias), u64, P,
+                                           ctypes.POINTER(SelectTuning)]
+        L.csaw_server_create.argtypes = [P, ctypes.POINTER(ServerOpts), PP]
+        L.csaw_server_destroy.argtypes = [P]
+        L.csaw_submit.argtypes = [P, ctypes.POINTER(Request), ctypes.POINTER(u64)]
+        L.csaw_poll.argtypes = [P, u64, ctypes.c_int64, ctypes.POINTER(ctypes.POINTER(Result))]
+        L.csaw_cancel.argtypes = [P, u64]
+        L.csaw_server_stats.argtypes = [P, ctypes.POINTER(ServerStats)]
         for name in ("csaw_graph_create", "csaw_graph_destroy", "csaw_graph_get_info", "csaw_walk",
-                     "csaw_sample", "csaw_sample_get_view", "csaw_sample_copy_edges"):
+                     "csaw_sample", "csaw_sample_get_view", "csaw_sample_copy_edges",
+                     "csaw_sample_plan_create", "csaw_sample_plan_run", "csaw_sample_plan_get_view",
+                     "csaw_sample_plan_copy_edges", "csaw_sample_plan_get_info", "csaw_sample_plan_destroy",
+                     "csaw_set_select_tuning", "csaw_get_select_tuning", "csaw_autotune_select",
+                     "csaw_server_create", "csaw_server_destroy", "csaw_submit", "csaw_poll", "csaw_cancel",
+                     "csaw_server_stats"):
             if hasattr(L, name):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -262,3 +320,193 @@ def _wrap_device(ptr, n, holder):
     t = torch.as_tensor(_Arr(), device="cuda") if n else torch.empty(0, dtype=torch.int32, device="cuda")
     t._csaw_holder = holder
     return t
+
+
+# --------------------------------------------------------------------------
+# Batched plans (csaw_sample_plan_*)
+
+class SamplePlan:
+    """The multi-instance sampling pipeline captured in a CUDA graph."""
+
+    def __init__(self, g: Graph, n_instances: int, max_seeds: int, fanout, bias="edge_weight"):
+        L = lib()
+        self._g = g
+        self._fan = np.ascontiguousarray(fanout, dtype=np.uint32)
+        b = make_bias(bias) if isinstance(bias, str) else bias
+        self._h = ctypes.c_void_p()
+        self.n_instances = n_instances
+        _check(L.csaw_sample_plan_create(g.handle, n_instances, max_seeds, len(self._fan), _ptr(self._fan),
+                                         ctypes.byref(b), ctypes.byref(self._h)))
+
+    def run(self, seeds, inst_offsets, seed: int = 0, stream=None):
+        L = lib()
+        if _is_torch(seeds):
+            n = seeds.numel()
+            _check(L.csaw_sample_plan_run(self._h, _ptr(seeds), n, _ptr(inst_offsets), seed, MEM_DEVICE,
+                                          _stream_handle(stream)))
+        else:
+            self._keep = (np.ascontiguousarray(seeds, dtype=np.uint32),
+                          np.ascontiguousarray(inst_offsets, dtype=np.uint64))
+            st = _stream_handle(stream) if stream is not None else None
+            _check(L.csaw_sample_plan_run(self._h, _ptr(self._keep[0]), len(self._keep[0]), _ptr(self._keep[1]),
+                                          seed, MEM_HOST, st))
+
+    def result(self) -> SampleResult:
+        """Waits for the last run; edges copied to host."""
+        L = lib()
+        v = SampleView()
+        _check(L.csaw_sample_plan_get_view(self._h, ctypes.byref(v)))
+        ng = v.depth * v.n_instances
+        eo = np.ctypeslib.as_array(v.edge_offsets, shape=(ng + 1,)).copy()
+        fs = np.ctypeslib.as_array(v.frontier_sizes, shape=(ng,)).copy() if ng else np.zeros(0, np.uint64)
+        src = np.empty(v.n_edges, dtype=np.uint32)
+        dst = np.empty(v.n_edges, dtype=np.uint32)
+        _check(L.csaw_sample_plan_copy_edges(self._h, _ptr(src), _ptr(dst)))
+        return SampleResult(v.depth, v.n_instances, v.n_edges, eo, fs, src, dst)
+
+    def n_edges(self) -> int:
+        v = SampleView()
+        _check(lib().csaw_sample_plan_get_view(self._h, ctypes.byref(v)))
+        return int(v.n_edges)
+
+    def info(self):
+        b, t, k = ctypes.c_uint64(), ctypes.c_uint32(), ctypes.c_uint32()
+        _check(lib().csaw_sample_plan_get_info(self._h, ctypes.byref(b), ctypes.byref(t), ctypes.byref(k)))
+        return {"device_bytes": b.value, "theta_warp": t.value, "select_blocks": k.value}
+
+    def close(self):
+        if self._h:
+            lib().csaw_sample_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def set_select_tuning(g: Graph, bias: str, theta_warp: int, blocks_per_sm: int = 0):
+    t = SelectTuning(theta_warp, blocks_per_sm)
+    _check(lib().csaw_set_select_tuning(g.handle, BIAS_KINDS[bias], ctypes.byref(t)))
+
+
+def get_select_tuning(g: Graph, bias: str):
+    t = SelectTuning()
+    _check(lib().csaw_get_select_tuning(g.handle, BIAS_KINDS[bias], ctypes.byref(t)))
+    return {"theta_warp": t.theta_warp, "blocks_per_sm": t.blocks_per_sm}
+
+
+def autotune_select(g: Graph, seeds, inst_offsets, fanout, bias="edge_weight", seed: int = 0):
+    """csaw_autotune_select on a host workload; returns the chosen tuning."""
+    s = np.ascontiguousarray(seeds, dtype=np.uint32)
+    io = np.ascontiguousarray(inst_offsets, dtype=np.uint64)
+    f = np.ascontiguousarray(fanout, dtype=np.uint32)
+    b = make_bias(bias)
+    t = SelectTuning()
+    _check(lib().csaw_autotune_select(g.handle, _ptr(s), _ptr(io), len(io) - 1, len(f), _ptr(f), ctypes.byref(b),
+                                      seed, _stream_handle(None), ctypes.byref(t)))
+    return {"theta_warp": t.theta_warp, "blocks_per_sm": t.blocks_per_sm}
+
+
+# --------------------------------------------------------------------------
+# Serving (csaw_server_*, csaw_submit, csaw_poll)
+
+@dataclass
+class ServedResult:
+    status: int
+    kind: int
+    sample: object          # SampleResult or None
+    path: object            # numpy [n, L+1] or None
+    estimate: int
+    t_submit_ns: int
+    t_admit_ns: int
+    t_start_ns: int
+    t_finish_ns: int
+
+
+class Server:
+    def __init__(self, g: Graph, budget_bytes: int, slots: int = 4):
+        self._g = g
+        o = ServerOpts(budget_bytes, slots)
+        self._h = ctypes.c_void_p()
+        _check(lib().csaw_server_create(g.handle, ctypes.byref(o), ctypes.byref(self._h)))
+
+    def submit_walk(self, starts, length: int, bias="edge_weight", seed: int = 0, mult=(1, 1, 1)) -> int:
+        st = np.ascontiguousarray(starts, dtype=np.uint32)
+        r = Request()
+        r.kind = REQ_WALK
+        r.bias = make_bias(bias, mult)
+        r.rng_seed = seed
+        r.starts = st.ctypes.data
+        r.n_walkers = len(st)
+        r.length = length
+        t = ctypes.c_uint64()
+        _check(lib().csaw_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
+        return t.value
+
+    def submit_sample(self, seeds, inst_offsets, fanout, bias="edge_weight", seed: int = 0) -> int:
+        s = np.ascontiguousarray(seeds, dtype=np.uint32)
+        io = np.ascontiguousarray(inst_offsets, dtype=np.uint64)
+        f = np.ascontiguousarray(fanout, dtype=np.uint32)
+        r = Request()
+        r.kind = REQ_SAMPLE
+        r.bias = make_bias(bias)
+        r.rng_seed = seed
+        r.seeds = s.ctypes.data if len(s) else None
+        r.inst_offsets = io.ctypes.data
+        r.n_instances = len(io) - 1
+        r.depth = len(f)
+        r.fanout = f.ctypes.data
+        t = ctypes.c_uint64()
+        _check(lib().csaw_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int, timeout_us: int = -1, copy: bool = True):
+        """Returns a ServedResult (raises CsawError on timeout, unknown ticket,
+        or a failed request)."""
+        L = lib()
+        out = ctypes.POINTER(Result)()
+        st = L.csaw_poll(self._h, ticket, timeout_us, ctypes.byref(out))
+        if not out:
+            _check(st)
+        r = out.contents
+        sample = path = None
+        if st == OK and copy:
+            if r.kind == REQ_SAMPLE:
+                ng = r.depth * r.n_instances
+                eo = np.ctypeslib.as_array(r.edge_offsets, shape=(ng + 1,)).copy()
+                fs = np.ctypeslib.as_array(r.frontier_sizes, shape=(max(ng, 1),))[:ng].copy()
+                n = int(r.n_edges)
+                src = np.ctypeslib.as_array(r.src, shape=(max(n, 1),))[:n].copy()
+                dst = np.ctypeslib.as_array(r.dst, shape=(max(n, 1),))[:n].copy()
+                sample = SampleResult(r.depth, r.n_instances, n, eo, fs, src, dst)
+            else:
+                n, ln = int(r.n_walkers), int(r.length)
+                path = np.ctypeslib.as_array(r.path, shape=(max(n, 1) * (ln + 1),))[: n * (ln + 1)].reshape(n, ln + 1).copy()
+        res = ServedResult(st, r.kind, sample, path, r.device_bytes_estimate, r.t_submit_ns, r.t_admit_ns,
+                           r.t_start_ns, r.t_finish_ns)
+        L.csaw_result_free(ctypes.cast(out, ctypes.c_void_p))
+        if st != OK:
+            raise CsawError(st, L.csaw_last_error().decode(errors="replace"))
+        return res
+
+    def cancel(self, ticket: int):
+        _check(lib().csaw_cancel(self._h, ticket))
+
+    def stats(self):
+        s = ServerStats()
+        _check(lib().csaw_server_stats(self._h, ctypes.byref(s)))
+        return {"pending": s.pending, "running": s.running, "bytes_in_use": s.bytes_in_use,
+                "budget_bytes": s.budget_bytes}
+
+    def close(self):
+        if self._h:
+            lib().csaw_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

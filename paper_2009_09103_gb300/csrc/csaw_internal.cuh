@@ -30,6 +30,10 @@ struct csaw_graph {
     uint64_t device_bytes = 0;
     int device = 0;
     int sm_count = 0;
+    // selection launch shape per bias kind (0 = default): warp-item degree
+    // threshold and resident blocks per SM
+    uint32_t tune_theta_w[4] = {0, 0, 0, 0};
+    uint32_t tune_blocks_per_sm[4] = {0, 0, 0, 0};
 };
 
 // ---------------------------------------------------------------------------
@@ -70,6 +74,9 @@ csaw_status scan_u32(const uint32_t* in, uint64_t* out, const uint64_t* n_dev, u
 size_t sort_scratch_bytes(uint64_t n_max);
 csaw_status radix_sort_u64(uint64_t* keys, uint64_t* alt, const uint64_t* n_dev, uint64_t n_max,
                            int bits, int sm_count, void* scratch, cudaStream_t s, uint64_t** result);
+
+// Releases a result made by the request server (tagged "CSRV").
+void free_server_result(void* result);
 
 // Validation of a bias argument against a graph; fills the effective kind
 // (EDGE_WEIGHT on a graph without weights is UNIFORM).

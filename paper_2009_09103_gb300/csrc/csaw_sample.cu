@@ -58,6 +58,7 @@ struct SelParams {
     uint32_t k;
     uint32_t layer;
     uint32_t k0, k1;
+    const uint32_t* key_dev;              // if set, the Philox key {k0, k1} is read here
     bool zero_bias;                       // some bias of this kind may be zero
     const uint64_t* __restrict__ pos;     // [n+1]
     const uint32_t* __restrict__ warp_list;
@@ -290,6 +291,10 @@ __device__ void cta_item(const SelParams& p, uint32_t e, uint64_t* S, uint32_t* 
 template <int KIND>
 __global__ void __launch_bounds__(SEL_THREADS) select_kernel(SelParams p)
 {
+    if (p.key_dev) {
+        p.k0 = p.key_dev[0];
+        p.k1 = p.key_dev[1];
+    }
     extern __shared__ __align__(16) unsigned char s_dyn[];
     __shared__ uint64_t s_wsum[SEL_WARPS];
     __shared__ unsigned long long s_item;
@@ -341,6 +346,7 @@ struct CountParams {
     const unsigned long long* n_dev;
     uint64_t vmask;
     uint32_t k;
+    uint32_t theta_w;              // warp items: degree <= theta_w (<= WARP_MAX_DEG), or take-all
     bool zero_bias;
     uint32_t* __restrict__ cnt;
     uint32_t* __restrict__ warp_list;
@@ -392,7 +398,7 @@ __global__ void count_kernel(CountParams p)
         }
         const uint32_t c = min(p.k, npos);
         const bool take_all = npos <= p.k;
-        const bool to_warp = e < n && c > 0 && (take_all || d <= WARP_MAX_DEG);
+        const bool to_warp = e < n && c > 0 && (take_all || d <= p.theta_w);
         const bool to_cta = e < n && c > 0 && !to_warp;
         if (e < n) p.cnt[e] = c;
         // warp-aggregated appends
@@ -414,11 +420,20 @@ __global__ void count_kernel(CountParams p)
 // ---------------------------------------------------------------------------
 // Frontier construction.
 
-// Keys of the seeds: instance of seed j from the offsets, checks ranges.
+// Keys of the seeds: instance of seed j from the offsets, checks ranges.  The
+// seed count is inst_off[n_inst] (clamped to cap, flag 4 when above); block 0
+// stores it in *n_out for the kernels that follow.
 __global__ void seed_keys_kernel(const uint32_t* __restrict__ seeds, const uint64_t* __restrict__ inst_off,
-                                 uint32_t n_inst, uint64_t n_seeds, uint32_t V, uint32_t vbits,
-                                 uint64_t* __restrict__ keys, uint32_t* __restrict__ err)
+                                 uint32_t n_inst, uint64_t cap, uint32_t V, uint32_t vbits,
+                                 uint64_t* __restrict__ keys, uint32_t* __restrict__ err,
+                                 uint64_t* __restrict__ n_out)
 {
+    uint64_t n_seeds = inst_off[n_inst];
+    if (n_seeds > cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, 4u);
+        n_seeds = cap;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *n_out = n_seeds;
     for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_seeds;
          j += (uint64_t)gridDim.x * blockDim.x) {
         // instance = last i with inst_off[i] <= j
@@ -427,9 +442,9 @@ __global__ void seed_keys_kernel(const uint32_t* __restrict__ seeds, const uint6
             const uint32_t mid = (lo + hi + 1) >> 1;
             if (inst_off[mid] <= j) lo = mid; else hi = mid - 1;
         }
-        const uint32_t s = seeds[j];
-        if (s >= V) atomicOr(err, 1u);
-        keys[j] = ((uint64_t)lo << vbits) | (s < V ? s : 0u);
+        const uint32_t sd = seeds[j];
+        if (sd >= V) atomicOr(err, 1u);
+        keys[j] = ((uint64_t)lo << vbits) | (sd < V ? sd : 0u);
     }
 }
 
@@ -500,15 +515,20 @@ __global__ void inst_bounds_kernel(const uint64_t* __restrict__ keys, const uint
 }
 
 // Edge offsets and frontier sizes of one layer:
-// eoff[i] = base + pos[foff[i]] for i <= n_inst; fsize[i] = foff[i+1] - foff[i].
+// eoff[i] = base + pos[foff[i]] for i <= n_inst; fsize[i] = foff[i+1] - foff[i];
+// *next_base = base + (edges of this layer).
 __global__ void layer_offsets_kernel(const uint64_t* __restrict__ foff, const uint64_t* __restrict__ pos,
-                                     uint32_t n_inst, uint64_t base, uint64_t* __restrict__ eoff,
-                                     uint64_t* __restrict__ fsize)
+                                     uint32_t n_inst, const uint64_t* __restrict__ base_dev,
+                                     uint64_t* __restrict__ eoff, uint64_t* __restrict__ fsize,
+                                     uint64_t* __restrict__ next_base)
 {
+    const uint64_t base = *base_dev;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n_inst;
          i += (uint64_t)gridDim.x * blockDim.x) {
-        eoff[i] = base + pos[foff[i]];
+        const uint64_t e = base + pos[foff[i]];
+        eoff[i] = e;
         if (i < n_inst) fsize[i] = foff[i + 1] - foff[i];
+        else *next_base = e;
     }
 }
 
@@ -531,17 +551,28 @@ static int bits_for(uint64_t maxval)
 }  // namespace csaw
 
 // ---------------------------------------------------------------------------
-// Result object.
+// Host pipeline.
+//
+// One sampling call is: the layer-0 frontier from the seeds, then per layer a
+// count/classify pass, a scan for edge positions, the persistent selection
+// kernel, and (but for the last layer) compaction into the next frontier.
+// Every kernel reads its element count from device memory, so the same
+// sequence serves two modes:
+//   - csaw_sample: waits once per layer to size that layer's edge buffers
+//     exactly (frontier arrays take the previous layer's edge count as bound);
+//   - a sample plan: every buffer at its upper bound, no waits, captured once
+//     into a CUDA graph and replayed for each new batch of seeds.
+
 struct csaw_sample_result {
+    uint32_t magic = 0x43534d50u;   // "CSMP"
     uint32_t depth = 0;
     uint32_t n_instances = 0;
     uint64_t n_edges = 0;
     std::vector<uint64_t> edge_offsets;     // host
     std::vector<uint64_t> frontier_sizes;   // host
-    std::vector<uint32_t*> src, dst;        // device, per layer
+    std::vector<uint32_t*> src, dst;        // device, per layer (owned)
     std::vector<const uint32_t*> src_c, dst_c;
     std::vector<uint64_t> layer_edges;
-    int device = 0;
     ~csaw_sample_result()
     {
         for (auto p : src) cudaFree(p);
@@ -586,7 +617,8 @@ static csaw_status launch_count(const CountParams& p, uint64_t n, int sm_count, 
     return CSAW_OK;
 }
 
-static int select_blocks(int kind, int sm_count)
+// Resident blocks of the selection kernel per SM (occupancy limit).
+static int select_occupancy(int kind)
 {
     static int cached[4] = {0, 0, 0, 0};
     if (!cached[kind]) {
@@ -609,185 +641,316 @@ static int select_blocks(int kind, int sm_count)
         if (e != cudaSuccess || per_sm < 1) per_sm = 1;
         cached[kind] = per_sm;
     }
-    return sm_count * cached[kind];
+    return cached[kind];
 }
 
+static int select_blocks(int kind, int sm_count)
+{
+    return sm_count * select_occupancy(kind);
+}
+
+// Launch shape of the selection kernel for this graph and kind: the tuned
+// values when set (csaw_set_select_tuning / csaw_autotune_select).
+static void select_shape(const csaw_graph* g, int kind, uint32_t* theta_w, int* blocks)
+{
+    const uint32_t tw = g->tune_theta_w[kind];
+    *theta_w = (tw == 0 || tw > WARP_MAX_DEG) ? WARP_MAX_DEG : tw;
+    const int occ = select_occupancy(kind);
+    int per = (int)g->tune_blocks_per_sm[kind];
+    if (per <= 0 || per > occ) per = occ;
+    *blocks = g->sm_count * per;
+}
+
+// Device counters of one call (zeroed at its start): error flags, the seed
+// count, the edge base of each layer, and eight words per layer.
+enum : int {
+    CT_ERR = 0,
+    CT_NSEEDS = 1,
+    CT_BASE = 2,                      // CT_BASE + l: first edge of layer l (l <= depth)
+    CT_LAYER = CT_BASE + CSAW_MAX_DEPTH + 2,
+    CT_WORDS = CT_LAYER + 8 * CSAW_MAX_DEPTH,
+};
+enum : int { L_N = 0, L_TOTAL = 1, L_ITEMS = 2, L_NEXT = 4, L_NEXT_F = 6 };
+
+struct LayerBufs {
+    uint64_t f_cap = 0, e_cap = 0;
+    uint64_t* F = nullptr;       // frontier keys [f_cap], sorted
+    uint64_t* FO = nullptr;      // instance bounds [n_inst + 1]
+    uint32_t* cnt = nullptr;     // [f_cap]
+    uint32_t* wlist = nullptr;   // [f_cap]
+    uint32_t* clist = nullptr;   // [f_cap]
+    uint64_t* pos = nullptr;     // [f_cap + 1]
+    uint32_t* src = nullptr;     // [e_cap]
+    uint32_t* dst = nullptr;     // [e_cap]
+    uint64_t* cand = nullptr;    // [e_cap] candidate keys (not on the last layer)
+    uint64_t* cand_alt = nullptr;
+    uint32_t* kept = nullptr;
+    uint64_t* kpos = nullptr;    // [e_cap + 1]
+};
+
+struct Pipeline {
+    csaw_graph* g = nullptr;
+    int kind = 0;
+    uint32_t n_inst = 0, depth = 0;
+    uint32_t fanout[CSAW_MAX_DEPTH] = {};
+    bool zero_bias = false;
+    int vbits = 1, kbits = 1;
+    uint64_t vmask = 1;
+    int sel_blocks = 1;
+    uint32_t theta_w = WARP_MAX_DEG;
+    uint32_t k0 = 0, k1 = 0;
+    const uint32_t* key_dev = nullptr;   // plan mode: Philox key in device memory
+    uint64_t* ctr = nullptr;             // [CT_WORDS]
+    void* scan_scr = nullptr;
+    void* sort_scr = nullptr;
+    uint64_t* hub_S = nullptr;
+    uint32_t* hub_bits = nullptr;
+    uint64_t* eoff = nullptr;            // [depth * n_inst + 1]
+    uint64_t* fsize = nullptr;           // [depth * n_inst]
+    uint64_t seeds_cap = 0;
+    uint64_t* seed_keys = nullptr;       // [seeds_cap]
+    uint64_t* seed_alt = nullptr;
+    uint32_t* seed_kept = nullptr;
+    uint64_t* seed_kpos = nullptr;       // [seeds_cap + 1]
+    LayerBufs L[CSAW_MAX_DEPTH];
+
+    uint64_t* lc(uint32_t l, int w) const { return ctr + CT_LAYER + 8 * l + w; }
+
+    void init(csaw_graph* gr, int k, uint32_t ninst, uint32_t dep, const uint32_t* fan, uint64_t seed)
+    {
+        g = gr;
+        kind = k;
+        n_inst = ninst;
+        depth = dep;
+        for (uint32_t l = 0; l < dep; ++l) fanout[l] = fan[l];
+        const int vb = bits_for(g->V - 1);
+        vbits = vb > 0 ? vb : 1;
+        kbits = vbits + bits_for(n_inst > 0 ? n_inst - 1 : 0);
+        vmask = (1ull << vbits) - 1;
+        zero_bias = (kind == CSAW_BIAS_EDGE_WEIGHT && g->min_weight == 0) ||
+                    (kind == CSAW_BIAS_NEIGHBOR_DEGREE && g->zero_degree_target);
+        select_shape(g, kind, &theta_w, &sel_blocks);
+        k0 = (uint32_t)seed;
+        k1 = (uint32_t)(seed >> 32);
+    }
+
+    // Capacities of a layer's per-entry and edge arrays.
+    uint64_t edge_bound(uint32_t l, uint64_t f) const
+    {
+        const uint64_t k = fanout[l] < g->max_degree ? fanout[l] : g->max_degree;
+        return f * k;
+    }
+};
+
+// Layer-0 frontier: sorted distinct (instance, seed) keys.
+static csaw_status enqueue_frontier0(Pipeline& P, const uint32_t* seeds, const uint64_t* inst_off,
+                                     cudaStream_t s)
+{
+    csaw_graph* g = P.g;
+    const uint64_t cap = P.seeds_cap;
+    check_inst_off_kernel<<<grid_for(P.n_inst, 256, g->sm_count), 256, 0, s>>>(inst_off, P.n_inst, (uint32_t*)(P.ctr + CT_ERR));
+    seed_keys_kernel<<<grid_for(cap, 256, g->sm_count), 256, 0, s>>>(
+        seeds, inst_off, P.n_inst, cap, g->V, P.vbits, P.seed_keys, (uint32_t*)(P.ctr + CT_ERR), P.ctr + CT_NSEEDS);
+    uint64_t* sorted = P.seed_keys;
+    if (cap) CSAW_TRY(radix_sort_u64(P.seed_keys, P.seed_alt, P.ctr + CT_NSEEDS, cap, P.kbits, g->sm_count, P.sort_scr, s, &sorted));
+    Visited none;
+    none.n = 0;
+    unique_filter_kernel<<<grid_for(cap, 256, g->sm_count), 256, 0, s>>>(sorted, P.ctr + CT_NSEEDS, none, P.vbits, P.seed_kept);
+    CSAW_TRY(scan_u32(P.seed_kept, P.seed_kpos, P.ctr + CT_NSEEDS, cap, P.scan_scr, P.lc(0, L_N), s));
+    scatter_kept_kernel<<<grid_for(cap, 256, g->sm_count), 256, 0, s>>>(sorted, P.ctr + CT_NSEEDS, P.seed_kept, P.seed_kpos, P.L[0].F);
+    inst_bounds_kernel<<<grid_for((uint64_t)P.n_inst + 1, 256, g->sm_count), 256, 0, s>>>(P.L[0].F, P.lc(0, L_N), P.n_inst, P.vbits, P.L[0].FO);
+    CSAW_CUDA(cudaGetLastError());
+    return CSAW_OK;
+}
+
+// Count/classify and the edge-position scan of layer l.
+static csaw_status enqueue_count(Pipeline& P, uint32_t l, cudaStream_t s)
+{
+    csaw_graph* g = P.g;
+    LayerBufs& B = P.L[l];
+    CountParams cp;
+    cp.off = g->off; cp.col = g->col; cp.w = g->w; cp.deg = g->deg;
+    cp.fkeys = B.F; cp.n_dev = (const unsigned long long*)P.lc(l, L_N); cp.vmask = P.vmask;
+    cp.k = P.fanout[l]; cp.theta_w = P.theta_w; cp.zero_bias = P.zero_bias;
+    cp.cnt = B.cnt; cp.warp_list = B.wlist; cp.cta_list = B.clist;
+    cp.n_items = (unsigned long long*)P.lc(l, L_ITEMS);
+    if (B.f_cap) {
+        switch (P.kind) {
+        case CSAW_BIAS_UNIFORM: CSAW_TRY(launch_count<CSAW_BIAS_UNIFORM>(cp, B.f_cap, g->sm_count, s)); break;
+        case CSAW_BIAS_EDGE_WEIGHT: CSAW_TRY(launch_count<CSAW_BIAS_EDGE_WEIGHT>(cp, B.f_cap, g->sm_count, s)); break;
+        default: CSAW_TRY(launch_count<CSAW_BIAS_NEIGHBOR_DEGREE>(cp, B.f_cap, g->sm_count, s)); break;
+        }
+    }
+    return scan_u32(B.cnt, B.pos, P.lc(l, L_N), B.f_cap, P.scan_scr, P.lc(l, L_TOTAL), s);
+}
+
+// Selection of layer l into its edge buffers, then its offsets.
+static csaw_status enqueue_select(Pipeline& P, uint32_t l, cudaStream_t s)
+{
+    csaw_graph* g = P.g;
+    LayerBufs& B = P.L[l];
+    if (B.f_cap) {
+        SelParams sp;
+        sp.off = g->off; sp.col = g->col; sp.w = g->w; sp.deg = g->deg;
+        sp.fkeys = B.F; sp.vbits = P.vbits; sp.vmask = P.vmask; sp.k = P.fanout[l]; sp.layer = l;
+        sp.k0 = P.k0; sp.k1 = P.k1; sp.key_dev = P.key_dev;
+        sp.zero_bias = P.zero_bias; sp.pos = B.pos; sp.warp_list = B.wlist; sp.cta_list = B.clist;
+        sp.n_items = (const unsigned long long*)P.lc(l, L_ITEMS);
+        sp.next = (unsigned long long*)P.lc(l, L_NEXT);
+        sp.out_src = B.src; sp.out_dst = B.dst; sp.out_cand = (l + 1 < P.depth) ? B.cand : nullptr;
+        sp.scratch_S = P.hub_S; sp.scratch_bits = P.hub_bits; sp.scratch_stride = g->max_degree;
+        switch (P.kind) {
+        case CSAW_BIAS_UNIFORM: CSAW_TRY(launch_select<CSAW_BIAS_UNIFORM>(sp, P.sel_blocks, s)); break;
+        case CSAW_BIAS_EDGE_WEIGHT: CSAW_TRY(launch_select<CSAW_BIAS_EDGE_WEIGHT>(sp, P.sel_blocks, s)); break;
+        default: CSAW_TRY(launch_select<CSAW_BIAS_NEIGHBOR_DEGREE>(sp, P.sel_blocks, s)); break;
+        }
+    }
+    layer_offsets_kernel<<<grid_for((uint64_t)P.n_inst + 1, 256, g->sm_count), 256, 0, s>>>(
+        B.FO, B.pos, P.n_inst, P.ctr + CT_BASE + l, P.eoff + (uint64_t)l * P.n_inst,
+        P.fsize + (uint64_t)l * P.n_inst, P.ctr + CT_BASE + l + 1);
+    CSAW_CUDA(cudaGetLastError());
+    return CSAW_OK;
+}
+
+// Update (Eq. 4): next frontier = sorted distinct picks of layer l that the
+// instance has not visited in layers 0..l.
+static csaw_status enqueue_compact(Pipeline& P, uint32_t l, cudaStream_t s)
+{
+    csaw_graph* g = P.g;
+    LayerBufs& B = P.L[l];
+    LayerBufs& N = P.L[l + 1];
+    uint64_t* sorted = B.cand;
+    if (B.e_cap) CSAW_TRY(radix_sort_u64(B.cand, B.cand_alt, P.lc(l, L_TOTAL), B.e_cap, P.kbits, g->sm_count, P.sort_scr, s, &sorted));
+    Visited vis;
+    vis.n = (int)l + 1;
+    for (uint32_t j = 0; j <= l; ++j) { vis.keys[j] = P.L[j].F; vis.foff[j] = P.L[j].FO; }
+    unique_filter_kernel<<<grid_for(B.e_cap, 256, g->sm_count), 256, 0, s>>>(sorted, P.lc(l, L_TOTAL), vis, P.vbits, B.kept);
+    CSAW_TRY(scan_u32(B.kept, B.kpos, P.lc(l, L_TOTAL), B.e_cap, P.scan_scr, P.lc(l + 1, L_N), s));
+    scatter_kept_kernel<<<grid_for(B.e_cap, 256, g->sm_count), 256, 0, s>>>(sorted, P.lc(l, L_TOTAL), B.kept, B.kpos, N.F);
+    inst_bounds_kernel<<<grid_for((uint64_t)P.n_inst + 1, 256, g->sm_count), 256, 0, s>>>(N.F, P.lc(l + 1, L_N), P.n_inst, P.vbits, N.FO);
+    CSAW_CUDA(cudaGetLastError());
+    return CSAW_OK;
+}
+
+// Buffers shared by every layer (counters, scratch, offsets, seed arrays).
+template <class Alloc>
+static csaw_status alloc_common(Pipeline& P, Alloc&& get)
+{
+    CSAW_TRY(get((void**)&P.ctr, sizeof(uint64_t) * CT_WORDS));
+    CSAW_TRY(get(&P.scan_scr, scan_scratch_bytes(0)));
+    CSAW_TRY(get(&P.sort_scr, sort_scratch_bytes(0)));
+    if (P.g->max_degree > CTA_SMEM_DEG) {
+        CSAW_TRY(get((void**)&P.hub_S, sizeof(uint64_t) * (size_t)P.sel_blocks * P.g->max_degree));
+        CSAW_TRY(get((void**)&P.hub_bits, sizeof(uint32_t) * (size_t)P.sel_blocks * ((P.g->max_degree + 31) / 32)));
+    }
+    const uint64_t ng = (uint64_t)P.depth * P.n_inst + 1;
+    CSAW_TRY(get((void**)&P.eoff, sizeof(uint64_t) * ng));
+    CSAW_TRY(get((void**)&P.fsize, sizeof(uint64_t) * ng));
+    const uint64_t sc = P.seeds_cap ? P.seeds_cap : 1;
+    CSAW_TRY(get((void**)&P.seed_keys, sizeof(uint64_t) * sc));
+    CSAW_TRY(get((void**)&P.seed_alt, sizeof(uint64_t) * sc));
+    CSAW_TRY(get((void**)&P.seed_kept, sizeof(uint32_t) * sc));
+    CSAW_TRY(get((void**)&P.seed_kpos, sizeof(uint64_t) * (sc + 1)));
+    return CSAW_OK;
+}
+
+// Per-entry arrays of layer l (frontier capacity f_cap) and its frontier keys.
+template <class Alloc>
+static csaw_status alloc_entries(Pipeline& P, uint32_t l, uint64_t f_cap, Alloc&& get)
+{
+    LayerBufs& B = P.L[l];
+    B.f_cap = f_cap;
+    const uint64_t f = f_cap ? f_cap : 1;
+    CSAW_TRY(get((void**)&B.F, sizeof(uint64_t) * f));
+    CSAW_TRY(get((void**)&B.FO, sizeof(uint64_t) * ((uint64_t)P.n_inst + 1)));
+    CSAW_TRY(get((void**)&B.cnt, sizeof(uint32_t) * f));
+    CSAW_TRY(get((void**)&B.wlist, sizeof(uint32_t) * f));
+    CSAW_TRY(get((void**)&B.clist, sizeof(uint32_t) * f));
+    CSAW_TRY(get((void**)&B.pos, sizeof(uint64_t) * (f + 1)));
+    return CSAW_OK;
+}
+
+// Edge arrays of layer l (capacity e_cap); src/dst come from `get_out`.
+template <class Alloc, class AllocOut>
+static csaw_status alloc_edges(Pipeline& P, uint32_t l, uint64_t e_cap, Alloc&& get, AllocOut&& get_out)
+{
+    LayerBufs& B = P.L[l];
+    B.e_cap = e_cap;
+    const uint64_t e = e_cap ? e_cap : 1;
+    CSAW_TRY(get_out((void**)&B.src, sizeof(uint32_t) * e));
+    CSAW_TRY(get_out((void**)&B.dst, sizeof(uint32_t) * e));
+    if (l + 1 < P.depth) {
+        if (e_cap >= 0xFFFFFFFFull)
+            return fail(CSAW_ERR_INVALID, "layer %u may produce %llu edges; frontier compaction sorts "
+                        "at most 2^32-1", l, (unsigned long long)e_cap);
+        CSAW_TRY(get((void**)&B.cand, sizeof(uint64_t) * e));
+        CSAW_TRY(get((void**)&B.cand_alt, sizeof(uint64_t) * e));
+        CSAW_TRY(get((void**)&B.kept, sizeof(uint32_t) * e));
+        CSAW_TRY(get((void**)&B.kpos, sizeof(uint64_t) * (e + 1)));
+    }
+    return CSAW_OK;
+}
+
+static csaw_status check_errors(uint64_t err)
+{
+    if (err & 1u) return fail(CSAW_ERR_INVALID, "a seed is not a vertex of the graph");
+    if (err & 2u) return fail(CSAW_ERR_INVALID, "inst_offsets must start at 0 and be non-decreasing");
+    if (err & 4u) return fail(CSAW_ERR_INVALID, "more seeds than the plan was created for");
+    return CSAW_OK;
+}
+
+// csaw_sample: exact edge buffers, one wait per layer.
 static csaw_status run_sample(csaw_graph* g, const uint32_t* seeds, const uint64_t* inst_off,
                               uint32_t n_inst, uint64_t n_seeds, uint32_t depth, const uint32_t* fanout,
                               int kind, uint64_t rng_seed, cudaStream_t s, csaw_sample_result* R)
 {
     Temps tmp(s);
-    const int vbits = bits_for(g->V - 1) > 0 ? bits_for(g->V - 1) : 1;
-    const int ibits = bits_for(n_inst > 0 ? n_inst - 1 : 0);
-    const int kbits = vbits + ibits;
-    const uint64_t vmask = (vbits >= 64) ? ~0ull : ((1ull << vbits) - 1);
-    const bool zero_bias = (kind == CSAW_BIAS_EDGE_WEIGHT && g->min_weight == 0) ||
-                           (kind == CSAW_BIAS_NEIGHBOR_DEGREE && g->zero_degree_target);
-
-    uint64_t* d_scalars;   // [0] err flags, [1] n_seeds, [2] total, [3] frontier count ...
-    CSAW_TRY(tmp.get(&d_scalars, 16));
-    CSAW_CUDA(cudaMemsetAsync(d_scalars, 0, 16 * sizeof(uint64_t), s));
-    uint32_t* d_err = (uint32_t*)d_scalars;
-    uint64_t* d_nseeds = d_scalars + 1;
-    CSAW_CUDA(cudaMemcpyAsync(d_nseeds, &n_seeds, sizeof(uint64_t), cudaMemcpyHostToDevice, s));
-
-    void* scan_scr;
-    CSAW_TRY(tmp.get((unsigned char**)&scan_scr, scan_scratch_bytes(0)));
-    void* sort_scr;
-    CSAW_TRY(tmp.get((unsigned char**)&sort_scr, sort_scratch_bytes(0)));
-
-    // Layer-0 frontier: sorted unique (instance, seed) keys.
-    std::vector<uint64_t*> F(depth, nullptr), FO(depth, nullptr);
-    std::vector<uint64_t> fcount(depth, 0);
-    {
-        uint64_t *keys, *alt, *kpos;
-        uint32_t* kept;
-        const uint64_t ns = n_seeds ? n_seeds : 1;
-        CSAW_TRY(tmp.get(&keys, ns));
-        CSAW_TRY(tmp.get(&alt, ns));
-        CSAW_TRY(tmp.get(&kept, ns));
-        CSAW_TRY(tmp.get(&kpos, ns + 1));
-        check_inst_off_kernel<<<grid_for(n_inst, 256, g->sm_count), 256, 0, s>>>(inst_off, n_inst, d_err);
-        if (n_seeds)
-            seed_keys_kernel<<<grid_for(n_seeds, 256, g->sm_count), 256, 0, s>>>(
-                seeds, inst_off, n_inst, n_seeds, g->V, vbits, keys, d_err);
-        uint64_t* sorted = keys;
-        if (n_seeds) CSAW_TRY(radix_sort_u64(keys, alt, d_nseeds, n_seeds, kbits, g->sm_count, sort_scr, s, &sorted));
-        Visited none;
-        none.n = 0;
-        unique_filter_kernel<<<grid_for(n_seeds, 256, g->sm_count), 256, 0, s>>>(sorted, d_nseeds, none, vbits, kept);
-        uint64_t* d_fc = d_scalars + 3;
-        CSAW_TRY(scan_u32(kept, kpos, d_nseeds, n_seeds, scan_scr, d_fc, s));
-        uint64_t h[2];
-        CSAW_CUDA(cudaMemcpyAsync(h, d_scalars, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
-        uint64_t hfc = 0;
-        CSAW_CUDA(cudaMemcpyAsync(&hfc, d_fc, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
-        CSAW_CUDA(cudaStreamSynchronize(s));
-        const uint32_t err = (uint32_t)h[0];
-        if (err & 1u) return fail(CSAW_ERR_INVALID, "a seed is not a vertex of the graph");
-        if (err & 2u) return fail(CSAW_ERR_INVALID, "inst_offsets must start at 0 and be non-decreasing");
-        fcount[0] = hfc;
-        CSAW_TRY(tmp.get(&F[0], hfc ? hfc : 1));
-        CSAW_TRY(tmp.get(&FO[0], (uint64_t)n_inst + 1));
-        scatter_kept_kernel<<<grid_for(n_seeds, 256, g->sm_count), 256, 0, s>>>(sorted, d_nseeds, kept, kpos, F[0]);
-        inst_bounds_kernel<<<grid_for((uint64_t)n_inst + 1, 256, g->sm_count), 256, 0, s>>>(F[0], d_fc, n_inst, vbits, FO[0]);
-        CSAW_CUDA(cudaGetLastError());
-    }
-
-    // Result arrays for offsets and sizes (device), copied to the host at the end.
-    uint64_t *d_eoff, *d_fsize;
-    CSAW_TRY(tmp.get(&d_eoff, (uint64_t)depth * n_inst + 1));
-    CSAW_TRY(tmp.get(&d_fsize, (uint64_t)depth * n_inst + 1));
+    auto get = [&](void** p, size_t bytes) -> csaw_status {
+        CSAW_TRY(dalloc(p, bytes, s));
+        tmp.ptrs.push_back(*p);
+        return CSAW_OK;
+    };
+    auto get_out = [&](void** p, size_t bytes) -> csaw_status { return dalloc(p, bytes, s); };
+    Pipeline P;
+    P.init(g, kind, n_inst, depth, fanout, rng_seed);
+    P.seeds_cap = n_seeds;
+    CSAW_TRY(alloc_common(P, get));
+    CSAW_CUDA(cudaMemsetAsync(P.ctr, 0, sizeof(uint64_t) * CT_WORDS, s));
+    CSAW_TRY(alloc_entries(P, 0, n_seeds, get));
+    CSAW_TRY(enqueue_frontier0(P, seeds, inst_off, s));
     R->src.assign(depth, nullptr);
     R->dst.assign(depth, nullptr);
     R->layer_edges.assign(depth, 0);
-    uint64_t base = 0;
-    const int sel_blocks = select_blocks(kind, g->sm_count);
-    uint64_t* scratch_S = nullptr;
-    uint32_t* scratch_bits = nullptr;
-    if (g->max_degree > CTA_SMEM_DEG) {
-        CSAW_TRY(tmp.get(&scratch_S, (uint64_t)sel_blocks * g->max_degree));
-        CSAW_TRY(tmp.get(&scratch_bits, (uint64_t)sel_blocks * ((g->max_degree + 31) / 32)));
-    }
-
     for (uint32_t l = 0; l < depth; ++l) {
-        const uint64_t n = fcount[l];
-        const uint32_t k = fanout[l];
-        uint64_t* d_n = d_scalars + 4;   // entries of this layer
-        CSAW_CUDA(cudaMemcpyAsync(d_n, &fcount[l], sizeof(uint64_t), cudaMemcpyHostToDevice, s));
-        uint32_t *cnt, *wlist, *clist;
-        uint64_t* pos;
-        const uint64_t nn = n ? n : 1;
-        CSAW_TRY(tmp.get(&cnt, nn));
-        CSAW_TRY(tmp.get(&wlist, nn));
-        CSAW_TRY(tmp.get(&clist, nn));
-        CSAW_TRY(tmp.get(&pos, nn + 1));
-        unsigned long long* d_items = (unsigned long long*)(d_scalars + 6);   // [6],[7] sizes, [8],[9] counters
-        CSAW_CUDA(cudaMemsetAsync(d_items, 0, 4 * sizeof(uint64_t), s));
-        CountParams cp;
-        cp.off = g->off; cp.col = g->col; cp.w = g->w; cp.deg = g->deg;
-        cp.fkeys = F[l]; cp.n_dev = (const unsigned long long*)d_n; cp.vmask = vmask; cp.k = k;
-        cp.zero_bias = zero_bias; cp.cnt = cnt; cp.warp_list = wlist; cp.cta_list = clist;
-        cp.n_items = d_items;
-        if (n) {
-            switch (kind) {
-            case CSAW_BIAS_UNIFORM: CSAW_TRY(launch_count<CSAW_BIAS_UNIFORM>(cp, n, g->sm_count, s)); break;
-            case CSAW_BIAS_EDGE_WEIGHT: CSAW_TRY(launch_count<CSAW_BIAS_EDGE_WEIGHT>(cp, n, g->sm_count, s)); break;
-            default: CSAW_TRY(launch_count<CSAW_BIAS_NEIGHBOR_DEGREE>(cp, n, g->sm_count, s)); break;
-            }
-        }
-        uint64_t* d_total = d_scalars + 5;
-        CSAW_TRY(scan_u32(cnt, pos, d_n, n, scan_scr, d_total, s));
-        uint64_t total = 0;
-        CSAW_CUDA(cudaMemcpyAsync(&total, d_total, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+        CSAW_TRY(enqueue_count(P, l, s));
+        uint64_t h[2] = {0, 0};
+        CSAW_CUDA(cudaMemcpyAsync(&h[0], P.ctr + CT_ERR, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+        CSAW_CUDA(cudaMemcpyAsync(&h[1], P.lc(l, L_TOTAL), sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
         CSAW_CUDA(cudaStreamSynchronize(s));
+        CSAW_TRY(check_errors(h[0]));
+        const uint64_t total = h[1];
         R->layer_edges[l] = total;
-        void* ps = nullptr;
-        void* pd = nullptr;
-        CSAW_CUDA(cudaMalloc(&ps, (total ? total : 1) * sizeof(uint32_t)));
-        R->src[l] = (uint32_t*)ps;
-        CSAW_CUDA(cudaMalloc(&pd, (total ? total : 1) * sizeof(uint32_t)));
-        R->dst[l] = (uint32_t*)pd;
-        const bool last = l + 1 == depth;
-        uint64_t *cand = nullptr, *cand_alt = nullptr;
-        if (!last) {
-            CSAW_TRY(tmp.get(&cand, total ? total : 1));
-            CSAW_TRY(tmp.get(&cand_alt, total ? total : 1));
+        CSAW_TRY(alloc_edges(P, l, total, get, get_out));
+        R->src[l] = P.L[l].src;
+        R->dst[l] = P.L[l].dst;
+        CSAW_TRY(enqueue_select(P, l, s));
+        if (l + 1 < depth) {
+            CSAW_TRY(alloc_entries(P, l + 1, total, get));
+            CSAW_TRY(enqueue_compact(P, l, s));
         }
-        if (n) {
-            SelParams sp;
-            sp.off = g->off; sp.col = g->col; sp.w = g->w; sp.deg = g->deg;
-            sp.fkeys = F[l]; sp.vbits = vbits; sp.vmask = vmask; sp.k = k; sp.layer = l;
-            sp.k0 = (uint32_t)rng_seed; sp.k1 = (uint32_t)(rng_seed >> 32);
-            sp.zero_bias = zero_bias; sp.pos = pos; sp.warp_list = wlist; sp.cta_list = clist;
-            sp.n_items = d_items; sp.next = d_items + 2;
-            sp.out_src = R->src[l]; sp.out_dst = R->dst[l]; sp.out_cand = cand;
-            sp.scratch_S = scratch_S; sp.scratch_bits = scratch_bits; sp.scratch_stride = g->max_degree;
-            switch (kind) {
-            case CSAW_BIAS_UNIFORM: CSAW_TRY(launch_select<CSAW_BIAS_UNIFORM>(sp, sel_blocks, s)); break;
-            case CSAW_BIAS_EDGE_WEIGHT: CSAW_TRY(launch_select<CSAW_BIAS_EDGE_WEIGHT>(sp, sel_blocks, s)); break;
-            default: CSAW_TRY(launch_select<CSAW_BIAS_NEIGHBOR_DEGREE>(sp, sel_blocks, s)); break;
-            }
-        }
-        layer_offsets_kernel<<<grid_for((uint64_t)n_inst + 1, 256, g->sm_count), 256, 0, s>>>(
-            FO[l], pos, n_inst, base, d_eoff + (uint64_t)l * n_inst, d_fsize + (uint64_t)l * n_inst);
-        CSAW_CUDA(cudaGetLastError());
-        base += total;
-        if (last) break;
-        // Update: next frontier = sorted unique picks minus visited.
-        uint64_t* sorted = cand;
-        if (total) CSAW_TRY(radix_sort_u64(cand, cand_alt, d_total, total, kbits, g->sm_count, sort_scr, s, &sorted));
-        uint32_t* kept;
-        uint64_t* kpos;
-        CSAW_TRY(tmp.get(&kept, total ? total : 1));
-        CSAW_TRY(tmp.get(&kpos, (total ? total : 1) + 1));
-        Visited vis;
-        vis.n = (int)l + 1;
-        for (uint32_t j = 0; j <= l; ++j) { vis.keys[j] = F[j]; vis.foff[j] = FO[j]; }
-        unique_filter_kernel<<<grid_for(total, 256, g->sm_count), 256, 0, s>>>(sorted, d_total, vis, vbits, kept);
-        uint64_t* d_fc = d_scalars + 10;
-        CSAW_TRY(scan_u32(kept, kpos, d_total, total, scan_scr, d_fc, s));
-        uint64_t hfc = 0;
-        CSAW_CUDA(cudaMemcpyAsync(&hfc, d_fc, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
-        CSAW_CUDA(cudaStreamSynchronize(s));
-        fcount[l + 1] = hfc;
-        CSAW_TRY(tmp.get(&F[l + 1], hfc ? hfc : 1));
-        CSAW_TRY(tmp.get(&FO[l + 1], (uint64_t)n_inst + 1));
-        scatter_kept_kernel<<<grid_for(total, 256, g->sm_count), 256, 0, s>>>(sorted, d_total, kept, kpos, F[l + 1]);
-        inst_bounds_kernel<<<grid_for((uint64_t)n_inst + 1, 256, g->sm_count), 256, 0, s>>>(F[l + 1], d_fc, n_inst, vbits, FO[l + 1]);
-        CSAW_CUDA(cudaGetLastError());
     }
-    R->n_edges = base;
-    R->edge_offsets.assign((size_t)depth * n_inst + 1, 0);
-    R->frontier_sizes.assign((size_t)depth * n_inst, 0);
-    if (depth * (uint64_t)n_inst > 0) {
-        CSAW_CUDA(cudaMemcpyAsync(R->edge_offsets.data(), d_eoff, sizeof(uint64_t) * ((size_t)depth * n_inst + 1),
-                                  cudaMemcpyDeviceToHost, s));
-        CSAW_CUDA(cudaMemcpyAsync(R->frontier_sizes.data(), d_fsize, sizeof(uint64_t) * (size_t)depth * n_inst,
-                                  cudaMemcpyDeviceToHost, s));
+    const uint64_t ng = (uint64_t)depth * n_inst;
+    R->edge_offsets.assign(ng + 1, 0);
+    R->frontier_sizes.assign(ng, 0);
+    if (ng) {
+        CSAW_CUDA(cudaMemcpyAsync(R->edge_offsets.data(), P.eoff, sizeof(uint64_t) * (ng + 1), cudaMemcpyDeviceToHost, s));
+        CSAW_CUDA(cudaMemcpyAsync(R->frontier_sizes.data(), P.fsize, sizeof(uint64_t) * ng, cudaMemcpyDeviceToHost, s));
     }
     CSAW_CUDA(cudaStreamSynchronize(s));
-    R->edge_offsets[(size_t)depth * n_inst] = base;
+    uint64_t total = 0;
+    for (uint32_t l = 0; l < depth; ++l) total += R->layer_edges[l];
+    R->n_edges = total;
+    R->edge_offsets[ng] = total;
     R->src_c.assign(R->src.begin(), R->src.end());
     R->dst_c.assign(R->dst.begin(), R->dst.end());
     return CSAW_OK;
@@ -810,6 +973,8 @@ extern "C" csaw_status csaw_sample(csaw_graph* g, const uint32_t* seeds, const u
     CSAW_TRY(check_bias(g, bias, false, &kind));
     if (depth < 1 || depth > CSAW_MAX_DEPTH) return fail(CSAW_ERR_INVALID, "depth must be 1..%u", CSAW_MAX_DEPTH);
     if (!fanout) return fail(CSAW_ERR_INVALID, "fanout is NULL");
+    for (uint32_t l = 0; l < depth; ++l)
+        if (fanout[l] == 0) return fail(CSAW_ERR_INVALID, "fanout[%u] is 0", l);
     if (!inst_offsets) return fail(CSAW_ERR_INVALID, "inst_offsets is NULL");
     if (mem_kind != CSAW_MEM_HOST && mem_kind != CSAW_MEM_DEVICE)
         return fail(CSAW_ERR_INVALID, "bad mem_kind %d", mem_kind);
@@ -820,7 +985,6 @@ extern "C" csaw_status csaw_sample(csaw_graph* g, const uint32_t* seeds, const u
     if (!R) return fail(CSAW_ERR_NOMEM, "host allocation failed");
     R->depth = depth;
     R->n_instances = n_instances;
-    cudaGetDevice(&R->device);
 
     uint64_t n_seeds = 0;
     const uint32_t* d_seeds = seeds;
@@ -899,9 +1063,326 @@ extern "C" csaw_status csaw_sample_copy_edges(csaw_sample_result* r, uint32_t* s
     return CSAW_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Sample plans: the whole multi-layer pipeline for a fixed instance count and
+// seed budget, with every buffer at its upper bound, captured once into a
+// CUDA graph.  Each run copies new seeds in and launches the graph: no host
+// waits, no allocation, one launch for all instances and layers.
+
+struct csaw_sample_plan {
+    uint32_t magic = 0x43504c4eu;   // "CPLN"
+    csaw::Pipeline P;
+    std::vector<void*> allocs;
+    uint32_t* in_seeds = nullptr;
+    uint64_t* in_io = nullptr;
+    uint32_t* in_key = nullptr;
+    uint64_t max_seeds = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t last = nullptr;
+    bool ran = false;
+    std::vector<uint64_t> h_eoff, h_fsize, h_layer_edges;
+    std::vector<const uint32_t*> src_c, dst_c;
+    ~csaw_sample_plan()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        for (void* p : allocs) cudaFree(p);
+    }
+};
+
+namespace csaw {
+
+static inline uint64_t sat_mul(uint64_t a, uint64_t b)
+{
+    if (a == 0 || b == 0) return 0;
+    return a > UINT64_MAX / b ? UINT64_MAX : a * b;
+}
+
+}  // namespace csaw
+
+extern "C" csaw_status csaw_sample_plan_create(csaw_graph* g, uint32_t n_instances, uint64_t max_seeds,
+                                               uint32_t depth, const uint32_t* fanout, const csaw_bias* bias,
+                                               csaw_sample_plan** out)
+{
+    clear_error();
+    if (!out) return fail(CSAW_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!g) return fail(CSAW_ERR_INVALID, "graph is NULL");
+    int kind;
+    CSAW_TRY(check_bias(g, bias, false, &kind));
+    if (depth < 1 || depth > CSAW_MAX_DEPTH) return fail(CSAW_ERR_INVALID, "depth must be 1..%u", CSAW_MAX_DEPTH);
+    if (!fanout) return fail(CSAW_ERR_INVALID, "fanout is NULL");
+    for (uint32_t l = 0; l < depth; ++l)
+        if (fanout[l] == 0) return fail(CSAW_ERR_INVALID, "fanout[%u] is 0", l);
+    if (n_instances == 0 || n_instances == 0xFFFFFFFFu) return fail(CSAW_ERR_INVALID, "bad instance count");
+    if (max_seeds == 0 || max_seeds >= 0xFFFFFFFFull) return fail(CSAW_ERR_INVALID, "bad seed budget");
+    csaw_sample_plan* pl = new (std::nothrow) csaw_sample_plan();
+    if (!pl) return fail(CSAW_ERR_NOMEM, "host allocation failed");
+    Pipeline& P = pl->P;
+    P.init(g, kind, n_instances, depth, fanout, 0);
+    P.seeds_cap = max_seeds;
+    pl->max_seeds = max_seeds;
+    auto get = [&](void** p, size_t bytes) -> csaw_status {
+        cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+        if (e != cudaSuccess) { *p = nullptr; return cuda_fail(e, "cudaMalloc(plan)"); }
+        pl->allocs.push_back(*p);
+        return CSAW_OK;
+    };
+    csaw_status st = alloc_common(P, get);
+    // Upper bounds: a layer emits at most min(k, max degree) edges per
+    // frontier vertex; a frontier is at most the previous layer's edges and
+    // at most one entry per (instance, vertex).
+    uint64_t f = max_seeds;
+    const uint64_t fmax = sat_mul(n_instances, g->V);
+    for (uint32_t l = 0; st == CSAW_OK && l < depth; ++l) {
+        st = alloc_entries(P, l, f, get);
+        const uint64_t e = P.edge_bound(l, f);
+        if (st == CSAW_OK) st = alloc_edges(P, l, e, get, get);
+        f = e < fmax ? e : fmax;
+    }
+    if (st == CSAW_OK) st = get((void**)&pl->in_seeds, sizeof(uint32_t) * max_seeds);
+    if (st == CSAW_OK) st = get((void**)&pl->in_io, sizeof(uint64_t) * ((size_t)n_instances + 1));
+    if (st == CSAW_OK) st = get((void**)&pl->in_key, 2 * sizeof(uint32_t));
+    if (st != CSAW_OK) { delete pl; return st; }
+    P.key_dev = pl->in_key;
+    cudaStream_t cs;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { delete pl; return cuda_fail(e, "cudaStreamCreate"); }
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        e = cudaMemsetAsync(P.ctr, 0, sizeof(uint64_t) * CT_WORDS, cs);
+        if (e != cudaSuccess) st = cuda_fail(e, "memset");
+        if (st == CSAW_OK) st = enqueue_frontier0(P, pl->in_seeds, pl->in_io, cs);
+        for (uint32_t l = 0; st == CSAW_OK && l < depth; ++l) {
+            st = enqueue_count(P, l, cs);
+            if (st == CSAW_OK) st = enqueue_select(P, l, cs);
+            if (st == CSAW_OK && l + 1 < depth) st = enqueue_compact(P, l, cs);
+        }
+        cudaGraph_t gr = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(cs, &gr);
+        if (st == CSAW_OK && e2 != cudaSuccess) st = cuda_fail(e2, "cudaStreamEndCapture");
+        if (st == CSAW_OK) {
+            pl->graph = gr;
+            e2 = cudaGraphInstantiate(&pl->exec, gr, 0);
+            if (e2 != cudaSuccess) st = cuda_fail(e2, "cudaGraphInstantiate");
+        } else if (gr) {
+            cudaGraphDestroy(gr);
+        }
+    } else {
+        st = cuda_fail(e, "cudaStreamBeginCapture");
+    }
+    cudaStreamDestroy(cs);
+    if (st != CSAW_OK) { delete pl; return st; }
+    *out = pl;
+    return CSAW_OK;
+}
+
+extern "C" csaw_status csaw_sample_plan_run(csaw_sample_plan* pl, const uint32_t* seeds, uint64_t n_seeds,
+                                            const uint64_t* inst_offsets, uint64_t rng_seed, int mem_kind,
+                                            void* stream)
+{
+    clear_error();
+    if (!pl) return fail(CSAW_ERR_INVALID, "plan is NULL");
+    if (!inst_offsets || (n_seeds && !seeds)) return fail(CSAW_ERR_INVALID, "NULL input");
+    if (n_seeds > pl->max_seeds)
+        return fail(CSAW_ERR_INVALID, "%llu seeds, plan holds %llu", (unsigned long long)n_seeds,
+                    (unsigned long long)pl->max_seeds);
+    if (mem_kind != CSAW_MEM_HOST && mem_kind != CSAW_MEM_DEVICE)
+        return fail(CSAW_ERR_INVALID, "bad mem_kind %d", mem_kind);
+    const uint32_t n_inst = pl->P.n_inst;
+    if (mem_kind == CSAW_MEM_HOST) {
+        if (inst_offsets[0] != 0 || inst_offsets[n_inst] != n_seeds)
+            return fail(CSAW_ERR_INVALID, "inst_offsets must run from 0 to n_seeds");
+        for (uint32_t i = 0; i < n_inst; ++i)
+            if (inst_offsets[i + 1] < inst_offsets[i]) return fail(CSAW_ERR_INVALID, "inst_offsets must be non-decreasing");
+        for (uint64_t j = 0; j < n_seeds; ++j)
+            if (seeds[j] >= pl->P.g->V) return fail(CSAW_ERR_INVALID, "seed %llu out of range", (unsigned long long)j);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const cudaMemcpyKind k = mem_kind == CSAW_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    const uint32_t key[2] = {(uint32_t)rng_seed, (uint32_t)(rng_seed >> 32)};
+    if (n_seeds) CSAW_CUDA(cudaMemcpyAsync(pl->in_seeds, seeds, sizeof(uint32_t) * n_seeds, k, s));
+    CSAW_CUDA(cudaMemcpyAsync(pl->in_io, inst_offsets, sizeof(uint64_t) * ((size_t)n_inst + 1), k, s));
+    CSAW_CUDA(cudaMemcpyAsync(pl->in_key, key, sizeof(key), cudaMemcpyHostToDevice, s));
+    CSAW_CUDA(cudaGraphLaunch(pl->exec, s));
+    pl->last = s;
+    pl->ran = true;
+    return CSAW_OK;
+}
+
+// Wait for the plan's last run and read its offsets and sizes.
+static csaw_status plan_collect(csaw_sample_plan* pl)
+{
+    if (!pl->ran) return fail(CSAW_ERR_INVALID, "the plan has not run");
+    Pipeline& P = pl->P;
+    CSAW_CUDA(cudaStreamSynchronize(pl->last));
+    const uint64_t ng = (uint64_t)P.depth * P.n_inst;
+    pl->h_eoff.assign(ng + 1, 0);
+    pl->h_fsize.assign(ng ? ng : 1, 0);
+    std::vector<uint64_t> ctr(CT_WORDS, 0);
+    CSAW_CUDA(cudaMemcpy(ctr.data(), P.ctr, sizeof(uint64_t) * CT_WORDS, cudaMemcpyDeviceToHost));
+    CSAW_TRY(check_errors(ctr[CT_ERR]));
+    CSAW_CUDA(cudaMemcpy(pl->h_eoff.data(), P.eoff, sizeof(uint64_t) * (ng + 1), cudaMemcpyDeviceToHost));
+    if (ng) CSAW_CUDA(cudaMemcpy(pl->h_fsize.data(), P.fsize, sizeof(uint64_t) * ng, cudaMemcpyDeviceToHost));
+    pl->h_layer_edges.assign(P.depth, 0);
+    for (uint32_t l = 0; l < P.depth; ++l) pl->h_layer_edges[l] = ctr[CT_LAYER + 8 * l + L_TOTAL];
+    pl->src_c.assign(P.depth, nullptr);
+    pl->dst_c.assign(P.depth, nullptr);
+    for (uint32_t l = 0; l < P.depth; ++l) { pl->src_c[l] = P.L[l].src; pl->dst_c[l] = P.L[l].dst; }
+    return CSAW_OK;
+}
+
+extern "C" csaw_status csaw_sample_plan_get_view(csaw_sample_plan* pl, csaw_sample_view* view)
+{
+    clear_error();
+    if (!pl || !view) return fail(CSAW_ERR_INVALID, "NULL argument");
+    CSAW_TRY(plan_collect(pl));
+    view->depth = pl->P.depth;
+    view->n_instances = pl->P.n_inst;
+    view->n_edges = pl->h_eoff.back();
+    view->edge_offsets = pl->h_eoff.data();
+    view->frontier_sizes = pl->h_fsize.data();
+    view->src = pl->src_c.data();
+    view->dst = pl->dst_c.data();
+    return CSAW_OK;
+}
+
+extern "C" csaw_status csaw_sample_plan_copy_edges(csaw_sample_plan* pl, uint32_t* src, uint32_t* dst)
+{
+    clear_error();
+    if (!pl) return fail(CSAW_ERR_INVALID, "plan is NULL");
+    CSAW_TRY(plan_collect(pl));
+    uint64_t at = 0;
+    for (uint32_t l = 0; l < pl->P.depth; ++l) {
+        const uint64_t n = pl->h_layer_edges[l];
+        if (n) {
+            if (!src || !dst) return fail(CSAW_ERR_INVALID, "NULL output");
+            CSAW_CUDA(cudaMemcpy(src + at, pl->P.L[l].src, n * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+            CSAW_CUDA(cudaMemcpy(dst + at, pl->P.L[l].dst, n * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+        }
+        at += n;
+    }
+    return CSAW_OK;
+}
+
+extern "C" csaw_status csaw_sample_plan_get_info(const csaw_sample_plan* pl, uint64_t* device_bytes,
+                                                 uint32_t* theta_warp, uint32_t* select_blocks)
+{
+    clear_error();
+    if (!pl) return fail(CSAW_ERR_INVALID, "plan is NULL");
+    if (device_bytes) {
+        uint64_t b = 0;
+        // sizes are not recorded per allocation; report capacities
+        const Pipeline& P = pl->P;
+        for (uint32_t l = 0; l < P.depth; ++l)
+            b += P.L[l].f_cap * 28 + P.L[l].e_cap * (8 + (l + 1 < P.depth ? 28 : 0));
+        b += P.seeds_cap * 28 + pl->max_seeds * 4;
+        *device_bytes = b;
+    }
+    if (theta_warp) *theta_warp = pl->P.theta_w;
+    if (select_blocks) *select_blocks = (uint32_t)pl->P.sel_blocks;
+    return CSAW_OK;
+}
+
+extern "C" csaw_status csaw_sample_plan_destroy(csaw_sample_plan* pl)
+{
+    clear_error();
+    if (pl && pl->ran) cudaStreamSynchronize(pl->last);
+    delete pl;
+    return CSAW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Launch-shape tuning of the selection path.
+
+extern "C" csaw_status csaw_set_select_tuning(csaw_graph* g, int32_t bias_kind, const csaw_select_tuning* t)
+{
+    clear_error();
+    if (!g || !t) return fail(CSAW_ERR_INVALID, "NULL argument");
+    if (bias_kind < 0 || bias_kind > CSAW_BIAS_NEIGHBOR_DEGREE) return fail(CSAW_ERR_INVALID, "bad bias kind");
+    if (t->theta_warp > WARP_MAX_DEG) return fail(CSAW_ERR_INVALID, "theta_warp above %u", WARP_MAX_DEG);
+    g->tune_theta_w[bias_kind] = t->theta_warp;
+    g->tune_blocks_per_sm[bias_kind] = t->blocks_per_sm;
+    return CSAW_OK;
+}
+
+extern "C" csaw_status csaw_get_select_tuning(const csaw_graph* g, int32_t bias_kind, csaw_select_tuning* t)
+{
+    clear_error();
+    if (!g || !t) return fail(CSAW_ERR_INVALID, "NULL argument");
+    if (bias_kind < 0 || bias_kind > CSAW_BIAS_NEIGHBOR_DEGREE) return fail(CSAW_ERR_INVALID, "bad bias kind");
+    uint32_t tw;
+    int blocks;
+    select_shape(g, bias_kind, &tw, &blocks);
+    t->theta_warp = tw;
+    t->blocks_per_sm = (uint32_t)(blocks / (g->sm_count > 0 ? g->sm_count : 1));
+    return CSAW_OK;
+}
+
+extern "C" csaw_status csaw_autotune_select(csaw_graph* g, const uint32_t* seeds, const uint64_t* inst_offsets,
+                                            uint32_t n_instances, uint32_t depth, const uint32_t* fanout,
+                                            const csaw_bias* bias, uint64_t rng_seed, void* stream,
+                                            csaw_select_tuning* best)
+{
+    clear_error();
+    if (!g || !best) return fail(CSAW_ERR_INVALID, "NULL argument");
+    int kind;
+    CSAW_TRY(check_bias(g, bias, false, &kind));
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint32_t thetas[] = {32, 64, 128, 256};
+    const int occ = select_occupancy(kind);
+    cudaEvent_t e0, e1;
+    CSAW_CUDA(cudaEventCreate(&e0));
+    CSAW_CUDA(cudaEventCreate(&e1));
+    float best_ms = -1.f;
+    csaw_select_tuning bt = {WARP_MAX_DEG, (uint32_t)occ};
+    const uint32_t saved_t = g->tune_theta_w[kind], saved_b = g->tune_blocks_per_sm[kind];
+    csaw_status st = CSAW_OK;
+    for (uint32_t th : thetas) {
+        for (int per = 1; per <= occ && st == CSAW_OK; ++per) {
+            g->tune_theta_w[kind] = th;
+            g->tune_blocks_per_sm[kind] = (uint32_t)per;
+            float ms = 0.f;
+            for (int rep = 0; rep < 2 && st == CSAW_OK; ++rep) {   // first run warms up
+                csaw_sample_result* r = nullptr;
+                cudaEventRecord(e0, s);
+                st = csaw_sample(g, seeds, inst_offsets, n_instances, depth, fanout, bias, rng_seed,
+                                 CSAW_MEM_HOST, stream, &r);
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
+                cudaEventElapsedTime(&ms, e0, e1);
+                delete r;
+            }
+            if (st == CSAW_OK && (best_ms < 0.f || ms < best_ms)) {
+                best_ms = ms;
+                bt.theta_warp = th;
+                bt.blocks_per_sm = (uint32_t)per;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != CSAW_OK) {
+        g->tune_theta_w[kind] = saved_t;
+        g->tune_blocks_per_sm[kind] = saved_b;
+        return st;
+    }
+    g->tune_theta_w[kind] = bt.theta_warp;
+    g->tune_blocks_per_sm[kind] = bt.blocks_per_sm;
+    *best = bt;
+    return CSAW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Results returned by this library start with a tag naming their type.
+
 extern "C" void csaw_result_free(void* result)
 {
-    delete (csaw_sample_result*)result;
+    if (!result) return;
+    const uint32_t tag = *(const uint32_t*)result;
+    if (tag == 0x43534d50u) delete (csaw_sample_result*)result;
+    else csaw::free_server_result(result);
 }
 
 // ---------------------------------------------------------------------------
@@ -1032,7 +1513,7 @@ extern "C" csaw_status csaw_select_noalloc(csaw_graph* g, const uint32_t* vertic
     cp.off = g->off; cp.col = g->col; cp.w = g->w; cp.deg = g->deg;
     cp.fkeys = keys; cp.n_dev = (const unsigned long long*)d_n; cp.vmask = vmask; cp.k = k;
     cp.zero_bias = zero_bias; cp.cnt = cnt; cp.warp_list = wlist; cp.cta_list = clist;
-    cp.n_items = d_items;
+    cp.n_items = d_items; cp.theta_w = WARP_MAX_DEG;
     if (n) {
         switch (kind) {
         case CSAW_BIAS_UNIFORM: CSAW_TRY(launch_count<CSAW_BIAS_UNIFORM>(cp, n, g->sm_count, s)); break;
@@ -1045,7 +1526,7 @@ extern "C" csaw_status csaw_select_noalloc(csaw_graph* g, const uint32_t* vertic
         SelParams sp;
         sp.off = g->off; sp.col = g->col; sp.w = g->w; sp.deg = g->deg;
         sp.fkeys = keys; sp.vbits = vbits; sp.vmask = vmask; sp.k = k; sp.layer = layer;
-        sp.k0 = (uint32_t)rng_seed; sp.k1 = (uint32_t)(rng_seed >> 32);
+        sp.k0 = (uint32_t)rng_seed; sp.k1 = (uint32_t)(rng_seed >> 32); sp.key_dev = nullptr;
         sp.zero_bias = zero_bias; sp.pos = out_offsets; sp.warp_list = wlist; sp.cta_list = clist;
         sp.n_items = d_items; sp.next = d_items + 2;
         sp.out_src = out_src; sp.out_dst = out_dst; sp.out_cand = nullptr;
