@@ -307,6 +307,252 @@ def run_reference(args, rank, world):
     }
 
 
+# --------------------------------------------------------------------------
+# Sampling workloads (not the default line): C-SAW's layered neighbour
+# sampling, one launch per instance against one batched call and against a
+# plan replayed as a CUDA graph; SEPS = sampled edges / GPU time.
+
+def sample_frontier_bytes(res, g, fanout, bias):
+    """Algorithmic bytes of the selection kernels of one run: per frontier
+    vertex v of degree d, 16 (offsets) + 4d (weights, or columns) + 4d
+    (degree gathers, neighbour-degree bias) + 8 per pick (edge written)."""
+    deg = np.diff(g.off).astype(np.int64)
+    n_inst = res.n_instances
+    total = 0
+    for lvl in range(res.depth):
+        a, b = int(res.edge_offsets[lvl * n_inst]), int(res.edge_offsets[(lvl + 1) * n_inst])
+        src = res.src[a:b]
+        # distinct (instance, source) pairs are the frontier vertices that emitted edges
+        inst = np.repeat(np.arange(n_inst), np.diff(res.edge_offsets[lvl * n_inst:(lvl + 1) * n_inst + 1]).astype(np.int64))
+        key = (inst.astype(np.int64) << 32) | src.astype(np.int64)
+        first = np.ones(len(key), dtype=bool)
+        first[1:] = key[1:] != key[:-1]
+        d = deg[src[first].astype(np.int64)]
+        per_row = 4 * d * (2 if bias == "neighbor_degree" else 1)
+        total += int((16 + per_row).sum()) + 8 * (b - a)
+    return total
+
+
+def time_gpu(torch, fn, reps=1):
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(reps):
+        fn()
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_sample_bench(args):
+    import torch
+    from paper_2009_09103_gb300 import build, csaw, inputs
+    build.build()
+    torch.cuda.set_device(0)
+    t0 = time.time()
+    if args.workload == "sample_s12":
+        wl = inputs.workload_sample_s12()
+        desc = ("layered biased neighbour sampling: RMAT scale 12, edge factor 16, weights uniform "
+                "[1,100], 256 uniform seeds as one instance, depth 2, fanout [10,5], edge-weight bias")
+    elif args.scale in (None, 24) and args.instances == 4096:
+        wl = inputs.workload_batched_s24()
+        desc = ("batched layered sampling: RMAT scale 24, edge factor 16, 4096 instances of log-uniform "
+                "[64,8192) distinct seeds, depth 2, fanout [25,10], neighbour-degree bias")
+    else:
+        g0 = inputs.rmat_csr(args.scale, 16, 255, args.scale)
+        sizes = inputs.loguniform_sizes(args.instances, 6.0, 7.0, args.scale, stream=4)
+        sd, io = inputs.distinct_seeds(sizes, g0.V, args.scale, stream=4)
+        wl = inputs.SampleWorkload(g0, sd, io, [25, 10], "neighbor_degree", 4)
+        desc = (f"batched layered sampling: RMAT scale {args.scale}, edge factor 16, {args.instances} instances "
+                "of log-uniform [64,8192) distinct seeds, depth 2, fanout [25,10], neighbour-degree bias")
+    g = wl.graph
+    log(f"[bench] {args.workload}: V={g.V} E={g.E} seeds={len(wl.seeds)} built in {time.time() - t0:.1f}s")
+    G = csaw.Graph(g.off, g.col, g.w)
+    n_inst = len(wl.inst_offsets) - 1
+    out = {}
+    # batched call (csaw_sample over all instances)
+    ref = csaw.sample(G, wl.seeds, wl.inst_offsets, wl.fanout, wl.bias, wl.rng_seed)
+    if args.autotune:
+        out["tuning"] = csaw.autotune_select(G, wl.seeds, wl.inst_offsets, wl.fanout, wl.bias, wl.rng_seed)
+    for _ in range(args.warmup):
+        csaw.sample(G, wl.seeds, wl.inst_offsets, wl.fanout, wl.bias, wl.rng_seed)
+    ms_call = time_gpu(torch, lambda: csaw.sample(G, wl.seeds, wl.inst_offsets, wl.fanout, wl.bias,
+                                                  wl.rng_seed, to_host=False), args.steps)
+    # plan: the same pipeline captured in a CUDA graph (seeds copied in each run)
+    plan = csaw.SamplePlan(G, n_inst, len(wl.seeds), wl.fanout, wl.bias)
+    ds = torch.from_numpy(wl.seeds.view(np.int32)).cuda()
+    dio = torch.from_numpy(wl.inst_offsets.view(np.int64)).cuda()
+    for _ in range(args.warmup):
+        plan.run(ds, dio, wl.rng_seed)
+    ms_plan = time_gpu(torch, lambda: plan.run(ds, dio, wl.rng_seed), args.steps)
+    got = plan.result()
+    plan_ok = bool(np.array_equal(got.dst, ref.dst) and np.array_equal(got.edge_offsets, ref.edge_offsets))
+    # one call per instance (each instance alone at its own index)
+    n_plain = min(n_inst, args.plain_instances)
+    pick = np.linspace(0, n_inst - 1, n_plain).astype(np.int64)
+    calls = []
+    for i in pick:
+        sub = np.zeros(n_inst + 1, dtype=np.uint64)
+        sub[i + 1:] = wl.inst_offsets[i + 1] - wl.inst_offsets[i]
+        calls.append((wl.seeds[wl.inst_offsets[i]:wl.inst_offsets[i + 1]].copy(), sub))
+    def plain():
+        for s_, io_ in calls:
+            csaw.sample(G, s_, io_, wl.fanout, wl.bias, wl.rng_seed, to_host=False)
+    ms_plain_sub = float("nan")
+    if n_plain:
+        plain()
+        ms_plain_sub = time_gpu(torch, plain, 1)
+    edges_sub = sum(int(ref.edge_offsets[l * n_inst + i + 1] - ref.edge_offsets[l * n_inst + i])
+                    for i in pick for l in range(len(wl.fanout)))
+    edges = int(ref.n_edges)
+    alg = sample_frontier_bytes(ref, g, wl.fanout, wl.bias)
+    peak, peak_kind = measured_peaks()
+    res = {
+        "metric": METRIC, "value": edges / (ms_plan / 1e3), "unit": "edges/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_plan, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32 biases / u64 prefix sums",
+        "data": "synthetic (seeded RMAT)",
+        "config": {"workload": desc, "sampled_edges_per_step": edges, "instances": n_inst},
+        "batched_plan_cuda_graph": {"ms": ms_plan, "seps": edges / (ms_plan / 1e3), "matches_sample": plan_ok,
+                                    **plan.info()},
+        "batched_call": {"ms": ms_call, "seps": edges / (ms_call / 1e3)},
+        "plain_one_call_per_instance": {"instances_timed": int(n_plain), "ms": ms_plain_sub,
+                                         "seps": edges_sub / (ms_plain_sub / 1e3)},
+        "selection_bytes_per_run": alg,
+        "gbs_over_whole_run": alg / (ms_plan / 1e3) / 1e9, "peak_gbs": peak, "peak_source": peak_kind,
+        **out,
+    }
+    plan.close()
+    G.close()
+    return res
+
+
+# --------------------------------------------------------------------------
+# Serving (not the default line): open-loop Poisson arrivals of a 50/50 mix of
+# sampling and walk requests into csaw_server, against the same requests run
+# one after another with plain calls.
+
+def serving_requests(g, n, seed):
+    from paper_2009_09103_gb300 import inputs
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(n):
+        if i % 2 == 0:
+            ns = max(1, int(2 ** (14 * rng.random())))
+            seeds = inputs.uniform_vertices(ns, g.V, 10_000 + i)
+            depth = int(rng.integers(1, 4))
+            fan = [int(x) for x in rng.choice([5, 10, 25], size=depth)]
+            reqs.append(("sample", seeds, np.array([0, ns], dtype=np.uint64), fan, 100 + i))
+        else:
+            nw = max(1, int(2 ** (16 * rng.random())))
+            starts = inputs.uniform_vertices(nw, g.V, 20_000 + i)
+            reqs.append(("walk", starts, int(rng.integers(10, 81)), 200 + i))
+    return reqs
+
+
+def req_edges(r, res):
+    return int(res.sample.n_edges) if r[0] == "sample" else int((res.path[:, 1:] != 0xFFFFFFFF).sum())
+
+
+def run_serve_bench(args):
+    import threading
+    import torch
+    from paper_2009_09103_gb300 import build, csaw, inputs
+    build.build()
+    torch.cuda.set_device(0)
+    t0 = time.time()
+    scale = args.scale or 26
+    g = inputs.rmat_csr(scale, 16, 255, scale)
+    log(f"[bench] serve: graph s{scale} V={g.V} E={g.E} built in {time.time() - t0:.1f}s")
+    G = csaw.Graph(g.off, g.col, g.w)
+    del g.col
+    reqs = serving_requests(g, args.requests, 5)
+    # serial plain service times
+    svc = []
+    edges = []
+    for r in reqs[: min(8, len(reqs))]:   # warm-up
+        if r[0] == "sample":
+            csaw.sample(G, r[1], r[2], r[3], "edge_weight", r[4])
+        else:
+            csaw.walk(G, r[1], r[2], "edge_weight", r[3])
+    torch.cuda.synchronize()
+    for r in reqs:
+        t = time.perf_counter()
+        if r[0] == "sample":
+            res = csaw.sample(G, r[1], r[2], r[3], "edge_weight", r[4])
+            edges.append(int(res.n_edges))
+        else:
+            p = csaw.walk(G, r[1], r[2], "edge_weight", r[3])
+            edges.append(int((p[:, 1:] != 0xFFFFFFFF).sum()))
+        svc.append(time.perf_counter() - t)
+    svc = np.array(svc)
+    total_edges = int(sum(edges))
+    serial_capacity = len(reqs) / svc.sum()
+    serial_seps = total_edges / svc.sum()
+    points = []
+    budget = 40 << 30
+    for frac in args.loads:
+        lam = frac * serial_capacity
+        rng = np.random.default_rng(int(frac * 1000))
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, size=len(reqs)))
+        # serial FIFO queue with the measured service times (one request at a time)
+        fin = np.zeros(len(reqs))
+        prev = 0.0
+        for i in range(len(reqs)):
+            start = max(arrivals[i], prev)
+            fin[i] = start + svc[i]
+            prev = fin[i]
+        lat_serial = fin - arrivals
+        srv = csaw.Server(G, budget_bytes=budget, slots=args.slots)
+        tickets = [None] * len(reqs)
+        base = time.perf_counter() + 0.05
+        def submitter():
+            for i, r in enumerate(reqs):
+                delay = base + arrivals[i] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                if r[0] == "sample":
+                    tickets[i] = (srv.submit_sample(r[1], r[2], r[3], "edge_weight", r[4]), time.perf_counter_ns())
+                else:
+                    tickets[i] = (srv.submit_walk(r[1], r[2], "edge_weight", r[3]), time.perf_counter_ns())
+        th = threading.Thread(target=submitter)
+        th.start()
+        th.join()
+        lat = []
+        first_sub, last_fin = None, 0
+        for i, r in enumerate(reqs):
+            res = srv.poll(tickets[i][0])
+            lat.append((res.t_finish_ns - res.t_submit_ns) / 1e9)
+            first_sub = res.t_submit_ns if first_sub is None else min(first_sub, res.t_submit_ns)
+            last_fin = max(last_fin, res.t_finish_ns)
+        srv.close()
+        span = (last_fin - first_sub) / 1e9
+        lat = np.array(lat)
+        points.append({"load_frac_of_serial_capacity": frac, "arrival_rate_per_s": lam,
+                       "served": {"seps": total_edges / span, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                                  "p99_ms": 1e3 * float(np.percentile(lat, 99))},
+                       "serial_plain": {"seps": total_edges / (fin[-1] - arrivals[0]),
+                                        "p50_ms": 1e3 * float(np.percentile(lat_serial, 50)),
+                                        "p99_ms": 1e3 * float(np.percentile(lat_serial, 99))}})
+        log(f"[bench] load {frac:.2f}: {points[-1]}")
+    G.close()
+    best = max(points, key=lambda p: p["served"]["seps"])
+    return {
+        "metric": METRIC + " and p50/p99 request latency", "value": best["served"]["seps"], "unit": "edges/s",
+        "n_gpus": 1, "steps": len(args.loads), "warmup": 1, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32 biases / u64 prefix sums",
+        "data": "synthetic (seeded RMAT, seeded request mix)",
+        "config": {"workload": f"serving: RMAT scale {scale} edge factor 16 resident; {len(reqs)} requests, "
+                               "50/50 layered sampling (seeds log-uniform [1,16384], depth 1-3, fanout from "
+                               "{5,10,25}) and weighted walks (starts log-uniform [1,65536], length U[10,80]); "
+                               f"Poisson arrivals; 40 GiB admission budget; {args.slots} slots",
+                   "sampled_edges": total_edges},
+        "serial_plain": {"capacity_req_per_s": serial_capacity, "seps": serial_seps},
+        "points": points,
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -315,12 +561,25 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-baseline-seconds", type=float, default=12.0,
                     help="oracle sample budget; 0 skips the CPU baseline")
-    ap.add_argument("--workload", default="walk", choices=["walk", "node2vec"])
+    ap.add_argument("--workload", default="walk",
+                    choices=["walk", "node2vec", "sample_s12", "batched_s24", "serve"])
+    ap.add_argument("--autotune", action="store_true", help="sampling workloads: autotune first")
+    ap.add_argument("--plain-instances", type=int, default=512,
+                    help="batched_s24: instances timed one call each (a uniform subset)")
+    ap.add_argument("--instances", type=int, default=4096, help="batched_s24 at another --scale")
+    ap.add_argument("--requests", type=int, default=200, help="serve: requests per load point")
+    ap.add_argument("--slots", type=int, default=8, help="serve: server slots")
+    ap.add_argument("--loads", type=float, nargs="+", default=[0.25, 0.5, 1.0, 1.5, 3.0],
+                    help="serve: arrival rates as multiples of the serial capacity")
     ap.add_argument("--scale", type=int, default=None, help="RMAT scale (default: the workload's)")
     args = ap.parse_args()
     if args.scale is None:
-        args.scale = {"walk": 20, "node2vec": 22}[args.workload]
+        args.scale = {"walk": 20, "node2vec": 22}.get(args.workload)
     rank, world, local = dist_env()
+    if args.workload in ("sample_s12", "batched_s24", "serve"):
+        res = run_sample_bench(args) if args.workload != "serve" else run_serve_bench(args)
+        print(json.dumps(res), flush=True)
+        return
 
     if args.impl == "reference":
         if world > 1:
