@@ -169,6 +169,8 @@ def run_walk_bench(args, rank, world):
     g = wl.graph
     log(f"[bench] {args.workload} graph: V={g.V} E={g.E} built in {time.time() - t0:.1f}s")
     G = csaw.Graph(g.off, g.col, g.w)
+    if args.cdf and wl.bias != "node2vec":
+        G.build_cdf(wl.bias)
     stream = torch.cuda.current_stream()
     starts = torch.from_numpy(wl.starts.view(np.int32)).to(dev)
     n = starts.numel()
@@ -230,8 +232,19 @@ def run_walk_bench(args, rank, world):
 
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / (ms_per_step / 1e3) / 1e9
-    tr = traffic_record("csaw_walk.cu", f"{args.workload}_s{args.scale}")
+    tr = traffic_record("csaw_walk.cu", f"{args.workload}_s{args.scale}" + ("_cdf" if args.cdf else ""))
     kname = "walk_kernel<NODE2VEC>" if wl.bias == "node2vec" else "walk_kernel<EDGE_WEIGHT>"
+    if args.cdf and wl.bias != "node2vec":
+        kname = "walk_cached_kernel<EDGE_WEIGHT>"
+        # per step: 16 (row offsets) + 8 (row total) + 8 per binary-search probe
+        # (ceil(log2 d) probes) + 4 (picked column) + 4 (path entry)
+        p = path.to(torch.int64) & 0xFFFFFFFF
+        a, b = p[:, :-1], p[:, 1:]
+        real = b != 0xFFFFFFFF
+        deg = (off_t[1:] - off_t[:-1])[a[real]].to(torch.float64)
+        probes = int(torch.ceil(torch.log2(deg.clamp(min=1))).sum())
+        alg_bytes = 16 * n_trans + 8 * n_trans + 8 * probes + 8 * n_trans + 4 * n + 4 * n * (wl.length + 1)
+        achieved = alg_bytes / (ms_per_step / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1),
                 "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
                 "frac": round(achieved / peak, 4),
@@ -245,6 +258,8 @@ def run_walk_bench(args, rank, world):
         "config": {"workload": walk_config(args, wl),
                    "parallelism": "replicas" if world > 1 else "1 GPU",
                    "l2": "flushed (512 MiB write) before every timed step",
+                   "cumulative_array": "cached per edge (built once per graph)" if args.cdf
+                   else "computed per step (streamed over the row)",
                    "sampled_edges_per_step": n_trans},
         "gpu_launches": args.steps,
         "roofline": roofline,
@@ -283,7 +298,7 @@ def run_reference(args, rank, world):
         return None
     wl = walk_workload(args)
     g = wl.graph
-    per_step = max(2.0, min(20.0, 60.0 / max(1, args.steps)))
+    per_step = args.ref_seconds or max(2.0, min(20.0, 60.0 / max(1, args.steps)))
     vals = []
     used_total = 0
     for _ in range(args.warmup):
@@ -369,8 +384,10 @@ def run_sample_bench(args):
     g = wl.graph
     log(f"[bench] {args.workload}: V={g.V} E={g.E} seeds={len(wl.seeds)} built in {time.time() - t0:.1f}s")
     G = csaw.Graph(g.off, g.col, g.w)
+    if args.cdf:
+        G.build_cdf(wl.bias)
     n_inst = len(wl.inst_offsets) - 1
-    out = {}
+    out = {"cumulative_array": "cached per edge" if args.cdf else "computed per selection"}
     # batched call (csaw_sample over all instances)
     ref = csaw.sample(G, wl.seeds, wl.inst_offsets, wl.fanout, wl.bias, wl.rng_seed)
     if args.autotune:
@@ -561,9 +578,13 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-baseline-seconds", type=float, default=12.0,
                     help="oracle sample budget; 0 skips the CPU baseline")
+    ap.add_argument("--ref-seconds", type=float, default=None,
+                    help="--impl reference: oracle seconds per step (default: about a minute in all)")
     ap.add_argument("--workload", default="walk",
                     choices=["walk", "node2vec", "sample_s12", "batched_s24", "serve"])
     ap.add_argument("--autotune", action="store_true", help="sampling workloads: autotune first")
+    ap.add_argument("--cdf", action="store_true",
+                    help="build the cached per-edge cumulative array of the static bias first")
     ap.add_argument("--plain-instances", type=int, default=512,
                     help="batched_s24: instances timed one call each (a uniform subset)")
     ap.add_argument("--instances", type=int, default=4096, help="batched_s24 at another --scale")
@@ -588,6 +609,9 @@ def main():
         res = run_reference(args, rank, world)
         if rank == 0:
             print(json.dumps(res), flush=True)
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
         return
 
     import torch

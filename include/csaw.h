@@ -127,6 +127,22 @@ typedef struct {
 
 csaw_status csaw_graph_get_info(const csaw_graph* g, csaw_graph_info* out);
 
+/* Build the cached cumulative bias array of a static bias kind
+ * (CSAW_BIAS_EDGE_WEIGHT or CSAW_BIAS_NEIGHBOR_DEGREE): per edge e of row v,
+ * the inclusive uint64 prefix sum of the row's biases up to e -- the CTPS of
+ * Sec. II-B computed once instead of at every selection (8 bytes per edge).
+ * Afterwards csaw_walk, csaw_sample and plans created later use it for that
+ * kind: a walk step or a draw is a binary search (O(log d)) instead of a pass
+ * over the row.  Picks are identical (same prefix sums, same draws).  Graphs
+ * where some bias of the kind is zero keep the streaming path.  Waits on
+ * `stream`.  Errors: CSAW_ERR_INVALID (dynamic or unweighted kind),
+ * CSAW_ERR_NOMEM, CSAW_ERR_CUDA. */
+csaw_status csaw_graph_build_cdf(csaw_graph* g, int32_t bias_kind, void* stream);
+
+/* Release a cached array.  Plans created while it existed must be destroyed
+ * first; no call may be running on the graph. */
+csaw_status csaw_graph_drop_cdf(csaw_graph* g, int32_t bias_kind);
+
 /* ---------------------------------------------------------------- walks */
 
 /* Biased random walks (Sec. II-A; static bias: edge weight or neighbour

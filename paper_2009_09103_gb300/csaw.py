@@ -102,6 +102,8 @@ def lib():
         L.csaw_graph_destroy.argtypes = [P]
         L.csaw_graph_get_info.argtypes = [P, ctypes.POINTER(GraphInfo)]
         L.csaw_walk.argtypes = [P, P, u64, u32, ctypes.POINTER(Bias), u64, P, i32, P]
+        L.csaw_graph_build_cdf.argtypes = [P, ctypes.c_int32, P]
+        L.csaw_graph_drop_cdf.argtypes = [P, ctypes.c_int32]
         if hasattr(L, "csaw_sample"):
             L.csaw_sample.argtypes = [P, P, P, u32, u32, P, ctypes.POINTER(Bias), u64, i32, P,
                                       ctypes.POINTER(P)]
@@ -127,6 +129,7 @@ def lib():
         L.csaw_cancel.argtypes = [P, u64]
         L.csaw_server_stats.argtypes = [P, ctypes.POINTER(ServerStats)]
         for name in ("csaw_graph_create", "csaw_graph_destroy", "csaw_graph_get_info", "csaw_walk",
+                     "csaw_graph_build_cdf", "csaw_graph_drop_cdf",
                      "csaw_sample", "csaw_sample_get_view", "csaw_sample_copy_edges",
                      "csaw_sample_plan_create", "csaw_sample_plan_run", "csaw_sample_plan_get_view",
                      "csaw_sample_plan_copy_edges", "csaw_sample_plan_get_info", "csaw_sample_plan_destroy",
@@ -204,6 +207,14 @@ class Graph:
         gi = GraphInfo()
         _check(lib().csaw_graph_get_info(self._h, ctypes.byref(gi)))
         return gi
+
+    def build_cdf(self, bias: str, stream=None):
+        """csaw_graph_build_cdf: cache the static bias's cumulative array."""
+        st = _stream_handle(stream) if stream is not None else None
+        _check(lib().csaw_graph_build_cdf(self._h, BIAS_KINDS[bias], st))
+
+    def drop_cdf(self, bias: str):
+        _check(lib().csaw_graph_drop_cdf(self._h, BIAS_KINDS[bias]))
 
     def close(self):
         if self._h:

@@ -165,6 +165,7 @@ extern "C" csaw_status csaw_graph_destroy(csaw_graph* g)
 {
     clear_error();
     if (!g) return CSAW_OK;
+    for (int k = 0; k < 4; ++k) cudaFree(g->cdf[k]);
     cudaFree(g->off);
     cudaFree(g->col);
     cudaFree(g->w);
@@ -292,5 +293,128 @@ extern "C" csaw_status csaw_graph_get_info(const csaw_graph* g, csaw_graph_info*
     out->max_degree = g->max_degree;
     out->max_weight = g->max_weight;
     out->device_bytes = g->device_bytes;
+    return CSAW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Cached cumulative bias arrays (the CTPS of Sec. II-B kept per edge for a
+// static bias).  One warp per row in rounds of 512 neighbours: each lane takes
+// four aligned groups of four, forms their inclusive sums, and a warp scan of
+// the lane totals gives every lane its offset; groups are written as two
+// 16-byte stores (partial groups at the row ends element by element).
+
+namespace csaw {
+
+bool cached_cdf_usable(const csaw_graph* g, int kind)
+{
+    if (kind == CSAW_BIAS_UNIFORM) return true;
+    if (kind == CSAW_BIAS_EDGE_WEIGHT) return g->cdf[kind] != nullptr && g->min_weight > 0;
+    if (kind == CSAW_BIAS_NEIGHBOR_DEGREE) return g->cdf[kind] != nullptr && !g->zero_degree_target;
+    return false;
+}
+
+template <int KIND>
+__global__ void build_cdf_kernel(const uint64_t* __restrict__ off, const uint32_t* __restrict__ col,
+                                 const uint32_t* __restrict__ w, const uint32_t* __restrict__ deg,
+                                 uint32_t V, uint64_t* __restrict__ cdf, unsigned long long* next_row)
+{
+    const int lane = threadIdx.x & 31;
+    while (true) {
+        unsigned long long v = 0;
+        if (lane == 0) v = atomicAdd(next_row, 1ull);
+        v = __shfl_sync(CSAW_FULL_MASK, v, 0);
+        if (v >= V) break;
+        const uint64_t beg = off[v], end = off[v + 1];
+        if (beg == end) continue;
+        const uint64_t abeg = beg & ~3ull;
+        uint64_t carry = 0;
+        for (uint64_t base = abeg; base < end; base += 512) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint64_t g0 = base + 128ull * u + 4ull * lane;
+                uint32_t b[4] = {0u, 0u, 0u, 0u};
+                if (g0 < end) {
+                    if constexpr (KIND == CSAW_BIAS_EDGE_WEIGHT) {
+                        const uint4 q = __ldg(reinterpret_cast<const uint4*>(w + g0));
+                        b[0] = q.x; b[1] = q.y; b[2] = q.z; b[3] = q.w;
+                    } else {
+                        const uint4 q = __ldg(reinterpret_cast<const uint4*>(col + g0));
+                        b[0] = __ldg(deg + q.x);
+                        b[1] = q.y < V ? __ldg(deg + q.y) : 0u;
+                        b[2] = q.z < V ? __ldg(deg + q.z) : 0u;
+                        b[3] = q.w < V ? __ldg(deg + q.w) : 0u;
+                    }
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (g0 + j < beg || g0 + j >= end) b[j] = 0u;
+                }
+                const uint64_t i0 = b[0], i1 = i0 + b[1], i2 = i1 + b[2], i3 = i2 + b[3];
+                const uint64_t incl = warp_inclusive_scan_u64(i3, lane);
+                const uint64_t off0 = carry + incl - i3;
+                if (g0 < end) {
+                    const uint64_t e[4] = {off0 + i0, off0 + i1, off0 + i2, off0 + i3};
+                    if (g0 >= beg && g0 + 4 <= end) {
+                        ulonglong2* dst = reinterpret_cast<ulonglong2*>(cdf + g0);
+                        dst[0] = make_ulonglong2(e[0], e[1]);
+                        dst[1] = make_ulonglong2(e[2], e[3]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            if (g0 + j >= beg && g0 + j < end) cdf[g0 + j] = e[j];
+                    }
+                }
+                carry += __shfl_sync(CSAW_FULL_MASK, incl, 31);
+            }
+        }
+    }
+}
+
+}  // namespace csaw
+
+extern "C" csaw_status csaw_graph_build_cdf(csaw_graph* g, int32_t bias_kind, void* stream)
+{
+    clear_error();
+    if (!g) return fail(CSAW_ERR_INVALID, "graph is NULL");
+    if (bias_kind != CSAW_BIAS_EDGE_WEIGHT && bias_kind != CSAW_BIAS_NEIGHBOR_DEGREE)
+        return fail(CSAW_ERR_INVALID, "only edge-weight and neighbour-degree biases are static");
+    if (bias_kind == CSAW_BIAS_EDGE_WEIGHT && !g->w)
+        return fail(CSAW_ERR_INVALID, "the graph has no weights (edge-weight bias is uniform)");
+    if (g->cdf[bias_kind]) return CSAW_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint64_t* cdf = nullptr;
+    // padded like col/w so that 16-byte stores of a row's last group stay inside
+    CSAW_CUDA(cudaMalloc(&cdf, sizeof(uint64_t) * (g->E + CSAW_EDGE_PAD)));
+    unsigned long long* ctr = nullptr;
+    cudaError_t e = cudaMalloc(&ctr, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) {
+        const unsigned blocks = (unsigned)g->sm_count * 8;
+        if (bias_kind == CSAW_BIAS_EDGE_WEIGHT)
+            build_cdf_kernel<CSAW_BIAS_EDGE_WEIGHT><<<blocks, 256, 0, s>>>(g->off, g->col, g->w, g->deg, g->V, cdf, ctr);
+        else
+            build_cdf_kernel<CSAW_BIAS_NEIGHBOR_DEGREE><<<blocks, 256, 0, s>>>(g->off, g->col, g->w, g->deg, g->V, cdf, ctr);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(ctr);
+    if (e != cudaSuccess) {
+        cudaFree(cdf);
+        return cuda_fail(e, "build cumulative array");
+    }
+    g->cdf[bias_kind] = cdf;
+    g->device_bytes += sizeof(uint64_t) * (g->E + CSAW_EDGE_PAD);
+    return CSAW_OK;
+}
+
+extern "C" csaw_status csaw_graph_drop_cdf(csaw_graph* g, int32_t bias_kind)
+{
+    clear_error();
+    if (!g) return fail(CSAW_ERR_INVALID, "graph is NULL");
+    if (bias_kind < 0 || bias_kind > 3) return fail(CSAW_ERR_INVALID, "bad bias kind");
+    if (g->cdf[bias_kind]) {
+        cudaFree(g->cdf[bias_kind]);
+        g->cdf[bias_kind] = nullptr;
+        g->device_bytes -= sizeof(uint64_t) * (g->E + CSAW_EDGE_PAD);
+    }
     return CSAW_OK;
 }

@@ -30,6 +30,9 @@ struct csaw_graph {
     uint64_t device_bytes = 0;
     int device = 0;
     int sm_count = 0;
+    // cached per-edge inclusive prefix sums of a static bias kind (or null):
+    // cdf[kind][e] = b(row start) + ... + b(e) within e's row
+    uint64_t* cdf[4] = {nullptr, nullptr, nullptr, nullptr};
     // selection launch shape per bias kind (0 = default): warp-item degree
     // threshold and resident blocks per SM
     uint32_t tune_theta_w[4] = {0, 0, 0, 0};
@@ -74,6 +77,16 @@ csaw_status scan_u32(const uint32_t* in, uint64_t* out, const uint64_t* n_dev, u
 size_t sort_scratch_bytes(uint64_t n_max);
 csaw_status radix_sort_u64(uint64_t* keys, uint64_t* alt, const uint64_t* n_dev, uint64_t n_max,
                            int bits, int sm_count, void* scratch, cudaStream_t s, uint64_t** result);
+
+// Walks that read a cached cumulative array (or, for uniform bias, none):
+// one thread per walker.  Defined in csaw_walk.cu.
+csaw_status launch_walk_cached(const csaw_graph* g, int kind, const uint32_t* starts, uint64_t n,
+                               uint32_t length, uint64_t rng_seed, uint32_t* path, cudaStream_t s);
+
+// Whether selection/walks of this kind can use a cached cumulative array:
+// uniform always (implicit), edge weight / neighbour degree when built and
+// no bias of the kind is zero.
+bool cached_cdf_usable(const csaw_graph* g, int kind);
 
 // Releases a result made by the request server (tagged "CSRV").
 void free_server_result(void* result);

@@ -44,6 +44,7 @@ constexpr uint32_t WARP_MAX_DEG = 256;     // warp items: degree <= this
 constexpr uint32_t CTA_SMEM_DEG = 8192;    // CTA items keep S in shared memory up to this
 constexpr uint32_t WARP_SLOT = WARP_MAX_DEG * 8 + (WARP_MAX_DEG / 32) * 4;   // bytes per warp
 constexpr size_t SEL_DYN_SMEM = (size_t)CTA_SMEM_DEG * 8 + (CTA_SMEM_DEG / 32) * 4;
+constexpr uint32_t PICK_MAX = 256;         // picks a cached-array warp item may hold
 
 static_assert(SEL_WARPS * WARP_SLOT <= SEL_DYN_SMEM, "warp slots reuse the CTA region");
 
@@ -71,6 +72,8 @@ struct SelParams {
     uint64_t* __restrict__ scratch_S;     // per-CTA slots for CTA items above CTA_SMEM_DEG
     uint32_t* __restrict__ scratch_bits;
     uint64_t scratch_stride;              // entries per slot (max degree)
+    const uint64_t* __restrict__ cdf;     // cached cumulative array (select_cdf_kernel)
+    bool skip_warp_items;                 // warp items are served by select_cdf_kernel
 };
 
 template <int KIND>
@@ -324,13 +327,129 @@ __global__ void __launch_bounds__(SEL_THREADS) select_kernel(SelParams p)
     // Warp items: each warp uses its own slice of the dynamic region.
     uint64_t* sS = (uint64_t*)(s_dyn + (size_t)wid * WARP_SLOT);
     uint32_t* sBits = (uint32_t*)(s_dyn + (size_t)wid * WARP_SLOT + WARP_MAX_DEG * 8);
-    const unsigned long long n_warp = p.n_items[0];
+    const unsigned long long n_warp = p.skip_warp_items ? 0ull : p.n_items[0];
     while (true) {
         unsigned long long it = 0;
         if (lane == 0) it = atomicAdd(p.next, 1ull);
         it = __shfl_sync(CSAW_FULL_MASK, it, 0);
         if (it >= n_warp) break;
         warp_item<KIND>(p, p.warp_list[it], sS, sBits, lane);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Selection over a cached cumulative array (static biases): one warp per
+// frontier vertex of any degree.  T is the row's last prefix sum; each of the
+// 32 attempts of a round binary-searches the row's prefix sums in global
+// memory (uniform bias: the pick is x itself), so a hub costs O(log d) per
+// attempt instead of a pass over its row.  Picks so far are kept in a
+// per-warp list in shared memory (at most PICK_MAX); collision resolution and
+// the updated-sampling fallback are those of draw_picks.
+
+__device__ __forceinline__ uint64_t cdf_at(const uint64_t* __restrict__ row, bool implicit, uint32_t i)
+{
+    return implicit ? (uint64_t)i + 1 : __ldg(row + i);
+}
+
+template <bool IMPLICIT>
+__global__ void __launch_bounds__(SEL_THREADS) select_cdf_kernel(SelParams p)
+{
+    __shared__ uint32_t s_picks[SEL_WARPS][PICK_MAX];
+    if (p.key_dev) {
+        p.k0 = p.key_dev[0];
+        p.k1 = p.key_dev[1];
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t* picks = s_picks[wid];
+    const uint32_t lt = lanemask_lt();
+    const unsigned long long n_warp = p.n_items[0];
+    while (true) {
+        unsigned long long it = 0;
+        if (lane == 0) it = atomicAdd(p.next, 1ull);
+        it = __shfl_sync(CSAW_FULL_MASK, it, 0);
+        if (it >= n_warp) break;
+        const uint32_t e = p.warp_list[it];
+        const uint64_t key = p.fkeys[e];
+        const uint32_t v = (uint32_t)(key & p.vmask);
+        const uint32_t inst = (uint32_t)(key >> p.vbits);
+        const uint64_t beg = __ldg(p.off + v);
+        const uint32_t d = (uint32_t)(__ldg(p.off + v + 1) - beg);
+        const uint64_t q0 = p.pos[e];
+        const uint32_t cnt = (uint32_t)(p.pos[e + 1] - q0);
+        if (cnt >= d) {
+            // every neighbour (all biases are positive here), CSR order
+            for (uint32_t j = lane; j < d; j += 32) emit(p, q0 + j, v, inst, __ldg(p.col + beg + j));
+            continue;
+        }
+        const uint64_t* row = p.cdf ? p.cdf + beg : nullptr;
+        const uint64_t T = cdf_at(row, IMPLICIT, d - 1);
+        uint32_t have = 0, a0 = 0;
+        while (have < cnt && a0 < CSAW_ATTEMPT_CAP) {
+            const uint64_t x = scale_draw(philox_draw(p.k0, p.k1, a0 + lane, v, p.layer, inst), T);
+            uint32_t i;
+            if (IMPLICIT) {
+                i = (uint32_t)x;
+            } else {
+                uint32_t lo = 0, hi = d - 1;
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (__ldg(row + mid) > x) hi = mid; else lo = mid + 1;
+                }
+                i = lo;
+            }
+            bool chosen = false;
+            for (uint32_t j = 0; j < have; ++j) chosen |= picks[j] == i;
+            const uint32_t peers = __match_any_sync(CSAW_FULL_MASK, i);
+            const bool fresh = !chosen && lane == __ffs(peers) - 1;
+            const uint32_t bal = __ballot_sync(CSAW_FULL_MASK, fresh);
+            const uint32_t rank = __popc(bal & lt);
+            const uint32_t need = cnt - have;
+            if (fresh && rank < need) {
+                picks[have + rank] = i;
+                emit(p, q0 + have + rank, v, inst, __ldg(p.col + beg + i));
+            }
+            have += min((uint32_t)__popc(bal), need);
+            a0 += 32;
+            __syncwarp();
+        }
+        if (have < cnt && lane == 0) {
+            // Updated sampling (attempts CSAW_ATTEMPT_CAP, ...): picks sorted
+            // ascending, the draw scaled to the unpicked total and moved past
+            // every picked interval that starts at or below it.
+            for (uint32_t a = 1; a < have; ++a) {
+                const uint32_t t = picks[a];
+                uint32_t b = a;
+                while (b > 0 && picks[b - 1] > t) { picks[b] = picks[b - 1]; --b; }
+                picks[b] = t;
+            }
+            uint64_t R = 0;
+            for (uint32_t j = 0; j < have; ++j) {
+                const uint32_t q = picks[j];
+                R += cdf_at(row, IMPLICIT, q) - (q ? cdf_at(row, IMPLICIT, q - 1) : 0);
+            }
+            for (uint32_t a = CSAW_ATTEMPT_CAP; have < cnt; ++a) {
+                uint64_t x = scale_draw(philox_draw(p.k0, p.k1, a, v, p.layer, inst), T - R);
+                for (uint32_t j = 0; j < have; ++j) {
+                    const uint32_t q = picks[j];
+                    const uint64_t start = q ? cdf_at(row, IMPLICIT, q - 1) : 0;
+                    if (x >= start) x += cdf_at(row, IMPLICIT, q) - start;
+                    else break;
+                }
+                uint32_t lo = 0, hi = d - 1;
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (cdf_at(row, IMPLICIT, mid) > x) hi = mid; else lo = mid + 1;
+                }
+                const uint32_t i = lo;
+                uint32_t b = have;
+                while (b > 0 && picks[b - 1] > i) { picks[b] = picks[b - 1]; --b; }
+                picks[b] = i;
+                R += cdf_at(row, IMPLICIT, i) - (i ? cdf_at(row, IMPLICIT, i - 1) : 0);
+                emit(p, q0 + have, v, inst, __ldg(p.col + beg + i));
+                ++have;
+            }
+        }
+        __syncwarp();
     }
 }
 
@@ -347,6 +466,7 @@ struct CountParams {
     uint64_t vmask;
     uint32_t k;
     uint32_t theta_w;              // warp items: degree <= theta_w (<= WARP_MAX_DEG), or take-all
+    bool cached;                   // cached cumulative array: warp items up to PICK_MAX picks
     bool zero_bias;
     uint32_t* __restrict__ cnt;
     uint32_t* __restrict__ warp_list;
@@ -398,7 +518,7 @@ __global__ void count_kernel(CountParams p)
         }
         const uint32_t c = min(p.k, npos);
         const bool take_all = npos <= p.k;
-        const bool to_warp = e < n && c > 0 && (take_all || d <= p.theta_w);
+        const bool to_warp = e < n && c > 0 && (take_all || (p.cached ? c <= PICK_MAX : d <= p.theta_w));
         const bool to_cta = e < n && c > 0 && !to_warp;
         if (e < n) p.cnt[e] = c;
         // warp-aggregated appends
@@ -698,6 +818,7 @@ struct Pipeline {
     uint64_t vmask = 1;
     int sel_blocks = 1;
     uint32_t theta_w = WARP_MAX_DEG;
+    bool cached = false;                 // selection over a cached cumulative array
     uint32_t k0 = 0, k1 = 0;
     const uint32_t* key_dev = nullptr;   // plan mode: Philox key in device memory
     uint64_t* ctr = nullptr;             // [CT_WORDS]
@@ -730,6 +851,7 @@ struct Pipeline {
         zero_bias = (kind == CSAW_BIAS_EDGE_WEIGHT && g->min_weight == 0) ||
                     (kind == CSAW_BIAS_NEIGHBOR_DEGREE && g->zero_degree_target);
         select_shape(g, kind, &theta_w, &sel_blocks);
+        cached = cached_cdf_usable(g, kind);
         k0 = (uint32_t)seed;
         k1 = (uint32_t)(seed >> 32);
     }
@@ -771,7 +893,7 @@ static csaw_status enqueue_count(Pipeline& P, uint32_t l, cudaStream_t s)
     CountParams cp;
     cp.off = g->off; cp.col = g->col; cp.w = g->w; cp.deg = g->deg;
     cp.fkeys = B.F; cp.n_dev = (const unsigned long long*)P.lc(l, L_N); cp.vmask = P.vmask;
-    cp.k = P.fanout[l]; cp.theta_w = P.theta_w; cp.zero_bias = P.zero_bias;
+    cp.k = P.fanout[l]; cp.theta_w = P.theta_w; cp.cached = P.cached; cp.zero_bias = P.zero_bias;
     cp.cnt = B.cnt; cp.warp_list = B.wlist; cp.cta_list = B.clist;
     cp.n_items = (unsigned long long*)P.lc(l, L_ITEMS);
     if (B.f_cap) {
@@ -799,6 +921,16 @@ static csaw_status enqueue_select(Pipeline& P, uint32_t l, cudaStream_t s)
         sp.next = (unsigned long long*)P.lc(l, L_NEXT);
         sp.out_src = B.src; sp.out_dst = B.dst; sp.out_cand = (l + 1 < P.depth) ? B.cand : nullptr;
         sp.scratch_S = P.hub_S; sp.scratch_bits = P.hub_bits; sp.scratch_stride = g->max_degree;
+        sp.cdf = P.cached && P.kind != CSAW_BIAS_UNIFORM ? g->cdf[P.kind] : nullptr;
+        sp.skip_warp_items = P.cached;
+        if (P.cached) {
+            // warp items over the cached array; CTA items (more than PICK_MAX
+            // picks) by the streaming kernel below
+            const int blocks = g->sm_count * 8;
+            if (P.kind == CSAW_BIAS_UNIFORM) select_cdf_kernel<true><<<blocks, SEL_THREADS, 0, s>>>(sp);
+            else select_cdf_kernel<false><<<blocks, SEL_THREADS, 0, s>>>(sp);
+            CSAW_CUDA(cudaGetLastError());
+        }
         switch (P.kind) {
         case CSAW_BIAS_UNIFORM: CSAW_TRY(launch_select<CSAW_BIAS_UNIFORM>(sp, P.sel_blocks, s)); break;
         case CSAW_BIAS_EDGE_WEIGHT: CSAW_TRY(launch_select<CSAW_BIAS_EDGE_WEIGHT>(sp, P.sel_blocks, s)); break;
@@ -1513,7 +1645,7 @@ extern "C" csaw_status csaw_select_noalloc(csaw_graph* g, const uint32_t* vertic
     cp.off = g->off; cp.col = g->col; cp.w = g->w; cp.deg = g->deg;
     cp.fkeys = keys; cp.n_dev = (const unsigned long long*)d_n; cp.vmask = vmask; cp.k = k;
     cp.zero_bias = zero_bias; cp.cnt = cnt; cp.warp_list = wlist; cp.cta_list = clist;
-    cp.n_items = d_items; cp.theta_w = WARP_MAX_DEG;
+    cp.n_items = d_items; cp.theta_w = WARP_MAX_DEG; cp.cached = false;
     if (n) {
         switch (kind) {
         case CSAW_BIAS_UNIFORM: CSAW_TRY(launch_count<CSAW_BIAS_UNIFORM>(cp, n, g->sm_count, s)); break;
@@ -1533,6 +1665,7 @@ extern "C" csaw_status csaw_select_noalloc(csaw_graph* g, const uint32_t* vertic
         sp.scratch_S = (uint64_t*)hub;
         sp.scratch_bits = (uint32_t*)(hub + (size_t)sel_blocks * g->max_degree * 8);
         sp.scratch_stride = g->max_degree;
+        sp.cdf = nullptr; sp.skip_warp_items = false;
         switch (kind) {
         case CSAW_BIAS_UNIFORM: CSAW_TRY(launch_select<CSAW_BIAS_UNIFORM>(sp, sel_blocks, s)); break;
         case CSAW_BIAS_EDGE_WEIGHT: CSAW_TRY(launch_select<CSAW_BIAS_EDGE_WEIGHT>(sp, sel_blocks, s)); break;

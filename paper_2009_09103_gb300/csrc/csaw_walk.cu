@@ -460,6 +460,92 @@ static csaw_status launch_walk(int kind, uint64_t max_bias, const WalkParams& p,
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Walks over a cached cumulative array (static biases): one thread per
+// walker.  A step loads the row's total T = cdf[end-1], maps the draw to x
+// and binary-searches the row's prefix sums (uniform bias: the pick is x),
+// so its cost is O(log d) dependent loads instead of a stream over the row;
+// 32 walkers per warp keep many searches in flight.  The picks are those of
+// the streaming kernel: the same prefix sums and the same draws.
+struct WalkCdfParams {
+    const uint64_t* __restrict__ off;
+    const uint32_t* __restrict__ col;
+    const uint64_t* __restrict__ cdf;   // null for uniform bias
+    uint32_t V;
+    const uint32_t* __restrict__ starts;
+    uint64_t n;
+    uint32_t L;
+    uint32_t* __restrict__ path;
+    uint32_t k0, k1;
+};
+
+template <bool UNIFORM>
+__global__ void __launch_bounds__(256) walk_cached_kernel(WalkCdfParams p)
+{
+    const uint64_t row_len = (uint64_t)p.L + 1;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t wk = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; wk < p.n; wk += stride) {
+        uint32_t* out = p.path + wk * row_len;
+        uint32_t cur = __ldg(p.starts + wk);
+        if (cur >= p.V) {
+            for (uint64_t t = 0; t < row_len; ++t) out[t] = CSAW_NONE;
+            continue;
+        }
+        out[0] = cur;
+        uint32_t s = 0;
+        for (; s < p.L; ++s) {
+            const uint64_t beg = __ldg(p.off + cur);
+            const uint64_t end = __ldg(p.off + cur + 1);
+            if (beg == end) break;
+            const uint64_t r = philox_draw(p.k0, p.k1, 0u, cur, s, (uint32_t)wk);
+            uint64_t i;
+            if constexpr (UNIFORM) {
+                i = scale_draw(r, end - beg);
+            } else {
+                const uint64_t T = __ldg(p.cdf + end - 1);
+                if (T == 0) break;
+                const uint64_t x = scale_draw(r, T);
+                // smallest e in [beg, end) with cdf[e] > x
+                uint64_t lo = beg, hi = end - 1;
+                while (lo < hi) {
+                    const uint64_t mid = lo + ((hi - lo) >> 1);
+                    if (__ldg(p.cdf + mid) > x) hi = mid; else lo = mid + 1;
+                }
+                i = lo - beg;
+            }
+            cur = __ldg(p.col + beg + i);
+            out[s + 1] = cur;
+        }
+        for (uint64_t t = (uint64_t)s + 1; t < row_len; ++t) out[t] = CSAW_NONE;
+    }
+}
+
+csaw_status launch_walk_cached(const csaw_graph* g, int kind, const uint32_t* starts, uint64_t n,
+                               uint32_t length, uint64_t rng_seed, uint32_t* path, cudaStream_t s)
+{
+    WalkCdfParams p;
+    p.off = g->off; p.col = g->col; p.cdf = kind == CSAW_BIAS_UNIFORM ? nullptr : g->cdf[kind];
+    p.V = g->V; p.starts = starts; p.n = n; p.L = length; p.path = path;
+    p.k0 = (uint32_t)rng_seed; p.k1 = (uint32_t)(rng_seed >> 32);
+    static int per_sm[2] = {0, 0};
+    const int u = kind == CSAW_BIAS_UNIFORM ? 1 : 0;
+    if (per_sm[u] == 0) {
+        cudaError_t e = u ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[u], walk_cached_kernel<true>, 256, 0)
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[u], walk_cached_kernel<false>, 256, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "occupancy(walk_cached)");
+        if (per_sm[u] < 1) per_sm[u] = 1;
+    }
+    uint64_t blocks = (n + 255) / 256;
+    const uint64_t cap = (uint64_t)g->sm_count * per_sm[u];
+    if (blocks > cap) blocks = cap;
+    if (u) walk_cached_kernel<true><<<(unsigned)blocks, 256, 0, s>>>(p);
+    else walk_cached_kernel<false><<<(unsigned)blocks, 256, 0, s>>>(p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "walk_cached_kernel launch");
+    return CSAW_OK;
+}
+
 }  // namespace csaw
 
 using namespace csaw;
@@ -499,6 +585,20 @@ extern "C" csaw_status csaw_walk(csaw_graph* g, const uint32_t* starts, uint64_t
         cudaError_t e = cudaMemcpyAsync(a, starts, sizeof(uint32_t) * n_walkers,
                                         cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) { dfree(a, s); dfree(b, s); return cuda_fail(e, "copy starts"); }
+    }
+    if (kind != CSAW_BIAS_NODE2VEC && cached_cdf_usable(g, kind)) {
+        // static bias with a cached cumulative array (or uniform): thread per walker
+        csaw_status st = launch_walk_cached(g, kind, d_starts, n_walkers, length, rng_seed, d_path, s);
+        if (mem_kind == CSAW_MEM_HOST) {
+            if (st == CSAW_OK) {
+                cudaError_t e = cudaMemcpyAsync(path, d_path, path_bytes, cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                if (e != cudaSuccess) st = cuda_fail(e, "copy path");
+            }
+            dfree((void*)d_starts, s);
+            dfree(d_path, s);
+        }
+        return st;
     }
     void* counter = nullptr;
     csaw_status st = dalloc(&counter, sizeof(unsigned long long), s);

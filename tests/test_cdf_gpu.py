@@ -1,0 +1,126 @@
+"""Cached cumulative bias arrays (static biases): walks and sampling read the
+per-edge prefix sums instead of streaming each row, with identical picks."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2009_09103_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+ALL = 0xFFFFFFFF
+
+
+@pytest.fixture(scope="module")
+def csaw():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2009_09103_gb300 import build
+    build.build()
+    from paper_2009_09103_gb300 import csaw as c
+    return c
+
+
+def star(d, seed, wmax=1000):
+    rng = np.random.default_rng(seed)
+    edges = [(0, j + 1) for j in range(d)] + [(j + 1, 0) for j in range(d)]
+    return inputs.csr_from_edges(d + 1, edges, list(rng.integers(1, wmax, size=d)) + [1] * d)
+
+
+@pytest.mark.parametrize("bias", ["edge_weight", "neighbor_degree"])
+def test_cached_walks_match_oracle(csaw, bias):
+    for g in (inputs.rmat_csr(12, 16, 100, 12), inputs.rmat_csr(8, 8, 40, 1), star(70001, 3)):
+        G = csaw.Graph(g.off, g.col, g.w)
+        G.build_cdf(bias)
+        starts = np.concatenate([np.arange(min(g.V, 5000), dtype=np.uint32),
+                                 inputs.uniform_vertices(300, g.V, 3)])
+        got = csaw.walk(G, starts, 20, bias, 77)
+        assert np.array_equal(got, oracle.walk(g, starts, 20, bias, 77))
+        G.close()
+
+
+def test_cached_walk_s20_subset(csaw):
+    import torch
+    wl = inputs.workload_walk_s20()
+    g = wl.graph
+    G = csaw.Graph(g.off, g.col, g.w)
+    s = torch.from_numpy(wl.starts.view(np.int32)).cuda()
+    streamed = csaw.walk(G, s, wl.length, wl.bias, wl.rng_seed)
+    G.build_cdf("edge_weight")
+    cached = csaw.walk(G, s, wl.length, wl.bias, wl.rng_seed)
+    torch.cuda.synchronize()
+    assert bool(torch.equal(streamed, cached))
+    pick = inputs.uniform_vertices(300, g.V, 12).astype(np.int64)
+    ref = oracle.walk(g, wl.starts[pick], wl.length, wl.bias, wl.rng_seed, walker_ids=pick.astype(np.uint64))
+    assert np.array_equal(cached[torch.from_numpy(pick).cuda()].cpu().numpy().view(np.uint32), ref)
+    G.close()
+
+
+@pytest.mark.parametrize("bias", ["edge_weight", "neighbor_degree"])
+@pytest.mark.parametrize("fanout", [[10, 5], [3, 3, 3], [ALL, 2], [40, 300]])
+def test_cached_sampling_matches_oracle(csaw, bias, fanout):
+    g = inputs.rmat_csr(12, 16, 100, 12)
+    G = csaw.Graph(g.off, g.col, g.w)
+    G.build_cdf(bias)
+    seeds = inputs.uniform_vertices(300, g.V, 1)
+    io = np.array([0, 1, 1, 50, 200, 300], dtype=np.uint64)
+    res = csaw.sample(G, seeds, io, fanout, bias, 7)
+    ref = oracle.sample(g, seeds, io, fanout, bias, 7)
+    assert np.array_equal(res.dst, ref["dst"]) and np.array_equal(res.src, ref["src"])
+    assert np.array_equal(res.edge_offsets, ref["edge_off"])
+    # a plan created with the cached array gives the same
+    plan = csaw.SamplePlan(G, 5, 300, fanout, bias)
+    plan.run(seeds, io, 7)
+    assert np.array_equal(plan.result().dst, ref["dst"])
+    plan.close()
+    G.close()
+
+
+def test_cached_sampling_hubs_and_fallback(csaw):
+    # hubs, k around PICK_MAX, and a heavy neighbour forcing updated sampling
+    for d, k, heavy in ((70000, 25, False), (9000, 300, False), (3000, 255, False), (40, 25, True),
+                        (9000, 30, True)):
+        g = star(d, d % 11)
+        if heavy:
+            w = g.w.copy()
+            w[d // 3] = 2**31          # row 0 holds the first d entries (CSR order)
+            g = inputs.CSRGraph(g.off, g.col, w)
+        G = csaw.Graph(g.off, g.col, g.w)
+        G.build_cdf("edge_weight")
+        seeds = np.zeros(6, dtype=np.uint32)
+        io = np.arange(7, dtype=np.uint64)
+        res = csaw.sample(G, seeds, io, [k], "edge_weight", 11)
+        ref = oracle.sample(g, seeds, io, [k], "edge_weight", 11)
+        assert np.array_equal(res.dst, ref["dst"]), (d, k, heavy)
+        G.close()
+
+
+def test_cached_array_not_used_with_zero_biases(csaw):
+    g0 = inputs.rmat_csr(10, 8, 5, 3)
+    w = g0.w.copy()
+    w[np.random.default_rng(4).random(len(w)) < 0.3] = 0
+    g = inputs.CSRGraph(g0.off, g0.col, w)
+    G = csaw.Graph(g.off, g.col, g.w)
+    G.build_cdf("edge_weight")
+    seeds = inputs.uniform_vertices(200, g.V, 9)
+    io = np.array([0, 100, 200], dtype=np.uint64)
+    res = csaw.sample(G, seeds, io, [3, 2], "edge_weight", 5)
+    ref = oracle.sample(g, seeds, io, [3, 2], "edge_weight", 5)
+    assert np.array_equal(res.dst, ref["dst"])
+    starts = np.arange(g.V, dtype=np.uint32)
+    assert np.array_equal(csaw.walk(G, starts, 10, "edge_weight", 2), oracle.walk(g, starts, 10, "edge_weight", 2))
+    G.drop_cdf("edge_weight")
+    G.close()
+
+
+def test_build_cdf_errors(csaw):
+    g = inputs.rmat_csr(8, 8, 40, 1)
+    G = csaw.Graph(g.off, g.col, None)
+    with pytest.raises(csaw.CsawError) as e:
+        G.build_cdf("edge_weight")
+    assert e.value.status == csaw.ERR_INVALID
+    with pytest.raises(csaw.CsawError) as e:
+        G.build_cdf("node2vec")
+    assert e.value.status == csaw.ERR_INVALID
+    G.build_cdf("neighbor_degree")
+    G.close()
