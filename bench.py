@@ -169,8 +169,9 @@ def run_walk_bench(args, rank, world):
     g = wl.graph
     log(f"[bench] {args.workload} graph: V={g.V} E={g.E} built in {time.time() - t0:.1f}s")
     G = csaw.Graph(g.off, g.col, g.w)
-    if args.cdf and wl.bias != "node2vec":
-        G.build_cdf(wl.bias)
+    if args.cdf:
+        # node2vec reads the edge weights' cumulative array (intersection path)
+        G.build_cdf("edge_weight" if wl.bias == "node2vec" else wl.bias)
     stream = torch.cuda.current_stream()
     starts = torch.from_numpy(wl.starts.view(np.int32)).to(dev)
     n = starts.numel()
@@ -267,6 +268,35 @@ def run_walk_bench(args, rank, world):
     }
     if clk:
         result["clocks"] = clk
+    if not args.cdf and wl.bias != "node2vec" and not args.no_variant:
+        # The same walks over the cached per-edge cumulative array (built once
+        # per graph): identical paths, a binary search per step instead of a
+        # pass over the row.  Reported beside the per-step path, timed the same way.
+        t_b = time.perf_counter()
+        G.build_cdf(wl.bias)
+        build_ms = (time.perf_counter() - t_b) * 1e3
+        path2 = torch.empty_like(path)
+        def step2():
+            csaw.walk(G, starts, wl.length, wl.bias, seed, wl.n2v_mult, path=path2, stream=stream)
+        for _ in range(args.warmup):
+            step2()
+        ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.fill_(i)
+            ev2[i][0].record(stream)
+            step2()
+            ev2[i][1].record(stream)
+        torch.cuda.synchronize()
+        ms2 = sum(a.elapsed_time(b) for a, b in ev2) / args.steps
+        same = bool(torch.equal(path, path2))
+        result["variant_cached_cumulative_array"] = {
+            "value": n_trans * world / (ms2 / 1e3), "unit": "edges/s", "ms_per_step": ms2,
+            "kernel": "walk_cached_kernel", "build_ms_once_per_graph": build_ms,
+            "extra_device_bytes": 8 * (g.E + 16), "identical_paths": same}
+        G.drop_cdf(wl.bias)
+        result["gpu_launches_variant"] = args.steps
     G.close()
     return result, (g, wl, n_trans)
 
@@ -483,6 +513,8 @@ def run_serve_bench(args):
     g = inputs.rmat_csr(scale, 16, 255, scale)
     log(f"[bench] serve: graph s{scale} V={g.V} E={g.E} built in {time.time() - t0:.1f}s")
     G = csaw.Graph(g.off, g.col, g.w)
+    if args.cdf:
+        G.build_cdf("edge_weight")
     del g.col
     reqs = serving_requests(g, args.requests, 5)
     # serial plain service times
@@ -563,7 +595,8 @@ def run_serve_bench(args):
         "config": {"workload": f"serving: RMAT scale {scale} edge factor 16 resident; {len(reqs)} requests, "
                                "50/50 layered sampling (seeds log-uniform [1,16384], depth 1-3, fanout from "
                                "{5,10,25}) and weighted walks (starts log-uniform [1,65536], length U[10,80]); "
-                               f"Poisson arrivals; 40 GiB admission budget; {args.slots} slots",
+                               f"Poisson arrivals; 40 GiB admission budget; {args.slots} slots; cumulative "
+                               f"array {'cached per edge' if args.cdf else 'computed per selection'}",
                    "sampled_edges": total_edges},
         "serial_plain": {"capacity_req_per_s": serial_capacity, "seps": serial_seps},
         "points": points,
@@ -583,6 +616,8 @@ def main():
     ap.add_argument("--workload", default="walk",
                     choices=["walk", "node2vec", "sample_s12", "batched_s24", "serve"])
     ap.add_argument("--autotune", action="store_true", help="sampling workloads: autotune first")
+    ap.add_argument("--no-variant", action="store_true",
+                    help="walks: skip the cached-array variant measured after the main line")
     ap.add_argument("--cdf", action="store_true",
                     help="build the cached per-edge cumulative array of the static bias first")
     ap.add_argument("--plain-instances", type=int, default=512,

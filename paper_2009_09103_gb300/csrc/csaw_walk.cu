@@ -40,6 +40,7 @@ struct WalkParams {
     uint32_t k0, k1;
     uint32_t m0, m1, m2;
     unsigned long long* next_walker;
+    const uint64_t* __restrict__ cdfw;   // cached edge-weight prefix sums (node2vec fast path) or null
 };
 
 struct PrevCtx {
@@ -226,6 +227,139 @@ struct Acc<true> {
     static __device__ __forceinline__ uint64_t scan(uint64_t x, int lane) { return warp_inclusive_scan_u64(x, lane); }
 };
 
+// ---------------------------------------------------------------------------
+// node2vec step from the intersection (when the weights' cumulative array is
+// cached, or all weights are one).  With W the row's weight prefix sums, J the
+// positions j of N(cur) whose id is in N(prev) (other than prev), and p the
+// position of prev in N(cur):
+//   S[i] = m2*W[i] + (m1-m2)*sum_{j in J, j<=i} w_j + (m0-m2)*w_p*[p <= i],
+// the same prefix sums the streaming pass forms (computed in wrapping 64-bit
+// arithmetic, exact because every true value fits).  J comes from binary
+// searches of the shorter list's ids in the longer list, so a hub row after a
+// low-degree previous vertex costs O(d_prev log d_cur) instead of O(d_cur);
+// the pick is a 32-way warp search over S.
+constexpr uint32_t JCAP = 256;
+
+__device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* __restrict__ a, uint32_t n, uint32_t u)
+{
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(a + mid) < u) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ uint32_t ceil_log2(uint32_t x)
+{
+    return x <= 1 ? 0u : 32u - __clz(x - 1);
+}
+
+// Whether the intersection path is expected to beat streaming the row.
+__device__ __forceinline__ bool n2v_fast_pays(uint32_t da, uint32_t db)
+{
+    const uint32_t mn = min(da, db), mx = max(da, db);
+    if (mn > JCAP) return false;
+    const uint32_t fast = ((mn + 31) / 32) * (ceil_log2(mx) + 2) + 2 * ceil_log2(da) + 24;
+    const uint32_t stream = 3 * ((da + TILE - 1) / TILE) + 6;
+    return fast < stream;
+}
+
+__device__ __forceinline__ bool n2v_fast_pick(const WalkParams& p, const Row& row, const PrevCtx& c,
+                                              uint64_t r, int lane, uint32_t* s_jpos, uint64_t* s_jw,
+                                              uint32_t* idx)
+{
+    const uint32_t da = row.d;
+    const uint32_t db = (uint32_t)(c.pend - c.pbeg);
+    const uint32_t* A = p.col + row.beg;
+    const uint32_t* B = p.col + c.pbeg;
+    const uint64_t* W = p.cdfw ? p.cdfw + row.beg : nullptr;
+    auto Wat = [&](uint32_t i) -> uint64_t { return W ? __ldg(W + i) : (uint64_t)i + 1; };
+    auto wof = [&](uint32_t i) -> uint64_t { return Wat(i) - (i ? Wat(i - 1) : 0); };
+    const uint32_t lt = lanemask_lt();
+    // J in ascending position order
+    uint32_t nj = 0;
+    if (db <= da) {
+        for (uint32_t t0 = 0; t0 < db; t0 += 32) {
+            const uint32_t j = t0 + lane;
+            int pos = -1;
+            if (j < db) {
+                const uint32_t u = __ldg(B + j);
+                if (u != c.prev) {
+                    const uint32_t k = lower_bound_u32(A, da, u);
+                    if (k < da && __ldg(A + k) == u) pos = (int)k;
+                }
+            }
+            const uint32_t bal = __ballot_sync(CSAW_FULL_MASK, pos >= 0);
+            if (pos >= 0) s_jpos[nj + __popc(bal & lt)] = (uint32_t)pos;
+            nj += __popc(bal);
+        }
+    } else {
+        for (uint32_t t0 = 0; t0 < da; t0 += 32) {
+            const uint32_t j = t0 + lane;
+            bool in = false;
+            if (j < da) {
+                const uint32_t u = __ldg(A + j);
+                if (u != c.prev) {
+                    const uint32_t k = lower_bound_u32(B, db, u);
+                    in = k < db && __ldg(B + k) == u;
+                }
+            }
+            const uint32_t bal = __ballot_sync(CSAW_FULL_MASK, in);
+            if (in) s_jpos[nj + __popc(bal & lt)] = j;
+            nj += __popc(bal);
+        }
+    }
+    __syncwarp();
+    // cumulative weights of the J entries
+    uint64_t sum_j = 0;
+    for (uint32_t t0 = 0; t0 < nj; t0 += 32) {
+        const uint32_t j = t0 + lane;
+        const uint64_t wj = j < nj ? wof(s_jpos[j]) : 0;
+        const uint64_t incl = warp_inclusive_scan_u64(wj, lane) + sum_j;
+        if (j < nj) s_jw[j] = incl;
+        sum_j = __shfl_sync(CSAW_FULL_MASK, incl, 31);
+    }
+    // position and weight of prev in N(cur)
+    uint32_t pp = 0;
+    if (lane == 0) pp = lower_bound_u32(A, da, c.prev);
+    pp = __shfl_sync(CSAW_FULL_MASK, pp, 0);
+    const bool has_p = pp < da && __ldg(A + pp) == c.prev;
+    const uint64_t wp = has_p ? wof(pp) : 0;
+    __syncwarp();
+    const uint64_t m2 = p.m2;
+    const uint64_t dm1 = (uint64_t)p.m1 - m2;   // wrapping differences
+    const uint64_t dm0 = (uint64_t)p.m0 - m2;
+    auto S = [&](uint32_t i) -> uint64_t {
+        // J entries at positions <= i
+        uint32_t lo = 0, hi = nj;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (s_jpos[mid] <= i) lo = mid + 1; else hi = mid;
+        }
+        const uint64_t ij = lo ? s_jw[lo - 1] : 0;
+        return m2 * Wat(i) + dm1 * ij + ((has_p && pp <= i) ? dm0 * wp : 0);
+    };
+    const uint64_t T = m2 * Wat(da - 1) + dm1 * sum_j + (has_p ? dm0 * wp : 0);
+    if (T == 0) return false;
+    const uint64_t x = scale_draw(r, T);
+    // smallest i with S(i) > x; S(da-1) = T > x
+    uint32_t lo = 0, hi = da - 1;
+    while (hi - lo >= 32) {
+        const uint32_t pk = lo + (uint32_t)(((uint64_t)(hi - lo) * (lane + 1)) / 32);
+        const uint32_t hit = __ballot_sync(CSAW_FULL_MASK, S(pk) > x);
+        const int k = __ffs(hit) - 1;   // lane 31's pivot is hi, so some lane hits
+        const uint32_t pk_hit = __shfl_sync(CSAW_FULL_MASK, pk, k);
+        const uint32_t pk_prev = __shfl_sync(CSAW_FULL_MASK, pk, k > 0 ? k - 1 : 0);
+        lo = k > 0 ? pk_prev + 1 : lo;
+        hi = pk_hit;
+    }
+    const uint32_t i = lo + lane;
+    const uint32_t hit = __ballot_sync(CSAW_FULL_MASK, i <= hi && S(i) > x);
+    *idx = lo + (__ffs(hit) - 1);
+    return true;
+}
+
 // Biases of round `rd` (tiles rd*U .. rd*U+U-1) into b[u][j].
 template <int KIND>
 __device__ __forceinline__ void load_round(const WalkParams& p, const Row& r, uint32_t rd,
@@ -281,12 +415,17 @@ __device__ __forceinline__ uint32_t locate_in_round(const Row& r, uint32_t rd, c
 // Returns false at a dead end (T == 0).
 template <int KIND, bool WIDE>
 __device__ __forceinline__ bool walk_pick(const WalkParams& p, const Row& row, const PrevCtx& c,
-                                          uint64_t r, uint64_t* s_chunk, uint32_t* s_seg, int lane,
-                                          uint32_t* idx)
+                                          uint64_t r, uint64_t* s_chunk, uint32_t* s_seg, uint32_t* s_jpos,
+                                          uint64_t* s_jw, int lane, uint32_t* idx)
 {
     using A = Acc<WIDE>;
     using T = typename A::T;
     if (row.d == 0) return false;
+    if constexpr (KIND == CSAW_BIAS_NODE2VEC) {
+        if (c.prev != CSAW_NONE && (p.cdfw != nullptr || p.w == nullptr) &&
+            n2v_fast_pays(row.d, (uint32_t)(c.pend - c.pbeg)))
+            return n2v_fast_pick(p, row, c, r, lane, s_jpos, s_jw, idx);
+    }
     if constexpr (KIND == CSAW_BIAS_UNIFORM) {
         *idx = (uint32_t)scale_draw(r, row.d);   // b = 1: S[i] = i + 1, the pick is x itself
         return true;
@@ -369,9 +508,13 @@ __global__ void __launch_bounds__(WALK_THREADS, (walk_min_blocks<KIND, WIDE>()))
 {
     __shared__ uint64_t s_chunk_all[WALK_WARPS][CHUNK_SLOTS];
     __shared__ uint32_t s_seg_all[KIND == CSAW_BIAS_NODE2VEC ? WALK_WARPS : 1][SEG_SMEM];
+    __shared__ uint32_t s_jpos_all[KIND == CSAW_BIAS_NODE2VEC ? WALK_WARPS : 1][KIND == CSAW_BIAS_NODE2VEC ? JCAP : 1];
+    __shared__ uint64_t s_jw_all[KIND == CSAW_BIAS_NODE2VEC ? WALK_WARPS : 1][KIND == CSAW_BIAS_NODE2VEC ? JCAP : 1];
     const int lane = threadIdx.x & 31;
     uint64_t* s_chunk = s_chunk_all[threadIdx.x >> 5];
     uint32_t* s_seg = s_seg_all[KIND == CSAW_BIAS_NODE2VEC ? (threadIdx.x >> 5) : 0];
+    uint32_t* s_jpos = s_jpos_all[KIND == CSAW_BIAS_NODE2VEC ? (threadIdx.x >> 5) : 0];
+    uint64_t* s_jw = s_jw_all[KIND == CSAW_BIAS_NODE2VEC ? (threadIdx.x >> 5) : 0];
     const uint64_t row_len = (uint64_t)p.L + 1;
 
     while (true) {
@@ -400,7 +543,7 @@ __global__ void __launch_bounds__(WALK_THREADS, (walk_min_blocks<KIND, WIDE>()))
             row.lo = (uint32_t)(row.beg - row.abeg);
             const uint64_t r = philox_draw(p.k0, p.k1, 0u, cur, s, (uint32_t)wk);
             uint32_t idx;
-            if (!walk_pick<KIND, WIDE>(p, row, c, r, s_chunk, s_seg, lane, &idx)) break;
+            if (!walk_pick<KIND, WIDE>(p, row, c, r, s_chunk, s_seg, s_jpos, s_jw, lane, &idx)) break;
             const uint32_t nxt = __ldg(p.col + row.beg + idx);
             if constexpr (KIND == CSAW_BIAS_NODE2VEC) {
                 c.prev = cur;
@@ -613,6 +756,7 @@ extern "C" csaw_status csaw_walk(csaw_graph* g, const uint32_t* starts, uint64_t
         p.k0 = (uint32_t)rng_seed; p.k1 = (uint32_t)(rng_seed >> 32);
         p.m0 = bias->n2v_mult[0]; p.m1 = bias->n2v_mult[1]; p.m2 = bias->n2v_mult[2];
         p.next_walker = (unsigned long long*)counter;
+        p.cdfw = g->cdf[CSAW_BIAS_EDGE_WEIGHT];
         uint64_t max_bias = 1;
         if (kind == CSAW_BIAS_EDGE_WEIGHT) max_bias = g->max_weight;
         else if (kind == CSAW_BIAS_NEIGHBOR_DEGREE) max_bias = g->max_degree;

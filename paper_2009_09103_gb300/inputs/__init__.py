@@ -45,11 +45,14 @@ def _load():
         u32, u64, i32, f64 = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_double
         lib.csaw_gen_rmat_draws.argtypes = [u32, u64, f64, f64, f64, u64, i32, P, P]
         lib.csaw_gen_build_csr.argtypes = [u32, u64, P, P, P, P, P]
+        lib.csaw_gen_build_csr_mt.argtypes = [u32, u64, P, P, i32, P, P, P]
+        lib.csaw_gen_weights_mt.argtypes = [u32, P, P, u32, u64, i32, P]
         lib.csaw_gen_weights.argtypes = [u32, P, P, u32, u64, P]
         lib.csaw_gen_uniform_vertices.argtypes = [u64, u32, u64, u64, P]
         lib.csaw_gen_loguniform_sizes.argtypes = [u32, f64, f64, u64, u64, P]
         lib.csaw_gen_distinct_seeds.argtypes = [u32, P, u32, u64, u64, P]
-        for f in ("csaw_gen_rmat_draws", "csaw_gen_build_csr", "csaw_gen_weights",
+        for f in ("csaw_gen_rmat_draws", "csaw_gen_build_csr", "csaw_gen_build_csr_mt",
+                  "csaw_gen_weights", "csaw_gen_weights_mt",
                   "csaw_gen_uniform_vertices", "csaw_gen_loguniform_sizes", "csaw_gen_distinct_seeds"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
@@ -94,13 +97,13 @@ def rmat_csr(scale: int, edge_factor: int, wmax: int, seed: int,
     off = np.empty(V + 1, dtype=np.uint64)
     col = np.empty(2 * m, dtype=np.uint32)
     ne = ctypes.c_uint64(0)
-    rc = lib.csaw_gen_build_csr(V, m, _p(src), _p(dst), _p(off), _p(col), ctypes.byref(ne))
+    rc = lib.csaw_gen_build_csr_mt(V, m, _p(src), _p(dst), threads, _p(off), _p(col), ctypes.byref(ne))
     if rc:
-        raise MemoryError(f"csaw_gen_build_csr failed ({rc})")
+        raise MemoryError(f"csaw_gen_build_csr_mt failed ({rc})")
     del src, dst
     col = col[: ne.value].copy()
     w = np.empty(ne.value, dtype=np.uint32)
-    rc = lib.csaw_gen_weights(V, _p(off), _p(col), wmax, seed, _p(w))
+    rc = lib.csaw_gen_weights_mt(V, _p(off), _p(col), wmax, seed, threads, _p(w))
     if rc:
         raise ValueError("csaw_gen_weights failed")
     return CSRGraph(off, col, w)

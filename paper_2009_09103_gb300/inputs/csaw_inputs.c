@@ -267,3 +267,187 @@ int csaw_gen_distinct_seeds(uint32_t n_inst, const uint64_t* sizes, uint32_t V, 
     free(set);
     return 0;
 }
+
+/* ---- Multi-threaded CSR build (same result as csaw_gen_build_csr) ----
+ * Degrees are counted with atomic increments, both directions of every edge
+ * are scattered into their rows through atomic cursors (so the order inside a
+ * row depends on thread timing), then every row is sorted and deduplicated on
+ * its own: the final CSR depends only on the edge multiset.               */
+typedef struct {
+    int n_threads, t;
+    uint64_t n_draws;
+    uint32_t V;
+    const uint32_t* src; const uint32_t* dst;
+    uint64_t* cnt;        /* degree, then cursor */
+    uint64_t* start;
+    uint32_t* tmp;
+    uint64_t* newlen;
+    uint64_t* off;
+    uint32_t* col;
+    uint64_t* next_row;   /* shared dynamic row counter */
+    int phase;
+} csr_job;
+
+static void sort_u32(uint32_t* a, uint64_t n, uint32_t* scratch)
+{
+    if (n < 64) {
+        for (uint64_t i = 1; i < n; ++i) {
+            uint32_t x = a[i];
+            uint64_t j = i;
+            while (j > 0 && a[j - 1] > x) { a[j] = a[j - 1]; --j; }
+            a[j] = x;
+        }
+        return;
+    }
+    uint32_t* in = a;
+    uint32_t* out = scratch;
+    for (int shift = 0; shift < 32; shift += 8) {
+        uint64_t c[257];
+        memset(c, 0, sizeof(c));
+        for (uint64_t i = 0; i < n; ++i) c[((in[i] >> shift) & 255u) + 1]++;
+        for (int b = 0; b < 256; ++b) c[b + 1] += c[b];
+        for (uint64_t i = 0; i < n; ++i) out[c[(in[i] >> shift) & 255u]++] = in[i];
+        uint32_t* t = in; in = out; out = t;
+    }
+    /* four passes: the sorted data is back in a */
+}
+
+static void* csr_worker(void* pv)
+{
+    csr_job* J = (csr_job*)pv;
+    const uint64_t n = J->n_draws;
+    const uint64_t lo = n * (uint64_t)J->t / (uint64_t)J->n_threads;
+    const uint64_t hi = n * (uint64_t)(J->t + 1) / (uint64_t)J->n_threads;
+    if (J->phase == 0) {
+        for (uint64_t e = lo; e < hi; ++e) {
+            uint32_t u = J->src[e], v = J->dst[e];
+            if (u == v) continue;
+            __atomic_fetch_add(&J->cnt[u], 1, __ATOMIC_RELAXED);
+            __atomic_fetch_add(&J->cnt[v], 1, __ATOMIC_RELAXED);
+        }
+    } else if (J->phase == 1) {
+        for (uint64_t e = lo; e < hi; ++e) {
+            uint32_t u = J->src[e], v = J->dst[e];
+            if (u == v) continue;
+            uint64_t p = __atomic_fetch_add(&J->cnt[u], 1, __ATOMIC_RELAXED);
+            J->tmp[p] = v;
+            p = __atomic_fetch_add(&J->cnt[v], 1, __ATOMIC_RELAXED);
+            J->tmp[p] = u;
+        }
+    } else {
+        uint32_t* scratch = NULL;
+        uint64_t scap = 0;
+        for (;;) {
+            uint64_t r0 = __atomic_fetch_add(J->next_row, 4096, __ATOMIC_RELAXED);
+            if (r0 >= J->V) break;
+            uint64_t r1 = r0 + 4096 > J->V ? J->V : r0 + 4096;
+            for (uint64_t v = r0; v < r1; ++v) {
+                uint32_t* row = J->tmp + J->start[v];
+                uint64_t d = J->start[v + 1] - J->start[v];
+                if (J->phase == 2) {
+                    if (d > scap) {
+                        free(scratch);
+                        scap = d * 2;
+                        scratch = (uint32_t*)malloc(sizeof(uint32_t) * scap);
+                        if (!scratch) { scap = 0; break; }
+                    }
+                    sort_u32(row, d, scratch);
+                    uint64_t m = 0;
+                    for (uint64_t i = 0; i < d; ++i) if (i == 0 || row[i] != row[i - 1]) row[m++] = row[i];
+                    J->newlen[v] = m;
+                } else {
+                    memcpy(J->col + J->off[v], row, sizeof(uint32_t) * J->newlen[v]);
+                }
+            }
+        }
+        free(scratch);
+    }
+    return NULL;
+}
+
+static void csr_run(csr_job* jobs, int T, int phase)
+{
+    pthread_t th[256];
+    for (int t = 0; t < T; ++t) jobs[t].phase = phase;
+    for (int t = 1; t < T; ++t) pthread_create(&th[t], NULL, csr_worker, &jobs[t]);
+    csr_worker(&jobs[0]);
+    for (int t = 1; t < T; ++t) pthread_join(th[t], NULL);
+}
+
+int csaw_gen_build_csr_mt(uint32_t V, uint64_t n_draws, const uint32_t* src, const uint32_t* dst,
+                          int n_threads, uint64_t* off, uint32_t* col, uint64_t* n_edges)
+{
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > 256) n_threads = 256;
+    uint64_t* cnt = (uint64_t*)calloc((uint64_t)V + 1, sizeof(uint64_t));
+    uint64_t* start = (uint64_t*)malloc(sizeof(uint64_t) * ((uint64_t)V + 1));
+    uint64_t* newlen = (uint64_t*)malloc(sizeof(uint64_t) * ((uint64_t)V + 1));
+    if (!cnt || !start || !newlen) { free(cnt); free(start); free(newlen); return 2; }
+    csr_job jobs[256];
+    uint64_t next_row = 0;
+    for (int t = 0; t < n_threads; ++t) {
+        csr_job j = { n_threads, t, n_draws, V, src, dst, cnt, start, NULL, newlen, off, col, &next_row, 0 };
+        jobs[t] = j;
+    }
+    csr_run(jobs, n_threads, 0);
+    uint64_t run = 0;
+    for (uint32_t v = 0; v < V; ++v) { start[v] = run; run += cnt[v]; cnt[v] = start[v]; }
+    start[V] = run;
+    uint32_t* tmp = (uint32_t*)malloc(sizeof(uint32_t) * (run ? run : 1));
+    if (!tmp) { free(cnt); free(start); free(newlen); return 2; }
+    for (int t = 0; t < n_threads; ++t) jobs[t].tmp = tmp;
+    csr_run(jobs, n_threads, 1);
+    next_row = 0;
+    csr_run(jobs, n_threads, 2);
+    uint64_t w = 0;
+    for (uint32_t v = 0; v < V; ++v) { off[v] = w; w += newlen[v]; }
+    off[V] = w;
+    next_row = 0;
+    csr_run(jobs, n_threads, 3);
+    *n_edges = w;
+    free(tmp); free(cnt); free(start); free(newlen);
+    return 0;
+}
+
+/* Weights of rows [r0, r1) (thread body of csaw_gen_weights_mt). */
+typedef struct { uint32_t r0, r1; const uint64_t* off; const uint32_t* col; uint32_t wmax; uint64_t seed; uint32_t* w; } wjob;
+
+static void* weights_worker(void* pv)
+{
+    wjob* J = (wjob*)pv;
+    for (uint32_t u = J->r0; u < J->r1; ++u) {
+        for (uint64_t p = J->off[u]; p < J->off[u + 1]; ++p) {
+            uint32_t v = J->col[p];
+            uint64_t lo = u < v ? u : v, hi = u < v ? v : u;
+            uint64_t h = mix64(stream_state(J->seed, 2, (lo << 32) | hi));
+            J->w[p] = 1u + (uint32_t)(h % J->wmax);
+        }
+    }
+    return NULL;
+}
+
+int csaw_gen_weights_mt(uint32_t V, const uint64_t* off, const uint32_t* col, uint32_t wmax,
+                        uint64_t seed, int n_threads, uint32_t* w)
+{
+    if (wmax == 0) return 1;
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > 256) n_threads = 256;
+    wjob jobs[256];
+    pthread_t th[256];
+    /* split by edges so that hub rows do not serialise one thread */
+    uint64_t E = off[V];
+    uint32_t r = 0;
+    for (int t = 0; t < n_threads; ++t) {
+        uint64_t target = E * (uint64_t)(t + 1) / (uint64_t)n_threads;
+        uint32_t r1 = r;
+        while (r1 < V && off[r1] < target) ++r1;
+        if (t == n_threads - 1) r1 = V;
+        wjob j = { r, r1, off, col, wmax, seed, w };
+        jobs[t] = j;
+        r = r1;
+    }
+    for (int t = 1; t < n_threads; ++t) pthread_create(&th[t], NULL, weights_worker, &jobs[t]);
+    weights_worker(&jobs[0]);
+    for (int t = 1; t < n_threads; ++t) pthread_join(th[t], NULL);
+    return 0;
+}

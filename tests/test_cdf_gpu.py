@@ -124,3 +124,63 @@ def test_build_cdf_errors(csaw):
     assert e.value.status == csaw.ERR_INVALID
     G.build_cdf("neighbor_degree")
     G.close()
+
+
+def hubby_graph(seed=5):
+    """Hubs joined to each other and to many low-degree vertices: node2vec
+    steps alternate hub -> leaf -> hub, the case the intersection path serves."""
+    rng = np.random.default_rng(seed)
+    n_hub, n_leaf = 6, 20000
+    und = set()
+    for h in range(n_hub):
+        for h2 in range(h + 1, n_hub):
+            und.add((h, h2))
+        for leaf in rng.choice(n_leaf, size=5000, replace=False):
+            und.add((h, n_hub + int(leaf)))
+    for _ in range(30000):
+        a, b = (int(x) for x in rng.integers(n_hub, n_hub + n_leaf, 2))
+        if a != b:
+            und.add((min(a, b), max(a, b)))
+    und = sorted(und)
+    edges = und + [(b, a) for a, b in und]
+    w = [int(x) for x in rng.integers(1, 50, size=len(und))]
+    return inputs.csr_from_edges(n_hub + n_leaf, edges, w + w)
+
+
+@pytest.mark.parametrize("mult", [(1, 2, 4), (3, 1, 2), (1, 2**20, 3)])
+def test_node2vec_intersection_path_matches_oracle(csaw, mult):
+    for g in (hubby_graph(), inputs.rmat_csr(12, 16, 40, 12)):
+        G = csaw.Graph(g.off, g.col, g.w)
+        G.build_cdf("edge_weight")
+        starts = np.concatenate([np.arange(min(g.V, 3000), dtype=np.uint32),
+                                 inputs.uniform_vertices(500, g.V, 1)])
+        got = csaw.walk(G, starts, 15, "node2vec", 9, mult)
+        assert np.array_equal(got, oracle.walk(g, starts, 15, "node2vec", 9, mult=mult))
+        G.close()
+    # no weights: the weight prefix sums are implicit
+    g = hubby_graph(7)
+    gu = inputs.CSRGraph(g.off, g.col, np.ones_like(g.w))
+    G = csaw.Graph(g.off, g.col, None)
+    starts = np.arange(3000, dtype=np.uint32)
+    assert np.array_equal(csaw.walk(G, starts, 15, "node2vec", 4, mult),
+                          oracle.walk(gu, starts, 15, "node2vec", 4, mult=mult))
+    G.close()
+
+
+def test_node2vec_s22_with_cached_weights(csaw):
+    import torch
+    wl = inputs.workload_node2vec_s22()
+    g = wl.graph
+    G = csaw.Graph(g.off, g.col, g.w)
+    G.build_cdf("edge_weight")
+    s = torch.from_numpy(wl.starts.view(np.int32)).cuda()
+    path = csaw.walk(G, s, wl.length, wl.bias, wl.rng_seed, wl.n2v_mult)
+    torch.cuda.synchronize()
+    deg = np.diff(g.off)
+    order = np.argsort(deg, kind="stable")
+    pick = np.unique(np.concatenate([order[-60:], inputs.uniform_vertices(200, g.V, 5).astype(np.int64)]))
+    ref = oracle.walk(g, wl.starts[pick], wl.length, wl.bias, wl.rng_seed, mult=wl.n2v_mult,
+                      walker_ids=pick.astype(np.uint64))
+    got = path[torch.from_numpy(pick).cuda()].cpu().numpy().view(np.uint32)
+    assert np.array_equal(got, ref)
+    G.close()

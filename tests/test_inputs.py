@@ -70,3 +70,22 @@ def test_seed_sets():
     u = inputs.uniform_vertices(100000, 1000, seed=9)
     counts = np.bincount(u, minlength=1000)
     assert counts.min() > 50 and counts.max() < 160
+
+
+def test_parallel_csr_build_equals_serial_build():
+    import ctypes
+    lib = inputs._load()
+    for scale, ef in ((9, 8), (14, 16)):
+        V, m = 1 << scale, ef << scale
+        src = np.empty(m, np.uint32)
+        dst = np.empty(m, np.uint32)
+        lib.csaw_gen_rmat_draws(scale, m, 0.57, 0.19, 0.19, 3, 4, inputs._p(src), inputs._p(dst))
+        outs = []
+        for fn, extra in ((lib.csaw_gen_build_csr, ()), (lib.csaw_gen_build_csr_mt, (7,))):
+            off = np.empty(V + 1, np.uint64)
+            col = np.empty(2 * m, np.uint32)
+            n = ctypes.c_uint64()
+            args = [V, m, inputs._p(src), inputs._p(dst), *extra, inputs._p(off), inputs._p(col), ctypes.byref(n)]
+            assert fn(*args) == 0
+            outs.append((off, col[: n.value]))
+        assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
