@@ -191,6 +191,24 @@ csaw_status csaw_sample(csaw_graph* g, const uint32_t* seeds, const uint64_t* in
                         const csaw_bias* bias, uint64_t rng_seed, int mem_kind, void* stream,
                         csaw_sample_result** out);
 
+/* Selection options.  attempt_cap: repeated-sampling attempts before the
+ * remaining picks switch to updated sampling (Sec. IV-B, Fig. 5(b)).  The
+ * default CSAW_ATTEMPT_CAP keeps the first k distinct hits of the draw
+ * sequence; 0 takes every pick by updated sampling -- one draw per pick, no
+ * rejection loop, the exact form of the paper's bipartite region search
+ * (Sec. IV-B, Theorem 2) generalised to any number of earlier picks.  Both
+ * give every pick the law b_j / (total of the unpicked biases); they use the
+ * draws differently, so their outputs differ. */
+typedef struct {
+    uint32_t attempt_cap;
+} csaw_sample_opts;
+
+/* csaw_sample with options (NULL = defaults). */
+csaw_status csaw_sample_ex(csaw_graph* g, const uint32_t* seeds, const uint64_t* inst_offsets,
+                           uint32_t n_instances, uint32_t depth, const uint32_t* fanout,
+                           const csaw_bias* bias, uint64_t rng_seed, int mem_kind, void* stream,
+                           const csaw_sample_opts* opts, csaw_sample_result** out);
+
 typedef struct {
     uint32_t depth;
     uint32_t n_instances;
@@ -239,6 +257,11 @@ void csaw_result_free(void* result);
 csaw_status csaw_sample_plan_create(csaw_graph* g, uint32_t n_instances, uint64_t max_seeds,
                                     uint32_t depth, const uint32_t* fanout, const csaw_bias* bias,
                                     csaw_sample_plan** out);
+
+/* csaw_sample_plan_create with selection options (NULL = defaults). */
+csaw_status csaw_sample_plan_create_ex(csaw_graph* g, uint32_t n_instances, uint64_t max_seeds,
+                                       uint32_t depth, const uint32_t* fanout, const csaw_bias* bias,
+                                       const csaw_sample_opts* opts, csaw_sample_plan** out);
 
 /* Run the plan on n_seeds seeds (<= max_seeds) split by inst_offsets
  * (n_instances + 1 entries, inst_offsets[n_instances] = n_seeds), in host or

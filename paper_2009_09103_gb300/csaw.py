@@ -43,6 +43,10 @@ class GraphInfo(ctypes.Structure):
                 ("device_bytes", ctypes.c_uint64)]
 
 
+class SampleOpts(ctypes.Structure):
+    _fields_ = [("attempt_cap", ctypes.c_uint32)]
+
+
 class SelectTuning(ctypes.Structure):
     _fields_ = [("theta_warp", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32)]
 
@@ -107,12 +111,16 @@ def lib():
         if hasattr(L, "csaw_sample"):
             L.csaw_sample.argtypes = [P, P, P, u32, u32, P, ctypes.POINTER(Bias), u64, i32, P,
                                       ctypes.POINTER(P)]
+            L.csaw_sample_ex.argtypes = [P, P, P, u32, u32, P, ctypes.POINTER(Bias), u64, i32, P,
+                                         ctypes.POINTER(SampleOpts), ctypes.POINTER(P)]
             L.csaw_sample_get_view.argtypes = [P, ctypes.POINTER(SampleView)]
             L.csaw_sample_copy_edges.argtypes = [P, P, P]
             L.csaw_result_free.argtypes = [P]
             L.csaw_result_free.restype = None
         PP = ctypes.POINTER(P)
         L.csaw_sample_plan_create.argtypes = [P, u32, u64, u32, P, ctypes.POINTER(Bias), PP]
+        L.csaw_sample_plan_create_ex.argtypes = [P, u32, u64, u32, P, ctypes.POINTER(Bias),
+                                                 ctypes.POINTER(SampleOpts), PP]
         L.csaw_sample_plan_run.argtypes = [P, P, u64, P, u64, i32, P]
         L.csaw_sample_plan_get_view.argtypes = [P, ctypes.POINTER(SampleView)]
         L.csaw_sample_plan_copy_edges.argtypes = [P, P, P]
@@ -130,8 +138,8 @@ def lib():
         L.csaw_server_stats.argtypes = [P, ctypes.POINTER(ServerStats)]
         for name in ("csaw_graph_create", "csaw_graph_destroy", "csaw_graph_get_info", "csaw_walk",
                      "csaw_graph_build_cdf", "csaw_graph_drop_cdf",
-                     "csaw_sample", "csaw_sample_get_view", "csaw_sample_copy_edges",
-                     "csaw_sample_plan_create", "csaw_sample_plan_run", "csaw_sample_plan_get_view",
+                     "csaw_sample", "csaw_sample_ex", "csaw_sample_get_view", "csaw_sample_copy_edges",
+                     "csaw_sample_plan_create", "csaw_sample_plan_create_ex", "csaw_sample_plan_run", "csaw_sample_plan_get_view",
                      "csaw_sample_plan_copy_edges", "csaw_sample_plan_get_info", "csaw_sample_plan_destroy",
                      "csaw_set_select_tuning", "csaw_get_select_tuning", "csaw_autotune_select",
                      "csaw_server_create", "csaw_server_destroy", "csaw_submit", "csaw_poll", "csaw_cancel",
@@ -277,7 +285,7 @@ class _SampleHandle:
 
 
 def sample(g: Graph, seeds, inst_offsets, fanout, bias="edge_weight", seed: int = 0,
-           stream=None, to_host: bool = True) -> SampleResult:
+           stream=None, to_host: bool = True, attempt_cap=None) -> SampleResult:
     """csaw_sample.  seeds/inst_offsets: numpy (host call) or torch CUDA
     tensors (device call).  Returns edges copied to host when to_host, else
     torch tensors that alias a library-owned result kept alive by the returned
@@ -296,8 +304,9 @@ def sample(g: Graph, seeds, inst_offsets, fanout, bias="edge_weight", seed: int 
         inst_offsets = np.ascontiguousarray(inst_offsets, dtype=np.uint64)
         n_inst = len(inst_offsets) - 1
         st = _stream_handle(stream) if stream is not None else None
-    _check(L.csaw_sample(g.handle, _ptr(seeds), _ptr(inst_offsets), n_inst, len(fan), _ptr(fan),
-                         ctypes.byref(b), seed, mem, st, ctypes.byref(out)))
+    opts = SampleOpts(ATTEMPT_CAP if attempt_cap is None else attempt_cap)
+    _check(L.csaw_sample_ex(g.handle, _ptr(seeds), _ptr(inst_offsets), n_inst, len(fan), _ptr(fan),
+                            ctypes.byref(b), seed, mem, st, ctypes.byref(opts), ctypes.byref(out)))
     holder = _SampleHandle(out)
     v = SampleView()
     _check(L.csaw_sample_get_view(out, ctypes.byref(v)))
@@ -339,15 +348,17 @@ def _wrap_device(ptr, n, holder):
 class SamplePlan:
     """The multi-instance sampling pipeline captured in a CUDA graph."""
 
-    def __init__(self, g: Graph, n_instances: int, max_seeds: int, fanout, bias="edge_weight"):
+    def __init__(self, g: Graph, n_instances: int, max_seeds: int, fanout, bias="edge_weight",
+                 attempt_cap=None):
         L = lib()
         self._g = g
         self._fan = np.ascontiguousarray(fanout, dtype=np.uint32)
         b = make_bias(bias) if isinstance(bias, str) else bias
         self._h = ctypes.c_void_p()
         self.n_instances = n_instances
-        _check(L.csaw_sample_plan_create(g.handle, n_instances, max_seeds, len(self._fan), _ptr(self._fan),
-                                         ctypes.byref(b), ctypes.byref(self._h)))
+        opts = SampleOpts(ATTEMPT_CAP if attempt_cap is None else attempt_cap)
+        _check(L.csaw_sample_plan_create_ex(g.handle, n_instances, max_seeds, len(self._fan), _ptr(self._fan),
+                                            ctypes.byref(b), ctypes.byref(opts), ctypes.byref(self._h)))
 
     def run(self, seeds, inst_offsets, seed: int = 0, stream=None):
         L = lib()

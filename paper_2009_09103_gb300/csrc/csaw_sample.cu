@@ -74,6 +74,7 @@ struct SelParams {
     uint64_t scratch_stride;              // entries per slot (max degree)
     const uint64_t* __restrict__ cdf;     // cached cumulative array (select_cdf_kernel)
     bool skip_warp_items;                 // warp items are served by select_cdf_kernel
+    uint32_t attempt_cap;                 // repeated-sampling attempts before updated sampling
 };
 
 template <int KIND>
@@ -111,12 +112,13 @@ __device__ void draw_picks(const SelParams& p, const uint64_t* S, uint32_t* bits
     const uint32_t lt = lanemask_lt();
     uint32_t have = 0;
     uint32_t a0 = 0;
-    while (have < cnt && a0 < CSAW_ATTEMPT_CAP) {
+    while (have < cnt && a0 < p.attempt_cap) {
+        const bool live = a0 + lane < p.attempt_cap;   // the last round may be partial
         const uint64_t r = philox_draw(p.k0, p.k1, a0 + lane, v, p.layer, inst);
-        const uint32_t i = upper_bound_S(S, d, scale_draw(r, T));
-        const bool chosen = (bits[i >> 5] >> (i & 31)) & 1u;
+        const uint32_t i = live ? upper_bound_S(S, d, scale_draw(r, T)) : 0xFFFFFFFFu;
+        const bool chosen = live && ((bits[i >> 5] >> (i & 31)) & 1u);
         const uint32_t peers = __match_any_sync(CSAW_FULL_MASK, i);
-        const bool fresh = !chosen && lane == __ffs(peers) - 1;
+        const bool fresh = live && !chosen && lane == __ffs(peers) - 1;
         const uint32_t bal = __ballot_sync(CSAW_FULL_MASK, fresh);
         const uint32_t rank = __popc(bal & lt);
         const uint32_t need = cnt - have;
@@ -129,7 +131,7 @@ __device__ void draw_picks(const SelParams& p, const uint64_t* S, uint32_t* bits
         __syncwarp();
     }
     if (have >= cnt) return;
-    // Updated sampling for the remaining picks (attempts CSAW_ATTEMPT_CAP, ...).
+    // Updated sampling for the remaining picks (attempts attempt_cap, ...).
     const uint32_t nwords = (d + 31) >> 5;
     uint64_t R = 0;
     for (uint32_t wi = lane; wi < nwords; wi += 32) {
@@ -142,7 +144,7 @@ __device__ void draw_picks(const SelParams& p, const uint64_t* S, uint32_t* bits
     }
     R = warp_sum_u64(R);
     if (lane == 0) {
-        for (uint32_t a = CSAW_ATTEMPT_CAP; have < cnt; ++a) {
+        for (uint32_t a = p.attempt_cap; have < cnt; ++a) {
             const uint64_t r = philox_draw(p.k0, p.k1, a, v, p.layer, inst);
             uint64_t x = scale_draw(r, T - R);
             // Walk the picked intervals in ascending order, skipping each one
@@ -384,10 +386,12 @@ __global__ void __launch_bounds__(SEL_THREADS) select_cdf_kernel(SelParams p)
         const uint64_t* row = p.cdf ? p.cdf + beg : nullptr;
         const uint64_t T = cdf_at(row, IMPLICIT, d - 1);
         uint32_t have = 0, a0 = 0;
-        while (have < cnt && a0 < CSAW_ATTEMPT_CAP) {
+        while (have < cnt && a0 < p.attempt_cap) {
+            const bool live = a0 + lane < p.attempt_cap;   // the last round may be partial
             const uint64_t x = scale_draw(philox_draw(p.k0, p.k1, a0 + lane, v, p.layer, inst), T);
-            uint32_t i;
-            if (IMPLICIT) {
+            uint32_t i = 0xFFFFFFFFu;
+            if (!live) {
+            } else if (IMPLICIT) {
                 i = (uint32_t)x;
             } else {
                 uint32_t lo = 0, hi = d - 1;
@@ -400,7 +404,7 @@ __global__ void __launch_bounds__(SEL_THREADS) select_cdf_kernel(SelParams p)
             bool chosen = false;
             for (uint32_t j = 0; j < have; ++j) chosen |= picks[j] == i;
             const uint32_t peers = __match_any_sync(CSAW_FULL_MASK, i);
-            const bool fresh = !chosen && lane == __ffs(peers) - 1;
+            const bool fresh = live && !chosen && lane == __ffs(peers) - 1;
             const uint32_t bal = __ballot_sync(CSAW_FULL_MASK, fresh);
             const uint32_t rank = __popc(bal & lt);
             const uint32_t need = cnt - have;
@@ -413,7 +417,7 @@ __global__ void __launch_bounds__(SEL_THREADS) select_cdf_kernel(SelParams p)
             __syncwarp();
         }
         if (have < cnt && lane == 0) {
-            // Updated sampling (attempts CSAW_ATTEMPT_CAP, ...): picks sorted
+            // Updated sampling (attempts attempt_cap, ...): picks sorted
             // ascending, the draw scaled to the unpicked total and moved past
             // every picked interval that starts at or below it.
             for (uint32_t a = 1; a < have; ++a) {
@@ -427,7 +431,7 @@ __global__ void __launch_bounds__(SEL_THREADS) select_cdf_kernel(SelParams p)
                 const uint32_t q = picks[j];
                 R += cdf_at(row, IMPLICIT, q) - (q ? cdf_at(row, IMPLICIT, q - 1) : 0);
             }
-            for (uint32_t a = CSAW_ATTEMPT_CAP; have < cnt; ++a) {
+            for (uint32_t a = p.attempt_cap; have < cnt; ++a) {
                 uint64_t x = scale_draw(philox_draw(p.k0, p.k1, a, v, p.layer, inst), T - R);
                 for (uint32_t j = 0; j < have; ++j) {
                     const uint32_t q = picks[j];
@@ -819,6 +823,7 @@ struct Pipeline {
     int sel_blocks = 1;
     uint32_t theta_w = WARP_MAX_DEG;
     bool cached = false;                 // selection over a cached cumulative array
+    uint32_t attempt_cap = CSAW_ATTEMPT_CAP;
     uint32_t k0 = 0, k1 = 0;
     const uint32_t* key_dev = nullptr;   // plan mode: Philox key in device memory
     uint64_t* ctr = nullptr;             // [CT_WORDS]
@@ -923,6 +928,7 @@ static csaw_status enqueue_select(Pipeline& P, uint32_t l, cudaStream_t s)
         sp.scratch_S = P.hub_S; sp.scratch_bits = P.hub_bits; sp.scratch_stride = g->max_degree;
         sp.cdf = P.cached && P.kind != CSAW_BIAS_UNIFORM ? g->cdf[P.kind] : nullptr;
         sp.skip_warp_items = P.cached;
+        sp.attempt_cap = P.attempt_cap;
         if (P.cached) {
             // warp items over the cached array; CTA items (more than PICK_MAX
             // picks) by the streaming kernel below
@@ -1034,7 +1040,8 @@ static csaw_status check_errors(uint64_t err)
 // csaw_sample: exact edge buffers, one wait per layer.
 static csaw_status run_sample(csaw_graph* g, const uint32_t* seeds, const uint64_t* inst_off,
                               uint32_t n_inst, uint64_t n_seeds, uint32_t depth, const uint32_t* fanout,
-                              int kind, uint64_t rng_seed, cudaStream_t s, csaw_sample_result* R)
+                              int kind, uint64_t rng_seed, uint32_t attempt_cap, cudaStream_t s,
+                              csaw_sample_result* R)
 {
     Temps tmp(s);
     auto get = [&](void** p, size_t bytes) -> csaw_status {
@@ -1045,6 +1052,7 @@ static csaw_status run_sample(csaw_graph* g, const uint32_t* seeds, const uint64
     auto get_out = [&](void** p, size_t bytes) -> csaw_status { return dalloc(p, bytes, s); };
     Pipeline P;
     P.init(g, kind, n_inst, depth, fanout, rng_seed);
+    P.attempt_cap = attempt_cap;
     P.seeds_cap = n_seeds;
     CSAW_TRY(alloc_common(P, get));
     CSAW_CUDA(cudaMemsetAsync(P.ctr, 0, sizeof(uint64_t) * CT_WORDS, s));
@@ -1092,12 +1100,13 @@ static csaw_status run_sample(csaw_graph* g, const uint32_t* seeds, const uint64
 
 using namespace csaw;
 
-extern "C" csaw_status csaw_sample(csaw_graph* g, const uint32_t* seeds, const uint64_t* inst_offsets,
-                                   uint32_t n_instances, uint32_t depth, const uint32_t* fanout,
-                                   const csaw_bias* bias, uint64_t rng_seed, int mem_kind, void* stream,
-                                   csaw_sample_result** out)
+extern "C" csaw_status csaw_sample_ex(csaw_graph* g, const uint32_t* seeds, const uint64_t* inst_offsets,
+                                      uint32_t n_instances, uint32_t depth, const uint32_t* fanout,
+                                      const csaw_bias* bias, uint64_t rng_seed, int mem_kind, void* stream,
+                                      const csaw_sample_opts* opts, csaw_sample_result** out)
 {
     clear_error();
+    const uint32_t attempt_cap = opts ? opts->attempt_cap : CSAW_ATTEMPT_CAP;
     if (!out) return fail(CSAW_ERR_INVALID, "out is NULL");
     *out = nullptr;
     if (!g) return fail(CSAW_ERR_INVALID, "graph is NULL");
@@ -1152,7 +1161,7 @@ extern "C" csaw_status csaw_sample(csaw_graph* g, const uint32_t* seeds, const u
     if (st == CSAW_OK && n_seeds >= 0xFFFFFFFFull) st = fail(CSAW_ERR_INVALID, "too many seeds");
     if (st == CSAW_OK && n_seeds > 0 && !seeds) st = fail(CSAW_ERR_INVALID, "seeds is NULL");
     if (st == CSAW_OK)
-        st = run_sample(g, d_seeds, d_io, n_instances, n_seeds, depth, fanout, kind, rng_seed, s, R);
+        st = run_sample(g, d_seeds, d_io, n_instances, n_seeds, depth, fanout, kind, rng_seed, attempt_cap, s, R);
     dfree(own_seeds, s);
     dfree(own_io, s);
     if (st != CSAW_OK) {
@@ -1162,6 +1171,15 @@ extern "C" csaw_status csaw_sample(csaw_graph* g, const uint32_t* seeds, const u
     }
     *out = R;
     return CSAW_OK;
+}
+
+extern "C" csaw_status csaw_sample(csaw_graph* g, const uint32_t* seeds, const uint64_t* inst_offsets,
+                                   uint32_t n_instances, uint32_t depth, const uint32_t* fanout,
+                                   const csaw_bias* bias, uint64_t rng_seed, int mem_kind, void* stream,
+                                   csaw_sample_result** out)
+{
+    return csaw_sample_ex(g, seeds, inst_offsets, n_instances, depth, fanout, bias, rng_seed, mem_kind,
+                          stream, nullptr, out);
 }
 
 extern "C" csaw_status csaw_sample_get_view(csaw_sample_result* r, csaw_sample_view* view)
@@ -1233,9 +1251,9 @@ static inline uint64_t sat_mul(uint64_t a, uint64_t b)
 
 }  // namespace csaw
 
-extern "C" csaw_status csaw_sample_plan_create(csaw_graph* g, uint32_t n_instances, uint64_t max_seeds,
-                                               uint32_t depth, const uint32_t* fanout, const csaw_bias* bias,
-                                               csaw_sample_plan** out)
+extern "C" csaw_status csaw_sample_plan_create_ex(csaw_graph* g, uint32_t n_instances, uint64_t max_seeds,
+                                                  uint32_t depth, const uint32_t* fanout, const csaw_bias* bias,
+                                                  const csaw_sample_opts* opts, csaw_sample_plan** out)
 {
     clear_error();
     if (!out) return fail(CSAW_ERR_INVALID, "out is NULL");
@@ -1253,6 +1271,7 @@ extern "C" csaw_status csaw_sample_plan_create(csaw_graph* g, uint32_t n_instanc
     if (!pl) return fail(CSAW_ERR_NOMEM, "host allocation failed");
     Pipeline& P = pl->P;
     P.init(g, kind, n_instances, depth, fanout, 0);
+    P.attempt_cap = opts ? opts->attempt_cap : CSAW_ATTEMPT_CAP;
     P.seeds_cap = max_seeds;
     pl->max_seeds = max_seeds;
     auto get = [&](void** p, size_t bytes) -> csaw_status {
@@ -1308,6 +1327,13 @@ extern "C" csaw_status csaw_sample_plan_create(csaw_graph* g, uint32_t n_instanc
     if (st != CSAW_OK) { delete pl; return st; }
     *out = pl;
     return CSAW_OK;
+}
+
+extern "C" csaw_status csaw_sample_plan_create(csaw_graph* g, uint32_t n_instances, uint64_t max_seeds,
+                                               uint32_t depth, const uint32_t* fanout, const csaw_bias* bias,
+                                               csaw_sample_plan** out)
+{
+    return csaw_sample_plan_create_ex(g, n_instances, max_seeds, depth, fanout, bias, nullptr, out);
 }
 
 extern "C" csaw_status csaw_sample_plan_run(csaw_sample_plan* pl, const uint32_t* seeds, uint64_t n_seeds,
@@ -1665,7 +1691,7 @@ extern "C" csaw_status csaw_select_noalloc(csaw_graph* g, const uint32_t* vertic
         sp.scratch_S = (uint64_t*)hub;
         sp.scratch_bits = (uint32_t*)(hub + (size_t)sel_blocks * g->max_degree * 8);
         sp.scratch_stride = g->max_degree;
-        sp.cdf = nullptr; sp.skip_warp_items = false;
+        sp.cdf = nullptr; sp.skip_warp_items = false; sp.attempt_cap = CSAW_ATTEMPT_CAP;
         switch (kind) {
         case CSAW_BIAS_UNIFORM: CSAW_TRY(launch_select<CSAW_BIAS_UNIFORM>(sp, sel_blocks, s)); break;
         case CSAW_BIAS_EDGE_WEIGHT: CSAW_TRY(launch_select<CSAW_BIAS_EDGE_WEIGHT>(sp, sel_blocks, s)); break;
