@@ -146,7 +146,7 @@ static int sort_blocks(uint64_t n_max, int sm_count)
     return (int)(tiles < cap ? tiles : cap);
 }
 
-size_t sort_scratch_bytes(uint64_t) { return sizeof(uint32_t) * (size_t)RADIX * SORT_MAX_BLOCKS + 64; }
+size_t sort_scratch_bytes(uint64_t) { return sizeof(uint32_t) * ((size_t)RADIX * SORT_MAX_BLOCKS + RADIX) + 64; }
 
 __global__ void __launch_bounds__(SORT_THREADS) sort_hist_kernel(const uint64_t* __restrict__ keys,
                                                                  const uint64_t* __restrict__ n_dev,
@@ -163,36 +163,43 @@ __global__ void __launch_bounds__(SORT_THREADS) sort_hist_kernel(const uint64_t*
     for (int d = threadIdx.x; d < RADIX; d += SORT_THREADS) hist[(size_t)d * gridDim.x + blockIdx.x] = s_h[d];
 }
 
-// Exclusive scan over hist[digit][block] (digit-major), in place; one block.
-__global__ void sort_scan_kernel(uint32_t* __restrict__ hist, int nblocks)
+// Exclusive scan of each digit's per-block counts, in place (one CTA per
+// digit, its counts are contiguous in the digit-major layout); the digit's
+// total goes to dtot[digit].
+__global__ void sort_scan_kernel(uint32_t* __restrict__ hist, int nblocks, uint32_t* __restrict__ dtot)
 {
     __shared__ uint64_t s_warp[33];
-    const int total = RADIX * nblocks;
-    const int per = (total + blockDim.x - 1) / blockDim.x;
-    const int lo = threadIdx.x * per;
-    const int hi = min(total, lo + per);
-    uint64_t s = 0;
-    for (int i = lo; i < hi; ++i) s += hist[i];
-    uint64_t excl;
-    block_exclusive_scan(s, &excl, s_warp);
-    uint64_t run = excl;
-    for (int i = lo; i < hi; ++i) {
-        const uint32_t v = hist[i];
-        hist[i] = (uint32_t)run;
-        run += v;
+    uint32_t* h = hist + (size_t)blockIdx.x * nblocks;
+    uint64_t carry = 0;
+    for (int base = 0; base < nblocks; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const uint32_t v = i < nblocks ? h[i] : 0u;
+        uint64_t excl;
+        const uint64_t tot = block_exclusive_scan(v, &excl, s_warp);
+        if (i < nblocks) h[i] = (uint32_t)(carry + excl);
+        carry += tot;
     }
+    if (threadIdx.x == 0) dtot[blockIdx.x] = (uint32_t)carry;
 }
 
 __global__ void __launch_bounds__(SORT_THREADS) sort_scatter_kernel(const uint64_t* __restrict__ keys,
                                                                     uint64_t* __restrict__ out,
                                                                     const uint64_t* __restrict__ n_dev,
                                                                     int shift,
-                                                                    const uint32_t* __restrict__ hist)
+                                                                    const uint32_t* __restrict__ hist,
+                                                                    const uint32_t* __restrict__ dtot)
 {
     __shared__ uint32_t s_base[RADIX];             // next output slot of each digit for this block
     __shared__ uint32_t s_cnt[SORT_WARPS][RADIX];  // per-warp digit counts, then warp offsets
+    __shared__ uint64_t s_warp[33];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int d = threadIdx.x; d < RADIX; d += SORT_THREADS) s_base[d] = hist[(size_t)d * gridDim.x + blockIdx.x];
+    {
+        // start of each digit = earlier digits' totals + earlier blocks' counts
+        static_assert(SORT_THREADS == RADIX, "one digit per thread");
+        uint64_t digit_base;
+        block_exclusive_scan(dtot[threadIdx.x], &digit_base, s_warp);
+        s_base[threadIdx.x] = (uint32_t)digit_base + hist[(size_t)threadIdx.x * gridDim.x + blockIdx.x];
+    }
     uint64_t lo, hi;
     block_range(*n_dev, SORT_TILE, &lo, &hi);
     const uint32_t lt = lanemask_lt();
@@ -251,12 +258,13 @@ csaw_status radix_sort_u64(uint64_t* keys, uint64_t* alt, const uint64_t* n_dev,
     if (n_max >= 0xFFFFFFFFull) return fail(CSAW_ERR_INVALID, "radix sort limited to 2^32-1 keys");
     const int nb = sort_blocks(n_max, sm_count);
     uint32_t* hist = (uint32_t*)scratch;
+    uint32_t* dtot = hist + (size_t)RADIX * SORT_MAX_BLOCKS;
     uint64_t* src = keys;
     uint64_t* dst = alt;
     for (int shift = 0; shift < bits; shift += 8) {
         sort_hist_kernel<<<nb, SORT_THREADS, 0, s>>>(src, n_dev, shift, hist);
-        sort_scan_kernel<<<1, 1024, 0, s>>>(hist, nb);
-        sort_scatter_kernel<<<nb, SORT_THREADS, 0, s>>>(src, dst, n_dev, shift, hist);
+        sort_scan_kernel<<<RADIX, 256, 0, s>>>(hist, nb, dtot);
+        sort_scatter_kernel<<<nb, SORT_THREADS, 0, s>>>(src, dst, n_dev, shift, hist, dtot);
         uint64_t* t = src; src = dst; dst = t;
     }
     cudaError_t e = cudaGetLastError();
