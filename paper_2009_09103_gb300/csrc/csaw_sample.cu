@@ -28,6 +28,7 @@
 // remaining picks use updated sampling (Sec. IV-B, Fig. 5(b)): the draw is
 // scaled to the unpicked total and mapped past the picked intervals, which is
 // the same choice as searching a recomputed prefix sum.
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -744,8 +745,13 @@ static csaw_status launch_count(const CountParams& p, uint64_t n, int sm_count, 
 // Resident blocks of the selection kernel per SM (occupancy limit).
 static int select_occupancy(int kind)
 {
-    static int cached[4] = {0, 0, 0, 0};
-    if (!cached[kind]) {
+    // looked up once per kind; the attribute is set before the value is
+    // published, so a thread that reads it may launch (calls may come from
+    // several threads, e.g. the request server's slots)
+    static std::atomic<int> cached[4];
+    const int have = cached[kind].load(std::memory_order_acquire);
+    if (have) return have;
+    {
         int per_sm = 1;
         cudaError_t e = cudaSuccess;
         switch (kind) {
@@ -763,9 +769,9 @@ static int select_occupancy(int kind)
             break;
         }
         if (e != cudaSuccess || per_sm < 1) per_sm = 1;
-        cached[kind] = per_sm;
+        cached[kind].store(per_sm, std::memory_order_release);
+        return per_sm;
     }
-    return cached[kind];
 }
 
 static int select_blocks(int kind, int sm_count)

@@ -16,6 +16,8 @@
 // a global counter and runs all its steps.  The path row is buffered one
 // 32-entry block per warp (lane j holds entry 32*blk + j) and written with
 // one coalesced store per block.
+#include <atomic>
+
 #include "csaw_internal.cuh"
 
 namespace csaw {
@@ -568,12 +570,15 @@ __global__ void __launch_bounds__(WALK_THREADS, (walk_min_blocks<KIND, WIDE>()))
 template <int KIND, bool WIDE>
 static csaw_status launch_walk_kw(const WalkParams& p, int sm_count, cudaStream_t s)
 {
-    static int per_sm = 0;
+    // resident blocks per SM, looked up once (calls may come from several threads)
+    static std::atomic<int> cached{0};
+    int per_sm = cached.load(std::memory_order_acquire);
     if (per_sm == 0) {
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel<KIND, WIDE>,
                                                                       WALK_THREADS, 0);
         if (e != cudaSuccess) return cuda_fail(e, "occupancy(walk)");
         if (per_sm < 1) per_sm = 1;
+        cached.store(per_sm, std::memory_order_release);
     }
     walk_kernel<KIND, WIDE><<<sm_count * per_sm, WALK_THREADS, 0, s>>>(p);
     cudaError_t e = cudaGetLastError();
@@ -671,16 +676,18 @@ csaw_status launch_walk_cached(const csaw_graph* g, int kind, const uint32_t* st
     p.off = g->off; p.col = g->col; p.cdf = kind == CSAW_BIAS_UNIFORM ? nullptr : g->cdf[kind];
     p.V = g->V; p.starts = starts; p.n = n; p.L = length; p.path = path;
     p.k0 = (uint32_t)rng_seed; p.k1 = (uint32_t)(rng_seed >> 32);
-    static int per_sm[2] = {0, 0};
+    static std::atomic<int> cached[2];
     const int u = kind == CSAW_BIAS_UNIFORM ? 1 : 0;
-    if (per_sm[u] == 0) {
-        cudaError_t e = u ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[u], walk_cached_kernel<true>, 256, 0)
-                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[u], walk_cached_kernel<false>, 256, 0);
+    int per_sm = cached[u].load(std::memory_order_acquire);
+    if (per_sm == 0) {
+        cudaError_t e = u ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_cached_kernel<true>, 256, 0)
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_cached_kernel<false>, 256, 0);
         if (e != cudaSuccess) return cuda_fail(e, "occupancy(walk_cached)");
-        if (per_sm[u] < 1) per_sm[u] = 1;
+        if (per_sm < 1) per_sm = 1;
+        cached[u].store(per_sm, std::memory_order_release);
     }
     uint64_t blocks = (n + 255) / 256;
-    const uint64_t cap = (uint64_t)g->sm_count * per_sm[u];
+    const uint64_t cap = (uint64_t)g->sm_count * per_sm;
     if (blocks > cap) blocks = cap;
     if (u) walk_cached_kernel<true><<<(unsigned)blocks, 256, 0, s>>>(p);
     else walk_cached_kernel<false><<<(unsigned)blocks, 256, 0, s>>>(p);

@@ -23,5 +23,5 @@ def test_reference_arm_two_ranks_gloo():
     assert len(lines) == 1, r.stdout
     out = json.loads(lines[0])
     assert out["impl"] == "reference" and out["n_gpus"] == 2
-    assert out["cpu_baseline"]["kind"] == "oracle" and out["cpu_baseline"]["cores"] == 1
+    assert out["cpu_baseline"]["kind"] == "oracle" and out["cpu_baseline"]["cores"] == (os.cpu_count() or 1)
     assert out["value"] > 0 and out["e2e"]["h2d_bytes_per_step"] == 0

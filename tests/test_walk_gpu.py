@@ -201,3 +201,13 @@ def test_walk_node2vec_wide_multipliers(csaw):
     mult = (1, 2**20, 3)
     assert np.array_equal(gpu_walk(csaw, g, starts, 10, "node2vec", 4, mult),
                           oracle.walk(g, starts, 10, "node2vec", 4, mult=mult))
+
+
+def test_walk_length_zero_and_one(csaw):
+    g = inputs.rmat_csr(10, 8, 50, 3)
+    starts = inputs.uniform_vertices(100, g.V, 4)
+    for L in (0, 1):
+        for bias in ("edge_weight", "uniform", "node2vec"):
+            got = gpu_walk(csaw, g, starts, L, bias, 5, (1, 2, 4))
+            assert got.shape == (100, L + 1)
+            assert np.array_equal(got, oracle.walk(g, starts, L, bias, 5, mult=(1, 2, 4)))
