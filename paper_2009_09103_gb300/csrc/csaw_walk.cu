@@ -6,7 +6,8 @@
 // the total T (keeping one running prefix per chunk in shared memory), maps
 // the draw to x in [0, T), then rescans only the chunk that holds x.  Biases
 // are read as 16-byte groups of four (a round is 4 groups per lane, 512
-// neighbours per warp); a lane sums its sixteen in 32 bits and the warp
+// neighbours per warp; interior rounds skip every bounds check); a lane sums
+// its sixteen in 32 bits and the warp
 // reduces with one redux.sync when the largest possible bias times 512 stays
 // below 2^32 (64-bit otherwise).  Locating x inside a 128-neighbour tile takes
 // one warp scan of per-lane sums and a four-step search in the hit lane.
@@ -25,9 +26,16 @@ namespace csaw {
 constexpr int WALK_THREADS = 256;
 constexpr int WALK_WARPS = WALK_THREADS / 32;
 constexpr uint32_t TILE = 128;              // neighbours per 16-byte load across the warp
-constexpr int U = 4;                        // tiles per round (four loads in flight per lane)
+#ifndef CSAW_WALK_U
+#define CSAW_WALK_U 4
+#endif
+constexpr int U = CSAW_WALK_U;              // tiles per round (U loads in flight per lane)
 constexpr uint32_t ROUND = TILE * U;        // 512 neighbours per round
 constexpr uint32_t CHUNK_SLOTS = 256;       // chunk prefixes per warp (shared memory)
+#ifndef CSAW_WALK_UNROLL
+#define CSAW_WALK_UNROLL 1
+#endif
+constexpr int PASS1_UNROLL = CSAW_WALK_UNROLL;   // rounds of pass 1 in flight
 
 struct WalkParams {
     const uint64_t* __restrict__ off;
@@ -413,6 +421,56 @@ __device__ __forceinline__ uint32_t locate_in_round(const Row& r, uint32_t rd, c
     return rd * ROUND + (uint32_t)ut * TILE + 4u * L + j - r.lo;
 }
 
+// Sum of the biases of an interior round rd (all of its groups inside the
+// row: rd >= 1 and (rd + 1) * ROUND <= span): no bounds checks or masks.
+template <int KIND, bool WIDE>
+__device__ __forceinline__ typename Acc<WIDE>::T sum_interior_round(const WalkParams& p, const Row& r,
+                                                                    uint32_t rd, int lane)
+{
+    using T = typename Acc<WIDE>::T;
+    T s = 0;
+    if constexpr (KIND == CSAW_BIAS_EDGE_WEIGHT) {
+        const uint4* base = reinterpret_cast<const uint4*>(p.w + r.abeg) + (rd * ROUND) / 4 + lane;
+        uint4 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = __ldg(base + u * (TILE / 4));
+#pragma unroll
+        for (int u = 0; u < U; ++u) s += (T)v[u].x + v[u].y + v[u].z + v[u].w;
+    } else {
+        const uint4* base = reinterpret_cast<const uint4*>(p.col + r.abeg) + (rd * ROUND) / 4 + lane;
+        uint4 c[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) c[u] = __ldg(base + u * (TILE / 4));
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            s += (T)__ldg(p.deg + c[u].x) + __ldg(p.deg + c[u].y) + __ldg(p.deg + c[u].z) + __ldg(p.deg + c[u].w);
+    }
+    return s;
+}
+
+// Biases of an interior round (no bounds checks or masks), for the locate step.
+template <int KIND>
+__device__ __forceinline__ void load_interior_round(const WalkParams& p, const Row& r, uint32_t rd,
+                                                    int lane, uint32_t (&b)[U][4])
+{
+    if constexpr (KIND == CSAW_BIAS_EDGE_WEIGHT) {
+        const uint4* base = reinterpret_cast<const uint4*>(p.w + r.abeg) + (rd * ROUND) / 4 + lane;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint4 v = __ldg(base + u * (TILE / 4));
+            b[u][0] = v.x; b[u][1] = v.y; b[u][2] = v.z; b[u][3] = v.w;
+        }
+    } else {
+        const uint4* base = reinterpret_cast<const uint4*>(p.col + r.abeg) + (rd * ROUND) / 4 + lane;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint4 c = __ldg(base + u * (TILE / 4));
+            b[u][0] = __ldg(p.deg + c.x); b[u][1] = __ldg(p.deg + c.y);
+            b[u][2] = __ldg(p.deg + c.z); b[u][3] = __ldg(p.deg + c.w);
+        }
+    }
+}
+
 // One walk step: the inverse transform pick for draw r over row `row`.
 // Returns false at a dead end (T == 0).
 template <int KIND, bool WIDE>
@@ -451,13 +509,17 @@ __device__ __forceinline__ bool walk_pick(const WalkParams& p, const Row& row, c
     uint64_t running = 0;
     for (uint32_t ch = 0; ch < nchunks; ++ch) {
         const uint32_t r_end = min(nrounds, (ch + 1) * G);
-#pragma unroll 2
+#pragma unroll PASS1_UNROLL
         for (uint32_t rd = ch * G; rd < r_end; ++rd) {
-            uint32_t b[U][4];
-            load_round<KIND>(p, row, rd, c, lane, s_seg, win, b);
             T s = 0;
+            if (KIND != CSAW_BIAS_NODE2VEC && rd >= 1 && (rd + 1) * ROUND <= row.span) {
+                s = sum_interior_round<KIND == CSAW_BIAS_NODE2VEC ? CSAW_BIAS_EDGE_WEIGHT : KIND, WIDE>(p, row, rd, lane);
+            } else {
+                uint32_t b[U][4];
+                load_round<KIND>(p, row, rd, c, lane, s_seg, win, b);
 #pragma unroll
-            for (int u = 0; u < U; ++u) s += (T)b[u][0] + b[u][1] + b[u][2] + b[u][3];
+                for (int u = 0; u < U; ++u) s += (T)b[u][0] + b[u][1] + b[u][2] + b[u][3];
+            }
             running += A::warp_sum(s);
         }
         if (lane == 0) s_chunk[ch] = running;
@@ -481,7 +543,10 @@ __device__ __forceinline__ bool walk_pick(const WalkParams& p, const Row& row, c
     const uint32_t r_end = min(nrounds, (ch + 1) * G);
     for (uint32_t rd = ch * G; rd < r_end; ++rd) {
         uint32_t b[U][4];
-        load_round<KIND>(p, row, rd, c, lane, s_seg, win, b);
+        if (KIND != CSAW_BIAS_NODE2VEC && rd >= 1 && (rd + 1) * ROUND <= row.span)
+            load_interior_round<KIND == CSAW_BIAS_NODE2VEC ? CSAW_BIAS_EDGE_WEIGHT : KIND>(p, row, rd, lane, b);
+        else
+            load_round<KIND>(p, row, rd, c, lane, s_seg, win, b);
         T s = 0;
 #pragma unroll
         for (int u = 0; u < U; ++u) s += (T)b[u][0] + b[u][1] + b[u][2] + b[u][3];
@@ -496,12 +561,18 @@ __device__ __forceinline__ bool walk_pick(const WalkParams& p, const Row& row, c
     return true;
 }
 
-// Resident blocks per SM the register budget is set for: the light biases
-// fit 48 registers, neighbour degree 64, node2vec's membership windows 80.
+// Resident blocks per SM the register budget is set for (the kernel is
+// latency-bound, so residency beats a few spilled registers): edge weight 6
+// (40 registers), neighbour degree 4 (64), node2vec's windows 3 (80).
+#ifndef CSAW_WALK_EW_BLOCKS
+#define CSAW_WALK_EW_BLOCKS 6   // edge-weight, 32-bit sums (swept: 5 -> 42.9 ms, 6 -> 39.9 ms, 7 -> 43.8 ms at s20)
+#endif
+
 template <int KIND, bool WIDE>
 constexpr int walk_min_blocks()
 {
-    return (KIND == CSAW_BIAS_UNIFORM || (KIND == CSAW_BIAS_EDGE_WEIGHT && !WIDE)) ? 5
+    return KIND == CSAW_BIAS_UNIFORM ? 5
+           : (KIND == CSAW_BIAS_EDGE_WEIGHT && !WIDE) ? CSAW_WALK_EW_BLOCKS
            : KIND == CSAW_BIAS_NODE2VEC ? 3 : 4;
 }
 
