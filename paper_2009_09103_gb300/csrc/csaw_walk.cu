@@ -109,9 +109,10 @@ __device__ __forceinline__ void group_bias(const WalkParams& p, const Row& r, ui
 // A = lower_bound(N(prev), smallest id of the tile) and holds up to SEG_SMEM
 // entries.  Tiles come in ascending id order, so the next tile's A is usually
 // found inside the staged window with no global access; the window is
-// reloaded (one coalesced read) only when A moves.  Ids beyond the window's
-// last entry are searched in the rest of N(prev) in global memory.  All lanes
-// call this together, for tiles in ascending order; win = {A, 0} restarts.
+// reloaded (one coalesced read from A) only when it does not cover the tile's
+// ids, so a short N(prev) is read once per row.  Ids beyond the window's last
+// entry are searched in the rest of N(prev) in global memory.  All lanes call
+// this together, for tiles in ascending order; win = {pbeg, 0} restarts.
 constexpr uint32_t SEG_SMEM = 256;
 
 struct N2vWin {
@@ -170,17 +171,20 @@ __device__ __forceinline__ void n2v_tile_bias(const WalkParams& p, const Row& r,
     if (mn > mx) return;   // no neighbour of the row in this tile
     // A = lower_bound(N(prev), mn): inside the staged window when its last
     // entry is >= mn, else in the rest of N(prev) after the window.
+    const uint64_t wend = win.A + win.n;
     uint64_t A;
     if (win.n > 0 && mn <= s_seg[win.n - 1]) {
         A = win.A + lower_bound_smem(s_seg, win.n, mn);
     } else {
-        const uint64_t from = win.n > 0 ? win.A + win.n : c.pbeg;
         uint64_t a0 = 0;
-        if (lane == 0) a0 = lower_bound_col(p.col, from, c.pend, mn);
+        if (lane == 0) a0 = lower_bound_col(p.col, wend, c.pend, mn);
         A = __shfl_sync(CSAW_FULL_MASK, a0, 0);
     }
+    // Re-stage only when the window does not cover the tile's ids: A lies
+    // past it, or the window ends below mx before the end of N(prev).
+    const bool covered = A < wend && (wend == c.pend || mx <= s_seg[win.n - 1]);
     __syncwarp();
-    if (win.n == 0 || A != win.A) {
+    if (!covered) {
         const uint64_t left = c.pend - A;
         const uint32_t n = left < SEG_SMEM ? (uint32_t)left : SEG_SMEM;
         for (uint32_t i = lane; i < n; i += 32) s_seg[i] = __ldg(p.col + A + i);
@@ -190,6 +194,7 @@ __device__ __forceinline__ void n2v_tile_bias(const WalkParams& p, const Row& r,
     }
     const bool to_end = win.A + win.n == c.pend;
     const uint32_t last = win.n > 0 ? s_seg[win.n - 1] : 0u;
+    const uint32_t off = (uint32_t)(A - win.A);   // entries below A are all < mn
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         if (!valid[j]) continue;
@@ -200,7 +205,7 @@ __device__ __forceinline__ void n2v_tile_bias(const WalkParams& p, const Row& r,
         } else {
             bool in;
             if (to_end || u <= last) {
-                const uint32_t at = lower_bound_smem(s_seg, win.n, u);
+                const uint32_t at = off + lower_bound_smem(s_seg + off, win.n - off, u);
                 in = at < win.n && s_seg[at] == u;
             } else {
                 const uint64_t at = lower_bound_col(p.col, win.A + win.n, c.pend, u);
@@ -490,7 +495,7 @@ __device__ __forceinline__ bool walk_pick(const WalkParams& p, const Row& row, c
         *idx = (uint32_t)scale_draw(r, row.d);   // b = 1: S[i] = i + 1, the pick is x itself
         return true;
     }
-    N2vWin win = {0, 0};
+    N2vWin win = {c.pbeg, 0};
     const uint32_t nrounds = (row.span + ROUND - 1) / ROUND;
     if (nrounds == 1) {
         uint32_t b[U][4];
@@ -538,7 +543,7 @@ __device__ __forceinline__ bool walk_pick(const WalkParams& p, const Row& row, c
     }
     uint64_t before = ch > 0 ? s_chunk[ch - 1] : 0;
     __syncwarp();
-    win.n = 0;   // pass 2 restarts the node2vec window at the chunk's first tile
+    win = {c.pbeg, 0};   // pass 2 restarts the node2vec window at the chunk's first tile
     // Pass 2: rescan that chunk's rounds.
     const uint32_t r_end = min(nrounds, (ch + 1) * G);
     for (uint32_t rd = ch * G; rd < r_end; ++rd) {

@@ -211,3 +211,38 @@ def test_walk_length_zero_and_one(csaw):
             got = gpu_walk(csaw, g, starts, L, bias, 5, (1, 2, 4))
             assert got.shape == (100, L + 1)
             assert np.array_equal(got, oracle.walk(g, starts, L, bias, 5, mult=(1, 2, 4)))
+
+
+def dense_overlap_graph(seed=11):
+    """Three hubs joined by heavy edges; hub 0 is adjacent to 20,000 leaves,
+    hubs 1 and 2 to random subsets of them (3,000 and 600).  A node2vec step at
+    hub 1 or 2 after hub 0 tests membership against a previous list far denser
+    than each 128-neighbour tile, which slides the staged window of N(prev)
+    and then falls back to global searches."""
+    rng = np.random.default_rng(seed)
+    n_hub, n_leaf = 3, 20000
+    und = {(0, 1): 10**6, (0, 2): 10**6, (1, 2): 10**6}
+    leaves = n_hub + np.arange(n_leaf)
+    for h, size in ((0, n_leaf), (1, 3000), (2, 600)):
+        for leaf in rng.choice(leaves, size=size, replace=False):
+            und[(h, int(leaf))] = int(rng.integers(1, 50))
+    for _ in range(20000):
+        a, b = (int(x) for x in rng.integers(n_hub, n_hub + n_leaf, 2))
+        if a != b:
+            und[(min(a, b), max(a, b))] = int(rng.integers(1, 50))
+    items = sorted(und.items())
+    edges = [e for e, _ in items] + [(b, a) for (a, b), _ in items]
+    w = [x for _, x in items]
+    return inputs.csr_from_edges(n_hub + n_leaf, edges, w + w)
+
+
+@pytest.mark.parametrize("mult", [(1, 2, 4), (3, 1, 2), (1, 4000, 3)])   # 10**6 * 4000 < 2**32
+def test_walk_node2vec_dense_previous_list(csaw, mult):
+    g = dense_overlap_graph()
+    starts = np.concatenate([np.repeat(np.arange(3, dtype=np.uint32), 400),
+                             inputs.uniform_vertices(800, g.V, 5)])
+    got = gpu_walk(csaw, g, starts, 12, "node2vec", 21, mult)
+    assert np.array_equal(got, oracle.walk(g, starts, 12, "node2vec", 21, mult=mult))
+    gu = inputs.CSRGraph(g.off, g.col, np.ones_like(g.w))
+    got = gpu_walk(csaw, inputs.CSRGraph(g.off, g.col, None), starts, 12, "node2vec", 22, mult)
+    assert np.array_equal(got, oracle.walk(gu, starts, 12, "node2vec", 22, mult=mult))
