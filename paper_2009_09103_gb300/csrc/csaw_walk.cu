@@ -113,7 +113,8 @@ __device__ __forceinline__ void group_bias(const WalkParams& p, const Row& r, ui
 // ids, so a short N(prev) is read once per row.  Ids beyond the window's last
 // entry are searched in the rest of N(prev) in global memory.  All lanes call
 // this together, for tiles in ascending order; win = {pbeg, 0} restarts.
-constexpr uint32_t SEG_SMEM = 256;
+constexpr uint32_t SEG_SMEM = 1024;
+constexpr uint32_t SEG_GROUP = 256;   // entries staged per coalesced step
 
 struct N2vWin {
     uint64_t A;    // first staged index of N(prev) in col[]
@@ -185,12 +186,24 @@ __device__ __forceinline__ void n2v_tile_bias(const WalkParams& p, const Row& r,
     const bool covered = A < wend && (wend == c.pend || mx <= s_seg[win.n - 1]);
     __syncwarp();
     if (!covered) {
+        // Stage from A in groups of SEG_GROUP until the tile's last id is
+        // covered, the buffer is full, or the staged density says the
+        // buffer cannot reach that id.
         const uint64_t left = c.pend - A;
-        const uint32_t n = left < SEG_SMEM ? (uint32_t)left : SEG_SMEM;
-        for (uint32_t i = lane; i < n; i += 32) s_seg[i] = __ldg(p.col + A + i);
+        const uint32_t cap = left < SEG_SMEM ? (uint32_t)left : SEG_SMEM;
+        uint32_t n = 0;
+        while (true) {
+            const uint32_t g = min(cap - n, SEG_GROUP);
+            for (uint32_t i = lane; i < g; i += 32) s_seg[n + i] = __ldg(p.col + A + n + i);
+            n += g;
+            __syncwarp();
+            if (n == cap) break;
+            const uint32_t hi = s_seg[n - 1];
+            if (hi >= mx) break;
+            if ((float)(mx - hi) * (float)n > (float)(cap - n) * (float)max(hi - s_seg[0], 1u)) break;
+        }
         win.A = A;
         win.n = n;
-        __syncwarp();
     }
     const bool to_end = win.A + win.n == c.pend;
     const uint32_t last = win.n > 0 ? s_seg[win.n - 1] : 0u;
@@ -487,6 +500,7 @@ __device__ __forceinline__ bool walk_pick(const WalkParams& p, const Row& row, c
     using T = typename A::T;
     if (row.d == 0) return false;
     if constexpr (KIND == CSAW_BIAS_NODE2VEC) {
+        __syncwarp();   // the last step's reads of the overlaid buffers are done
         if (c.prev != CSAW_NONE && (p.cdfw != nullptr || p.w == nullptr) &&
             n2v_fast_pays(row.d, (uint32_t)(c.pend - c.pbeg)))
             return n2v_fast_pick(p, row, c, r, lane, s_jpos, s_jw, idx);
@@ -584,15 +598,16 @@ constexpr int walk_min_blocks()
 template <int KIND, bool WIDE>
 __global__ void __launch_bounds__(WALK_THREADS, (walk_min_blocks<KIND, WIDE>())) walk_kernel(WalkParams p)
 {
-    __shared__ uint64_t s_chunk_all[WALK_WARPS][CHUNK_SLOTS];
-    __shared__ uint32_t s_seg_all[KIND == CSAW_BIAS_NODE2VEC ? WALK_WARPS : 1][SEG_SMEM];
-    __shared__ uint32_t s_jpos_all[KIND == CSAW_BIAS_NODE2VEC ? WALK_WARPS : 1][KIND == CSAW_BIAS_NODE2VEC ? JCAP : 1];
-    __shared__ uint64_t s_jw_all[KIND == CSAW_BIAS_NODE2VEC ? WALK_WARPS : 1][KIND == CSAW_BIAS_NODE2VEC ? JCAP : 1];
+    // Per warp: the chunk prefix table, then (node2vec) the N(prev) window.
+    // The intersection path's buffers overlay them: a step uses one or the other.
+    constexpr uint32_t WARP_WORDS = CHUNK_SLOTS + (KIND == CSAW_BIAS_NODE2VEC ? SEG_SMEM / 2 : 0);
+    static_assert(KIND != CSAW_BIAS_NODE2VEC || JCAP * 12 <= WARP_WORDS * 8, "intersection buffers overflow");
+    __shared__ uint64_t s_warp_all[WALK_WARPS][WARP_WORDS];
     const int lane = threadIdx.x & 31;
-    uint64_t* s_chunk = s_chunk_all[threadIdx.x >> 5];
-    uint32_t* s_seg = s_seg_all[KIND == CSAW_BIAS_NODE2VEC ? (threadIdx.x >> 5) : 0];
-    uint32_t* s_jpos = s_jpos_all[KIND == CSAW_BIAS_NODE2VEC ? (threadIdx.x >> 5) : 0];
-    uint64_t* s_jw = s_jw_all[KIND == CSAW_BIAS_NODE2VEC ? (threadIdx.x >> 5) : 0];
+    uint64_t* s_chunk = s_warp_all[threadIdx.x >> 5];
+    uint32_t* s_seg = reinterpret_cast<uint32_t*>(s_chunk + (KIND == CSAW_BIAS_NODE2VEC ? CHUNK_SLOTS : 0));
+    uint64_t* s_jw = s_chunk;
+    uint32_t* s_jpos = reinterpret_cast<uint32_t*>(s_chunk + JCAP);
     const uint64_t row_len = (uint64_t)p.L + 1;
 
     while (true) {
