@@ -208,25 +208,33 @@ __device__ __forceinline__ void n2v_tile_bias(const WalkParams& p, const Row& r,
     const bool to_end = win.A + win.n == c.pend;
     const uint32_t last = win.n > 0 ? s_seg[win.n - 1] : 0u;
     const uint32_t off = (uint32_t)(A - win.A);   // entries below A are all < mn
-#pragma unroll
+    // One id per iteration, rotating uu/b/valid so that the body (and its
+    // searches) is emitted once: the kernel's code has to fit the
+    // instruction cache.
+    uint32_t vm = (valid[0] ? 1u : 0u) | (valid[1] ? 2u : 0u) | (valid[2] ? 4u : 0u) | (valid[3] ? 8u : 0u);
+#pragma unroll 1
     for (int j = 0; j < 4; ++j) {
-        if (!valid[j]) continue;
-        const uint32_t u = uu[j];
-        uint32_t m;
-        if (u == c.prev) {
-            m = p.m0;
-        } else {
-            bool in;
-            if (to_end || u <= last) {
-                const uint32_t at = off + lower_bound_smem(s_seg + off, win.n - off, u);
-                in = at < win.n && s_seg[at] == u;
+        const uint32_t u = uu[0];
+        if (vm & 1u) {
+            uint32_t m;
+            if (u == c.prev) {
+                m = p.m0;
             } else {
-                const uint64_t at = lower_bound_col(p.col, win.A + win.n, c.pend, u);
-                in = at < c.pend && __ldg(p.col + at) == u;
+                bool in;
+                if (to_end || u <= last) {
+                    const uint32_t at = off + lower_bound_smem(s_seg + off, win.n - off, u);
+                    in = at < win.n && s_seg[at] == u;
+                } else {
+                    const uint64_t at = lower_bound_col(p.col, win.A + win.n, c.pend, u);
+                    in = at < c.pend && __ldg(p.col + at) == u;
+                }
+                m = in ? p.m1 : p.m2;
             }
-            m = in ? p.m1 : p.m2;
+            b[0] *= m;
         }
-        b[j] *= m;
+        uu[0] = uu[1]; uu[1] = uu[2]; uu[2] = uu[3];
+        const uint32_t t = b[0]; b[0] = b[1]; b[1] = b[2]; b[2] = b[3]; b[3] = t;
+        vm >>= 1;
     }
 }
 
@@ -531,8 +539,16 @@ __device__ __forceinline__ bool walk_pick(const WalkParams& p, const Row& row, c
 #pragma unroll PASS1_UNROLL
         for (uint32_t rd = ch * G; rd < r_end; ++rd) {
             T s = 0;
-            if (KIND != CSAW_BIAS_NODE2VEC && rd >= 1 && (rd + 1) * ROUND <= row.span) {
-                s = sum_interior_round<KIND == CSAW_BIAS_NODE2VEC ? CSAW_BIAS_EDGE_WEIGHT : KIND, WIDE>(p, row, rd, lane);
+            if constexpr (KIND == CSAW_BIAS_NODE2VEC) {
+                // only the round's sum is needed: tiles in a rolled loop
+#pragma unroll 1
+                for (int u = 0; u < U; ++u) {
+                    uint32_t t[4];
+                    n2v_tile_bias(p, row, rd * ROUND + u * TILE, c, lane, s_seg, win, t);
+                    s += (T)t[0] + t[1] + t[2] + t[3];
+                }
+            } else if (rd >= 1 && (rd + 1) * ROUND <= row.span) {
+                s = sum_interior_round<KIND, WIDE>(p, row, rd, lane);
             } else {
                 uint32_t b[U][4];
                 load_round<KIND>(p, row, rd, c, lane, s_seg, win, b);
