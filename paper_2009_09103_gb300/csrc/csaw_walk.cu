@@ -396,16 +396,32 @@ __device__ __forceinline__ bool n2v_fast_pick(const WalkParams& p, const Row& ro
     return true;
 }
 
-// Biases of round `rd` (tiles rd*U .. rd*U+U-1) into b[u][j].
+// Biases of round `rd` (tiles rd*U .. rd*U+U-1) into b[u][j].  node2vec
+// tiles are formed in a rolled loop (one emitted copy of the tile code) and
+// pass through s_round (ROUND words of this warp's shared memory, each lane
+// reading back only what it wrote) so that b is not live across it.
 template <int KIND>
 __device__ __forceinline__ void load_round(const WalkParams& p, const Row& r, uint32_t rd,
                                            const PrevCtx& c, int lane, uint32_t* s_seg, N2vWin& win,
-                                           uint32_t (&b)[U][4])
+                                           uint32_t* s_round, uint32_t (&b)[U][4])
 {
+    if constexpr (KIND == CSAW_BIAS_NODE2VEC) {
+        uint4* s4 = reinterpret_cast<uint4*>(s_round);
+#pragma unroll 1
+        for (int u = 0; u < U; ++u) {
+            uint32_t t[4] = {0u, 0u, 0u, 0u};
+            if (rd * ROUND + u * TILE < r.span)   // warp-uniform: tiles past the row are empty
+                n2v_tile_bias(p, r, rd * ROUND + u * TILE, c, lane, s_seg, win, t);
+            s4[u * 32 + lane] = make_uint4(t[0], t[1], t[2], t[3]);
+        }
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-        if constexpr (KIND == CSAW_BIAS_NODE2VEC) n2v_tile_bias(p, r, rd * ROUND + u * TILE, c, lane, s_seg, win, b[u]);
-        else group_bias<KIND>(p, r, rd * ROUND + u * TILE + 4u * lane, c, b[u]);
+        for (int u = 0; u < U; ++u) {
+            const uint4 v = s4[u * 32 + lane];
+            b[u][0] = v.x; b[u][1] = v.y; b[u][2] = v.z; b[u][3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < U; ++u) group_bias<KIND>(p, r, rd * ROUND + u * TILE + 4u * lane, c, b[u]);
     }
 }
 
@@ -518,10 +534,14 @@ __device__ __forceinline__ bool walk_pick(const WalkParams& p, const Row& row, c
         return true;
     }
     N2vWin win = {c.pbeg, 0};
+    // node2vec round biases pass through the chunk table's space: it is free
+    // in a one-round step, and in pass 2 once the chunk has been found
+    static_assert(ROUND <= 2 * CHUNK_SLOTS, "a round must fit the chunk table");
+    uint32_t* s_round = reinterpret_cast<uint32_t*>(s_chunk);
     const uint32_t nrounds = (row.span + ROUND - 1) / ROUND;
     if (nrounds == 1) {
         uint32_t b[U][4];
-        load_round<KIND>(p, row, 0, c, lane, s_seg, win, b);
+        load_round<KIND>(p, row, 0, c, lane, s_seg, win, s_round, b);
         T s = 0;
 #pragma unroll
         for (int u = 0; u < U; ++u) s += (T)b[u][0] + b[u][1] + b[u][2] + b[u][3];
@@ -551,7 +571,7 @@ __device__ __forceinline__ bool walk_pick(const WalkParams& p, const Row& row, c
                 s = sum_interior_round<KIND, WIDE>(p, row, rd, lane);
             } else {
                 uint32_t b[U][4];
-                load_round<KIND>(p, row, rd, c, lane, s_seg, win, b);
+                load_round<KIND>(p, row, rd, c, lane, s_seg, win, s_round, b);
 #pragma unroll
                 for (int u = 0; u < U; ++u) s += (T)b[u][0] + b[u][1] + b[u][2] + b[u][3];
             }
@@ -581,7 +601,7 @@ __device__ __forceinline__ bool walk_pick(const WalkParams& p, const Row& row, c
         if (KIND != CSAW_BIAS_NODE2VEC && rd >= 1 && (rd + 1) * ROUND <= row.span)
             load_interior_round<KIND == CSAW_BIAS_NODE2VEC ? CSAW_BIAS_EDGE_WEIGHT : KIND>(p, row, rd, lane, b);
         else
-            load_round<KIND>(p, row, rd, c, lane, s_seg, win, b);
+            load_round<KIND>(p, row, rd, c, lane, s_seg, win, s_round, b);
         T s = 0;
 #pragma unroll
         for (int u = 0; u < U; ++u) s += (T)b[u][0] + b[u][1] + b[u][2] + b[u][3];
@@ -618,7 +638,7 @@ __global__ void __launch_bounds__(WALK_THREADS, (walk_min_blocks<KIND, WIDE>()))
     // The intersection path's buffers overlay them: a step uses one or the other.
     constexpr uint32_t WARP_WORDS = CHUNK_SLOTS + (KIND == CSAW_BIAS_NODE2VEC ? SEG_SMEM / 2 : 0);
     static_assert(KIND != CSAW_BIAS_NODE2VEC || JCAP * 12 <= WARP_WORDS * 8, "intersection buffers overflow");
-    __shared__ uint64_t s_warp_all[WALK_WARPS][WARP_WORDS];
+    __shared__ __align__(16) uint64_t s_warp_all[WALK_WARPS][WARP_WORDS];
     const int lane = threadIdx.x & 31;
     uint64_t* s_chunk = s_warp_all[threadIdx.x >> 5];
     uint32_t* s_seg = reinterpret_cast<uint32_t*>(s_chunk + (KIND == CSAW_BIAS_NODE2VEC ? CHUNK_SLOTS : 0));
