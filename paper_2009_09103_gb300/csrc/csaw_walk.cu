@@ -115,6 +115,7 @@ __device__ __forceinline__ void group_bias(const WalkParams& p, const Row& r, ui
 // this together, for tiles in ascending order; win = {pbeg, 0} restarts.
 constexpr uint32_t SEG_SMEM = 1024;
 constexpr uint32_t SEG_GROUP = 256;   // entries staged per coalesced step
+constexpr uint32_t N2V_SCAN = 32;     // N(prev) entries in a tile's id range compared directly
 
 struct N2vWin {
     uint64_t A;    // first staged index of N(prev) in col[]
@@ -137,6 +138,17 @@ __device__ __forceinline__ uint32_t lower_bound_smem(const uint32_t* s, uint32_t
     while (lo < hi) {
         const uint32_t mid = (lo + hi) >> 1;
         if (s[mid] < u) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// first index i of the sorted s[0, n) with s[i] > u
+__device__ __forceinline__ uint32_t upper_bound_smem(const uint32_t* s, uint32_t n, uint32_t u)
+{
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (s[mid] <= u) lo = mid + 1; else hi = mid;
     }
     return lo;
 }
@@ -208,6 +220,24 @@ __device__ __forceinline__ void n2v_tile_bias(const WalkParams& p, const Row& r,
     const bool to_end = win.A + win.n == c.pend;
     const uint32_t last = win.n > 0 ? s_seg[win.n - 1] : 0u;
     const uint32_t off = (uint32_t)(A - win.A);   // entries below A are all < mn
+    if (to_end || mx <= last) {
+        // All of N(prev) within [mn, mx] is staged: s_seg[off, e).  When it is
+        // short (a hub after a low-degree vertex), each lane compares its ids
+        // with every entry instead of searching for each id.
+        const uint32_t e = off + upper_bound_smem(s_seg + off, win.n - off, mx);
+        if (e - off <= N2V_SCAN) {
+            uint32_t hit = 0u;   // bit j: uu[j] is in N(prev)
+            for (uint32_t i = off; i < e; ++i) {
+                const uint32_t y = s_seg[i];
+                hit |= (uu[0] == y ? 1u : 0u) | (uu[1] == y ? 2u : 0u) | (uu[2] == y ? 4u : 0u) |
+                       (uu[3] == y ? 8u : 0u);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (valid[j]) b[j] *= uu[j] == c.prev ? p.m0 : ((hit >> j) & 1u) ? p.m1 : p.m2;
+            return;
+        }
+    }
     // One id per iteration, rotating uu/b/valid so that the body (and its
     // searches) is emitted once: the kernel's code has to fit the
     // instruction cache.
