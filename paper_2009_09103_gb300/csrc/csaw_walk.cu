@@ -108,11 +108,14 @@ __device__ __forceinline__ void group_bias(const WalkParams& p, const Row& r, ui
 // window of N(prev) is kept staged in this warp's shared buffer: it starts at
 // A = lower_bound(N(prev), smallest id of the tile) and holds up to SEG_SMEM
 // entries.  Tiles come in ascending id order, so the next tile's A is usually
-// found inside the staged window with no global access; the window is
-// reloaded (one coalesced read from A) only when it does not cover the tile's
-// ids, so a short N(prev) is read once per row.  Ids beyond the window's last
-// entry are searched in the rest of N(prev) in global memory.  All lanes call
-// this together, for tiles in ascending order; win = {pbeg, 0} restarts.
+// found inside the staged window (most often at the cursor left by the last
+// tile) with no global access; the window is reloaded from A (coalesced reads
+// in groups of SEG_GROUP) only when it does not cover the tile's ids.  When at
+// most N2V_SCAN staged entries fall in the tile's id range, each lane compares
+// its ids with them; otherwise each id is binary-searched in the window, and
+// ids beyond the window's last entry in the rest of N(prev) in global memory.
+// All lanes call this together, for tiles in ascending order; win = {pbeg, 0,
+// 0} restarts.
 constexpr uint32_t SEG_SMEM = 1024;
 constexpr uint32_t SEG_GROUP = 256;   // entries staged per coalesced step
 constexpr uint32_t N2V_SCAN = 32;     // N(prev) entries in a tile's id range compared directly
@@ -120,6 +123,7 @@ constexpr uint32_t N2V_SCAN = 32;     // N(prev) entries in a tile's id range co
 struct N2vWin {
     uint64_t A;    // first staged index of N(prev) in col[]
     uint32_t n;    // staged entries
+    uint32_t cur;  // staged entries before cur are below every later tile's ids
 };
 
 __device__ __forceinline__ uint64_t lower_bound_col(const uint32_t* __restrict__ col, uint64_t lo,
@@ -138,17 +142,6 @@ __device__ __forceinline__ uint32_t lower_bound_smem(const uint32_t* s, uint32_t
     while (lo < hi) {
         const uint32_t mid = (lo + hi) >> 1;
         if (s[mid] < u) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-
-// first index i of the sorted s[0, n) with s[i] > u
-__device__ __forceinline__ uint32_t upper_bound_smem(const uint32_t* s, uint32_t n, uint32_t u)
-{
-    uint32_t lo = 0, hi = n;
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (s[mid] <= u) lo = mid + 1; else hi = mid;
     }
     return lo;
 }
@@ -187,7 +180,9 @@ __device__ __forceinline__ void n2v_tile_bias(const WalkParams& p, const Row& r,
     const uint64_t wend = win.A + win.n;
     uint64_t A;
     if (win.n > 0 && mn <= s_seg[win.n - 1]) {
-        A = win.A + lower_bound_smem(s_seg, win.n, mn);
+        // cur < n here, and usually s_seg[cur] >= mn already
+        const uint32_t k0 = win.cur;
+        A = win.A + (s_seg[k0] >= mn ? k0 : k0 + 1 + lower_bound_smem(s_seg + k0 + 1, win.n - k0 - 1, mn));
     } else {
         uint64_t a0 = 0;
         if (lane == 0) a0 = lower_bound_col(p.col, wend, c.pend, mn);
@@ -216,28 +211,31 @@ __device__ __forceinline__ void n2v_tile_bias(const WalkParams& p, const Row& r,
         }
         win.A = A;
         win.n = n;
+        win.cur = 0;
     }
     const bool to_end = win.A + win.n == c.pend;
     const uint32_t last = win.n > 0 ? s_seg[win.n - 1] : 0u;
     const uint32_t off = (uint32_t)(A - win.A);   // entries below A are all < mn
-    if (to_end || mx <= last) {
-        // All of N(prev) within [mn, mx] is staged: s_seg[off, e).  When it is
-        // short (a hub after a low-degree vertex), each lane compares its ids
-        // with every entry instead of searching for each id.
-        const uint32_t e = off + upper_bound_smem(s_seg + off, win.n - off, mx);
-        if (e - off <= N2V_SCAN) {
-            uint32_t hit = 0u;   // bit j: uu[j] is in N(prev)
-            for (uint32_t i = off; i < e; ++i) {
-                const uint32_t y = s_seg[i];
-                hit |= (uu[0] == y ? 1u : 0u) | (uu[1] == y ? 2u : 0u) | (uu[2] == y ? 4u : 0u) |
-                       (uu[3] == y ? 8u : 0u);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (valid[j]) b[j] *= uu[j] == c.prev ? p.m0 : ((hit >> j) & 1u) ? p.m1 : p.m2;
-            return;
+    if ((to_end || mx <= last) &&
+        !(off + N2V_SCAN < win.n && s_seg[off + N2V_SCAN] <= mx)) {
+        // All of N(prev) within [mn, mx] is staged, at most N2V_SCAN entries
+        // from off (a hub after a low-degree vertex, say): each lane compares
+        // its ids with every entry (a merge step) instead of searching.
+        uint32_t hit = 0u;   // bit j: uu[j] is in N(prev)
+        uint32_t i = off;
+        for (; i < win.n; ++i) {
+            const uint32_t y = s_seg[i];
+            if (y > mx) break;
+            hit |= (uu[0] == y ? 1u : 0u) | (uu[1] == y ? 2u : 0u) | (uu[2] == y ? 4u : 0u) |
+                   (uu[3] == y ? 8u : 0u);
         }
+        win.cur = i;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (valid[j]) b[j] *= uu[j] == c.prev ? p.m0 : ((hit >> j) & 1u) ? p.m1 : p.m2;
+        return;
     }
+    win.cur = off;
     // One id per iteration, rotating uu/b/valid so that the body (and its
     // searches) is emitted once: the kernel's code has to fit the
     // instruction cache.
@@ -563,7 +561,7 @@ __device__ __forceinline__ bool walk_pick(const WalkParams& p, const Row& row, c
         *idx = (uint32_t)scale_draw(r, row.d);   // b = 1: S[i] = i + 1, the pick is x itself
         return true;
     }
-    N2vWin win = {c.pbeg, 0};
+    N2vWin win = {c.pbeg, 0, 0};
     // node2vec round biases pass through the chunk table's space: it is free
     // in a one-round step, and in pass 2 once the chunk has been found
     static_assert(ROUND <= 2 * CHUNK_SLOTS, "a round must fit the chunk table");
@@ -623,7 +621,7 @@ __device__ __forceinline__ bool walk_pick(const WalkParams& p, const Row& row, c
     }
     uint64_t before = ch > 0 ? s_chunk[ch - 1] : 0;
     __syncwarp();
-    win = {c.pbeg, 0};   // pass 2 restarts the node2vec window at the chunk's first tile
+    win = {c.pbeg, 0, 0};   // pass 2 restarts the node2vec window at the chunk's first tile
     // Pass 2: rescan that chunk's rounds.
     const uint32_t r_end = min(nrounds, (ch + 1) * G);
     for (uint32_t rd = ch * G; rd < r_end; ++rd) {
