@@ -109,15 +109,16 @@ __device__ __forceinline__ void group_bias(const WalkParams& p, const Row& r, ui
 // A = lower_bound(N(prev), smallest id of the tile) and holds up to SEG_SMEM
 // entries.  Tiles come in ascending id order, so the next tile's A is usually
 // found inside the staged window (most often at the cursor left by the last
-// tile) with no global access; the window is reloaded from A (coalesced reads
-// in groups of SEG_GROUP) only when it does not cover the tile's ids.  When at
-// most N2V_SCAN staged entries fall in the tile's id range, each lane compares
-// its ids with them; otherwise each id is binary-searched in the window, and
-// ids beyond the window's last entry in the rest of N(prev) in global memory.
-// All lanes call this together, for tiles in ascending order; win = {pbeg, 0,
-// 0} restarts.
+// tile) with no global access; the window is reloaded from A (SEG_GROUP
+// entries, then as many as their density says the tile needs) only when it
+// does not cover the tile's ids.  When at most N2V_SCAN staged entries fall in
+// the tile's id range, each lane compares its ids with them; otherwise each id
+// is searched in the window (a lane's first id by bisection, its later ones by
+// galloping on from the last hit), and ids beyond the window's last entry in
+// the rest of N(prev) in global memory.  All lanes call this together, for
+// tiles in ascending order; win = {pbeg, 0, 0} restarts.
 constexpr uint32_t SEG_SMEM = 1024;
-constexpr uint32_t SEG_GROUP = 256;   // entries staged per coalesced step
+constexpr uint32_t SEG_GROUP = 256;   // entries staged in the first coalesced step
 constexpr uint32_t N2V_SCAN = 32;     // N(prev) entries in a tile's id range compared directly
 
 struct N2vWin {
@@ -198,16 +199,18 @@ __device__ __forceinline__ void n2v_tile_bias(const WalkParams& p, const Row& r,
         // buffer cannot reach that id.
         const uint64_t left = c.pend - A;
         const uint32_t cap = left < SEG_SMEM ? (uint32_t)left : SEG_SMEM;
-        uint32_t n = 0;
+        uint32_t n = 0, g = min(cap, SEG_GROUP);
         while (true) {
-            const uint32_t g = min(cap - n, SEG_GROUP);
             for (uint32_t i = lane; i < g; i += 32) s_seg[n + i] = __ldg(p.col + A + n + i);
             n += g;
             __syncwarp();
             if (n == cap) break;
             const uint32_t hi = s_seg[n - 1];
             if (hi >= mx) break;
-            if ((float)(mx - hi) * (float)n > (float)(cap - n) * (float)max(hi - s_seg[0], 1u)) break;
+            const float need = __fdividef((float)(mx - hi) * (float)n, (float)max(hi - s_seg[0], 1u));
+            if (need > (float)(cap - n)) break;
+            // the estimate, with a margin, in one more step
+            g = min(cap - n, ((uint32_t)(need * 1.25f) + 32u) & ~31u);
         }
         win.A = A;
         win.n = n;
@@ -238,7 +241,9 @@ __device__ __forceinline__ void n2v_tile_bias(const WalkParams& p, const Row& r,
     win.cur = off;
     // One id per iteration, rotating uu/b/valid so that the body (and its
     // searches) is emitted once: the kernel's code has to fit the
-    // instruction cache.
+    // instruction cache.  A lane's ids ascend, so after a binary search for
+    // its first id each later search gallops on from where the last ended.
+    uint32_t pos = ~0u;   // none yet
     uint32_t vm = (valid[0] ? 1u : 0u) | (valid[1] ? 2u : 0u) | (valid[2] ? 4u : 0u) | (valid[3] ? 8u : 0u);
 #pragma unroll 1
     for (int j = 0; j < 4; ++j) {
@@ -250,8 +255,16 @@ __device__ __forceinline__ void n2v_tile_bias(const WalkParams& p, const Row& r,
             } else {
                 bool in;
                 if (to_end || u <= last) {
-                    const uint32_t at = off + lower_bound_smem(s_seg + off, win.n - off, u);
+                    uint32_t lo = off, hi = win.n;
+                    if (pos != ~0u) {
+                        lo = pos;
+                        uint32_t bound = 1;
+                        while (lo + bound - 1 < win.n && s_seg[lo + bound - 1] < u) { lo += bound; bound <<= 1; }
+                        hi = min(lo + bound - 1, win.n);
+                    }
+                    const uint32_t at = lo + lower_bound_smem(s_seg + lo, hi - lo, u);
                     in = at < win.n && s_seg[at] == u;
+                    pos = at;
                 } else {
                     const uint64_t at = lower_bound_col(p.col, win.A + win.n, c.pend, u);
                     in = at < c.pend && __ldg(p.col + at) == u;
