@@ -135,6 +135,29 @@ def walk_bytes(torch, off_t, path):
     return n_trans, 16 * n_trans + 4 * deg_sum + 4 * n_trans + 4 * n + 4 * n * row + 16 * n_dead
 
 
+def node2vec_bytes(torch, off_t, path):
+    """Algorithmic bytes of one node2vec walk launch: per transition a->b,
+    16 (offsets of a) + 8*deg(a) (columns and weights of the row, both needed
+    for the biases) and, from the second step on, 16 (offsets of the previous
+    vertex t) + 4*deg(t) (its sorted list, read once by the merge that tests
+    membership); per walker 4 (start) and 4*(L+1) (its path row); per dead
+    end 16 (offsets)."""
+    p = path.to(torch.int64) & 0xFFFFFFFF
+    a, b = p[:, :-1], p[:, 1:]
+    real = b != 0xFFFFFFFF
+    deg = (off_t[1:] - off_t[:-1])
+    n_trans = int(real.sum())
+    deg_sum = int(deg[a[real]].sum())
+    with_prev = real[:, 1:]                    # transitions taken at step t >= 1
+    prev = p[:, :-2][with_prev]
+    n_prev = int(with_prev.sum())
+    prev_sum = int(deg[prev].sum())
+    n_dead = int(((~real) & (a != 0xFFFFFFFF)).sum())
+    n, row = path.shape
+    return n_trans, (16 * n_trans + 8 * deg_sum + 16 * n_prev + 4 * prev_sum
+                     + 4 * n + 4 * n * row + 16 * n_dead)
+
+
 def walk_workload(args):
     from paper_2009_09103_gb300 import inputs
     if args.workload == "node2vec":
@@ -186,7 +209,7 @@ def run_walk_bench(args, rank, world):
         step()
     torch.cuda.synchronize()
     off_t = torch.from_numpy(g.off.astype(np.int64)).to(dev)
-    n_trans, alg_bytes = walk_bytes(torch, off_t, path)
+    n_trans, alg_bytes = (node2vec_bytes if wl.bias == "node2vec" else walk_bytes)(torch, off_t, path)
 
     clocks = Clocks(dev.index)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))

@@ -25,3 +25,55 @@ def test_reference_arm_two_ranks_gloo():
     assert out["impl"] == "reference" and out["n_gpus"] == 2
     assert out["cpu_baseline"]["kind"] == "oracle" and out["cpu_baseline"]["cores"] == (os.cpu_count() or 1)
     assert out["value"] > 0 and out["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def _bench_module():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_walk_byte_models_match_a_direct_count():
+    """The roofline numerators, counted transition by transition."""
+    torch = pytest.importorskip("torch")
+    import numpy as np
+    bench = _bench_module()
+    NONE = 0xFFFFFFFF
+    rng = np.random.default_rng(3)
+    deg = rng.integers(0, 9, size=40)
+    off = np.zeros(41, dtype=np.int64)
+    off[1:] = np.cumsum(deg)
+    n, L = 30, 7
+    path = np.full((n, L + 1), NONE, dtype=np.uint32)
+    for i in range(n):
+        v = int(rng.integers(0, 40))
+        path[i, 0] = v
+        for t in range(L):
+            if deg[v] == 0 or rng.random() < 0.1:
+                break
+            v = int(rng.integers(0, 40))
+            path[i, t + 1] = v
+    ew = n2v = 0
+    n_trans = 0
+    for i in range(n):
+        ew += 4 + 4 * (L + 1)
+        n2v += 4 + 4 * (L + 1)
+        for t in range(L):
+            a, b = path[i, t], path[i, t + 1]
+            if a == NONE:
+                break
+            if b == NONE:
+                ew += 16
+                n2v += 16
+                break
+            n_trans += 1
+            ew += 16 + 4 * deg[a] + 4
+            n2v += 16 + 8 * deg[a]
+            if t >= 1:
+                n2v += 16 + 4 * deg[path[i, t - 1]]
+    off_t = torch.from_numpy(off)
+    path_t = torch.from_numpy(path.view(np.int32))
+    assert bench.walk_bytes(torch, off_t, path_t) == (n_trans, ew)
+    assert bench.node2vec_bytes(torch, off_t, path_t) == (n_trans, n2v)
