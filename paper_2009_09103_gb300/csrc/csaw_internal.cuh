@@ -110,16 +110,51 @@ __device__ __forceinline__ uint64_t philox_draw(uint32_t k0, uint32_t k1, uint32
     uint32_t c0 = attempt, c1 = vertex, c2 = layer, c3 = instance;
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
-        const uint32_t lo0 = 0xD2511F53u * c0;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
-        const uint32_t lo1 = 0xCD9E8D57u * c2;
-        c0 = hi1 ^ c1 ^ k0;
-        c1 = lo1;
-        c2 = hi0 ^ c3 ^ k1;
-        c3 = lo0;
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c0;   // one wide multiply: both halves
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        c0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        c1 = (uint32_t)p1;
+        c2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        c3 = (uint32_t)p0;
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
+    }
+    return ((uint64_t)c1 << 32) | (uint64_t)c0;
+}
+
+// The ten round keys of one seed, computed once on the host: round r uses
+// (k0 + r * 0x9E3779B9, k1 + r * 0xBB67AE85) mod 2^32.  Passed in a kernel's
+// parameters, each is a constant operand of its round.
+struct PhiloxKeys {
+    uint32_t k0[10], k1[10];
+};
+
+inline PhiloxKeys philox_round_keys(uint64_t seed)
+{
+    PhiloxKeys K;
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        K.k0[r] = k0;
+        K.k1[r] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return K;
+}
+
+// philox_draw with precomputed round keys (same output).
+__device__ __forceinline__ uint64_t philox_draw(const PhiloxKeys& K, uint32_t attempt, uint32_t vertex,
+                                                uint32_t layer, uint32_t instance)
+{
+    uint32_t c0 = attempt, c1 = vertex, c2 = layer, c3 = instance;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        c0 = (uint32_t)(p1 >> 32) ^ c1 ^ K.k0[r];
+        c1 = (uint32_t)p1;
+        c2 = (uint32_t)(p0 >> 32) ^ c3 ^ K.k1[r];
+        c3 = (uint32_t)p0;
     }
     return ((uint64_t)c1 << 32) | (uint64_t)c0;
 }

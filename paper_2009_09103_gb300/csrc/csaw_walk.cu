@@ -47,7 +47,7 @@ struct WalkParams {
     uint64_t n;
     uint32_t L;
     uint32_t* __restrict__ path;
-    uint32_t k0, k1;
+    PhiloxKeys keys;                      // round keys of the seed
     uint32_t m0, m1, m2;
     unsigned long long* next_walker;
     const uint64_t* __restrict__ cdfw;   // cached edge-weight prefix sums (node2vec fast path) or null
@@ -574,6 +574,28 @@ __device__ __forceinline__ bool walk_pick(const WalkParams& p, const Row& row, c
         *idx = (uint32_t)scale_draw(r, row.d);   // b = 1: S[i] = i + 1, the pick is x itself
         return true;
     }
+    if constexpr (KIND != CSAW_BIAS_NODE2VEC) {
+        if (row.span <= TILE) {
+            // One tile: lane l holds positions 4l .. 4l+3; its inclusive
+            // prefix over lanes gives S at 4l+3, the total is lane 31's.
+            uint32_t b[4];
+            group_bias<KIND>(p, row, 4u * lane, c, b);
+            const T sl = (T)b[0] + b[1] + b[2] + b[3];
+            const T incl = A::scan(sl, lane);
+            const uint64_t total = (uint64_t)__shfl_sync(CSAW_FULL_MASK, incl, 31);
+            if (total == 0) return false;
+            const uint64_t x = scale_draw(r, total);
+            const uint32_t hit = __ballot_sync(CSAW_FULL_MASK, (uint64_t)incl > x);
+            const int L = __ffs(hit) - 1;
+            const uint64_t e0 = (uint64_t)(incl - sl) + b[0];
+            const uint64_t e1 = e0 + b[1];
+            const uint64_t e2 = e1 + b[2];
+            uint32_t j = e0 > x ? 0u : (e1 > x ? 1u : (e2 > x ? 2u : 3u));
+            j = __shfl_sync(CSAW_FULL_MASK, j, L);
+            *idx = 4u * (uint32_t)L + j - row.lo;
+            return true;
+        }
+    }
     N2vWin win = {c.pbeg, 0, 0};
     // node2vec round biases pass through the chunk table's space: it is free
     // in a one-round step, and in pass 2 once the chunk has been found
@@ -711,7 +733,7 @@ __global__ void __launch_bounds__(WALK_THREADS, (walk_min_blocks<KIND, WIDE>()))
             row.d = (uint32_t)(row.end - row.beg);
             row.span = (uint32_t)(row.end - row.abeg);
             row.lo = (uint32_t)(row.beg - row.abeg);
-            const uint64_t r = philox_draw(p.k0, p.k1, 0u, cur, s, (uint32_t)wk);
+            const uint64_t r = philox_draw(p.keys, 0u, cur, s, (uint32_t)wk);
             uint32_t idx;
             if (!walk_pick<KIND, WIDE>(p, row, c, r, s_chunk, s_seg, s_jpos, s_jw, lane, &idx)) break;
             const uint32_t nxt = __ldg(p.col + row.beg + idx);
@@ -793,7 +815,7 @@ struct WalkCdfParams {
     uint64_t n;
     uint32_t L;
     uint32_t* __restrict__ path;
-    uint32_t k0, k1;
+    PhiloxKeys keys;
 };
 
 template <bool UNIFORM>
@@ -814,7 +836,7 @@ __global__ void __launch_bounds__(256) walk_cached_kernel(WalkCdfParams p)
             const uint64_t beg = __ldg(p.off + cur);
             const uint64_t end = __ldg(p.off + cur + 1);
             if (beg == end) break;
-            const uint64_t r = philox_draw(p.k0, p.k1, 0u, cur, s, (uint32_t)wk);
+            const uint64_t r = philox_draw(p.keys, 0u, cur, s, (uint32_t)wk);
             uint64_t i;
             if constexpr (UNIFORM) {
                 i = scale_draw(r, end - beg);
@@ -843,7 +865,7 @@ csaw_status launch_walk_cached(const csaw_graph* g, int kind, const uint32_t* st
     WalkCdfParams p;
     p.off = g->off; p.col = g->col; p.cdf = kind == CSAW_BIAS_UNIFORM ? nullptr : g->cdf[kind];
     p.V = g->V; p.starts = starts; p.n = n; p.L = length; p.path = path;
-    p.k0 = (uint32_t)rng_seed; p.k1 = (uint32_t)(rng_seed >> 32);
+    p.keys = philox_round_keys(rng_seed);
     static std::atomic<int> cached[2];
     const int u = kind == CSAW_BIAS_UNIFORM ? 1 : 0;
     int per_sm = cached[u].load(std::memory_order_acquire);
@@ -928,7 +950,7 @@ extern "C" csaw_status csaw_walk(csaw_graph* g, const uint32_t* starts, uint64_t
         WalkParams p;
         p.off = g->off; p.col = g->col; p.w = g->w; p.deg = g->deg; p.V = g->V;
         p.starts = d_starts; p.n = n_walkers; p.L = length; p.path = d_path;
-        p.k0 = (uint32_t)rng_seed; p.k1 = (uint32_t)(rng_seed >> 32);
+        p.keys = philox_round_keys(rng_seed);
         p.m0 = bias->n2v_mult[0]; p.m1 = bias->n2v_mult[1]; p.m2 = bias->n2v_mult[2];
         p.next_walker = (unsigned long long*)counter;
         p.cdfw = g->cdf[CSAW_BIAS_EDGE_WEIGHT];
