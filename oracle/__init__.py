@@ -64,6 +64,8 @@ def _load():
         lib.ref_sample.argtypes = [P, P, P, u32, P, P, u32, u32, P, i32, P, u64, u32,
                                    P, P, P, P]
         lib.ref_sample.restype = i32
+        lib.ref_mdrw.argtypes = [P, P, u32, P, P, u64, u32, u32, u64, P, P]
+        lib.ref_mdrw.restype = i32
         lib.ref_free.argtypes = [P]
         lib.ref_free.restype = None
         _lib = lib
@@ -144,6 +146,25 @@ def walk(g, starts, length: int, bias: str, seed: int, mult=(1, 1, 1), walker_id
     if rc != 0:
         raise ValueError(f"oracle walk failed ({rc})")
     return path
+
+
+def mdrw(g, pools, steps: int, seed: int, instance_ids=None):
+    """Multi-dimensional random walk.  pools: uint32[n][pool_size] initial
+    pools.  Returns (src, dst), each uint32[n][steps]; instance_ids (uint64)
+    gives the RNG instance of each row when only a subset is run."""
+    lib = _load()
+    off, col, _ = _graph_args(g)
+    pl = np.ascontiguousarray(pools, dtype=np.uint32)
+    if pl.ndim != 2 or pl.shape[1] == 0:
+        raise ValueError("pools must be [n][pool_size] with pool_size >= 1")
+    ids = np.ascontiguousarray(instance_ids, dtype=np.uint64) if instance_ids is not None else None
+    n, m = pl.shape
+    src = np.empty((n, steps), dtype=np.uint32)
+    dst = np.empty((n, steps), dtype=np.uint32)
+    rc = lib.ref_mdrw(_p(off), _p(col), len(off) - 1, _p(pl), _p(ids), n, m, steps, seed, _p(src), _p(dst))
+    if rc != 0:
+        raise ValueError(f"oracle mdrw failed ({rc})")
+    return src, dst
 
 
 def sample(g, seeds, inst_offsets, fanout, bias: str, seed: int, attempt_cap: int = ATTEMPT_CAP):

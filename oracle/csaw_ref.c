@@ -468,4 +468,67 @@ int ref_sample(const uint64_t* off, const uint32_t* col, const uint32_t* w, uint
     return rc;
 }
 
+/* Multi-dimensional random walk (frontier sampling), Sec. II-A, written with
+ * the API of Sec. III-C as the case study of Sec. III-D applies it (Figs. 3
+ * and 4).  Each instance keeps a pool of pool_size vertices (slot order).
+ * At step s:
+ *   VertexBias (Eq. 2): the bias of a pool vertex is its degree; a slot whose
+ *     entry is not a vertex (>= V, e.g. NONE) has bias 0.
+ *   Select: one slot by inverse transform sampling over the pool's prefix sums
+ *     in slot order, draw counter {0, NONE, s, instance}.
+ *   EdgeBias = 1 (Sec. III-D): one neighbour u of the chosen v, S[t] = t + 1,
+ *     draw counter {0, v, s, instance} (the counter of a walk step at v).
+ *   Update (Eq. 4): u replaces v in its slot; (v, u) is the step's sampled
+ *     edge.
+ * A pool whose biases sum to 0 stops the instance; the rest of its rows of
+ * src and dst is NONE.  instance_ids (may be NULL) gives each instance's RNG
+ * index when only a subset is run. */
+int ref_mdrw(const uint64_t* off, const uint32_t* col, uint32_t V, const uint32_t* pools,
+             const uint64_t* instance_ids, uint64_t n, uint32_t pool_size, uint32_t steps,
+             uint64_t seed, uint32_t* src, uint32_t* dst)
+{
+    if (pool_size == 0) return REF_ERR_INVALID;
+    uint32_t maxd = 0;
+    for (uint32_t v = 0; v < V; ++v) {
+        uint64_t d = off[v + 1] - off[v];
+        if (d > maxd) maxd = (uint32_t)d;
+    }
+    uint32_t* pool = (uint32_t*)malloc(sizeof(uint32_t) * pool_size);
+    uint64_t* S = (uint64_t*)malloc(sizeof(uint64_t) * pool_size);
+    uint64_t* Sn = (uint64_t*)malloc(sizeof(uint64_t) * (maxd ? maxd : 1));
+    if (!pool || !S || !Sn) { free(pool); free(S); free(Sn); return REF_ERR_NOMEM; }
+    for (uint64_t i = 0; i < n; ++i) {
+        uint32_t inst = instance_ids ? (uint32_t)instance_ids[i] : (uint32_t)i;
+        uint32_t* srow = src + i * (uint64_t)steps;
+        uint32_t* drow = dst + i * (uint64_t)steps;
+        memcpy(pool, pools + i * (uint64_t)pool_size, sizeof(uint32_t) * pool_size);
+        uint32_t s = 0;
+        for (; s < steps; ++s) {
+            /* VertexBias and the pool's prefix sums */
+            uint64_t run = 0;
+            for (uint32_t j = 0; j < pool_size; ++j) {
+                uint32_t v = pool[j];
+                run += v < V ? off[v + 1] - off[v] : 0;
+                S[j] = run;
+            }
+            if (run == 0) break;
+            uint64_t x = ref_scale(ref_draw(seed, 0, REF_NONE, s, inst), run);
+            uint32_t slot = upper_bound_u64(S, pool_size, x);
+            uint32_t v = pool[slot];
+            /* EdgeBias = 1 over N(v) */
+            uint32_t d = (uint32_t)(off[v + 1] - off[v]);
+            for (uint32_t t = 0; t < d; ++t) Sn[t] = (uint64_t)t + 1;
+            uint64_t y = ref_scale(ref_draw(seed, 0, v, s, inst), d);
+            uint32_t u = col[off[v] + upper_bound_u64(Sn, d, y)];
+            /* Update */
+            pool[slot] = u;
+            srow[s] = v;
+            drow[s] = u;
+        }
+        for (; s < steps; ++s) { srow[s] = REF_NONE; drow[s] = REF_NONE; }
+    }
+    free(pool); free(S); free(Sn);
+    return REF_OK;
+}
+
 void ref_free(void* p) { free(p); }

@@ -42,6 +42,12 @@ MUTATIONS = {
     # Update: visited filter dropped
     "no_visited_filter": ("if (!in_sorted(visited, nvis, cand[j])) cand[nn++] = cand[j];",
                           "cand[nn++] = cand[j];"),
+    # multi-dimensional random walk: VertexBias not the degree, Update
+    # dropped, neighbour draw keyed by the slot instead of the vertex
+    "mdrw_vertex_bias_uniform": ("run += v < V ? off[v + 1] - off[v] : 0;", "run += v < V ? 1 : 0;"),
+    "mdrw_no_update": ("            pool[slot] = u;\n", ""),
+    "mdrw_neighbour_key": ("uint64_t y = ref_scale(ref_draw(seed, 0, v, s, inst), d);",
+                           "uint64_t y = ref_scale(ref_draw(seed, 0, slot, s, inst), d);"),
     # walk key ignores the step
     "walk_key_step": ("uint64_t x = ref_scale(ref_draw(seed, 0, cur, s, inst), run);",
                       "uint64_t x = ref_scale(ref_draw(seed, 0, cur, 0, inst), run);"),

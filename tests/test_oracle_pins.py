@@ -418,3 +418,102 @@ def test_sampling_instances_are_independent():
         a = full["edge_off"][lvl * 3 + 1], full["edge_off"][lvl * 3 + 2]
         b = solo["edge_off"][lvl * 2 + 1], solo["edge_off"][lvl * 2 + 2]
         assert np.array_equal(full["dst"][a[0]:a[1]], solo["dst"][b[0]:b[1]])
+
+
+# --------------------------------------------------------------------------
+# Multi-dimensional random walk (frontier sampling, Sec. II-A; Figs. 3-4)
+
+NONE = 0xFFFFFFFF
+
+def test_mdrw_single_slot_pool_is_a_uniform_walk():
+    # With one slot the pool pick is forced and the step is a uniform walk
+    # step at the same draw counter {0, v, s, instance}.
+    g = inputs.rmat_csr(8, 8, 40, 6)
+    starts = inputs.uniform_vertices(300, g.V, 2)
+    src, dst = oracle.mdrw(g, starts[:, None], 30, 77)
+    path = oracle.walk(g, starts, 30, "uniform", 77)
+    taken = path[:, 1:] != NONE
+    assert (~taken).any() and taken.any()           # dead ends and real steps both occur
+    assert np.array_equal(src, np.where(taken, path[:, :-1], NONE))
+    assert np.array_equal(dst, path[:, 1:])
+
+
+def _degree_ladder_graph(degs):
+    """Vertices 0..len(degs)-1 with the given degrees, each joined to its own leaves."""
+    edges, nxt = [], len(degs)
+    for v, d in enumerate(degs):
+        for _ in range(d):
+            edges += [(v, nxt), (nxt, v)]
+            nxt += 1
+    return inputs.csr_from_edges(nxt, edges)
+
+
+def test_mdrw_pool_pick_follows_vertex_degree():
+    # VertexBias (Eq. 2) is the degree: the first pick from pool {0,1,2,3} with
+    # degrees 1,2,3,4 has probabilities 1:2:3:4; empty slots (NONE) never win.
+    g = _degree_ladder_graph([1, 2, 3, 4])
+    n = 40000
+    pools = np.tile(np.array([0, NONE, 1, 2, 3], dtype=np.uint32), (n, 1))
+    src, _ = oracle.mdrw(g, pools, 1, 5)
+    counts = np.bincount(src[:, 0], minlength=4)[:4]
+    assert counts.sum() == n
+    assert stats.chisquare(counts, n * np.array([1, 2, 3, 4]) / 10).pvalue > 1e-6
+
+
+def test_mdrw_neighbour_pick_is_uniform_whatever_the_weights():
+    # EdgeBias = 1 (Sec. III-D case study): the weights play no part.
+    d = 8
+    edges = [(0, j + 1) for j in range(d)] + [(j + 1, 0) for j in range(d)]
+    g = inputs.csr_from_edges(d + 1, edges, [1, 1000, 1, 1, 50, 1, 1, 7] + [1] * d)
+    n = 40000
+    _, dst = oracle.mdrw(g, np.zeros((n, 1), dtype=np.uint32), 1, 9)
+    counts = np.bincount(dst[:, 0], minlength=d + 1)[1:]
+    assert counts.sum() == n
+    assert stats.chisquare(counts).pvalue > 1e-6
+
+
+def test_mdrw_update_replaces_the_picked_vertex():
+    # Update (Eq. 4): the step's edge (v, u) is a graph edge, v is in the pool,
+    # and the next pool is the multiset with one v replaced by u.
+    g = inputs.rmat_csr(7, 8, 40, 3)
+    adj = set()
+    for v in range(g.V):
+        for u in g.col[g.off[v]:g.off[v + 1]]:
+            adj.add((v, int(u)))
+    pools = inputs.uniform_vertices(40 * 6, g.V, 8).reshape(40, 6)
+    src, dst = oracle.mdrw(g, pools, 60, 13)
+    for i in range(40):
+        pool = sorted(int(x) for x in pools[i])
+        for s in range(60):
+            v, u = int(src[i, s]), int(dst[i, s])
+            if v == NONE:
+                assert (src[i, s:] == NONE).all() and (dst[i, s:] == NONE).all()
+                assert sum(int(g.off[x + 1] - g.off[x]) for x in pool) == 0
+                break
+            assert (v, u) in adj and v in pool
+            pool.remove(v)
+            pool = sorted(pool + [u])
+
+
+def test_mdrw_stops_when_the_pool_has_no_edges():
+    g = inputs.csr_from_edges(4, [(0, 1), (1, 0)])   # 2 and 3 isolated
+    src, dst = oracle.mdrw(g, np.array([[2, 3, NONE], [2, 0, 3]], dtype=np.uint32), 5, 1)
+    assert (src[0] == NONE).all() and (dst[0] == NONE).all()
+    assert list(src[1]) == [0, 1, 0, 1, 0] and list(dst[1]) == [1, 0, 1, 0, 1]
+
+
+def test_mdrw_sampled_edges_are_uniform_in_steady_state():
+    # Frontier sampling's stationary law is proportional to the pool's degree
+    # sum, under which every directed edge is sampled with equal probability.
+    # A connected, non-bipartite, irregular graph; 4-slot pools; after burn-in
+    # the sampled edges must be uniform over E.
+    und = [(0, 1), (1, 2), (2, 0), (2, 3), (3, 4), (4, 5), (5, 3), (5, 6), (6, 0), (1, 4)]
+    edges = und + [(b, a) for a, b in und]
+    g = inputs.csr_from_edges(7, edges)
+    n, steps, burn = 3000, 120, 40
+    pools = inputs.uniform_vertices(n * 4, 7, 21).reshape(n, 4)
+    src, dst = oracle.mdrw(g, pools, steps, 3)
+    key = {e: i for i, e in enumerate(sorted(edges))}
+    s, d = src[:, burn:].ravel(), dst[:, burn:].ravel()
+    counts = np.bincount([key[(int(a), int(b))] for a, b in zip(s, d)], minlength=len(edges))
+    assert stats.chisquare(counts).pvalue > 1e-6
