@@ -544,6 +544,102 @@ def run_sample_bench(args):
 
 
 # --------------------------------------------------------------------------
+# Multi-dimensional random walk (frontier sampling), not the default line.
+
+def run_mdrw_bench(args):
+    import torch
+    from paper_2009_09103_gb300 import build, csaw, inputs
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    t0 = time.time()
+    wl = inputs.workload_mdrw_s20()
+    g = wl.graph
+    n, m = wl.pools.shape
+    log(f"[bench] mdrw graph: V={g.V} E={g.E} pools {n}x{m} built in {time.time() - t0:.1f}s")
+    G = csaw.Graph(g.off, g.col, g.w)
+    stream = torch.cuda.current_stream()
+    pools = torch.from_numpy(wl.pools.view(np.int32)).to(dev)
+    src = torch.empty((n, wl.steps), dtype=torch.int32, device=dev)
+    dst = torch.empty_like(src)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    def step():
+        csaw.mdrw(G, pools, wl.steps, wl.rng_seed, src=src, dst=dst, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    n_edges = int((src != -1).sum())
+    clocks = Clocks(dev.index)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    clocks.start()
+    for i in range(args.steps):
+        flush.fill_(i)
+        evs[i][0].record(stream)
+        step()
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    # end to end through the C ABI with pinned host buffers (copies inside the call)
+    h_pools = torch.empty((n, m), dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+    h_pools[:] = wl.pools
+    h_src = torch.empty((n, wl.steps), dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+    h_dst = torch.empty((n, wl.steps), dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+    csaw.mdrw(G, h_pools, wl.steps, wl.rng_seed, src=h_src, dst=h_dst)
+    t1 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        csaw.mdrw(G, h_pools, wl.steps, wl.rng_seed, src=h_src, dst=h_dst)
+    e2e_s = (time.perf_counter() - t1) / e2e_steps
+    same = bool(np.array_equal(h_src, src.cpu().numpy().view(np.uint32)) and
+                np.array_equal(h_dst, dst.cpu().numpy().view(np.uint32)))
+    G.close()
+    # per step: 16 (offsets of v) + 4 (the picked column) + 4 (degree of u) +
+    # 8 (the sampled edge); per instance: 4 per pool slot read
+    alg = 32 * n_edges + 4 * n * m
+    peak, peak_kind = measured_peaks()
+    achieved = alg / (ms / 1e3) / 1e9
+    res = {
+        "metric": METRIC, "value": n_edges / (ms / 1e3), "unit": "edges/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32 degrees / u64 prefix sums",
+        "data": "synthetic (seeded RMAT)",
+        "config": {"workload": f"multi-dimensional random walk: RMAT scale 20, edge factor 16, {n} instances, "
+                               f"pools of {m} vertices with edges (uniform), {wl.steps} steps; VertexBias = "
+                               "degree, EdgeBias = 1",
+                   "l2": "flushed (512 MiB write) before every timed step", "sampled_edges_per_step": n_edges},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "hbm", "kernel": "mdrw_kernel", "achieved": round(achieved, 1), "peak": peak,
+                     "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": None, "algorithmic_bytes_per_launch": alg},
+        "e2e": {"value": n_edges / e2e_s, "unit": "edges/s", "h2d_bytes_per_step": 4 * n * m,
+                "d2h_bytes_per_step": 8 * n * wl.steps, "matches_device_run": same},
+    }
+    if clk:
+        res["clocks"] = clk
+    if args.cpu_baseline_seconds > 0:
+        import oracle
+        oracle.build()
+        done, used, t_used = 0, 0, 0.0
+        for i in np.linspace(0, n - 1, n).astype(np.int64):
+            t = time.perf_counter()
+            rs, _ = oracle.mdrw(g, wl.pools[i:i + 1], wl.steps, wl.rng_seed,
+                                instance_ids=np.array([i], dtype=np.uint64))
+            t_used += time.perf_counter() - t
+            done += int((rs != 0xFFFFFFFF).sum())
+            used += 1
+            if t_used > args.cpu_baseline_seconds:
+                break
+        res["cpu_baseline"] = {"value": done / t_used, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                               "sample": f"{used} instances in order, all {wl.steps} steps, {t_used:.1f} s"}
+    return res
+
+
+# --------------------------------------------------------------------------
 # Serving (not the default line): open-loop Poisson arrivals of a 50/50 mix of
 # sampling and walk requests into csaw_server, against the same requests run
 # one after another with plain calls.
@@ -695,7 +791,7 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=None,
                     help="--impl reference: oracle seconds per step (default: about a minute in all)")
     ap.add_argument("--workload", default="walk",
-                    choices=["walk", "node2vec", "sample_s12", "batched_s24", "serve"])
+                    choices=["walk", "node2vec", "sample_s12", "batched_s24", "serve", "mdrw"])
     ap.add_argument("--autotune", action="store_true", help="sampling workloads: autotune first")
     ap.add_argument("--no-variant", action="store_true",
                     help="walks: skip the cached-array variant measured after the main line")
@@ -713,8 +809,9 @@ def main():
     if args.scale is None:
         args.scale = {"walk": 20, "node2vec": 22}.get(args.workload)
     rank, world, local = dist_env()
-    if args.workload in ("sample_s12", "batched_s24", "serve"):
-        res = run_sample_bench(args) if args.workload != "serve" else run_serve_bench(args)
+    if args.workload in ("sample_s12", "batched_s24", "serve", "mdrw"):
+        res = (run_serve_bench(args) if args.workload == "serve" else
+               run_mdrw_bench(args) if args.workload == "mdrw" else run_sample_bench(args))
         print(json.dumps(res), flush=True)
         return
 

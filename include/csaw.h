@@ -163,6 +163,36 @@ csaw_status csaw_walk(csaw_graph* g, const uint32_t* starts, uint64_t n_walkers,
                       const csaw_bias* bias, uint64_t rng_seed, uint32_t* path, int mem_kind,
                       void* stream);
 
+/* Multi-dimensional random walk, or frontier sampling (Sec. II-A), as the
+ * API of Sec. III-C expresses it in the case study of Sec. III-D (Figs. 3-4):
+ * each instance keeps a pool of pool_size vertices, and every step
+ *   1. selects one pool slot with probability proportional to its vertex's
+ *      degree (VertexBias, Eq. 2), by inverse transform sampling over the
+ *      pool's prefix sums in slot order;
+ *   2. selects one neighbour u of that vertex v uniformly (EdgeBias = 1);
+ *   3. puts u in v's slot (Update, Eq. 4) and emits the sampled edge (v, u).
+ *   pools      uint32[n_instances][pool_size] initial pools, row-major; an
+ *              entry >= n_vertices (e.g. CSAW_NONE) is an empty slot (bias 0)
+ *   pool_size  1 .. CSAW_MDRW_MAX_POOL
+ *   steps      steps per instance
+ *   src, dst   uint32[n_instances][steps] row-major outputs: the edge of step s
+ *              of instance i is (src[i][s], dst[i][s]).  An instance whose
+ *              pool degrees sum to zero stops; the rest of its rows are
+ *              CSAW_NONE.
+ * The pool draw of instance i at step s uses attempt 0, vertex = CSAW_NONE,
+ * layer = s, instance = i; the neighbour draw uses vertex = v (the counter of
+ * a walk step at v), so a one-slot pool walks exactly like csaw_walk with
+ * uniform bias.  Edge weights are not used.  With host memory the call
+ * copies in, runs and copies out before it returns; with device memory it is
+ * queued on `stream`.  The pools buffer is only read.  Errors:
+ * CSAW_ERR_INVALID (NULL graph or buffers, pool_size out of range,
+ * n_instances >= 2^32), CSAW_ERR_NOMEM, CSAW_ERR_CUDA. */
+#define CSAW_MDRW_MAX_POOL 65536u
+
+csaw_status csaw_mdrw(csaw_graph* g, const uint32_t* pools, uint64_t n_instances, uint32_t pool_size,
+                      uint32_t steps, uint64_t rng_seed, uint32_t* src, uint32_t* dst, int mem_kind,
+                      void* stream);
+
 /* ---------------------------------------------------------------- sampling */
 
 /* Layered biased neighbour sampling over many independent instances

@@ -106,6 +106,7 @@ def lib():
         L.csaw_graph_destroy.argtypes = [P]
         L.csaw_graph_get_info.argtypes = [P, ctypes.POINTER(GraphInfo)]
         L.csaw_walk.argtypes = [P, P, u64, u32, ctypes.POINTER(Bias), u64, P, i32, P]
+        L.csaw_mdrw.argtypes = [P, P, u64, u32, u32, u64, P, P, i32, P]
         L.csaw_graph_build_cdf.argtypes = [P, ctypes.c_int32, P]
         L.csaw_graph_drop_cdf.argtypes = [P, ctypes.c_int32]
         if hasattr(L, "csaw_sample"):
@@ -259,6 +260,38 @@ def walk(g: Graph, starts, length: int, bias="edge_weight", seed: int = 0, mult=
     _check(L.csaw_walk(g.handle, _ptr(starts), n, length, ctypes.byref(b), seed, _ptr(path),
                        MEM_HOST, st))
     return path
+
+
+def mdrw(g: Graph, pools, steps: int, seed: int = 0, src=None, dst=None, stream=None):
+    """csaw_mdrw (multi-dimensional random walk).  pools is [n_instances,
+    pool_size]: a torch CUDA int32 tensor (device call, asynchronous on
+    `stream`, returns torch int32 tensors) or a numpy array (host call, returns
+    numpy uint32).  Returns (src, dst), each [n_instances, steps]."""
+    L = lib()
+    if _is_torch(pools):
+        import torch
+        if pools.dim() != 2:
+            raise ValueError("pools must be [n_instances, pool_size]")
+        pools = pools.contiguous()
+        n, m = pools.shape
+        if src is None:
+            src = torch.empty((n, steps), dtype=torch.int32, device=pools.device)
+        if dst is None:
+            dst = torch.empty((n, steps), dtype=torch.int32, device=pools.device)
+        _check(L.csaw_mdrw(g.handle, _ptr(pools), n, m, steps, seed, _ptr(src), _ptr(dst),
+                           MEM_DEVICE, _stream_handle(stream)))
+        return src, dst
+    pools = np.ascontiguousarray(pools, dtype=np.uint32)
+    if pools.ndim != 2:
+        raise ValueError("pools must be [n_instances, pool_size]")
+    n, m = pools.shape
+    if src is None:
+        src = np.empty((n, steps), dtype=np.uint32)
+    if dst is None:
+        dst = np.empty((n, steps), dtype=np.uint32)
+    st = _stream_handle(stream) if stream is not None else None
+    _check(L.csaw_mdrw(g.handle, _ptr(pools), n, m, steps, seed, _ptr(src), _ptr(dst), MEM_HOST, st))
+    return src, dst
 
 
 @dataclass

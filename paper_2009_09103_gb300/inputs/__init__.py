@@ -200,6 +200,26 @@ def workload_node2vec_s22(graph_seed: int = 22) -> WalkWorkload:
     return WalkWorkload(g, starts, 40, "node2vec", (1, 2, 4), 3)
 
 
+@dataclass
+class MdrwWorkload:
+    graph: CSRGraph
+    pools: np.ndarray     # uint32[n_instances][pool_size]
+    steps: int
+    rng_seed: int
+
+
+def workload_mdrw_s20(graph_seed: int = 20, n_inst: int = 2000, pool_size: int = 2000,
+                      steps: int = 2000) -> MdrwWorkload:
+    """Multi-dimensional random walk on the weighted-walk graph (RMAT s20 ef16):
+    2000 instances, each a pool of 2000 vertices drawn uniformly among those
+    with an edge (the frontier size of the paper's evaluation, Sec. VI), 2000
+    steps; Philox seed 5."""
+    g = rmat_csr(20, 16, 255, graph_seed)
+    live = np.flatnonzero(np.diff(g.off) > 0).astype(np.uint32)
+    idx = uniform_vertices(n_inst * pool_size, len(live), graph_seed, stream=5)
+    return MdrwWorkload(g, live[idx].reshape(n_inst, pool_size), steps, 5)
+
+
 def workload_batched_s24(graph_seed: int = 24, n_inst: int = 4096) -> SampleWorkload:
     """RMAT s24 ef16; 4096 instances of log-uniform [64, 8192) distinct seeds;
     depth 2, fanout [25, 10]; neighbour-degree bias."""
