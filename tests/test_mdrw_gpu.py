@@ -41,7 +41,7 @@ def run_both(csaw, g, pools, steps, seed):
 
 
 @pytest.mark.parametrize("gname", ["triangle_pendant_isolated", "rmat_s8", "rmat_s12"])
-@pytest.mark.parametrize("pool_size", [1, 3, 32, 33, 100, 2000])
+@pytest.mark.parametrize("pool_size", [1, 3, 32, 33, 100, 2000, 2048, 2049])
 def test_mdrw_bit_exact_small(csaw, gname, pool_size):
     g = graphs()[gname]
     n = 64 if pool_size >= 1000 else 200
