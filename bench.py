@@ -603,6 +603,7 @@ def run_mdrw_bench(args):
     alg = 32 * n_edges + 4 * n * m
     peak, peak_kind = measured_peaks()
     achieved = alg / (ms / 1e3) / 1e9
+    tr = traffic_record("csaw_mdrw.cu", "mdrw_s20")
     res = {
         "metric": METRIC, "value": n_edges / (ms / 1e3), "unit": "edges/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -615,7 +616,8 @@ def run_mdrw_bench(args):
         "gpu_launches": args.steps,
         "roofline": {"bound": "hbm", "kernel": "mdrw_kernel", "achieved": round(achieved, 1), "peak": peak,
                      "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": None, "algorithmic_bytes_per_launch": alg},
+                     "traffic": tr["traffic_bytes_per_launch"] if tr else None,
+                     "algorithmic_bytes_per_launch": alg},
         "e2e": {"value": n_edges / e2e_s, "unit": "edges/s", "h2d_bytes_per_step": 4 * n * m,
                 "d2h_bytes_per_step": 8 * n * wl.steps, "matches_device_run": same},
     }
