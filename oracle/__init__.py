@@ -61,6 +61,8 @@ def _load():
         lib.ref_select.restype = i64
         lib.ref_walk.argtypes = [P, P, P, u32, P, P, u64, u32, i32, P, u64, P]
         lib.ref_walk.restype = i32
+        lib.ref_walk_tele.argtypes = [P, P, P, u32, P, P, u64, u32, i32, P, u64, i32, u32, P]
+        lib.ref_walk_tele.restype = i32
         lib.ref_sample.argtypes = [P, P, P, u32, P, P, u32, u32, P, i32, P, u64, u32,
                                    P, P, P, P]
         lib.ref_sample.restype = i32
@@ -132,17 +134,26 @@ def select(g, v: int, k: int, bias: str, seed: int, layer: int, instance: int,
     return out[:n].copy()
 
 
-def walk(g, starts, length: int, bias: str, seed: int, mult=(1, 1, 1), walker_ids=None):
+TELEPORT = {None: 0, "restart": 1, "jump": 2}
+
+
+def walk(g, starts, length: int, bias: str, seed: int, mult=(1, 1, 1), walker_ids=None,
+         teleport=None, teleport_q32: int = 0):
     """Path matrix uint32[n][length+1]; walker_ids (uint64) gives the RNG
-    instance of each row when only a subset of walkers is run."""
+    instance of each row when only a subset of walkers is run.  teleport
+    ("restart" or "jump") with probability teleport_q32 / 2^32 per step."""
     lib = _load()
     off, col, w = _graph_args(g)
     s = _u32(starts)
     ids = np.ascontiguousarray(walker_ids, dtype=np.uint64) if walker_ids is not None else None
     m = _u32(mult)
     path = np.empty((len(s), length + 1), dtype=np.uint32)
-    rc = lib.ref_walk(_p(off), _p(col), _p(w), len(off) - 1, _p(s), _p(ids), len(s), length,
-                      BIAS[bias], _p(m), seed, _p(path))
+    if teleport is None:
+        rc = lib.ref_walk(_p(off), _p(col), _p(w), len(off) - 1, _p(s), _p(ids), len(s), length,
+                          BIAS[bias], _p(m), seed, _p(path))
+    else:
+        rc = lib.ref_walk_tele(_p(off), _p(col), _p(w), len(off) - 1, _p(s), _p(ids), len(s), length,
+                               BIAS[bias], _p(m), seed, TELEPORT[teleport], teleport_q32, _p(path))
     if rc != 0:
         raise ValueError(f"oracle walk failed ({rc})")
     return path

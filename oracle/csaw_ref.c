@@ -273,11 +273,35 @@ int64_t ref_select(const uint64_t* off, const uint32_t* col, const uint32_t* w, 
  * NODE2VEC).  path is [n][L+1] row-major; path[w][0] = start.  The draw of
  * walker w at step s is attempt 0, vertex = current vertex, layer = s,
  * instance = walker_ids ? walker_ids[w] : w.  A walker at a vertex with no
- * neighbour of positive bias stops; the rest of its row is REF_NONE.        */
-int ref_walk(const uint64_t* off, const uint32_t* col, const uint32_t* w, uint32_t V,
-             const uint32_t* starts, const uint64_t* walker_ids, uint64_t n, uint32_t L,
-             int kind, const uint32_t mult[3], uint64_t seed, uint32_t* path)
+ * neighbour of positive bias stops; the rest of its row is REF_NONE.
+ *
+ * Random walk with restart or with jump (Sec. II-A; the Update of Eq. 4 that
+ * returns a vertex other than the sampled neighbour): when tele is
+ * REF_TELE_RESTART or REF_TELE_JUMP, each step first draws attempt 1 (same
+ * vertex, layer and instance); if its upper 32 bits are below tele_q32 the
+ * step teleports instead of moving to a neighbour: to the walker's start
+ * (restart) or to vertex floor(r2 * V / 2^64) with r2 the draw of attempt 2
+ * (jump).  A walker at a vertex with no neighbour of positive bias teleports
+ * the same way instead of stopping.  After a teleport the walk has no
+ * previous vertex (node2vec's next step uses the weights alone).           */
+#define REF_TELE_NONE 0
+#define REF_TELE_RESTART 1
+#define REF_TELE_JUMP 2
+
+static uint32_t teleport_target(int tele, uint32_t start, uint32_t V, uint64_t seed, uint32_t cur,
+                                uint32_t s, uint32_t inst)
 {
+    if (tele == REF_TELE_RESTART) return start;
+    return (uint32_t)ref_scale(ref_draw(seed, 2, cur, s, inst), V);
+}
+
+int ref_walk_tele(const uint64_t* off, const uint32_t* col, const uint32_t* w, uint32_t V,
+                  const uint32_t* starts, const uint64_t* walker_ids, uint64_t n, uint32_t L,
+                  int kind, const uint32_t mult[3], uint64_t seed, int tele, uint32_t tele_q32,
+                  uint32_t* path)
+{
+    if (tele != REF_TELE_NONE && tele != REF_TELE_RESTART && tele != REF_TELE_JUMP)
+        return REF_ERR_INVALID;
     ref_graph g = { off, col, w, V };
     uint32_t maxd = 0;
     for (uint32_t v = 0; v < V; ++v) {
@@ -295,12 +319,24 @@ int ref_walk(const uint64_t* off, const uint32_t* col, const uint32_t* w, uint32
         row[0] = cur;
         uint32_t s = 0;
         for (; s < L; ++s) {
+            if (tele != REF_TELE_NONE && (uint32_t)(ref_draw(seed, 1, cur, s, inst) >> 32) < tele_q32) {
+                cur = teleport_target(tele, starts[i], V, seed, cur, s, inst);
+                prev = REF_NONE;
+                row[s + 1] = cur;
+                continue;
+            }
             uint32_t d = (uint32_t)(off[cur + 1] - off[cur]);
             int rc = edge_biases(&g, cur, kind, mult, prev, b);
             if (rc != REF_OK) { free(b); free(S); return rc; }
             uint64_t run = 0;
             for (uint32_t j = 0; j < d; ++j) { run += b[j]; S[j] = run; }
-            if (d == 0 || run == 0) break;         /* dead end */
+            if (d == 0 || run == 0) {              /* dead end */
+                if (tele == REF_TELE_NONE) break;
+                cur = teleport_target(tele, starts[i], V, seed, cur, s, inst);
+                prev = REF_NONE;
+                row[s + 1] = cur;
+                continue;
+            }
             uint64_t x = ref_scale(ref_draw(seed, 0, cur, s, inst), run);
             uint32_t j = upper_bound_u64(S, d, x);
             prev = cur;
@@ -311,6 +347,14 @@ int ref_walk(const uint64_t* off, const uint32_t* col, const uint32_t* w, uint32
     }
     free(b); free(S);
     return REF_OK;
+}
+
+int ref_walk(const uint64_t* off, const uint32_t* col, const uint32_t* w, uint32_t V,
+             const uint32_t* starts, const uint64_t* walker_ids, uint64_t n, uint32_t L,
+             int kind, const uint32_t mult[3], uint64_t seed, uint32_t* path)
+{
+    return ref_walk_tele(off, col, w, V, starts, walker_ids, n, L, kind, mult, seed, REF_TELE_NONE, 0,
+                         path);
 }
 
 /* ------------------------------------------------------------------------ */

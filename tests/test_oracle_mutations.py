@@ -48,6 +48,12 @@ MUTATIONS = {
     "mdrw_no_update": ("            pool[slot] = u;\n", ""),
     "mdrw_neighbour_key": ("uint64_t y = ref_scale(ref_draw(seed, 0, v, s, inst), d);",
                            "uint64_t y = ref_scale(ref_draw(seed, 0, slot, s, inst), d);"),
+    # walks with restart / jump: restart to the wrong vertex, dead ends that
+    # stop, a jump range one short
+    "restart_to_current": ("if (tele == REF_TELE_RESTART) return start;", "if (tele == REF_TELE_RESTART) return cur;"),
+    "teleport_dead_end_stops": ("if (tele == REF_TELE_NONE) break;", "break;"),
+    "jump_range": ("return (uint32_t)ref_scale(ref_draw(seed, 2, cur, s, inst), V);",
+                   "return (uint32_t)ref_scale(ref_draw(seed, 2, cur, s, inst), V - 1);"),
     # walk key ignores the step
     "walk_key_step": ("uint64_t x = ref_scale(ref_draw(seed, 0, cur, s, inst), run);",
                       "uint64_t x = ref_scale(ref_draw(seed, 0, cur, 0, inst), run);"),

@@ -517,3 +517,56 @@ def test_mdrw_sampled_edges_are_uniform_in_steady_state():
     s, d = src[:, burn:].ravel(), dst[:, burn:].ravel()
     counts = np.bincount([key[(int(a), int(b))] for a, b in zip(s, d)], minlength=len(edges))
     assert stats.chisquare(counts).pvalue > 1e-6
+
+
+# --------------------------------------------------------------------------
+# Random walk with restart and with jump (Sec. II-A; Update, Eq. 4)
+
+Q32_ALWAYS = 0xFFFFFFFF   # teleport probability 1 - 2^-32
+
+
+def test_teleport_with_probability_zero_is_the_plain_walk():
+    g = inputs.rmat_csr(8, 8, 40, 2)
+    deg = np.diff(g.off)
+    starts = np.flatnonzero(deg > 0).astype(np.uint32)[:200]   # no dead end is reachable from these
+    ref = oracle.walk(g, starts, 30, "edge_weight", 8)
+    for mode in ("restart", "jump"):
+        assert np.array_equal(oracle.walk(g, starts, 30, "edge_weight", 8, teleport=mode, teleport_q32=0), ref)
+
+
+def test_teleport_always_restarts_or_jumps_uniformly():
+    g = inputs.rmat_csr(6, 8, 40, 2)
+    starts = inputs.uniform_vertices(400, g.V, 1)
+    p = oracle.walk(g, starts, 25, "node2vec", 4, mult=(1, 2, 4), teleport="restart", teleport_q32=Q32_ALWAYS)
+    assert (p == starts[:, None]).all()
+    p = oracle.walk(g, starts, 200, "edge_weight", 4, teleport="jump", teleport_q32=Q32_ALWAYS)
+    assert (p < g.V).all()
+    counts = np.bincount(p[:, 1:].ravel(), minlength=g.V)
+    assert counts.sum() == 400 * 200
+    assert stats.chisquare(counts).pvalue > 1e-6
+
+
+def test_restart_walk_law_is_personalized_pagerank():
+    # With restart probability c (and a dead end that restarts), the state after
+    # enough steps follows pi = c e_s (I - (1-c) P)^-1, P the biased
+    # transition matrix with the dead end's row sent to the start.
+    und = [(0, 1, 3), (1, 2, 1), (2, 0, 2), (2, 3, 5), (3, 4, 1), (4, 2, 2), (1, 4, 4)]
+    edges = [(a, b) for a, b, _ in und] + [(b, a) for a, b, _ in und] + [(3, 5)]   # 5: dead end
+    wts = [x for *_, x in und] * 2 + [6]
+    g = inputs.csr_from_edges(6, edges, wts)
+    V, start, c = 6, 1, 0.25
+    P = np.zeros((V, V))
+    for (a, b), x in zip(edges, wts):
+        P[a, b] += x
+    P[5, start] = 1.0
+    P /= P.sum(axis=1, keepdims=True)
+    e = np.zeros(V)
+    e[start] = 1.0
+    pi = c * e @ np.linalg.inv(np.eye(V) - (1 - c) * P)
+    q32 = int(round(c * 2**32))
+    n, L = 40000, 60
+    path = oracle.walk(g, np.full(n, start, dtype=np.uint32), L, "edge_weight", 17,
+                       teleport="restart", teleport_q32=q32)
+    assert (path[:, L] < V).all()   # restart walks never stop
+    counts = np.bincount(path[:, L], minlength=V)
+    assert stats.chisquare(counts, n * pi).pvalue > 1e-6
