@@ -163,6 +163,32 @@ csaw_status csaw_walk(csaw_graph* g, const uint32_t* starts, uint64_t n_walkers,
                       const csaw_bias* bias, uint64_t rng_seed, uint32_t* path, int mem_kind,
                       void* stream);
 
+/* Random walk with restart or with jump (Sec. II-A; the Update of Eq. 4
+ * returning a vertex other than the sampled neighbour): csaw_walk with
+ * options (NULL = plain walk).  With teleport = CSAW_TELEPORT_RESTART or
+ * _JUMP, every step of walker w at vertex v first draws attempt 1 (vertex v,
+ * layer s, instance w); if the draw's upper 32 bits are below teleport_q32
+ * (a per-step probability of teleport_q32 / 2^32) the walker goes to its
+ * start vertex (restart) or to vertex floor(r2 * n_vertices / 2^64), r2 the
+ * draw of attempt 2 (jump), instead of to a neighbour.  A walker at a vertex
+ * with no neighbour of positive bias teleports the same way instead of
+ * stopping.  After a teleport a node2vec walk has no previous vertex (its
+ * next step uses the weights alone).  Teleporting walks always stream the
+ * biases (a cached cumulative array is not used).  Errors: those of
+ * csaw_walk, and CSAW_ERR_INVALID for an unknown teleport mode. */
+#define CSAW_TELEPORT_NONE 0
+#define CSAW_TELEPORT_RESTART 1
+#define CSAW_TELEPORT_JUMP 2
+
+typedef struct {
+    int32_t teleport;        /* CSAW_TELEPORT_* */
+    uint32_t teleport_q32;   /* teleport probability per step, in units of 2^-32 */
+} csaw_walk_opts;
+
+csaw_status csaw_walk_ex(csaw_graph* g, const uint32_t* starts, uint64_t n_walkers, uint32_t length,
+                         const csaw_bias* bias, uint64_t rng_seed, uint32_t* path, int mem_kind,
+                         void* stream, const csaw_walk_opts* opts);
+
 /* Multi-dimensional random walk, or frontier sampling (Sec. II-A), as the
  * API of Sec. III-C expresses it in the case study of Sec. III-D (Figs. 3-4):
  * each instance keeps a pool of pool_size vertices, and every step

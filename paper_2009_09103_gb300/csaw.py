@@ -37,6 +37,13 @@ class Bias(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("n2v_mult", ctypes.c_uint32 * 3)]
 
 
+class WalkOpts(ctypes.Structure):
+    _fields_ = [("teleport", ctypes.c_int32), ("teleport_q32", ctypes.c_uint32)]
+
+
+TELEPORT = {None: 0, "restart": 1, "jump": 2}
+
+
 class GraphInfo(ctypes.Structure):
     _fields_ = [("n_vertices", ctypes.c_uint32), ("n_edges", ctypes.c_uint64),
                 ("max_degree", ctypes.c_uint32), ("max_weight", ctypes.c_uint32),
@@ -106,6 +113,8 @@ def lib():
         L.csaw_graph_destroy.argtypes = [P]
         L.csaw_graph_get_info.argtypes = [P, ctypes.POINTER(GraphInfo)]
         L.csaw_walk.argtypes = [P, P, u64, u32, ctypes.POINTER(Bias), u64, P, i32, P]
+        L.csaw_walk_ex.argtypes = [P, P, u64, u32, ctypes.POINTER(Bias), u64, P, i32, P,
+                                   ctypes.POINTER(WalkOpts)]
         L.csaw_mdrw.argtypes = [P, P, u64, u32, u32, u64, P, P, i32, P]
         L.csaw_graph_build_cdf.argtypes = [P, ctypes.c_int32, P]
         L.csaw_graph_drop_cdf.argtypes = [P, ctypes.c_int32]
@@ -238,27 +247,34 @@ class Graph:
 
 
 def walk(g: Graph, starts, length: int, bias="edge_weight", seed: int = 0, mult=(1, 1, 1),
-         path=None, stream=None):
-    """csaw_walk.  Device call when `starts` is a torch CUDA tensor (returns a
-    torch int32 tensor [n, length+1] holding uint32 vertex ids, asynchronous on
-    `stream`); host call when `starts` is a numpy array (returns numpy uint32)."""
+         path=None, stream=None, teleport=None, teleport_q32: int = 0):
+    """csaw_walk (csaw_walk_ex with teleport = "restart" or "jump" and a
+    per-step probability teleport_q32 / 2^32).  Device call when `starts` is
+    a torch CUDA tensor (returns a torch int32 tensor [n, length+1] holding
+    uint32 vertex ids, asynchronous on `stream`); host call when `starts` is
+    a numpy array (returns numpy uint32)."""
     L = lib()
     b = make_bias(bias, mult) if isinstance(bias, str) else bias
+    opts = WalkOpts(TELEPORT[teleport], teleport_q32) if teleport is not None else None
+
+    def call(sp, pp, mem, st):
+        if opts is None:
+            return L.csaw_walk(g.handle, sp, n, length, ctypes.byref(b), seed, pp, mem, st)
+        return L.csaw_walk_ex(g.handle, sp, n, length, ctypes.byref(b), seed, pp, mem, st, ctypes.byref(opts))
+
     if _is_torch(starts):
         import torch
         n = starts.numel()
         if path is None:
             path = torch.empty((n, length + 1), dtype=torch.int32, device=starts.device)
-        _check(L.csaw_walk(g.handle, _ptr(starts), n, length, ctypes.byref(b), seed, _ptr(path),
-                           MEM_DEVICE, _stream_handle(stream)))
+        _check(call(_ptr(starts), _ptr(path), MEM_DEVICE, _stream_handle(stream)))
         return path
     starts = np.ascontiguousarray(starts, dtype=np.uint32)
     n = len(starts)
     if path is None:
         path = np.empty((n, length + 1), dtype=np.uint32)
     st = _stream_handle(stream) if stream is not None else None
-    _check(L.csaw_walk(g.handle, _ptr(starts), n, length, ctypes.byref(b), seed, _ptr(path),
-                       MEM_HOST, st))
+    _check(call(_ptr(starts), _ptr(path), MEM_HOST, st))
     return path
 
 

@@ -49,6 +49,8 @@ struct WalkParams {
     uint32_t* __restrict__ path;
     PhiloxKeys keys;                      // round keys of the seed
     uint32_t m0, m1, m2;
+    uint32_t tele;                        // CSAW_TELEPORT_RESTART or _JUMP (teleporting kernels)
+    uint32_t tele_q32;                    // teleport probability per step, in units of 2^-32
     unsigned long long* next_walker;
     const uint64_t* __restrict__ cdfw;   // cached edge-weight prefix sums (node2vec fast path) or null
 };
@@ -694,7 +696,13 @@ constexpr int walk_min_blocks()
            : KIND == CSAW_BIAS_NODE2VEC ? 3 : 4;
 }
 
-template <int KIND, bool WIDE>
+// TELE: random walk with restart or with jump (Sec. II-A; an Update, Eq. 4,
+// that returns a vertex other than the sampled neighbour).  Each step first
+// draws attempt 1; if its upper 32 bits are below tele_q32 the walker goes to
+// its start (restart) or to vertex floor(r2 * V / 2^64), r2 the draw of
+// attempt 2 (jump), instead of to a neighbour; a dead end teleports the same
+// way instead of stopping, and node2vec's next step has no previous vertex.
+template <int KIND, bool WIDE, bool TELE>
 __global__ void __launch_bounds__(WALK_THREADS, (walk_min_blocks<KIND, WIDE>())) walk_kernel(WalkParams p)
 {
     // Per warp: the chunk prefix table, then (node2vec) the N(prev) window.
@@ -726,21 +734,42 @@ __global__ void __launch_bounds__(WALK_THREADS, (walk_min_blocks<KIND, WIDE>()))
         uint32_t buf = lane == 0 ? cur : CSAW_NONE;   // entries of the current 32-block
         uint64_t flushed = 0;                         // entries [0, flushed) are in memory
         for (uint32_t s = 0; s < p.L; ++s) {
-            Row row;
-            row.beg = __ldg(p.off + cur);
-            row.end = __ldg(p.off + cur + 1);
-            row.abeg = row.beg & ~3ull;
-            row.d = (uint32_t)(row.end - row.beg);
-            row.span = (uint32_t)(row.end - row.abeg);
-            row.lo = (uint32_t)(row.beg - row.abeg);
-            const uint64_t r = philox_draw(p.keys, 0u, cur, s, (uint32_t)wk);
-            uint32_t idx;
-            if (!walk_pick<KIND, WIDE>(p, row, c, r, s_chunk, s_seg, s_jpos, s_jw, lane, &idx)) break;
-            const uint32_t nxt = __ldg(p.col + row.beg + idx);
-            if constexpr (KIND == CSAW_BIAS_NODE2VEC) {
-                c.prev = cur;
-                c.pbeg = row.beg;
-                c.pend = row.end;
+            uint32_t nxt = 0;
+            bool jump = false;   // warp-uniform: every lane draws the same
+            if constexpr (TELE)
+                jump = (uint32_t)(philox_draw(p.keys, 1u, cur, s, (uint32_t)wk) >> 32) < p.tele_q32;
+            if (!jump) {
+                Row row;
+                row.beg = __ldg(p.off + cur);
+                row.end = __ldg(p.off + cur + 1);
+                row.abeg = row.beg & ~3ull;
+                row.d = (uint32_t)(row.end - row.beg);
+                row.span = (uint32_t)(row.end - row.abeg);
+                row.lo = (uint32_t)(row.beg - row.abeg);
+                const uint64_t r = philox_draw(p.keys, 0u, cur, s, (uint32_t)wk);
+                uint32_t idx;
+                if (walk_pick<KIND, WIDE>(p, row, c, r, s_chunk, s_seg, s_jpos, s_jw, lane, &idx)) {
+                    nxt = __ldg(p.col + row.beg + idx);
+                    if constexpr (KIND == CSAW_BIAS_NODE2VEC) {
+                        c.prev = cur;
+                        c.pbeg = row.beg;
+                        c.pend = row.end;
+                    }
+                } else {
+                    if constexpr (!TELE) break;
+                    jump = true;   // a dead end teleports
+                }
+            }
+            if constexpr (TELE) {
+                if (jump) {
+                    nxt = p.tele == CSAW_TELEPORT_RESTART
+                              ? __ldg(p.starts + wk)
+                              : (uint32_t)scale_draw(philox_draw(p.keys, 2u, cur, s, (uint32_t)wk), p.V);
+                    if constexpr (KIND == CSAW_BIAS_NODE2VEC) {
+                        c.prev = CSAW_NONE;
+                        c.pbeg = c.pend = 0;
+                    }
+                }
             }
             cur = nxt;
             const uint64_t t = (uint64_t)s + 1;
@@ -757,23 +786,30 @@ __global__ void __launch_bounds__(WALK_THREADS, (walk_min_blocks<KIND, WIDE>()))
     }
 }
 
-template <int KIND, bool WIDE>
-static csaw_status launch_walk_kw(const WalkParams& p, int sm_count, cudaStream_t s)
+template <int KIND, bool WIDE, bool TELE>
+static csaw_status launch_walk_kwt(const WalkParams& p, int sm_count, cudaStream_t s)
 {
     // resident blocks per SM, looked up once (calls may come from several threads)
     static std::atomic<int> cached{0};
     int per_sm = cached.load(std::memory_order_acquire);
     if (per_sm == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel<KIND, WIDE>,
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel<KIND, WIDE, TELE>,
                                                                       WALK_THREADS, 0);
         if (e != cudaSuccess) return cuda_fail(e, "occupancy(walk)");
         if (per_sm < 1) per_sm = 1;
         cached.store(per_sm, std::memory_order_release);
     }
-    walk_kernel<KIND, WIDE><<<sm_count * per_sm, WALK_THREADS, 0, s>>>(p);
+    walk_kernel<KIND, WIDE, TELE><<<sm_count * per_sm, WALK_THREADS, 0, s>>>(p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "walk_kernel launch");
     return CSAW_OK;
+}
+
+template <int KIND, bool WIDE>
+static csaw_status launch_walk_kw(const WalkParams& p, int sm_count, cudaStream_t s)
+{
+    return p.tele ? launch_walk_kwt<KIND, WIDE, true>(p, sm_count, s)
+                  : launch_walk_kwt<KIND, WIDE, false>(p, sm_count, s);
 }
 
 // max_bias: an upper bound of any bias of this call; 32-bit round sums when
@@ -890,14 +926,17 @@ csaw_status launch_walk_cached(const csaw_graph* g, int kind, const uint32_t* st
 
 using namespace csaw;
 
-extern "C" csaw_status csaw_walk(csaw_graph* g, const uint32_t* starts, uint64_t n_walkers,
-                                 uint32_t length, const csaw_bias* bias, uint64_t rng_seed,
-                                 uint32_t* path, int mem_kind, void* stream)
+extern "C" csaw_status csaw_walk_ex(csaw_graph* g, const uint32_t* starts, uint64_t n_walkers,
+                                    uint32_t length, const csaw_bias* bias, uint64_t rng_seed,
+                                    uint32_t* path, int mem_kind, void* stream, const csaw_walk_opts* opts)
 {
     clear_error();
     if (!g) return fail(CSAW_ERR_INVALID, "graph is NULL");
     int kind;
     CSAW_TRY(check_bias(g, bias, true, &kind));
+    const uint32_t tele = opts ? (uint32_t)opts->teleport : CSAW_TELEPORT_NONE;
+    if (tele != CSAW_TELEPORT_NONE && tele != CSAW_TELEPORT_RESTART && tele != CSAW_TELEPORT_JUMP)
+        return fail(CSAW_ERR_INVALID, "unknown teleport mode %d", opts->teleport);
     if (mem_kind != CSAW_MEM_HOST && mem_kind != CSAW_MEM_DEVICE)
         return fail(CSAW_ERR_INVALID, "bad mem_kind %d", mem_kind);
     if (n_walkers == 0) return CSAW_OK;
@@ -926,7 +965,7 @@ extern "C" csaw_status csaw_walk(csaw_graph* g, const uint32_t* starts, uint64_t
                                         cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) { dfree(a, s); dfree(b, s); return cuda_fail(e, "copy starts"); }
     }
-    if (kind != CSAW_BIAS_NODE2VEC && cached_cdf_usable(g, kind)) {
+    if (tele == CSAW_TELEPORT_NONE && kind != CSAW_BIAS_NODE2VEC && cached_cdf_usable(g, kind)) {
         // static bias with a cached cumulative array (or uniform): thread per walker
         csaw_status st = launch_walk_cached(g, kind, d_starts, n_walkers, length, rng_seed, d_path, s);
         if (mem_kind == CSAW_MEM_HOST) {
@@ -952,6 +991,8 @@ extern "C" csaw_status csaw_walk(csaw_graph* g, const uint32_t* starts, uint64_t
         p.starts = d_starts; p.n = n_walkers; p.L = length; p.path = d_path;
         p.keys = philox_round_keys(rng_seed);
         p.m0 = bias->n2v_mult[0]; p.m1 = bias->n2v_mult[1]; p.m2 = bias->n2v_mult[2];
+        p.tele = tele;
+        p.tele_q32 = tele != CSAW_TELEPORT_NONE ? opts->teleport_q32 : 0u;
         p.next_walker = (unsigned long long*)counter;
         p.cdfw = g->cdf[CSAW_BIAS_EDGE_WEIGHT];
         uint64_t max_bias = 1;
@@ -975,4 +1016,11 @@ extern "C" csaw_status csaw_walk(csaw_graph* g, const uint32_t* starts, uint64_t
         dfree(d_path, s);
     }
     return st;
+}
+
+extern "C" csaw_status csaw_walk(csaw_graph* g, const uint32_t* starts, uint64_t n_walkers,
+                                 uint32_t length, const csaw_bias* bias, uint64_t rng_seed,
+                                 uint32_t* path, int mem_kind, void* stream)
+{
+    return csaw_walk_ex(g, starts, n_walkers, length, bias, rng_seed, path, mem_kind, stream, nullptr);
 }

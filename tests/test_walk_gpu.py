@@ -246,3 +246,52 @@ def test_walk_node2vec_dense_previous_list(csaw, mult):
     gu = inputs.CSRGraph(g.off, g.col, np.ones_like(g.w))
     got = gpu_walk(csaw, inputs.CSRGraph(g.off, g.col, None), starts, 12, "node2vec", 22, mult)
     assert np.array_equal(got, oracle.walk(gu, starts, 12, "node2vec", 22, mult=mult))
+
+
+Q32_ALWAYS = 0xFFFFFFFF
+
+
+@pytest.mark.parametrize("mode", ["restart", "jump"])
+@pytest.mark.parametrize("bias,mult", [("uniform", (1, 1, 1)), ("edge_weight", (1, 1, 1)),
+                                       ("neighbor_degree", (1, 1, 1)), ("node2vec", (1, 2, 4))])
+@pytest.mark.parametrize("q32", [0, 1 << 30, 3 << 30, Q32_ALWAYS])
+def test_walk_teleport_bit_exact(csaw, mode, bias, mult, q32):
+    # random walk with restart / with jump (Sec. II-A); graphs with dead ends
+    for g in (small_graphs()["dead_end_zero_w"], small_graphs()["rmat_s12"]):
+        starts = np.concatenate([np.arange(min(g.V, 500), dtype=np.uint32),
+                                 inputs.uniform_vertices(300, g.V, 3)])
+        G = csaw.Graph(g.off, g.col, g.w)
+        got = csaw.walk(G, starts, 40, bias, 77, mult, teleport=mode, teleport_q32=q32)
+        G.close()
+        ref = oracle.walk(g, starts, 40, bias, 77, mult=mult, teleport=mode, teleport_q32=q32)
+        assert np.array_equal(got, ref), (mode, bias, q32)
+
+
+def test_walk_teleport_hubs_and_device_buffers(csaw):
+    import torch
+    rng = np.random.default_rng(3)
+    d = 70001
+    edges = [(0, j + 1) for j in range(d)] + [(j + 1, 0) for j in range(d)]
+    w = list(rng.integers(1, 2**20, size=d)) + [1] * d
+    g = inputs.csr_from_edges(d + 1, edges, w)
+    starts = np.concatenate([np.zeros(64, dtype=np.uint32), inputs.uniform_vertices(64, g.V, 2)])
+    G = csaw.Graph(g.off, g.col, g.w)
+    G.build_cdf("edge_weight")   # a teleporting walk streams even with the cached array
+    for mode in ("restart", "jump"):
+        got = csaw.walk(G, torch.from_numpy(starts.view(np.int32)).cuda(), 20, "edge_weight", 5,
+                        teleport=mode, teleport_q32=1 << 31).cpu().numpy().view(np.uint32)
+        ref = oracle.walk(g, starts, 20, "edge_weight", 5, teleport=mode, teleport_q32=1 << 31)
+        assert np.array_equal(got, ref), mode
+    with pytest.raises(csaw.CsawError):
+        csaw.lib()   # the library is loaded
+        bad = csaw.WalkOpts(7, 0)
+        b = csaw.make_bias("edge_weight")
+        csaw._check(csaw.lib().csaw_walk_ex(G.handle, csaw._ptr(starts), len(starts), 3, ctypes_byref(b), 1,
+                                             csaw._ptr(np.empty((len(starts), 4), dtype=np.uint32)),
+                                             csaw.MEM_HOST, None, ctypes_byref(bad)))
+    G.close()
+
+
+def ctypes_byref(x):
+    import ctypes
+    return ctypes.byref(x)
