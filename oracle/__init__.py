@@ -66,6 +66,8 @@ def _load():
         lib.ref_sample.argtypes = [P, P, P, u32, P, P, u32, u32, P, i32, P, u64, u32,
                                    P, P, P, P]
         lib.ref_sample.restype = i32
+        lib.ref_layer_sample.argtypes = [P, P, P, u32, P, P, u32, u32, P, i32, u64, u32, P, P, P, P]
+        lib.ref_layer_sample.restype = i32
         lib.ref_mdrw.argtypes = [P, P, u32, P, P, u64, u32, u32, u64, P, P]
         lib.ref_mdrw.restype = i32
         lib.ref_free.argtypes = [P]
@@ -178,8 +180,10 @@ def mdrw(g, pools, steps: int, seed: int, instance_ids=None):
     return src, dst
 
 
-def sample(g, seeds, inst_offsets, fanout, bias: str, seed: int, attempt_cap: int = ATTEMPT_CAP):
-    """Layered sampling.  Returns dict with src, dst (uint32), edge_off
+def sample(g, seeds, inst_offsets, fanout, bias: str, seed: int, attempt_cap: int = ATTEMPT_CAP,
+           layer: bool = False):
+    """Layered sampling (layer=True: layer sampling, fanout[l] pool entries
+    per instance and layer).  Returns dict with src, dst (uint32), edge_off
     (uint64[depth*n_inst+1], grouped by layer then instance) and fsize
     (uint64[(depth+1)*n_inst], frontier size per layer and instance)."""
     lib = _load()
@@ -191,9 +195,14 @@ def sample(g, seeds, inst_offsets, fanout, bias: str, seed: int, attempt_cap: in
     n_inst = len(io) - 1
     depth = len(fo)
     ps, pd, pe, pf = (ctypes.c_void_p() for _ in range(4))
-    rc = lib.ref_sample(_p(off), _p(col), _p(w), len(off) - 1, _p(s), _p(io), n_inst, depth, _p(fo),
-                        BIAS[bias], _p(m), seed, attempt_cap,
-                        ctypes.byref(ps), ctypes.byref(pd), ctypes.byref(pe), ctypes.byref(pf))
+    if layer:
+        rc = lib.ref_layer_sample(_p(off), _p(col), _p(w), len(off) - 1, _p(s), _p(io), n_inst, depth,
+                                  _p(fo), BIAS[bias], seed, attempt_cap,
+                                  ctypes.byref(ps), ctypes.byref(pd), ctypes.byref(pe), ctypes.byref(pf))
+    else:
+        rc = lib.ref_sample(_p(off), _p(col), _p(w), len(off) - 1, _p(s), _p(io), n_inst, depth, _p(fo),
+                            BIAS[bias], _p(m), seed, attempt_cap,
+                            ctypes.byref(ps), ctypes.byref(pd), ctypes.byref(pe), ctypes.byref(pf))
     if rc != 0:
         raise ValueError(f"oracle sample failed ({rc})")
     eo = np.ctypeslib.as_array((ctypes.c_uint64 * (depth * n_inst + 1)).from_address(pe.value)).copy()

@@ -417,13 +417,57 @@ static int push_edge(edge_buf* e, uint32_t s, uint32_t d)
     return REF_OK;
 }
 
-int ref_sample(const uint64_t* off, const uint32_t* col, const uint32_t* w, uint32_t V,
-               const uint32_t* seeds, const uint64_t* inst_off, uint32_t n_inst,
-               uint32_t depth, const uint32_t* fanout, int kind, const uint32_t mult[3],
-               uint64_t seed, uint32_t attempt_cap,
-               uint32_t** out_src, uint32_t** out_dst, uint64_t** out_edge_off,
-               uint64_t** out_fsize)
+/* Layer sampling (Sec. II-A; Sec. III-B, Fig. 2(b) with the whole frontier as
+ * the current frontier): every edge (v, u) of the instance's frontier, in
+ * ascending v and then CSR order, is one entry of the NeighborPool; EdgeBias
+ * gives each its bias; Select picks k entries without replacement by the
+ * same rule as a vertex's neighbours (select_core), with draws keyed
+ * {attempt, NONE, layer, instance}.  Picks go to E in pick order. */
+static int layer_select(const ref_graph* g, const uint32_t* F, uint32_t nf, uint32_t k, int kind,
+                        const uint32_t mult[3], uint64_t seed, uint32_t layer, uint32_t inst,
+                        uint32_t attempt_cap, edge_buf* E)
 {
+    uint64_t D = 0;
+    for (uint32_t fi = 0; fi < nf; ++fi) D += g->off[F[fi] + 1] - g->off[F[fi]];
+    if (D >= 0xFFFFFFFFull) return REF_ERR_INVALID;
+    uint32_t* b = (uint32_t*)malloc(sizeof(uint32_t) * (D ? D : 1));
+    uint32_t* idx = (uint32_t*)malloc(sizeof(uint32_t) * (D ? D : 1));
+    uint64_t* start = (uint64_t*)malloc(sizeof(uint64_t) * ((uint64_t)nf + 1));
+    if (!b || !idx || !start) { free(b); free(idx); free(start); return REF_ERR_NOMEM; }
+    uint64_t pos = 0;
+    int rc = REF_OK;
+    for (uint32_t fi = 0; fi < nf && rc == REF_OK; ++fi) {
+        start[fi] = pos;
+        rc = edge_biases(g, F[fi], kind, mult, REF_NONE, b + pos);
+        pos += g->off[F[fi] + 1] - g->off[F[fi]];
+    }
+    start[nf] = pos;
+    if (rc == REF_OK) {
+        key_draws K = { seed, REF_NONE, layer, inst };
+        int64_t n = select_core(b, (uint32_t)D, k, attempt_cap, draw_from_key, &K, idx);
+        if (n < 0) rc = REF_ERR_NOMEM;
+        for (int64_t j = 0; j < n && rc == REF_OK; ++j) {
+            uint32_t lo = 0, hi = nf;   /* the pool entry's frontier vertex: last start <= idx */
+            while (hi - lo > 1) {
+                uint32_t mid = (lo + hi) / 2;
+                if (start[mid] <= idx[j]) lo = mid; else hi = mid;
+            }
+            uint32_t v = F[lo];
+            rc = push_edge(E, v, g->col[g->off[v] + (idx[j] - start[lo])]);
+        }
+    }
+    free(b); free(idx); free(start);
+    return rc;
+}
+
+static int sample_impl(const uint64_t* off, const uint32_t* col, const uint32_t* w, uint32_t V,
+                       const uint32_t* seeds, const uint64_t* inst_off, uint32_t n_inst,
+                       uint32_t depth, const uint32_t* fanout, int kind, const uint32_t mult[3],
+                       uint64_t seed, uint32_t attempt_cap, int layer_mode,
+                       uint32_t** out_src, uint32_t** out_dst, uint64_t** out_edge_off,
+                       uint64_t** out_fsize)
+{
+    ref_graph gr = { off, col, w, V };
     if (kind == REF_BIAS_NODE2VEC) return REF_ERR_INVALID;   /* needs a walk's previous vertex */
     uint64_t ngroups = (uint64_t)depth * n_inst;
     edge_buf* per = (edge_buf*)calloc(ngroups ? ngroups : 1, sizeof(edge_buf));
@@ -454,12 +498,16 @@ int ref_sample(const uint64_t* off, const uint32_t* col, const uint32_t* w, uint
 
         for (uint32_t l = 0; l < depth && rc == REF_OK; ++l) {
             edge_buf* E = &per[(uint64_t)l * n_inst + i];
-            for (uint32_t fi = 0; fi < nf; ++fi) {
-                uint32_t v = F[fi];
-                int64_t n = ref_select(off, col, w, V, v, fanout[l], kind, mult, REF_NONE,
-                                       seed, l, i, attempt_cap, picks);
-                if (n < 0) { rc = n == -2 ? REF_ERR_NOMEM : REF_ERR_OVERFLOW; break; }
-                for (int64_t j = 0; j < n && rc == REF_OK; ++j) rc = push_edge(E, v, picks[j]);
+            if (layer_mode) {
+                rc = layer_select(&gr, F, nf, fanout[l], kind, mult, seed, l, i, attempt_cap, E);
+            } else {
+                for (uint32_t fi = 0; fi < nf; ++fi) {
+                    uint32_t v = F[fi];
+                    int64_t n = ref_select(off, col, w, V, v, fanout[l], kind, mult, REF_NONE,
+                                           seed, l, i, attempt_cap, picks);
+                    if (n < 0) { rc = n == -2 ? REF_ERR_NOMEM : REF_ERR_OVERFLOW; break; }
+                    for (int64_t j = 0; j < n && rc == REF_OK; ++j) rc = push_edge(E, v, picks[j]);
+                }
             }
             if (rc != REF_OK) break;
             /* Update: next frontier = sorted set of picks minus visited. */
@@ -510,6 +558,31 @@ int ref_sample(const uint64_t* off, const uint32_t* col, const uint32_t* w, uint
     free(per); free(picks);
     if (rc != REF_OK) free(fsize);
     return rc;
+}
+
+int ref_sample(const uint64_t* off, const uint32_t* col, const uint32_t* w, uint32_t V,
+               const uint32_t* seeds, const uint64_t* inst_off, uint32_t n_inst,
+               uint32_t depth, const uint32_t* fanout, int kind, const uint32_t mult[3],
+               uint64_t seed, uint32_t attempt_cap,
+               uint32_t** out_src, uint32_t** out_dst, uint64_t** out_edge_off,
+               uint64_t** out_fsize)
+{
+    return sample_impl(off, col, w, V, seeds, inst_off, n_inst, depth, fanout, kind, mult, seed,
+                       attempt_cap, 0, out_src, out_dst, out_edge_off, out_fsize);
+}
+
+/* Layer sampling: ref_sample's loop with layer_select in place of the
+ * per-vertex selection; layer_size[l] is the number of pool entries picked
+ * per instance at layer l. */
+int ref_layer_sample(const uint64_t* off, const uint32_t* col, const uint32_t* w, uint32_t V,
+                     const uint32_t* seeds, const uint64_t* inst_off, uint32_t n_inst,
+                     uint32_t depth, const uint32_t* layer_size, int kind, uint64_t seed,
+                     uint32_t attempt_cap, uint32_t** out_src, uint32_t** out_dst,
+                     uint64_t** out_edge_off, uint64_t** out_fsize)
+{
+    const uint32_t ones[3] = { 1, 1, 1 };
+    return sample_impl(off, col, w, V, seeds, inst_off, n_inst, depth, layer_size, kind, ones, seed,
+                       attempt_cap, 1, out_src, out_dst, out_edge_off, out_fsize);
 }
 
 /* Multi-dimensional random walk (frontier sampling), Sec. II-A, written with

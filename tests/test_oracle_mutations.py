@@ -54,6 +54,12 @@ MUTATIONS = {
     "teleport_dead_end_stops": ("if (tele == REF_TELE_NONE) break;", "break;"),
     "jump_range": ("return (uint32_t)ref_scale(ref_draw(seed, 2, cur, s, inst), V);",
                    "return (uint32_t)ref_scale(ref_draw(seed, 2, cur, s, inst), V - 1);"),
+    # layer sampling: pool entries mapped to the wrong frontier vertex, pool
+    # biases that ignore the kind
+    "layer_pool_mapping": ("if (start[mid] <= idx[j]) lo = mid; else hi = mid;",
+                           "if (start[mid] < idx[j]) lo = mid; else hi = mid;"),
+    "layer_pool_unbiased": ("rc = edge_biases(g, F[fi], kind, mult, REF_NONE, b + pos);",
+                            "rc = edge_biases(g, F[fi], REF_BIAS_UNIFORM, mult, REF_NONE, b + pos);"),
     # walk key ignores the step
     "walk_key_step": ("uint64_t x = ref_scale(ref_draw(seed, 0, cur, s, inst), run);",
                       "uint64_t x = ref_scale(ref_draw(seed, 0, cur, 0, inst), run);"),

@@ -570,3 +570,68 @@ def test_restart_walk_law_is_personalized_pagerank():
     assert (path[:, L] < V).all()   # restart walks never stop
     counts = np.bincount(path[:, L], minlength=V)
     assert stats.chisquare(counts, n * pi).pvalue > 1e-6
+
+
+# --------------------------------------------------------------------------
+# Layer sampling (Sec. II-A; Fig. 2(b) with the whole frontier as the current
+# frontier): one pool of all frontier edges per instance and layer
+
+def test_layer_sampling_takes_the_whole_pool_in_order():
+    # layer size at least the pool: every edge of the seeds, ascending source
+    # then CSR order, and the next frontier is every new neighbour
+    g = inputs.rmat_csr(8, 8, 40, 4)
+    seeds = np.array([9, 3, 200, 3], dtype=np.uint32)
+    io = np.array([0, 4], dtype=np.uint64)
+    r = oracle.sample(g, seeds, io, [10**6, 0], "edge_weight", 2, layer=True)
+    exp_src, exp_dst = [], []
+    for v in (3, 9, 200):
+        for u in g.col[g.off[v]:g.off[v + 1]]:
+            exp_src.append(v)
+            exp_dst.append(int(u))
+    n0 = int(r["edge_off"][1])
+    assert list(r["src"][:n0]) == exp_src and list(r["dst"][:n0]) == exp_dst
+    assert r["fsize"][1] == len(set(exp_dst) - {3, 9, 200})
+
+
+def test_layer_sampling_pick_follows_edge_bias_over_the_pool():
+    # frontier {0, 1}: vertex 0 has edges of weight 1, 2, 3, vertex 1 edges of
+    # weight 4 and 10; the first pick of each instance follows the weights
+    # over the whole pool (not a vertex first, then a neighbour)
+    edges = [(0, 2), (0, 3), (0, 4), (1, 5), (1, 6)]
+    wts = [1, 2, 3, 4, 10]
+    g = inputs.csr_from_edges(7, edges + [(b, a) for a, b in edges], wts + wts)
+    n = 30000
+    seeds = np.tile(np.array([0, 1], dtype=np.uint32), n)
+    io = np.arange(0, 2 * n + 1, 2, dtype=np.uint64)
+    r = oracle.sample(g, seeds, io, [2], "edge_weight", 6, layer=True)
+    first = r["dst"][r["edge_off"][:-1].astype(np.int64)]
+    counts = np.bincount(first, minlength=7)[2:]
+    assert counts.sum() == n
+    assert stats.chisquare(counts, n * np.array(wts) / sum(wts)).pvalue > 1e-6
+
+
+def test_layer_sampling_counts_and_distinct_picks():
+    g = inputs.rmat_csr(9, 8, 40, 5)
+    g.w[::5] = 0   # zero biases are never picked
+    sizes = inputs.loguniform_sizes(40, 0.0, 5.0, 3)
+    seeds, io = inputs.distinct_seeds(sizes, g.V, 3)
+    r = oracle.sample(g, seeds, io, [25, 60], "edge_weight", 9, layer=True)
+    wmap = {}
+    for v in range(g.V):
+        for j in range(int(g.off[v]), int(g.off[v + 1])):
+            wmap[(v, int(g.col[j]))] = int(g.w[j])
+    n_inst = len(io) - 1
+    F = [sorted(set(int(x) for x in seeds[io[i]:io[i + 1]])) for i in range(n_inst)]
+    visited = [set(f) for f in F]
+    for l, k in enumerate((25, 60)):
+        for i in range(n_inst):
+            a, b = int(r["edge_off"][l * n_inst + i]), int(r["edge_off"][l * n_inst + i + 1])
+            pairs = list(zip(r["src"][a:b].tolist(), r["dst"][a:b].tolist()))
+            npos = sum(1 for v in F[i] for j in range(int(g.off[v]), int(g.off[v + 1])) if g.w[j] > 0)
+            assert len(pairs) == min(k, npos) and len(set(pairs)) == len(pairs)
+            assert all(wmap.get(p, 0) > 0 and p[0] in F[i] for p in pairs)
+            # Update: the next frontier is the new picked vertices
+            F[i] = sorted(set(u for _, u in pairs) - visited[i])
+            visited[i] |= set(F[i])
+            assert r["fsize"][(l + 1) * n_inst + i] == len(F[i])
+    assert r["fsize"].shape[0] == 3 * n_inst
