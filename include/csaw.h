@@ -265,6 +265,25 @@ csaw_status csaw_sample_ex(csaw_graph* g, const uint32_t* seeds, const uint64_t*
                            const csaw_bias* bias, uint64_t rng_seed, int mem_kind, void* stream,
                            const csaw_sample_opts* opts, csaw_sample_result** out);
 
+/* Layer sampling (Sec. II-A: a constant number of neighbours for all the
+ * vertices of the frontier together), written as Fig. 2(b) with the whole
+ * frontier as the current frontier: per instance and layer l, the
+ * NeighborPool is every edge (v, u) of the instance's frontier, ascending v
+ * and then CSR order, with its EdgeBias (uniform, edge weight or neighbour
+ * degree); Select picks layer_size[l] entries without replacement by the rule
+ * of csaw_sample (first distinct hits of repeated sampling, updated sampling
+ * after opts->attempt_cap attempts, all positive entries when there are at
+ * most layer_size[l]), with the draw of attempt a keyed {a, CSAW_NONE, l,
+ * instance}; Update is that of csaw_sample.  Arguments, result layout
+ * (edges grouped by layer, then instance, in pick order), ownership and
+ * errors are those of csaw_sample_ex, with layer_size in place of fanout
+ * (CSAW_FANOUT_ALL takes the whole pool).  The pool of one instance must
+ * hold fewer than 2^32 edges. */
+csaw_status csaw_layer_sample(csaw_graph* g, const uint32_t* seeds, const uint64_t* inst_offsets,
+                              uint32_t n_instances, uint32_t depth, const uint32_t* layer_size,
+                              const csaw_bias* bias, uint64_t rng_seed, int mem_kind, void* stream,
+                              const csaw_sample_opts* opts, csaw_sample_result** out);
+
 typedef struct {
     uint32_t depth;
     uint32_t n_instances;

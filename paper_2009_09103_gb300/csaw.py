@@ -123,6 +123,8 @@ def lib():
                                       ctypes.POINTER(P)]
             L.csaw_sample_ex.argtypes = [P, P, P, u32, u32, P, ctypes.POINTER(Bias), u64, i32, P,
                                          ctypes.POINTER(SampleOpts), ctypes.POINTER(P)]
+            L.csaw_layer_sample.argtypes = [P, P, P, u32, u32, P, ctypes.POINTER(Bias), u64, i32, P,
+                                            ctypes.POINTER(SampleOpts), ctypes.POINTER(P)]
             L.csaw_sample_get_view.argtypes = [P, ctypes.POINTER(SampleView)]
             L.csaw_sample_copy_edges.argtypes = [P, P, P]
             L.csaw_result_free.argtypes = [P]
@@ -333,8 +335,16 @@ class _SampleHandle:
             pass
 
 
+def layer_sample(g: Graph, seeds, inst_offsets, layer_sizes, bias="edge_weight", seed: int = 0,
+                 stream=None, to_host: bool = True, attempt_cap=None) -> SampleResult:
+    """csaw_layer_sample (layer sampling: layer_sizes[l] picks per instance
+    from the pool of all its frontier's edges).  Same arguments and result
+    as sample()."""
+    return sample(g, seeds, inst_offsets, layer_sizes, bias, seed, stream, to_host, attempt_cap, _layer=True)
+
+
 def sample(g: Graph, seeds, inst_offsets, fanout, bias="edge_weight", seed: int = 0,
-           stream=None, to_host: bool = True, attempt_cap=None) -> SampleResult:
+           stream=None, to_host: bool = True, attempt_cap=None, _layer: bool = False) -> SampleResult:
     """csaw_sample.  seeds/inst_offsets: numpy (host call) or torch CUDA
     tensors (device call).  Returns edges copied to host when to_host, else
     torch tensors that alias a library-owned result kept alive by the returned
@@ -354,8 +364,9 @@ def sample(g: Graph, seeds, inst_offsets, fanout, bias="edge_weight", seed: int 
         n_inst = len(inst_offsets) - 1
         st = _stream_handle(stream) if stream is not None else None
     opts = SampleOpts(ATTEMPT_CAP if attempt_cap is None else attempt_cap)
-    _check(L.csaw_sample_ex(g.handle, _ptr(seeds), _ptr(inst_offsets), n_inst, len(fan), _ptr(fan),
-                            ctypes.byref(b), seed, mem, st, ctypes.byref(opts), ctypes.byref(out)))
+    fn = L.csaw_layer_sample if _layer else L.csaw_sample_ex
+    _check(fn(g.handle, _ptr(seeds), _ptr(inst_offsets), n_inst, len(fan), _ptr(fan),
+              ctypes.byref(b), seed, mem, st, ctypes.byref(opts), ctypes.byref(out)))
     holder = _SampleHandle(out)
     v = SampleView()
     _check(L.csaw_sample_get_view(out, ctypes.byref(v)))

@@ -802,6 +802,225 @@ enum : int {
 };
 enum : int { L_N = 0, L_TOTAL = 1, L_ITEMS = 2, L_NEXT = 4, L_NEXT_F = 6 };
 
+// ---------------------------------------------------------------------------
+// Layer sampling (Sec. II-A; Fig. 2(b) with the whole frontier as the current
+// frontier).  Per instance and layer, the NeighborPool is every edge of the
+// instance's frontier, ascending source then CSR order, with its edge bias;
+// Select picks k entries without replacement by the rule of draw_picks
+// (repeated sampling for attempt_cap attempts, then updated sampling; all
+// positive entries when there are at most k), draws keyed {attempt, NONE,
+// layer, instance}.  One warp per instance.  The count kernel writes
+// min(k, positive entries) at the instance's first frontier entry and 0 at
+// its others, so the layer's scan places each instance's picks; the select
+// kernel writes them in pick order.  A pick is found in two levels: the
+// entry (frontier vertex) by a binary search of the inclusive prefix of
+// entry totals, then the row position by a warp scan of the row's biases
+// (a binary search of the cached cumulative array when present; the draw
+// itself for uniform bias).
+struct LayerSelParams {
+    SelParams s;                         // graph, frontier keys, k, layer, key, outputs, pos
+    const uint64_t* __restrict__ FO;     // [n_inst + 1] frontier bounds of each instance
+    uint32_t n_inst;
+    uint32_t* cnt;                       // count kernel: [frontier]
+    uint64_t* VP;                        // select: [frontier] prefix of entry totals in the instance
+    uint64_t* p_eid;                     // select: [edges] edge index of each pick
+    uint64_t* p_start;                   // select: [edges] pool prefix before each pick
+    uint32_t* p_bias;                    // select: [edges] bias of each pick
+};
+
+// Total and positive count of row v's biases (warp-cooperative).
+template <int KIND>
+__device__ __forceinline__ void layer_row_total(const SelParams& p, uint64_t beg, uint32_t d, int lane,
+                                                uint64_t* total, uint32_t* npos)
+{
+    if constexpr (KIND == CSAW_BIAS_UNIFORM) {
+        *total = d;
+        *npos = d;
+        return;
+    }
+    if (p.cdf && !p.zero_bias) {
+        *total = d ? __ldg(p.cdf + beg + d - 1) : 0ull;
+        *npos = d;
+        return;
+    }
+    uint64_t t = 0;
+    uint32_t c = 0;
+    for (uint32_t j = lane; j < d; j += 32) {
+        const uint32_t b = sel_bias<KIND>(p, beg + j);
+        t += b;
+        c += b > 0;
+    }
+    *total = warp_sum_u64(t);
+    *npos = __reduce_add_sync(CSAW_FULL_MASK, c);
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(SEL_THREADS) layer_count_kernel(LayerSelParams P)
+{
+    const int lane = threadIdx.x & 31;
+    const uint64_t gw = ((uint64_t)blockIdx.x * SEL_THREADS + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * SEL_THREADS) >> 5;
+    const SelParams& p = P.s;
+    for (uint64_t i = gw; i < P.n_inst; i += nw) {
+        const uint64_t a = P.FO[i], b = P.FO[i + 1];
+        uint64_t npos = 0;
+        for (uint64_t e = a; e < b; ++e) {
+            const uint32_t v = (uint32_t)(p.fkeys[e] & p.vmask);
+            const uint64_t beg = __ldg(p.off + v);
+            const uint32_t d = (uint32_t)(__ldg(p.off + v + 1) - beg);
+            if (!p.zero_bias) {
+                npos += d;
+            } else {
+                uint64_t t;
+                uint32_t c;
+                layer_row_total<KIND>(p, beg, d, lane, &t, &c);
+                npos += c;
+            }
+        }
+        for (uint64_t e = a + lane; e < b; e += 32)
+            P.cnt[e] = e == a ? (uint32_t)(npos < p.k ? npos : p.k) : 0u;
+    }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(SEL_THREADS) layer_select_kernel(LayerSelParams P)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = lanemask_lt();
+    const uint64_t gw = ((uint64_t)blockIdx.x * SEL_THREADS + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * SEL_THREADS) >> 5;
+    SelParams p = P.s;
+    if (p.key_dev) {
+        p.k0 = p.key_dev[0];
+        p.k1 = p.key_dev[1];
+    }
+    for (uint64_t i = gw; i < P.n_inst; i += nw) {
+        const uint64_t a = P.FO[i], b = P.FO[i + 1];
+        if (a == b) continue;
+        const uint64_t q0 = p.pos[a];
+        const uint32_t k = (uint32_t)(p.pos[a + 1] - q0);
+        if (k == 0) continue;
+        const uint32_t inst = (uint32_t)i;
+        // entry totals, their inclusive prefix (VP) and the positive entries
+        uint64_t T = 0, npos = 0;
+        for (uint64_t e = a; e < b; ++e) {
+            const uint32_t v = (uint32_t)(p.fkeys[e] & p.vmask);
+            const uint64_t beg = __ldg(p.off + v);
+            const uint32_t d = (uint32_t)(__ldg(p.off + v + 1) - beg);
+            uint64_t t;
+            uint32_t c;
+            layer_row_total<KIND>(p, beg, d, lane, &t, &c);
+            T += t;
+            npos += c;
+            if (lane == 0) P.VP[e] = T;
+        }
+        __syncwarp();
+        if (npos <= p.k) {
+            // take every positive entry, pool order
+            uint64_t q = q0;
+            for (uint64_t e = a; e < b; ++e) {
+                const uint32_t v = (uint32_t)(p.fkeys[e] & p.vmask);
+                const uint64_t beg = __ldg(p.off + v);
+                const uint32_t d = (uint32_t)(__ldg(p.off + v + 1) - beg);
+                for (uint32_t base = 0; base < d; base += 32) {
+                    const uint32_t j = base + lane;
+                    const bool take = j < d && (!p.zero_bias || sel_bias<KIND>(p, beg + j) > 0);
+                    const uint32_t bal = __ballot_sync(CSAW_FULL_MASK, take);
+                    if (take) emit(p, q + __popc(bal & lt), v, inst, __ldg(p.col + beg + j));
+                    q += __popc(bal);
+                }
+            }
+            continue;
+        }
+        uint32_t have = 0;
+        uint64_t R = 0;   // sum of the picked biases
+        for (uint32_t at = 0; have < k; ++at) {
+            const uint64_t r = philox_draw(p.k0, p.k1, at, CSAW_NONE, p.layer, inst);
+            uint64_t x;
+            if (at < p.attempt_cap) {
+                x = scale_draw(r, T);
+            } else {
+                // updated sampling: the draw over the unpicked total, mapped
+                // past the picked intervals (fixpoint of y = x + picked
+                // biases starting at or below y)
+                x = scale_draw(r, T - R);
+                uint64_t y = x;
+                while (true) {
+                    uint64_t add = 0;
+                    for (uint32_t t = lane; t < have; t += 32)
+                        if (P.p_start[q0 + t] <= y) add += P.p_bias[q0 + t];
+                    const uint64_t ny = x + warp_sum_u64(add);
+                    if (ny == y) break;
+                    y = ny;
+                }
+                x = y;
+            }
+            // the entry: first with VP > x
+            uint64_t lo = a, hi = b;
+            while (lo < hi) {
+                const uint64_t mid = lo + ((hi - lo) >> 1);
+                if (P.VP[mid] > x) hi = mid; else lo = mid + 1;
+            }
+            const uint64_t e = lo;
+            const uint64_t before = e > a ? P.VP[e - 1] : 0ull;
+            const uint64_t xr = x - before;
+            const uint32_t v = (uint32_t)(p.fkeys[e] & p.vmask);
+            const uint64_t beg = __ldg(p.off + v);
+            const uint32_t d = (uint32_t)(__ldg(p.off + v + 1) - beg);
+            // the row position: first j with S_row[j] > xr, and S_row[j-1]
+            uint32_t j = 0;
+            uint64_t sprev = 0, sj = 0;
+            if constexpr (KIND == CSAW_BIAS_UNIFORM) {
+                j = (uint32_t)xr;
+                sprev = xr;
+                sj = xr + 1;
+            } else if (p.cdf) {
+                uint32_t l2 = 0, h2 = d;
+                while (l2 < h2) {
+                    const uint32_t mid = (l2 + h2) >> 1;
+                    if (__ldg(p.cdf + beg + mid) > xr) h2 = mid; else l2 = mid + 1;
+                }
+                j = l2;
+                sprev = j ? __ldg(p.cdf + beg + j - 1) : 0ull;
+                sj = __ldg(p.cdf + beg + j);
+            } else {
+                uint64_t base = 0;
+                for (uint32_t c0 = 0; c0 < d; c0 += 32) {
+                    const uint32_t jj = c0 + lane;
+                    const uint32_t bl = jj < d ? sel_bias<KIND>(p, beg + jj) : 0u;
+                    const uint64_t incl = base + warp_inclusive_scan_u64(bl, lane);
+                    const uint32_t hit = __ballot_sync(CSAW_FULL_MASK, incl > xr);
+                    if (hit) {
+                        const int L = __ffs(hit) - 1;
+                        j = c0 + (uint32_t)L;
+                        sj = __shfl_sync(CSAW_FULL_MASK, incl, L);
+                        sprev = sj - __shfl_sync(CSAW_FULL_MASK, (uint64_t)bl, L);
+                        break;
+                    }
+                    base = __shfl_sync(CSAW_FULL_MASK, incl, 31);
+                }
+            }
+            const uint64_t eid = beg + j;
+            bool dup = false;
+            if (at < p.attempt_cap) {
+                for (uint32_t t = lane; t < have; t += 32) dup |= P.p_eid[q0 + t] == eid;
+                dup = __any_sync(CSAW_FULL_MASK, dup);
+            }
+            if (!dup) {
+                if (lane == 0) {
+                    P.p_eid[q0 + have] = eid;
+                    P.p_start[q0 + have] = before + sprev;
+                    P.p_bias[q0 + have] = (uint32_t)(sj - sprev);
+                    emit(p, q0 + have, v, inst, __ldg(p.col + eid));
+                }
+                R += sj - sprev;
+                ++have;
+                __syncwarp();
+            }
+        }
+    }
+}
+
 struct LayerBufs {
     uint64_t f_cap = 0, e_cap = 0;
     uint64_t* F = nullptr;       // frontier keys [f_cap], sorted
@@ -1043,11 +1262,77 @@ static csaw_status check_errors(uint64_t err)
     return CSAW_OK;
 }
 
+// Layer sampling: the parameters of layer l's count and select kernels.
+static LayerSelParams layer_params(const Pipeline& P, uint32_t l)
+{
+    const csaw_graph* g = P.g;
+    const LayerBufs& B = P.L[l];
+    LayerSelParams lp = {};
+    SelParams& sp = lp.s;
+    sp.off = g->off; sp.col = g->col; sp.w = g->w; sp.deg = g->deg;
+    sp.fkeys = B.F; sp.vbits = P.vbits; sp.vmask = P.vmask; sp.k = P.fanout[l]; sp.layer = l;
+    sp.k0 = P.k0; sp.k1 = P.k1; sp.key_dev = P.key_dev;
+    sp.zero_bias = P.zero_bias; sp.pos = B.pos;
+    sp.out_src = B.src; sp.out_dst = B.dst; sp.out_cand = (l + 1 < P.depth) ? B.cand : nullptr;
+    sp.cdf = P.cached && P.kind != CSAW_BIAS_UNIFORM ? g->cdf[P.kind] : nullptr;
+    sp.attempt_cap = P.attempt_cap;
+    lp.FO = B.FO;
+    lp.n_inst = P.n_inst;
+    lp.cnt = B.cnt;
+    return lp;
+}
+
+static int layer_grid(const Pipeline& P)
+{
+    const uint64_t want = ((uint64_t)P.n_inst + SEL_WARPS - 1) / SEL_WARPS;
+    const uint64_t cap = (uint64_t)P.g->sm_count * 8;
+    return (int)(want < 1 ? 1 : want < cap ? want : cap);
+}
+
+// Layer l of layer sampling: per-instance pick counts, then their scan.
+static csaw_status enqueue_layer_count(Pipeline& P, uint32_t l, cudaStream_t s)
+{
+    LayerBufs& B = P.L[l];
+    if (B.f_cap && P.n_inst) {
+        const LayerSelParams lp = layer_params(P, l);
+        switch (P.kind) {
+        case CSAW_BIAS_UNIFORM: layer_count_kernel<CSAW_BIAS_UNIFORM><<<layer_grid(P), SEL_THREADS, 0, s>>>(lp); break;
+        case CSAW_BIAS_EDGE_WEIGHT: layer_count_kernel<CSAW_BIAS_EDGE_WEIGHT><<<layer_grid(P), SEL_THREADS, 0, s>>>(lp); break;
+        default: layer_count_kernel<CSAW_BIAS_NEIGHBOR_DEGREE><<<layer_grid(P), SEL_THREADS, 0, s>>>(lp); break;
+        }
+        CSAW_CUDA(cudaGetLastError());
+    }
+    return scan_u32(B.cnt, B.pos, P.lc(l, L_N), B.f_cap, P.scan_scr, P.lc(l, L_TOTAL), s);
+}
+
+// Layer l of layer sampling: the picks of every instance, then the offsets.
+static csaw_status enqueue_layer_select(Pipeline& P, uint32_t l, uint64_t* VP, uint64_t* p_eid,
+                                        uint64_t* p_start, uint32_t* p_bias, cudaStream_t s)
+{
+    csaw_graph* g = P.g;
+    LayerBufs& B = P.L[l];
+    if (B.f_cap && P.n_inst) {
+        LayerSelParams lp = layer_params(P, l);
+        lp.VP = VP; lp.p_eid = p_eid; lp.p_start = p_start; lp.p_bias = p_bias;
+        switch (P.kind) {
+        case CSAW_BIAS_UNIFORM: layer_select_kernel<CSAW_BIAS_UNIFORM><<<layer_grid(P), SEL_THREADS, 0, s>>>(lp); break;
+        case CSAW_BIAS_EDGE_WEIGHT: layer_select_kernel<CSAW_BIAS_EDGE_WEIGHT><<<layer_grid(P), SEL_THREADS, 0, s>>>(lp); break;
+        default: layer_select_kernel<CSAW_BIAS_NEIGHBOR_DEGREE><<<layer_grid(P), SEL_THREADS, 0, s>>>(lp); break;
+        }
+        CSAW_CUDA(cudaGetLastError());
+    }
+    layer_offsets_kernel<<<grid_for((uint64_t)P.n_inst + 1, 256, g->sm_count), 256, 0, s>>>(
+        B.FO, B.pos, P.n_inst, P.ctr + CT_BASE + l, P.eoff + (uint64_t)l * P.n_inst,
+        P.fsize + (uint64_t)l * P.n_inst, P.ctr + CT_BASE + l + 1);
+    CSAW_CUDA(cudaGetLastError());
+    return CSAW_OK;
+}
+
 // csaw_sample: exact edge buffers, one wait per layer.
 static csaw_status run_sample(csaw_graph* g, const uint32_t* seeds, const uint64_t* inst_off,
                               uint32_t n_inst, uint64_t n_seeds, uint32_t depth, const uint32_t* fanout,
-                              int kind, uint64_t rng_seed, uint32_t attempt_cap, cudaStream_t s,
-                              csaw_sample_result* R)
+                              int kind, uint64_t rng_seed, uint32_t attempt_cap, bool layer_mode,
+                              cudaStream_t s, csaw_sample_result* R)
 {
     Temps tmp(s);
     auto get = [&](void** p, size_t bytes) -> csaw_status {
@@ -1068,7 +1353,7 @@ static csaw_status run_sample(csaw_graph* g, const uint32_t* seeds, const uint64
     R->dst.assign(depth, nullptr);
     R->layer_edges.assign(depth, 0);
     for (uint32_t l = 0; l < depth; ++l) {
-        CSAW_TRY(enqueue_count(P, l, s));
+        CSAW_TRY(layer_mode ? enqueue_layer_count(P, l, s) : enqueue_count(P, l, s));
         uint64_t h[2] = {0, 0};
         CSAW_CUDA(cudaMemcpyAsync(&h[0], P.ctr + CT_ERR, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
         CSAW_CUDA(cudaMemcpyAsync(&h[1], P.lc(l, L_TOTAL), sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
@@ -1079,7 +1364,18 @@ static csaw_status run_sample(csaw_graph* g, const uint32_t* seeds, const uint64
         CSAW_TRY(alloc_edges(P, l, total, get, get_out));
         R->src[l] = P.L[l].src;
         R->dst[l] = P.L[l].dst;
-        CSAW_TRY(enqueue_select(P, l, s));
+        if (layer_mode) {
+            uint64_t *VP = nullptr, *p_eid = nullptr, *p_start = nullptr;
+            uint32_t* p_bias = nullptr;
+            const uint64_t f = P.L[l].f_cap ? P.L[l].f_cap : 1, e = total ? total : 1;
+            CSAW_TRY(get((void**)&VP, sizeof(uint64_t) * f));
+            CSAW_TRY(get((void**)&p_eid, sizeof(uint64_t) * e));
+            CSAW_TRY(get((void**)&p_start, sizeof(uint64_t) * e));
+            CSAW_TRY(get((void**)&p_bias, sizeof(uint32_t) * e));
+            CSAW_TRY(enqueue_layer_select(P, l, VP, p_eid, p_start, p_bias, s));
+        } else {
+            CSAW_TRY(enqueue_select(P, l, s));
+        }
         if (l + 1 < depth) {
             CSAW_TRY(alloc_entries(P, l + 1, total, get));
             CSAW_TRY(enqueue_compact(P, l, s));
@@ -1106,10 +1402,10 @@ static csaw_status run_sample(csaw_graph* g, const uint32_t* seeds, const uint64
 
 using namespace csaw;
 
-extern "C" csaw_status csaw_sample_ex(csaw_graph* g, const uint32_t* seeds, const uint64_t* inst_offsets,
-                                      uint32_t n_instances, uint32_t depth, const uint32_t* fanout,
-                                      const csaw_bias* bias, uint64_t rng_seed, int mem_kind, void* stream,
-                                      const csaw_sample_opts* opts, csaw_sample_result** out)
+static csaw_status sample_entry(csaw_graph* g, const uint32_t* seeds, const uint64_t* inst_offsets,
+                                uint32_t n_instances, uint32_t depth, const uint32_t* fanout,
+                                const csaw_bias* bias, uint64_t rng_seed, int mem_kind, void* stream,
+                                const csaw_sample_opts* opts, bool layer_mode, csaw_sample_result** out)
 {
     clear_error();
     const uint32_t attempt_cap = opts ? opts->attempt_cap : CSAW_ATTEMPT_CAP;
@@ -1167,7 +1463,8 @@ extern "C" csaw_status csaw_sample_ex(csaw_graph* g, const uint32_t* seeds, cons
     if (st == CSAW_OK && n_seeds >= 0xFFFFFFFFull) st = fail(CSAW_ERR_INVALID, "too many seeds");
     if (st == CSAW_OK && n_seeds > 0 && !seeds) st = fail(CSAW_ERR_INVALID, "seeds is NULL");
     if (st == CSAW_OK)
-        st = run_sample(g, d_seeds, d_io, n_instances, n_seeds, depth, fanout, kind, rng_seed, attempt_cap, s, R);
+        st = run_sample(g, d_seeds, d_io, n_instances, n_seeds, depth, fanout, kind, rng_seed, attempt_cap,
+                        layer_mode, s, R);
     dfree(own_seeds, s);
     dfree(own_io, s);
     if (st != CSAW_OK) {
@@ -1177,6 +1474,24 @@ extern "C" csaw_status csaw_sample_ex(csaw_graph* g, const uint32_t* seeds, cons
     }
     *out = R;
     return CSAW_OK;
+}
+
+extern "C" csaw_status csaw_sample_ex(csaw_graph* g, const uint32_t* seeds, const uint64_t* inst_offsets,
+                                      uint32_t n_instances, uint32_t depth, const uint32_t* fanout,
+                                      const csaw_bias* bias, uint64_t rng_seed, int mem_kind, void* stream,
+                                      const csaw_sample_opts* opts, csaw_sample_result** out)
+{
+    return sample_entry(g, seeds, inst_offsets, n_instances, depth, fanout, bias, rng_seed, mem_kind, stream,
+                        opts, false, out);
+}
+
+extern "C" csaw_status csaw_layer_sample(csaw_graph* g, const uint32_t* seeds, const uint64_t* inst_offsets,
+                                         uint32_t n_instances, uint32_t depth, const uint32_t* layer_size,
+                                         const csaw_bias* bias, uint64_t rng_seed, int mem_kind, void* stream,
+                                         const csaw_sample_opts* opts, csaw_sample_result** out)
+{
+    return sample_entry(g, seeds, inst_offsets, n_instances, depth, layer_size, bias, rng_seed, mem_kind,
+                        stream, opts, true, out);
 }
 
 extern "C" csaw_status csaw_sample(csaw_graph* g, const uint32_t* seeds, const uint64_t* inst_offsets,
