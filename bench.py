@@ -642,6 +642,110 @@ def run_mdrw_bench(args):
 
 
 # --------------------------------------------------------------------------
+# Layer sampling, not the default line.
+
+def run_layer_bench(args):
+    import torch
+    from paper_2009_09103_gb300 import build, csaw, inputs
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    t0 = time.time()
+    wl = inputs.workload_layer_s20()
+    g = wl.graph
+    n_inst = len(wl.inst_offsets) - 1
+    log(f"[bench] layer graph: V={g.V} E={g.E} instances={n_inst} built in {time.time() - t0:.1f}s")
+    G = csaw.Graph(g.off, g.col, g.w)
+    if args.cdf:
+        G.build_cdf(wl.bias)
+    ds = torch.from_numpy(wl.seeds.view(np.int32)).to(dev)
+    dio = torch.from_numpy(wl.inst_offsets.view(np.int64)).to(dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    def step():
+        return csaw.layer_sample(G, ds, dio, wl.fanout, wl.bias, wl.rng_seed, stream=stream, to_host=False)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(dev.index)
+    clocks.start()
+    evs = []
+    for i in range(args.steps):
+        flush.fill_(i)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = step()
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    edges = int(res.n_edges)
+    # end to end: host seeds in, edges copied out, through the C ABI
+    t1 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        ref = csaw.layer_sample(G, wl.seeds, wl.inst_offsets, wl.fanout, wl.bias, wl.rng_seed)
+    e2e_s = (time.perf_counter() - t1) / e2e_steps
+    G.close()
+    # per frontier vertex: 16 (offsets) + 4 per pool entry (its bias, read
+    # for the totals); per pick: 8 (the sampled edge).  Frontiers follow
+    # Update: the next one is the new picked vertices.
+    deg = np.diff(g.off).astype(np.int64)
+    front = [np.unique(wl.seeds[int(wl.inst_offsets[i]):int(wl.inst_offsets[i + 1])]) for i in range(n_inst)]
+    visited = [set(f.tolist()) for f in front]
+    eo = ref.edge_offsets.astype(np.int64)
+    alg = 8 * edges
+    for l in range(len(wl.fanout)):
+        alg += sum(16 * len(f) + 4 * int(deg[f.astype(np.int64)].sum()) for f in front)
+        nxt = []
+        for i in range(n_inst):
+            new = sorted(set(ref.dst[eo[l * n_inst + i]:eo[l * n_inst + i + 1]].tolist()) - visited[i])
+            visited[i].update(new)
+            nxt.append(np.array(new, dtype=np.int64))
+        front = nxt
+    peak, peak_kind = measured_peaks()
+    achieved = alg / (ms / 1e3) / 1e9
+    out = {
+        "metric": METRIC, "value": edges / (ms / 1e3), "unit": "edges/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32 biases / u64 prefix sums",
+        "data": "synthetic (seeded RMAT)",
+        "config": {"workload": f"layer sampling: RMAT scale 20, edge factor 16, {n_inst} instances of 64 seeds, "
+                               f"depth 2, {wl.fanout} picks per instance and layer, edge-weight bias",
+                   "l2": "flushed (512 MiB write) before every timed step", "sampled_edges_per_step": edges,
+                   "cumulative_array": "cached per edge" if args.cdf else "computed per selection"},
+        "roofline": {"bound": "hbm", "kernel": "layer_select_kernel", "achieved": round(achieved, 1),
+                     "peak": peak, "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": None, "algorithmic_bytes_per_step": alg},
+        "e2e": {"value": edges / e2e_s, "unit": "edges/s", "h2d_bytes_per_step": 4 * len(wl.seeds) + 8 * (n_inst + 1),
+                "d2h_bytes_per_step": 8 * edges},
+    }
+    if clk:
+        out["clocks"] = clk
+    if args.cpu_baseline_seconds > 0:
+        import oracle
+        oracle.build()
+        done, used, t_used = 0, 0, 0.0
+        for i in range(n_inst):
+            sub = np.zeros(n_inst + 1, dtype=np.uint64)
+            sub[i + 1:] = wl.inst_offsets[i + 1] - wl.inst_offsets[i]
+            t = time.perf_counter()
+            r = oracle.sample(g, wl.seeds[int(wl.inst_offsets[i]):int(wl.inst_offsets[i + 1])], sub, wl.fanout,
+                              wl.bias, wl.rng_seed, layer=True)
+            t_used += time.perf_counter() - t
+            done += int(r["edge_off"][-1])
+            used += 1
+            if t_used > args.cpu_baseline_seconds:
+                break
+        out["cpu_baseline"] = {"value": done / t_used, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                               "sample": f"{used} instances, full depth, {t_used:.1f} s single-threaded"}
+    return out
+
+
+# --------------------------------------------------------------------------
 # Serving (not the default line): open-loop Poisson arrivals of a 50/50 mix of
 # sampling and walk requests into csaw_server, against the same requests run
 # one after another with plain calls.
@@ -793,7 +897,7 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=None,
                     help="--impl reference: oracle seconds per step (default: about a minute in all)")
     ap.add_argument("--workload", default="walk",
-                    choices=["walk", "node2vec", "sample_s12", "batched_s24", "serve", "mdrw"])
+                    choices=["walk", "node2vec", "sample_s12", "batched_s24", "serve", "mdrw", "layer"])
     ap.add_argument("--autotune", action="store_true", help="sampling workloads: autotune first")
     ap.add_argument("--no-variant", action="store_true",
                     help="walks: skip the cached-array variant measured after the main line")
@@ -811,9 +915,10 @@ def main():
     if args.scale is None:
         args.scale = {"walk": 20, "node2vec": 22}.get(args.workload)
     rank, world, local = dist_env()
-    if args.workload in ("sample_s12", "batched_s24", "serve", "mdrw"):
+    if args.workload in ("sample_s12", "batched_s24", "serve", "mdrw", "layer"):
         res = (run_serve_bench(args) if args.workload == "serve" else
-               run_mdrw_bench(args) if args.workload == "mdrw" else run_sample_bench(args))
+               run_mdrw_bench(args) if args.workload == "mdrw" else
+               run_layer_bench(args) if args.workload == "layer" else run_sample_bench(args))
         print(json.dumps(res), flush=True)
         return
 

@@ -826,7 +826,15 @@ struct LayerSelParams {
     uint64_t* p_eid;                     // select: [edges] edge index of each pick
     uint64_t* p_start;                   // select: [edges] pool prefix before each pick
     uint32_t* p_bias;                    // select: [edges] bias of each pick
+    uint64_t* ctb;                       // select: [frontier] chunk table base of each entry (~0: none)
+    uint64_t* ct;                        // select: [warps][LAYER_CT_CAP] chunk prefix tables
 };
+
+// Rows longer than LAYER_CHUNK keep the running sum at the end of every
+// LAYER_CHUNK biases (taken in the totals pass) in the warp's table of
+// LAYER_CT_CAP entries, so a pick bisects the table and scans one chunk.
+constexpr uint32_t LAYER_CHUNK = 512;
+constexpr uint32_t LAYER_CT_CAP = 4096;
 
 // Total and positive count of row v's biases (warp-cooperative).
 template <int KIND>
@@ -901,15 +909,39 @@ __global__ void __launch_bounds__(SEL_THREADS) layer_select_kernel(LayerSelParam
         const uint32_t k = (uint32_t)(p.pos[a + 1] - q0);
         if (k == 0) continue;
         const uint32_t inst = (uint32_t)i;
-        // entry totals, their inclusive prefix (VP) and the positive entries
+        // entry totals, their inclusive prefix (VP) and the positive entries;
+        // long rows also leave their chunk prefixes in this warp's table
         uint64_t T = 0, npos = 0;
+        uint64_t* ct = P.ct + gw * LAYER_CT_CAP;
+        uint32_t ct_used = 0;
         for (uint64_t e = a; e < b; ++e) {
             const uint32_t v = (uint32_t)(p.fkeys[e] & p.vmask);
             const uint64_t beg = __ldg(p.off + v);
             const uint32_t d = (uint32_t)(__ldg(p.off + v + 1) - beg);
-            uint64_t t;
-            uint32_t c;
-            layer_row_total<KIND>(p, beg, d, lane, &t, &c);
+            uint64_t t = 0;
+            uint32_t c = 0;
+            const uint32_t nch = (d + LAYER_CHUNK - 1) / LAYER_CHUNK;
+            const bool table = KIND != CSAW_BIAS_UNIFORM && !p.cdf && d > LAYER_CHUNK &&
+                               ct_used + nch <= LAYER_CT_CAP;
+            if (table) {
+                for (uint32_t ch = 0; ch < nch; ++ch) {
+                    uint64_t tt = 0;
+                    uint32_t cc = 0;
+                    for (uint32_t j = ch * LAYER_CHUNK + lane; j < min(d, (ch + 1) * LAYER_CHUNK); j += 32) {
+                        const uint32_t bb = sel_bias<KIND>(p, beg + j);
+                        tt += bb;
+                        cc += bb > 0;
+                    }
+                    t += warp_sum_u64(tt);
+                    c += __reduce_add_sync(CSAW_FULL_MASK, cc);
+                    if (lane == 0) ct[ct_used + ch] = t;
+                }
+                if (lane == 0) P.ctb[e] = ct_used;
+                ct_used += nch;
+            } else {
+                layer_row_total<KIND>(p, beg, d, lane, &t, &c);
+                if (lane == 0) P.ctb[e] = ~0ull;
+            }
             T += t;
             npos += c;
             if (lane == 0) P.VP[e] = T;
@@ -985,7 +1017,20 @@ __global__ void __launch_bounds__(SEL_THREADS) layer_select_kernel(LayerSelParam
                 sj = __ldg(p.cdf + beg + j);
             } else {
                 uint64_t base = 0;
-                for (uint32_t c0 = 0; c0 < d; c0 += 32) {
+                uint32_t c_begin = 0;
+                const uint64_t cb = P.ctb[e];
+                if (cb != ~0ull) {
+                    // the chunk holding xr: first whose running sum exceeds it
+                    const uint32_t nch = (d + LAYER_CHUNK - 1) / LAYER_CHUNK;
+                    uint32_t l2 = 0, h2 = nch;
+                    while (l2 < h2) {
+                        const uint32_t mid = (l2 + h2) >> 1;
+                        if (ct[cb + mid] > xr) h2 = mid; else l2 = mid + 1;
+                    }
+                    c_begin = l2 * LAYER_CHUNK;
+                    base = l2 ? ct[cb + l2 - 1] : 0ull;
+                }
+                for (uint32_t c0 = c_begin; c0 < d; c0 += 32) {
                     const uint32_t jj = c0 + lane;
                     const uint32_t bl = jj < d ? sel_bias<KIND>(p, beg + jj) : 0u;
                     const uint64_t incl = base + warp_inclusive_scan_u64(bl, lane);
@@ -1307,13 +1352,15 @@ static csaw_status enqueue_layer_count(Pipeline& P, uint32_t l, cudaStream_t s)
 
 // Layer l of layer sampling: the picks of every instance, then the offsets.
 static csaw_status enqueue_layer_select(Pipeline& P, uint32_t l, uint64_t* VP, uint64_t* p_eid,
-                                        uint64_t* p_start, uint32_t* p_bias, cudaStream_t s)
+                                        uint64_t* p_start, uint32_t* p_bias, uint64_t* ctb, uint64_t* ct,
+                                        cudaStream_t s)
 {
     csaw_graph* g = P.g;
     LayerBufs& B = P.L[l];
     if (B.f_cap && P.n_inst) {
         LayerSelParams lp = layer_params(P, l);
         lp.VP = VP; lp.p_eid = p_eid; lp.p_start = p_start; lp.p_bias = p_bias;
+        lp.ctb = ctb; lp.ct = ct;
         switch (P.kind) {
         case CSAW_BIAS_UNIFORM: layer_select_kernel<CSAW_BIAS_UNIFORM><<<layer_grid(P), SEL_THREADS, 0, s>>>(lp); break;
         case CSAW_BIAS_EDGE_WEIGHT: layer_select_kernel<CSAW_BIAS_EDGE_WEIGHT><<<layer_grid(P), SEL_THREADS, 0, s>>>(lp); break;
@@ -1372,7 +1419,10 @@ static csaw_status run_sample(csaw_graph* g, const uint32_t* seeds, const uint64
             CSAW_TRY(get((void**)&p_eid, sizeof(uint64_t) * e));
             CSAW_TRY(get((void**)&p_start, sizeof(uint64_t) * e));
             CSAW_TRY(get((void**)&p_bias, sizeof(uint32_t) * e));
-            CSAW_TRY(enqueue_layer_select(P, l, VP, p_eid, p_start, p_bias, s));
+            uint64_t *ctb = nullptr, *ct = nullptr;
+            CSAW_TRY(get((void**)&ctb, sizeof(uint64_t) * f));
+            CSAW_TRY(get((void**)&ct, sizeof(uint64_t) * LAYER_CT_CAP * (uint64_t)layer_grid(P) * SEL_WARPS));
+            CSAW_TRY(enqueue_layer_select(P, l, VP, p_eid, p_start, p_bias, ctb, ct, s));
         } else {
             CSAW_TRY(enqueue_select(P, l, s));
         }

@@ -220,6 +220,18 @@ def workload_mdrw_s20(graph_seed: int = 20, n_inst: int = 2000, pool_size: int =
     return MdrwWorkload(g, live[idx].reshape(n_inst, pool_size), steps, 5)
 
 
+def workload_layer_s20(graph_seed: int = 20, n_inst: int = 2000, seeds_per_inst: int = 64) -> SampleWorkload:
+    """Layer sampling on the weighted-walk graph (RMAT s20 ef16): 2000
+    instances (the sampling instances of the paper's evaluation, Sec. VI) of
+    64 distinct seeds among the vertices with an edge; depth 2, 512 picks per
+    instance and layer; edge-weight bias; Philox seed 6."""
+    g = rmat_csr(20, 16, 255, graph_seed)
+    live = np.flatnonzero(np.diff(g.off) > 0).astype(np.uint32)
+    sizes = np.full(n_inst, seeds_per_inst, dtype=np.uint64)
+    idx, offs = distinct_seeds(sizes, len(live), graph_seed, stream=6)
+    return SampleWorkload(g, live[idx], offs, [512, 512], "edge_weight", 6)
+
+
 def workload_batched_s24(graph_seed: int = 24, n_inst: int = 4096) -> SampleWorkload:
     """RMAT s24 ef16; 4096 instances of log-uniform [64, 8192) distinct seeds;
     depth 2, fanout [25, 10]; neighbour-degree bias."""

@@ -87,3 +87,30 @@ def test_layer_sample_device_inputs(csaw):
                           torch.from_numpy(io.view(np.int64)).cuda(), [30, 30], "neighbor_degree", 4)
     G.close()
     same(r, oracle.sample(g, seeds, io, [30, 30], "neighbor_degree", 4, layer=True))
+
+
+def test_layer_sample_row_beyond_the_chunk_table(csaw):
+    # vertex 0: 2.2 M neighbours (more chunks than a warp's table holds, so
+    # its picks scan the row); vertex 1: 10,000 (in the table)
+    d0, d1 = 2_200_000, 10_000
+    V = d0 + 2
+    leaves = np.arange(2, V, dtype=np.uint32)
+    deg = np.ones(V, dtype=np.int64)
+    deg[0], deg[1] = d0, d1
+    deg[2:2 + d1] = 2
+    off = np.zeros(V + 1, dtype=np.uint64)
+    off[1:] = np.cumsum(deg)
+    col = np.empty(int(off[-1]), dtype=np.uint32)
+    col[0:d0] = leaves
+    col[d0:d0 + d1] = leaves[:d1]
+    rest = col[d0 + d1:]
+    rest[:2 * d1] = np.tile(np.array([0, 1], dtype=np.uint32), d1)
+    rest[2 * d1:] = 0
+    w = np.random.default_rng(4).integers(1, 500, size=len(col)).astype(np.uint32)
+    g = inputs.CSRGraph(off, col, w)
+    seeds = np.array([0, 1, 1, 0], dtype=np.uint32)
+    io = np.array([0, 2, 3, 4], dtype=np.uint64)
+    G = csaw.Graph(g.off, g.col, g.w)
+    r = csaw.layer_sample(G, seeds, io, [300, 20], "edge_weight", 12)
+    G.close()
+    same(r, oracle.sample(g, seeds, io, [300, 20], "edge_weight", 12, layer=True))
