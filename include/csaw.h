@@ -189,6 +189,35 @@ csaw_status csaw_walk_ex(csaw_graph* g, const uint32_t* starts, uint64_t n_walke
                          const csaw_bias* bias, uint64_t rng_seed, uint32_t* path, int mem_kind,
                          void* stream, const csaw_walk_opts* opts);
 
+/* Random walks over a graph kept in host memory (out-of-memory sampling,
+ * Sec. V-A: graph partitions and workload-aware partition scheduling).
+ *   row_offsets, cols, weights  a host CSR as for csaw_graph_create (weights
+ *                 NULL = all ones); only read, never copied whole
+ *   device_budget_bytes  the device memory for one partition slot: vertex
+ *                 ranges are cut so that a range's offsets and columns (and for
+ *                 edge weight its weights and 8-byte prefix sums) fit it
+ *   starts, path  host arrays as for csaw_walk with host memory
+ *   stats         if not NULL: partitions, partition loads, bytes loaded
+ * Each round loads the partition that holds the most active walkers and
+ * advances every walker in it until it leaves the partition, finishes or
+ * meets a dead end.  Draws and prefix sums are those of csaw_walk, so the
+ * paths equal csaw_walk's for the same graph, starts and seed.  Bias: uniform
+ * or edge weight.  Walker state and the path use device memory beyond the
+ * budget.  Synchronous on `stream`.  Errors: CSAW_ERR_INVALID (bad CSR
+ * offsets or columns, bias kind or start), CSAW_ERR_NOMEM (a row larger than the budget,
+ * or device allocation), CSAW_ERR_CUDA. */
+typedef struct {
+    uint32_t partitions;     /* vertex ranges the graph was cut into */
+    uint64_t loads;          /* partition uploads (scheduling rounds) */
+    uint64_t bytes_loaded;   /* host-to-device bytes of those uploads */
+} csaw_oom_stats;
+
+csaw_status csaw_walk_oom(const uint64_t* row_offsets, const uint32_t* cols, const uint32_t* weights,
+                          uint32_t n_vertices, uint64_t n_edges, uint64_t device_budget_bytes,
+                          const uint32_t* starts, uint64_t n_walkers, uint32_t length,
+                          const csaw_bias* bias, uint64_t rng_seed, uint32_t* path,
+                          csaw_oom_stats* stats, void* stream);
+
 /* Multi-dimensional random walk, or frontier sampling (Sec. II-A), as the
  * API of Sec. III-C expresses it in the case study of Sec. III-D (Figs. 3-4):
  * each instance keeps a pool of pool_size vertices, and every step

@@ -44,6 +44,10 @@ class WalkOpts(ctypes.Structure):
 TELEPORT = {None: 0, "restart": 1, "jump": 2}
 
 
+class OomStats(ctypes.Structure):
+    _fields_ = [("partitions", ctypes.c_uint32), ("loads", ctypes.c_uint64), ("bytes_loaded", ctypes.c_uint64)]
+
+
 class GraphInfo(ctypes.Structure):
     _fields_ = [("n_vertices", ctypes.c_uint32), ("n_edges", ctypes.c_uint64),
                 ("max_degree", ctypes.c_uint32), ("max_weight", ctypes.c_uint32),
@@ -116,6 +120,8 @@ def lib():
         L.csaw_walk_ex.argtypes = [P, P, u64, u32, ctypes.POINTER(Bias), u64, P, i32, P,
                                    ctypes.POINTER(WalkOpts)]
         L.csaw_mdrw.argtypes = [P, P, u64, u32, u32, u64, P, P, i32, P]
+        L.csaw_walk_oom.argtypes = [P, P, P, u32, u64, u64, P, u64, u32, ctypes.POINTER(Bias), u64, P,
+                                    ctypes.POINTER(OomStats), P]
         L.csaw_graph_build_cdf.argtypes = [P, ctypes.c_int32, P]
         L.csaw_graph_drop_cdf.argtypes = [P, ctypes.c_int32]
         if hasattr(L, "csaw_sample"):
@@ -278,6 +284,25 @@ def walk(g: Graph, starts, length: int, bias="edge_weight", seed: int = 0, mult=
     st = _stream_handle(stream) if stream is not None else None
     _check(call(_ptr(starts), _ptr(path), MEM_HOST, st))
     return path
+
+
+def walk_oom(off, col, w, starts, length: int, bias="edge_weight", seed: int = 0,
+             budget_bytes: int = 1 << 30, stream=None):
+    """csaw_walk_oom: walks over a host CSR (numpy off uint64, col uint32, w
+    uint32 or None) streamed through `budget_bytes` of device memory.
+    Returns (path uint32[n, length+1], stats dict)."""
+    L = lib()
+    off = np.ascontiguousarray(off, dtype=np.uint64)
+    col = np.ascontiguousarray(col, dtype=np.uint32)
+    w = np.ascontiguousarray(w, dtype=np.uint32) if w is not None else None
+    starts = np.ascontiguousarray(starts, dtype=np.uint32)
+    b = make_bias(bias) if isinstance(bias, str) else bias
+    path = np.empty((len(starts), length + 1), dtype=np.uint32)
+    st = OomStats()
+    _check(L.csaw_walk_oom(_ptr(off), _ptr(col), _ptr(w), len(off) - 1, len(col), budget_bytes, _ptr(starts),
+                           len(starts), length, ctypes.byref(b), seed, _ptr(path), ctypes.byref(st),
+                           _stream_handle(stream) if stream is not None else None))
+    return path, {"partitions": st.partitions, "loads": st.loads, "bytes_loaded": st.bytes_loaded}
 
 
 def mdrw(g: Graph, pools, steps: int, seed: int = 0, src=None, dst=None, stream=None):

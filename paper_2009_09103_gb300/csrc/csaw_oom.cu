@@ -1,0 +1,277 @@
+// csaw_oom.cu -- random walks over a graph that stays in host memory
+// (out-of-memory sampling, Sec. V-A: graph partitions and workload-aware
+// partition scheduling).
+//
+// The CSR lives in host memory and is cut into vertex ranges whose rows fit a
+// device slot of the given budget.  Walkers keep their state (current vertex,
+// step) on the device.  Each round counts the active walkers per partition,
+// loads the partition with the most of them (the workload-aware schedule of
+// Sec. V-A: partitions with more active instances go first), builds its
+// edge-weight prefix sums on the device and advances every walker that stands
+// in it until the walker leaves the partition, finishes or meets a dead end.
+// A walk step draws from the counter {0, vertex, step, walker} exactly as
+// csaw_walk does, and picks by the same prefix sums, so the paths equal
+// csaw_walk's whatever the partitioning and the order of rounds.
+#include <algorithm>
+#include <vector>
+
+#include "csaw_internal.cuh"
+
+namespace csaw {
+
+struct OomWalkParams {
+    const uint64_t* __restrict__ off;   // slot: rebased offsets of [v0, v1], off[0] = 0
+    const uint32_t* __restrict__ col;   // slot: columns of the partition's rows
+    const uint64_t* __restrict__ cdf;   // slot: inclusive row prefix sums (null: uniform)
+    uint32_t v0, v1;
+    uint64_t n;
+    uint32_t L;
+    PhiloxKeys keys;
+    uint32_t* cur;                      // [n] current vertex
+    uint32_t* step;                     // [n] steps taken
+    uint32_t* __restrict__ path;        // [n][L+1]
+};
+
+// One thread per walker: steps while the walker stands in [v0, v1).
+__global__ void __launch_bounds__(256) oom_walk_kernel(OomWalkParams p)
+{
+    const uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= p.n) return;
+    uint32_t s = p.step[w];
+    uint32_t cur = p.cur[w];
+    if (s >= p.L || cur < p.v0 || cur >= p.v1) return;
+    uint32_t* row = p.path + w * ((uint64_t)p.L + 1);
+    while (s < p.L && cur >= p.v0 && cur < p.v1) {
+        const uint64_t beg = __ldg(p.off + (cur - p.v0));
+        const uint32_t d = (uint32_t)(__ldg(p.off + (cur - p.v0) + 1) - beg);
+        const uint64_t T = p.cdf ? (d ? __ldg(p.cdf + beg + d - 1) : 0ull) : d;
+        if (T == 0) {   // dead end: the rest of the row stays CSAW_NONE
+            s = p.L;
+            break;
+        }
+        const uint64_t x = scale_draw(philox_draw(p.keys, 0u, cur, s, (uint32_t)w), T);
+        uint32_t j;
+        if (p.cdf) {
+            uint32_t lo = 0, hi = d;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (__ldg(p.cdf + beg + mid) > x) hi = mid; else lo = mid + 1;
+            }
+            j = lo;
+        } else {
+            j = (uint32_t)x;   // uniform: S[i] = i + 1
+        }
+        cur = __ldg(p.col + beg + j);
+        ++s;
+        row[s] = cur;
+    }
+    p.cur[w] = cur;
+    p.step[w] = s;
+}
+
+// Inclusive prefix sums of each row's weights in a loaded partition (warp per row).
+__global__ void __launch_bounds__(256) oom_cdf_kernel(const uint64_t* __restrict__ off,
+                                                     const uint32_t* __restrict__ w, uint32_t rows,
+                                                     uint64_t* __restrict__ cdf)
+{
+    const int lane = threadIdx.x & 31;
+    const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t r = gw; r < rows; r += nw) {
+        const uint64_t beg = off[r], end = off[r + 1];
+        uint64_t carry = 0;
+        for (uint64_t base = beg; base < end; base += 32) {
+            const uint64_t i = base + lane;
+            const uint64_t incl = carry + warp_inclusive_scan_u64(i < end ? (uint64_t)__ldg(w + i) : 0ull, lane);
+            if (i < end) cdf[i] = incl;
+            carry = __shfl_sync(CSAW_FULL_MASK, incl, 31);
+        }
+    }
+}
+
+// Start state: path rows [start, NONE, ...], walkers at their starts.
+__global__ void oom_init_kernel(const uint32_t* __restrict__ starts, uint64_t n, uint32_t L, uint32_t V,
+                                uint32_t* cur, uint32_t* step, uint32_t* path)
+{
+    const uint64_t row_len = (uint64_t)L + 1;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * row_len;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t w = t / row_len, k = t % row_len;
+        const uint32_t s0 = __ldg(starts + w);
+        path[t] = k == 0 ? s0 : CSAW_NONE;
+        if (k == 0) {
+            cur[w] = s0;
+            step[w] = s0 < V ? 0u : L;   // an invalid start never moves
+        }
+    }
+}
+
+// Active walkers per partition (partition bounds in vb[0..np]).
+__global__ void oom_count_kernel(const uint32_t* __restrict__ cur, const uint32_t* __restrict__ step, uint64_t n,
+                                 uint32_t L, const uint32_t* __restrict__ vb, uint32_t np,
+                                 unsigned long long* counts)
+{
+    for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n;
+         w += (uint64_t)gridDim.x * blockDim.x) {
+        if (step[w] >= L) continue;
+        const uint32_t v = cur[w];
+        uint32_t lo = 0, hi = np;   // last q with vb[q] <= v
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (vb[mid] <= v) lo = mid; else hi = mid;
+        }
+        atomicAdd(counts + lo, 1ull);
+    }
+}
+
+}  // namespace csaw
+
+using namespace csaw;
+
+extern "C" csaw_status csaw_walk_oom(const uint64_t* row_offsets, const uint32_t* cols, const uint32_t* weights,
+                                     uint32_t n_vertices, uint64_t n_edges, uint64_t device_budget_bytes,
+                                     const uint32_t* starts, uint64_t n_walkers, uint32_t length,
+                                     const csaw_bias* bias, uint64_t rng_seed, uint32_t* path,
+                                     csaw_oom_stats* stats, void* stream)
+{
+    clear_error();
+    if (stats) *stats = csaw_oom_stats{};
+    if (!row_offsets || (n_edges && !cols)) return fail(CSAW_ERR_INVALID, "row_offsets/cols is NULL");
+    if (!bias) return fail(CSAW_ERR_INVALID, "bias is NULL");
+    const int kind = bias->kind;
+    if (kind != CSAW_BIAS_UNIFORM && kind != CSAW_BIAS_EDGE_WEIGHT)
+        return fail(CSAW_ERR_INVALID, "out-of-memory walks take uniform or edge-weight bias");
+    const bool weighted = kind == CSAW_BIAS_EDGE_WEIGHT && weights != nullptr;
+    if (n_walkers == 0) return CSAW_OK;
+    if (!starts || !path) return fail(CSAW_ERR_INVALID, "starts/path is NULL");
+    if (n_walkers > 0xFFFFFFFFull) return fail(CSAW_ERR_INVALID, "at most 2^32-1 walkers per call");
+    if (length == 0xFFFFFFFFu) return fail(CSAW_ERR_INVALID, "length too large");
+    for (uint64_t i = 0; i < n_walkers; ++i)
+        if (starts[i] >= n_vertices)
+            return fail(CSAW_ERR_INVALID, "start %u of walker %llu out of range", starts[i], (unsigned long long)i);
+    if (n_vertices == 0 || row_offsets[0] != 0 || row_offsets[n_vertices] != n_edges)
+        return fail(CSAW_ERR_INVALID, "row_offsets must run from 0 to n_edges");
+    for (uint32_t v = 0; v < n_vertices; ++v)
+        if (row_offsets[v + 1] < row_offsets[v]) return fail(CSAW_ERR_INVALID, "row_offsets must not decrease");
+    // every column a vertex (a walker outside every partition would never finish)
+    for (uint64_t i = 0; i < n_edges; ++i)
+        if (cols[i] >= n_vertices) return fail(CSAW_ERR_INVALID, "column %llu out of range", (unsigned long long)i);
+    cudaStream_t s = (cudaStream_t)stream;
+
+    // Partitions: vertex ranges whose slot (offsets, columns, and for edge
+    // weight the weights and prefix sums) fits the budget; one slot is reused
+    // for every partition.
+    const uint64_t per_edge = weighted ? 16 : 4, per_vertex = 8;
+    const uint64_t slot = device_budget_bytes;
+    std::vector<uint32_t> vb{0};
+    {
+        uint64_t edges = 0;
+        uint32_t v = 0, first = 0;
+        while (v < n_vertices) {
+            const uint64_t d = row_offsets[v + 1] - row_offsets[v];
+            const uint64_t need = (edges + d) * per_edge + ((uint64_t)(v - first) + 2) * per_vertex;
+            if (need > slot) {
+                if (v == first)
+                    return fail(CSAW_ERR_NOMEM, "the row of vertex %u (%llu edges) exceeds the device budget", v,
+                                (unsigned long long)d);
+                vb.push_back(v);
+                first = v;
+                edges = 0;
+                continue;
+            }
+            edges += d;
+            ++v;
+        }
+        vb.push_back(n_vertices);
+    }
+    const uint32_t np = (uint32_t)vb.size() - 1;
+    uint64_t max_edges = 0, max_rows = 0;
+    for (uint32_t q = 0; q < np; ++q) {
+        max_edges = std::max(max_edges, row_offsets[vb[q + 1]] - row_offsets[vb[q]]);
+        max_rows = std::max<uint64_t>(max_rows, vb[q + 1] - vb[q]);
+    }
+
+    const uint64_t row_len = (uint64_t)length + 1;
+    void *d_starts = nullptr, *d_path = nullptr, *d_cur = nullptr, *d_step = nullptr, *d_vb = nullptr;
+    void *d_cnt = nullptr, *s_off = nullptr, *s_col = nullptr, *s_w = nullptr, *s_cdf = nullptr;
+    auto cleanup = [&]() {
+        for (void* p : {d_starts, d_path, d_cur, d_step, d_vb, d_cnt, s_off, s_col, s_w, s_cdf}) dfree(p, s);
+    };
+    csaw_status st = dalloc(&d_starts, sizeof(uint32_t) * n_walkers, s);
+    if (st == CSAW_OK) st = dalloc(&d_path, sizeof(uint32_t) * n_walkers * row_len, s);
+    if (st == CSAW_OK) st = dalloc(&d_cur, sizeof(uint32_t) * n_walkers, s);
+    if (st == CSAW_OK) st = dalloc(&d_step, sizeof(uint32_t) * n_walkers, s);
+    if (st == CSAW_OK) st = dalloc(&d_vb, sizeof(uint32_t) * (np + 1), s);
+    if (st == CSAW_OK) st = dalloc(&d_cnt, sizeof(unsigned long long) * np, s);
+    if (st == CSAW_OK) st = dalloc(&s_off, sizeof(uint64_t) * (max_rows + 1), s);
+    if (st == CSAW_OK) st = dalloc(&s_col, sizeof(uint32_t) * (max_edges ? max_edges : 1), s);
+    if (st == CSAW_OK && weighted) st = dalloc(&s_w, sizeof(uint32_t) * (max_edges ? max_edges : 1), s);
+    if (st == CSAW_OK && weighted) st = dalloc(&s_cdf, sizeof(uint64_t) * (max_edges ? max_edges : 1), s);
+    if (st != CSAW_OK) { cleanup(); return st; }
+    cudaError_t e = cudaMemcpyAsync(d_starts, starts, sizeof(uint32_t) * n_walkers, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_vb, vb.data(), sizeof(uint32_t) * (np + 1), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "copy starts"); }
+    oom_init_kernel<<<1024, 256, 0, s>>>((const uint32_t*)d_starts, n_walkers, length, n_vertices,
+                                         (uint32_t*)d_cur, (uint32_t*)d_step, (uint32_t*)d_path);
+
+    OomWalkParams p;
+    p.keys = philox_round_keys(rng_seed);
+    p.n = n_walkers;
+    p.L = length;
+    p.cur = (uint32_t*)d_cur;
+    p.step = (uint32_t*)d_step;
+    p.path = (uint32_t*)d_path;
+    std::vector<unsigned long long> counts(np);
+    std::vector<uint64_t> rebased;
+    csaw_oom_stats acc{};
+    acc.partitions = np;
+    const unsigned walk_blocks = (unsigned)((n_walkers + 255) / 256);
+    while (true) {
+        e = cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * np, s);
+        if (e != cudaSuccess) break;
+        oom_count_kernel<<<1024, 256, 0, s>>>((const uint32_t*)d_cur, (const uint32_t*)d_step, n_walkers, length,
+                                              (const uint32_t*)d_vb, np, (unsigned long long*)d_cnt);
+        e = cudaMemcpyAsync(counts.data(), d_cnt, sizeof(unsigned long long) * np, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) break;
+        // workload-aware schedule: the partition with the most active walkers
+        uint32_t q = 0;
+        for (uint32_t k = 1; k < np; ++k)
+            if (counts[k] > counts[q]) q = k;
+        if (counts[q] == 0) break;   // every walker finished
+        const uint32_t v0 = vb[q], v1 = vb[q + 1];
+        const uint64_t e0 = row_offsets[v0], ne = row_offsets[v1] - e0;
+        rebased.resize((size_t)(v1 - v0) + 1);
+        for (uint32_t v = v0; v <= v1; ++v) rebased[v - v0] = row_offsets[v] - e0;
+        e = cudaMemcpyAsync(s_off, rebased.data(), sizeof(uint64_t) * rebased.size(), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && ne)
+            e = cudaMemcpyAsync(s_col, cols + e0, sizeof(uint32_t) * ne, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && weighted && ne)
+            e = cudaMemcpyAsync(s_w, weights + e0, sizeof(uint32_t) * ne, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) break;
+        acc.loads += 1;
+        acc.bytes_loaded += sizeof(uint64_t) * rebased.size() + ne * (weighted ? 8 : 4);
+        if (weighted) {
+            const uint64_t blocks = std::min<uint64_t>(((uint64_t)(v1 - v0) + 7) / 8, 4096);
+            oom_cdf_kernel<<<(unsigned)(blocks ? blocks : 1), 256, 0, s>>>((const uint64_t*)s_off,
+                                                                        (const uint32_t*)s_w, v1 - v0,
+                                                                        (uint64_t*)s_cdf);
+        }
+        p.off = (const uint64_t*)s_off;
+        p.col = (const uint32_t*)s_col;
+        p.cdf = weighted ? (const uint64_t*)s_cdf : nullptr;
+        p.v0 = v0;
+        p.v1 = v1;
+        oom_walk_kernel<<<walk_blocks, 256, 0, s>>>(p);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) break;
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(path, d_path, sizeof(uint32_t) * n_walkers * row_len, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cleanup();
+    if (e != cudaSuccess) return cuda_fail(e, "out-of-memory walk");
+    if (stats) *stats = acc;
+    return CSAW_OK;
+}
