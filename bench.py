@@ -746,6 +746,51 @@ def run_layer_bench(args):
 
 
 # --------------------------------------------------------------------------
+# Out-of-memory walks (graph in host memory), not the default line.
+
+def run_oom_bench(args):
+    import torch
+    from paper_2009_09103_gb300 import build, csaw, inputs
+    build.build()
+    torch.cuda.set_device(0)
+    scale = args.scale or 22
+    t0 = time.time()
+    g = inputs.rmat_csr(scale, 16, 255, scale)
+    graph_bytes = 8 * (g.V + 1) + 16 * g.E   # offsets, columns, weights and prefix sums
+    budget = graph_bytes // 4
+    starts = np.arange(0, g.V, 4, dtype=np.uint32)
+    L = 40
+    log(f"[bench] oom graph s{scale}: V={g.V} E={g.E} built in {time.time() - t0:.1f}s; budget {budget >> 20} MiB")
+    path, st = csaw.walk_oom(g.off, g.col, g.w, starts, L, "edge_weight", 7, budget_bytes=budget)   # warm-up
+    times = []
+    for _ in range(max(1, min(args.steps, 3))):
+        t = time.perf_counter()
+        path, st = csaw.walk_oom(g.off, g.col, g.w, starts, L, "edge_weight", 7, budget_bytes=budget)
+        times.append(time.perf_counter() - t)
+    edges = int((path[:, 1:] != 0xFFFFFFFF).sum())
+    # the same walks with the whole graph resident (host buffers, copies inside the call)
+    G = csaw.Graph(g.off, g.col, g.w)
+    ref = csaw.walk(G, starts, L, "edge_weight", 7)
+    t = time.perf_counter()
+    ref = csaw.walk(G, starts, L, "edge_weight", 7)
+    t_mem = time.perf_counter() - t
+    G.close()
+    s_oom = float(np.median(times))
+    return {
+        "metric": METRIC, "value": edges / s_oom, "unit": "edges/s", "n_gpus": 1, "steps": len(times),
+        "warmup": 1, "ms_per_step": 1e3 * s_oom, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32 biases / u64 prefix sums", "data": "synthetic (seeded RMAT)",
+        "config": {"workload": f"out-of-memory weighted walk: RMAT scale {scale}, edge factor 16 in host memory, "
+                               f"device budget of a quarter of the graph ({budget >> 20} MiB), {len(starts)} walkers, "
+                               f"length {L}",
+                   "timing": "wall clock of the whole call (host CSR in, path out)", "sampled_edges": edges},
+        "partitions": st["partitions"], "loads": st["loads"], "gb_loaded": st["bytes_loaded"] / 1e9,
+        "identical_to_in_memory_walk": bool(np.array_equal(path, ref)),
+        "in_memory_walk_seconds": t_mem,
+    }
+
+
+# --------------------------------------------------------------------------
 # Serving (not the default line): open-loop Poisson arrivals of a 50/50 mix of
 # sampling and walk requests into csaw_server, against the same requests run
 # one after another with plain calls.
@@ -897,7 +942,7 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=None,
                     help="--impl reference: oracle seconds per step (default: about a minute in all)")
     ap.add_argument("--workload", default="walk",
-                    choices=["walk", "node2vec", "sample_s12", "batched_s24", "serve", "mdrw", "layer"])
+                    choices=["walk", "node2vec", "sample_s12", "batched_s24", "serve", "mdrw", "layer", "oom"])
     ap.add_argument("--autotune", action="store_true", help="sampling workloads: autotune first")
     ap.add_argument("--no-variant", action="store_true",
                     help="walks: skip the cached-array variant measured after the main line")
@@ -915,9 +960,10 @@ def main():
     if args.scale is None:
         args.scale = {"walk": 20, "node2vec": 22}.get(args.workload)
     rank, world, local = dist_env()
-    if args.workload in ("sample_s12", "batched_s24", "serve", "mdrw", "layer"):
+    if args.workload in ("sample_s12", "batched_s24", "serve", "mdrw", "layer", "oom"):
         res = (run_serve_bench(args) if args.workload == "serve" else
                run_mdrw_bench(args) if args.workload == "mdrw" else
+               run_oom_bench(args) if args.workload == "oom" else
                run_layer_bench(args) if args.workload == "layer" else run_sample_bench(args))
         print(json.dumps(res), flush=True)
         return
