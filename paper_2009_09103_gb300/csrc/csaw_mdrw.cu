@@ -83,6 +83,9 @@ __global__ void __launch_bounds__(MDRW_THREADS) mdrw_kernel(MdrwParams p)
         uint32_t* drow = p.dst + wk * p.steps;
         uint32_t bsrc = CSAW_NONE, bdst = CSAW_NONE;   // step 32*blk + lane of the current block
         uint64_t flushed = 0;                          // steps [0, flushed) are in memory
+        // the pool draw depends on the step alone: the next one is computed
+        // while this step waits for the graph
+        uint64_t r_pool = philox_draw(p.keys, 0u, CSAW_NONE, 0u, inst);
         for (uint32_t s = 0; s < p.steps; ++s) {
             // top level: this lane's run of blocks
             const uint32_t b0 = (uint32_t)lane * (SMALL ? 2u : p.per_lane);
@@ -96,7 +99,7 @@ __global__ void __launch_bounds__(MDRW_THREADS) mdrw_kernel(MdrwParams p)
             const uint64_t incl = warp_inclusive_scan_u64(tl, lane);
             const uint64_t T = __shfl_sync(CSAW_FULL_MASK, incl, 31);
             if (T == 0) break;   // no vertex of the pool has an edge
-            const uint64_t x = scale_draw(philox_draw(p.keys, 0u, CSAW_NONE, s, inst), T);
+            const uint64_t x = scale_draw(r_pool, T);
             const int L = __ffs(__ballot_sync(CSAW_FULL_MASK, incl > x)) - 1;
             uint32_t B = 0;
             uint64_t before = 0;
@@ -131,6 +134,7 @@ __global__ void __launch_bounds__(MDRW_THREADS) mdrw_kernel(MdrwParams p)
             // EdgeBias = 1: the neighbour is the draw itself
             const uint32_t t = (uint32_t)scale_draw(philox_draw(p.keys, 0u, v, s, inst), dv);
             const uint32_t u = __ldg(p.col + __ldg(p.off + v) + t);
+            r_pool = philox_draw(p.keys, 0u, CSAW_NONE, s + 1u, inst);
             const uint32_t du = __ldg(p.deg + u);
             __syncwarp();   // every lane has read this step's pool
             if constexpr (SMALL) {
