@@ -212,6 +212,20 @@ typedef struct {
     uint64_t bytes_loaded;   /* host-to-device bytes of those uploads */
 } csaw_oom_stats;
 
+/* The partitions csaw_walk_oom cuts a host CSR into for a device budget
+ * (host only; no device work).  Vertex ranges [bounds[q], bounds[q+1]) are
+ * taken greedily in vertex order, each as long as its offsets (8 bytes per
+ * row + 8) and, per edge, its column (4) and, when weighted, its weight (4)
+ * and prefix sum (8) fit device_budget_bytes.
+ *   bounds      NULL to ask for the count only, else bounds_cap entries
+ *               receiving the n_partitions + 1 range starts (the last is
+ *               n_vertices)
+ * Errors: CSAW_ERR_INVALID (NULL pointers, no vertices, decreasing offsets,
+ * bounds too short), CSAW_ERR_NOMEM (a row larger than the budget). */
+csaw_status csaw_oom_plan(const uint64_t* row_offsets, uint32_t n_vertices, int weighted,
+                          uint64_t device_budget_bytes, uint32_t* bounds, uint32_t bounds_cap,
+                          uint32_t* n_partitions);
+
 csaw_status csaw_walk_oom(const uint64_t* row_offsets, const uint32_t* cols, const uint32_t* weights,
                           uint32_t n_vertices, uint64_t n_edges, uint64_t device_budget_bytes,
                           const uint32_t* starts, uint64_t n_walkers, uint32_t length,

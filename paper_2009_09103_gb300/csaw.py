@@ -120,6 +120,7 @@ def lib():
         L.csaw_walk_ex.argtypes = [P, P, u64, u32, ctypes.POINTER(Bias), u64, P, i32, P,
                                    ctypes.POINTER(WalkOpts)]
         L.csaw_mdrw.argtypes = [P, P, u64, u32, u32, u64, P, P, i32, P]
+        L.csaw_oom_plan.argtypes = [P, u32, i32, u64, P, u32, ctypes.POINTER(u32)]
         L.csaw_walk_oom.argtypes = [P, P, P, u32, u64, u64, P, u64, u32, ctypes.POINTER(Bias), u64, P,
                                     ctypes.POINTER(OomStats), P]
         L.csaw_graph_build_cdf.argtypes = [P, ctypes.c_int32, P]
@@ -284,6 +285,19 @@ def walk(g: Graph, starts, length: int, bias="edge_weight", seed: int = 0, mult=
     st = _stream_handle(stream) if stream is not None else None
     _check(call(_ptr(starts), _ptr(path), MEM_HOST, st))
     return path
+
+
+def oom_plan(off, budget_bytes: int, weighted: bool = True) -> np.ndarray:
+    """csaw_oom_plan: the vertex ranges csaw_walk_oom would use (host only).
+    Returns bounds uint32[n_partitions + 1]."""
+    L = lib()
+    off = np.ascontiguousarray(off, dtype=np.uint64)
+    n = ctypes.c_uint32()
+    _check(L.csaw_oom_plan(_ptr(off), len(off) - 1, int(weighted), budget_bytes, None, 0, ctypes.byref(n)))
+    bounds = np.empty(n.value + 1, dtype=np.uint32)
+    _check(L.csaw_oom_plan(_ptr(off), len(off) - 1, int(weighted), budget_bytes, _ptr(bounds), len(bounds),
+                           ctypes.byref(n)))
+    return bounds
 
 
 def walk_oom(off, col, w, starts, length: int, bias="edge_weight", seed: int = 0,

@@ -128,6 +128,45 @@ __global__ void oom_count_kernel(const uint32_t* __restrict__ cur, const uint32_
 
 using namespace csaw;
 
+extern "C" csaw_status csaw_oom_plan(const uint64_t* row_offsets, uint32_t n_vertices, int weighted,
+                                     uint64_t device_budget_bytes, uint32_t* bounds, uint32_t bounds_cap,
+                                     uint32_t* n_partitions)
+{
+    clear_error();
+    if (!row_offsets || !n_partitions) return fail(CSAW_ERR_INVALID, "row_offsets/n_partitions is NULL");
+    if (n_vertices == 0) return fail(CSAW_ERR_INVALID, "no vertices");
+    // a partition [first, v) needs 8 bytes per offset (rows + 1) and, per
+    // edge, its column (4) and for edge weight its weight (4) and prefix sum (8)
+    const uint64_t per_edge = weighted ? 16 : 4, per_vertex = 8;
+    uint32_t np = 0, first = 0, v = 0;
+    uint64_t edges = 0;
+    if (bounds && bounds_cap > 0) bounds[0] = 0;
+    while (v < n_vertices) {
+        if (row_offsets[v + 1] < row_offsets[v]) return fail(CSAW_ERR_INVALID, "row_offsets must not decrease");
+        const uint64_t d = row_offsets[v + 1] - row_offsets[v];
+        const uint64_t need = (edges + d) * per_edge + ((uint64_t)(v - first) + 2) * per_vertex;
+        if (need > device_budget_bytes) {
+            if (v == first)
+                return fail(CSAW_ERR_NOMEM, "the row of vertex %u (%llu edges) exceeds the device budget", v,
+                            (unsigned long long)d);
+            ++np;
+            if (bounds && np < bounds_cap) bounds[np] = v;
+            first = v;
+            edges = 0;
+            continue;
+        }
+        edges += d;
+        ++v;
+    }
+    ++np;
+    if (bounds) {
+        if (np + 1 > bounds_cap) return fail(CSAW_ERR_INVALID, "bounds holds %u entries, %u needed", bounds_cap, np + 1);
+        bounds[np] = n_vertices;
+    }
+    *n_partitions = np;
+    return CSAW_OK;
+}
+
 extern "C" csaw_status csaw_walk_oom(const uint64_t* row_offsets, const uint32_t* cols, const uint32_t* weights,
                                      uint32_t n_vertices, uint64_t n_edges, uint64_t device_budget_bytes,
                                      const uint32_t* starts, uint64_t n_walkers, uint32_t length,
@@ -158,33 +197,12 @@ extern "C" csaw_status csaw_walk_oom(const uint64_t* row_offsets, const uint32_t
         if (cols[i] >= n_vertices) return fail(CSAW_ERR_INVALID, "column %llu out of range", (unsigned long long)i);
     cudaStream_t s = (cudaStream_t)stream;
 
-    // Partitions: vertex ranges whose slot (offsets, columns, and for edge
-    // weight the weights and prefix sums) fits the budget; one slot is reused
-    // for every partition.
-    const uint64_t per_edge = weighted ? 16 : 4, per_vertex = 8;
-    const uint64_t slot = device_budget_bytes;
-    std::vector<uint32_t> vb{0};
-    {
-        uint64_t edges = 0;
-        uint32_t v = 0, first = 0;
-        while (v < n_vertices) {
-            const uint64_t d = row_offsets[v + 1] - row_offsets[v];
-            const uint64_t need = (edges + d) * per_edge + ((uint64_t)(v - first) + 2) * per_vertex;
-            if (need > slot) {
-                if (v == first)
-                    return fail(CSAW_ERR_NOMEM, "the row of vertex %u (%llu edges) exceeds the device budget", v,
-                                (unsigned long long)d);
-                vb.push_back(v);
-                first = v;
-                edges = 0;
-                continue;
-            }
-            edges += d;
-            ++v;
-        }
-        vb.push_back(n_vertices);
-    }
-    const uint32_t np = (uint32_t)vb.size() - 1;
+    // Partitions: vertex ranges whose slot fits the budget; one slot is
+    // reused for every partition.
+    uint32_t np = 0;
+    CSAW_TRY(csaw_oom_plan(row_offsets, n_vertices, weighted ? 1 : 0, device_budget_bytes, nullptr, 0, &np));
+    std::vector<uint32_t> vb((size_t)np + 1);
+    CSAW_TRY(csaw_oom_plan(row_offsets, n_vertices, weighted ? 1 : 0, device_budget_bytes, vb.data(), np + 1, &np));
     uint64_t max_edges = 0, max_rows = 0;
     for (uint32_t q = 0; q < np; ++q) {
         max_edges = std::max(max_edges, row_offsets[vb[q + 1]] - row_offsets[vb[q]]);
