@@ -135,6 +135,27 @@ def walk_bytes(torch, off_t, path):
     return n_trans, 16 * n_trans + 4 * deg_sum + 4 * n_trans + 4 * n + 4 * n * row + 16 * n_dead
 
 
+def walk_sector_bytes(torch, off_t, path):
+    """Sector-granular bytes of one edge-weight walk launch: the distinct
+    32-byte sectors each unit must touch.  Per transition a->b: the sectors
+    holding off[a] and off[a+1] (16 bytes from byte 8a), those spanned by a's
+    weights w[off[a]:off[a+1]] and the one holding the picked column; per dead
+    end the sectors of its offsets; per walker 4 (start) and its path row
+    4*(L+1), written whole."""
+    p = path.to(torch.int64) & 0xFFFFFFFF
+    a, b = p[:, :-1], p[:, 1:]
+    real = b != 0xFFFFFFFF
+    av = a[real]
+    beg, end = off_t[av], off_t[av + 1]
+    off_sec = (8 * av + 15) // 32 - (8 * av) // 32 + 1
+    w_sec = (4 * end - 1) // 32 - (4 * beg) // 32 + 1
+    dead = a[(~real) & (a != 0xFFFFFFFF)]
+    dead_sec = (8 * dead + 15) // 32 - (8 * dead) // 32 + 1
+    n, row = path.shape
+    return 32 * (int(off_sec.sum()) + int(w_sec.sum()) + int(av.numel()) + int(dead_sec.sum())) \
+        + 4 * n + 4 * n * row
+
+
 def node2vec_bytes(torch, off_t, path):
     """Algorithmic bytes of one node2vec walk launch: per transition a->b,
     16 (offsets of a) + 8*deg(a) (columns and weights of the row, both needed
@@ -210,6 +231,7 @@ def run_walk_bench(args, rank, world):
     torch.cuda.synchronize()
     off_t = torch.from_numpy(g.off.astype(np.int64)).to(dev)
     n_trans, alg_bytes = (node2vec_bytes if wl.bias == "node2vec" else walk_bytes)(torch, off_t, path)
+    sector_bytes = walk_sector_bytes(torch, off_t, path) if wl.bias == "edge_weight" else None
 
     clocks = Clocks(dev.index)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -274,6 +296,10 @@ def run_walk_bench(args, rank, world):
                 "frac": round(achieved / peak, 4),
                 "traffic": tr["traffic_bytes_per_launch"] if tr else None,
                 "algorithmic_bytes_per_launch": alg_bytes}
+    if sector_bytes is not None and not args.cdf:
+        # the same launch counted in distinct 32-byte sectors
+        roofline["sector_bytes_per_launch"] = sector_bytes
+        roofline["sector_frac"] = round(sector_bytes / (ms_per_step / 1e3) / 1e9 / peak, 4)
     result = {
         "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,

@@ -77,3 +77,39 @@ def test_walk_byte_models_match_a_direct_count():
     path_t = torch.from_numpy(path.view(np.int32))
     assert bench.walk_bytes(torch, off_t, path_t) == (n_trans, ew)
     assert bench.node2vec_bytes(torch, off_t, path_t) == (n_trans, n2v)
+
+
+def test_walk_sector_bytes_match_a_direct_count():
+    """Distinct 32-byte sectors per transition, counted address by address."""
+    torch = pytest.importorskip("torch")
+    import numpy as np
+    bench = _bench_module()
+    NONE = 0xFFFFFFFF
+    rng = np.random.default_rng(5)
+    deg = rng.integers(0, 40, size=60)
+    off = np.zeros(61, dtype=np.int64)
+    off[1:] = np.cumsum(deg)
+    n, L = 25, 9
+    path = np.full((n, L + 1), NONE, dtype=np.uint32)
+    for i in range(n):
+        v = int(rng.integers(0, 60))
+        path[i, 0] = v
+        for t in range(L):
+            if deg[v] == 0 or rng.random() < 0.1:
+                break
+            v = int(rng.integers(0, 60))
+            path[i, t + 1] = v
+    total = 0
+    for i in range(n):
+        total += 4 + 4 * (L + 1)
+        for t in range(L):
+            a, b = int(path[i, t]), int(path[i, t + 1])
+            if a == NONE:
+                break
+            sectors = {(8 * a + k) // 32 for k in range(16)}
+            if b == NONE:
+                total += 32 * len(sectors)
+                break
+            wsec = {(4 * e + k) // 32 for e in range(off[a], off[a + 1]) for k in range(4)}
+            total += 32 * (len(sectors) + len(wsec) + 1)
+    assert bench.walk_sector_bytes(torch, torch.from_numpy(off), torch.from_numpy(path.view(np.int32))) == total
