@@ -89,3 +89,19 @@ def test_parallel_csr_build_equals_serial_build():
             assert fn(*args) == 0
             outs.append((off, col[: n.value]))
         assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_workloads_mdrw_and_layer_s20_shape():
+    # MDRW pools and layer-sampling seeds are drawn among vertices with an
+    # edge; layer seeds are distinct within an instance; both are seeded
+    wm = inputs.workload_mdrw_s20()
+    deg = np.diff(wm.graph.off)
+    assert wm.pools.shape == (2000, 2000) and wm.steps == 2000
+    assert (deg[wm.pools.astype(np.int64)] > 0).all()
+    wl = inputs.workload_layer_s20()
+    io = wl.inst_offsets.astype(np.int64)
+    assert len(io) == 2001 and (np.diff(io) == 64).all() and wl.fanout == [512, 512]
+    assert (deg[wl.seeds.astype(np.int64)] > 0).all()
+    for i in range(0, 2000, 97):
+        assert len(set(wl.seeds[io[i]:io[i + 1]].tolist())) == 64
+    assert np.array_equal(inputs.workload_layer_s20().seeds, wl.seeds)
