@@ -72,6 +72,38 @@ def traffic_record(kernel_src: str, workload: str):
     return None
 
 
+def roofline_block(kernel, tr, ms, alg_bytes, sector_bytes=None):
+    """DRAM-based roofline of one kernel.  achieved = the DRAM bytes of one
+    launch (dram__bytes_read.sum + dram__bytes_write.sum from the ncu record
+    taken on this kernel's current source and this workload) over the
+    launch's CUDA-event time; peak = the measured HBM copy bandwidth.  The
+    method's own bytes -- algorithmic, and counted in 32-byte sectors -- are
+    reported beside it as L2-inclusive work: much of it is served by L2."""
+    peak, peak_kind = measured_peaks()
+    sec = ms / 1e3
+    l2inc = {"algorithmic_bytes_per_launch": alg_bytes,
+             "algorithmic_gbs": round(alg_bytes / sec / 1e9, 1),
+             "algorithmic_over_hbm_peak": round(alg_bytes / sec / 1e9 / peak, 4)}
+    if sector_bytes is not None:
+        l2inc["sector_bytes_per_launch"] = sector_bytes
+        l2inc["sector_over_hbm_peak"] = round(sector_bytes / sec / 1e9 / peak, 4)
+    blk = {"bound": "hbm", "kernel": kernel, "peak": peak, "peak_source": peak_kind, "unit": "GB/s"}
+    if tr:
+        dram = tr["traffic_bytes_per_launch"]
+        ach = dram / sec / 1e9
+        blk.update({"achieved": round(ach, 1), "frac": round(ach / peak, 4), "traffic": dram,
+                    "basis": "DRAM bytes per launch (ncu record of this kernel source) / event time"})
+        if tr.get("l2_hit_rate_pct") is not None:
+            blk["l2_hit_rate_pct"] = tr["l2_hit_rate_pct"]
+        if tr.get("ncu_duration_ns"):
+            blk["ncu_duration_ms"] = tr["ncu_duration_ns"] / 1e6
+    else:
+        blk.update({"achieved": None, "frac": None, "traffic": None,
+                    "basis": "no DRAM record taken on the current kernel source"})
+    blk["l2_inclusive"] = l2inc
+    return blk
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -276,8 +308,6 @@ def run_walk_bench(args, rank, world):
            "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * n * (wl.length + 1),
            "matches_device_run": e2e_ok}
 
-    peak, peak_kind = measured_peaks()
-    achieved = alg_bytes / (ms_per_step / 1e3) / 1e9
     tr = traffic_record("csaw_walk.cu", f"{args.workload}_s{args.scale}" + ("_cdf" if args.cdf else ""))
     kname = "walk_kernel<NODE2VEC>" if wl.bias == "node2vec" else "walk_kernel<EDGE_WEIGHT>"
     if args.cdf and wl.bias != "node2vec":
@@ -290,16 +320,8 @@ def run_walk_bench(args, rank, world):
         deg = (off_t[1:] - off_t[:-1])[a[real]].to(torch.float64)
         probes = int(torch.ceil(torch.log2(deg.clamp(min=1))).sum())
         alg_bytes = 16 * n_trans + 8 * n_trans + 8 * probes + 8 * n_trans + 4 * n + 4 * n * (wl.length + 1)
-        achieved = alg_bytes / (ms_per_step / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1),
-                "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
-                "frac": round(achieved / peak, 4),
-                "traffic": tr["traffic_bytes_per_launch"] if tr else None,
-                "algorithmic_bytes_per_launch": alg_bytes}
-    if sector_bytes is not None and not args.cdf:
-        # the same launch counted in distinct 32-byte sectors
-        roofline["sector_bytes_per_launch"] = sector_bytes
-        roofline["sector_frac"] = round(sector_bytes / (ms_per_step / 1e3) / 1e9 / peak, 4)
+    roofline = roofline_block(kname, tr, ms_per_step, alg_bytes,
+                              sector_bytes if (sector_bytes is not None and not args.cdf) else None)
     result = {
         "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -430,9 +452,9 @@ def run_reference(args, rank, world):
 
 
 # --------------------------------------------------------------------------
-# Sampling workloads (not the default line): C-SAW's layered neighbour
-# sampling, one launch per instance against one batched call and against a
-# plan replayed as a CUDA graph; SEPS = sampled edges / GPU time.
+# Batched sampling (config: RMAT s24, 4096 instances): C-SAW's layered
+# neighbour sampling as one batched plan replayed as a CUDA graph, against one
+# plain csaw_sample call per instance; SEPS = sampled edges / GPU time.
 
 def sample_frontier_bytes(res, g, fanout, bias):
     """Algorithmic bytes of the selection kernels of one run: per frontier
@@ -455,16 +477,124 @@ def sample_frontier_bytes(res, g, fanout, bias):
     return total
 
 
-def time_gpu(torch, fn, reps=1):
+def time_gpu(torch, fn, reps=1, flush=None):
+    """Mean ms of fn() over reps, CUDA events on the current stream; with
+    flush, a buffer larger than L2 is written before each rep (outside the
+    events)."""
     st = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
     torch.cuda.synchronize()
-    e0.record(st)
-    for _ in range(reps):
+    for i in range(reps):
+        if flush is not None:
+            flush.fill_(i)
+        evs[i][0].record(st)
         fn()
-    e1.record(st)
+        evs[i][1].record(st)
     torch.cuda.synchronize()
-    return e0.elapsed_time(e1) / reps
+    return sum(a.elapsed_time(b) for a, b in evs) / reps
+
+
+BATCHED_DESC = ("batched layered sampling: RMAT scale 24, edge factor 16, 4096 instances of log-uniform "
+                "[64,8192) distinct seeds, depth 2, fanout [25,10], neighbour-degree bias")
+
+
+def batched_leg(torch, csaw, wl, G, cdf, steps, warmup, plain_instances, flush):
+    """The batched plan (one CUDA graph over all instances and layers) against
+    one plain csaw_sample call per instance (each alone at its own index) on
+    the same graph; returns SEPS and times of both."""
+    if cdf:
+        G.build_cdf(wl.bias)
+    n_inst = len(wl.inst_offsets) - 1
+    plan = csaw.SamplePlan(G, n_inst, len(wl.seeds), wl.fanout, wl.bias)
+    ds = torch.from_numpy(wl.seeds.view(np.int32)).cuda()
+    dio = torch.from_numpy(wl.inst_offsets.view(np.int64)).cuda()
+    for _ in range(warmup):
+        plan.run(ds, dio, wl.rng_seed)
+    ms_plan = time_gpu(torch, lambda: plan.run(ds, dio, wl.rng_seed), steps, flush)
+    res = plan.result()
+    info = plan.info()
+    plan.close()
+    edges = int(res.n_edges)
+    n_plain = min(n_inst, plain_instances)
+    pick = np.unique(np.linspace(0, n_inst - 1, n_plain).astype(np.int64))
+    calls = []
+    for i in pick:
+        sub = np.zeros(n_inst + 1, dtype=np.uint64)
+        sub[i + 1:] = wl.inst_offsets[i + 1] - wl.inst_offsets[i]
+        calls.append((wl.seeds[wl.inst_offsets[i]:wl.inst_offsets[i + 1]].copy(), sub))
+
+    def plain():
+        for s_, io_ in calls:
+            csaw.sample(G, s_, io_, wl.fanout, wl.bias, wl.rng_seed, to_host=False)
+    plain_edges = sum(int(res.edge_offsets[l * n_inst + i + 1] - res.edge_offsets[l * n_inst + i])
+                      for i in pick for l in range(len(wl.fanout)))
+    if calls:   # warm-up call: the allocator pool and the kernels' first use
+        csaw.sample(G, calls[0][0], calls[0][1], wl.fanout, wl.bias, wl.rng_seed, to_host=False)
+    ms_plain = time_gpu(torch, plain, 1, flush)
+    if cdf:
+        G.drop_cdf(wl.bias)
+    seps_b, seps_p = edges / (ms_plan / 1e3), plain_edges / (ms_plain / 1e3)
+    return res, {
+        "batched_plan": {"ms_per_run": ms_plan, "seps": seps_b, "sampled_edges": edges, "runs_timed": steps,
+                         "select_blocks": info["select_blocks"], "theta_warp": info["theta_warp"],
+                         "plan_device_bytes": info["device_bytes"]},
+        "plain_one_call_per_instance": {
+            "instances_timed": int(len(pick)), "instances_total": n_inst,
+            "subset": "all instances" if len(pick) == n_inst else
+                      f"{len(pick)} instances uniformly spaced over the {n_inst}",
+            "ms": ms_plain, "sampled_edges": plain_edges, "seps": seps_p,
+            "timing": "one csaw_sample call per instance (host seeds in, edges left on the device), "
+                      "CUDA events around the whole sequence"},
+        "batched_over_plain_seps": seps_b / seps_p,
+    }
+
+
+def batched_workload(args, inputs):
+    if args.workload == "sample_s12":
+        wl = inputs.workload_sample_s12()
+        desc = ("layered biased neighbour sampling: RMAT scale 12, edge factor 16, weights uniform "
+                "[1,100], 256 uniform seeds as one instance, depth 2, fanout [10,5], edge-weight bias")
+    elif args.scale in (None, 24) and args.instances == 4096:
+        wl, desc = inputs.workload_batched_s24(), BATCHED_DESC
+    else:
+        g0 = inputs.rmat_csr(args.scale, 16, 255, args.scale)
+        sizes = inputs.loguniform_sizes(args.instances, 6.0, 7.0, args.scale, stream=4)
+        sd, io = inputs.distinct_seeds(sizes, g0.V, args.scale, stream=4)
+        wl = inputs.SampleWorkload(g0, sd, io, [25, 10], "neighbor_degree", 4)
+        desc = (f"batched layered sampling: RMAT scale {args.scale}, edge factor 16, {args.instances} instances "
+                "of log-uniform [64,8192) distinct seeds, depth 2, fanout [25,10], neighbour-degree bias")
+    return wl, desc
+
+
+def batched_block(args):
+    """Both forms of the batched comparison (streamed and cached cumulative
+    arrays) on the RMAT s24 workload; the block the default run carries."""
+    import torch
+    from paper_2009_09103_gb300 import csaw, inputs
+    t0 = time.time()
+    wl, desc = inputs.workload_batched_s24(), BATCHED_DESC
+    g = wl.graph
+    log(f"[bench] batched: V={g.V} E={g.E} seeds={len(wl.seeds)} built in {time.time() - t0:.1f}s")
+    G = csaw.Graph(g.off, g.col, g.w)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    res, streamed = batched_leg(torch, csaw, wl, G, False, args.batched_steps, 1, args.plain_instances, flush)
+    _, cached = batched_leg(torch, csaw, wl, G, True, args.batched_steps, 1, args.plain_instances, flush)
+    clk = clocks.stop()
+    G.close()
+    alg = sample_frontier_bytes(res, g, wl.fanout, wl.bias)
+    out = {"workload": desc, "sampled_edges_per_run": int(res.n_edges),
+           "l2": "flushed (512 MiB write) before every timed run",
+           "streamed_cumulative_array": streamed, "cached_cumulative_array": cached,
+           "selection_algorithmic_bytes_per_run": alg,
+           "selection_algorithmic_gbs_streamed": alg / (streamed["batched_plan"]["ms_per_run"] / 1e3) / 1e9}
+    tr = traffic_record("csaw_sample.cu", "batched_s24")
+    if tr:
+        out["select_kernel_dram"] = tr
+    if clk:
+        out["clocks"] = clk
+    return out
 
 
 def run_sample_bench(args):
@@ -473,85 +603,43 @@ def run_sample_bench(args):
     build.build()
     torch.cuda.set_device(0)
     t0 = time.time()
-    if args.workload == "sample_s12":
-        wl = inputs.workload_sample_s12()
-        desc = ("layered biased neighbour sampling: RMAT scale 12, edge factor 16, weights uniform "
-                "[1,100], 256 uniform seeds as one instance, depth 2, fanout [10,5], edge-weight bias")
-    elif args.scale in (None, 24) and args.instances == 4096:
-        wl = inputs.workload_batched_s24()
-        desc = ("batched layered sampling: RMAT scale 24, edge factor 16, 4096 instances of log-uniform "
-                "[64,8192) distinct seeds, depth 2, fanout [25,10], neighbour-degree bias")
-    else:
-        g0 = inputs.rmat_csr(args.scale, 16, 255, args.scale)
-        sizes = inputs.loguniform_sizes(args.instances, 6.0, 7.0, args.scale, stream=4)
-        sd, io = inputs.distinct_seeds(sizes, g0.V, args.scale, stream=4)
-        wl = inputs.SampleWorkload(g0, sd, io, [25, 10], "neighbor_degree", 4)
-        desc = (f"batched layered sampling: RMAT scale {args.scale}, edge factor 16, {args.instances} instances "
-                "of log-uniform [64,8192) distinct seeds, depth 2, fanout [25,10], neighbour-degree bias")
+    wl, desc = batched_workload(args, inputs)
     g = wl.graph
     log(f"[bench] {args.workload}: V={g.V} E={g.E} seeds={len(wl.seeds)} built in {time.time() - t0:.1f}s")
     G = csaw.Graph(g.off, g.col, g.w)
-    if args.cdf:
-        G.build_cdf(wl.bias)
-    n_inst = len(wl.inst_offsets) - 1
-    out = {"cumulative_array": "cached per edge" if args.cdf else "computed per selection"}
-    # batched call (csaw_sample over all instances)
-    ref = csaw.sample(G, wl.seeds, wl.inst_offsets, wl.fanout, wl.bias, wl.rng_seed)
     if args.autotune:
-        out["tuning"] = csaw.autotune_select(G, wl.seeds, wl.inst_offsets, wl.fanout, wl.bias, wl.rng_seed)
-    for _ in range(args.warmup):
-        csaw.sample(G, wl.seeds, wl.inst_offsets, wl.fanout, wl.bias, wl.rng_seed)
+        tuning = csaw.autotune_select(G, wl.seeds, wl.inst_offsets, wl.fanout, wl.bias, wl.rng_seed)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    ref = csaw.sample(G, wl.seeds, wl.inst_offsets, wl.fanout, wl.bias, wl.rng_seed)
+    res, legs = batched_leg(torch, csaw, wl, G, args.cdf, args.steps, args.warmup, args.plain_instances, flush)
+    plan_ok = bool(np.array_equal(res.dst, ref.dst) and np.array_equal(res.edge_offsets, ref.edge_offsets))
     ms_call = time_gpu(torch, lambda: csaw.sample(G, wl.seeds, wl.inst_offsets, wl.fanout, wl.bias,
-                                                  wl.rng_seed, to_host=False), args.steps)
-    # plan: the same pipeline captured in a CUDA graph (seeds copied in each run)
-    plan = csaw.SamplePlan(G, n_inst, len(wl.seeds), wl.fanout, wl.bias)
-    ds = torch.from_numpy(wl.seeds.view(np.int32)).cuda()
-    dio = torch.from_numpy(wl.inst_offsets.view(np.int64)).cuda()
-    for _ in range(args.warmup):
-        plan.run(ds, dio, wl.rng_seed)
-    ms_plan = time_gpu(torch, lambda: plan.run(ds, dio, wl.rng_seed), args.steps)
-    got = plan.result()
-    plan_ok = bool(np.array_equal(got.dst, ref.dst) and np.array_equal(got.edge_offsets, ref.edge_offsets))
-    # one call per instance (each instance alone at its own index)
-    n_plain = min(n_inst, args.plain_instances)
-    pick = np.linspace(0, n_inst - 1, n_plain).astype(np.int64)
-    calls = []
-    for i in pick:
-        sub = np.zeros(n_inst + 1, dtype=np.uint64)
-        sub[i + 1:] = wl.inst_offsets[i + 1] - wl.inst_offsets[i]
-        calls.append((wl.seeds[wl.inst_offsets[i]:wl.inst_offsets[i + 1]].copy(), sub))
-    def plain():
-        for s_, io_ in calls:
-            csaw.sample(G, s_, io_, wl.fanout, wl.bias, wl.rng_seed, to_host=False)
-    ms_plain_sub = float("nan")
-    if n_plain:
-        plain()
-        ms_plain_sub = time_gpu(torch, plain, 1)
-    edges_sub = sum(int(ref.edge_offsets[l * n_inst + i + 1] - ref.edge_offsets[l * n_inst + i])
-                    for i in pick for l in range(len(wl.fanout)))
+                                                  wl.rng_seed, to_host=False), args.steps, flush)
     edges = int(ref.n_edges)
     alg = sample_frontier_bytes(ref, g, wl.fanout, wl.bias)
     peak, peak_kind = measured_peaks()
-    res = {
+    ms_plan = legs["batched_plan"]["ms_per_run"]
+    out = {
         "metric": METRIC, "value": edges / (ms_plan / 1e3), "unit": "edges/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_plan, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32 biases / u64 prefix sums",
         "data": "synthetic (seeded RMAT)",
-        "config": {"workload": desc, "sampled_edges_per_step": edges, "instances": n_inst},
-        "batched_plan_cuda_graph": {"ms": ms_plan, "seps": edges / (ms_plan / 1e3), "matches_sample": plan_ok,
-                                    **plan.info()},
+        "config": {"workload": desc, "sampled_edges_per_step": edges, "instances": len(wl.inst_offsets) - 1,
+                   "cumulative_array": "cached per edge" if args.cdf else "computed per selection",
+                   "l2": "flushed (512 MiB write) before every timed run"},
+        **legs,
+        "plan_matches_sample": plan_ok,
         "batched_call": {"ms": ms_call, "seps": edges / (ms_call / 1e3)},
-        "plain_one_call_per_instance": {"instances_timed": int(n_plain), "ms": ms_plain_sub,
-                                         "seps": edges_sub / (ms_plain_sub / 1e3)},
         "selection_bytes_per_run": alg,
         "gbs_over_whole_run": alg / (ms_plan / 1e3) / 1e9, "peak_gbs": peak, "peak_source": peak_kind,
-        **out,
     }
-    plan.close()
+    if args.autotune:
+        out["tuning"] = tuning
     G.close()
     if args.cpu_baseline_seconds > 0:
         import oracle
         oracle.build()
+        n_inst = len(wl.inst_offsets) - 1
         done, used, t_used = 0, 0, 0.0
         for i in np.argsort(np.diff(wl.inst_offsets).astype(np.int64), kind="stable"):
             sub = np.zeros(n_inst + 1, dtype=np.uint64)
@@ -564,9 +652,9 @@ def run_sample_bench(args):
             used += 1
             if t_used > args.cpu_baseline_seconds:
                 break
-        res["cpu_baseline"] = {"value": done / t_used, "unit": "edges/s", "cores": 1, "kind": "oracle",
+        out["cpu_baseline"] = {"value": done / t_used, "unit": "edges/s", "cores": 1, "kind": "oracle",
                                "sample": f"{used} instances (smallest first), full depth, {t_used:.1f} s"}
-    return res
+    return out
 
 
 # --------------------------------------------------------------------------
@@ -627,8 +715,6 @@ def run_mdrw_bench(args):
     # per step: 16 (offsets of v) + 4 (the picked column) + 4 (degree of u) +
     # 8 (the sampled edge); per instance: 4 per pool slot read
     alg = 32 * n_edges + 4 * n * m
-    peak, peak_kind = measured_peaks()
-    achieved = alg / (ms / 1e3) / 1e9
     tr = traffic_record("csaw_mdrw.cu", "mdrw_s20")
     res = {
         "metric": METRIC, "value": n_edges / (ms / 1e3), "unit": "edges/s", "n_gpus": 1,
@@ -640,10 +726,7 @@ def run_mdrw_bench(args):
                                "degree, EdgeBias = 1",
                    "l2": "flushed (512 MiB write) before every timed step", "sampled_edges_per_step": n_edges},
         "gpu_launches": args.steps,
-        "roofline": {"bound": "hbm", "kernel": "mdrw_kernel", "achieved": round(achieved, 1), "peak": peak,
-                     "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": tr["traffic_bytes_per_launch"] if tr else None,
-                     "algorithmic_bytes_per_launch": alg},
+        "roofline": roofline_block("mdrw_kernel", tr, ms, alg),
         "e2e": {"value": n_edges / e2e_s, "unit": "edges/s", "h2d_bytes_per_step": 4 * n * m,
                 "d2h_bytes_per_step": 8 * n * wl.steps, "matches_device_run": same},
     }
@@ -732,8 +815,7 @@ def run_layer_bench(args):
             visited[i].update(new)
             nxt.append(np.array(new, dtype=np.int64))
         front = nxt
-    peak, peak_kind = measured_peaks()
-    achieved = alg / (ms / 1e3) / 1e9
+    tr = traffic_record("csaw_sample.cu", "layer_s20" + ("_cdf" if args.cdf else ""))
     out = {
         "metric": METRIC, "value": edges / (ms / 1e3), "unit": "edges/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -743,9 +825,7 @@ def run_layer_bench(args):
                                f"depth 2, {wl.fanout} picks per instance and layer, edge-weight bias",
                    "l2": "flushed (512 MiB write) before every timed step", "sampled_edges_per_step": edges,
                    "cumulative_array": "cached per edge" if args.cdf else "computed per selection"},
-        "roofline": {"bound": "hbm", "kernel": "layer_select_kernel", "achieved": round(achieved, 1),
-                     "peak": peak, "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": None, "algorithmic_bytes_per_step": alg},
+        "roofline": roofline_block("layer_select_kernel", tr, ms, alg),
         "e2e": {"value": edges / e2e_s, "unit": "edges/s", "h2d_bytes_per_step": 4 * len(wl.seeds) + 8 * (n_inst + 1),
                 "d2h_bytes_per_step": 8 * edges},
     }
@@ -817,56 +897,28 @@ def run_oom_bench(args):
 
 
 # --------------------------------------------------------------------------
-# Serving (not the default line): open-loop Poisson arrivals of a 50/50 mix of
-# sampling and walk requests into csaw_server, against the same requests run
-# one after another with plain calls.
-
-def serving_requests(g, n, seed):
-    from paper_2009_09103_gb300 import inputs
-    rng = np.random.default_rng(seed)
-    reqs = []
-    for i in range(n):
-        if i % 2 == 0:
-            ns = max(1, int(2 ** (14 * rng.random())))
-            seeds = inputs.uniform_vertices(ns, g.V, 10_000 + i)
-            depth = int(rng.integers(1, 4))
-            fan = [int(x) for x in rng.choice([5, 10, 25], size=depth)]
-            reqs.append(("sample", seeds, np.array([0, ns], dtype=np.uint64), fan, 100 + i))
-        else:
-            nw = max(1, int(2 ** (16 * rng.random())))
-            starts = inputs.uniform_vertices(nw, g.V, 20_000 + i)
-            reqs.append(("walk", starts, int(rng.integers(10, 81)), 200 + i))
-    return reqs
-
+# Serving (config: RMAT s26 resident): open-loop Poisson arrivals of a 50/50
+# mix of sampling and walk requests into csaw_server, against the same
+# requests run one after another with plain calls.
 
 def req_edges(r, res):
     return int(res.sample.n_edges) if r[0] == "sample" else int((res.path[:, 1:] != 0xFFFFFFFF).sum())
 
 
-def run_serve_bench(args):
+def served_leg(csaw, G, reqs, loads, slots, budget):
+    """Serial plain service times, then the server at each load point.
+    Serial plain is a FIFO queue of one request at a time whose service times
+    are each request's measured wall time as a plain host call (csaw_sample /
+    csaw_walk with host inputs and host results) run alone."""
     import threading
     import torch
-    from paper_2009_09103_gb300 import build, csaw, inputs
-    build.build()
-    torch.cuda.set_device(0)
-    t0 = time.time()
-    scale = args.scale or 26
-    g = inputs.rmat_csr(scale, 16, 255, scale)
-    log(f"[bench] serve: graph s{scale} V={g.V} E={g.E} built in {time.time() - t0:.1f}s")
-    G = csaw.Graph(g.off, g.col, g.w)
-    if args.cdf:
-        G.build_cdf("edge_weight")
-    del g.col
-    reqs = serving_requests(g, args.requests, 5)
-    # serial plain service times
-    svc = []
-    edges = []
     for r in reqs[: min(8, len(reqs))]:   # warm-up
         if r[0] == "sample":
             csaw.sample(G, r[1], r[2], r[3], "edge_weight", r[4])
         else:
             csaw.walk(G, r[1], r[2], "edge_weight", r[3])
     torch.cuda.synchronize()
+    svc, edges = [], []
     for r in reqs:
         t = time.perf_counter()
         if r[0] == "sample":
@@ -879,14 +931,11 @@ def run_serve_bench(args):
     svc = np.array(svc)
     total_edges = int(sum(edges))
     serial_capacity = len(reqs) / svc.sum()
-    serial_seps = total_edges / svc.sum()
     points = []
-    budget = 40 << 30
-    for frac in args.loads:
+    for frac in loads:
         lam = frac * serial_capacity
         rng = np.random.default_rng(int(frac * 1000))
         arrivals = np.cumsum(rng.exponential(1.0 / lam, size=len(reqs)))
-        # serial FIFO queue with the measured service times (one request at a time)
         fin = np.zeros(len(reqs))
         prev = 0.0
         for i in range(len(reqs)):
@@ -894,10 +943,9 @@ def run_serve_bench(args):
             fin[i] = start + svc[i]
             prev = fin[i]
         lat_serial = fin - arrivals
-        srv = csaw.Server(G, budget_bytes=budget, slots=args.slots)
-        # warm every slot (first use of its stream and of the memory pool)
-        # with the largest requests of the mix before the timed arrivals
-        big = sorted(range(len(reqs)), key=lambda i: -edges[i])[: 2 * args.slots]
+        srv = csaw.Server(G, budget_bytes=budget, slots=slots)
+        # warm the server with the largest requests of the mix before the timed arrivals
+        big = sorted(range(len(reqs)), key=lambda i: -edges[i])[: 2 * slots]
         warm = []
         for i in big:
             r = reqs[i]
@@ -907,22 +955,23 @@ def run_serve_bench(args):
             srv.poll(t)
         tickets = [None] * len(reqs)
         base = time.perf_counter() + 0.05
+
         def submitter():
             for i, r in enumerate(reqs):
                 delay = base + arrivals[i] - time.perf_counter()
                 if delay > 0:
                     time.sleep(delay)
                 if r[0] == "sample":
-                    tickets[i] = (srv.submit_sample(r[1], r[2], r[3], "edge_weight", r[4]), time.perf_counter_ns())
+                    tickets[i] = srv.submit_sample(r[1], r[2], r[3], "edge_weight", r[4])
                 else:
-                    tickets[i] = (srv.submit_walk(r[1], r[2], "edge_weight", r[3]), time.perf_counter_ns())
+                    tickets[i] = srv.submit_walk(r[1], r[2], "edge_weight", r[3])
         th = threading.Thread(target=submitter)
         th.start()
         th.join()
         lat = []
         first_sub, last_fin = None, 0
         for i, r in enumerate(reqs):
-            res = srv.poll(tickets[i][0])
+            res = srv.poll(tickets[i])
             lat.append((res.t_finish_ns - res.t_submit_ns) / 1e9)
             first_sub = res.t_submit_ns if first_sub is None else min(first_sub, res.t_submit_ns)
             last_fin = max(last_fin, res.t_finish_ns)
@@ -932,28 +981,79 @@ def run_serve_bench(args):
         slow = np.argsort(-lat)[:3]
         worst = [{"kind": reqs[i][0], "size": int(len(reqs[i][1])), "edges": int(edges[i]),
                   "latency_ms": 1e3 * float(lat[i]), "serial_service_ms": 1e3 * float(svc[i])} for i in slow]
-        points.append({"load_frac_of_serial_capacity": frac, "arrival_rate_per_s": lam,
-                       "served": {"seps": total_edges / span, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
-                                  "p99_ms": 1e3 * float(np.percentile(lat, 99)), "slowest": worst},
-                       "serial_plain": {"seps": total_edges / (fin[-1] - arrivals[0]),
-                                        "p50_ms": 1e3 * float(np.percentile(lat_serial, 50)),
-                                        "p99_ms": 1e3 * float(np.percentile(lat_serial, 99))}})
-        log(f"[bench] load {frac:.2f}: {points[-1]}")
+        pt = {"load_frac_of_serial_capacity": frac, "arrival_rate_per_s": lam,
+              "served": {"seps": total_edges / span, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                         "p99_ms": 1e3 * float(np.percentile(lat, 99)), "slowest": worst},
+              "serial_plain": {"seps": total_edges / (fin[-1] - arrivals[0]),
+                               "p50_ms": 1e3 * float(np.percentile(lat_serial, 50)),
+                               "p99_ms": 1e3 * float(np.percentile(lat_serial, 99))}}
+        pt["served_wins_p99"] = pt["served"]["p99_ms"] <= pt["serial_plain"]["p99_ms"]
+        pt["served_wins_seps"] = pt["served"]["seps"] >= pt["serial_plain"]["seps"]
+        points.append(pt)
+        log(f"[bench] load {frac:.2f}: served {pt['served']['seps'] / 1e6:.1f} M SEPS p50/p99 "
+            f"{pt['served']['p50_ms']:.1f}/{pt['served']['p99_ms']:.1f} ms; serial "
+            f"{pt['serial_plain']['seps'] / 1e6:.1f} M SEPS {pt['serial_plain']['p50_ms']:.1f}/"
+            f"{pt['serial_plain']['p99_ms']:.1f} ms")
+    return {"serial_plain": {"capacity_req_per_s": serial_capacity, "seps": total_edges / svc.sum(),
+                             "service_ms_p50": 1e3 * float(np.percentile(svc, 50)),
+                             "service_ms_p99": 1e3 * float(np.percentile(svc, 99))},
+            "sampled_edges": total_edges, "points": points}
+
+
+def serve_desc(scale, n, slots):
+    return (f"serving: RMAT scale {scale} edge factor 16 resident; {n} requests, 50/50 layered sampling "
+            "(seeds log-uniform [1,16384], depth 1-3, fanout from {5,10,25}) and weighted walks (starts "
+            "log-uniform [1,65536], length U[10,80]); Poisson arrivals; 40 GiB admission budget; "
+            f"{slots} slots")
+
+
+def served_block(args, forms=("streamed", "cached")):
+    """The serving comparison on the resident graph, with the cumulative
+    arrays streamed per selection and cached per edge."""
+    import torch
+    from paper_2009_09103_gb300 import csaw, inputs
+    t0 = time.time()
+    scale = args.serve_scale
+    g = inputs.rmat_csr(scale, 16, 255, scale)
+    log(f"[bench] serve: graph s{scale} V={g.V} E={g.E} built in {time.time() - t0:.1f}s")
+    G = csaw.Graph(g.off, g.col, g.w)
+    V = g.V
+    del g
+    reqs = inputs.serving_requests(V, args.requests, 5)
+    out = {"workload": serve_desc(scale, len(reqs), args.slots)}
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    for form in forms:
+        if form == "cached":
+            G.build_cdf("edge_weight")
+        out[form + "_cumulative_array"] = served_leg(csaw, G, reqs, args.loads, args.slots, 40 << 30)
+        if form == "cached":
+            G.drop_cdf("edge_weight")
+    clk = clocks.stop()
     G.close()
-    best = max(points, key=lambda p: p["served"]["seps"])
+    if clk:
+        out["clocks"] = clk
+    return out
+
+
+def run_serve_bench(args):
+    import torch
+    from paper_2009_09103_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    args.serve_scale = args.scale or 26
+    blk = served_block(args, ("cached",) if args.cdf else ("streamed",))
+    leg = blk["cached_cumulative_array" if args.cdf else "streamed_cumulative_array"]
+    best = max(leg["points"], key=lambda p: p["served"]["seps"])
     return {
         "metric": METRIC + " and p50/p99 request latency", "value": best["served"]["seps"], "unit": "edges/s",
         "n_gpus": 1, "steps": len(args.loads), "warmup": 1, "ms_per_step": None, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32 biases / u64 prefix sums",
         "data": "synthetic (seeded RMAT, seeded request mix)",
-        "config": {"workload": f"serving: RMAT scale {scale} edge factor 16 resident; {len(reqs)} requests, "
-                               "50/50 layered sampling (seeds log-uniform [1,16384], depth 1-3, fanout from "
-                               "{5,10,25}) and weighted walks (starts log-uniform [1,65536], length U[10,80]); "
-                               f"Poisson arrivals; 40 GiB admission budget; {args.slots} slots; cumulative "
-                               f"array {'cached per edge' if args.cdf else 'computed per selection'}",
-                   "sampled_edges": total_edges},
-        "serial_plain": {"capacity_req_per_s": serial_capacity, "seps": serial_seps},
-        "points": points,
+        "config": {"workload": blk["workload"] + "; cumulative array "
+                   + ("cached per edge" if args.cdf else "computed per selection"),
+                   "sampled_edges": leg["sampled_edges"]},
+        **leg,
     }
 
 
@@ -974,8 +1074,12 @@ def main():
                     help="walks: skip the cached-array variant measured after the main line")
     ap.add_argument("--cdf", action="store_true",
                     help="build the cached per-edge cumulative array of the static bias first")
-    ap.add_argument("--plain-instances", type=int, default=512,
-                    help="batched_s24: instances timed one call each (a uniform subset)")
+    ap.add_argument("--plain-instances", type=int, default=4096,
+                    help="batched: instances timed one call each (a uniform subset when fewer than all)")
+    ap.add_argument("--batched-steps", type=int, default=2, help="batched block: timed plan runs per form")
+    ap.add_argument("--serve-scale", type=int, default=26, help="served block: RMAT scale of the graph")
+    ap.add_argument("--no-batched", action="store_true", help="default run: skip the batched block")
+    ap.add_argument("--no-served", action="store_true", help="default run: skip the served block")
     ap.add_argument("--instances", type=int, default=4096, help="batched_s24 at another --scale")
     ap.add_argument("--requests", type=int, default=200, help="serve: requests per load point")
     ap.add_argument("--slots", type=int, default=8, help="serve: server slots")
@@ -1021,6 +1125,14 @@ def main():
         result["cpu_baseline_all_cores"] = {"value": v, "unit": "edges/s", "cores": cores, "kind": "oracle",
                                             "sample": f"{used} walkers in {cores} disjoint shards, one copy "
                                                       f"of the oracle per core, {t:.1f} s"}
+    if rank == 0 and world == 1:
+        # the batched and served forms against plain one-call-per-request
+        # sampling, on their own configurations (RMAT s24 and s26)
+        del g, wl
+        if not args.no_batched:
+            result["batched"] = batched_block(args)
+        if not args.no_served:
+            result["served"] = served_block(args)
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:

@@ -544,7 +544,8 @@ csaw_status csaw_server_stats(csaw_server* s, csaw_server_stats_t* out);
  * Limits: n <= CSAW_NOALLOC_MAX_ITEMS; a graph whose maximum degree needs more
  * than the scratch left for one CTA's cumulative array (about 5.5 million
  * neighbours) is rejected.  Errors: CSAW_ERR_INVALID (limits, NULL arrays,
- * a vertex outside the graph, node2vec bias), CSAW_ERR_CUDA.
+ * a vertex outside the graph, node2vec bias, a current device other than the
+ * graph's), CSAW_ERR_CUDA.  n = 0 is valid: out_offsets[0] is set to 0.
  * The call issues work on `stream` and waits once, after checking the
  * vertices, before it launches the selection.  It calls no cudaMalloc,
  * cudaFree or other allocating routine.  The first call made on a device

@@ -1997,6 +1997,9 @@ extern "C" csaw_status csaw_select_noalloc(csaw_graph* g, const uint32_t* vertic
                     (unsigned long long)capacity, (unsigned long long)((uint64_t)n * per));
     int device = 0;
     CSAW_CUDA(cudaGetDevice(&device));
+    if (device != g->device)
+        return fail(CSAW_ERR_INVALID, "the current device (%d) is not the graph's device (%d)", device,
+                    g->device);
     int sel_blocks = select_blocks(kind, g->sm_count);
     if (g->max_degree > CTA_SMEM_DEG) {
         const uint64_t slot = (uint64_t)g->max_degree * 8 + ((uint64_t)g->max_degree + 31) / 32 * 4;

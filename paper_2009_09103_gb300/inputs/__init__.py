@@ -239,3 +239,33 @@ def workload_batched_s24(graph_seed: int = 24, n_inst: int = 4096) -> SampleWork
     sizes = loguniform_sizes(n_inst, 6.0, 7.0, graph_seed, stream=4)
     seeds, offs = distinct_seeds(sizes, g.V, graph_seed, stream=4)
     return SampleWorkload(g, seeds, offs, [25, 10], "neighbor_degree", 4)
+
+
+def serving_requests(V: int, n: int, seed: int = 5):
+    """The serving mix on a graph of V vertices: n requests alternating
+    layered sampling and weighted walks.  Sampling: one instance of
+    floor(2^(14u)) seeds (at least 1, uniform over the vertices), depth 1-3,
+    fanout per layer from {5, 10, 25}, Philox seed 100 + i.  Walks:
+    floor(2^(16u)) starts (at least 1, uniform), length uniform in [10, 80],
+    Philox seed 200 + i.  Returns tuples ("sample", seeds, inst_offsets,
+    fanout, rng_seed) and ("walk", starts, length, rng_seed)."""
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(n):
+        if i % 2 == 0:
+            ns = max(1, int(2 ** (14 * rng.random())))
+            seeds = uniform_vertices(ns, V, 10_000 + i)
+            depth = int(rng.integers(1, 4))
+            fan = [int(x) for x in rng.choice([5, 10, 25], size=depth)]
+            reqs.append(("sample", seeds, np.array([0, ns], dtype=np.uint64), fan, 100 + i))
+        else:
+            nw = max(1, int(2 ** (16 * rng.random())))
+            starts = uniform_vertices(nw, V, 20_000 + i)
+            reqs.append(("walk", starts, int(rng.integers(10, 81)), 200 + i))
+    return reqs
+
+
+def workload_serve_s26(graph_seed: int = 26) -> CSRGraph:
+    """The serving graph: RMAT s26 ef16 (about 2.1 billion directed edges),
+    weights uniform in [1, 255]; requests come from serving_requests."""
+    return rmat_csr(26, 16, 255, graph_seed)

@@ -113,3 +113,20 @@ def test_walk_sector_bytes_match_a_direct_count():
             wsec = {(4 * e + k) // 32 for e in range(off[a], off[a + 1]) for k in range(4)}
             total += 32 * (len(sectors) + len(wsec) + 1)
     assert bench.walk_sector_bytes(torch, torch.from_numpy(off), torch.from_numpy(path.view(np.int32))) == total
+
+
+def test_roofline_block_is_dram_based():
+    """frac is the DRAM fraction: ncu DRAM bytes per launch / event time /
+    measured HBM peak; the method's L2-inclusive bytes are reported apart."""
+    bench = _bench_module()
+    peak, _ = bench.measured_peaks()
+    tr = {"traffic_bytes_per_launch": 45_000_000_000, "ncu_duration_ns": 39_000_000, "l2_hit_rate_pct": 91.0}
+    blk = bench.roofline_block("k", tr, 40.0, 460_000_000_000, 463_000_000_000)
+    assert blk["bound"] == "hbm" and blk["traffic"] == tr["traffic_bytes_per_launch"]
+    assert abs(blk["achieved"] - 45e9 / 0.040 / 1e9) < 0.1
+    assert abs(blk["frac"] - blk["achieved"] / peak) < 1e-4 and blk["frac"] < 1.2
+    assert blk["l2_inclusive"]["algorithmic_bytes_per_launch"] == 460_000_000_000
+    assert blk["l2_inclusive"]["sector_bytes_per_launch"] == 463_000_000_000
+    assert blk["l2_hit_rate_pct"] == 91.0
+    none = bench.roofline_block("k", None, 40.0, 1000)
+    assert none["frac"] is None and none["traffic"] is None

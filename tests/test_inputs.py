@@ -105,3 +105,20 @@ def test_workloads_mdrw_and_layer_s20_shape():
     for i in range(0, 2000, 97):
         assert len(set(wl.seeds[io[i]:io[i + 1]].tolist())) == 64
     assert np.array_equal(inputs.workload_layer_s20().seeds, wl.seeds)
+
+
+def test_serving_requests_mix():
+    """The serving mix alternates sampling and walks with the stated size
+    ranges, and is a pure function of its seed."""
+    a = inputs.serving_requests(1 << 20, 40, 5)
+    b = inputs.serving_requests(1 << 20, 40, 5)
+    assert [r[0] for r in a] == ["sample", "walk"] * 20
+    for ra, rb in zip(a, b):
+        assert ra[0] == rb[0] and np.array_equal(ra[1], rb[1])
+    for r in a:
+        assert r[1].max() < (1 << 20)
+        if r[0] == "sample":
+            assert 1 <= len(r[1]) <= 16384 and list(r[2]) == [0, len(r[1])]
+            assert 1 <= len(r[3]) <= 3 and set(r[3]) <= {5, 10, 25}
+        else:
+            assert 1 <= len(r[1]) <= 65536 and 10 <= r[2] <= 80

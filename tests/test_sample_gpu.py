@@ -171,25 +171,70 @@ def instance_subset_oracle(g, seeds, io, pick, fanout, bias, seed):
     return oracle.sample(g, np.concatenate(parts), sub_io, fanout, bias, seed)
 
 
-def test_sample_batched_s24_subset(csaw):
+@pytest.fixture(scope="module")
+def s24():
     """4096 instances of log-uniform [64, 8192) seeds on RMAT s24 ef16, fanout
-    [25, 10], neighbour-degree bias: the full batched run, checked against the
-    oracle on a subset of instances and by invariants."""
-    wl = inputs.workload_batched_s24()
+    [25, 10], neighbour-degree bias."""
+    return inputs.workload_batched_s24()
+
+
+def s24_pick(wl, g):
+    """A stratified instance subset: the smallest and largest instances, the
+    instance holding the highest-degree seed, fixed ids and a uniform sample."""
+    n = len(wl.inst_offsets) - 1
+    sizes = np.diff(wl.inst_offsets).astype(np.int64)
+    deg = np.diff(g.off).astype(np.int64)
+    hub_seed = int(np.argmax(deg[wl.seeds.astype(np.int64)]))
+    hub_inst = int(np.searchsorted(wl.inst_offsets, hub_seed, side="right")) - 1
+    rnd = inputs.uniform_vertices(4, n, 41).astype(np.int64)
+    return sorted(set([int(np.argmin(sizes)), int(np.argmax(sizes)), hub_inst, 17, 2048, n - 1]
+                      + rnd.tolist()))
+
+
+def check_subset(res, ref, n, pick, depth):
+    for lvl in range(depth):
+        for i in pick:
+            a0, a1 = res.edge_offsets[lvl * n + i], res.edge_offsets[lvl * n + i + 1]
+            b0, b1 = ref["edge_off"][lvl * n + i], ref["edge_off"][lvl * n + i + 1]
+            assert np.array_equal(res.dst[a0:a1], ref["dst"][b0:b1]), (lvl, i)
+            assert np.array_equal(res.src[a0:a1], ref["src"][b0:b1]), (lvl, i)
+            assert res.frontier_sizes[lvl * n + i] == ref["fsize"][lvl * n + i]
+
+
+def test_sample_batched_s24_subset(csaw, s24):
+    """The full batched csaw_sample run, checked against the oracle on a
+    stratified subset of instances and by invariants."""
+    wl = s24
     g = wl.graph
     G = csaw.Graph(g.off, g.col, g.w)
     res = csaw.sample(G, wl.seeds, wl.inst_offsets, wl.fanout, wl.bias, wl.rng_seed)
     n = len(wl.inst_offsets) - 1
-    sizes = np.diff(wl.inst_offsets)
-    pick = [int(np.argmin(sizes)), 17, 2048, n - 1]
+    pick = s24_pick(wl, g)
     ref = instance_subset_oracle(g, wl.seeds, wl.inst_offsets, pick, wl.fanout, wl.bias, wl.rng_seed)
-    for lvl in range(2):
-        for i in pick:
-            a0, a1 = res.edge_offsets[lvl * n + i], res.edge_offsets[lvl * n + i + 1]
-            b0, b1 = ref["edge_off"][lvl * n + i], ref["edge_off"][lvl * n + i + 1]
-            assert np.array_equal(res.dst[a0:a1], ref["dst"][b0:b1])
-            assert np.array_equal(res.src[a0:a1], ref["src"][b0:b1])
-            assert res.frontier_sizes[lvl * n + i] == ref["fsize"][lvl * n + i]
+    check_subset(res, ref, n, pick, 2)
     # layer 0 frontier sizes are the distinct seeds
-    assert np.array_equal(res.frontier_sizes[:n], sizes)
+    assert np.array_equal(res.frontier_sizes[:n], np.diff(wl.inst_offsets))
+    G.close()
+
+
+def test_sample_plan_batched_s24_subset(csaw, s24):
+    """The batched plan (one CUDA graph over all 4096 instances and both
+    layers) -- the launch the batched throughput is measured on -- against
+    the oracle on a stratified instance subset, and against csaw_sample on
+    its whole output."""
+    wl = s24
+    g = wl.graph
+    G = csaw.Graph(g.off, g.col, g.w)
+    n = len(wl.inst_offsets) - 1
+    plan = csaw.SamplePlan(G, n, len(wl.seeds), wl.fanout, wl.bias)
+    plan.run(wl.seeds, wl.inst_offsets, wl.rng_seed)
+    res = plan.result()
+    pick = s24_pick(wl, g)
+    ref = instance_subset_oracle(g, wl.seeds, wl.inst_offsets, pick, wl.fanout, wl.bias, wl.rng_seed)
+    check_subset(res, ref, n, pick, 2)
+    plan.close()
+    whole = csaw.sample(G, wl.seeds, wl.inst_offsets, wl.fanout, wl.bias, wl.rng_seed)
+    assert np.array_equal(res.edge_offsets, whole.edge_offsets)
+    assert np.array_equal(res.frontier_sizes, whole.frontier_sizes)
+    assert np.array_equal(res.src, whole.src) and np.array_equal(res.dst, whole.dst)
     G.close()

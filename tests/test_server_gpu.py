@@ -1,10 +1,9 @@
 """The request server: admission by memory budget, concurrent slots, and
-results identical alone and in the mix."""
-import time
-
+results identical alone, in the mix and to the oracle."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_2009_09103_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -60,9 +59,15 @@ def test_results_same_alone_and_in_the_mix(env):
             alone = csaw.sample(G, r[1], r[2], r[3], "edge_weight", r[4])
             assert np.array_equal(s.sample.dst, alone.dst) and np.array_equal(s.sample.src, alone.src)
             assert np.array_equal(s.sample.edge_offsets, alone.edge_offsets)
+            ref = oracle.sample(g, r[1], r[2], r[3], "edge_weight", r[4])
+            assert np.array_equal(s.sample.src, ref["src"]) and np.array_equal(s.sample.dst, ref["dst"])
+            assert np.array_equal(s.sample.edge_offsets, ref["edge_off"])
+            n_inst = len(r[2]) - 1
+            assert np.array_equal(s.sample.frontier_sizes, ref["fsize"][: len(r[3]) * n_inst])
         else:
             alone = csaw.walk(G, r[1], r[2], "edge_weight", r[3])
             assert np.array_equal(s.path, alone)
+            assert np.array_equal(s.path, oracle.walk(g, r[1], r[2], "edge_weight", r[3]))
         assert s.t_submit_ns <= s.t_admit_ns <= s.t_start_ns <= s.t_finish_ns
 
 

@@ -42,21 +42,23 @@ def first_layer(seeds, io):
     return np.concatenate(vs).astype(np.uint32), np.concatenate(ins)
 
 
-def noalloc(torch, csaw, L, G, vs, ins, k, bias, seed):
+def noalloc(torch, csaw, L, G, vs, ins, k, bias, seed, expect=0):
     n = len(vs)
     cap = n * min(k, G.info().max_degree)
     dv = torch.from_numpy(vs.view(np.int32)).cuda()
     di = torch.from_numpy(ins.view(np.int32)).cuda()
     src = torch.empty(max(cap, 1), dtype=torch.int32, device="cuda")
     dst = torch.empty(max(cap, 1), dtype=torch.int32, device="cuda")
-    off = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    off = torch.full((n + 1,), -1, dtype=torch.int64, device="cuda")
     b = csaw.make_bias(bias)
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     st = L.csaw_select_noalloc(G.handle, ctypes.c_void_p(dv.data_ptr()), ctypes.c_void_p(di.data_ptr()),
                                n, k, 0, ctypes.byref(b), seed, ctypes.c_void_p(src.data_ptr()),
                                ctypes.c_void_p(dst.data_ptr()), cap, ctypes.c_void_p(off.data_ptr()), stream)
-    assert st == 0, L.csaw_last_error()
+    assert st == expect, L.csaw_last_error()
     torch.cuda.synchronize()
+    if expect != 0:
+        return None
     o = off.cpu().numpy().view(np.uint64)
     total = int(o[-1])
     return (src[:total].cpu().numpy().view(np.uint32), dst[:total].cpu().numpy().view(np.uint32), o)
@@ -106,4 +108,33 @@ def test_noalloc_rejects_oversized_requests(env):
                                too_many * 5, p, None)
     assert st == csaw.ERR_INVALID
     assert b"at most" in L.csaw_last_error()
+    G.close()
+
+
+def test_noalloc_edge_cases(env):
+    """A vertex outside the graph is refused and leaves the next call intact;
+    an empty call writes out_offsets[0] = 0; k = CSAW_FANOUT_ALL takes every
+    neighbour as csaw_sample does."""
+    torch, csaw, L = env
+    g = inputs.rmat_csr(12, 16, 100, 12)
+    G = csaw.Graph(g.off, g.col, g.w)
+    seeds = inputs.uniform_vertices(300, g.V, 4)
+    io = np.array([0, 100, 300], dtype=np.uint64)
+    vs, ins = first_layer(seeds, io)
+    bad = vs.copy()
+    bad[len(bad) // 2] = g.V
+    assert noalloc(torch, csaw, L, G, bad, ins, 5, "edge_weight", 3, expect=csaw.ERR_INVALID) is None
+    assert b"not in the graph" in L.csaw_last_error()
+    ref = csaw.sample(G, seeds, io, [5], "edge_weight", 3)
+    src, dst, _ = noalloc(torch, csaw, L, G, vs, ins, 5, "edge_weight", 3)
+    assert np.array_equal(src, ref.src) and np.array_equal(dst, ref.dst)
+    empty = np.zeros(0, dtype=np.uint32)
+    src, dst, off = noalloc(torch, csaw, L, G, empty, empty, 5, "edge_weight", 3)
+    assert len(src) == 0 and off.tolist() == [0]
+    ALL = 0xFFFFFFFF
+    for bias in ("edge_weight", "neighbor_degree"):
+        ref = csaw.sample(G, seeds, io, [ALL], bias, 8)
+        src, dst, off = noalloc(torch, csaw, L, G, vs, ins, ALL, bias, 8)
+        assert np.array_equal(src, ref.src) and np.array_equal(dst, ref.dst)
+        assert int(off[-1]) == int(np.diff(g.off)[vs.astype(np.int64)].sum())
     G.close()
