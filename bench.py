@@ -36,6 +36,11 @@ METRIC = "SEPS (sampled edges per second)"
 L2_FLUSH_BYTES = 512 << 20
 
 
+def jdump(obj) -> str:
+    """One JSON line; numpy scalars become Python numbers."""
+    return json.dumps(obj, default=lambda o: o.item() if hasattr(o, "item") else str(o))
+
+
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
@@ -211,6 +216,21 @@ def node2vec_bytes(torch, off_t, path):
                      + 4 * n + 4 * n * row + 16 * n_dead)
 
 
+def cached_walk_bytes(torch, off_t, path, length):
+    """Algorithmic bytes of one walk launch over the cached cumulative array:
+    per step 16 (row offsets) + 8 (row total) + 8 per binary-search probe
+    (ceil(log2 d) probes) + 4 (picked column) + 4 (path entry); per walker 4
+    (start) and 4 * (L + 1) (its path row)."""
+    p = path.to(torch.int64) & 0xFFFFFFFF
+    a, b = p[:, :-1], p[:, 1:]
+    real = b != 0xFFFFFFFF
+    n_trans = int(real.sum())
+    deg = (off_t[1:] - off_t[:-1])[a[real]].to(torch.float64)
+    probes = int(torch.ceil(torch.log2(deg.clamp(min=1))).sum())
+    n = path.shape[0]
+    return 16 * n_trans + 8 * n_trans + 8 * probes + 8 * n_trans + 4 * n + 4 * n * (length + 1)
+
+
 def walk_workload(args):
     from paper_2009_09103_gb300 import inputs
     if args.workload == "node2vec":
@@ -312,14 +332,7 @@ def run_walk_bench(args, rank, world):
     kname = "walk_kernel<NODE2VEC>" if wl.bias == "node2vec" else "walk_kernel<EDGE_WEIGHT>"
     if args.cdf and wl.bias != "node2vec":
         kname = "walk_cached_kernel<EDGE_WEIGHT>"
-        # per step: 16 (row offsets) + 8 (row total) + 8 per binary-search probe
-        # (ceil(log2 d) probes) + 4 (picked column) + 4 (path entry)
-        p = path.to(torch.int64) & 0xFFFFFFFF
-        a, b = p[:, :-1], p[:, 1:]
-        real = b != 0xFFFFFFFF
-        deg = (off_t[1:] - off_t[:-1])[a[real]].to(torch.float64)
-        probes = int(torch.ceil(torch.log2(deg.clamp(min=1))).sum())
-        alg_bytes = 16 * n_trans + 8 * n_trans + 8 * probes + 8 * n_trans + 4 * n + 4 * n * (wl.length + 1)
+        alg_bytes = cached_walk_bytes(torch, off_t, path, wl.length)
     roofline = roofline_block(kname, tr, ms_per_step, alg_bytes,
                               sector_bytes if (sector_bytes is not None and not args.cdf) else None)
     result = {
@@ -365,7 +378,10 @@ def run_walk_bench(args, rank, world):
         result["variant_cached_cumulative_array"] = {
             "value": n_trans * world / (ms2 / 1e3), "unit": "edges/s", "ms_per_step": ms2,
             "kernel": "walk_cached_kernel", "build_ms_once_per_graph": build_ms,
-            "extra_device_bytes": 8 * (g.E + 16), "identical_paths": same}
+            "extra_device_bytes": 8 * (g.E + 16), "identical_paths": same,
+            "roofline": roofline_block("walk_cached_kernel<EDGE_WEIGHT>",
+                                       traffic_record("csaw_walk.cu", f"walk_s{args.scale}_cdf"), ms2,
+                                       cached_walk_bytes(torch, off_t, path2, wl.length))}
         G.drop_cdf(wl.bias)
         result["gpu_launches_variant"] = args.steps
     G.close()
@@ -987,8 +1003,8 @@ def served_leg(csaw, G, reqs, loads, slots, budget):
               "serial_plain": {"seps": total_edges / (fin[-1] - arrivals[0]),
                                "p50_ms": 1e3 * float(np.percentile(lat_serial, 50)),
                                "p99_ms": 1e3 * float(np.percentile(lat_serial, 99))}}
-        pt["served_wins_p99"] = pt["served"]["p99_ms"] <= pt["serial_plain"]["p99_ms"]
-        pt["served_wins_seps"] = pt["served"]["seps"] >= pt["serial_plain"]["seps"]
+        pt["served_wins_p99"] = bool(pt["served"]["p99_ms"] <= pt["serial_plain"]["p99_ms"])
+        pt["served_wins_seps"] = bool(pt["served"]["seps"] >= pt["serial_plain"]["seps"])
         points.append(pt)
         log(f"[bench] load {frac:.2f}: served {pt['served']['seps'] / 1e6:.1f} M SEPS p50/p99 "
             f"{pt['served']['p50_ms']:.1f}/{pt['served']['p99_ms']:.1f} ms; serial "
@@ -1095,7 +1111,7 @@ def main():
                run_mdrw_bench(args) if args.workload == "mdrw" else
                run_oom_bench(args) if args.workload == "oom" else
                run_layer_bench(args) if args.workload == "layer" else run_sample_bench(args))
-        print(json.dumps(res), flush=True)
+        print(jdump(res), flush=True)
         return
 
     if args.impl == "reference":
@@ -1104,7 +1120,7 @@ def main():
             dist.init_process_group("gloo")
         res = run_reference(args, rank, world)
         if rank == 0:
-            print(json.dumps(res), flush=True)
+            print(jdump(res), flush=True)
         if world > 1:
             dist.barrier()
             dist.destroy_process_group()
@@ -1134,7 +1150,7 @@ def main():
         if not args.no_served:
             result["served"] = served_block(args)
     if rank == 0:
-        print(json.dumps(result), flush=True)
+        print(jdump(result), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 

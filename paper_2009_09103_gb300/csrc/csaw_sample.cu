@@ -76,6 +76,13 @@ struct SelParams {
     const uint64_t* __restrict__ cdf;     // cached cumulative array (select_cdf_kernel)
     bool skip_warp_items;                 // warp items are served by select_cdf_kernel
     uint32_t attempt_cap;                 // repeated-sampling attempts before updated sampling
+    // shared hub arrays of the layer (select_cdf_kernel over hub items):
+    // item q is frontier entry item_e[q] of distinct hub item_h[q], whose
+    // prefix sums are hubS[hub_off[h] ..]; null outside that mode
+    const uint32_t* __restrict__ item_e = nullptr;
+    const uint32_t* __restrict__ item_h = nullptr;
+    const uint64_t* __restrict__ hub_off = nullptr;
+    const uint64_t* __restrict__ hubS = nullptr;
 };
 
 template <int KIND>
@@ -365,13 +372,15 @@ __global__ void __launch_bounds__(SEL_THREADS) select_cdf_kernel(SelParams p)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint32_t* picks = s_picks[wid];
     const uint32_t lt = lanemask_lt();
-    const unsigned long long n_warp = p.n_items[0];
+    const bool hub = p.hub_off != nullptr;
+    const unsigned long long n_warp = hub ? p.n_items[2] : p.n_items[0];
+    unsigned long long* counter = hub ? p.next + 2 : p.next;
     while (true) {
         unsigned long long it = 0;
-        if (lane == 0) it = atomicAdd(p.next, 1ull);
+        if (lane == 0) it = atomicAdd(counter, 1ull);
         it = __shfl_sync(CSAW_FULL_MASK, it, 0);
         if (it >= n_warp) break;
-        const uint32_t e = p.warp_list[it];
+        const uint32_t e = hub ? p.item_e[it] : p.warp_list[it];
         const uint64_t key = p.fkeys[e];
         const uint32_t v = (uint32_t)(key & p.vmask);
         const uint32_t inst = (uint32_t)(key >> p.vbits);
@@ -384,7 +393,7 @@ __global__ void __launch_bounds__(SEL_THREADS) select_cdf_kernel(SelParams p)
             for (uint32_t j = lane; j < d; j += 32) emit(p, q0 + j, v, inst, __ldg(p.col + beg + j));
             continue;
         }
-        const uint64_t* row = p.cdf ? p.cdf + beg : nullptr;
+        const uint64_t* row = hub ? p.hubS + p.hub_off[p.item_h[it]] : p.cdf ? p.cdf + beg : nullptr;
         const uint64_t T = cdf_at(row, IMPLICIT, d - 1);
         uint32_t have = 0, a0 = 0;
         while (have < cnt && a0 < p.attempt_cap) {
@@ -476,7 +485,10 @@ struct CountParams {
     uint32_t* __restrict__ cnt;
     uint32_t* __restrict__ warp_list;
     uint32_t* __restrict__ cta_list;
-    unsigned long long* n_items;   // [0] warp, [1] CTA
+    unsigned long long* n_items;   // [0] warp, [1] CTA, [2] hub
+    // hub items (degree above theta_w, at most PICK_MAX picks) when the layer
+    // shares one cumulative array per distinct hub; null: they are CTA items
+    uint32_t* __restrict__ hub_list = nullptr;
 };
 
 // Number of positive biases of v's neighbours (only when zeros are possible).
@@ -524,22 +536,220 @@ __global__ void count_kernel(CountParams p)
         const uint32_t c = min(p.k, npos);
         const bool take_all = npos <= p.k;
         const bool to_warp = e < n && c > 0 && (take_all || (p.cached ? c <= PICK_MAX : d <= p.theta_w));
-        const bool to_cta = e < n && c > 0 && !to_warp;
+        const bool to_hub = e < n && c > 0 && !to_warp && p.hub_list != nullptr && c <= PICK_MAX;
+        const bool to_cta = e < n && c > 0 && !to_warp && !to_hub;
         if (e < n) p.cnt[e] = c;
         // warp-aggregated appends
         const uint32_t bw = __ballot_sync(CSAW_FULL_MASK, to_warp);
         const uint32_t bc = __ballot_sync(CSAW_FULL_MASK, to_cta);
-        unsigned long long basew = 0, basec = 0;
+        const uint32_t bh = __ballot_sync(CSAW_FULL_MASK, to_hub);
+        unsigned long long basew = 0, basec = 0, baseh = 0;
         if (lane == 0) {
             if (bw) basew = atomicAdd(p.n_items, (unsigned long long)__popc(bw));
             if (bc) basec = atomicAdd(p.n_items + 1, (unsigned long long)__popc(bc));
+            if (bh) baseh = atomicAdd(p.n_items + 2, (unsigned long long)__popc(bh));
         }
         basew = __shfl_sync(CSAW_FULL_MASK, basew, 0);
         basec = __shfl_sync(CSAW_FULL_MASK, basec, 0);
+        baseh = __shfl_sync(CSAW_FULL_MASK, baseh, 0);
         const uint32_t lt = lanemask_lt();
         if (to_warp) p.warp_list[basew + __popc(bw & lt)] = (uint32_t)e;
         if (to_cta) p.cta_list[basec + __popc(bc & lt)] = (uint32_t)e;
+        if (to_hub) p.hub_list[baseh + __popc(bh & lt)] = (uint32_t)e;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Shared hub arrays.  With a static bias the cumulative array of a vertex is
+// the same for every instance (the draws differ, the biases do not), and
+// under neighbour-degree bias the same hubs recur in the frontiers of
+// thousands of instances.  So the layer's hub items (degree above theta_w)
+// are grouped by vertex: the distinct hub vertices H[h] get consecutive
+// ranges hubS[hub_off[h] .. hub_off[h] + d) of one scratch array, each
+// vertex's inclusive prefix sums are built there once, and every (instance,
+// hub) item draws from them by binary search (select_cdf_kernel in hub
+// mode).  Same prefix sums, same draws: the picks are unchanged.
+
+// keys[j] = e << vbits | v for hub item j (entry e at vertex v); sorted on
+// their low vbits bits by the stable radix sort, items of one vertex end up
+// adjacent and in entry order.
+__global__ void hub_keys_kernel(const uint32_t* __restrict__ hub_list, const unsigned long long* n_dev,
+                                const uint64_t* __restrict__ fkeys, uint64_t vmask, uint32_t vbits,
+                                uint64_t* __restrict__ keys)
+{
+    const uint64_t n = *n_dev;
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t e = hub_list[j];
+        keys[j] = ((uint64_t)e << vbits) | (fkeys[e] & vmask);
+    }
+}
+
+// flag[q] = 1 where a new vertex starts in the sorted keys.
+__global__ void hub_flag_kernel(const uint64_t* __restrict__ sorted, const unsigned long long* n_dev,
+                                uint64_t vmask, uint32_t* __restrict__ flag)
+{
+    const uint64_t n = *n_dev;
+    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (uint64_t)gridDim.x * blockDim.x)
+        flag[q] = (q == 0 || ((sorted[q] ^ sorted[q - 1]) & vmask) != 0) ? 1u : 0u;
+}
+
+constexpr uint32_t HUB_WARP_DEG = 2048;   // hubs up to this degree: one warp builds each
+
+// Item q: its entry and its hub index (hpos = exclusive scan of flag); the
+// first item of each vertex records the distinct hub and its degree, and
+// lists the hub for a whole CTA when it is above HUB_WARP_DEG.
+__global__ void hub_items_kernel(const uint64_t* __restrict__ sorted, const unsigned long long* n_dev,
+                                 const uint32_t* __restrict__ flag, const uint64_t* __restrict__ hpos,
+                                 uint64_t vmask, uint32_t vbits, const uint64_t* __restrict__ off,
+                                 uint32_t* __restrict__ item_e, uint32_t* __restrict__ item_h,
+                                 uint32_t* __restrict__ H, uint32_t* __restrict__ dh,
+                                 uint32_t* __restrict__ big_list, unsigned long long* n_big)
+{
+    const uint64_t n = *n_dev;
+    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t key = sorted[q];
+        const uint32_t v = (uint32_t)(key & vmask);
+        const uint32_t h = (uint32_t)(hpos[q] + flag[q] - 1);
+        item_e[q] = (uint32_t)(key >> vbits);
+        item_h[q] = h;
+        if (flag[q]) {
+            const uint32_t d = (uint32_t)(__ldg(off + v + 1) - __ldg(off + v));
+            H[h] = v;
+            dh[h] = d;
+            if (d > HUB_WARP_DEG) big_list[atomicAdd(n_big, 1ull)] = h;
+        }
+    }
+}
+
+struct HubBuildParams {
+    const uint64_t* __restrict__ off;
+    const uint32_t* __restrict__ col;
+    const uint32_t* __restrict__ w;
+    const uint32_t* __restrict__ deg;
+    const uint32_t* __restrict__ H;
+    const uint32_t* __restrict__ dh;
+    const uint64_t* __restrict__ hub_off;
+    const unsigned long long* nh;    // distinct hubs
+    const uint32_t* __restrict__ big_list;
+    const unsigned long long* n_big; // hubs above HUB_WARP_DEG
+    unsigned long long* next;        // [0] CTA counter, [1] warp counter
+    uint64_t* __restrict__ S;
+};
+
+// Bias of edge e (static kinds).
+template <int KIND>
+__device__ __forceinline__ uint32_t hub_bias(const HubBuildParams& p, uint64_t e)
+{
+    if constexpr (KIND == CSAW_BIAS_EDGE_WEIGHT) return __ldg(p.w + e);
+    else return __ldg(p.deg + __ldg(p.col + e));
+}
+
+// Inclusive prefix sums of the biases of row [beg, beg + d) into out, by one
+// warp: rounds of 256 neighbours, eight per lane in lane-interleaved tiles.
+template <int KIND>
+__device__ void hub_row_scan_warp(const HubBuildParams& p, uint64_t beg, uint32_t d, uint64_t* out, int lane)
+{
+    uint64_t carry = 0;
+    for (uint32_t base = 0; base < d; base += 256) {
+        uint32_t b[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const uint32_t j = base + 32u * t + lane;
+            b[t] = j < d ? hub_bias<KIND>(p, beg + j) : 0u;
+        }
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const uint64_t incl = warp_inclusive_scan_u64(b[t], lane) + carry;
+            const uint32_t j = base + 32u * t + lane;
+            if (j < d) out[j] = incl;
+            carry = __shfl_sync(CSAW_FULL_MASK, incl, 31);
+        }
+    }
+}
+
+// One kernel for all distinct hubs of the layer: CTAs first take the hubs
+// above HUB_WARP_DEG from their list (eight warps scan 2048-neighbour tiles,
+// segment offsets added in warp order, as in cta_item), then every warp
+// takes the smaller hubs one at a time.  Work is claimed from two counters.
+template <int KIND>
+__global__ void __launch_bounds__(SEL_THREADS) hub_cdf_kernel(HubBuildParams p)
+{
+    __shared__ uint64_t s_wsum[SEL_WARPS];
+    __shared__ unsigned long long s_item;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned long long nh = *p.nh, n_big = *p.n_big;
+    while (true) {
+        if (threadIdx.x == 0) s_item = atomicAdd(p.next, 1ull);
+        __syncthreads();
+        const unsigned long long it = s_item;
+        __syncthreads();
+        if (it >= n_big) break;
+        const uint32_t h = p.big_list[it];
+        const uint32_t d = p.dh[h];
+        const uint64_t beg = __ldg(p.off + p.H[h]);
+        uint64_t* out = p.S + p.hub_off[h];
+        uint64_t carry = 0;
+        for (uint32_t base = 0; base < d; base += SEL_WARPS * 256u) {
+            const uint32_t seg = base + (uint32_t)wid * 256u;
+            uint32_t b[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const uint32_t j = seg + 32u * t + lane;
+                b[t] = j < d ? hub_bias<KIND>(p, beg + j) : 0u;
+            }
+            uint64_t incl[8];
+            uint64_t run = 0;
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                incl[t] = warp_inclusive_scan_u64(b[t], lane) + run;
+                run = __shfl_sync(CSAW_FULL_MASK, incl[t], 31);
+            }
+            if (lane == 0) s_wsum[wid] = run;
+            __syncthreads();
+            uint64_t offw = carry, tile = 0;
+#pragma unroll
+            for (int w2 = 0; w2 < SEL_WARPS; ++w2) {
+                const uint64_t sw = s_wsum[w2];
+                if (w2 < wid) offw += sw;
+                tile += sw;
+            }
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const uint32_t j = seg + 32u * t + lane;
+                if (j < d) out[j] = offw + incl[t];
+            }
+            carry += tile;
+            __syncthreads();
+        }
+    }
+    // small hubs: one warp each
+    while (true) {
+        unsigned long long h = 0;
+        if (lane == 0) h = atomicAdd(p.next + 1, 1ull);
+        h = __shfl_sync(CSAW_FULL_MASK, h, 0);
+        if (h >= nh) break;
+        const uint32_t d = p.dh[h];
+        if (d > HUB_WARP_DEG) continue;
+        hub_row_scan_warp<KIND>(p, __ldg(p.off + p.H[h]), d, p.S + p.hub_off[h], lane);
+    }
+}
+
+// Edges in rows longer than theta: the size of the shared hub scratch when
+// every such row is a hub of the layer.
+__global__ void hub_edges_kernel(const uint64_t* __restrict__ off, uint32_t V, uint32_t theta,
+                                 unsigned long long* __restrict__ out)
+{
+    unsigned long long t = 0;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V;
+         v += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t d = off[v + 1] - off[v];
+        if (d > theta) t += d;
+    }
+    t = warp_sum_u64(t);
+    if ((threadIdx.x & 31) == 0 && t) atomicAdd(out, t);
 }
 
 // ---------------------------------------------------------------------------
@@ -792,15 +1002,20 @@ static void select_shape(const csaw_graph* g, int kind, uint32_t* theta_w, int* 
 }
 
 // Device counters of one call (zeroed at its start): error flags, the seed
-// count, the edge base of each layer, and eight words per layer.
+// count, the edge base of each layer, and sixteen words per layer.
+constexpr int L_WORDS = 16;
 enum : int {
     CT_ERR = 0,
     CT_NSEEDS = 1,
     CT_BASE = 2,                      // CT_BASE + l: first edge of layer l (l <= depth)
     CT_LAYER = CT_BASE + CSAW_MAX_DEPTH + 2,
-    CT_WORDS = CT_LAYER + 8 * CSAW_MAX_DEPTH,
+    CT_WORDS = CT_LAYER + L_WORDS * CSAW_MAX_DEPTH,
 };
-enum : int { L_N = 0, L_TOTAL = 1, L_ITEMS = 2, L_NEXT = 4, L_NEXT_F = 6 };
+// per layer: frontier entries, edges, item counts (warp, CTA, hub) and their
+// work counters, distinct hubs, their edges, hubs built by a whole CTA and
+// the two build counters
+enum : int { L_N = 0, L_TOTAL = 1, L_ITEMS = 2, L_NEXT = 5, L_NH = 8, L_HUBE = 9, L_NBIG = 10,
+             L_HNEXT = 11 };
 
 // ---------------------------------------------------------------------------
 // Layer sampling (Sec. II-A; Fig. 2(b) with the whole frontier as the current
@@ -1093,6 +1308,8 @@ struct Pipeline {
     int sel_blocks = 1;
     uint32_t theta_w = WARP_MAX_DEG;
     bool cached = false;                 // selection over a cached cumulative array
+    bool hub_path = false;               // shared hub arrays per layer (static bias, streamed)
+    bool cta_slots = false;              // CTA items may exceed CTA_SMEM_DEG: global slots
     uint32_t attempt_cap = CSAW_ATTEMPT_CAP;
     uint32_t k0 = 0, k1 = 0;
     const uint32_t* key_dev = nullptr;   // plan mode: Philox key in device memory
@@ -1109,8 +1326,23 @@ struct Pipeline {
     uint32_t* seed_kept = nullptr;
     uint64_t* seed_kpos = nullptr;       // [seeds_cap + 1]
     LayerBufs L[CSAW_MAX_DEPTH];
+    // hub grouping of one layer at a time (hub_cap items), and the shared
+    // hub prefix sums (hubS_cap entries)
+    uint64_t hub_cap = 0, hubS_cap = 0;
+    uint32_t* hlist = nullptr;           // [hub_cap] hub items in count order
+    uint64_t* hkeys = nullptr;           // [hub_cap] sort keys
+    uint64_t* halt = nullptr;            // [hub_cap]
+    uint32_t* hflag = nullptr;           // [hub_cap]
+    uint64_t* hpos = nullptr;            // [hub_cap + 1]
+    uint32_t* item_e = nullptr;          // [hub_cap]
+    uint32_t* item_h = nullptr;          // [hub_cap]
+    uint32_t* hubH = nullptr;            // [hub_cap] distinct hub vertices
+    uint32_t* hubD = nullptr;            // [hub_cap] their degrees
+    uint32_t* hubBig = nullptr;          // [hub_cap] hubs built by a whole CTA
+    uint64_t* hub_off = nullptr;         // [hub_cap + 1]
+    uint64_t* hubS = nullptr;            // [hubS_cap]
 
-    uint64_t* lc(uint32_t l, int w) const { return ctr + CT_LAYER + 8 * l + w; }
+    uint64_t* lc(uint32_t l, int w) const { return ctr + CT_LAYER + L_WORDS * l + w; }
 
     void init(csaw_graph* gr, int k, uint32_t ninst, uint32_t dep, const uint32_t* fan, uint64_t seed)
     {
@@ -1127,6 +1359,12 @@ struct Pipeline {
                     (kind == CSAW_BIAS_NEIGHBOR_DEGREE && g->zero_degree_target);
         select_shape(g, kind, &theta_w, &sel_blocks);
         cached = cached_cdf_usable(g, kind);
+        hub_path = !cached && (kind == CSAW_BIAS_EDGE_WEIGHT || kind == CSAW_BIAS_NEIGHBOR_DEGREE);
+        // CTA items exist for picks above PICK_MAX (or, without the hub
+        // path, any long row); only rows above CTA_SMEM_DEG need a slot
+        bool big_k = false;
+        for (uint32_t l = 0; l < dep; ++l) big_k |= fan[l] > PICK_MAX && fan[l] != CSAW_FANOUT_ALL;
+        cta_slots = g->max_degree > CTA_SMEM_DEG && (big_k || (!cached && !hub_path));
         k0 = (uint32_t)seed;
         k1 = (uint32_t)(seed >> 32);
     }
@@ -1160,6 +1398,29 @@ static csaw_status enqueue_frontier0(Pipeline& P, const uint32_t* seeds, const u
     return CSAW_OK;
 }
 
+// Hub grouping of layer l: sort the hub items by vertex, number the distinct
+// hub vertices, and give each a range of the shared scratch (exclusive scan
+// of their degrees; the layer's total is L_HUBE).
+static csaw_status enqueue_hub_groups(Pipeline& P, uint32_t l, cudaStream_t s)
+{
+    csaw_graph* g = P.g;
+    const uint64_t cap = P.L[l].f_cap;
+    const unsigned long long* n_hub = (const unsigned long long*)P.lc(l, L_ITEMS + 2);
+    const unsigned grid = grid_for(cap, 256, g->sm_count);
+    hub_keys_kernel<<<grid, 256, 0, s>>>(P.hlist, n_hub, P.L[l].F, P.vmask, (uint32_t)P.vbits, P.hkeys);
+    uint64_t* sorted = P.hkeys;
+    CSAW_TRY(radix_sort_u64(P.hkeys, P.halt, (const uint64_t*)n_hub, cap, P.vbits, g->sm_count, P.sort_scr, s,
+                            &sorted));
+    hub_flag_kernel<<<grid, 256, 0, s>>>(sorted, n_hub, P.vmask, P.hflag);
+    CSAW_TRY(scan_u32(P.hflag, P.hpos, (const uint64_t*)n_hub, cap, P.scan_scr, P.lc(l, L_NH), s));
+    hub_items_kernel<<<grid, 256, 0, s>>>(sorted, n_hub, P.hflag, P.hpos, P.vmask, (uint32_t)P.vbits, g->off,
+                                          P.item_e, P.item_h, P.hubH, P.hubD, P.hubBig,
+                                          (unsigned long long*)P.lc(l, L_NBIG));
+    CSAW_TRY(scan_u32(P.hubD, P.hub_off, P.lc(l, L_NH), cap, P.scan_scr, P.lc(l, L_HUBE), s));
+    CSAW_CUDA(cudaGetLastError());
+    return CSAW_OK;
+}
+
 // Count/classify and the edge-position scan of layer l.
 static csaw_status enqueue_count(Pipeline& P, uint32_t l, cudaStream_t s)
 {
@@ -1171,6 +1432,7 @@ static csaw_status enqueue_count(Pipeline& P, uint32_t l, cudaStream_t s)
     cp.k = P.fanout[l]; cp.theta_w = P.theta_w; cp.cached = P.cached; cp.zero_bias = P.zero_bias;
     cp.cnt = B.cnt; cp.warp_list = B.wlist; cp.cta_list = B.clist;
     cp.n_items = (unsigned long long*)P.lc(l, L_ITEMS);
+    cp.hub_list = P.hub_path ? P.hlist : nullptr;
     if (B.f_cap) {
         switch (P.kind) {
         case CSAW_BIAS_UNIFORM: CSAW_TRY(launch_count<CSAW_BIAS_UNIFORM>(cp, B.f_cap, g->sm_count, s)); break;
@@ -1178,7 +1440,9 @@ static csaw_status enqueue_count(Pipeline& P, uint32_t l, cudaStream_t s)
         default: CSAW_TRY(launch_count<CSAW_BIAS_NEIGHBOR_DEGREE>(cp, B.f_cap, g->sm_count, s)); break;
         }
     }
-    return scan_u32(B.cnt, B.pos, P.lc(l, L_N), B.f_cap, P.scan_scr, P.lc(l, L_TOTAL), s);
+    CSAW_TRY(scan_u32(B.cnt, B.pos, P.lc(l, L_N), B.f_cap, P.scan_scr, P.lc(l, L_TOTAL), s));
+    if (P.hub_path && B.f_cap) CSAW_TRY(enqueue_hub_groups(P, l, s));
+    return CSAW_OK;
 }
 
 // Selection of layer l into its edge buffers, then its offsets.
@@ -1211,6 +1475,24 @@ static csaw_status enqueue_select(Pipeline& P, uint32_t l, cudaStream_t s)
         case CSAW_BIAS_UNIFORM: CSAW_TRY(launch_select<CSAW_BIAS_UNIFORM>(sp, P.sel_blocks, s)); break;
         case CSAW_BIAS_EDGE_WEIGHT: CSAW_TRY(launch_select<CSAW_BIAS_EDGE_WEIGHT>(sp, P.sel_blocks, s)); break;
         default: CSAW_TRY(launch_select<CSAW_BIAS_NEIGHBOR_DEGREE>(sp, P.sel_blocks, s)); break;
+        }
+        if (P.hub_path) {
+            // the layer's distinct hubs: prefix sums built once each, then
+            // every hub item draws from them
+            HubBuildParams hp;
+            hp.off = g->off; hp.col = g->col; hp.w = g->w; hp.deg = g->deg;
+            hp.H = P.hubH; hp.dh = P.hubD; hp.hub_off = P.hub_off;
+            hp.nh = (const unsigned long long*)P.lc(l, L_NH);
+            hp.big_list = P.hubBig; hp.n_big = (const unsigned long long*)P.lc(l, L_NBIG);
+            hp.next = (unsigned long long*)P.lc(l, L_HNEXT); hp.S = P.hubS;
+            const int blocks = g->sm_count * 4;
+            if (P.kind == CSAW_BIAS_EDGE_WEIGHT) hub_cdf_kernel<CSAW_BIAS_EDGE_WEIGHT><<<blocks, SEL_THREADS, 0, s>>>(hp);
+            else hub_cdf_kernel<CSAW_BIAS_NEIGHBOR_DEGREE><<<blocks, SEL_THREADS, 0, s>>>(hp);
+            SelParams hs = sp;
+            hs.cdf = nullptr;
+            hs.item_e = P.item_e; hs.item_h = P.item_h; hs.hub_off = P.hub_off; hs.hubS = P.hubS;
+            select_cdf_kernel<false><<<g->sm_count * 8, SEL_THREADS, 0, s>>>(hs);
+            CSAW_CUDA(cudaGetLastError());
         }
     }
     layer_offsets_kernel<<<grid_for((uint64_t)P.n_inst + 1, 256, g->sm_count), 256, 0, s>>>(
@@ -1247,7 +1529,7 @@ static csaw_status alloc_common(Pipeline& P, Alloc&& get)
     CSAW_TRY(get((void**)&P.ctr, sizeof(uint64_t) * CT_WORDS));
     CSAW_TRY(get(&P.scan_scr, scan_scratch_bytes(0)));
     CSAW_TRY(get(&P.sort_scr, sort_scratch_bytes(0)));
-    if (P.g->max_degree > CTA_SMEM_DEG) {
+    if (P.cta_slots) {
         CSAW_TRY(get((void**)&P.hub_S, sizeof(uint64_t) * (size_t)P.sel_blocks * P.g->max_degree));
         CSAW_TRY(get((void**)&P.hub_bits, sizeof(uint32_t) * (size_t)P.sel_blocks * ((P.g->max_degree + 31) / 32)));
     }
@@ -1259,6 +1541,26 @@ static csaw_status alloc_common(Pipeline& P, Alloc&& get)
     CSAW_TRY(get((void**)&P.seed_alt, sizeof(uint64_t) * sc));
     CSAW_TRY(get((void**)&P.seed_kept, sizeof(uint32_t) * sc));
     CSAW_TRY(get((void**)&P.seed_kpos, sizeof(uint64_t) * (sc + 1)));
+    return CSAW_OK;
+}
+
+// Hub grouping buffers for layers of up to `cap` frontier entries.
+template <class Alloc>
+static csaw_status alloc_hub(Pipeline& P, uint64_t cap, Alloc&& get)
+{
+    P.hub_cap = cap;
+    const uint64_t c = cap ? cap : 1;
+    CSAW_TRY(get((void**)&P.hlist, sizeof(uint32_t) * c));
+    CSAW_TRY(get((void**)&P.hkeys, sizeof(uint64_t) * c));
+    CSAW_TRY(get((void**)&P.halt, sizeof(uint64_t) * c));
+    CSAW_TRY(get((void**)&P.hflag, sizeof(uint32_t) * c));
+    CSAW_TRY(get((void**)&P.hpos, sizeof(uint64_t) * (c + 1)));
+    CSAW_TRY(get((void**)&P.item_e, sizeof(uint32_t) * c));
+    CSAW_TRY(get((void**)&P.item_h, sizeof(uint32_t) * c));
+    CSAW_TRY(get((void**)&P.hubH, sizeof(uint32_t) * c));
+    CSAW_TRY(get((void**)&P.hubD, sizeof(uint32_t) * c));
+    CSAW_TRY(get((void**)&P.hubBig, sizeof(uint32_t) * c));
+    CSAW_TRY(get((void**)&P.hub_off, sizeof(uint64_t) * (c + 1)));
     return CSAW_OK;
 }
 
@@ -1399,14 +1701,29 @@ static csaw_status run_sample(csaw_graph* g, const uint32_t* seeds, const uint64
     R->src.assign(depth, nullptr);
     R->dst.assign(depth, nullptr);
     R->layer_edges.assign(depth, 0);
+    const bool hubs = P.hub_path && !layer_mode;
     for (uint32_t l = 0; l < depth; ++l) {
+        // the layer's hub grouping buffers and shared hub prefix sums live
+        // until its selection is done
+        Temps layer_tmp(s);
+        auto get_layer = [&](void** p, size_t bytes) -> csaw_status {
+            CSAW_TRY(dalloc(p, bytes, s));
+            layer_tmp.ptrs.push_back(*p);
+            return CSAW_OK;
+        };
+        if (hubs) CSAW_TRY(alloc_hub(P, P.L[l].f_cap, get_layer));
         CSAW_TRY(layer_mode ? enqueue_layer_count(P, l, s) : enqueue_count(P, l, s));
-        uint64_t h[2] = {0, 0};
+        uint64_t h[3] = {0, 0, 0};
         CSAW_CUDA(cudaMemcpyAsync(&h[0], P.ctr + CT_ERR, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
         CSAW_CUDA(cudaMemcpyAsync(&h[1], P.lc(l, L_TOTAL), sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+        if (hubs) CSAW_CUDA(cudaMemcpyAsync(&h[2], P.lc(l, L_HUBE), sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
         CSAW_CUDA(cudaStreamSynchronize(s));
         CSAW_TRY(check_errors(h[0]));
         const uint64_t total = h[1];
+        if (hubs) {
+            P.hubS_cap = h[2];
+            CSAW_TRY(get_layer((void**)&P.hubS, sizeof(uint64_t) * (h[2] ? h[2] : 1)));
+        }
         R->layer_edges[l] = total;
         CSAW_TRY(alloc_edges(P, l, total, get, get_out));
         R->src[l] = P.L[l].src;
@@ -1655,13 +1972,34 @@ extern "C" csaw_status csaw_sample_plan_create_ex(csaw_graph* g, uint32_t n_inst
     // Upper bounds: a layer emits at most min(k, max degree) edges per
     // frontier vertex; a frontier is at most the previous layer's edges and
     // at most one entry per (instance, vertex).
-    uint64_t f = max_seeds;
+    uint64_t f = max_seeds, f_max = 0;
     const uint64_t fmax = sat_mul(n_instances, g->V);
     for (uint32_t l = 0; st == CSAW_OK && l < depth; ++l) {
         st = alloc_entries(P, l, f, get);
+        if (f > f_max) f_max = f;
         const uint64_t e = P.edge_bound(l, f);
         if (st == CSAW_OK) st = alloc_edges(P, l, e, get, get);
         f = e < fmax ? e : fmax;
+    }
+    if (st == CSAW_OK && P.hub_path) {
+        // shared hub prefix sums: at most every edge of the rows above
+        // theta_w, and at most max degree per hub item
+        st = alloc_hub(P, f_max, get);
+        uint64_t e_hub = 0;
+        unsigned long long* d_sum = nullptr;
+        if (st == CSAW_OK) st = get((void**)&d_sum, sizeof(unsigned long long));
+        if (st == CSAW_OK) {
+            cudaError_t e = cudaMemset(d_sum, 0, sizeof(unsigned long long));
+            if (e == cudaSuccess) {
+                hub_edges_kernel<<<grid_for(g->V, 256, g->sm_count), 256>>>(g->off, g->V, P.theta_w, d_sum);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = cudaMemcpy(&e_hub, d_sum, sizeof(uint64_t), cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) st = cuda_fail(e, "hub edge count");
+        }
+        const uint64_t by_items = sat_mul(f_max, g->max_degree);
+        P.hubS_cap = e_hub < by_items ? e_hub : by_items;
+        if (st == CSAW_OK) st = get((void**)&P.hubS, sizeof(uint64_t) * (P.hubS_cap ? P.hubS_cap : 1));
     }
     if (st == CSAW_OK) st = get((void**)&pl->in_seeds, sizeof(uint32_t) * max_seeds);
     if (st == CSAW_OK) st = get((void**)&pl->in_io, sizeof(uint64_t) * ((size_t)n_instances + 1));
@@ -1755,7 +2093,7 @@ static csaw_status plan_collect(csaw_sample_plan* pl)
     CSAW_CUDA(cudaMemcpy(pl->h_eoff.data(), P.eoff, sizeof(uint64_t) * (ng + 1), cudaMemcpyDeviceToHost));
     if (ng) CSAW_CUDA(cudaMemcpy(pl->h_fsize.data(), P.fsize, sizeof(uint64_t) * ng, cudaMemcpyDeviceToHost));
     pl->h_layer_edges.assign(P.depth, 0);
-    for (uint32_t l = 0; l < P.depth; ++l) pl->h_layer_edges[l] = ctr[CT_LAYER + 8 * l + L_TOTAL];
+    for (uint32_t l = 0; l < P.depth; ++l) pl->h_layer_edges[l] = ctr[CT_LAYER + L_WORDS * l + L_TOTAL];
     pl->src_c.assign(P.depth, nullptr);
     pl->dst_c.assign(P.depth, nullptr);
     for (uint32_t l = 0; l < P.depth; ++l) { pl->src_c[l] = P.L[l].src; pl->dst_c[l] = P.L[l].dst; }

@@ -47,9 +47,48 @@ struct Request {
     csaw_result* result = nullptr;
 };
 
+// The sum of the f largest vertex degrees of the graph, from a table of the
+// distinct degrees in descending order with running counts and sums: the
+// most neighbours that the distinct hubs of an f-vertex frontier can have.
+struct DegreeTable {
+    std::vector<uint32_t> deg;       // distinct degrees, descending
+    std::vector<uint64_t> count;     // vertices with degree >= deg[i]
+    std::vector<uint64_t> sum;       // their degrees' sum
+    uint64_t top_sum(uint64_t f) const
+    {
+        if (deg.empty() || f == 0) return 0;
+        size_t lo = 0, hi = count.size();
+        while (lo < hi) {
+            const size_t mid = (lo + hi) / 2;
+            if (count[mid] >= f) hi = mid; else lo = mid + 1;
+        }
+        if (lo == count.size()) return sum.back();
+        const uint64_t before_c = lo ? count[lo - 1] : 0, before_s = lo ? sum[lo - 1] : 0;
+        return before_s + (f - before_c) * deg[lo];
+    }
+};
+
+static csaw_status build_degree_table(const csaw_graph* g, DegreeTable* t)
+{
+    std::vector<uint32_t> d(g->V);
+    if (g->V) CSAW_CUDA(cudaMemcpy(d.data(), g->deg, sizeof(uint32_t) * g->V, cudaMemcpyDeviceToHost));
+    std::vector<uint64_t> hist((size_t)g->max_degree + 1, 0);
+    for (uint32_t x : d) ++hist[x <= g->max_degree ? x : g->max_degree];
+    uint64_t c = 0, sm = 0;
+    for (uint64_t x = g->max_degree; x >= 1; --x) {
+        if (!hist[x]) continue;
+        c += hist[x];
+        sm += hist[x] * x;
+        t->deg.push_back((uint32_t)x);
+        t->count.push_back(c);
+        t->sum.push_back(sm);
+    }
+    return CSAW_OK;
+}
+
 // Device bytes a request may hold at once (an upper bound of what csaw_walk
 // or csaw_sample allocates for it).
-static uint64_t estimate_bytes(const csaw_graph* g, const Request& r)
+static uint64_t estimate_bytes(const csaw_graph* g, const DegreeTable& dt, const Request& r)
 {
     if (r.kind == CSAW_REQ_WALK) {
         const uint64_t n = r.starts.size();
@@ -60,17 +99,23 @@ static uint64_t estimate_bytes(const csaw_graph* g, const Request& r)
     uint64_t b = 4 * S + 8 * ((uint64_t)r.n_instances + 1) + 64 * 1024;
     b += 16 * (uint64_t)depth * r.n_instances + 8;   // offsets and sizes
     b += 28 * S + 8;                                 // seed keys, sort, compaction
-    if (g->max_degree > 8192) b += (uint64_t)g->sm_count * 4 * ((uint64_t)g->max_degree * 8 + g->max_degree / 8 + 8);
-    uint64_t f = S;
+    bool big_k = false;
+    for (uint32_t l = 0; l < depth; ++l) big_k |= r.fanout[l] > 256 && r.fanout[l] != CSAW_FANOUT_ALL;
+    if (g->max_degree > 8192 && big_k)               // per-CTA slots of long rows
+        b += (uint64_t)g->sm_count * 4 * ((uint64_t)g->max_degree * 8 + g->max_degree / 8 + 8);
+    uint64_t f = S, hub = 0;
     for (uint32_t l = 0; l < depth; ++l) {
         const uint64_t k = r.fanout[l] < g->max_degree ? r.fanout[l] : g->max_degree;
         const uint64_t e = f * k;
         b += f * 36 + 8 * (uint64_t)(r.n_instances + 1);   // frontier keys, counts, lists, positions
         b += e * 8;                                         // sampled edges
         if (l + 1 < depth) b += e * 28;                     // candidates, sort, compaction
+        // hub grouping and shared hub prefix sums, held for one layer at a time
+        const uint64_t h = 60 * f + 8 * dt.top_sum(f) + 64;
+        if (h > hub) hub = h;
         f = e;
     }
-    return b;
+    return b + hub;
 }
 
 static csaw_result* new_result(const Request& r)
@@ -140,6 +185,7 @@ using namespace csaw;
 
 struct csaw_server {
     csaw_graph* g = nullptr;
+    DegreeTable degrees;
     uint64_t budget = 0;
     uint32_t slots = 0;
     std::mutex mu;
@@ -202,6 +248,10 @@ extern "C" csaw_status csaw_server_create(csaw_graph* g, const csaw_server_opts*
     sv->budget = opts->budget_bytes;
     sv->slots = opts->slots;
     cudaError_t e = cudaSetDevice(g->device);
+    if (e == cudaSuccess) {
+        const csaw_status st = build_degree_table(g, &sv->degrees);
+        if (st != CSAW_OK) { delete sv; return st; }
+    }
     for (uint32_t i = 0; e == cudaSuccess && i < opts->slots; ++i) {
         cudaStream_t st;
         e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
@@ -274,7 +324,7 @@ extern "C" csaw_status csaw_submit(csaw_server* sv, const csaw_request* r, uint6
         st = fail(CSAW_ERR_INVALID, "unknown request kind %d", r->kind);
     }
     if (st != CSAW_OK) { delete rq; return st; }
-    rq->estimate = estimate_bytes(sv->g, *rq);
+    rq->estimate = estimate_bytes(sv->g, sv->degrees, *rq);
     if (rq->estimate > sv->budget) {
         const uint64_t est = rq->estimate;
         delete rq;

@@ -842,6 +842,17 @@ static csaw_status launch_walk(int kind, uint64_t max_bias, const WalkParams& p,
 // so its cost is O(log d) dependent loads instead of a stream over the row;
 // 32 walkers per warp keep many searches in flight.  The picks are those of
 // the streaming kernel: the same prefix sums and the same draws.
+//
+// Path stores: a warp's 32 walkers (consecutive rows) stage their next 16
+// path entries in a shared-memory tile, one tile row per walker; when the
+// tile is full (or the walk ends) the warp writes it out two walkers at a
+// time, each walker's entries as 64 consecutive bytes of its row.  Stores
+// from one thread per walker would put 32 different rows behind every warp
+// store, each sector written a few bytes at a time.
+constexpr int WC_THREADS = 256;
+constexpr int WC_WARPS = WC_THREADS / 32;
+constexpr int WC_TILE = 16;                  // path entries staged per walker
+
 struct WalkCdfParams {
     const uint64_t* __restrict__ off;
     const uint32_t* __restrict__ col;
@@ -854,44 +865,80 @@ struct WalkCdfParams {
     PhiloxKeys keys;
 };
 
-template <bool UNIFORM>
-__global__ void __launch_bounds__(256) walk_cached_kernel(WalkCdfParams p)
+// Writes the staged entries t in [t0, t_end) of the warp's walkers base ..
+// base + 31 (those below n): per iteration, lanes 0-15 store 16 consecutive
+// entries of one walker's row and lanes 16-31 those of the next walker.
+__device__ __forceinline__ void walk_tile_flush(const WalkCdfParams& p, uint32_t (*tile)[WC_TILE + 1],
+                                                uint64_t base, uint64_t row_len, uint64_t t0, uint64_t t_end,
+                                                int lane)
 {
+    __syncwarp();
+    const int half = lane >> 4, c = lane & 15;
+    const uint64_t t = t0 + (uint64_t)c;
+    uint64_t wk = base + (uint64_t)half;
+    uint32_t* out = p.path + wk * row_len + t;
+    const uint64_t step = 2 * row_len;
+#pragma unroll 2
+    for (int i = half; i < 32; i += 2) {
+        if (wk < p.n && t < t_end) *out = tile[i][c];
+        wk += 2;
+        out += step;
+    }
+    __syncwarp();
+}
+
+template <bool UNIFORM>
+__global__ void __launch_bounds__(WC_THREADS) walk_cached_kernel(WalkCdfParams p)
+{
+    __shared__ uint32_t s_tile[WC_WARPS][32][WC_TILE + 1];   // +1: conflict-free column writes
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t (*tile)[WC_TILE + 1] = s_tile[wid];
     const uint64_t row_len = (uint64_t)p.L + 1;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t wk = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; wk < p.n; wk += stride) {
-        uint32_t* out = p.path + wk * row_len;
-        uint32_t cur = __ldg(p.starts + wk);
-        if (cur >= p.V) {
-            for (uint64_t t = 0; t < row_len; ++t) out[t] = CSAW_NONE;
-            continue;
-        }
-        out[0] = cur;
-        uint32_t s = 0;
-        for (; s < p.L; ++s) {
-            const uint64_t beg = __ldg(p.off + cur);
-            const uint64_t end = __ldg(p.off + cur + 1);
-            if (beg == end) break;
-            const uint64_t r = philox_draw(p.keys, 0u, cur, s, (uint32_t)wk);
-            uint64_t i;
-            if constexpr (UNIFORM) {
-                i = scale_draw(r, end - beg);
-            } else {
-                const uint64_t T = __ldg(p.cdf + end - 1);
-                if (T == 0) break;
-                const uint64_t x = scale_draw(r, T);
-                // smallest e in [beg, end) with cdf[e] > x
-                uint64_t lo = beg, hi = end - 1;
-                while (lo < hi) {
-                    const uint64_t mid = lo + ((hi - lo) >> 1);
-                    if (__ldg(p.cdf + mid) > x) hi = mid; else lo = mid + 1;
+    const uint64_t n_warps = (uint64_t)gridDim.x * WC_WARPS;
+    for (uint64_t base = ((uint64_t)blockIdx.x * WC_WARPS + wid) * 32; base < p.n; base += n_warps * 32) {
+        const uint64_t wk = base + (uint64_t)lane;
+        // alive: still walking; cur = CSAW_NONE once stopped (or never started)
+        uint32_t cur = wk < p.n ? __ldg(p.starts + wk) : CSAW_NONE;
+        if (cur >= p.V) cur = CSAW_NONE;
+        bool alive = cur != CSAW_NONE;
+        tile[lane][0] = cur;
+        uint64_t t0 = 0;                   // path position of tile column 0
+        for (uint32_t s = 0; s < p.L; ++s) {
+            if (alive) {
+                const uint64_t beg = __ldg(p.off + cur);
+                const uint64_t end = __ldg(p.off + cur + 1);
+                bool stop = beg == end;
+                uint64_t i = 0;
+                if (!stop) {
+                    const uint64_t r = philox_draw(p.keys, 0u, cur, s, (uint32_t)wk);
+                    if constexpr (UNIFORM) {
+                        i = scale_draw(r, end - beg);
+                    } else {
+                        const uint64_t T = __ldg(p.cdf + end - 1);
+                        stop = T == 0;
+                        if (!stop) {
+                            const uint64_t x = scale_draw(r, T);
+                            // smallest e in [beg, end) with cdf[e] > x
+                            uint64_t lo = beg, hi = end - 1;
+                            while (lo < hi) {
+                                const uint64_t mid = lo + ((hi - lo) >> 1);
+                                if (__ldg(p.cdf + mid) > x) hi = mid; else lo = mid + 1;
+                            }
+                            i = lo - beg;
+                        }
+                    }
                 }
-                i = lo - beg;
+                if (stop) { alive = false; cur = CSAW_NONE; }
+                else cur = __ldg(p.col + beg + i);
             }
-            cur = __ldg(p.col + beg + i);
-            out[s + 1] = cur;
+            const uint64_t t = (uint64_t)s + 1;      // path position of this step's vertex
+            tile[lane][t - t0] = cur;
+            if (t - t0 == WC_TILE - 1 || t == p.L) {
+                walk_tile_flush(p, tile, base, row_len, t0, t + 1, lane);
+                t0 = t + 1;
+            }
         }
-        for (uint64_t t = (uint64_t)s + 1; t < row_len; ++t) out[t] = CSAW_NONE;
+        if (p.L == 0) walk_tile_flush(p, tile, base, row_len, 0, 1, lane);
     }
 }
 
@@ -906,17 +953,17 @@ csaw_status launch_walk_cached(const csaw_graph* g, int kind, const uint32_t* st
     const int u = kind == CSAW_BIAS_UNIFORM ? 1 : 0;
     int per_sm = cached[u].load(std::memory_order_acquire);
     if (per_sm == 0) {
-        cudaError_t e = u ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_cached_kernel<true>, 256, 0)
-                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_cached_kernel<false>, 256, 0);
+        cudaError_t e = u ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_cached_kernel<true>, WC_THREADS, 0)
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_cached_kernel<false>, WC_THREADS, 0);
         if (e != cudaSuccess) return cuda_fail(e, "occupancy(walk_cached)");
         if (per_sm < 1) per_sm = 1;
         cached[u].store(per_sm, std::memory_order_release);
     }
-    uint64_t blocks = (n + 255) / 256;
+    uint64_t blocks = (n + WC_THREADS - 1) / WC_THREADS;
     const uint64_t cap = (uint64_t)g->sm_count * per_sm;
     if (blocks > cap) blocks = cap;
-    if (u) walk_cached_kernel<true><<<(unsigned)blocks, 256, 0, s>>>(p);
-    else walk_cached_kernel<false><<<(unsigned)blocks, 256, 0, s>>>(p);
+    if (u) walk_cached_kernel<true><<<(unsigned)blocks, WC_THREADS, 0, s>>>(p);
+    else walk_cached_kernel<false><<<(unsigned)blocks, WC_THREADS, 0, s>>>(p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "walk_cached_kernel launch");
     return CSAW_OK;

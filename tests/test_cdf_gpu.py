@@ -39,6 +39,24 @@ def test_cached_walks_match_oracle(csaw, bias):
         G.close()
 
 
+@pytest.mark.parametrize("bias", ["edge_weight", "uniform"])
+def test_cached_walk_tile_boundaries_and_dead_ends(csaw, bias):
+    """Path rows are staged 16 entries at a time per walker and written out
+    by the warp: lengths around the tile size, ragged warps and walkers that
+    stop at a vertex without neighbours."""
+    dead = inputs.csr_from_edges(6, [(0, 1), (1, 2), (3, 4), (5, 0), (5, 3)], [2, 3, 5, 1, 7])
+    for g in (dead, inputs.rmat_csr(8, 8, 40, 1)):
+        G = csaw.Graph(g.off, g.col, g.w)
+        if bias != "uniform":
+            G.build_cdf(bias)
+        for n in (1, 33, 70):
+            starts = inputs.uniform_vertices(n, g.V, n)
+            for length in (0, 1, 14, 15, 16, 17, 31, 32, 47, 80):
+                got = csaw.walk(G, starts, length, bias, 5)
+                assert np.array_equal(got, oracle.walk(g, starts, length, bias, 5)), (g.V, n, length)
+        G.close()
+
+
 def test_cached_walk_s20_subset(csaw):
     import torch
     wl = inputs.workload_walk_s20()

@@ -238,3 +238,48 @@ def test_sample_plan_batched_s24_subset(csaw, s24):
     assert np.array_equal(res.frontier_sizes, whole.frontier_sizes)
     assert np.array_equal(res.src, whole.src) and np.array_equal(res.dst, whole.dst)
     G.close()
+
+
+def test_sample_shared_hub_arrays(csaw):
+    """Hub vertices that recur in many instances' frontiers share one
+    cumulative array per layer: degrees around the warp/CTA build split
+    (2048) and the shared-memory limit (8192), many instances seeded on the
+    same hubs, duplicated hubs inside an instance, both static biases and a
+    low warp threshold -- bit-exact against the oracle."""
+    rng = np.random.default_rng(12)
+    # three stars whose leaves are shared, plus a ring through the leaves
+    centres = [(0, 2047), (1, 2049), (2, 9000)]
+    n_leaf = 9000
+    V = 3 + n_leaf
+    edges, w = [], []
+    for c, d in centres:
+        for j in range(d):
+            u = 3 + j
+            edges += [(c, u), (u, c)]
+            w += [int(rng.integers(1, 300))] * 2
+    for j in range(n_leaf):
+        a, b = 3 + j, 3 + (j + 1) % n_leaf
+        edges += [(a, b), (b, a)]
+        w += [int(rng.integers(1, 300))] * 2
+    key = {}
+    for (a, b), x in zip(edges, w):
+        key[(a, b)] = x
+    es = sorted(key)
+    g = inputs.csr_from_edges(V, es, [key[e] for e in es])
+    n_inst = 40
+    seeds = np.concatenate([np.concatenate([np.array([0, 1, 2], dtype=np.uint32), inputs.uniform_vertices(5, V, i)])
+                            for i in range(n_inst)]).astype(np.uint32)
+    io = np.arange(0, 8 * n_inst + 1, 8, dtype=np.uint64)
+    G = csaw.Graph(g.off, g.col, g.w)
+    for bias in ("edge_weight", "neighbor_degree"):
+        for fan in ([25, 10], [3, 40, 2]):
+            ref = oracle.sample(g, seeds, io, fan, bias, 5)
+            check_equal(csaw.sample(G, seeds, io, fan, bias, 5), ref, n_inst, len(fan))
+            csaw.set_select_tuning(G, bias, 32, 0)
+            check_equal(csaw.sample(G, seeds, io, fan, bias, 5), ref, n_inst, len(fan))
+            plan = csaw.SamplePlan(G, n_inst, len(seeds), fan, bias)
+            plan.run(seeds, io, 5)
+            check_equal(plan.result(), ref, n_inst, len(fan))
+            plan.close()
+            csaw.set_select_tuning(G, bias, 0, 0)
+    G.close()
