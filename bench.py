@@ -549,7 +549,8 @@ def batched_leg(torch, csaw, wl, G, cdf, steps, warmup, plain_instances, flush):
     ms_plain = time_gpu(torch, plain, 1, flush)
     if cdf:
         G.drop_cdf(wl.bias)
-    seps_b, seps_p = edges / (ms_plan / 1e3), plain_edges / (ms_plain / 1e3)
+    seps_b = edges / (ms_plan / 1e3)
+    seps_p = plain_edges / (ms_plain / 1e3) if plain_edges and ms_plain > 0 else None
     return res, {
         "batched_plan": {"ms_per_run": ms_plan, "seps": seps_b, "sampled_edges": edges, "runs_timed": steps,
                          "select_blocks": info["select_blocks"], "theta_warp": info["theta_warp"],
@@ -561,7 +562,7 @@ def batched_leg(torch, csaw, wl, G, cdf, steps, warmup, plain_instances, flush):
             "ms": ms_plain, "sampled_edges": plain_edges, "seps": seps_p,
             "timing": "one csaw_sample call per instance (host seeds in, edges left on the device), "
                       "CUDA events around the whole sequence"},
-        "batched_over_plain_seps": seps_b / seps_p,
+        "batched_over_plain_seps": seps_b / seps_p if seps_p else None,
     }
 
 

@@ -437,14 +437,19 @@ csaw_status csaw_autotune_select(csaw_graph* g, const uint32_t* seeds, const uin
  * estimate fits budget_bytes and one of `slots` slots is free; every slot has
  * its own CUDA stream, so admitted requests run concurrently and their work
  * overlaps on the GPU.  A request that arrives while others run is admitted as
- * soon as a slot and enough budget are free.  Each request's draws depend only
- * on its own arguments and seed, so its result is bit-for-bit the one that
- * csaw_sample / csaw_walk return for it alone.  The paper has no serving
- * layer: this runs its selection (Sec. III-IV) for a stream of independent
- * instances (Sec. IV-A). */
+ * soon as a slot and enough budget are free.  Continuous batching: a slot that
+ * frees up takes the oldest waiting request and, with it, up to max_batch - 1
+ * other waiting requests of the same kind and bias that fit the budget; their
+ * instances (sampling) or walkers (walks) run as one multi-instance launch
+ * (the batched multi-instance sampling of Sec. V-B) and finish together.
+ * Each request's draws depend only on its own arguments and seed, so its
+ * result is bit-for-bit the one that csaw_sample / csaw_walk return for it
+ * alone.  The paper has no serving layer: this runs its selection (Sec.
+ * III-IV) for a stream of independent instances (Sec. IV-A). */
 typedef struct {
     uint64_t budget_bytes;   /* device bytes that admitted requests may hold at once */
-    uint32_t slots;          /* concurrent requests (1 .. 256) */
+    uint32_t slots;          /* concurrent batches (1 .. 256) */
+    uint32_t max_batch;      /* requests per batch (0 = 32; 1 = no batching) */
 } csaw_server_opts;
 
 enum { CSAW_REQ_SAMPLE = 0, CSAW_REQ_WALK = 1 };
@@ -503,9 +508,11 @@ csaw_status csaw_server_create(csaw_graph* g, const csaw_server_opts* opts, csaw
  * must outlive the server. */
 csaw_status csaw_server_destroy(csaw_server* s);
 
-/* Queue a request; *ticket identifies it.  Errors: CSAW_ERR_INVALID (bad
- * arguments), CSAW_ERR_NOMEM (its estimate exceeds the whole budget),
- * CSAW_ERR_ABORTED (server shutting down). */
+/* Queue a request; *ticket identifies it.  Its arguments are checked here
+ * (offsets, seeds and starts in range, fanouts positive), so a batch never
+ * fails for one request's input.  Errors: CSAW_ERR_INVALID (bad arguments),
+ * CSAW_ERR_NOMEM (its estimate exceeds the whole budget), CSAW_ERR_ABORTED
+ * (server shutting down). */
 csaw_status csaw_submit(csaw_server* s, const csaw_request* r, uint64_t* ticket);
 
 /* Wait up to timeout_us (< 0: forever, 0: no wait) for a request.  When it

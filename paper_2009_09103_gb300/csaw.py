@@ -63,7 +63,7 @@ class SelectTuning(ctypes.Structure):
 
 
 class ServerOpts(ctypes.Structure):
-    _fields_ = [("budget_bytes", ctypes.c_uint64), ("slots", ctypes.c_uint32)]
+    _fields_ = [("budget_bytes", ctypes.c_uint64), ("slots", ctypes.c_uint32), ("max_batch", ctypes.c_uint32)]
 
 
 class Request(ctypes.Structure):
@@ -547,9 +547,11 @@ class ServedResult:
 
 
 class Server:
-    def __init__(self, g: Graph, budget_bytes: int, slots: int = 4):
+    def __init__(self, g: Graph, budget_bytes: int, slots: int = 4, max_batch: int = 0):
+        """max_batch: requests a slot runs together (0 = the library's
+        default, 1 = one request per launch)."""
         self._g = g
-        o = ServerOpts(budget_bytes, slots)
+        o = ServerOpts(budget_bytes, slots, max_batch)
         self._h = ctypes.c_void_p()
         _check(lib().csaw_server_create(g.handle, ctypes.byref(o), ctypes.byref(self._h)))
 

@@ -159,7 +159,7 @@ using namespace csaw;
 
 extern "C" const char* csaw_last_error(void) { return g_last_error; }
 
-extern "C" uint32_t csaw_version(void) { return 10000u; }
+extern "C" uint32_t csaw_version(void) { return 10100u; }
 
 extern "C" csaw_status csaw_graph_destroy(csaw_graph* g)
 {

@@ -78,6 +78,30 @@ size_t sort_scratch_bytes(uint64_t n_max);
 csaw_status radix_sort_u64(uint64_t* keys, uint64_t* alt, const uint64_t* n_dev, uint64_t n_max,
                            int bits, int sm_count, void* scratch, cudaStream_t s, uint64_t** result);
 
+// Several walk requests in one launch (the request server's batches):
+// walker w belongs to request r with start[r] <= w < start[r + 1]; its draws
+// use that request's key and its index w - start[r] (the instance word), and
+// its row of len[r] + 1 entries starts at path + row0[r] + (w - start[r]) *
+// (len[r] + 1).  Device arrays.
+struct WalkSegments {
+    const uint64_t* __restrict__ start;   // [n + 1]
+    const uint32_t* __restrict__ len;     // [n]
+    const uint32_t* __restrict__ key;     // [2 n]
+    const uint64_t* __restrict__ row0;    // [n]
+    uint32_t n;
+    // walkers a warp takes before its block exits (0: until all are done).
+    // Short-lived blocks let the kernels of a request that arrives later
+    // (on a higher-priority stream) start without waiting for this launch.
+    uint32_t warp_budget;
+};
+
+// The walks of a batch of requests (same bias) in one launch: d_starts holds
+// the n walkers of all requests in segment order, max_len is the longest
+// length.  Results are those of csaw_walk for each request alone.  Defined
+// in csaw_walk.cu.
+csaw_status walk_batch(const csaw_graph* g, const csaw_bias* bias, const uint32_t* d_starts, uint64_t n,
+                       const WalkSegments& seg, uint32_t max_len, uint32_t* d_path, cudaStream_t s);
+
 // Walks that read a cached cumulative array (or, for uniform bias, none):
 // one thread per walker.  Defined in csaw_walk.cu.
 csaw_status launch_walk_cached(const csaw_graph* g, int kind, const uint32_t* starts, uint64_t n,
@@ -90,6 +114,21 @@ bool cached_cdf_usable(const csaw_graph* g, int kind);
 
 // Releases a result made by the request server (tagged "CSRV").
 void free_server_result(void* result);
+
+// Several sampling requests in one multi-instance run (the request server's
+// batches).  Device tables: each instance's Philox key (two words), its index
+// within its request (the instance word of its draws) and its fanout at every
+// layer ([depth][n_inst], 0 past its request's depth).  fan_max[l] (host) is
+// the largest fanout of layer l.  The result has csaw_sample's layout over
+// the batch's instances; each request's instances keep their own draws.
+struct SampleTables {
+    const uint32_t* inst_key;
+    const uint32_t* inst_id;
+    const uint32_t* inst_fan;
+};
+csaw_status sample_batch(csaw_graph* g, const uint32_t* d_seeds, const uint64_t* d_inst_off, uint32_t n_inst,
+                         uint64_t n_seeds, uint32_t depth, const uint32_t* fan_max, const SampleTables& t,
+                         int kind, cudaStream_t s, csaw_sample_result** out);
 
 // Validation of a bias argument against a graph; fills the effective kind
 // (EDGE_WEIGHT on a graph without weights is UNIFORM).

@@ -83,7 +83,32 @@ struct SelParams {
     const uint32_t* __restrict__ item_h = nullptr;
     const uint64_t* __restrict__ hub_off = nullptr;
     const uint64_t* __restrict__ hubS = nullptr;
+    uint64_t hubS_cap = 0;                // entries of hubS
+    uint32_t* err = nullptr;              // error flags (8: a hub range beyond hubS_cap)
+    // instances of several requests in one run (null: one request): per
+    // instance its Philox key, its index within its request (the draw
+    // counter's instance word) and its picks per vertex at this layer
+    const uint32_t* __restrict__ inst_key = nullptr;   // [2 * n_inst]
+    const uint32_t* __restrict__ inst_id = nullptr;    // [n_inst]
+    const uint32_t* __restrict__ inst_k = nullptr;     // [n_inst]
 };
+
+// The draw key of one frontier entry: Philox key words and the instance word
+// of the counter.
+struct DrawKey {
+    uint32_t k0, k1, id;
+};
+
+__device__ __forceinline__ DrawKey draw_key(const SelParams& p, uint32_t inst)
+{
+    if (p.inst_key) return {__ldg(p.inst_key + 2 * inst), __ldg(p.inst_key + 2 * inst + 1), __ldg(p.inst_id + inst)};
+    return {p.k0, p.k1, inst};
+}
+
+__device__ __forceinline__ uint32_t picks_of(const SelParams& p, uint32_t inst)
+{
+    return p.inst_k ? __ldg(p.inst_k + inst) : p.k;
+}
 
 template <int KIND>
 __device__ __forceinline__ uint32_t sel_bias(const SelParams& p, uint64_t e)
@@ -117,12 +142,13 @@ __device__ void draw_picks(const SelParams& p, const uint64_t* S, uint32_t* bits
                            uint64_t T, uint32_t cnt, uint64_t q0, uint32_t v, uint32_t inst,
                            uint64_t beg, int lane)
 {
+    const DrawKey dk = draw_key(p, inst);
     const uint32_t lt = lanemask_lt();
     uint32_t have = 0;
     uint32_t a0 = 0;
     while (have < cnt && a0 < p.attempt_cap) {
         const bool live = a0 + lane < p.attempt_cap;   // the last round may be partial
-        const uint64_t r = philox_draw(p.k0, p.k1, a0 + lane, v, p.layer, inst);
+        const uint64_t r = philox_draw(dk.k0, dk.k1, a0 + lane, v, p.layer, dk.id);
         const uint32_t i = live ? upper_bound_S(S, d, scale_draw(r, T)) : 0xFFFFFFFFu;
         const bool chosen = live && ((bits[i >> 5] >> (i & 31)) & 1u);
         const uint32_t peers = __match_any_sync(CSAW_FULL_MASK, i);
@@ -153,7 +179,7 @@ __device__ void draw_picks(const SelParams& p, const uint64_t* S, uint32_t* bits
     R = warp_sum_u64(R);
     if (lane == 0) {
         for (uint32_t a = p.attempt_cap; have < cnt; ++a) {
-            const uint64_t r = philox_draw(p.k0, p.k1, a, v, p.layer, inst);
+            const uint64_t r = philox_draw(dk.k0, dk.k1, a, v, p.layer, dk.id);
             uint64_t x = scale_draw(r, T - R);
             // Walk the picked intervals in ascending order, skipping each one
             // that starts at or below the running position.
@@ -228,7 +254,7 @@ __device__ void warp_item(const SelParams& p, uint32_t e, uint64_t* sS, uint32_t
             npos += __popc(__ballot_sync(CSAW_FULL_MASK, b[t] > 0));
         }
     }
-    if (npos <= p.k) {
+    if (npos <= picks_of(p, inst)) {
         uint64_t q = q0;
 #pragma unroll
         for (int t = 0; t < TILES; ++t) {
@@ -393,12 +419,17 @@ __global__ void __launch_bounds__(SEL_THREADS) select_cdf_kernel(SelParams p)
             for (uint32_t j = lane; j < d; j += 32) emit(p, q0 + j, v, inst, __ldg(p.col + beg + j));
             continue;
         }
+        if (hub && p.hub_off[p.item_h[it]] + d > p.hubS_cap) {
+            if (lane == 0) atomicOr(p.err, 8u);   // never happens when the scratch is sized right
+            continue;
+        }
         const uint64_t* row = hub ? p.hubS + p.hub_off[p.item_h[it]] : p.cdf ? p.cdf + beg : nullptr;
+        const DrawKey dk = draw_key(p, inst);
         const uint64_t T = cdf_at(row, IMPLICIT, d - 1);
         uint32_t have = 0, a0 = 0;
         while (have < cnt && a0 < p.attempt_cap) {
             const bool live = a0 + lane < p.attempt_cap;   // the last round may be partial
-            const uint64_t x = scale_draw(philox_draw(p.k0, p.k1, a0 + lane, v, p.layer, inst), T);
+            const uint64_t x = scale_draw(philox_draw(dk.k0, dk.k1, a0 + lane, v, p.layer, dk.id), T);
             uint32_t i = 0xFFFFFFFFu;
             if (!live) {
             } else if (IMPLICIT) {
@@ -442,7 +473,7 @@ __global__ void __launch_bounds__(SEL_THREADS) select_cdf_kernel(SelParams p)
                 R += cdf_at(row, IMPLICIT, q) - (q ? cdf_at(row, IMPLICIT, q - 1) : 0);
             }
             for (uint32_t a = p.attempt_cap; have < cnt; ++a) {
-                uint64_t x = scale_draw(philox_draw(p.k0, p.k1, a, v, p.layer, inst), T - R);
+                uint64_t x = scale_draw(philox_draw(dk.k0, dk.k1, a, v, p.layer, dk.id), T - R);
                 for (uint32_t j = 0; j < have; ++j) {
                     const uint32_t q = picks[j];
                     const uint64_t start = q ? cdf_at(row, IMPLICIT, q - 1) : 0;
@@ -489,6 +520,9 @@ struct CountParams {
     // hub items (degree above theta_w, at most PICK_MAX picks) when the layer
     // shares one cumulative array per distinct hub; null: they are CTA items
     uint32_t* __restrict__ hub_list = nullptr;
+    // picks per vertex of each instance at this layer (null: k for all)
+    const uint32_t* __restrict__ inst_k = nullptr;
+    uint32_t vbits = 0;
 };
 
 // Number of positive biases of v's neighbours (only when zeros are possible).
@@ -533,8 +567,9 @@ __global__ void count_kernel(CountParams p)
                 if (lane == l) npos = c;
             }
         }
-        const uint32_t c = min(p.k, npos);
-        const bool take_all = npos <= p.k;
+        const uint32_t k = (p.inst_k && e < n) ? __ldg(p.inst_k + (uint32_t)(p.fkeys[e] >> p.vbits)) : p.k;
+        const uint32_t c = min(k, npos);
+        const bool take_all = npos <= k;
         const bool to_warp = e < n && c > 0 && (take_all || (p.cached ? c <= PICK_MAX : d <= p.theta_w));
         const bool to_hub = e < n && c > 0 && !to_warp && p.hub_list != nullptr && c <= PICK_MAX;
         const bool to_cta = e < n && c > 0 && !to_warp && !to_hub;
@@ -570,18 +605,19 @@ __global__ void count_kernel(CountParams p)
 // hub) item draws from them by binary search (select_cdf_kernel in hub
 // mode).  Same prefix sums, same draws: the picks are unchanged.
 
-// keys[j] = e << vbits | v for hub item j (entry e at vertex v); sorted on
-// their low vbits bits by the stable radix sort, items of one vertex end up
-// adjacent and in entry order.
+// keys[j] = e << vshift | v for hub item j (entry e at vertex v), vshift =
+// the vertex bits rounded up to whole bytes: the radix sort orders whole
+// bytes, so the sorted low vshift bits hold the vertex alone.  Sorted stably,
+// the items of one vertex end up adjacent.
 __global__ void hub_keys_kernel(const uint32_t* __restrict__ hub_list, const unsigned long long* n_dev,
-                                const uint64_t* __restrict__ fkeys, uint64_t vmask, uint32_t vbits,
+                                const uint64_t* __restrict__ fkeys, uint64_t vmask, uint32_t vshift,
                                 uint64_t* __restrict__ keys)
 {
     const uint64_t n = *n_dev;
     for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
          j += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t e = hub_list[j];
-        keys[j] = ((uint64_t)e << vbits) | (fkeys[e] & vmask);
+        keys[j] = ((uint64_t)e << vshift) | (fkeys[e] & vmask);
     }
 }
 
@@ -602,7 +638,7 @@ constexpr uint32_t HUB_WARP_DEG = 2048;   // hubs up to this degree: one warp bu
 // lists the hub for a whole CTA when it is above HUB_WARP_DEG.
 __global__ void hub_items_kernel(const uint64_t* __restrict__ sorted, const unsigned long long* n_dev,
                                  const uint32_t* __restrict__ flag, const uint64_t* __restrict__ hpos,
-                                 uint64_t vmask, uint32_t vbits, const uint64_t* __restrict__ off,
+                                 uint64_t vmask, uint32_t vshift, const uint64_t* __restrict__ off,
                                  uint32_t* __restrict__ item_e, uint32_t* __restrict__ item_h,
                                  uint32_t* __restrict__ H, uint32_t* __restrict__ dh,
                                  uint32_t* __restrict__ big_list, unsigned long long* n_big)
@@ -613,7 +649,7 @@ __global__ void hub_items_kernel(const uint64_t* __restrict__ sorted, const unsi
         const uint64_t key = sorted[q];
         const uint32_t v = (uint32_t)(key & vmask);
         const uint32_t h = (uint32_t)(hpos[q] + flag[q] - 1);
-        item_e[q] = (uint32_t)(key >> vbits);
+        item_e[q] = (uint32_t)(key >> vshift);
         item_h[q] = h;
         if (flag[q]) {
             const uint32_t d = (uint32_t)(__ldg(off + v + 1) - __ldg(off + v));
@@ -637,6 +673,8 @@ struct HubBuildParams {
     const unsigned long long* n_big; // hubs above HUB_WARP_DEG
     unsigned long long* next;        // [0] CTA counter, [1] warp counter
     uint64_t* __restrict__ S;
+    uint64_t S_cap;                  // entries of S
+    uint32_t* err;                   // flag 8: a hub range beyond S_cap (skipped)
 };
 
 // Bias of edge e (static kinds).
@@ -689,6 +727,10 @@ __global__ void __launch_bounds__(SEL_THREADS) hub_cdf_kernel(HubBuildParams p)
         if (it >= n_big) break;
         const uint32_t h = p.big_list[it];
         const uint32_t d = p.dh[h];
+        if (p.hub_off[h] + d > p.S_cap) {
+            if (threadIdx.x == 0) atomicOr(p.err, 8u);
+            continue;
+        }
         const uint64_t beg = __ldg(p.off + p.H[h]);
         uint64_t* out = p.S + p.hub_off[h];
         uint64_t carry = 0;
@@ -733,6 +775,10 @@ __global__ void __launch_bounds__(SEL_THREADS) hub_cdf_kernel(HubBuildParams p)
         if (h >= nh) break;
         const uint32_t d = p.dh[h];
         if (d > HUB_WARP_DEG) continue;
+        if (p.hub_off[h] + d > p.S_cap) {
+            if (lane == 0) atomicOr(p.err, 8u);
+            continue;
+        }
         hub_row_scan_warp<KIND>(p, __ldg(p.off + p.H[h]), d, p.S + p.hub_off[h], lane);
     }
 }
@@ -1313,6 +1359,10 @@ struct Pipeline {
     uint32_t attempt_cap = CSAW_ATTEMPT_CAP;
     uint32_t k0 = 0, k1 = 0;
     const uint32_t* key_dev = nullptr;   // plan mode: Philox key in device memory
+    // several requests in one run: per-instance draw keys and fanouts (device)
+    const uint32_t* inst_key = nullptr;  // [2 * n_inst]
+    const uint32_t* inst_id = nullptr;   // [n_inst]
+    const uint32_t* inst_fan = nullptr;  // [depth][n_inst]
     uint64_t* ctr = nullptr;             // [CT_WORDS]
     void* scan_scr = nullptr;
     void* sort_scr = nullptr;
@@ -1407,13 +1457,14 @@ static csaw_status enqueue_hub_groups(Pipeline& P, uint32_t l, cudaStream_t s)
     const uint64_t cap = P.L[l].f_cap;
     const unsigned long long* n_hub = (const unsigned long long*)P.lc(l, L_ITEMS + 2);
     const unsigned grid = grid_for(cap, 256, g->sm_count);
-    hub_keys_kernel<<<grid, 256, 0, s>>>(P.hlist, n_hub, P.L[l].F, P.vmask, (uint32_t)P.vbits, P.hkeys);
+    const uint32_t vshift = ((uint32_t)P.vbits + 7u) & ~7u;
+    hub_keys_kernel<<<grid, 256, 0, s>>>(P.hlist, n_hub, P.L[l].F, P.vmask, vshift, P.hkeys);
     uint64_t* sorted = P.hkeys;
-    CSAW_TRY(radix_sort_u64(P.hkeys, P.halt, (const uint64_t*)n_hub, cap, P.vbits, g->sm_count, P.sort_scr, s,
-                            &sorted));
+    CSAW_TRY(radix_sort_u64(P.hkeys, P.halt, (const uint64_t*)n_hub, cap, (int)vshift, g->sm_count, P.sort_scr,
+                            s, &sorted));
     hub_flag_kernel<<<grid, 256, 0, s>>>(sorted, n_hub, P.vmask, P.hflag);
     CSAW_TRY(scan_u32(P.hflag, P.hpos, (const uint64_t*)n_hub, cap, P.scan_scr, P.lc(l, L_NH), s));
-    hub_items_kernel<<<grid, 256, 0, s>>>(sorted, n_hub, P.hflag, P.hpos, P.vmask, (uint32_t)P.vbits, g->off,
+    hub_items_kernel<<<grid, 256, 0, s>>>(sorted, n_hub, P.hflag, P.hpos, P.vmask, vshift, g->off,
                                           P.item_e, P.item_h, P.hubH, P.hubD, P.hubBig,
                                           (unsigned long long*)P.lc(l, L_NBIG));
     CSAW_TRY(scan_u32(P.hubD, P.hub_off, P.lc(l, L_NH), cap, P.scan_scr, P.lc(l, L_HUBE), s));
@@ -1433,6 +1484,8 @@ static csaw_status enqueue_count(Pipeline& P, uint32_t l, cudaStream_t s)
     cp.cnt = B.cnt; cp.warp_list = B.wlist; cp.cta_list = B.clist;
     cp.n_items = (unsigned long long*)P.lc(l, L_ITEMS);
     cp.hub_list = P.hub_path ? P.hlist : nullptr;
+    cp.inst_k = P.inst_fan ? P.inst_fan + (uint64_t)l * P.n_inst : nullptr;
+    cp.vbits = (uint32_t)P.vbits;
     if (B.f_cap) {
         switch (P.kind) {
         case CSAW_BIAS_UNIFORM: CSAW_TRY(launch_count<CSAW_BIAS_UNIFORM>(cp, B.f_cap, g->sm_count, s)); break;
@@ -1463,6 +1516,8 @@ static csaw_status enqueue_select(Pipeline& P, uint32_t l, cudaStream_t s)
         sp.cdf = P.cached && P.kind != CSAW_BIAS_UNIFORM ? g->cdf[P.kind] : nullptr;
         sp.skip_warp_items = P.cached;
         sp.attempt_cap = P.attempt_cap;
+        sp.inst_key = P.inst_key; sp.inst_id = P.inst_id;
+        sp.inst_k = P.inst_fan ? P.inst_fan + (uint64_t)l * P.n_inst : nullptr;
         if (P.cached) {
             // warp items over the cached array; CTA items (more than PICK_MAX
             // picks) by the streaming kernel below
@@ -1485,12 +1540,14 @@ static csaw_status enqueue_select(Pipeline& P, uint32_t l, cudaStream_t s)
             hp.nh = (const unsigned long long*)P.lc(l, L_NH);
             hp.big_list = P.hubBig; hp.n_big = (const unsigned long long*)P.lc(l, L_NBIG);
             hp.next = (unsigned long long*)P.lc(l, L_HNEXT); hp.S = P.hubS;
+            hp.S_cap = P.hubS_cap; hp.err = (uint32_t*)(P.ctr + CT_ERR);
             const int blocks = g->sm_count * 4;
             if (P.kind == CSAW_BIAS_EDGE_WEIGHT) hub_cdf_kernel<CSAW_BIAS_EDGE_WEIGHT><<<blocks, SEL_THREADS, 0, s>>>(hp);
             else hub_cdf_kernel<CSAW_BIAS_NEIGHBOR_DEGREE><<<blocks, SEL_THREADS, 0, s>>>(hp);
             SelParams hs = sp;
             hs.cdf = nullptr;
             hs.item_e = P.item_e; hs.item_h = P.item_h; hs.hub_off = P.hub_off; hs.hubS = P.hubS;
+            hs.hubS_cap = P.hubS_cap; hs.err = (uint32_t*)(P.ctr + CT_ERR);
             select_cdf_kernel<false><<<g->sm_count * 8, SEL_THREADS, 0, s>>>(hs);
             CSAW_CUDA(cudaGetLastError());
         }
@@ -1606,6 +1663,7 @@ static csaw_status check_errors(uint64_t err)
     if (err & 1u) return fail(CSAW_ERR_INVALID, "a seed is not a vertex of the graph");
     if (err & 2u) return fail(CSAW_ERR_INVALID, "inst_offsets must start at 0 and be non-decreasing");
     if (err & 4u) return fail(CSAW_ERR_INVALID, "more seeds than the plan was created for");
+    if (err & 8u) return fail(CSAW_ERR_CUDA, "internal: the shared hub scratch was too small");
     return CSAW_OK;
 }
 
@@ -1681,7 +1739,7 @@ static csaw_status enqueue_layer_select(Pipeline& P, uint32_t l, uint64_t* VP, u
 static csaw_status run_sample(csaw_graph* g, const uint32_t* seeds, const uint64_t* inst_off,
                               uint32_t n_inst, uint64_t n_seeds, uint32_t depth, const uint32_t* fanout,
                               int kind, uint64_t rng_seed, uint32_t attempt_cap, bool layer_mode,
-                              cudaStream_t s, csaw_sample_result* R)
+                              cudaStream_t s, csaw_sample_result* R, const SampleTables* tabs = nullptr)
 {
     Temps tmp(s);
     auto get = [&](void** p, size_t bytes) -> csaw_status {
@@ -1694,6 +1752,11 @@ static csaw_status run_sample(csaw_graph* g, const uint32_t* seeds, const uint64
     P.init(g, kind, n_inst, depth, fanout, rng_seed);
     P.attempt_cap = attempt_cap;
     P.seeds_cap = n_seeds;
+    if (tabs) {
+        P.inst_key = tabs->inst_key;
+        P.inst_id = tabs->inst_id;
+        P.inst_fan = tabs->inst_fan;
+    }
     CSAW_TRY(alloc_common(P, get));
     CSAW_CUDA(cudaMemsetAsync(P.ctr, 0, sizeof(uint64_t) * CT_WORDS, s));
     CSAW_TRY(alloc_entries(P, 0, n_seeds, get));
@@ -1755,13 +1818,36 @@ static csaw_status run_sample(csaw_graph* g, const uint32_t* seeds, const uint64
         CSAW_CUDA(cudaMemcpyAsync(R->edge_offsets.data(), P.eoff, sizeof(uint64_t) * (ng + 1), cudaMemcpyDeviceToHost, s));
         CSAW_CUDA(cudaMemcpyAsync(R->frontier_sizes.data(), P.fsize, sizeof(uint64_t) * ng, cudaMemcpyDeviceToHost, s));
     }
+    uint64_t err_end = 0;
+    CSAW_CUDA(cudaMemcpyAsync(&err_end, P.ctr + CT_ERR, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
     CSAW_CUDA(cudaStreamSynchronize(s));
+    CSAW_TRY(check_errors(err_end));
     uint64_t total = 0;
     for (uint32_t l = 0; l < depth; ++l) total += R->layer_edges[l];
     R->n_edges = total;
     R->edge_offsets[ng] = total;
     R->src_c.assign(R->src.begin(), R->src.end());
     R->dst_c.assign(R->dst.begin(), R->dst.end());
+    return CSAW_OK;
+}
+
+csaw_status sample_batch(csaw_graph* g, const uint32_t* d_seeds, const uint64_t* d_inst_off, uint32_t n_inst,
+                         uint64_t n_seeds, uint32_t depth, const uint32_t* fan_max, const SampleTables& t,
+                         int kind, cudaStream_t s, csaw_sample_result** out)
+{
+    *out = nullptr;
+    csaw_sample_result* R = new (std::nothrow) csaw_sample_result();
+    if (!R) return fail(CSAW_ERR_NOMEM, "host allocation failed");
+    R->depth = depth;
+    R->n_instances = n_inst;
+    const csaw_status st = run_sample(g, d_seeds, d_inst_off, n_inst, n_seeds, depth, fan_max, kind, 0,
+                                      CSAW_ATTEMPT_CAP, false, s, R, &t);
+    if (st != CSAW_OK) {
+        cudaStreamSynchronize(s);
+        delete R;
+        return st;
+    }
+    *out = R;
     return CSAW_OK;
 }
 

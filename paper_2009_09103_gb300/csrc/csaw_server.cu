@@ -5,10 +5,15 @@
 // own CUDA stream, so admitted requests run concurrently and their kernels
 // overlap on the GPU; a request that arrives while others run starts as soon
 // as a slot and enough budget are free, without waiting for the running ones
-// to finish.  Every request's draws are keyed by its own seed and its own
-// instance / walker indices, so its result is the same alone or in the mix.
-// The paper has no serving layer; this wraps its selection path (Sec. III-IV)
-// for a stream of independent sampling and walk instances (Sec. IV-A).
+// to finish.  A slot that frees up takes the oldest waiting request together
+// with the other waiting requests of the same kind and bias (continuous
+// batching): their instances, or walkers, run as one multi-instance launch --
+// the batched multi-instance sampling of Sec. V-B -- with each request's own
+// seed and its own instance / walker indices in the draws, so every result
+// is the same alone, in a batch or in the mix.  Inputs go in and results come
+// out through each slot's pinned staging buffer.  The paper has no serving
+// layer; this runs its selection path (Sec. III-IV) for a stream of
+// independent sampling and walk instances (Sec. IV-A).
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -142,41 +147,283 @@ void free_server_result(void* p)
     delete r;
 }
 
-// Runs one request on stream s; fills res (status and host arrays).
-static void execute(csaw_graph* g, Request& rq, csaw_result* res, cudaStream_t s)
+// One slot: two streams and a pinned staging buffer (grown on demand).
+// Small batches run on the high-priority stream, so that their blocks are
+// scheduled ahead of the waiting blocks of large batches in other slots;
+// the batched walk kernels keep their blocks short for the same reason.
+struct Lane {
+    cudaStream_t lo = nullptr, hi = nullptr;
+    cudaStream_t s = nullptr;          // the stream of the current batch
+    unsigned char* pin = nullptr;
+    size_t pin_cap = 0;
+};
+
+constexpr uint64_t SMALL_BATCH_EDGES = 1ull << 18;   // at most this many sampled edges: high priority
+constexpr uint32_t WALK_WARP_BUDGET = 4;              // walkers (or 32-walker groups) per warp and block
+
+static csaw_status lane_pinned(Lane& L, size_t bytes)
 {
-    if (rq.kind == CSAW_REQ_WALK) {
-        const uint64_t n = rq.starts.size();
-        res->n_walkers = n;
-        res->length = rq.length;
-        res->path = new (std::nothrow) uint32_t[n * ((uint64_t)rq.length + 1) + 1];
-        if (!res->path) { res->status = CSAW_ERR_NOMEM; return; }
-        res->status = csaw_walk(g, rq.starts.data(), n, rq.length, &rq.bias, rq.rng_seed, res->path,
-                                CSAW_MEM_HOST, s);
-        return;
+    if (bytes <= L.pin_cap) return CSAW_OK;
+    if (L.pin) {
+        CSAW_CUDA(cudaStreamSynchronize(L.s));
+        cudaFreeHost(L.pin);
+        L.pin = nullptr;
+        L.pin_cap = 0;
     }
-    csaw_sample_result* sr = nullptr;
-    res->status = csaw_sample(g, rq.seeds.data(), rq.io.data(), rq.n_instances, (uint32_t)rq.fanout.size(),
-                              rq.fanout.data(), &rq.bias, rq.rng_seed, CSAW_MEM_HOST, s, &sr);
-    if (res->status != CSAW_OK) return;
+    size_t cap = bytes < (1u << 20) ? (1u << 20) : bytes;
+    cap += cap / 4;
+    void* p = nullptr;
+    CSAW_CUDA(cudaHostAlloc(&p, cap, cudaHostAllocDefault));
+    L.pin = (unsigned char*)p;
+    L.pin_cap = cap;
+    return CSAW_OK;
+}
+
+static inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// Walk requests of one bias in one launch.  Inputs are packed in the staging
+// buffer as [segment starts u64 (R+1) | row offsets u64 (R) | lengths u32 (R)
+// | keys u32 (2R) | start vertices u32 (n)], copied in once; the path matrix
+// of every request comes back in one copy.
+static csaw_status execute_walks(csaw_graph* g, Lane& L, std::vector<Request*>& batch)
+{
+    const size_t R = batch.size();
+    uint64_t n = 0, rows = 0;
+    uint32_t max_len = 0;
+    for (Request* rq : batch) {
+        n += rq->starts.size();
+        rows += (uint64_t)rq->starts.size() * ((uint64_t)rq->length + 1);
+        max_len = rq->length > max_len ? rq->length : max_len;
+    }
+    const size_t o_start = 0, o_row0 = align16(o_start + 8 * (R + 1)), o_len = align16(o_row0 + 8 * R);
+    const size_t o_key = align16(o_len + 4 * R), o_starts = align16(o_key + 8 * R);
+    const size_t in_bytes = align16(o_starts + 4 * n);
+    const size_t out_bytes = 4 * rows;
+    CSAW_TRY(lane_pinned(L, in_bytes > out_bytes ? in_bytes : out_bytes));
+    uint64_t* h_start = (uint64_t*)(L.pin + o_start);
+    uint64_t* h_row0 = (uint64_t*)(L.pin + o_row0);
+    uint32_t* h_len = (uint32_t*)(L.pin + o_len);
+    uint32_t* h_key = (uint32_t*)(L.pin + o_key);
+    uint32_t* h_starts = (uint32_t*)(L.pin + o_starts);
+    uint64_t w = 0, row = 0;
+    for (size_t r = 0; r < R; ++r) {
+        const Request* rq = batch[r];
+        h_start[r] = w;
+        h_row0[r] = row;
+        h_len[r] = rq->length;
+        h_key[2 * r] = (uint32_t)rq->rng_seed;
+        h_key[2 * r + 1] = (uint32_t)(rq->rng_seed >> 32);
+        if (!rq->starts.empty()) std::memcpy(h_starts + w, rq->starts.data(), 4 * rq->starts.size());
+        w += rq->starts.size();
+        row += (uint64_t)rq->starts.size() * ((uint64_t)rq->length + 1);
+    }
+    h_start[R] = w;
+    void* d_in = nullptr;
+    void* d_path = nullptr;
+    CSAW_TRY(dalloc(&d_in, in_bytes, L.s));
+    csaw_status st = dalloc(&d_path, out_bytes ? out_bytes : 4, L.s);
+    if (st == CSAW_OK) {
+        cudaError_t e = cudaMemcpyAsync(d_in, L.pin, in_bytes, cudaMemcpyHostToDevice, L.s);
+        if (e != cudaSuccess) st = cuda_fail(e, "copy walk batch in");
+    }
+    if (st == CSAW_OK) {
+        unsigned char* d = (unsigned char*)d_in;
+        WalkSegments seg;
+        seg.start = (const uint64_t*)(d + o_start);
+        seg.row0 = (const uint64_t*)(d + o_row0);
+        seg.len = (const uint32_t*)(d + o_len);
+        seg.key = (const uint32_t*)(d + o_key);
+        seg.n = (uint32_t)R;
+        seg.warp_budget = WALK_WARP_BUDGET;
+        st = walk_batch(g, &batch[0]->bias, (const uint32_t*)(d + o_starts), n, seg, max_len, (uint32_t*)d_path,
+                        L.s);
+    }
+    if (st == CSAW_OK && out_bytes) {
+        cudaError_t e = cudaMemcpyAsync(L.pin, d_path, out_bytes, cudaMemcpyDeviceToHost, L.s);
+        if (e != cudaSuccess) st = cuda_fail(e, "copy paths out");
+    }
+    dfree(d_in, L.s);
+    dfree(d_path, L.s);
+    if (st == CSAW_OK) {
+        cudaError_t e = cudaStreamSynchronize(L.s);
+        if (e != cudaSuccess) st = cuda_fail(e, "walk batch");
+    }
+    if (st != CSAW_OK) return st;
+    const uint32_t* h_path = (const uint32_t*)L.pin;
+    row = 0;
+    for (Request* rq : batch) {
+        csaw_result* res = rq->result;
+        const uint64_t cnt = (uint64_t)rq->starts.size() * ((uint64_t)rq->length + 1);
+        res->n_walkers = rq->starts.size();
+        res->length = rq->length;
+        res->path = new (std::nothrow) uint32_t[cnt + 1];
+        if (!res->path) {
+            res->status = CSAW_ERR_NOMEM;
+        } else {
+            std::memcpy(res->path, h_path + row, 4 * cnt);
+            res->status = CSAW_OK;
+        }
+        row += cnt;
+    }
+    return CSAW_OK;
+}
+
+// Sampling requests of one bias in one multi-instance run.  The batch's
+// instances are the requests' instances in order; the tables give each one
+// its request's key, its own index and its request's fanout per layer (0
+// past the request's depth).  Inputs are packed as [instance offsets u64
+// (N+1) | keys u32 (2N) | indices u32 (N) | fanouts u32 (depth N) | seeds u32
+// (S)]; every layer's edges come back in one copy each for src and dst.
+static csaw_status execute_samples(csaw_graph* g, Lane& L, std::vector<Request*>& batch)
+{
+    uint64_t N = 0, S = 0;
+    uint32_t depth = 0;
+    for (Request* rq : batch) {
+        N += rq->n_instances;
+        S += rq->seeds.size();
+        depth = (uint32_t)rq->fanout.size() > depth ? (uint32_t)rq->fanout.size() : depth;
+    }
+    if (N >= 0xFFFFFFFFull || S >= 0xFFFFFFFFull) return fail(CSAW_ERR_INVALID, "batch too large");
+    const size_t o_io = 0, o_key = align16(8 * (N + 1)), o_id = align16(o_key + 8 * N);
+    const size_t o_fan = align16(o_id + 4 * N), o_seeds = align16(o_fan + 4 * (size_t)depth * N);
+    const size_t in_bytes = align16(o_seeds + 4 * S);
+    CSAW_TRY(lane_pinned(L, in_bytes));
+    uint64_t* h_io = (uint64_t*)(L.pin + o_io);
+    uint32_t* h_key = (uint32_t*)(L.pin + o_key);
+    uint32_t* h_id = (uint32_t*)(L.pin + o_id);
+    uint32_t* h_fan = (uint32_t*)(L.pin + o_fan);
+    uint32_t* h_seeds = (uint32_t*)(L.pin + o_seeds);
+    std::vector<uint32_t> fan_max(depth, 0);
+    uint64_t i0 = 0, s0 = 0;
+    for (Request* rq : batch) {
+        for (uint32_t i = 0; i < rq->n_instances; ++i) {
+            h_io[i0 + i] = s0 + rq->io[i];
+            h_key[2 * (i0 + i)] = (uint32_t)rq->rng_seed;
+            h_key[2 * (i0 + i) + 1] = (uint32_t)(rq->rng_seed >> 32);
+            h_id[i0 + i] = i;
+            for (uint32_t l = 0; l < depth; ++l)
+                h_fan[(uint64_t)l * N + i0 + i] = l < rq->fanout.size() ? rq->fanout[l] : 0u;
+        }
+        for (uint32_t l = 0; l < rq->fanout.size(); ++l)
+            fan_max[l] = rq->fanout[l] > fan_max[l] ? rq->fanout[l] : fan_max[l];
+        if (!rq->seeds.empty()) std::memcpy(h_seeds + s0, rq->seeds.data(), 4 * rq->seeds.size());
+        i0 += rq->n_instances;
+        s0 += rq->seeds.size();
+    }
+    h_io[N] = S;
+    int kind;
+    CSAW_TRY(check_bias(g, &batch[0]->bias, false, &kind));
+    void* d_in = nullptr;
+    CSAW_TRY(dalloc(&d_in, in_bytes, L.s));
+    csaw_sample_result* R = nullptr;
+    csaw_status st = CSAW_OK;
+    cudaError_t e = cudaMemcpyAsync(d_in, L.pin, in_bytes, cudaMemcpyHostToDevice, L.s);
+    if (e != cudaSuccess) st = cuda_fail(e, "copy sample batch in");
+    if (st == CSAW_OK) {
+        unsigned char* d = (unsigned char*)d_in;
+        SampleTables t;
+        t.inst_key = (const uint32_t*)(d + o_key);
+        t.inst_id = (const uint32_t*)(d + o_id);
+        t.inst_fan = (const uint32_t*)(d + o_fan);
+        st = sample_batch(g, (const uint32_t*)(d + o_seeds), (const uint64_t*)(d + o_io), (uint32_t)N, S, depth,
+                          fan_max.data(), t, kind, L.s, &R);
+    }
+    dfree(d_in, L.s);
+    if (st != CSAW_OK) return st;
     csaw_sample_view v;
-    csaw_sample_get_view(sr, &v);
-    res->depth = v.depth;
-    res->n_instances = v.n_instances;
-    res->n_edges = v.n_edges;
-    const uint64_t ng = (uint64_t)v.depth * v.n_instances;
-    res->edge_offsets = new (std::nothrow) uint64_t[ng + 1];
-    res->frontier_sizes = new (std::nothrow) uint64_t[ng + 1];
-    res->src = new (std::nothrow) uint32_t[v.n_edges + 1];
-    res->dst = new (std::nothrow) uint32_t[v.n_edges + 1];
-    if (!res->edge_offsets || !res->frontier_sizes || !res->src || !res->dst) {
-        res->status = CSAW_ERR_NOMEM;
-    } else {
-        std::memcpy(res->edge_offsets, v.edge_offsets, sizeof(uint64_t) * (ng + 1));
-        std::memcpy(res->frontier_sizes, v.frontier_sizes, sizeof(uint64_t) * (ng ? ng : 1));
-        res->status = csaw_sample_copy_edges(sr, res->src, res->dst);
+    csaw_sample_get_view(R, &v);
+    // every layer's edges: src at [0, E), dst at [E, 2E) of the staging buffer
+    const uint64_t E = v.n_edges;
+    st = lane_pinned(L, 8 * E + 16);
+    uint32_t* h_src = (uint32_t*)L.pin;
+    uint32_t* h_dst = h_src + E;
+    for (uint32_t l = 0; st == CSAW_OK && l < depth; ++l) {
+        const uint64_t a = v.edge_offsets[(uint64_t)l * N], b = v.edge_offsets[(uint64_t)(l + 1) * N];
+        if (b > a) {
+            e = cudaMemcpyAsync(h_src + a, v.src[l], 4 * (b - a), cudaMemcpyDeviceToHost, L.s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(h_dst + a, v.dst[l], 4 * (b - a), cudaMemcpyDeviceToHost, L.s);
+            if (e != cudaSuccess) st = cuda_fail(e, "copy edges out");
+        }
     }
-    csaw_result_free(sr);
+    if (st == CSAW_OK) {
+        e = cudaStreamSynchronize(L.s);
+        if (e != cudaSuccess) st = cuda_fail(e, "sample batch");
+    }
+    if (st != CSAW_OK) {
+        csaw_result_free(R);
+        return st;
+    }
+    // each request: its instances' edges of its own layers, in csaw_sample's layout
+    i0 = 0;
+    for (Request* rq : batch) {
+        csaw_result* res = rq->result;
+        const uint32_t n = rq->n_instances, dep = (uint32_t)rq->fanout.size();
+        const uint64_t ng = (uint64_t)dep * n;
+        uint64_t total = 0;
+        for (uint32_t l = 0; l < dep; ++l)
+            total += v.edge_offsets[(uint64_t)l * N + i0 + n] - v.edge_offsets[(uint64_t)l * N + i0];
+        res->depth = dep;
+        res->n_instances = n;
+        res->n_edges = total;
+        res->edge_offsets = new (std::nothrow) uint64_t[ng + 1];
+        res->frontier_sizes = new (std::nothrow) uint64_t[ng + 1];
+        res->src = new (std::nothrow) uint32_t[total + 1];
+        res->dst = new (std::nothrow) uint32_t[total + 1];
+        if (!res->edge_offsets || !res->frontier_sizes || !res->src || !res->dst) {
+            res->status = CSAW_ERR_NOMEM;
+        } else {
+            uint64_t at = 0;
+            for (uint32_t l = 0; l < dep; ++l) {
+                const uint64_t* eo = v.edge_offsets + (uint64_t)l * N + i0;
+                for (uint32_t i = 0; i < n; ++i) {
+                    res->edge_offsets[(uint64_t)l * n + i] = at + (eo[i] - eo[0]);
+                    res->frontier_sizes[(uint64_t)l * n + i] = v.frontier_sizes[(uint64_t)l * N + i0 + i];
+                }
+                const uint64_t cnt = eo[n] - eo[0];
+                std::memcpy(res->src + at, h_src + eo[0], 4 * cnt);
+                std::memcpy(res->dst + at, h_dst + eo[0], 4 * cnt);
+                at += cnt;
+            }
+            res->edge_offsets[ng] = total;
+            res->status = CSAW_OK;
+        }
+        i0 += n;
+    }
+    csaw_result_free(R);
+    return CSAW_OK;
+}
+
+// Sampled edges a request produces at most (walk steps; sampling without
+// the visited filter).
+static uint64_t edge_bound(const Request* rq)
+{
+    if (rq->kind == CSAW_REQ_WALK) return (uint64_t)rq->starts.size() * rq->length;
+    uint64_t f = rq->seeds.size(), total = 0;
+    for (uint32_t k : rq->fanout) {
+        const uint64_t e = f > (1ull << 40) / (k ? k : 1) ? (1ull << 40) : f * k;
+        total += e;
+        f = e;
+    }
+    return total;
+}
+
+// Runs a batch (one kind, one bias) on the slot; fills every request's result.
+static void execute(csaw_graph* g, Lane& L, std::vector<Request*>& batch)
+{
+    uint64_t edges = 0;
+    for (const Request* rq : batch) edges += edge_bound(rq);
+    L.s = edges <= SMALL_BATCH_EDGES ? L.hi : L.lo;
+    const csaw_status st = batch[0]->kind == CSAW_REQ_WALK ? execute_walks(g, L, batch)
+                                                            : execute_samples(g, L, batch);
+    if (st != CSAW_OK)
+        for (Request* rq : batch) rq->result->status = st;
+}
+
+static bool same_bias(const csaw_bias& a, const csaw_bias& b)
+{
+    return a.kind == b.kind && (a.kind != CSAW_BIAS_NODE2VEC ||
+                                (a.n2v_mult[0] == b.n2v_mult[0] && a.n2v_mult[1] == b.n2v_mult[1] &&
+                                 a.n2v_mult[2] == b.n2v_mult[2]));
 }
 
 }  // namespace csaw
@@ -188,6 +435,7 @@ struct csaw_server {
     DegreeTable degrees;
     uint64_t budget = 0;
     uint32_t slots = 0;
+    uint32_t max_batch = 32;
     std::mutex mu;
     std::condition_variable cv_work;
     std::condition_variable cv_done;
@@ -198,36 +446,68 @@ struct csaw_server {
     uint32_t running = 0;
     bool stop = false;
     std::vector<std::thread> workers;
-    std::vector<cudaStream_t> streams;
+    std::vector<Lane> lanes;
+
+    // The oldest waiting request, then (up to max_batch in all) every other
+    // waiting request of the same kind and bias whose estimate still fits
+    // the budget, in arrival order.  Called with mu held.
+    void take_batch(std::vector<Request*>& batch)
+    {
+        batch.clear();
+        Request* head = pending.front();
+        pending.pop_front();
+        batch.push_back(head);
+        uint64_t est = head->estimate;
+        uint64_t items = head->kind == CSAW_REQ_WALK ? head->starts.size() : head->n_instances;
+        uint64_t seeds = head->seeds.size();
+        for (auto it = pending.begin(); it != pending.end() && batch.size() < max_batch;) {
+            Request* rq = *it;
+            const uint64_t more = rq->kind == CSAW_REQ_WALK ? rq->starts.size() : rq->n_instances;
+            if (rq->kind == head->kind && same_bias(rq->bias, head->bias) &&
+                in_use + est + rq->estimate <= budget && items + more < 0x7FFFFFFFull &&
+                seeds + rq->seeds.size() < 0x7FFFFFFFull) {
+                batch.push_back(rq);
+                est += rq->estimate;
+                items += more;
+                seeds += rq->seeds.size();
+                it = pending.erase(it);
+            } else {
+                ++it;
+            }
+        }
+    }
 
     void worker(uint32_t slot)
     {
         cudaSetDevice(g->device);
-        cudaStream_t s = streams[slot];
+        Lane& L = lanes[slot];
+        std::vector<Request*> batch;
         std::unique_lock<std::mutex> lk(mu);
         while (true) {
             cv_work.wait(lk, [&] {
                 return stop || (!pending.empty() && in_use + pending.front()->estimate <= budget);
             });
-            if (stop && pending.empty()) break;
-            if (stop) {
-                // shutting down: pending requests are aborted by destroy
-                break;
+            if (stop) break;   // pending requests are aborted by destroy
+            take_batch(batch);
+            const int64_t t_admit = now_ns();
+            for (Request* rq : batch) {
+                in_use += rq->estimate;
+                ++running;
+                rq->state = Request::RUNNING;
+                rq->result->t_admit_ns = t_admit;
             }
-            Request* rq = pending.front();
-            pending.pop_front();
-            in_use += rq->estimate;
-            ++running;
-            rq->state = Request::RUNNING;
-            rq->result->t_admit_ns = now_ns();
             lk.unlock();
-            rq->result->t_start_ns = now_ns();
-            execute(g, *rq, rq->result, s);
-            rq->result->t_finish_ns = now_ns();
+            const int64_t t_start = now_ns();
+            for (Request* rq : batch) rq->result->t_start_ns = t_start;
+            execute(g, L, batch);
+            const int64_t t_finish = now_ns();
             lk.lock();
-            in_use -= rq->estimate;
-            --running;
-            rq->state = Request::DONE;
+            for (Request* rq : batch) {
+                rq->result->t_finish_ns = t_finish;
+                in_use -= rq->estimate;
+                --running;
+                rq->state = Request::DONE;
+            }
             cv_done.notify_all();
             cv_work.notify_all();
         }
@@ -247,18 +527,25 @@ extern "C" csaw_status csaw_server_create(csaw_graph* g, const csaw_server_opts*
     sv->g = g;
     sv->budget = opts->budget_bytes;
     sv->slots = opts->slots;
+    sv->max_batch = opts->max_batch ? opts->max_batch : 32;
     cudaError_t e = cudaSetDevice(g->device);
     if (e == cudaSuccess) {
         const csaw_status st = build_degree_table(g, &sv->degrees);
         if (st != CSAW_OK) { delete sv; return st; }
     }
+    sv->lanes.resize(opts->slots);
+    int prio_lo = 0, prio_hi = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
     for (uint32_t i = 0; e == cudaSuccess && i < opts->slots; ++i) {
-        cudaStream_t st;
-        e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-        if (e == cudaSuccess) sv->streams.push_back(st);
+        e = cudaStreamCreateWithPriority(&sv->lanes[i].lo, cudaStreamNonBlocking, prio_lo);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&sv->lanes[i].hi, cudaStreamNonBlocking, prio_hi);
+        sv->lanes[i].s = sv->lanes[i].lo;
     }
     if (e != cudaSuccess) {
-        for (auto st : sv->streams) cudaStreamDestroy(st);
+        for (auto& L : sv->lanes) {
+            if (L.lo) cudaStreamDestroy(L.lo);
+            if (L.hi) cudaStreamDestroy(L.hi);
+        }
         delete sv;
         return cuda_fail(e, "cudaStreamCreate(server)");
     }
@@ -286,7 +573,13 @@ extern "C" csaw_status csaw_server_destroy(csaw_server* sv)
         free_server_result(kv.second->result);
         delete kv.second;
     }
-    for (auto st : sv->streams) cudaStreamDestroy(st);
+    for (auto& L : sv->lanes) {
+        cudaStreamSynchronize(L.lo);
+        cudaStreamSynchronize(L.hi);
+        cudaStreamDestroy(L.lo);
+        cudaStreamDestroy(L.hi);
+        if (L.pin) cudaFreeHost(L.pin);
+    }
     delete sv;
     return CSAW_OK;
 }
@@ -304,6 +597,8 @@ extern "C" csaw_status csaw_submit(csaw_server* sv, const csaw_request* r, uint6
     csaw_status st = check_bias(sv->g, &r->bias, r->kind == CSAW_REQ_WALK, &kind);
     if (st == CSAW_OK && r->kind == CSAW_REQ_WALK) {
         if (r->n_walkers && !r->starts) st = fail(CSAW_ERR_INVALID, "starts is NULL");
+        else if (r->n_walkers >= 0x7FFFFFFFull) st = fail(CSAW_ERR_INVALID, "too many walkers");
+        else if (r->length == 0xFFFFFFFFu) st = fail(CSAW_ERR_INVALID, "length too large");
         else rq->starts.assign(r->starts, r->starts + r->n_walkers);
         rq->length = r->length;
         for (uint64_t i = 0; st == CSAW_OK && i < r->n_walkers; ++i)
@@ -317,8 +612,15 @@ extern "C" csaw_status csaw_submit(csaw_server* sv, const csaw_request* r, uint6
             rq->fanout.assign(r->fanout, r->fanout + r->depth);
             const uint64_t ns = rq->io.back();
             if (rq->io[0] != 0) st = fail(CSAW_ERR_INVALID, "inst_offsets must start at 0");
-            else if (ns && !r->seeds) st = fail(CSAW_ERR_INVALID, "seeds is NULL");
-            else rq->seeds.assign(r->seeds, r->seeds + ns);
+            for (uint32_t i = 0; st == CSAW_OK && i < rq->n_instances; ++i)
+                if (rq->io[i + 1] < rq->io[i]) st = fail(CSAW_ERR_INVALID, "inst_offsets must be non-decreasing");
+            for (uint32_t l = 0; st == CSAW_OK && l < r->depth; ++l)
+                if (rq->fanout[l] == 0) st = fail(CSAW_ERR_INVALID, "fanout[%u] is 0", l);
+            if (st == CSAW_OK && ns && !r->seeds) st = fail(CSAW_ERR_INVALID, "seeds is NULL");
+            if (st == CSAW_OK && ns >= 0x7FFFFFFFull) st = fail(CSAW_ERR_INVALID, "too many seeds");
+            if (st == CSAW_OK) rq->seeds.assign(r->seeds, r->seeds + ns);
+            for (uint64_t j = 0; st == CSAW_OK && j < ns; ++j)
+                if (rq->seeds[j] >= sv->g->V) st = fail(CSAW_ERR_INVALID, "seed %llu out of range", (unsigned long long)j);
         }
     } else if (st == CSAW_OK) {
         st = fail(CSAW_ERR_INVALID, "unknown request kind %d", r->kind);

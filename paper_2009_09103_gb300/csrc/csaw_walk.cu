@@ -37,6 +37,28 @@ constexpr uint32_t CHUNK_SLOTS = 256;       // chunk prefixes per warp (shared m
 #endif
 constexpr int PASS1_UNROLL = CSAW_WALK_UNROLL;   // rounds of pass 1 in flight
 
+// Which segment walker w is in, and its place there.
+struct WalkerSlot {
+    uint32_t k0, k1, id, L;
+    uint64_t row0;
+};
+
+__device__ __forceinline__ WalkerSlot walker_slot(const WalkSegments& sg, uint64_t w)
+{
+    uint32_t lo = 0, hi = sg.n;   // last r with start[r] <= w
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(sg.start + mid) <= w) lo = mid; else hi = mid;
+    }
+    WalkerSlot ws;
+    ws.id = (uint32_t)(w - __ldg(sg.start + lo));
+    ws.L = __ldg(sg.len + lo);
+    ws.k0 = __ldg(sg.key + 2 * lo);
+    ws.k1 = __ldg(sg.key + 2 * lo + 1);
+    ws.row0 = __ldg(sg.row0 + lo) + (uint64_t)ws.id * ((uint64_t)ws.L + 1);
+    return ws;
+}
+
 struct WalkParams {
     const uint64_t* __restrict__ off;
     const uint32_t* __restrict__ col;
@@ -53,6 +75,7 @@ struct WalkParams {
     uint32_t tele_q32;                    // teleport probability per step, in units of 2^-32
     unsigned long long* next_walker;
     const uint64_t* __restrict__ cdfw;   // cached edge-weight prefix sums (node2vec fast path) or null
+    WalkSegments seg;                     // batched kernels: several requests in one launch
 };
 
 struct PrevCtx {
@@ -702,9 +725,12 @@ constexpr int walk_min_blocks()
 // its start (restart) or to vertex floor(r2 * V / 2^64), r2 the draw of
 // attempt 2 (jump), instead of to a neighbour; a dead end teleports the same
 // way instead of stopping, and node2vec's next step has no previous vertex.
-template <int KIND, bool WIDE, bool TELE>
+// BATCH: walkers of several requests (WalkSegments), each with its own
+// seed, walker index and length; the draws are those of its request alone.
+template <int KIND, bool WIDE, bool TELE, bool BATCH = false>
 __global__ void __launch_bounds__(WALK_THREADS, (walk_min_blocks<KIND, WIDE>())) walk_kernel(WalkParams p)
 {
+    static_assert(!(TELE && BATCH), "teleporting walks are not batched");
     // Per warp: the chunk prefix table, then (node2vec) the N(prev) window.
     // The intersection path's buffers overlay them: a step uses one or the other.
     constexpr uint32_t WARP_WORDS = CHUNK_SLOTS + (KIND == CSAW_BIAS_NODE2VEC ? SEG_SMEM / 2 : 0);
@@ -715,14 +741,25 @@ __global__ void __launch_bounds__(WALK_THREADS, (walk_min_blocks<KIND, WIDE>()))
     uint32_t* s_seg = reinterpret_cast<uint32_t*>(s_chunk + (KIND == CSAW_BIAS_NODE2VEC ? CHUNK_SLOTS : 0));
     uint64_t* s_jw = s_chunk;
     uint32_t* s_jpos = reinterpret_cast<uint32_t*>(s_chunk + JCAP);
-    const uint64_t row_len = (uint64_t)p.L + 1;
-
-    while (true) {
+    for (uint32_t taken = 0;; ++taken) {
+        if constexpr (BATCH) {
+            if (p.seg.warp_budget && taken >= p.seg.warp_budget) break;
+        }
         unsigned long long wk = 0;
         if (lane == 0) wk = atomicAdd(p.next_walker, 1ull);
         wk = __shfl_sync(CSAW_FULL_MASK, wk, 0);
         if (wk >= p.n) break;
-        uint32_t* out = p.path + wk * row_len;
+        uint32_t L = p.L;
+        uint32_t* out;
+        WalkerSlot ws;
+        if constexpr (BATCH) {
+            ws = walker_slot(p.seg, wk);
+            L = ws.L;
+            out = p.path + ws.row0;
+        } else {
+            out = p.path + wk * ((uint64_t)p.L + 1);
+        }
+        const uint64_t row_len = (uint64_t)L + 1;
         uint32_t cur = __ldg(p.starts + wk);
         if (cur >= p.V) {
             for (uint64_t t = lane; t < row_len; t += 32) out[t] = CSAW_NONE;
@@ -733,7 +770,7 @@ __global__ void __launch_bounds__(WALK_THREADS, (walk_min_blocks<KIND, WIDE>()))
         c.pbeg = c.pend = 0;
         uint32_t buf = lane == 0 ? cur : CSAW_NONE;   // entries of the current 32-block
         uint64_t flushed = 0;                         // entries [0, flushed) are in memory
-        for (uint32_t s = 0; s < p.L; ++s) {
+        for (uint32_t s = 0; s < L; ++s) {
             uint32_t nxt = 0;
             bool jump = false;   // warp-uniform: every lane draws the same
             if constexpr (TELE)
@@ -746,7 +783,9 @@ __global__ void __launch_bounds__(WALK_THREADS, (walk_min_blocks<KIND, WIDE>()))
                 row.d = (uint32_t)(row.end - row.beg);
                 row.span = (uint32_t)(row.end - row.abeg);
                 row.lo = (uint32_t)(row.beg - row.abeg);
-                const uint64_t r = philox_draw(p.keys, 0u, cur, s, (uint32_t)wk);
+                uint64_t r;
+                if constexpr (BATCH) r = philox_draw(ws.k0, ws.k1, 0u, cur, s, ws.id);
+                else r = philox_draw(p.keys, 0u, cur, s, (uint32_t)wk);
                 uint32_t idx;
                 if (walk_pick<KIND, WIDE>(p, row, c, r, s_chunk, s_seg, s_jpos, s_jw, lane, &idx)) {
                     nxt = __ldg(p.col + row.beg + idx);
@@ -786,20 +825,27 @@ __global__ void __launch_bounds__(WALK_THREADS, (walk_min_blocks<KIND, WIDE>()))
     }
 }
 
-template <int KIND, bool WIDE, bool TELE>
+template <int KIND, bool WIDE, bool TELE, bool BATCH = false>
 static csaw_status launch_walk_kwt(const WalkParams& p, int sm_count, cudaStream_t s)
 {
     // resident blocks per SM, looked up once (calls may come from several threads)
     static std::atomic<int> cached{0};
     int per_sm = cached.load(std::memory_order_acquire);
     if (per_sm == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel<KIND, WIDE, TELE>,
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel<KIND, WIDE, TELE, BATCH>,
                                                                       WALK_THREADS, 0);
         if (e != cudaSuccess) return cuda_fail(e, "occupancy(walk)");
         if (per_sm < 1) per_sm = 1;
         cached.store(per_sm, std::memory_order_release);
     }
-    walk_kernel<KIND, WIDE, TELE><<<sm_count * per_sm, WALK_THREADS, 0, s>>>(p);
+    uint64_t blocks = (uint64_t)sm_count * per_sm;
+    if (BATCH && p.seg.warp_budget) {
+        // enough warps that each takes at most warp_budget walkers
+        const uint64_t per_block = (uint64_t)WALK_WARPS * p.seg.warp_budget;
+        blocks = (p.n + per_block - 1) / per_block;
+        if (blocks < 1) blocks = 1;
+    }
+    walk_kernel<KIND, WIDE, TELE, BATCH><<<(unsigned)blocks, WALK_THREADS, 0, s>>>(p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "walk_kernel launch");
     return CSAW_OK;
@@ -834,6 +880,27 @@ static csaw_status launch_walk(int kind, uint64_t max_bias, const WalkParams& p,
     }
 }
 
+// launch_walk for a batch of requests (p.seg set, no teleports).
+static csaw_status launch_walk_batch(int kind, uint64_t max_bias, const WalkParams& p, int sm_count,
+                                     cudaStream_t s)
+{
+    const bool wide = max_bias * ROUND >= (1ull << 32);
+    switch (kind) {
+    case CSAW_BIAS_UNIFORM: return launch_walk_kwt<CSAW_BIAS_UNIFORM, false, false, true>(p, sm_count, s);
+    case CSAW_BIAS_EDGE_WEIGHT:
+        return wide ? launch_walk_kwt<CSAW_BIAS_EDGE_WEIGHT, true, false, true>(p, sm_count, s)
+                    : launch_walk_kwt<CSAW_BIAS_EDGE_WEIGHT, false, false, true>(p, sm_count, s);
+    case CSAW_BIAS_NEIGHBOR_DEGREE:
+        return wide ? launch_walk_kwt<CSAW_BIAS_NEIGHBOR_DEGREE, true, false, true>(p, sm_count, s)
+                    : launch_walk_kwt<CSAW_BIAS_NEIGHBOR_DEGREE, false, false, true>(p, sm_count, s);
+    case CSAW_BIAS_NODE2VEC:
+        return wide ? launch_walk_kwt<CSAW_BIAS_NODE2VEC, true, false, true>(p, sm_count, s)
+                    : launch_walk_kwt<CSAW_BIAS_NODE2VEC, false, false, true>(p, sm_count, s);
+    default:
+        return fail(CSAW_ERR_INVALID, "unknown bias kind %d", kind);
+    }
+}
+
 
 // ---------------------------------------------------------------------------
 // Walks over a cached cumulative array (static biases): one thread per
@@ -863,6 +930,7 @@ struct WalkCdfParams {
     uint32_t L;
     uint32_t* __restrict__ path;
     PhiloxKeys keys;
+    WalkSegments seg;                    // batched kernel: several requests in one launch
 };
 
 // Writes the staged entries t in [t0, t_end) of the warp's walkers base ..
@@ -887,7 +955,25 @@ __device__ __forceinline__ void walk_tile_flush(const WalkCdfParams& p, uint32_t
     __syncwarp();
 }
 
-template <bool UNIFORM>
+// The same for a batch, where each walker has its own row start (row0,
+// relative to path) and row length (rl, 0 for lanes without a walker).
+__device__ __forceinline__ void walk_tile_flush_rows(const WalkCdfParams& p, uint32_t (*tile)[WC_TILE + 1],
+                                                     uint64_t row0, uint64_t rl, uint64_t t0, int lane)
+{
+    __syncwarp();
+    const int half = lane >> 4, c = lane & 15;
+    const uint64_t t = t0 + (uint64_t)c;
+#pragma unroll 2
+    for (int i0 = 0; i0 < 32; i0 += 2) {
+        const int i = i0 + half;
+        const uint64_t r0 = __shfl_sync(CSAW_FULL_MASK, row0, i);
+        const uint64_t n = __shfl_sync(CSAW_FULL_MASK, rl, i);
+        if (t < n) p.path[r0 + t] = tile[i][c];
+    }
+    __syncwarp();
+}
+
+template <bool UNIFORM, bool BATCH = false>
 __global__ void __launch_bounds__(WC_THREADS) walk_cached_kernel(WalkCdfParams p)
 {
     __shared__ uint32_t s_tile[WC_WARPS][32][WC_TILE + 1];   // +1: conflict-free column writes
@@ -897,20 +983,35 @@ __global__ void __launch_bounds__(WC_THREADS) walk_cached_kernel(WalkCdfParams p
     const uint64_t n_warps = (uint64_t)gridDim.x * WC_WARPS;
     for (uint64_t base = ((uint64_t)blockIdx.x * WC_WARPS + wid) * 32; base < p.n; base += n_warps * 32) {
         const uint64_t wk = base + (uint64_t)lane;
+        // batch: this lane's request (key, index, length) and row; the warp
+        // runs to the longest length among its lanes
+        WalkerSlot ws{};
+        uint32_t L = p.L;
+        uint64_t rl = 0;
+        if constexpr (BATCH) {
+            if (wk < p.n) {
+                ws = walker_slot(p.seg, wk);
+                rl = (uint64_t)ws.L + 1;
+            }
+            L = __reduce_max_sync(CSAW_FULL_MASK, ws.L);
+        }
         // alive: still walking; cur = CSAW_NONE once stopped (or never started)
         uint32_t cur = wk < p.n ? __ldg(p.starts + wk) : CSAW_NONE;
         if (cur >= p.V) cur = CSAW_NONE;
         bool alive = cur != CSAW_NONE;
         tile[lane][0] = cur;
         uint64_t t0 = 0;                   // path position of tile column 0
-        for (uint32_t s = 0; s < p.L; ++s) {
+        for (uint32_t s = 0; s < L; ++s) {
+            if constexpr (BATCH) alive = alive && s < ws.L;
             if (alive) {
                 const uint64_t beg = __ldg(p.off + cur);
                 const uint64_t end = __ldg(p.off + cur + 1);
                 bool stop = beg == end;
                 uint64_t i = 0;
                 if (!stop) {
-                    const uint64_t r = philox_draw(p.keys, 0u, cur, s, (uint32_t)wk);
+                    uint64_t r;
+                    if constexpr (BATCH) r = philox_draw(ws.k0, ws.k1, 0u, cur, s, ws.id);
+                    else r = philox_draw(p.keys, 0u, cur, s, (uint32_t)wk);
                     if constexpr (UNIFORM) {
                         i = scale_draw(r, end - beg);
                     } else {
@@ -933,13 +1034,44 @@ __global__ void __launch_bounds__(WC_THREADS) walk_cached_kernel(WalkCdfParams p
             }
             const uint64_t t = (uint64_t)s + 1;      // path position of this step's vertex
             tile[lane][t - t0] = cur;
-            if (t - t0 == WC_TILE - 1 || t == p.L) {
-                walk_tile_flush(p, tile, base, row_len, t0, t + 1, lane);
+            if (t - t0 == WC_TILE - 1 || t == L) {
+                if constexpr (BATCH) walk_tile_flush_rows(p, tile, ws.row0, rl, t0, lane);
+                else walk_tile_flush(p, tile, base, row_len, t0, t + 1, lane);
                 t0 = t + 1;
             }
         }
-        if (p.L == 0) walk_tile_flush(p, tile, base, row_len, 0, 1, lane);
+        if (L == 0) {
+            if constexpr (BATCH) walk_tile_flush_rows(p, tile, ws.row0, rl, 0, lane);
+            else walk_tile_flush(p, tile, base, row_len, 0, 1, lane);
+        }
     }
+}
+
+template <bool UNIFORM, bool BATCH>
+static csaw_status launch_walk_cached_k(const WalkCdfParams& p, int sm_count, cudaStream_t s)
+{
+    static std::atomic<int> cached{0};
+    int per_sm = cached.load(std::memory_order_acquire);
+    if (per_sm == 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_cached_kernel<UNIFORM, BATCH>,
+                                                                      WC_THREADS, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "occupancy(walk_cached)");
+        if (per_sm < 1) per_sm = 1;
+        cached.store(per_sm, std::memory_order_release);
+    }
+    uint64_t blocks = (p.n + WC_THREADS - 1) / WC_THREADS;
+    uint64_t cap = (uint64_t)sm_count * per_sm;
+    if (BATCH && p.seg.warp_budget) {
+        // each warp walks at most warp_budget groups of 32 walkers
+        const uint64_t per_block = (uint64_t)WC_THREADS * p.seg.warp_budget;
+        cap = (p.n + per_block - 1) / per_block;
+    }
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    walk_cached_kernel<UNIFORM, BATCH><<<(unsigned)blocks, WC_THREADS, 0, s>>>(p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "walk_cached_kernel launch");
+    return CSAW_OK;
 }
 
 csaw_status launch_walk_cached(const csaw_graph* g, int kind, const uint32_t* starts, uint64_t n,
@@ -949,24 +1081,54 @@ csaw_status launch_walk_cached(const csaw_graph* g, int kind, const uint32_t* st
     p.off = g->off; p.col = g->col; p.cdf = kind == CSAW_BIAS_UNIFORM ? nullptr : g->cdf[kind];
     p.V = g->V; p.starts = starts; p.n = n; p.L = length; p.path = path;
     p.keys = philox_round_keys(rng_seed);
-    static std::atomic<int> cached[2];
-    const int u = kind == CSAW_BIAS_UNIFORM ? 1 : 0;
-    int per_sm = cached[u].load(std::memory_order_acquire);
-    if (per_sm == 0) {
-        cudaError_t e = u ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_cached_kernel<true>, WC_THREADS, 0)
-                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_cached_kernel<false>, WC_THREADS, 0);
-        if (e != cudaSuccess) return cuda_fail(e, "occupancy(walk_cached)");
-        if (per_sm < 1) per_sm = 1;
-        cached[u].store(per_sm, std::memory_order_release);
+    p.seg = WalkSegments{};
+    return kind == CSAW_BIAS_UNIFORM ? launch_walk_cached_k<true, false>(p, g->sm_count, s)
+                                     : launch_walk_cached_k<false, false>(p, g->sm_count, s);
+}
+
+csaw_status walk_batch(const csaw_graph* g, const csaw_bias* bias, const uint32_t* d_starts, uint64_t n,
+                       const WalkSegments& seg, uint32_t max_len, uint32_t* d_path, cudaStream_t s)
+{
+    int kind;
+    CSAW_TRY(check_bias(g, bias, true, &kind));
+    if (n == 0) return CSAW_OK;
+    if (kind != CSAW_BIAS_NODE2VEC && cached_cdf_usable(g, kind)) {
+        WalkCdfParams p;
+        p.off = g->off; p.col = g->col; p.cdf = kind == CSAW_BIAS_UNIFORM ? nullptr : g->cdf[kind];
+        p.V = g->V; p.starts = d_starts; p.n = n; p.L = max_len; p.path = d_path;
+        p.keys = philox_round_keys(0);
+        p.seg = seg;
+        return kind == CSAW_BIAS_UNIFORM ? launch_walk_cached_k<true, true>(p, g->sm_count, s)
+                                         : launch_walk_cached_k<false, true>(p, g->sm_count, s);
     }
-    uint64_t blocks = (n + WC_THREADS - 1) / WC_THREADS;
-    const uint64_t cap = (uint64_t)g->sm_count * per_sm;
-    if (blocks > cap) blocks = cap;
-    if (u) walk_cached_kernel<true><<<(unsigned)blocks, WC_THREADS, 0, s>>>(p);
-    else walk_cached_kernel<false><<<(unsigned)blocks, WC_THREADS, 0, s>>>(p);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "walk_cached_kernel launch");
-    return CSAW_OK;
+    void* counter = nullptr;
+    CSAW_TRY(dalloc(&counter, sizeof(unsigned long long), s));
+    csaw_status st = CSAW_OK;
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) st = cuda_fail(e, "memset counter");
+    if (st == CSAW_OK) {
+        WalkParams p;
+        p.off = g->off; p.col = g->col; p.w = g->w; p.deg = g->deg; p.V = g->V;
+        p.starts = d_starts; p.n = n; p.L = max_len; p.path = d_path;
+        p.keys = philox_round_keys(0);
+        p.m0 = bias->n2v_mult[0]; p.m1 = bias->n2v_mult[1]; p.m2 = bias->n2v_mult[2];
+        p.tele = CSAW_TELEPORT_NONE;
+        p.tele_q32 = 0;
+        p.next_walker = (unsigned long long*)counter;
+        p.cdfw = g->cdf[CSAW_BIAS_EDGE_WEIGHT];
+        p.seg = seg;
+        uint64_t max_bias = 1;
+        if (kind == CSAW_BIAS_EDGE_WEIGHT) max_bias = g->max_weight;
+        else if (kind == CSAW_BIAS_NEIGHBOR_DEGREE) max_bias = g->max_degree;
+        else if (kind == CSAW_BIAS_NODE2VEC) {
+            uint64_t m = 1;
+            for (int i = 0; i < 3; ++i) m = bias->n2v_mult[i] > m ? bias->n2v_mult[i] : m;
+            max_bias = (uint64_t)g->max_weight * m;
+        }
+        st = launch_walk_batch(kind, max_bias, p, g->sm_count, s);
+    }
+    dfree(counter, s);
+    return st;
 }
 
 }  // namespace csaw
@@ -1042,6 +1204,7 @@ extern "C" csaw_status csaw_walk_ex(csaw_graph* g, const uint32_t* starts, uint6
         p.tele_q32 = tele != CSAW_TELEPORT_NONE ? opts->teleport_q32 : 0u;
         p.next_walker = (unsigned long long*)counter;
         p.cdfw = g->cdf[CSAW_BIAS_EDGE_WEIGHT];
+        p.seg = WalkSegments{};
         uint64_t max_bias = 1;
         if (kind == CSAW_BIAS_EDGE_WEIGHT) max_bias = g->max_weight;
         else if (kind == CSAW_BIAS_NEIGHBOR_DEGREE) max_bias = g->max_degree;

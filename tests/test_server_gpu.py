@@ -157,3 +157,79 @@ def test_invalid_requests(env):
         srv.submit_sample(np.array([0], dtype=np.uint32), np.array([0, 1], dtype=np.uint64), [2], "node2vec")
     assert e.value.status == csaw.ERR_INVALID
     srv.close()
+
+
+def test_batches_of_waiting_requests(env):
+    """One slot and a burst of requests: the waiting ones run as batches
+    (one multi-instance launch per kind and bias) and every result equals its
+    request alone and the oracle -- mixed depths, fanouts, instance counts,
+    walk lengths, empty requests and node2vec walks."""
+    csaw, g, G = env
+    rng = np.random.default_rng(5)
+    reqs = []
+    for i in range(30):
+        if i % 3 == 0:
+            n_inst = int(rng.integers(0, 4))
+            ns = int(rng.integers(0, 300))
+            seeds = inputs.uniform_vertices(ns, g.V, 300 + i)
+            cuts = np.sort(rng.integers(0, ns + 1, size=max(n_inst - 1, 0)))
+            io = np.concatenate([[0], cuts, [ns]]).astype(np.uint64) if n_inst else np.array([0], dtype=np.uint64)
+            if n_inst == 0:
+                seeds = seeds[:0]
+            fan = [int(x) for x in rng.choice([1, 5, 25, 300], size=int(rng.integers(1, 4)))]
+            reqs.append(("sample", seeds, io, fan, 40 + i, "edge_weight"))
+        elif i % 3 == 1:
+            nw = int(rng.integers(0, 2000))
+            reqs.append(("walk", inputs.uniform_vertices(nw, g.V, 500 + i), int(rng.integers(0, 50)), 60 + i,
+                         "edge_weight", (1, 1, 1)))
+        else:
+            nw = int(rng.integers(1, 500))
+            reqs.append(("walk", inputs.uniform_vertices(nw, g.V, 700 + i), int(rng.integers(1, 30)), 80 + i,
+                         "node2vec", (1, 2, 4)))
+    srv = csaw.Server(G, budget_bytes=8 << 30, slots=1)
+    tickets = []
+    for r in reqs:
+        if r[0] == "sample":
+            tickets.append(srv.submit_sample(r[1], r[2], r[3], r[5], r[4]))
+        else:
+            tickets.append(srv.submit_walk(r[1], r[2], r[4], r[3], r[5]))
+    served = [srv.poll(t) for t in tickets]
+    srv.close()
+    starts = [s.t_start_ns for s in served]
+    assert len(set(starts)) < len(starts), "no two requests ran in one batch"
+    for r, s in zip(reqs, served):
+        if r[0] == "sample":
+            ref = oracle.sample(g, r[1], r[2], r[3], r[5], r[4])
+            assert np.array_equal(s.sample.edge_offsets, ref["edge_off"])
+            assert np.array_equal(s.sample.src, ref["src"]) and np.array_equal(s.sample.dst, ref["dst"])
+            n_inst = len(r[2]) - 1
+            assert np.array_equal(s.sample.frontier_sizes, ref["fsize"][: len(r[3]) * n_inst])
+        else:
+            assert np.array_equal(s.path, oracle.walk(g, r[1], r[2], r[4], r[3], mult=r[5]))
+
+
+def test_batches_with_cached_arrays(env):
+    """Batched walks and sampling over the cached cumulative array (the
+    thread-per-walker kernel with per-request rows) equal the oracle."""
+    csaw, g, _ = env
+    G = csaw.Graph(g.off, g.col, g.w)
+    G.build_cdf("edge_weight")
+    srv = csaw.Server(G, budget_bytes=8 << 30, slots=1)
+    reqs = []
+    for i in range(12):
+        if i % 2:
+            reqs.append(("walk", inputs.uniform_vertices(37 * i + 1, g.V, 900 + i), 3 * i, 11 + i))
+        else:
+            reqs.append(("sample", inputs.uniform_vertices(20 * i + 1, g.V, 950 + i),
+                         np.array([0, 20 * i + 1], dtype=np.uint64), [10, 3], 13 + i))
+    tickets = [srv.submit_walk(r[1], r[2], "edge_weight", r[3]) if r[0] == "walk"
+               else srv.submit_sample(r[1], r[2], r[3], "edge_weight", r[4]) for r in reqs]
+    served = [srv.poll(t) for t in tickets]
+    srv.close()
+    for r, s in zip(reqs, served):
+        if r[0] == "walk":
+            assert np.array_equal(s.path, oracle.walk(g, r[1], r[2], "edge_weight", r[3]))
+        else:
+            ref = oracle.sample(g, r[1], r[2], r[3], "edge_weight", r[4])
+            assert np.array_equal(s.sample.dst, ref["dst"]) and np.array_equal(s.sample.edge_offsets, ref["edge_off"])
+    G.close()
