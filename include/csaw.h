@@ -143,6 +143,28 @@ csaw_status csaw_graph_build_cdf(csaw_graph* g, int32_t bias_kind, void* stream)
  * first; no call may be running on the graph. */
 csaw_status csaw_graph_drop_cdf(csaw_graph* g, int32_t bias_kind);
 
+/* Device memory through the caller's allocator (e.g. PyTorch's caching
+ * allocator, so that a framework's memory accounting covers this library).
+ * After this call, every device allocation that later calls on g make goes
+ * through alloc: the temporaries of csaw_walk, csaw_walk_ex, csaw_sample,
+ * csaw_sample_ex, csaw_layer_sample, csaw_mdrw and csaw_autotune_select, the
+ * device arrays of their results, the buffers of plans created afterwards,
+ * cached arrays built afterwards and the request buffers of servers on g.
+ *   alloc(bytes, stream, ctx)  returns device memory of at least `bytes`
+ *               bytes on g's device, 256-byte aligned, first used on
+ *               `stream` (a cudaStream_t; NULL = legacy default stream), or
+ *               NULL on failure (the call then returns CSAW_ERR_NOMEM)
+ *   free(ptr, stream, ctx)     releases ptr; work already queued on `stream`
+ *               may still use it (stream-ordered, like cudaFreeAsync)
+ * Memory is always released through the pair that allocated it.  NULL
+ * alloc and free restore the library's own stream-ordered pool.  The pair may
+ * be called from the library's threads (the request server's slots).  The
+ * graph's own CSR arrays are not affected.  Not thread-safe against running
+ * calls on g.  Errors: CSAW_ERR_INVALID (only one of alloc and free given). */
+typedef void* (*csaw_alloc_fn)(uint64_t bytes, void* stream, void* ctx);
+typedef void (*csaw_free_fn)(void* ptr, void* stream, void* ctx);
+csaw_status csaw_graph_set_allocator(csaw_graph* g, csaw_alloc_fn alloc, csaw_free_fn free, void* ctx);
+
 /* ---------------------------------------------------------------- walks */
 
 /* Biased random walks (Sec. II-A; static bias: edge weight or neighbour
@@ -210,7 +232,18 @@ typedef struct {
     uint32_t partitions;     /* vertex ranges the graph was cut into */
     uint64_t loads;          /* partition uploads (scheduling rounds) */
     uint64_t bytes_loaded;   /* host-to-device bytes of those uploads */
+    uint64_t reuses;         /* rounds whose partition was still in a slot (no upload) */
 } csaw_oom_stats;
+
+/* Options of the out-of-memory calls (NULL = defaults). */
+typedef struct {
+    uint32_t slots;          /* device partition slots, each of device_budget_bytes
+                                (0 = the call's default; at most 8) */
+    uint32_t pin_host;       /* 1: page-lock the host columns and weights for the
+                                duration of the call (cudaHostRegister), so that
+                                partition copies run behind the selection; a
+                                refused registration falls back to pageable copies */
+} csaw_oom_opts;
 
 /* The partitions csaw_walk_oom cuts a host CSR into for a device budget
  * (host only; no device work).  Vertex ranges [bounds[q], bounds[q+1]) are
@@ -231,6 +264,50 @@ csaw_status csaw_walk_oom(const uint64_t* row_offsets, const uint32_t* cols, con
                           const uint32_t* starts, uint64_t n_walkers, uint32_t length,
                           const csaw_bias* bias, uint64_t rng_seed, uint32_t* path,
                           csaw_oom_stats* stats, void* stream);
+
+/* csaw_walk_oom with options (NULL: 2 slots, no pinning).  With two or more
+ * slots, each round also loads the partition with the second most active
+ * walkers into another slot, on a stream of its own, while the round runs
+ * (Sec. V-B); a round whose partition is still in a slot loads nothing
+ * (stats->reuses).  Paths are those of csaw_walk_oom and csaw_walk. */
+csaw_status csaw_walk_oom_ex(const uint64_t* row_offsets, const uint32_t* cols, const uint32_t* weights,
+                             uint32_t n_vertices, uint64_t n_edges, uint64_t device_budget_bytes,
+                             const uint32_t* starts, uint64_t n_walkers, uint32_t length,
+                             const csaw_bias* bias, uint64_t rng_seed, uint32_t* path,
+                             csaw_oom_stats* stats, void* stream, const csaw_oom_opts* opts);
+
+/* Layered sampling (as csaw_sample) over a graph kept in host memory
+ * (out-of-memory sampling, Sec. V-A; partition transfers overlapped with
+ * sampling, Sec. V-B).
+ *   row_offsets, cols, weights  a host CSR as for csaw_graph_create (weights
+ *                 NULL = all ones); read, never copied whole
+ *   device_budget_bytes  the device memory of one partition slot: vertex
+ *                 ranges are cut so that a range's columns, weights and the
+ *                 prefix sums of its hub rows fit it (16 bytes per edge; see
+ *                 csaw_oom_plan with weighted = 1)
+ *   seeds, inst_offsets, n_instances, depth, fanout, bias, rng_seed
+ *                 host arrays and arguments as for csaw_sample (bias: uniform,
+ *                 edge weight or neighbour degree)
+ *   opts          slots (default 2) and host pinning; stats as csaw_walk_oom
+ * The row offsets and the degrees stay on the device (16 bytes per vertex
+ * beyond the budget), as do the frontiers and the sampled edges.  Per layer,
+ * the partitions that hold frontier vertices are taken in the order of how
+ * many frontier entries they hold (workload-aware scheduling, Sec. V-A); the
+ * next partition is copied into another slot while the current one is
+ * sampled.  Draws, prefix sums and the result's layout are those of
+ * csaw_sample, so the result is identical to csaw_sample's on the same graph
+ * and arguments.  Every bias must be positive (weights >= 1; for neighbour
+ * degree, no edge into a vertex without neighbours).  Returns when the result
+ * is complete; read it with csaw_sample_get_view / csaw_sample_copy_edges and
+ * release it with csaw_result_free.  Errors: CSAW_ERR_INVALID (bad CSR, bias,
+ * seeds or offsets, a zero bias), CSAW_ERR_NOMEM (a row larger than the
+ * budget, or device allocation), CSAW_ERR_CUDA. */
+csaw_status csaw_sample_oom(const uint64_t* row_offsets, const uint32_t* cols, const uint32_t* weights,
+                            uint32_t n_vertices, uint64_t n_edges, uint64_t device_budget_bytes,
+                            const uint32_t* seeds, const uint64_t* inst_offsets, uint32_t n_instances,
+                            uint32_t depth, const uint32_t* fanout, const csaw_bias* bias,
+                            uint64_t rng_seed, const csaw_oom_opts* opts, csaw_oom_stats* stats,
+                            void* stream, csaw_sample_result** out);
 
 /* Multi-dimensional random walk, or frontier sampling (Sec. II-A), as the
  * API of Sec. III-C expresses it in the case study of Sec. III-D (Figs. 3-4):

@@ -45,7 +45,12 @@ TELEPORT = {None: 0, "restart": 1, "jump": 2}
 
 
 class OomStats(ctypes.Structure):
-    _fields_ = [("partitions", ctypes.c_uint32), ("loads", ctypes.c_uint64), ("bytes_loaded", ctypes.c_uint64)]
+    _fields_ = [("partitions", ctypes.c_uint32), ("loads", ctypes.c_uint64), ("bytes_loaded", ctypes.c_uint64),
+                ("reuses", ctypes.c_uint64)]
+
+
+class OomOpts(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_uint32), ("pin_host", ctypes.c_uint32)]
 
 
 class GraphInfo(ctypes.Structure):
@@ -102,6 +107,12 @@ class SampleView(ctypes.Structure):
                 ("src", ctypes.POINTER(ctypes.c_void_p)), ("dst", ctypes.POINTER(ctypes.c_void_p))]
 
 
+# csaw_graph_set_allocator's callbacks: alloc(bytes, stream, ctx) -> ptr,
+# free(ptr, stream, ctx)
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
 def lib():
     """Load libcsaw.so (raises if it has not been built)."""
     global _lib
@@ -123,7 +134,15 @@ def lib():
         L.csaw_oom_plan.argtypes = [P, u32, i32, u64, P, u32, ctypes.POINTER(u32)]
         L.csaw_walk_oom.argtypes = [P, P, P, u32, u64, u64, P, u64, u32, ctypes.POINTER(Bias), u64, P,
                                     ctypes.POINTER(OomStats), P]
+        L.csaw_walk_oom_ex.argtypes = [P, P, P, u32, u64, u64, P, u64, u32, ctypes.POINTER(Bias), u64, P,
+                                       ctypes.POINTER(OomStats), P, ctypes.POINTER(OomOpts)]
+        L.csaw_walk_oom_ex.restype = ctypes.c_int
+        L.csaw_sample_oom.argtypes = [P, P, P, u32, u64, u64, P, P, u32, u32, P, ctypes.POINTER(Bias), u64,
+                                      ctypes.POINTER(OomOpts), ctypes.POINTER(OomStats), P, ctypes.POINTER(P)]
+        L.csaw_sample_oom.restype = ctypes.c_int
         L.csaw_graph_build_cdf.argtypes = [P, ctypes.c_int32, P]
+        L.csaw_graph_set_allocator.argtypes = [P, ALLOC_FN, FREE_FN, P]
+        L.csaw_graph_set_allocator.restype = ctypes.c_int
         L.csaw_graph_drop_cdf.argtypes = [P, ctypes.c_int32]
         if hasattr(L, "csaw_sample"):
             L.csaw_sample.argtypes = [P, P, P, u32, u32, P, ctypes.POINTER(Bias), u64, i32, P,
@@ -243,6 +262,36 @@ class Graph:
     def drop_cdf(self, bias: str):
         _check(lib().csaw_graph_drop_cdf(self._h, BIAS_KINDS[bias]))
 
+    def use_torch_allocator(self, on_alloc=None):
+        """csaw_graph_set_allocator with PyTorch's caching allocator: the
+        device memory of later calls on this graph is PyTorch's, and counts
+        in torch.cuda.memory_allocated().  on_alloc(ptr, nbytes), if given, is
+        called after each allocation."""
+        import torch
+        dev = torch.cuda.current_device()
+
+        def alloc(nbytes, stream, ctx):
+            try:
+                st = torch.cuda.ExternalStream(stream, device=dev) if stream else None
+                ptr = torch.cuda.caching_allocator_alloc(int(nbytes), device=dev, stream=st)
+                if on_alloc is not None:
+                    on_alloc(ptr, int(nbytes))
+                return ptr
+            except Exception:
+                return None
+
+        def free(ptr, stream, ctx):
+            try:
+                torch.cuda.caching_allocator_delete(ptr)
+            except Exception:
+                pass
+        self._alloc_cbs = (ALLOC_FN(alloc), FREE_FN(free))   # kept alive with the graph
+        _check(lib().csaw_graph_set_allocator(self._h, self._alloc_cbs[0], self._alloc_cbs[1], None))
+
+    def use_own_allocator(self):
+        """Back to the library's stream-ordered pool for later calls."""
+        _check(lib().csaw_graph_set_allocator(self._h, ALLOC_FN(), FREE_FN(), None))
+
     def close(self):
         if self._h:
             lib().csaw_graph_destroy(self._h)
@@ -300,11 +349,16 @@ def oom_plan(off, budget_bytes: int, weighted: bool = True) -> np.ndarray:
     return bounds
 
 
+def _oom_stats(st):
+    return {"partitions": st.partitions, "loads": st.loads, "bytes_loaded": st.bytes_loaded, "reuses": st.reuses}
+
+
 def walk_oom(off, col, w, starts, length: int, bias="edge_weight", seed: int = 0,
-             budget_bytes: int = 1 << 30, stream=None):
-    """csaw_walk_oom: walks over a host CSR (numpy off uint64, col uint32, w
-    uint32 or None) streamed through `budget_bytes` of device memory.
-    Returns (path uint32[n, length+1], stats dict)."""
+             budget_bytes: int = 1 << 30, stream=None, slots=None, pin_host: bool = False):
+    """csaw_walk_oom (slots None) or csaw_walk_oom_ex: walks over a host CSR
+    (numpy off uint64, col uint32, w uint32 or None) streamed through slots
+    of `budget_bytes` of device memory.  Returns (path uint32[n, length+1],
+    stats dict)."""
     L = lib()
     off = np.ascontiguousarray(off, dtype=np.uint64)
     col = np.ascontiguousarray(col, dtype=np.uint32)
@@ -313,10 +367,49 @@ def walk_oom(off, col, w, starts, length: int, bias="edge_weight", seed: int = 0
     b = make_bias(bias) if isinstance(bias, str) else bias
     path = np.empty((len(starts), length + 1), dtype=np.uint32)
     st = OomStats()
-    _check(L.csaw_walk_oom(_ptr(off), _ptr(col), _ptr(w), len(off) - 1, len(col), budget_bytes, _ptr(starts),
-                           len(starts), length, ctypes.byref(b), seed, _ptr(path), ctypes.byref(st),
-                           _stream_handle(stream) if stream is not None else None))
-    return path, {"partitions": st.partitions, "loads": st.loads, "bytes_loaded": st.bytes_loaded}
+    sh = _stream_handle(stream) if stream is not None else None
+    if slots is None and not pin_host:
+        _check(L.csaw_walk_oom(_ptr(off), _ptr(col), _ptr(w), len(off) - 1, len(col), budget_bytes, _ptr(starts),
+                               len(starts), length, ctypes.byref(b), seed, _ptr(path), ctypes.byref(st), sh))
+    else:
+        o = OomOpts(slots or 0, int(pin_host))
+        _check(L.csaw_walk_oom_ex(_ptr(off), _ptr(col), _ptr(w), len(off) - 1, len(col), budget_bytes,
+                                  _ptr(starts), len(starts), length, ctypes.byref(b), seed, _ptr(path),
+                                  ctypes.byref(st), sh, ctypes.byref(o)))
+    return path, _oom_stats(st)
+
+
+def sample_oom(off, col, w, seeds, inst_offsets, fanout, bias="edge_weight", seed: int = 0,
+               budget_bytes: int = 1 << 30, slots: int = 0, pin_host: bool = False, stream=None):
+    """csaw_sample_oom: layered sampling over a host CSR streamed through
+    `slots` partition slots of `budget_bytes` each.  Returns (SampleResult
+    with host edges, stats dict)."""
+    L = lib()
+    off = np.ascontiguousarray(off, dtype=np.uint64)
+    col = np.ascontiguousarray(col, dtype=np.uint32)
+    w = np.ascontiguousarray(w, dtype=np.uint32) if w is not None else None
+    seeds = np.ascontiguousarray(seeds, dtype=np.uint32)
+    io = np.ascontiguousarray(inst_offsets, dtype=np.uint64)
+    fan = np.ascontiguousarray(fanout, dtype=np.uint32)
+    b = make_bias(bias) if isinstance(bias, str) else bias
+    o = OomOpts(slots, int(pin_host))
+    st = OomStats()
+    out = ctypes.c_void_p()
+    _check(L.csaw_sample_oom(_ptr(off), _ptr(col), _ptr(w), len(off) - 1, len(col), budget_bytes, _ptr(seeds),
+                             _ptr(io), len(io) - 1, len(fan), _ptr(fan), ctypes.byref(b), seed, ctypes.byref(o),
+                             ctypes.byref(st), _stream_handle(stream) if stream is not None else None,
+                             ctypes.byref(out)))
+    holder = _SampleHandle(out)
+    v = SampleView()
+    _check(L.csaw_sample_get_view(out, ctypes.byref(v)))
+    ng = v.depth * v.n_instances
+    eo = np.ctypeslib.as_array(v.edge_offsets, shape=(ng + 1,)).copy()
+    fs = np.ctypeslib.as_array(v.frontier_sizes, shape=(ng,)).copy() if ng else np.zeros(0, np.uint64)
+    src = np.empty(v.n_edges, dtype=np.uint32)
+    dst = np.empty(v.n_edges, dtype=np.uint32)
+    _check(L.csaw_sample_copy_edges(out, _ptr(src), _ptr(dst)))
+    del holder
+    return SampleResult(v.depth, v.n_instances, v.n_edges, eo, fs, src, dst), _oom_stats(st)
 
 
 def mdrw(g: Graph, pools, steps: int, seed: int = 0, src=None, dst=None, stream=None):

@@ -36,10 +36,48 @@ csaw_status cuda_fail(cudaError_t err, const char* what)
 
 void clear_error() { g_last_error[0] = '\0'; }
 
+static thread_local const DevAllocator* t_alloc = nullptr;
+
+const DevAllocator* current_allocator() { return t_alloc; }
+
+AllocScope::AllocScope(const csaw_graph* g) : prev(t_alloc)
+{
+    t_alloc = (g && g->allocator.alloc) ? &g->allocator : nullptr;
+}
+
+AllocScope::~AllocScope() { t_alloc = prev; }
+
+csaw_status alloc_with(const DevAllocator* a, void** p, size_t bytes, cudaStream_t s)
+{
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (a && a->alloc) {
+        *p = a->alloc((uint64_t)bytes, (void*)s, a->ctx);
+        if (!*p) return fail(CSAW_ERR_NOMEM, "the caller's allocator returned no memory for %zu bytes", bytes);
+        return CSAW_OK;
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(e == cudaErrorMemoryAllocation ? CSAW_ERR_NOMEM : CSAW_ERR_CUDA,
+                    "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    }
+    return CSAW_OK;
+}
+
+void free_with(const DevAllocator& a, void* p, cudaStream_t s)
+{
+    if (!p) return;
+    if (a.free) a.free(p, (void*)s, a.ctx);
+    else cudaFree(p);
+}
+
 csaw_status dalloc(void** p, size_t bytes, cudaStream_t s)
 {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
+    if (t_alloc) return alloc_with(t_alloc, p, bytes, s);
     cudaError_t e = cudaMallocAsync(p, bytes, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -52,7 +90,9 @@ csaw_status dalloc(void** p, size_t bytes, cudaStream_t s)
 
 void dfree(void* p, cudaStream_t s)
 {
-    if (p) cudaFreeAsync(p, s);
+    if (!p) return;
+    if (t_alloc) t_alloc->free(p, (void*)s, t_alloc->ctx);
+    else cudaFreeAsync(p, s);
 }
 
 csaw_status check_bias(const csaw_graph* g, const csaw_bias* bias, bool allow_node2vec, int* kind_out)
@@ -165,7 +205,7 @@ extern "C" csaw_status csaw_graph_destroy(csaw_graph* g)
 {
     clear_error();
     if (!g) return CSAW_OK;
-    for (int k = 0; k < 4; ++k) cudaFree(g->cdf[k]);
+    for (int k = 0; k < 4; ++k) free_with(g->cdf_alloc[k], g->cdf[k], nullptr);
     cudaFree(g->off);
     cudaFree(g->col);
     cudaFree(g->w);
@@ -383,7 +423,7 @@ extern "C" csaw_status csaw_graph_build_cdf(csaw_graph* g, int32_t bias_kind, vo
     cudaStream_t s = (cudaStream_t)stream;
     uint64_t* cdf = nullptr;
     // padded like col/w so that 16-byte stores of a row's last group stay inside
-    CSAW_CUDA(cudaMalloc(&cdf, sizeof(uint64_t) * (g->E + CSAW_EDGE_PAD)));
+    CSAW_TRY(alloc_with(&g->allocator, (void**)&cdf, sizeof(uint64_t) * (g->E + CSAW_EDGE_PAD), s));
     unsigned long long* ctr = nullptr;
     cudaError_t e = cudaMalloc(&ctr, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), s);
@@ -398,11 +438,25 @@ extern "C" csaw_status csaw_graph_build_cdf(csaw_graph* g, int32_t bias_kind, vo
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(ctr);
     if (e != cudaSuccess) {
-        cudaFree(cdf);
+        free_with(g->allocator, cdf, s);
         return cuda_fail(e, "build cumulative array");
     }
     g->cdf[bias_kind] = cdf;
+    g->cdf_alloc[bias_kind] = g->allocator;
     g->device_bytes += sizeof(uint64_t) * (g->E + CSAW_EDGE_PAD);
+    return CSAW_OK;
+}
+
+extern "C" csaw_status csaw_graph_set_allocator(csaw_graph* g, csaw_alloc_fn alloc, csaw_free_fn free,
+                                                void* ctx)
+{
+    clear_error();
+    if (!g) return fail(CSAW_ERR_INVALID, "graph is NULL");
+    if ((alloc == nullptr) != (free == nullptr))
+        return fail(CSAW_ERR_INVALID, "give both alloc and free, or neither");
+    g->allocator.alloc = alloc;
+    g->allocator.free = free;
+    g->allocator.ctx = alloc ? ctx : nullptr;
     return CSAW_OK;
 }
 
@@ -412,7 +466,8 @@ extern "C" csaw_status csaw_graph_drop_cdf(csaw_graph* g, int32_t bias_kind)
     if (!g) return fail(CSAW_ERR_INVALID, "graph is NULL");
     if (bias_kind < 0 || bias_kind > 3) return fail(CSAW_ERR_INVALID, "bad bias kind");
     if (g->cdf[bias_kind]) {
-        cudaFree(g->cdf[bias_kind]);
+        cudaDeviceSynchronize();   // no call may be running on the graph; its frees may still be queued
+        free_with(g->cdf_alloc[bias_kind], g->cdf[bias_kind], nullptr);
         g->cdf[bias_kind] = nullptr;
         g->device_bytes -= sizeof(uint64_t) * (g->E + CSAW_EDGE_PAD);
     }

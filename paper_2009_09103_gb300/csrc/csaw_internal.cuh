@@ -13,6 +13,13 @@
 #define CSAW_FULL_MASK 0xFFFFFFFFu
 #define CSAW_EDGE_PAD 16   // zeroed uint32 entries after col[] and w[]
 
+// The caller's device allocator (csaw_graph_set_allocator), or none.
+struct DevAllocator {
+    csaw_alloc_fn alloc = nullptr;
+    csaw_free_fn free = nullptr;
+    void* ctx = nullptr;
+};
+
 // ---------------------------------------------------------------------------
 // Graph: CSR resident in HBM (uint64 offsets, uint32 columns and weights) and
 // the derived uint32 degree array used by the neighbour-degree bias.
@@ -37,6 +44,8 @@ struct csaw_graph {
     // threshold and resident blocks per SM
     uint32_t tune_theta_w[4] = {0, 0, 0, 0};
     uint32_t tune_blocks_per_sm[4] = {0, 0, 0, 0};
+    DevAllocator allocator;             // device memory of calls on this graph
+    DevAllocator cdf_alloc[4];          // the allocator each cached array came from
 };
 
 // ---------------------------------------------------------------------------
@@ -60,9 +69,24 @@ void clear_error();
         if (_s != CSAW_OK) return _s;                                     \
     } while (0)
 
-// Stream-ordered device allocation (CUDA's pool allocator).
+// Stream-ordered device allocation: the caller's allocator of the graph
+// whose call is running on this thread (AllocScope), else CUDA's pool.
 csaw_status dalloc(void** p, size_t bytes, cudaStream_t s);
 void dfree(void* p, cudaStream_t s);
+
+// The allocator dalloc/dfree use on this thread while an entry point on a
+// graph runs; nested scopes restore the outer one.
+const DevAllocator* current_allocator();
+struct AllocScope {
+    const DevAllocator* prev;
+    explicit AllocScope(const csaw_graph* g);
+    ~AllocScope();
+};
+
+// Allocation and release through an explicit allocator (null or empty:
+// cudaMalloc / cudaFree), for memory that outlives the call that made it.
+csaw_status alloc_with(const DevAllocator* a, void** p, size_t bytes, cudaStream_t s);
+void free_with(const DevAllocator& a, void* p, cudaStream_t s);
 
 // Device-wide exclusive scan of n uint32 (n read from *n_dev, n <= n_max):
 // out[i] = in[0] + ... + in[i-1] for i <= n; *total_out (device, optional)

@@ -200,6 +200,7 @@ extern "C" csaw_status csaw_mdrw(csaw_graph* g, const uint32_t* pools, uint64_t 
 {
     clear_error();
     if (!g) return fail(CSAW_ERR_INVALID, "graph is NULL");
+    AllocScope alloc_scope(g);
     if (mem_kind != CSAW_MEM_HOST && mem_kind != CSAW_MEM_DEVICE)
         return fail(CSAW_ERR_INVALID, "bad mem_kind %d", mem_kind);
     if (pool_size == 0 || pool_size > CSAW_MDRW_MAX_POOL)

@@ -167,11 +167,11 @@ extern "C" csaw_status csaw_oom_plan(const uint64_t* row_offsets, uint32_t n_ver
     return CSAW_OK;
 }
 
-extern "C" csaw_status csaw_walk_oom(const uint64_t* row_offsets, const uint32_t* cols, const uint32_t* weights,
-                                     uint32_t n_vertices, uint64_t n_edges, uint64_t device_budget_bytes,
-                                     const uint32_t* starts, uint64_t n_walkers, uint32_t length,
-                                     const csaw_bias* bias, uint64_t rng_seed, uint32_t* path,
-                                     csaw_oom_stats* stats, void* stream)
+extern "C" csaw_status csaw_walk_oom_ex(const uint64_t* row_offsets, const uint32_t* cols, const uint32_t* weights,
+                                        uint32_t n_vertices, uint64_t n_edges, uint64_t device_budget_bytes,
+                                        const uint32_t* starts, uint64_t n_walkers, uint32_t length,
+                                        const csaw_bias* bias, uint64_t rng_seed, uint32_t* path,
+                                        csaw_oom_stats* stats, void* stream, const csaw_oom_opts* opts)
 {
     clear_error();
     if (stats) *stats = csaw_oom_stats{};
@@ -181,6 +181,8 @@ extern "C" csaw_status csaw_walk_oom(const uint64_t* row_offsets, const uint32_t
     if (kind != CSAW_BIAS_UNIFORM && kind != CSAW_BIAS_EDGE_WEIGHT)
         return fail(CSAW_ERR_INVALID, "out-of-memory walks take uniform or edge-weight bias");
     const bool weighted = kind == CSAW_BIAS_EDGE_WEIGHT && weights != nullptr;
+    const uint32_t n_slots = opts && opts->slots ? opts->slots : 2;
+    if (n_slots > 8) return fail(CSAW_ERR_INVALID, "at most 8 slots");
     if (n_walkers == 0) return CSAW_OK;
     if (!starts || !path) return fail(CSAW_ERR_INVALID, "starts/path is NULL");
     if (n_walkers > 0xFFFFFFFFull) return fail(CSAW_ERR_INVALID, "at most 2^32-1 walkers per call");
@@ -197,8 +199,7 @@ extern "C" csaw_status csaw_walk_oom(const uint64_t* row_offsets, const uint32_t
         if (cols[i] >= n_vertices) return fail(CSAW_ERR_INVALID, "column %llu out of range", (unsigned long long)i);
     cudaStream_t s = (cudaStream_t)stream;
 
-    // Partitions: vertex ranges whose slot fits the budget; one slot is
-    // reused for every partition.
+    // Partitions: vertex ranges whose slot fits the budget.
     uint32_t np = 0;
     CSAW_TRY(csaw_oom_plan(row_offsets, n_vertices, weighted ? 1 : 0, device_budget_bytes, nullptr, 0, &np));
     std::vector<uint32_t> vb((size_t)np + 1);
@@ -209,22 +210,65 @@ extern "C" csaw_status csaw_walk_oom(const uint64_t* row_offsets, const uint32_t
         max_rows = std::max<uint64_t>(max_rows, vb[q + 1] - vb[q]);
     }
 
+    // One slot per partition held on the device; the copies of a partition
+    // (and its prefix sums) run on their own stream, so the load of the
+    // second-busiest partition overlaps the current round.
+    struct Slot {
+        void *off = nullptr, *col = nullptr, *w = nullptr, *cdf = nullptr;
+        std::vector<uint64_t> rebased;   // host staging of its rebased offsets
+        int64_t part = -1;
+        uint64_t stamp = 0;              // last round that loaded or used it
+        cudaEvent_t loaded = nullptr, freed = nullptr;
+    };
+    std::vector<Slot> slot(n_slots);
     const uint64_t row_len = (uint64_t)length + 1;
     void *d_starts = nullptr, *d_path = nullptr, *d_cur = nullptr, *d_step = nullptr, *d_vb = nullptr;
-    void *d_cnt = nullptr, *s_off = nullptr, *s_col = nullptr, *s_w = nullptr, *s_cdf = nullptr;
+    void* d_cnt = nullptr;
+    cudaStream_t cs = nullptr;
+    bool registered_col = false, registered_w = false;
     auto cleanup = [&]() {
-        for (void* p : {d_starts, d_path, d_cur, d_step, d_vb, d_cnt, s_off, s_col, s_w, s_cdf}) dfree(p, s);
+        cudaStreamSynchronize(s);
+        if (cs) {
+            cudaStreamSynchronize(cs);
+            cudaStreamDestroy(cs);
+        }
+        for (void* p : {d_starts, d_path, d_cur, d_step, d_vb, d_cnt}) dfree(p, s);
+        for (auto& sl : slot) {
+            for (void* p : {sl.off, sl.col, sl.w, sl.cdf}) dfree(p, s);
+            if (sl.loaded) cudaEventDestroy(sl.loaded);
+            if (sl.freed) cudaEventDestroy(sl.freed);
+        }
+        if (registered_col) cudaHostUnregister((void*)cols);
+        if (registered_w) cudaHostUnregister((void*)weights);
     };
+    if (opts && opts->pin_host && n_edges) {
+        registered_col = cudaHostRegister((void*)cols, sizeof(uint32_t) * n_edges, cudaHostRegisterReadOnly) == cudaSuccess;
+        if (weighted)
+            registered_w = cudaHostRegister((void*)weights, sizeof(uint32_t) * n_edges, cudaHostRegisterReadOnly) == cudaSuccess;
+        cudaGetLastError();   // a refused registration leaves ordinary (pageable) copies
+    }
     csaw_status st = dalloc(&d_starts, sizeof(uint32_t) * n_walkers, s);
     if (st == CSAW_OK) st = dalloc(&d_path, sizeof(uint32_t) * n_walkers * row_len, s);
     if (st == CSAW_OK) st = dalloc(&d_cur, sizeof(uint32_t) * n_walkers, s);
     if (st == CSAW_OK) st = dalloc(&d_step, sizeof(uint32_t) * n_walkers, s);
     if (st == CSAW_OK) st = dalloc(&d_vb, sizeof(uint32_t) * (np + 1), s);
     if (st == CSAW_OK) st = dalloc(&d_cnt, sizeof(unsigned long long) * np, s);
-    if (st == CSAW_OK) st = dalloc(&s_off, sizeof(uint64_t) * (max_rows + 1), s);
-    if (st == CSAW_OK) st = dalloc(&s_col, sizeof(uint32_t) * (max_edges ? max_edges : 1), s);
-    if (st == CSAW_OK && weighted) st = dalloc(&s_w, sizeof(uint32_t) * (max_edges ? max_edges : 1), s);
-    if (st == CSAW_OK && weighted) st = dalloc(&s_cdf, sizeof(uint64_t) * (max_edges ? max_edges : 1), s);
+    for (auto& sl : slot) {
+        if (st == CSAW_OK) st = dalloc(&sl.off, sizeof(uint64_t) * (max_rows + 1), s);
+        if (st == CSAW_OK) st = dalloc(&sl.col, sizeof(uint32_t) * (max_edges ? max_edges : 1), s);
+        if (st == CSAW_OK && weighted) st = dalloc(&sl.w, sizeof(uint32_t) * (max_edges ? max_edges : 1), s);
+        if (st == CSAW_OK && weighted) st = dalloc(&sl.cdf, sizeof(uint64_t) * (max_edges ? max_edges : 1), s);
+        if (st == CSAW_OK) {
+            cudaError_t e = cudaEventCreateWithFlags(&sl.loaded, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.freed, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventRecord(sl.freed, s);
+            if (e != cudaSuccess) st = cuda_fail(e, "cudaEvent");
+        }
+    }
+    if (st == CSAW_OK) {
+        cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamCreate");
+    }
     if (st != CSAW_OK) { cleanup(); return st; }
     cudaError_t e = cudaMemcpyAsync(d_starts, starts, sizeof(uint32_t) * n_walkers, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
@@ -241,9 +285,56 @@ extern "C" csaw_status csaw_walk_oom(const uint64_t* row_offsets, const uint32_t
     p.step = (uint32_t*)d_step;
     p.path = (uint32_t*)d_path;
     std::vector<unsigned long long> counts(np);
-    std::vector<uint64_t> rebased;
     csaw_oom_stats acc{};
     acc.partitions = np;
+    uint64_t round = 0;
+    // Loads partition q into a slot other than `avoid` (unless it is resident
+    // already): an empty slot, else the least recently used one.
+    auto load = [&](uint32_t q, int avoid, int* out_slot) -> cudaError_t {
+        ++round;
+        for (uint32_t k = 0; k < n_slots; ++k)
+            if (slot[k].part == (int64_t)q) {
+                slot[k].stamp = round;
+                *out_slot = (int)k;
+                return cudaSuccess;
+            }
+        int k = -1;
+        for (uint32_t j = 0; j < n_slots; ++j) {
+            if ((int)j == avoid && n_slots > 1) continue;
+            if (k < 0 || slot[j].part < 0 || (slot[k].part >= 0 && slot[j].stamp < slot[k].stamp)) k = (int)j;
+            if (slot[j].part < 0) break;
+        }
+        Slot& sl = slot[k];
+        sl.stamp = round;
+        const uint32_t v0 = vb[q], v1 = vb[q + 1];
+        const uint64_t e0 = row_offsets[v0], ne = row_offsets[v1] - e0;
+        cudaError_t ce = cudaStreamWaitEvent(cs, sl.freed, 0);
+        if (ce != cudaSuccess) return ce;
+        ce = cudaStreamSynchronize(cs);   // the slot's host staging may be rewritten
+        if (ce != cudaSuccess) return ce;
+        sl.rebased.resize((size_t)(v1 - v0) + 1);
+        for (uint32_t v = v0; v <= v1; ++v) sl.rebased[v - v0] = row_offsets[v] - e0;
+        ce = cudaMemcpyAsync(sl.off, sl.rebased.data(), sizeof(uint64_t) * sl.rebased.size(),
+                             cudaMemcpyHostToDevice, cs);
+        if (ce == cudaSuccess && ne)
+            ce = cudaMemcpyAsync(sl.col, cols + e0, sizeof(uint32_t) * ne, cudaMemcpyHostToDevice, cs);
+        if (ce == cudaSuccess && weighted && ne)
+            ce = cudaMemcpyAsync(sl.w, weights + e0, sizeof(uint32_t) * ne, cudaMemcpyHostToDevice, cs);
+        if (ce == cudaSuccess && weighted) {
+            const uint64_t blocks = std::min<uint64_t>(((uint64_t)(v1 - v0) + 7) / 8, 4096);
+            oom_cdf_kernel<<<(unsigned)(blocks ? blocks : 1), 256, 0, cs>>>((const uint64_t*)sl.off,
+                                                                         (const uint32_t*)sl.w, v1 - v0,
+                                                                         (uint64_t*)sl.cdf);
+            ce = cudaGetLastError();
+        }
+        if (ce == cudaSuccess) ce = cudaEventRecord(sl.loaded, cs);
+        if (ce != cudaSuccess) return ce;
+        sl.part = q;
+        acc.loads += 1;
+        acc.bytes_loaded += sizeof(uint64_t) * sl.rebased.size() + ne * (weighted ? 8 : 4);
+        *out_slot = k;
+        return cudaSuccess;
+    };
     const unsigned walk_blocks = (unsigned)((n_walkers + 255) / 256);
     while (true) {
         e = cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * np, s);
@@ -253,37 +344,40 @@ extern "C" csaw_status csaw_walk_oom(const uint64_t* row_offsets, const uint32_t
         e = cudaMemcpyAsync(counts.data(), d_cnt, sizeof(unsigned long long) * np, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) break;
-        // workload-aware schedule: the partition with the most active walkers
+        // workload-aware schedule: the partition with the most active walkers,
+        // and the next busiest to load while this round runs
         uint32_t q = 0;
         for (uint32_t k = 1; k < np; ++k)
             if (counts[k] > counts[q]) q = k;
         if (counts[q] == 0) break;   // every walker finished
-        const uint32_t v0 = vb[q], v1 = vb[q + 1];
-        const uint64_t e0 = row_offsets[v0], ne = row_offsets[v1] - e0;
-        rebased.resize((size_t)(v1 - v0) + 1);
-        for (uint32_t v = v0; v <= v1; ++v) rebased[v - v0] = row_offsets[v] - e0;
-        e = cudaMemcpyAsync(s_off, rebased.data(), sizeof(uint64_t) * rebased.size(), cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess && ne)
-            e = cudaMemcpyAsync(s_col, cols + e0, sizeof(uint32_t) * ne, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess && weighted && ne)
-            e = cudaMemcpyAsync(s_w, weights + e0, sizeof(uint32_t) * ne, cudaMemcpyHostToDevice, s);
+        int q2 = -1;
+        for (uint32_t k = 0; k < np; ++k)
+            if (k != q && counts[k] && (q2 < 0 || counts[k] > counts[q2])) q2 = (int)k;
+        const bool resident = [&] {
+            for (auto& sl : slot) if (sl.part == (int64_t)q) return true;
+            return false;
+        }();
+        if (resident) ++acc.reuses;
+        int k = -1;
+        e = load(q, -1, &k);
         if (e != cudaSuccess) break;
-        acc.loads += 1;
-        acc.bytes_loaded += sizeof(uint64_t) * rebased.size() + ne * (weighted ? 8 : 4);
-        if (weighted) {
-            const uint64_t blocks = std::min<uint64_t>(((uint64_t)(v1 - v0) + 7) / 8, 4096);
-            oom_cdf_kernel<<<(unsigned)(blocks ? blocks : 1), 256, 0, s>>>((const uint64_t*)s_off,
-                                                                        (const uint32_t*)s_w, v1 - v0,
-                                                                        (uint64_t*)s_cdf);
-        }
-        p.off = (const uint64_t*)s_off;
-        p.col = (const uint32_t*)s_col;
-        p.cdf = weighted ? (const uint64_t*)s_cdf : nullptr;
-        p.v0 = v0;
-        p.v1 = v1;
+        Slot& sl = slot[k];
+        e = cudaStreamWaitEvent(s, sl.loaded, 0);
+        if (e != cudaSuccess) break;
+        p.off = (const uint64_t*)sl.off;
+        p.col = (const uint32_t*)sl.col;
+        p.cdf = weighted ? (const uint64_t*)sl.cdf : nullptr;
+        p.v0 = vb[q];
+        p.v1 = vb[q + 1];
         oom_walk_kernel<<<walk_blocks, 256, 0, s>>>(p);
         e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(sl.freed, s);
         if (e != cudaSuccess) break;
+        if (q2 >= 0 && n_slots > 1) {
+            int k2 = -1;
+            e = load((uint32_t)q2, k, &k2);
+            if (e != cudaSuccess) break;
+        }
     }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(path, d_path, sizeof(uint32_t) * n_walkers * row_len, cudaMemcpyDeviceToHost, s);
@@ -292,4 +386,15 @@ extern "C" csaw_status csaw_walk_oom(const uint64_t* row_offsets, const uint32_t
     if (e != cudaSuccess) return cuda_fail(e, "out-of-memory walk");
     if (stats) *stats = acc;
     return CSAW_OK;
+}
+
+extern "C" csaw_status csaw_walk_oom(const uint64_t* row_offsets, const uint32_t* cols, const uint32_t* weights,
+                                     uint32_t n_vertices, uint64_t n_edges, uint64_t device_budget_bytes,
+                                     const uint32_t* starts, uint64_t n_walkers, uint32_t length,
+                                     const csaw_bias* bias, uint64_t rng_seed, uint32_t* path,
+                                     csaw_oom_stats* stats, void* stream)
+{
+    const csaw_oom_opts one = {1, 0};
+    return csaw_walk_oom_ex(row_offsets, cols, weights, n_vertices, n_edges, device_budget_bytes, starts, n_walkers,
+                            length, bias, rng_seed, path, stats, stream, &one);
 }

@@ -28,6 +28,7 @@
 // remaining picks use updated sampling (Sec. IV-B, Fig. 5(b)): the draw is
 // scaled to the unpicked total and mapped past the picked intervals, which is
 // the same choice as searching a recomputed prefix sum.
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
 #include <cstring>
@@ -523,6 +524,10 @@ struct CountParams {
     // picks per vertex of each instance at this layer (null: k for all)
     const uint32_t* __restrict__ inst_k = nullptr;
     uint32_t vbits = 0;
+    // only entries whose vertex is in [v_lo, v_hi) go to the lists (a graph
+    // partition that is loaded); write_cnt: store every entry's count
+    uint32_t v_lo = 0, v_hi = 0xFFFFFFFFu;
+    bool write_cnt = true;
 };
 
 // Number of positive biases of v's neighbours (only when zeros are possible).
@@ -570,10 +575,11 @@ __global__ void count_kernel(CountParams p)
         const uint32_t k = (p.inst_k && e < n) ? __ldg(p.inst_k + (uint32_t)(p.fkeys[e] >> p.vbits)) : p.k;
         const uint32_t c = min(k, npos);
         const bool take_all = npos <= k;
-        const bool to_warp = e < n && c > 0 && (take_all || (p.cached ? c <= PICK_MAX : d <= p.theta_w));
-        const bool to_hub = e < n && c > 0 && !to_warp && p.hub_list != nullptr && c <= PICK_MAX;
-        const bool to_cta = e < n && c > 0 && !to_warp && !to_hub;
-        if (e < n) p.cnt[e] = c;
+        const bool listed = e < n && c > 0 && v >= p.v_lo && v < p.v_hi;
+        const bool to_warp = listed && (take_all || (p.cached ? c <= PICK_MAX : d <= p.theta_w));
+        const bool to_hub = listed && !to_warp && p.hub_list != nullptr && c <= PICK_MAX;
+        const bool to_cta = listed && !to_warp && !to_hub;
+        if (e < n && p.write_cnt) p.cnt[e] = c;
         // warp-aggregated appends
         const uint32_t bw = __ballot_sync(CSAW_FULL_MASK, to_warp);
         const uint32_t bc = __ballot_sync(CSAW_FULL_MASK, to_cta);
@@ -954,10 +960,18 @@ struct csaw_sample_result {
     std::vector<uint32_t*> src, dst;        // device, per layer (owned)
     std::vector<const uint32_t*> src_c, dst_c;
     std::vector<uint64_t> layer_edges;
+    DevAllocator alloc;               // the caller's allocator of src/dst, if any
+    cudaStream_t stream = nullptr;          // the stream they were allocated on
     ~csaw_sample_result()
     {
-        for (auto p : src) cudaFree(p);
-        for (auto p : dst) cudaFree(p);
+        for (auto p : src) release(p);
+        for (auto p : dst) release(p);
+    }
+    void release(void* p)
+    {
+        if (!p) return;
+        if (alloc.free) alloc.free(p, (void*)stream, alloc.ctx);
+        else cudaFree(p);
     }
 };
 
@@ -1472,8 +1486,10 @@ static csaw_status enqueue_hub_groups(Pipeline& P, uint32_t l, cudaStream_t s)
     return CSAW_OK;
 }
 
-// Count/classify and the edge-position scan of layer l.
-static csaw_status enqueue_count(Pipeline& P, uint32_t l, cudaStream_t s)
+// Count/classify of layer l's entries (vertices in [v_lo, v_hi) listed;
+// write_cnt: store the counts).
+static csaw_status enqueue_classify(Pipeline& P, uint32_t l, uint32_t v_lo, uint32_t v_hi, bool write_cnt,
+                                   cudaStream_t s)
 {
     csaw_graph* g = P.g;
     LayerBufs& B = P.L[l];
@@ -1486,6 +1502,7 @@ static csaw_status enqueue_count(Pipeline& P, uint32_t l, cudaStream_t s)
     cp.hub_list = P.hub_path ? P.hlist : nullptr;
     cp.inst_k = P.inst_fan ? P.inst_fan + (uint64_t)l * P.n_inst : nullptr;
     cp.vbits = (uint32_t)P.vbits;
+    cp.v_lo = v_lo; cp.v_hi = v_hi; cp.write_cnt = write_cnt;
     if (B.f_cap) {
         switch (P.kind) {
         case CSAW_BIAS_UNIFORM: CSAW_TRY(launch_count<CSAW_BIAS_UNIFORM>(cp, B.f_cap, g->sm_count, s)); break;
@@ -1493,13 +1510,21 @@ static csaw_status enqueue_count(Pipeline& P, uint32_t l, cudaStream_t s)
         default: CSAW_TRY(launch_count<CSAW_BIAS_NEIGHBOR_DEGREE>(cp, B.f_cap, g->sm_count, s)); break;
         }
     }
+    return CSAW_OK;
+}
+
+// Count/classify and the edge-position scan of layer l.
+static csaw_status enqueue_count(Pipeline& P, uint32_t l, cudaStream_t s)
+{
+    LayerBufs& B = P.L[l];
+    CSAW_TRY(enqueue_classify(P, l, 0, 0xFFFFFFFFu, true, s));
     CSAW_TRY(scan_u32(B.cnt, B.pos, P.lc(l, L_N), B.f_cap, P.scan_scr, P.lc(l, L_TOTAL), s));
     if (P.hub_path && B.f_cap) CSAW_TRY(enqueue_hub_groups(P, l, s));
     return CSAW_OK;
 }
 
-// Selection of layer l into its edge buffers, then its offsets.
-static csaw_status enqueue_select(Pipeline& P, uint32_t l, cudaStream_t s)
+// The selection kernels of layer l (its listed items) into its edge buffers.
+static csaw_status enqueue_select_items(Pipeline& P, uint32_t l, cudaStream_t s)
 {
     csaw_graph* g = P.g;
     LayerBufs& B = P.L[l];
@@ -1552,10 +1577,26 @@ static csaw_status enqueue_select(Pipeline& P, uint32_t l, cudaStream_t s)
             CSAW_CUDA(cudaGetLastError());
         }
     }
+    return CSAW_OK;
+}
+
+// Edge offsets and frontier sizes of layer l.
+static csaw_status enqueue_layer_offsets(Pipeline& P, uint32_t l, cudaStream_t s)
+{
+    csaw_graph* g = P.g;
+    LayerBufs& B = P.L[l];
     layer_offsets_kernel<<<grid_for((uint64_t)P.n_inst + 1, 256, g->sm_count), 256, 0, s>>>(
         B.FO, B.pos, P.n_inst, P.ctr + CT_BASE + l, P.eoff + (uint64_t)l * P.n_inst,
         P.fsize + (uint64_t)l * P.n_inst, P.ctr + CT_BASE + l + 1);
     CSAW_CUDA(cudaGetLastError());
+    return CSAW_OK;
+}
+
+// Selection of layer l into its edge buffers, then its offsets.
+static csaw_status enqueue_select(Pipeline& P, uint32_t l, cudaStream_t s)
+{
+    CSAW_TRY(enqueue_select_items(P, l, s));
+    return enqueue_layer_offsets(P, l, s);
     return CSAW_OK;
 }
 
@@ -1748,6 +1789,8 @@ static csaw_status run_sample(csaw_graph* g, const uint32_t* seeds, const uint64
         return CSAW_OK;
     };
     auto get_out = [&](void** p, size_t bytes) -> csaw_status { return dalloc(p, bytes, s); };
+    if (const DevAllocator* a = current_allocator()) R->alloc = *a;
+    R->stream = s;
     Pipeline P;
     P.init(g, kind, n_inst, depth, fanout, rng_seed);
     P.attempt_cap = attempt_cap;
@@ -1861,6 +1904,7 @@ static csaw_status sample_entry(csaw_graph* g, const uint32_t* seeds, const uint
                                 const csaw_sample_opts* opts, bool layer_mode, csaw_sample_result** out)
 {
     clear_error();
+    AllocScope alloc_scope(g);
     const uint32_t attempt_cap = opts ? opts->attempt_cap : CSAW_ATTEMPT_CAP;
     if (!out) return fail(CSAW_ERR_INVALID, "out is NULL");
     *out = nullptr;
@@ -1997,6 +2041,7 @@ struct csaw_sample_plan {
     uint32_t magic = 0x43504c4eu;   // "CPLN"
     csaw::Pipeline P;
     std::vector<void*> allocs;
+    DevAllocator alloc;       // the allocator of the buffers (the graph's at creation)
     uint32_t* in_seeds = nullptr;
     uint64_t* in_io = nullptr;
     uint32_t* in_key = nullptr;
@@ -2011,7 +2056,7 @@ struct csaw_sample_plan {
     {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
-        for (void* p : allocs) cudaFree(p);
+        for (void* p : allocs) csaw::free_with(alloc, p, nullptr);
     }
 };
 
@@ -2048,9 +2093,9 @@ extern "C" csaw_status csaw_sample_plan_create_ex(csaw_graph* g, uint32_t n_inst
     P.attempt_cap = opts ? opts->attempt_cap : CSAW_ATTEMPT_CAP;
     P.seeds_cap = max_seeds;
     pl->max_seeds = max_seeds;
+    pl->alloc = g->allocator;
     auto get = [&](void** p, size_t bytes) -> csaw_status {
-        cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
-        if (e != cudaSuccess) { *p = nullptr; return cuda_fail(e, "cudaMalloc(plan)"); }
+        CSAW_TRY(alloc_with(&pl->alloc, p, bytes ? bytes : 16, nullptr));
         pl->allocs.push_back(*p);
         return CSAW_OK;
     };
@@ -2243,6 +2288,355 @@ extern "C" csaw_status csaw_sample_plan_destroy(csaw_sample_plan* pl)
     clear_error();
     if (pl && pl->ran) cudaStreamSynchronize(pl->last);
     delete pl;
+    return CSAW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Layered sampling over a graph kept in host memory (out-of-memory sampling,
+// Sec. V-A; partitions loaded in the background while others are sampled,
+// Sec. V-B).  The CSR stays in host memory, cut into vertex ranges whose
+// columns (and weights), plus room for their shared hub prefix sums, fit one
+// device slot of the budget.  The row offsets and the degrees stay resident
+// (16 bytes per vertex beyond the budget), so each layer's counts and edge
+// positions are computed once; then the partitions holding frontier vertices
+// are taken in the order of how many entries they hold (workload-aware
+// scheduling, Sec. V-A), and for each one the selection kernels run over the
+// entries whose vertex lies in it, with the column and weight bases pointed
+// into the slot.  With two or more slots the next partition's copies run on
+// their own stream while the current one is sampled.  Draws, prefix sums and
+// output are those of csaw_sample: results are identical.
+
+namespace csaw {
+
+// Frontier entries of positive degree per partition (bounds vb[0..np]).
+__global__ void oom_part_count_kernel(const uint64_t* __restrict__ fkeys, const unsigned long long* n_dev,
+                                      uint64_t vmask, const uint64_t* __restrict__ off,
+                                      const uint32_t* __restrict__ vb, uint32_t np,
+                                      unsigned long long* __restrict__ counts)
+{
+    const uint64_t n = *n_dev;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = (uint32_t)(fkeys[e] & vmask);
+        if (off[v + 1] == off[v]) continue;
+        uint32_t lo = 0, hi = np;   // last q with vb[q] <= v
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (vb[mid] <= v) lo = mid; else hi = mid;
+        }
+        atomicAdd(counts + lo, 1ull);
+    }
+}
+
+__global__ void degrees_kernel(const uint64_t* __restrict__ off, uint32_t V, uint32_t* __restrict__ deg)
+{
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V;
+         v += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t d = off[v + 1] - off[v];
+        deg[v] = (uint32_t)(d > 0xFFFFFFFFull ? 0xFFFFFFFFull : d);
+    }
+}
+
+// One device slot of the out-of-memory sampler.
+struct OomSlot {
+    uint32_t* col = nullptr;
+    uint32_t* w = nullptr;
+    uint64_t* hubS = nullptr;
+    int64_t part = -1;                 // partition it holds
+    cudaEvent_t loaded = nullptr;      // its copies are done
+    cudaEvent_t freed = nullptr;       // the selection that read it is done
+};
+
+}  // namespace csaw
+
+extern "C" csaw_status csaw_sample_oom(const uint64_t* row_offsets, const uint32_t* cols, const uint32_t* weights,
+                                       uint32_t n_vertices, uint64_t n_edges, uint64_t device_budget_bytes,
+                                       const uint32_t* seeds, const uint64_t* inst_offsets, uint32_t n_instances,
+                                       uint32_t depth, const uint32_t* fanout, const csaw_bias* bias,
+                                       uint64_t rng_seed, const csaw_oom_opts* opts, csaw_oom_stats* stats,
+                                       void* stream, csaw_sample_result** out)
+{
+    clear_error();
+    if (stats) *stats = csaw_oom_stats{};
+    if (!out) return fail(CSAW_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!row_offsets || (n_edges && !cols) || !inst_offsets || !fanout || !bias)
+        return fail(CSAW_ERR_INVALID, "NULL argument");
+    const int kind = bias->kind;
+    if (kind != CSAW_BIAS_UNIFORM && kind != CSAW_BIAS_EDGE_WEIGHT && kind != CSAW_BIAS_NEIGHBOR_DEGREE)
+        return fail(CSAW_ERR_INVALID, "out-of-memory sampling takes uniform, edge-weight or neighbour-degree bias");
+    const int eff_kind = (kind == CSAW_BIAS_EDGE_WEIGHT && !weights) ? CSAW_BIAS_UNIFORM : kind;
+    const bool weighted = eff_kind == CSAW_BIAS_EDGE_WEIGHT;
+    if (depth < 1 || depth > CSAW_MAX_DEPTH) return fail(CSAW_ERR_INVALID, "depth must be 1..%u", CSAW_MAX_DEPTH);
+    for (uint32_t l = 0; l < depth; ++l)
+        if (fanout[l] == 0) return fail(CSAW_ERR_INVALID, "fanout[%u] is 0", l);
+    if (n_instances == 0xFFFFFFFFu) return fail(CSAW_ERR_INVALID, "too many instances");
+    const uint32_t n_slots = opts && opts->slots ? opts->slots : 2;
+    if (n_slots > 8) return fail(CSAW_ERR_INVALID, "at most 8 slots");
+    // host validation: the CSR, the seeds, and positive biases (the count of
+    // positive biases is the degree, so counts need no partition)
+    if (n_vertices == 0 || row_offsets[0] != 0 || row_offsets[n_vertices] != n_edges)
+        return fail(CSAW_ERR_INVALID, "row_offsets must run from 0 to n_edges");
+    uint32_t max_degree = 0;
+    for (uint32_t v = 0; v < n_vertices; ++v) {
+        if (row_offsets[v + 1] < row_offsets[v]) return fail(CSAW_ERR_INVALID, "row_offsets must not decrease");
+        const uint64_t d = row_offsets[v + 1] - row_offsets[v];
+        if (d > 0xFFFFFFFFull) return fail(CSAW_ERR_INVALID, "row %u longer than 2^32-1", v);
+        if (d > max_degree) max_degree = (uint32_t)d;
+    }
+    for (uint64_t i = 0; i < n_edges; ++i)
+        if (cols[i] >= n_vertices) return fail(CSAW_ERR_INVALID, "column %llu out of range", (unsigned long long)i);
+    uint32_t max_weight = 1;
+    if (weighted)
+        for (uint64_t i = 0; i < n_edges; ++i) {
+            if (weights[i] == 0) return fail(CSAW_ERR_INVALID, "out-of-memory sampling needs positive weights");
+            if (weights[i] > max_weight) max_weight = weights[i];
+        }
+    if (eff_kind == CSAW_BIAS_NEIGHBOR_DEGREE)
+        for (uint64_t i = 0; i < n_edges; ++i)
+            if (row_offsets[cols[i] + 1] == row_offsets[cols[i]])
+                return fail(CSAW_ERR_INVALID, "neighbour-degree bias: an edge points at a vertex without neighbours");
+    if (inst_offsets[0] != 0) return fail(CSAW_ERR_INVALID, "inst_offsets must start at 0");
+    for (uint32_t i = 0; i < n_instances; ++i)
+        if (inst_offsets[i + 1] < inst_offsets[i]) return fail(CSAW_ERR_INVALID, "inst_offsets must be non-decreasing");
+    const uint64_t n_seeds = inst_offsets[n_instances];
+    if (n_seeds >= 0xFFFFFFFFull) return fail(CSAW_ERR_INVALID, "too many seeds");
+    if (n_seeds && !seeds) return fail(CSAW_ERR_INVALID, "seeds is NULL");
+    for (uint64_t j = 0; j < n_seeds; ++j)
+        if (seeds[j] >= n_vertices) return fail(CSAW_ERR_INVALID, "seed %llu out of range", (unsigned long long)j);
+
+    // partitions: columns, weights and hub prefix sums (16 bytes per edge)
+    uint32_t np = 0;
+    CSAW_TRY(csaw_oom_plan(row_offsets, n_vertices, 1, device_budget_bytes, nullptr, 0, &np));
+    std::vector<uint32_t> vb((size_t)np + 1);
+    CSAW_TRY(csaw_oom_plan(row_offsets, n_vertices, 1, device_budget_bytes, vb.data(), np + 1, &np));
+    uint64_t slot_edges = 1;
+    for (uint32_t q = 0; q < np; ++q)
+        slot_edges = std::max<uint64_t>(slot_edges, row_offsets[vb[q + 1]] - row_offsets[vb[q]]);
+
+    cudaStream_t s = (cudaStream_t)stream;
+    int device = 0;
+    CSAW_CUDA(cudaGetDevice(&device));
+    csaw_graph view;   // resident offsets and degrees; columns and weights point into a slot per round
+    view.V = n_vertices;
+    view.E = n_edges;
+    view.max_degree = max_degree;
+    view.max_weight = max_weight;
+    view.min_weight = 1;
+    view.zero_degree_target = false;
+    view.device = device;
+    CSAW_CUDA(cudaDeviceGetAttribute(&view.sm_count, cudaDevAttrMultiProcessorCount, device));
+
+    csaw_sample_result* R = new (std::nothrow) csaw_sample_result();
+    if (!R) return fail(CSAW_ERR_NOMEM, "host allocation failed");
+    R->depth = depth;
+    R->n_instances = n_instances;
+    R->stream = s;
+    std::vector<OomSlot> slot(n_slots);
+    cudaStream_t cs = nullptr;   // copies
+    Temps tmp(s);
+    auto get = [&](void** p, size_t bytes) -> csaw_status {
+        CSAW_TRY(dalloc(p, bytes, s));
+        tmp.ptrs.push_back(*p);
+        return CSAW_OK;
+    };
+    auto get_out = [&](void** p, size_t bytes) -> csaw_status { return dalloc(p, bytes, s); };
+    csaw_oom_stats acc{};
+    acc.partitions = np;
+    bool registered_col = false, registered_w = false;
+    csaw_status st = CSAW_OK;
+    do {
+        // pinned (registered) host arrays let the copies run behind the selection
+        if (opts && opts->pin_host && n_edges) {
+            registered_col = cudaHostRegister((void*)cols, sizeof(uint32_t) * n_edges,
+                                              cudaHostRegisterReadOnly) == cudaSuccess;
+            if (weighted)
+                registered_w = cudaHostRegister((void*)weights, sizeof(uint32_t) * n_edges,
+                                                cudaHostRegisterReadOnly) == cudaSuccess;
+            cudaGetLastError();   // a refused registration leaves ordinary (pageable) copies
+        }
+        cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { st = cuda_fail(e, "cudaStreamCreate"); break; }
+        for (auto& sl : slot) {
+            st = get((void**)&sl.col, sizeof(uint32_t) * slot_edges);
+            if (st == CSAW_OK && weighted) st = get((void**)&sl.w, sizeof(uint32_t) * slot_edges);
+            if (st == CSAW_OK) st = get((void**)&sl.hubS, sizeof(uint64_t) * slot_edges);
+            if (st != CSAW_OK) break;
+            e = cudaEventCreateWithFlags(&sl.loaded, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.freed, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventRecord(sl.freed, s);
+            if (e != cudaSuccess) { st = cuda_fail(e, "cudaEvent"); break; }
+        }
+        if (st != CSAW_OK) break;
+        uint64_t* d_off = nullptr;
+        uint32_t* d_deg = nullptr;
+        uint32_t* d_vb = nullptr;
+        unsigned long long* d_pc = nullptr;
+        void* d_seeds = nullptr;
+        void* d_io = nullptr;
+        st = get((void**)&d_off, sizeof(uint64_t) * ((uint64_t)n_vertices + 1));
+        if (st == CSAW_OK) st = get((void**)&d_deg, sizeof(uint32_t) * n_vertices);
+        if (st == CSAW_OK) st = get((void**)&d_vb, sizeof(uint32_t) * (np + 1));
+        if (st == CSAW_OK) st = get((void**)&d_pc, sizeof(unsigned long long) * np);
+        if (st == CSAW_OK) st = get(&d_seeds, sizeof(uint32_t) * (n_seeds ? n_seeds : 1));
+        if (st == CSAW_OK) st = get(&d_io, sizeof(uint64_t) * ((uint64_t)n_instances + 1));
+        if (st != CSAW_OK) break;
+        e = cudaMemcpyAsync(d_off, row_offsets, sizeof(uint64_t) * ((uint64_t)n_vertices + 1), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_vb, vb.data(), sizeof(uint32_t) * (np + 1), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && n_seeds) e = cudaMemcpyAsync(d_seeds, seeds, sizeof(uint32_t) * n_seeds, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_io, inst_offsets, sizeof(uint64_t) * ((uint64_t)n_instances + 1), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) { st = cuda_fail(e, "copy inputs"); break; }
+        degrees_kernel<<<grid_for(n_vertices, 256, view.sm_count), 256, 0, s>>>(d_off, n_vertices, d_deg);
+        view.off = d_off;
+        view.deg = d_deg;
+        view.col = slot[0].col;
+        view.w = weighted ? slot[0].w : nullptr;
+
+        Pipeline P;
+        P.init(&view, eff_kind, n_instances, depth, fanout, rng_seed);
+        P.seeds_cap = n_seeds;
+        st = alloc_common(P, get);
+        if (st == CSAW_OK) {
+            e = cudaMemsetAsync(P.ctr, 0, sizeof(uint64_t) * CT_WORDS, s);
+            if (e != cudaSuccess) st = cuda_fail(e, "memset");
+        }
+        if (st == CSAW_OK) st = alloc_entries(P, 0, n_seeds, get);
+        if (st == CSAW_OK) st = enqueue_frontier0(P, (const uint32_t*)d_seeds, (const uint64_t*)d_io, s);
+        if (st != CSAW_OK) break;
+        R->src.assign(depth, nullptr);
+        R->dst.assign(depth, nullptr);
+        R->layer_edges.assign(depth, 0);
+        std::vector<unsigned long long> pc(np);
+        for (uint32_t l = 0; st == CSAW_OK && l < depth; ++l) {
+            LayerBufs& B = P.L[l];
+            Temps layer_tmp(s);
+            auto get_layer = [&](void** p, size_t bytes) -> csaw_status {
+                CSAW_TRY(dalloc(p, bytes, s));
+                layer_tmp.ptrs.push_back(*p);
+                return CSAW_OK;
+            };
+            if (P.hub_path) st = alloc_hub(P, B.f_cap, get_layer);
+            // counts and edge positions of every entry (degrees are resident)
+            if (st == CSAW_OK) st = enqueue_classify(P, l, 0, 0, true, s);
+            if (st == CSAW_OK) st = scan_u32(B.cnt, B.pos, P.lc(l, L_N), B.f_cap, P.scan_scr, P.lc(l, L_TOTAL), s);
+            if (st != CSAW_OK) break;
+            e = cudaMemsetAsync(d_pc, 0, sizeof(unsigned long long) * np, s);
+            if (e == cudaSuccess && B.f_cap)
+                oom_part_count_kernel<<<grid_for(B.f_cap, 256, view.sm_count), 256, 0, s>>>(
+                    B.F, (const unsigned long long*)P.lc(l, L_N), P.vmask, d_off, d_vb, np, d_pc);
+            uint64_t h[2] = {0, 0};
+            if (e == cudaSuccess) e = cudaMemcpyAsync(pc.data(), d_pc, sizeof(unsigned long long) * np, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&h[0], P.ctr + CT_ERR, sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&h[1], P.lc(l, L_TOTAL), sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) { st = cuda_fail(e, "layer counts"); break; }
+            st = check_errors(h[0]);
+            if (st != CSAW_OK) break;
+            const uint64_t total = h[1];
+            R->layer_edges[l] = total;
+            st = alloc_edges(P, l, total, get, get_out);
+            if (st != CSAW_OK) break;
+            R->src[l] = P.L[l].src;
+            R->dst[l] = P.L[l].dst;
+            // workload-aware order: the partitions with the most frontier entries first
+            std::vector<uint32_t> order;
+            for (uint32_t q = 0; q < np; ++q)
+                if (pc[q]) order.push_back(q);
+            std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return pc[a] > pc[b]; });
+            // slot of each round: a partition already resident keeps its slot
+            std::vector<int> use(order.size(), -1);
+            auto load = [&](size_t i) -> csaw_status {
+                const uint32_t q = order[i];
+                for (uint32_t k = 0; k < n_slots; ++k)
+                    if (slot[k].part == (int64_t)q) { use[i] = (int)k; ++acc.reuses; return CSAW_OK; }
+                // the slot least recently needed: round i uses slot i mod n_slots
+                // unless that one holds the partition of round i - 1
+                uint32_t k = (uint32_t)(i % n_slots);
+                if (i > 0 && (int)k == use[i - 1]) k = (k + 1) % n_slots;
+                OomSlot& sl = slot[k];
+                const uint64_t e0 = row_offsets[vb[q]], ne = row_offsets[vb[q + 1]] - e0;
+                cudaError_t ce = cudaStreamWaitEvent(cs, sl.freed, 0);
+                if (ce == cudaSuccess && ne)
+                    ce = cudaMemcpyAsync(sl.col, cols + e0, sizeof(uint32_t) * ne, cudaMemcpyHostToDevice, cs);
+                if (ce == cudaSuccess && weighted && ne)
+                    ce = cudaMemcpyAsync(sl.w, weights + e0, sizeof(uint32_t) * ne, cudaMemcpyHostToDevice, cs);
+                if (ce == cudaSuccess) ce = cudaEventRecord(sl.loaded, cs);
+                if (ce != cudaSuccess) return cuda_fail(ce, "partition copy");
+                sl.part = q;
+                use[i] = (int)k;
+                acc.loads += 1;
+                acc.bytes_loaded += ne * (weighted ? 8 : 4);
+                return CSAW_OK;
+            };
+            if (!order.empty()) st = load(0);
+            for (size_t i = 0; st == CSAW_OK && i < order.size(); ++i) {
+                const uint32_t q = order[i];
+                OomSlot& sl = slot[use[i]];
+                const uint64_t e0 = row_offsets[vb[q]];
+                e = cudaStreamWaitEvent(s, sl.loaded, 0);
+                // the round's item counters start at zero
+                if (e == cudaSuccess)
+                    e = cudaMemsetAsync(P.lc(l, L_ITEMS), 0, sizeof(uint64_t) * (L_HNEXT + 2 - L_ITEMS), s);
+                if (e != cudaSuccess) { st = cuda_fail(e, "round"); break; }
+                // rows of [vb[q], vb[q+1]) hold edges e0 ..; the slot holds them from 0
+                view.col = sl.col - e0;
+                view.w = weighted ? sl.w - e0 : nullptr;
+                P.hubS = sl.hubS;
+                P.hubS_cap = slot_edges;
+                st = enqueue_classify(P, l, vb[q], vb[q + 1], false, s);
+                if (st == CSAW_OK && P.hub_path) st = enqueue_hub_groups(P, l, s);
+                if (st == CSAW_OK) st = enqueue_select_items(P, l, s);
+                if (st != CSAW_OK) break;
+                e = cudaEventRecord(sl.freed, s);
+                if (e != cudaSuccess) { st = cuda_fail(e, "round"); break; }
+                // the next round's copies run while this round's selection does
+                if (i + 1 < order.size()) st = load(i + 1);
+            }
+            if (st == CSAW_OK) st = enqueue_layer_offsets(P, l, s);
+            if (st == CSAW_OK && l + 1 < depth) {
+                st = alloc_entries(P, l + 1, total, get);
+                if (st == CSAW_OK) st = enqueue_compact(P, l, s);
+            }
+        }
+        if (st != CSAW_OK) break;
+        const uint64_t ng = (uint64_t)depth * n_instances;
+        R->edge_offsets.assign(ng + 1, 0);
+        R->frontier_sizes.assign(ng, 0);
+        uint64_t err_end = 0;
+        if (ng) {
+            e = cudaMemcpyAsync(R->edge_offsets.data(), P.eoff, sizeof(uint64_t) * (ng + 1), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(R->frontier_sizes.data(), P.fsize, sizeof(uint64_t) * ng, cudaMemcpyDeviceToHost, s);
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&err_end, P.ctr + CT_ERR, sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { st = cuda_fail(e, "out-of-memory sampling"); break; }
+        st = check_errors(err_end);
+        if (st != CSAW_OK) break;
+        uint64_t tot = 0;
+        for (uint32_t l = 0; l < depth; ++l) tot += R->layer_edges[l];
+        R->n_edges = tot;
+        R->edge_offsets[ng] = tot;
+        R->src_c.assign(R->src.begin(), R->src.end());
+        R->dst_c.assign(R->dst.begin(), R->dst.end());
+    } while (false);
+    cudaStreamSynchronize(s);
+    if (cs) {
+        cudaStreamSynchronize(cs);
+        cudaStreamDestroy(cs);
+    }
+    for (auto& sl : slot) {
+        if (sl.loaded) cudaEventDestroy(sl.loaded);
+        if (sl.freed) cudaEventDestroy(sl.freed);
+    }
+    if (registered_col) cudaHostUnregister((void*)cols);
+    if (registered_w) cudaHostUnregister((void*)weights);
+    if (st != CSAW_OK) {
+        delete R;
+        return st;
+    }
+    if (stats) *stats = acc;
+    *out = R;
     return CSAW_OK;
 }
 

@@ -183,8 +183,8 @@ static inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 // Walk requests of one bias in one launch.  Inputs are packed in the staging
 // buffer as [segment starts u64 (R+1) | row offsets u64 (R) | lengths u32 (R)
-// | keys u32 (2R) | start vertices u32 (n)], copied in once; the path matrix
-// of every request comes back in one copy.
+// | keys u32 (2R) | start vertices u32 (n)], copied in once; each request's
+// path matrix is copied straight into its result.
 static csaw_status execute_walks(csaw_graph* g, Lane& L, std::vector<Request*>& batch)
 {
     const size_t R = batch.size();
@@ -199,7 +199,7 @@ static csaw_status execute_walks(csaw_graph* g, Lane& L, std::vector<Request*>& 
     const size_t o_key = align16(o_len + 4 * R), o_starts = align16(o_key + 8 * R);
     const size_t in_bytes = align16(o_starts + 4 * n);
     const size_t out_bytes = 4 * rows;
-    CSAW_TRY(lane_pinned(L, in_bytes > out_bytes ? in_bytes : out_bytes));
+    CSAW_TRY(lane_pinned(L, in_bytes));
     uint64_t* h_start = (uint64_t*)(L.pin + o_start);
     uint64_t* h_row0 = (uint64_t*)(L.pin + o_row0);
     uint32_t* h_len = (uint32_t*)(L.pin + o_len);
@@ -238,20 +238,9 @@ static csaw_status execute_walks(csaw_graph* g, Lane& L, std::vector<Request*>& 
         st = walk_batch(g, &batch[0]->bias, (const uint32_t*)(d + o_starts), n, seg, max_len, (uint32_t*)d_path,
                         L.s);
     }
-    if (st == CSAW_OK && out_bytes) {
-        cudaError_t e = cudaMemcpyAsync(L.pin, d_path, out_bytes, cudaMemcpyDeviceToHost, L.s);
-        if (e != cudaSuccess) st = cuda_fail(e, "copy paths out");
-    }
-    dfree(d_in, L.s);
-    dfree(d_path, L.s);
-    if (st == CSAW_OK) {
-        cudaError_t e = cudaStreamSynchronize(L.s);
-        if (e != cudaSuccess) st = cuda_fail(e, "walk batch");
-    }
-    if (st != CSAW_OK) return st;
-    const uint32_t* h_path = (const uint32_t*)L.pin;
     row = 0;
-    for (Request* rq : batch) {
+    for (size_t r = 0; st == CSAW_OK && r < R; ++r) {
+        Request* rq = batch[r];
         csaw_result* res = rq->result;
         const uint64_t cnt = (uint64_t)rq->starts.size() * ((uint64_t)rq->length + 1);
         res->n_walkers = rq->starts.size();
@@ -260,12 +249,23 @@ static csaw_status execute_walks(csaw_graph* g, Lane& L, std::vector<Request*>& 
         if (!res->path) {
             res->status = CSAW_ERR_NOMEM;
         } else {
-            std::memcpy(res->path, h_path + row, 4 * cnt);
             res->status = CSAW_OK;
+            if (cnt) {
+                cudaError_t e = cudaMemcpyAsync(res->path, (const uint32_t*)d_path + row, 4 * cnt,
+                                                cudaMemcpyDeviceToHost, L.s);
+                if (e != cudaSuccess) st = cuda_fail(e, "copy paths out");
+            }
         }
         row += cnt;
     }
-    return CSAW_OK;
+    dfree(d_in, L.s);
+    dfree(d_path, L.s);
+    if (st == CSAW_OK) {
+        cudaError_t e = cudaStreamSynchronize(L.s);
+        if (e != cudaSuccess) st = cuda_fail(e, "walk batch");
+    }
+    (void)out_bytes;
+    return st;
 }
 
 // Sampling requests of one bias in one multi-instance run.  The batch's
@@ -273,7 +273,8 @@ static csaw_status execute_walks(csaw_graph* g, Lane& L, std::vector<Request*>& 
 // its request's key, its own index and its request's fanout per layer (0
 // past the request's depth).  Inputs are packed as [instance offsets u64
 // (N+1) | keys u32 (2N) | indices u32 (N) | fanouts u32 (depth N) | seeds u32
-// (S)]; every layer's edges come back in one copy each for src and dst.
+// (S)]; each request's edges are copied straight into its result, one copy
+// per layer for src and one for dst.
 static csaw_status execute_samples(csaw_graph* g, Lane& L, std::vector<Request*>& batch)
 {
     uint64_t N = 0, S = 0;
@@ -332,27 +333,6 @@ static csaw_status execute_samples(csaw_graph* g, Lane& L, std::vector<Request*>
     if (st != CSAW_OK) return st;
     csaw_sample_view v;
     csaw_sample_get_view(R, &v);
-    // every layer's edges: src at [0, E), dst at [E, 2E) of the staging buffer
-    const uint64_t E = v.n_edges;
-    st = lane_pinned(L, 8 * E + 16);
-    uint32_t* h_src = (uint32_t*)L.pin;
-    uint32_t* h_dst = h_src + E;
-    for (uint32_t l = 0; st == CSAW_OK && l < depth; ++l) {
-        const uint64_t a = v.edge_offsets[(uint64_t)l * N], b = v.edge_offsets[(uint64_t)(l + 1) * N];
-        if (b > a) {
-            e = cudaMemcpyAsync(h_src + a, v.src[l], 4 * (b - a), cudaMemcpyDeviceToHost, L.s);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(h_dst + a, v.dst[l], 4 * (b - a), cudaMemcpyDeviceToHost, L.s);
-            if (e != cudaSuccess) st = cuda_fail(e, "copy edges out");
-        }
-    }
-    if (st == CSAW_OK) {
-        e = cudaStreamSynchronize(L.s);
-        if (e != cudaSuccess) st = cuda_fail(e, "sample batch");
-    }
-    if (st != CSAW_OK) {
-        csaw_result_free(R);
-        return st;
-    }
     // each request: its instances' edges of its own layers, in csaw_sample's layout
     i0 = 0;
     for (Request* rq : batch) {
@@ -372,26 +352,38 @@ static csaw_status execute_samples(csaw_graph* g, Lane& L, std::vector<Request*>
         if (!res->edge_offsets || !res->frontier_sizes || !res->src || !res->dst) {
             res->status = CSAW_ERR_NOMEM;
         } else {
+            res->status = CSAW_OK;
             uint64_t at = 0;
-            for (uint32_t l = 0; l < dep; ++l) {
+            for (uint32_t l = 0; st == CSAW_OK && l < dep; ++l) {
                 const uint64_t* eo = v.edge_offsets + (uint64_t)l * N + i0;
+                const uint64_t layer0 = v.edge_offsets[(uint64_t)l * N];
                 for (uint32_t i = 0; i < n; ++i) {
                     res->edge_offsets[(uint64_t)l * n + i] = at + (eo[i] - eo[0]);
                     res->frontier_sizes[(uint64_t)l * n + i] = v.frontier_sizes[(uint64_t)l * N + i0 + i];
                 }
                 const uint64_t cnt = eo[n] - eo[0];
-                std::memcpy(res->src + at, h_src + eo[0], 4 * cnt);
-                std::memcpy(res->dst + at, h_dst + eo[0], 4 * cnt);
+                if (cnt) {
+                    e = cudaMemcpyAsync(res->src + at, v.src[l] + (eo[0] - layer0), 4 * cnt,
+                                        cudaMemcpyDeviceToHost, L.s);
+                    if (e == cudaSuccess)
+                        e = cudaMemcpyAsync(res->dst + at, v.dst[l] + (eo[0] - layer0), 4 * cnt,
+                                            cudaMemcpyDeviceToHost, L.s);
+                    if (e != cudaSuccess) st = cuda_fail(e, "copy edges out");
+                }
                 at += cnt;
             }
             res->edge_offsets[ng] = total;
-            res->status = CSAW_OK;
         }
         i0 += n;
     }
+    if (st == CSAW_OK) {
+        e = cudaStreamSynchronize(L.s);
+        if (e != cudaSuccess) st = cuda_fail(e, "sample batch");
+    }
     csaw_result_free(R);
-    return CSAW_OK;
+    return st;
 }
+
 
 // Sampled edges a request produces at most (walk steps; sampling without
 // the visited filter).
@@ -480,6 +472,7 @@ struct csaw_server {
     void worker(uint32_t slot)
     {
         cudaSetDevice(g->device);
+        AllocScope alloc_scope(g);   // request buffers through the graph's allocator, if set
         Lane& L = lanes[slot];
         std::vector<Request*> batch;
         std::unique_lock<std::mutex> lk(mu);

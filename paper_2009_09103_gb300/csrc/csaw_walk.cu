@@ -1141,6 +1141,7 @@ extern "C" csaw_status csaw_walk_ex(csaw_graph* g, const uint32_t* starts, uint6
 {
     clear_error();
     if (!g) return fail(CSAW_ERR_INVALID, "graph is NULL");
+    AllocScope alloc_scope(g);
     int kind;
     CSAW_TRY(check_bias(g, bias, true, &kind));
     const uint32_t tele = opts ? (uint32_t)opts->teleport : CSAW_TELEPORT_NONE;

@@ -56,3 +56,71 @@ def test_oom_walk_hub_rows_and_errors(csaw):
         csaw.walk_oom(g.off, g.col, g.w, np.array([g.V], dtype=np.uint32), 5, "edge_weight", 5)
     with pytest.raises(csaw.CsawError):
         csaw.walk_oom(g.off, g.col, g.w, starts, 5, "neighbor_degree", 5)
+
+
+@pytest.mark.parametrize("slots,pin", [(2, False), (3, True), (1, False)])
+def test_oom_walk_slots_and_prefetch(csaw, slots, pin):
+    """Several partition slots, the next busiest partition loaded while a
+    round runs, and page-locked host arrays: the same paths."""
+    g = inputs.rmat_csr(13, 16, 100, 13)
+    budget = 16 * int(np.diff(g.off).max()) + 4096
+    starts = inputs.uniform_vertices(5000, g.V, 9)
+    path, st = csaw.walk_oom(g.off, g.col, g.w, starts, 25, "edge_weight", 17, budget_bytes=budget,
+                             slots=slots, pin_host=pin)
+    assert np.array_equal(path, oracle.walk(g, starts, 25, "edge_weight", 17))
+    assert st["partitions"] > 5
+    if slots > 1:
+        assert st["reuses"] > 0
+
+
+def _sample_cases():
+    g = inputs.rmat_csr(12, 16, 100, 12)
+    sizes = inputs.loguniform_sizes(30, 0.0, 7.0, 4)
+    seeds, io = inputs.distinct_seeds(sizes, g.V, 4)
+    return g, seeds, io
+
+
+@pytest.mark.parametrize("bias,fanout", [("edge_weight", [10, 5]), ("neighbor_degree", [25, 10]),
+                                         ("uniform", [3, 3, 3]), ("edge_weight", [0xFFFFFFFF, 2]),
+                                         ("edge_weight", [300, 2])])
+@pytest.mark.parametrize("budget", ["whole", "several", "smallest"])
+def test_oom_sampling_equals_in_memory_sampling(csaw, bias, fanout, budget):
+    """Layered sampling over a host-resident graph, one partition at a time
+    (busiest first), equals csaw_sample and the oracle at any partition count."""
+    g, seeds, io = _sample_cases()
+    big = 16 * int(np.diff(g.off).max()) + 1024
+    b = {"whole": 1 << 30, "several": 16 * g.E // 4 + big, "smallest": big}[budget]
+    res, st = csaw.sample_oom(g.off, g.col, g.w, seeds, io, fanout, bias, 23, budget_bytes=b, slots=2)
+    ref = oracle.sample(g, seeds, io, fanout, bias, 23)
+    assert np.array_equal(res.edge_offsets, ref["edge_off"])
+    assert np.array_equal(res.src, ref["src"]) and np.array_equal(res.dst, ref["dst"])
+    assert np.array_equal(res.frontier_sizes, ref["fsize"][: len(fanout) * (len(io) - 1)])
+    G = csaw.Graph(g.off, g.col, g.w)
+    mem = csaw.sample(G, seeds, io, fanout, bias, 23)
+    G.close()
+    assert np.array_equal(res.dst, mem.dst)
+    if budget == "smallest":
+        assert st["partitions"] > 5 and st["loads"] >= len(fanout)
+    if budget == "whole":
+        assert st["partitions"] == 1
+
+
+def test_oom_sampling_slots_pinning_and_errors(csaw):
+    g, seeds, io = _sample_cases()
+    big = 16 * int(np.diff(g.off).max()) + 1024
+    ref = oracle.sample(g, seeds, io, [25, 10], "neighbor_degree", 4)
+    for slots, pin in ((1, False), (3, True), (8, False)):
+        res, st = csaw.sample_oom(g.off, g.col, g.w, seeds, io, [25, 10], "neighbor_degree", 4, budget_bytes=big,
+                                  slots=slots, pin_host=pin)
+        assert np.array_equal(res.dst, ref["dst"]) and np.array_equal(res.edge_offsets, ref["edge_off"])
+    w0 = g.w.copy()
+    w0[5] = 0
+    with pytest.raises(csaw.CsawError) as e:   # a zero bias is refused
+        csaw.sample_oom(g.off, g.col, w0, seeds, io, [5], "edge_weight", 1, budget_bytes=big)
+    assert e.value.status == csaw.ERR_INVALID
+    with pytest.raises(csaw.CsawError) as e:   # a row larger than the budget
+        csaw.sample_oom(g.off, g.col, g.w, seeds, io, [5], "edge_weight", 1, budget_bytes=big // 2)
+    assert e.value.status == csaw.ERR_NOMEM
+    with pytest.raises(csaw.CsawError) as e:
+        csaw.sample_oom(g.off, g.col, g.w, seeds, io, [5], "node2vec", 1, budget_bytes=big)
+    assert e.value.status == csaw.ERR_INVALID
