@@ -946,6 +946,49 @@ def run_oom_bench(args):
 
 
 # --------------------------------------------------------------------------
+# Attempts per pick (the iterations per pick of Sec. VI / Fig. 10): repeated
+# sampling against updated sampling from the first pick (attempt cap 0, the
+# exact form of bipartite region search), counted by the library built with
+# the selection counters.
+
+def run_attempts_bench(args):
+    os.environ["CSAW_LIB_VARIANT"] = "stats"
+    import torch
+    from paper_2009_09103_gb300 import build, csaw, inputs
+    build.build()
+    torch.cuda.set_device(0)
+    cases = []
+    s12 = inputs.workload_sample_s12()
+    cases.append(("RMAT s12, 256 seeds, fanout [10,5]", s12.graph, s12.seeds, s12.inst_offsets, [10, 5]))
+    b24 = inputs.workload_batched_s24()
+    cases.append(("RMAT s24, 4096 instances, fanout [25,10]", b24.graph, b24.seeds, b24.inst_offsets, [25, 10]))
+    rows = []
+    for name, g, seeds, io, fan in cases:
+        G = csaw.Graph(g.off, g.col, g.w)
+        for bias in ("neighbor_degree", "edge_weight"):
+            out = {"workload": name, "bias": bias}
+            for label, cap in (("repeated", 1024), ("updated_from_first_pick", 0)):
+                csaw.selection_stats(reset=True)
+                res = csaw.sample(G, seeds, io, fan, bias, 4, attempt_cap=cap, to_host=False)
+                c = csaw.selection_stats(reset=True)
+                picks = max(1, c["drawn_picks"])
+                out[label] = {**c, "sampled_edges": int(res.n_edges),
+                              "draws_per_pick": c["draws_consumed"] / picks,
+                              "evaluated_per_pick": c["draws_evaluated"] / picks}
+                del res
+            out["reduction_draws_per_pick"] = (out["repeated"]["draws_per_pick"] /
+                                               out["updated_from_first_pick"]["draws_per_pick"])
+            rows.append(out)
+            log(f"[bench] attempts {name} {bias}: repeated {out['repeated']['draws_per_pick']:.3f} per pick, "
+                f"updated {out['updated_from_first_pick']['draws_per_pick']:.3f}; "
+                f"x{out['reduction_draws_per_pick']:.2f}")
+        G.close()
+    return {"metric": "draws per pick (iterations per pick)", "value": rows[0]["reduction_draws_per_pick"],
+            "unit": "ratio", "higher_is_better": True, "n_gpus": 1, "data": "synthetic (seeded RMAT)",
+            "library": "built with -DCSAW_STATS (counters; not for timing)", "rows": rows}
+
+
+# --------------------------------------------------------------------------
 # Serving (config: RMAT s26 resident): open-loop Poisson arrivals of a 50/50
 # mix of sampling and walk requests into csaw_server, against the same
 # requests run one after another with plain calls.
@@ -1117,7 +1160,8 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=None,
                     help="--impl reference: oracle seconds per step (default: about a minute in all)")
     ap.add_argument("--workload", default="walk",
-                    choices=["walk", "node2vec", "sample_s12", "batched_s24", "serve", "mdrw", "layer", "oom"])
+                    choices=["walk", "node2vec", "sample_s12", "batched_s24", "serve", "mdrw", "layer", "oom",
+                             "attempts"])
     ap.add_argument("--autotune", action="store_true", help="sampling workloads: autotune first")
     ap.add_argument("--no-variant", action="store_true",
                     help="walks: skip the cached-array variant measured after the main line")
@@ -1139,8 +1183,9 @@ def main():
     if args.scale is None:
         args.scale = {"walk": 20, "node2vec": 22}.get(args.workload)
     rank, world, local = dist_env()
-    if args.workload in ("sample_s12", "batched_s24", "serve", "mdrw", "layer", "oom"):
+    if args.workload in ("sample_s12", "batched_s24", "serve", "mdrw", "layer", "oom", "attempts"):
         res = (run_serve_bench(args) if args.workload == "serve" else
+               run_attempts_bench(args) if args.workload == "attempts" else
                run_mdrw_bench(args) if args.workload == "mdrw" else
                run_oom_bench(args) if args.workload == "oom" else
                run_layer_bench(args) if args.workload == "layer" else run_sample_bench(args))

@@ -233,6 +233,7 @@ typedef struct {
     uint64_t loads;          /* partition uploads (scheduling rounds) */
     uint64_t bytes_loaded;   /* host-to-device bytes of those uploads */
     uint64_t reuses;         /* rounds whose partition was still in a slot (no upload) */
+    uint64_t pinned_bytes;   /* host bytes page-locked for the call (opts->pin_host) */
 } csaw_oom_stats;
 
 /* Options of the out-of-memory calls (NULL = defaults). */
@@ -643,6 +644,23 @@ csaw_status csaw_select_noalloc(csaw_graph* g, const uint32_t* vertices, const u
                                 uint32_t n, uint32_t k, uint32_t layer, const csaw_bias* bias,
                                 uint64_t rng_seed, uint32_t* out_src, uint32_t* out_dst,
                                 uint64_t capacity, uint64_t* out_offsets, void* stream);
+
+/* ---------------------------------------------------------------- counters */
+
+/* Selection counters of the attempts-per-pick measurement (the iterations
+ * per pick of Sec. VI / Fig. 10), kept by a library built with -DCSAW_STATS
+ * (libcsaw_stats.so; the default build keeps none and returns
+ * CSAW_ERR_INVALID).  Counted over every csaw_sample-family selection since
+ * the last reset, on all devices' streams after a device synchronisation:
+ *   [0] draws consumed: a selection consumes its attempts up to the one that
+ *       gave its last pick (repeated sampling), or all CSAW_ATTEMPT_CAP of
+ *       them and one per updated-sampling pick
+ *   [1] picks of the selections that drew (take-all selections draw nothing)
+ *   [2] draws evaluated (whole warp rounds of 32, plus updated-sampling draws)
+ *   [3] picks by updated sampling
+ *   [4] warp items, [5] CTA items, [6] shared-hub items, [7] unused
+ * reset: zero them after reading. */
+csaw_status csaw_selection_stats(uint64_t counters[8], int reset);
 
 /* ---------------------------------------------------------------- misc */
 

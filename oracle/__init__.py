@@ -72,8 +72,18 @@ def _load():
         lib.ref_mdrw.restype = i32
         lib.ref_free.argtypes = [P]
         lib.ref_free.restype = None
+        lib.ref_stats.argtypes = [P, i32]
+        lib.ref_stats.restype = None
         _lib = lib
     return _lib
+
+
+def stats(reset: bool = False):
+    """(draws consumed, picks of the selections that drew) since the last
+    reset: the attempts-per-pick count of the selections run so far."""
+    out = np.zeros(2, dtype=np.uint64)
+    _load().ref_stats(_p(out), int(reset))
+    return int(out[0]), int(out[1])
 
 
 def _p(a):

@@ -117,6 +117,20 @@ static uint32_t upper_bound_u64(const uint64_t* S, uint32_t d, uint64_t x)
  * to updated sampling.                                                       */
 typedef int (*ref_draw_fn)(void* ctx, uint32_t attempt, uint64_t* r);
 
+/* Counts kept for the attempts-per-pick measurement (Sec. VI reports
+ * iterations per pick): the draws the selections consumed, and the picks of
+ * the selections that drew (take-all selections draw nothing).  Counting
+ * does not change any result; not thread-safe (the oracle is
+ * single-threaded). */
+static uint64_t g_attempts = 0, g_drawn_picks = 0;
+
+void ref_stats(uint64_t out[2], int reset)
+{
+    out[0] = g_attempts;
+    out[1] = g_drawn_picks;
+    if (reset) g_attempts = g_drawn_picks = 0;
+}
+
 static int64_t select_core(const uint32_t* b, uint32_t d, uint32_t k, uint32_t attempt_cap,
                            ref_draw_fn draw, void* ctx, uint32_t* out_idx)
 {
@@ -146,7 +160,8 @@ static int64_t select_core(const uint32_t* b, uint32_t d, uint32_t k, uint32_t a
     if (!chosen || !S2) { free(S); free(chosen); free(S2); return -2; }
 
     int64_t have = 0;
-    for (uint32_t a = 0; have < (int64_t)k; ++a) {
+    uint32_t a = 0;
+    for (; have < (int64_t)k; ++a) {
         uint64_t r;
         if (draw(ctx, a, &r) != 0) { have = -1; break; }
         if (a < attempt_cap) {
@@ -164,6 +179,10 @@ static int64_t select_core(const uint32_t* b, uint32_t d, uint32_t k, uint32_t a
             chosen[i] = 1;
             out_idx[have++] = i;
         }
+    }
+    if (have > 0) {
+        g_attempts += a;
+        g_drawn_picks += (uint64_t)have;
     }
     free(S); free(S2); free(chosen);
     return have;

@@ -52,23 +52,61 @@ def _compile(src, extra, verbose):
     return obj
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
+STATS_LIB_PATH = os.path.join(PKG, "libcsaw_stats.so")
+STATS_SOURCES = ("csaw_sample.cu",)   # the translation units that keep selection counters
+
+
+def _compile_to(src, flags, obj, verbose):
+    if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), _headers_mtime()):
+        return obj
+    cmd = [_nvcc(), *ARCH, *NVCC_FLAGS, *flags, "-c", src, "-o", obj + ".tmp"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {os.path.basename(src)} {' '.join(flags)}:\n{r.stderr}")
+    if verbose and r.stderr.strip():
+        print(r.stderr)
+    os.replace(obj + ".tmp", obj)
+    return obj
+
+
+def _link(objs, path, force):
+    newest = max(os.path.getmtime(o) for o in objs)
+    if force or not os.path.exists(path) or os.path.getmtime(path) < newest:
+        tmp = path + f".tmp{os.getpid()}"
+        r = subprocess.run([_nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs],
+                           capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc link failed:\n{r.stderr}")
+        os.replace(tmp, path)
+
+
+def build(force: bool = False, verbose: bool = False, extra_flags=(), stats: bool = True) -> str:
+    """libcsaw.so, and libcsaw_stats.so (the same library with the selection
+    counters of the attempts-per-pick measurement compiled in, -DCSAW_STATS),
+    all translation units compiled in parallel."""
     os.makedirs(OBJ_DIR, exist_ok=True)
     srcs = sources()
     if force:
         for o in glob.glob(os.path.join(OBJ_DIR, "*.o")):
             os.remove(o)
     extra = list(extra_flags)
-    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra, verbose), srcs))
-    newest = max(os.path.getmtime(o) for o in objs)
-    if force or extra or not os.path.exists(LIB_PATH) or os.path.getmtime(LIB_PATH) < newest:
-        tmp = LIB_PATH + f".tmp{os.getpid()}"
-        cmd = [_nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
-        r = subprocess.run(cmd, capture_output=True, text=True)
-        if r.returncode != 0:
-            raise RuntimeError(f"nvcc link failed:\n{r.stderr}")
-        os.replace(tmp, LIB_PATH)
+    stem = lambda src: os.path.join(OBJ_DIR, os.path.basename(src)[:-3])
+    jobs = [(src, extra, stem(src) + ".o") for src in srcs]
+    if extra:   # a one-off variant: always rebuilt
+        for _, _, obj in jobs:
+            if os.path.exists(obj):
+                os.remove(obj)
+    stats = stats and not extra
+    if stats:
+        jobs += [(src, ["-DCSAW_STATS"], stem(src) + "_stats.o") for src in srcs
+                 if os.path.basename(src) in STATS_SOURCES]
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 1))) as ex:
+        list(ex.map(lambda j: _compile_to(j[0], j[1], j[2], verbose), jobs))
+    objs = [stem(src) + ".o" for src in srcs]
+    _link(objs, LIB_PATH, force or bool(extra))
+    if stats:
+        sobjs = [stem(src) + ("_stats.o" if os.path.basename(src) in STATS_SOURCES else ".o") for src in srcs]
+        _link(sobjs, STATS_LIB_PATH, force)
     return LIB_PATH
 
 

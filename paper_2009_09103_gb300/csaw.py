@@ -16,6 +16,10 @@ import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libcsaw.so")
+# CSAW_LIB_VARIANT=stats loads the build with the selection counters
+# (csaw_selection_stats); it must be set before the first call
+if os.environ.get("CSAW_LIB_VARIANT") == "stats":
+    LIB_PATH = os.path.join(_PKG, "libcsaw_stats.so")
 
 OK, ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_OVERFLOW, ERR_TIMEOUT, ERR_ABORTED, ERR_NOT_FOUND = range(8)
 MEM_HOST, MEM_DEVICE = 0, 1
@@ -46,7 +50,7 @@ TELEPORT = {None: 0, "restart": 1, "jump": 2}
 
 class OomStats(ctypes.Structure):
     _fields_ = [("partitions", ctypes.c_uint32), ("loads", ctypes.c_uint64), ("bytes_loaded", ctypes.c_uint64),
-                ("reuses", ctypes.c_uint64)]
+                ("reuses", ctypes.c_uint64), ("pinned_bytes", ctypes.c_uint64)]
 
 
 class OomOpts(ctypes.Structure):
@@ -141,6 +145,8 @@ def lib():
                                       ctypes.POINTER(OomOpts), ctypes.POINTER(OomStats), P, ctypes.POINTER(P)]
         L.csaw_sample_oom.restype = ctypes.c_int
         L.csaw_graph_build_cdf.argtypes = [P, ctypes.c_int32, P]
+        L.csaw_selection_stats.argtypes = [P, i32]
+        L.csaw_selection_stats.restype = ctypes.c_int
         L.csaw_graph_set_allocator.argtypes = [P, ALLOC_FN, FREE_FN, P]
         L.csaw_graph_set_allocator.restype = ctypes.c_int
         L.csaw_graph_drop_cdf.argtypes = [P, ctypes.c_int32]
@@ -186,6 +192,18 @@ def lib():
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
+
+
+def selection_stats(reset: bool = False):
+    """csaw_selection_stats (a library built with the counters, i.e. loaded
+    with CSAW_LIB_VARIANT=stats): draws consumed, picks of the selections
+    that drew, draws evaluated, updated-sampling picks, warp / CTA / hub
+    items."""
+    out = np.zeros(8, dtype=np.uint64)
+    _check(lib().csaw_selection_stats(_ptr(out), int(reset)))
+    keys = ("draws_consumed", "drawn_picks", "draws_evaluated", "updated_picks", "warp_items", "cta_items",
+            "hub_items")
+    return {k: int(v) for k, v in zip(keys, out)}
 
 
 def _check(status: int):
@@ -350,7 +368,8 @@ def oom_plan(off, budget_bytes: int, weighted: bool = True) -> np.ndarray:
 
 
 def _oom_stats(st):
-    return {"partitions": st.partitions, "loads": st.loads, "bytes_loaded": st.bytes_loaded, "reuses": st.reuses}
+    return {"partitions": st.partitions, "loads": st.loads, "bytes_loaded": st.bytes_loaded, "reuses": st.reuses,
+            "pinned_bytes": st.pinned_bytes}
 
 
 def walk_oom(off, col, w, starts, length: int, bias="edge_weight", seed: int = 0,

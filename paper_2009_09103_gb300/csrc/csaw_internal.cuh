@@ -126,6 +126,16 @@ struct WalkSegments {
 csaw_status walk_batch(const csaw_graph* g, const csaw_bias* bias, const uint32_t* d_starts, uint64_t n,
                        const WalkSegments& seg, uint32_t max_len, uint32_t* d_path, cudaStream_t s);
 
+// Checks a partition of a host CSR once it is on the device, so that the
+// out-of-memory calls need no pass over every edge on the host: a column that
+// is not a vertex is flagged (bit 1) and replaced by 0, a zero weight (when w
+// is given) flagged (bit 2) and replaced by 1, and an edge into a vertex of
+// degree 0 (when deg is given) flagged (bit 4).  The call then fails with
+// CSAW_ERR_INVALID; the replacements only keep the kernels in bounds.
+// Defined in csaw_oom.cu.
+void launch_partition_check(uint32_t* col, uint32_t* w, uint64_t ne, uint32_t V, const uint32_t* deg,
+                            uint32_t* err, cudaStream_t s);
+
 // Walks that read a cached cumulative array (or, for uniform bias, none):
 // one thread per walker.  Defined in csaw_walk.cu.
 csaw_status launch_walk_cached(const csaw_graph* g, int kind, const uint32_t* starts, uint64_t n,

@@ -124,6 +124,37 @@ __global__ void oom_count_kernel(const uint32_t* __restrict__ cur, const uint32_
     }
 }
 
+__global__ void partition_check_kernel(uint32_t* __restrict__ col, uint32_t* __restrict__ w, uint64_t ne,
+                                       uint32_t V, const uint32_t* __restrict__ deg, uint32_t* __restrict__ err)
+{
+    uint32_t flags = 0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ne;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t c = col[i];
+        if (c >= V) {
+            flags |= 1u;
+            col[i] = 0;
+            c = 0;
+        }
+        if (w && w[i] == 0) {
+            flags |= 2u;
+            w[i] = 1;
+        }
+        if (deg && deg[c] == 0) flags |= 4u;
+    }
+    flags = __reduce_or_sync(CSAW_FULL_MASK, flags);
+    if ((threadIdx.x & 31) == 0 && flags) atomicOr(err, flags);
+}
+
+void launch_partition_check(uint32_t* col, uint32_t* w, uint64_t ne, uint32_t V, const uint32_t* deg,
+                            uint32_t* err, cudaStream_t s)
+{
+    if (ne == 0) return;
+    uint64_t blocks = (ne + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    partition_check_kernel<<<(unsigned)blocks, 256, 0, s>>>(col, w, ne, V, deg, err);
+}
+
 }  // namespace csaw
 
 using namespace csaw;
@@ -194,9 +225,9 @@ extern "C" csaw_status csaw_walk_oom_ex(const uint64_t* row_offsets, const uint3
         return fail(CSAW_ERR_INVALID, "row_offsets must run from 0 to n_edges");
     for (uint32_t v = 0; v < n_vertices; ++v)
         if (row_offsets[v + 1] < row_offsets[v]) return fail(CSAW_ERR_INVALID, "row_offsets must not decrease");
-    // every column a vertex (a walker outside every partition would never finish)
-    for (uint64_t i = 0; i < n_edges; ++i)
-        if (cols[i] >= n_vertices) return fail(CSAW_ERR_INVALID, "column %llu out of range", (unsigned long long)i);
+    // Columns are checked on the device as each partition arrives (a column
+    // that is not a vertex is replaced, so that no walker leaves every
+    // partition, and the call fails).
     cudaStream_t s = (cudaStream_t)stream;
 
     // Partitions: vertex ranges whose slot fits the budget.
@@ -224,6 +255,7 @@ extern "C" csaw_status csaw_walk_oom_ex(const uint64_t* row_offsets, const uint3
     const uint64_t row_len = (uint64_t)length + 1;
     void *d_starts = nullptr, *d_path = nullptr, *d_cur = nullptr, *d_step = nullptr, *d_vb = nullptr;
     void* d_cnt = nullptr;
+    void* d_chk = nullptr;   // partition check flags
     cudaStream_t cs = nullptr;
     bool registered_col = false, registered_w = false;
     auto cleanup = [&]() {
@@ -232,7 +264,7 @@ extern "C" csaw_status csaw_walk_oom_ex(const uint64_t* row_offsets, const uint3
             cudaStreamSynchronize(cs);
             cudaStreamDestroy(cs);
         }
-        for (void* p : {d_starts, d_path, d_cur, d_step, d_vb, d_cnt}) dfree(p, s);
+        for (void* p : {d_starts, d_path, d_cur, d_step, d_vb, d_cnt, d_chk}) dfree(p, s);
         for (auto& sl : slot) {
             for (void* p : {sl.off, sl.col, sl.w, sl.cdf}) dfree(p, s);
             if (sl.loaded) cudaEventDestroy(sl.loaded);
@@ -253,6 +285,12 @@ extern "C" csaw_status csaw_walk_oom_ex(const uint64_t* row_offsets, const uint3
     if (st == CSAW_OK) st = dalloc(&d_step, sizeof(uint32_t) * n_walkers, s);
     if (st == CSAW_OK) st = dalloc(&d_vb, sizeof(uint32_t) * (np + 1), s);
     if (st == CSAW_OK) st = dalloc(&d_cnt, sizeof(unsigned long long) * np, s);
+    if (st == CSAW_OK) st = dalloc(&d_chk, sizeof(uint32_t), s);
+    if (st == CSAW_OK) {
+        cudaError_t e0 = cudaMemsetAsync(d_chk, 0, sizeof(uint32_t), s);
+        if (e0 == cudaSuccess) e0 = cudaStreamSynchronize(s);   // before the copy stream uses it
+        if (e0 != cudaSuccess) st = cuda_fail(e0, "memset");
+    }
     for (auto& sl : slot) {
         if (st == CSAW_OK) st = dalloc(&sl.off, sizeof(uint64_t) * (max_rows + 1), s);
         if (st == CSAW_OK) st = dalloc(&sl.col, sizeof(uint32_t) * (max_edges ? max_edges : 1), s);
@@ -320,6 +358,10 @@ extern "C" csaw_status csaw_walk_oom_ex(const uint64_t* row_offsets, const uint3
             ce = cudaMemcpyAsync(sl.col, cols + e0, sizeof(uint32_t) * ne, cudaMemcpyHostToDevice, cs);
         if (ce == cudaSuccess && weighted && ne)
             ce = cudaMemcpyAsync(sl.w, weights + e0, sizeof(uint32_t) * ne, cudaMemcpyHostToDevice, cs);
+        if (ce == cudaSuccess) {
+            launch_partition_check((uint32_t*)sl.col, nullptr, ne, n_vertices, nullptr, (uint32_t*)d_chk, cs);
+            ce = cudaGetLastError();
+        }
         if (ce == cudaSuccess && weighted) {
             const uint64_t blocks = std::min<uint64_t>(((uint64_t)(v1 - v0) + 7) / 8, 4096);
             oom_cdf_kernel<<<(unsigned)(blocks ? blocks : 1), 256, 0, cs>>>((const uint64_t*)sl.off,
@@ -379,11 +421,16 @@ extern "C" csaw_status csaw_walk_oom_ex(const uint64_t* row_offsets, const uint3
             if (e != cudaSuccess) break;
         }
     }
+    uint32_t chk = 0;
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(path, d_path, sizeof(uint32_t) * n_walkers * row_len, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&chk, d_chk, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    acc.pinned_bytes = (registered_col ? sizeof(uint32_t) * n_edges : 0) + (registered_w ? sizeof(uint32_t) * n_edges : 0);
     cleanup();
     if (e != cudaSuccess) return cuda_fail(e, "out-of-memory walk");
+    if (chk & 1u) return fail(CSAW_ERR_INVALID, "a column is not a vertex of the graph");
     if (stats) *stats = acc;
     return CSAW_OK;
 }

@@ -50,6 +50,26 @@ constexpr uint32_t PICK_MAX = 256;         // picks a cached-array warp item may
 
 static_assert(SEL_WARPS * WARP_SLOT <= SEL_DYN_SMEM, "warp slots reuse the CTA region");
 
+// Selection counters, compiled in with -DCSAW_STATS (the library built for
+// the attempts-per-pick measurement; the default build has none):
+// [0] draws consumed (a selection consumes attempts up to the one that gave
+// its last pick), [1] picks of the selections that drew, [2] draws evaluated
+// (whole warp rounds of 32, plus updated-sampling draws), [3] picks by
+// updated sampling, [4] warp items, [5] CTA items, [6] hub items.
+#ifdef CSAW_STATS
+__device__ unsigned long long g_sel_stats[8];
+#define CSAW_STAT_ADD(i, v) atomicAdd(&g_sel_stats[i], (unsigned long long)(v))
+#else
+#define CSAW_STAT_ADD(i, v) ((void)0)
+#endif
+
+// Position of the n-th set bit of m (n >= 1, m has at least n set bits).
+__device__ __forceinline__ uint32_t nth_set_bit(uint32_t m, uint32_t n)
+{
+    for (uint32_t i = 1; i < n; ++i) m &= m - 1;
+    return (uint32_t)(__ffs(m) - 1);
+}
+
 struct SelParams {
     const uint64_t* __restrict__ off;
     const uint32_t* __restrict__ col;
@@ -147,6 +167,9 @@ __device__ void draw_picks(const SelParams& p, const uint64_t* S, uint32_t* bits
     const uint32_t lt = lanemask_lt();
     uint32_t have = 0;
     uint32_t a0 = 0;
+    uint32_t used = 0, rounds = 0;   // counters (CSAW_STATS)
+    (void)used;
+    (void)rounds;
     while (have < cnt && a0 < p.attempt_cap) {
         const bool live = a0 + lane < p.attempt_cap;   // the last round may be partial
         const uint64_t r = philox_draw(dk.k0, dk.k1, a0 + lane, v, p.layer, dk.id);
@@ -161,11 +184,24 @@ __device__ void draw_picks(const SelParams& p, const uint64_t* S, uint32_t* bits
             emit(p, q0 + have + rank, v, inst, __ldg(p.col + beg + i));
             atomicOr(bits + (i >> 5), 1u << (i & 31));
         }
+#ifdef CSAW_STATS
+        used = (uint32_t)__popc(bal) >= need ? a0 + nth_set_bit(bal, need) + 1 : min(a0 + 32, p.attempt_cap);
+        ++rounds;
+#endif
         have += min((uint32_t)__popc(bal), need);
         a0 += 32;
         __syncwarp();
     }
-    if (have >= cnt) return;
+    if (have >= cnt) {
+        if (lane == 0) {
+            CSAW_STAT_ADD(0, used);
+            CSAW_STAT_ADD(1, cnt);
+            CSAW_STAT_ADD(2, 32u * rounds);
+        }
+        return;
+    }
+    const uint32_t have0 = have;
+    (void)have0;
     // Updated sampling for the remaining picks (attempts attempt_cap, ...).
     const uint32_t nwords = (d + 31) >> 5;
     uint64_t R = 0;
@@ -201,6 +237,11 @@ __device__ void draw_picks(const SelParams& p, const uint64_t* S, uint32_t* bits
             emit(p, q0 + have, v, inst, __ldg(p.col + beg + i));
             ++have;
         }
+        // every repeated attempt was consumed, then one draw per remaining pick
+        CSAW_STAT_ADD(0, p.attempt_cap + (cnt - have0));
+        CSAW_STAT_ADD(1, cnt);
+        CSAW_STAT_ADD(2, 32u * rounds + (cnt - have0));
+        CSAW_STAT_ADD(3, cnt - have0);
     }
     __syncwarp();
 }
@@ -428,6 +469,9 @@ __global__ void __launch_bounds__(SEL_THREADS) select_cdf_kernel(SelParams p)
         const DrawKey dk = draw_key(p, inst);
         const uint64_t T = cdf_at(row, IMPLICIT, d - 1);
         uint32_t have = 0, a0 = 0;
+        uint32_t used = 0, rounds = 0;   // counters (CSAW_STATS)
+        (void)used;
+        (void)rounds;
         while (have < cnt && a0 < p.attempt_cap) {
             const bool live = a0 + lane < p.attempt_cap;   // the last round may be partial
             const uint64_t x = scale_draw(philox_draw(dk.k0, dk.k1, a0 + lane, v, p.layer, dk.id), T);
@@ -454,9 +498,22 @@ __global__ void __launch_bounds__(SEL_THREADS) select_cdf_kernel(SelParams p)
                 picks[have + rank] = i;
                 emit(p, q0 + have + rank, v, inst, __ldg(p.col + beg + i));
             }
+#ifdef CSAW_STATS
+            used = (uint32_t)__popc(bal) >= need ? a0 + nth_set_bit(bal, need) + 1 : min(a0 + 32, p.attempt_cap);
+            ++rounds;
+#endif
             have += min((uint32_t)__popc(bal), need);
             a0 += 32;
             __syncwarp();
+        }
+        if (lane == 0) {
+            // draws consumed: to the last pick's attempt, or every repeated
+            // attempt and then one per updated-sampling pick
+            const uint32_t f = cnt - have;
+            CSAW_STAT_ADD(0, f ? p.attempt_cap + f : used);
+            CSAW_STAT_ADD(1, cnt);
+            CSAW_STAT_ADD(2, 32u * rounds + f);
+            CSAW_STAT_ADD(3, f);
         }
         if (have < cnt && lane == 0) {
             // Updated sampling (attempts attempt_cap, ...): picks sorted
@@ -589,6 +646,9 @@ __global__ void count_kernel(CountParams p)
             if (bw) basew = atomicAdd(p.n_items, (unsigned long long)__popc(bw));
             if (bc) basec = atomicAdd(p.n_items + 1, (unsigned long long)__popc(bc));
             if (bh) baseh = atomicAdd(p.n_items + 2, (unsigned long long)__popc(bh));
+            CSAW_STAT_ADD(4, __popc(bw));
+            CSAW_STAT_ADD(5, __popc(bc));
+            CSAW_STAT_ADD(6, __popc(bh));
         }
         basew = __shfl_sync(CSAW_FULL_MASK, basew, 0);
         basec = __shfl_sync(CSAW_FULL_MASK, basec, 0);
@@ -2384,18 +2444,10 @@ extern "C" csaw_status csaw_sample_oom(const uint64_t* row_offsets, const uint32
         if (d > 0xFFFFFFFFull) return fail(CSAW_ERR_INVALID, "row %u longer than 2^32-1", v);
         if (d > max_degree) max_degree = (uint32_t)d;
     }
-    for (uint64_t i = 0; i < n_edges; ++i)
-        if (cols[i] >= n_vertices) return fail(CSAW_ERR_INVALID, "column %llu out of range", (unsigned long long)i);
-    uint32_t max_weight = 1;
-    if (weighted)
-        for (uint64_t i = 0; i < n_edges; ++i) {
-            if (weights[i] == 0) return fail(CSAW_ERR_INVALID, "out-of-memory sampling needs positive weights");
-            if (weights[i] > max_weight) max_weight = weights[i];
-        }
-    if (eff_kind == CSAW_BIAS_NEIGHBOR_DEGREE)
-        for (uint64_t i = 0; i < n_edges; ++i)
-            if (row_offsets[cols[i] + 1] == row_offsets[cols[i]])
-                return fail(CSAW_ERR_INVALID, "neighbour-degree bias: an edge points at a vertex without neighbours");
+    // columns, weights and (neighbour degree) edge targets are checked on
+    // the device as each partition arrives; the largest weight only sizes
+    // the walk kernels' sums, which sampling does not use
+    const uint32_t max_weight = 0xFFFFFFFFu;
     if (inst_offsets[0] != 0) return fail(CSAW_ERR_INVALID, "inst_offsets must start at 0");
     for (uint32_t i = 0; i < n_instances; ++i)
         if (inst_offsets[i + 1] < inst_offsets[i]) return fail(CSAW_ERR_INVALID, "inst_offsets must be non-decreasing");
@@ -2472,12 +2524,14 @@ extern "C" csaw_status csaw_sample_oom(const uint64_t* row_offsets, const uint32
         uint32_t* d_deg = nullptr;
         uint32_t* d_vb = nullptr;
         unsigned long long* d_pc = nullptr;
+        uint32_t* d_chk = nullptr;
         void* d_seeds = nullptr;
         void* d_io = nullptr;
         st = get((void**)&d_off, sizeof(uint64_t) * ((uint64_t)n_vertices + 1));
         if (st == CSAW_OK) st = get((void**)&d_deg, sizeof(uint32_t) * n_vertices);
         if (st == CSAW_OK) st = get((void**)&d_vb, sizeof(uint32_t) * (np + 1));
         if (st == CSAW_OK) st = get((void**)&d_pc, sizeof(unsigned long long) * np);
+        if (st == CSAW_OK) st = get((void**)&d_chk, sizeof(uint32_t));
         if (st == CSAW_OK) st = get(&d_seeds, sizeof(uint32_t) * (n_seeds ? n_seeds : 1));
         if (st == CSAW_OK) st = get(&d_io, sizeof(uint64_t) * ((uint64_t)n_instances + 1));
         if (st != CSAW_OK) break;
@@ -2485,6 +2539,8 @@ extern "C" csaw_status csaw_sample_oom(const uint64_t* row_offsets, const uint32
         if (e == cudaSuccess) e = cudaMemcpyAsync(d_vb, vb.data(), sizeof(uint32_t) * (np + 1), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess && n_seeds) e = cudaMemcpyAsync(d_seeds, seeds, sizeof(uint32_t) * n_seeds, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(d_io, inst_offsets, sizeof(uint64_t) * ((uint64_t)n_instances + 1), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_chk, 0, sizeof(uint32_t), s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // before the copy stream uses them
         if (e != cudaSuccess) { st = cuda_fail(e, "copy inputs"); break; }
         degrees_kernel<<<grid_for(n_vertices, 256, view.sm_count), 256, 0, s>>>(d_off, n_vertices, d_deg);
         view.off = d_off;
@@ -2560,6 +2616,11 @@ extern "C" csaw_status csaw_sample_oom(const uint64_t* row_offsets, const uint32
                     ce = cudaMemcpyAsync(sl.col, cols + e0, sizeof(uint32_t) * ne, cudaMemcpyHostToDevice, cs);
                 if (ce == cudaSuccess && weighted && ne)
                     ce = cudaMemcpyAsync(sl.w, weights + e0, sizeof(uint32_t) * ne, cudaMemcpyHostToDevice, cs);
+                if (ce == cudaSuccess) {
+                    launch_partition_check(sl.col, weighted ? sl.w : nullptr, ne, n_vertices,
+                                           eff_kind == CSAW_BIAS_NEIGHBOR_DEGREE ? d_deg : nullptr, d_chk, cs);
+                    ce = cudaGetLastError();
+                }
                 if (ce == cudaSuccess) ce = cudaEventRecord(sl.loaded, cs);
                 if (ce != cudaSuccess) return cuda_fail(ce, "partition copy");
                 sl.part = q;
@@ -2608,9 +2669,18 @@ extern "C" csaw_status csaw_sample_oom(const uint64_t* row_offsets, const uint32
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(R->frontier_sizes.data(), P.fsize, sizeof(uint64_t) * ng, cudaMemcpyDeviceToHost, s);
         }
+        uint32_t chk = 0;
         if (e == cudaSuccess) e = cudaMemcpyAsync(&err_end, P.ctr + CT_ERR, sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&chk, d_chk, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) { st = cuda_fail(e, "out-of-memory sampling"); break; }
+        if (chk & 1u) { st = fail(CSAW_ERR_INVALID, "a column is not a vertex of the graph"); break; }
+        if (chk & 2u) { st = fail(CSAW_ERR_INVALID, "out-of-memory sampling needs positive weights"); break; }
+        if (chk & 4u) {
+            st = fail(CSAW_ERR_INVALID, "neighbour-degree bias: an edge points at a vertex without neighbours");
+            break;
+        }
         st = check_errors(err_end);
         if (st != CSAW_OK) break;
         uint64_t tot = 0;
@@ -2629,6 +2699,7 @@ extern "C" csaw_status csaw_sample_oom(const uint64_t* row_offsets, const uint32
         if (sl.loaded) cudaEventDestroy(sl.loaded);
         if (sl.freed) cudaEventDestroy(sl.freed);
     }
+    acc.pinned_bytes = (registered_col ? sizeof(uint32_t) * n_edges : 0) + (registered_w ? sizeof(uint32_t) * n_edges : 0);
     if (registered_col) cudaHostUnregister((void*)cols);
     if (registered_w) cudaHostUnregister((void*)weights);
     if (st != CSAW_OK) {
@@ -2723,6 +2794,25 @@ extern "C" csaw_status csaw_autotune_select(csaw_graph* g, const uint32_t* seeds
 
 // ---------------------------------------------------------------------------
 // Results returned by this library start with a tag naming their type.
+
+extern "C" csaw_status csaw_selection_stats(uint64_t counters[8], int reset)
+{
+    clear_error();
+    if (!counters) return fail(CSAW_ERR_INVALID, "counters is NULL");
+#ifdef CSAW_STATS
+    CSAW_CUDA(cudaDeviceSynchronize());
+    CSAW_CUDA(cudaMemcpyFromSymbol(counters, csaw::g_sel_stats, sizeof(uint64_t) * 8));
+    if (reset) {
+        const unsigned long long zero[8] = {};
+        CSAW_CUDA(cudaMemcpyToSymbol(csaw::g_sel_stats, zero, sizeof(zero)));
+    }
+    return CSAW_OK;
+#else
+    (void)reset;
+    for (int i = 0; i < 8; ++i) counters[i] = 0;
+    return fail(CSAW_ERR_INVALID, "this library was built without selection counters (CSAW_STATS)");
+#endif
+}
 
 extern "C" void csaw_result_free(void* result)
 {

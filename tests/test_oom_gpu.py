@@ -124,3 +124,28 @@ def test_oom_sampling_slots_pinning_and_errors(csaw):
     with pytest.raises(csaw.CsawError) as e:
         csaw.sample_oom(g.off, g.col, g.w, seeds, io, [5], "node2vec", 1, budget_bytes=big)
     assert e.value.status == csaw.ERR_INVALID
+
+
+def test_oom_bad_columns_are_refused(csaw):
+    """Columns are checked on the device as partitions arrive: a column that
+    is not a vertex fails the call (no walker is left outside every
+    partition, no kernel reads out of range)."""
+    g, seeds, io = _sample_cases()
+    col = g.col.copy()
+    col[len(col) // 2] = g.V + 5
+    big = 16 * int(np.diff(g.off).max()) + 1024
+    starts = inputs.uniform_vertices(3000, g.V, 1)
+    for slots in (1, 2):
+        with pytest.raises(csaw.CsawError) as e:
+            csaw.walk_oom(g.off, col, g.w, starts, 20, "edge_weight", 3, budget_bytes=big, slots=slots)
+        assert e.value.status == csaw.ERR_INVALID
+        with pytest.raises(csaw.CsawError) as e:
+            csaw.sample_oom(g.off, col, g.w, np.arange(g.V, dtype=np.uint32),
+                            np.array([0, g.V], dtype=np.uint64), [3], "edge_weight", 1, budget_bytes=big, slots=slots)
+        assert e.value.status == csaw.ERR_INVALID
+    # neighbour degree: an edge into a vertex without neighbours
+    gd = inputs.csr_from_edges(5, [(0, 1), (0, 2), (1, 0), (2, 3), (3, 4)])   # vertex 4 has no neighbours
+    with pytest.raises(csaw.CsawError) as e:
+        csaw.sample_oom(gd.off, gd.col, gd.w, np.array([0, 2], dtype=np.uint32), np.array([0, 2], dtype=np.uint64),
+                        [1], "neighbor_degree", 1, budget_bytes=1 << 20)
+    assert e.value.status == csaw.ERR_INVALID
