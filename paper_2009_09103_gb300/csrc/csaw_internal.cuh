@@ -133,6 +133,11 @@ csaw_status walk_batch(const csaw_graph* g, const csaw_bias* bias, const uint32_
 // degree 0 (when deg is given) flagged (bit 4).  The call then fails with
 // CSAW_ERR_INVALID; the replacements only keep the kernels in bounds.
 // Defined in csaw_oom.cu.
+// Page-locks a caller's host range for the duration of a call (read-only
+// registration where the device supports it, else ordinary); false if
+// refused, with the CUDA error cleared.  Defined in csaw_oom.cu.
+bool host_register(void* p, size_t bytes);
+
 void launch_partition_check(uint32_t* col, uint32_t* w, uint64_t ne, uint32_t V, const uint32_t* deg,
                             uint32_t* err, cudaStream_t s);
 

@@ -146,6 +146,15 @@ __global__ void partition_check_kernel(uint32_t* __restrict__ col, uint32_t* __r
     if ((threadIdx.x & 31) == 0 && flags) atomicOr(err, flags);
 }
 
+bool host_register(void* p, size_t bytes)
+{
+    if (cudaHostRegister(p, bytes, cudaHostRegisterReadOnly) == cudaSuccess) return true;
+    cudaGetLastError();
+    if (cudaHostRegister(p, bytes, cudaHostRegisterDefault) == cudaSuccess) return true;
+    cudaGetLastError();
+    return false;
+}
+
 void launch_partition_check(uint32_t* col, uint32_t* w, uint64_t ne, uint32_t V, const uint32_t* deg,
                             uint32_t* err, cudaStream_t s)
 {
@@ -274,9 +283,9 @@ extern "C" csaw_status csaw_walk_oom_ex(const uint64_t* row_offsets, const uint3
         if (registered_w) cudaHostUnregister((void*)weights);
     };
     if (opts && opts->pin_host && n_edges) {
-        registered_col = cudaHostRegister((void*)cols, sizeof(uint32_t) * n_edges, cudaHostRegisterReadOnly) == cudaSuccess;
+        registered_col = host_register((void*)cols, sizeof(uint32_t) * n_edges);
         if (weighted)
-            registered_w = cudaHostRegister((void*)weights, sizeof(uint32_t) * n_edges, cudaHostRegisterReadOnly) == cudaSuccess;
+            registered_w = host_register((void*)weights, sizeof(uint32_t) * n_edges);
         cudaGetLastError();   // a refused registration leaves ordinary (pageable) copies
     }
     csaw_status st = dalloc(&d_starts, sizeof(uint32_t) * n_walkers, s);

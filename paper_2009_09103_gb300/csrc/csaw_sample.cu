@@ -2500,11 +2500,9 @@ extern "C" csaw_status csaw_sample_oom(const uint64_t* row_offsets, const uint32
     do {
         // pinned (registered) host arrays let the copies run behind the selection
         if (opts && opts->pin_host && n_edges) {
-            registered_col = cudaHostRegister((void*)cols, sizeof(uint32_t) * n_edges,
-                                              cudaHostRegisterReadOnly) == cudaSuccess;
+            registered_col = host_register((void*)cols, sizeof(uint32_t) * n_edges);
             if (weighted)
-                registered_w = cudaHostRegister((void*)weights, sizeof(uint32_t) * n_edges,
-                                                cudaHostRegisterReadOnly) == cudaSuccess;
+                registered_w = host_register((void*)weights, sizeof(uint32_t) * n_edges);
             cudaGetLastError();   // a refused registration leaves ordinary (pageable) copies
         }
         cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);

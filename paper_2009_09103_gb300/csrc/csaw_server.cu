@@ -159,7 +159,6 @@ struct Lane {
 };
 
 constexpr uint64_t SMALL_BATCH_EDGES = 1ull << 18;   // at most this many sampled edges: high priority
-constexpr uint32_t WALK_WARP_BUDGET = 4;              // walkers (or 32-walker groups) per warp and block
 
 static csaw_status lane_pinned(Lane& L, size_t bytes)
 {
@@ -184,7 +183,10 @@ static inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 // Walk requests of one bias in one launch.  Inputs are packed in the staging
 // buffer as [segment starts u64 (R+1) | row offsets u64 (R) | lengths u32 (R)
 // | keys u32 (2R) | start vertices u32 (n)], copied in once; each request's
-// path matrix is copied straight into its result.
+// path matrix is copied straight into its result.  A batch of one runs the
+// walk kernels of csaw_walk; larger batches run their batched forms, with
+// persistent grids (short-lived blocks were measured slower: a block holds
+// its SM until its slowest walker is done).
 static csaw_status execute_walks(csaw_graph* g, Lane& L, std::vector<Request*>& batch)
 {
     const size_t R = batch.size();
@@ -234,9 +236,15 @@ static csaw_status execute_walks(csaw_graph* g, Lane& L, std::vector<Request*>& 
         seg.len = (const uint32_t*)(d + o_len);
         seg.key = (const uint32_t*)(d + o_key);
         seg.n = (uint32_t)R;
-        seg.warp_budget = WALK_WARP_BUDGET;
-        st = walk_batch(g, &batch[0]->bias, (const uint32_t*)(d + o_starts), n, seg, max_len, (uint32_t*)d_path,
-                        L.s);
+        seg.warp_budget = 0;
+        if (R == 1) {
+            const Request* rq = batch[0];
+            st = csaw_walk(g, (const uint32_t*)(d + o_starts), n, rq->length, &rq->bias, rq->rng_seed,
+                           (uint32_t*)d_path, CSAW_MEM_DEVICE, L.s);
+        } else {
+            st = walk_batch(g, &batch[0]->bias, (const uint32_t*)(d + o_starts), n, seg, max_len,
+                            (uint32_t*)d_path, L.s);
+        }
     }
     row = 0;
     for (size_t r = 0; st == CSAW_OK && r < R; ++r) {
@@ -641,7 +649,7 @@ extern "C" csaw_status csaw_submit(csaw_server* sv, const csaw_request* r, uint6
         sv->pending.push_back(rq);
         *ticket = rq->ticket;
     }
-    sv->cv_work.notify_all();
+    sv->cv_work.notify_one();   // one idle slot takes it (and whatever else waits)
     return CSAW_OK;
 }
 
