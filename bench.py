@@ -61,20 +61,25 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def traffic_record(kernel_src: str, workload: str):
-    """dram bytes per launch from the committed ncu summary, if it was taken
-    on the current source of the kernel's translation unit and this workload."""
+def traffic_records(kernel_src: str, workload: str):
+    """The committed ncu DRAM records of this workload's kernels in one
+    translation unit, if they were taken on its current source."""
     p = os.path.join(ROOT, "profiles", "roofline_traffic.json")
     if not os.path.exists(p):
-        return None
+        return []
     with open(p) as f:
         recs = json.load(f)
     src = open(os.path.join(ROOT, "paper_2009_09103_gb300", "csrc", kernel_src), "rb").read()
     sha = hashlib.sha256(src).hexdigest()[:16]
-    for r in recs:
-        if r.get("source") == kernel_src and r.get("source_sha") == sha and r.get("workload") == workload:
-            return r
-    return None
+    return [r for r in recs if r.get("source") == kernel_src and r.get("source_sha") == sha
+            and r.get("workload") == workload]
+
+
+def traffic_record(kernel_src: str, workload: str):
+    """dram bytes per launch from the committed ncu summary, if it was taken
+    on the current source of the kernel's translation unit and this workload."""
+    recs = traffic_records(kernel_src, workload)
+    return recs[0] if recs else None
 
 
 def roofline_block(kernel, tr, ms, alg_bytes, sector_bytes=None):
@@ -606,9 +611,17 @@ def batched_block(args):
            "streamed_cumulative_array": streamed, "cached_cumulative_array": cached,
            "selection_algorithmic_bytes_per_run": alg,
            "selection_algorithmic_gbs_streamed": alg / (streamed["batched_plan"]["ms_per_run"] / 1e3) / 1e9}
-    tr = traffic_record("csaw_sample.cu", "batched_s24")
-    if tr:
-        out["select_kernel_dram"] = tr
+    # the plan's kernels run inside one CUDA graph, so their DRAM rates come
+    # from the ncu record alone (bytes over ncu's serialised kernel time)
+    peak, peak_kind = measured_peaks()
+    kd = []
+    for r in traffic_records("csaw_sample.cu", "batched_s24"):
+        gbs = r["traffic_bytes_per_launch"] / (r["ncu_duration_ns"] / 1e9) / 1e9
+        kd.append({"kernel": r["kernel"], "dram_bytes_per_launch": r["traffic_bytes_per_launch"],
+                   "ncu_ms_per_launch": r["ncu_duration_ns"] / 1e6, "dram_gbs": round(gbs, 1),
+                   "frac_of_hbm_peak": round(gbs / peak, 4), "peak_gbs": peak, "peak_source": peak_kind})
+    if kd:
+        out["kernels_dram_streamed"] = kd
     if clk:
         out["clocks"] = clk
     return out

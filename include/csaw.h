@@ -520,6 +520,9 @@ csaw_status csaw_autotune_select(csaw_graph* g, const uint32_t* seeds, const uin
  * other waiting requests of the same kind and bias that fit the budget; their
  * instances (sampling) or walkers (walks) run as one multi-instance launch
  * (the batched multi-instance sampling of Sec. V-B) and finish together.
+ * Requests that can produce more than 2^18 sampled edges are large: at most
+ * one large batch runs at a time, and small batches run beside it on
+ * high-priority streams, so that neither waits behind the other's kernels.
  * Each request's draws depend only on its own arguments and seed, so its
  * result is bit-for-bit the one that csaw_sample / csaw_walk return for it
  * alone.  The paper has no serving layer: this runs its selection (Sec.

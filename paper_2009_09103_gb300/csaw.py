@@ -20,6 +20,9 @@ LIB_PATH = os.path.join(_PKG, "libcsaw.so")
 # (csaw_selection_stats); it must be set before the first call
 if os.environ.get("CSAW_LIB_VARIANT") == "stats":
     LIB_PATH = os.path.join(_PKG, "libcsaw_stats.so")
+# CSAW_LIB_PATH points the binding at another build of the library
+if os.environ.get("CSAW_LIB_PATH"):
+    LIB_PATH = os.environ["CSAW_LIB_PATH"]
 
 OK, ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_OVERFLOW, ERR_TIMEOUT, ERR_ABORTED, ERR_NOT_FOUND = range(8)
 MEM_HOST, MEM_DEVICE = 0, 1

@@ -430,7 +430,7 @@ __device__ __forceinline__ uint64_t cdf_at(const uint64_t* __restrict__ row, boo
 }
 
 template <bool IMPLICIT>
-__global__ void __launch_bounds__(SEL_THREADS) select_cdf_kernel(SelParams p)
+__global__ void __launch_bounds__(SEL_THREADS, 8) select_cdf_kernel(SelParams p)
 {
     __shared__ uint32_t s_picks[SEL_WARPS][PICK_MAX];
     if (p.key_dev) {
@@ -779,7 +779,7 @@ __device__ void hub_row_scan_warp(const HubBuildParams& p, uint64_t beg, uint32_
 // segment offsets added in warp order, as in cta_item), then every warp
 // takes the smaller hubs one at a time.  Work is claimed from two counters.
 template <int KIND>
-__global__ void __launch_bounds__(SEL_THREADS) hub_cdf_kernel(HubBuildParams p)
+__global__ void __launch_bounds__(SEL_THREADS, 8) hub_cdf_kernel(HubBuildParams p)
 {
     __shared__ uint64_t s_wsum[SEL_WARPS];
     __shared__ unsigned long long s_item;
@@ -1626,7 +1626,7 @@ static csaw_status enqueue_select_items(Pipeline& P, uint32_t l, cudaStream_t s)
             hp.big_list = P.hubBig; hp.n_big = (const unsigned long long*)P.lc(l, L_NBIG);
             hp.next = (unsigned long long*)P.lc(l, L_HNEXT); hp.S = P.hubS;
             hp.S_cap = P.hubS_cap; hp.err = (uint32_t*)(P.ctr + CT_ERR);
-            const int blocks = g->sm_count * 4;
+            const int blocks = g->sm_count * 8;
             if (P.kind == CSAW_BIAS_EDGE_WEIGHT) hub_cdf_kernel<CSAW_BIAS_EDGE_WEIGHT><<<blocks, SEL_THREADS, 0, s>>>(hp);
             else hub_cdf_kernel<CSAW_BIAS_NEIGHBOR_DEGREE><<<blocks, SEL_THREADS, 0, s>>>(hp);
             SelParams hs = sp;

@@ -48,6 +48,7 @@ struct Request {
     std::vector<uint32_t> starts;
     uint32_t length = 0;
     uint64_t estimate = 0;
+    bool large = false;            // more than SMALL_BATCH_EDGES sampled edges possible
     enum { PENDING, RUNNING, DONE } state = PENDING;
     csaw_result* result = nullptr;
 };
@@ -410,9 +411,7 @@ static uint64_t edge_bound(const Request* rq)
 // Runs a batch (one kind, one bias) on the slot; fills every request's result.
 static void execute(csaw_graph* g, Lane& L, std::vector<Request*>& batch)
 {
-    uint64_t edges = 0;
-    for (const Request* rq : batch) edges += edge_bound(rq);
-    L.s = edges <= SMALL_BATCH_EDGES ? L.hi : L.lo;
+    L.s = batch[0]->large ? L.lo : L.hi;
     const csaw_status st = batch[0]->kind == CSAW_REQ_WALK ? execute_walks(g, L, batch)
                                                             : execute_samples(g, L, batch);
     if (st != CSAW_OK)
@@ -444,18 +443,32 @@ struct csaw_server {
     uint64_t next_ticket = 1;
     uint64_t in_use = 0;
     uint32_t running = 0;
+    uint32_t large_running = 0;    // large batches running (at most one)
     bool stop = false;
     std::vector<std::thread> workers;
     std::vector<Lane> lanes;
 
-    // The oldest waiting request, then (up to max_batch in all) every other
-    // waiting request of the same kind and bias whose estimate still fits
-    // the budget, in arrival order.  Called with mu held.
+    // Two classes: large requests (more than SMALL_BATCH_EDGES sampled edges
+    // possible) run one batch at a time, so that each sees the GPU nearly to
+    // itself; small ones run beside them on the high-priority streams.  The
+    // oldest waiting request that may start now: one whose estimate fits the
+    // budget, and small or with no large batch running.  Called with mu held.
+    std::deque<Request*>::iterator startable()
+    {
+        for (auto it = pending.begin(); it != pending.end(); ++it)
+            if (in_use + (*it)->estimate <= budget && (!(*it)->large || large_running == 0)) return it;
+        return pending.end();
+    }
+
+    // That request, then (up to max_batch in all) every other waiting request
+    // of the same kind, bias and class whose estimate still fits the budget,
+    // in arrival order.  Called with mu held.
     void take_batch(std::vector<Request*>& batch)
     {
         batch.clear();
-        Request* head = pending.front();
-        pending.pop_front();
+        auto first = startable();
+        Request* head = *first;
+        pending.erase(first);
         batch.push_back(head);
         uint64_t est = head->estimate;
         uint64_t items = head->kind == CSAW_REQ_WALK ? head->starts.size() : head->n_instances;
@@ -463,7 +476,7 @@ struct csaw_server {
         for (auto it = pending.begin(); it != pending.end() && batch.size() < max_batch;) {
             Request* rq = *it;
             const uint64_t more = rq->kind == CSAW_REQ_WALK ? rq->starts.size() : rq->n_instances;
-            if (rq->kind == head->kind && same_bias(rq->bias, head->bias) &&
+            if (rq->kind == head->kind && same_bias(rq->bias, head->bias) && rq->large == head->large &&
                 in_use + est + rq->estimate <= budget && items + more < 0x7FFFFFFFull &&
                 seeds + rq->seeds.size() < 0x7FFFFFFFull) {
                 batch.push_back(rq);
@@ -485,11 +498,11 @@ struct csaw_server {
         std::vector<Request*> batch;
         std::unique_lock<std::mutex> lk(mu);
         while (true) {
-            cv_work.wait(lk, [&] {
-                return stop || (!pending.empty() && in_use + pending.front()->estimate <= budget);
-            });
+            cv_work.wait(lk, [&] { return stop || startable() != pending.end(); });
             if (stop) break;   // pending requests are aborted by destroy
             take_batch(batch);
+            const bool large = batch[0]->large;
+            if (large) ++large_running;
             const int64_t t_admit = now_ns();
             for (Request* rq : batch) {
                 in_use += rq->estimate;
@@ -509,6 +522,7 @@ struct csaw_server {
                 --running;
                 rq->state = Request::DONE;
             }
+            if (large) --large_running;
             cv_done.notify_all();
             cv_work.notify_all();
         }
@@ -628,6 +642,7 @@ extern "C" csaw_status csaw_submit(csaw_server* sv, const csaw_request* r, uint6
     }
     if (st != CSAW_OK) { delete rq; return st; }
     rq->estimate = estimate_bytes(sv->g, sv->degrees, *rq);
+    rq->large = edge_bound(rq) > SMALL_BATCH_EDGES;
     if (rq->estimate > sv->budget) {
         const uint64_t est = rq->estimate;
         delete rq;

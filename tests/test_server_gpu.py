@@ -73,14 +73,34 @@ def test_results_same_alone_and_in_the_mix(env):
 
 def test_requests_overlap_on_the_device(env):
     csaw, g, G = env
-    srv = csaw.Server(G, budget_bytes=4 << 30, slots=4)
-    starts = inputs.uniform_vertices(1 << 15, g.V, 3)
+    srv = csaw.Server(G, budget_bytes=4 << 30, slots=4, max_batch=1)
+    starts = inputs.uniform_vertices(3000, g.V, 3)   # 3000 x 80 steps: small requests
     ts = [srv.submit_walk(starts, 80, "edge_weight", k) for k in range(8)]
     res = [srv.poll(t) for t in ts]
     srv.close()
     # some request started before another finished: slots run concurrently
     spans = sorted((r.t_start_ns, r.t_finish_ns) for r in res)
     assert any(spans[i + 1][0] < spans[i][1] for i in range(len(spans) - 1))
+
+
+def test_large_requests_run_one_batch_at_a_time(env):
+    """Requests that can produce more than 2^18 sampled edges run one batch
+    at a time; small ones still start while a large one runs."""
+    csaw, g, G = env
+    srv = csaw.Server(G, budget_bytes=8 << 30, slots=4, max_batch=1)
+    big = inputs.uniform_vertices(1 << 15, g.V, 4)          # 32768 x 80 steps: large
+    small = inputs.uniform_vertices(500, g.V, 5)            # 500 x 20 steps: small
+    tb = [srv.submit_walk(big, 80, "edge_weight", k) for k in range(4)]
+    ts = [srv.submit_walk(small, 20, "edge_weight", 10 + k) for k in range(4)]
+    rb = [srv.poll(t) for t in tb]
+    rs = [srv.poll(t) for t in ts]
+    srv.close()
+    spans = sorted((r.t_start_ns, r.t_finish_ns) for r in rb)
+    assert all(spans[i + 1][0] >= spans[i][1] for i in range(len(spans) - 1))
+    # the small requests did not wait for all the large ones
+    assert min(r.t_finish_ns for r in rs) < max(r.t_finish_ns for r in rb)
+    for k, r in enumerate(rs):
+        assert np.array_equal(r.path, oracle.walk(g, small, 20, "edge_weight", 10 + k))
 
 
 def test_admission_by_budget(env):
