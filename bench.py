@@ -222,18 +222,21 @@ def node2vec_bytes(torch, off_t, path):
 
 
 def cached_walk_bytes(torch, off_t, path, length):
-    """Algorithmic bytes of one walk launch over the cached cumulative array:
-    per step 16 (row offsets) + 8 (row total) + 8 per binary-search probe
-    (ceil(log2 d) probes) + 4 (picked column) + 4 (path entry); per walker 4
-    (start) and 4 * (L + 1) (its path row)."""
+    """Algorithmic bytes of one walk launch over the cumulative array and its
+    summary: per step 16 (row offsets) + 8 (row total) + 8 per summary probe
+    (ceil(log2(G + 1)) probes over the row's G = (end-1)/8 - beg/8 summary
+    entries) + 32 (one half of the 8-entry group) + 4 (picked column) + 4
+    (path entry); per walker 4 (start) and 4 * (L + 1) (its path row)."""
     p = path.to(torch.int64) & 0xFFFFFFFF
     a, b = p[:, :-1], p[:, 1:]
     real = b != 0xFFFFFFFF
     n_trans = int(real.sum())
-    deg = (off_t[1:] - off_t[:-1])[a[real]].to(torch.float64)
-    probes = int(torch.ceil(torch.log2(deg.clamp(min=1))).sum())
+    av = a[real]
+    beg, end = off_t[av], off_t[av + 1]
+    G = ((end - 1) >> 3) - (beg >> 3)
+    probes = int(torch.ceil(torch.log2((G + 1).to(torch.float64))).sum())
     n = path.shape[0]
-    return 16 * n_trans + 8 * n_trans + 8 * probes + 8 * n_trans + 4 * n + 4 * n * (length + 1)
+    return (16 + 8 + 32 + 4 + 4) * n_trans + 8 * probes + 4 * n + 4 * n * (length + 1)
 
 
 def walk_workload(args):
@@ -258,6 +261,35 @@ def walk_config(args, wl):
             f"{g.V:,} walkers (one per vertex), length {wl.length}, edge-weight bias")
 
 
+def walk_mode(args, wl):
+    """How the main line's walk gets its cumulative bias arrays: "build" (a
+    static bias: the call builds the array over all rows, then every step is a
+    search of it -- the array's construction is inside every timed step),
+    "cached" (--cdf: built once per graph, before timing) or "streaming"
+    (--streaming, or node2vec's dynamic bias: every step streams its row)."""
+    if args.cdf:
+        return "cached"
+    if args.streaming or wl.bias == "node2vec":
+        return "streaming"
+    return "build"
+
+
+def time_steps(torch, fn, steps, warmup, stream, flush):
+    """CUDA-event times (ms) of `steps` calls of fn on `stream` after
+    `warmup` untimed ones, with L2 flushed before each."""
+    for _ in range(warmup):
+        fn()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for i in range(steps):
+        flush.fill_(i)
+        evs[i][0].record(stream)
+        fn()
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
 def run_walk_bench(args, rank, world):
     import torch
     from paper_2009_09103_gb300 import build, csaw, inputs
@@ -268,9 +300,10 @@ def run_walk_bench(args, rank, world):
     t0 = time.time()
     wl = walk_workload(args)
     g = wl.graph
-    log(f"[bench] {args.workload} graph: V={g.V} E={g.E} built in {time.time() - t0:.1f}s")
+    mode = walk_mode(args, wl)
+    log(f"[bench] {args.workload} graph: V={g.V} E={g.E} built in {time.time() - t0:.1f}s; mode {mode}")
     G = csaw.Graph(g.off, g.col, g.w)
-    if args.cdf:
+    if mode == "cached":
         # node2vec reads the edge weights' cumulative array (intersection path)
         G.build_cdf("edge_weight" if wl.bias == "node2vec" else wl.bias)
     stream = torch.cuda.current_stream()
@@ -279,9 +312,10 @@ def run_walk_bench(args, rank, world):
     path = torch.empty((n, wl.length + 1), dtype=torch.int32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     seed = wl.rng_seed + rank  # replicas: independent walks per rank
+    per_call = mode == "build"
 
     def step():
-        csaw.walk(G, starts, wl.length, wl.bias, seed, wl.n2v_mult, path=path, stream=stream)
+        csaw.walk(G, starts, wl.length, wl.bias, seed, wl.n2v_mult, path=path, stream=stream, build_cdf=per_call)
 
     for _ in range(args.warmup):
         step()
@@ -321,25 +355,66 @@ def run_walk_bench(args, rank, world):
     h_path = torch.empty((n, wl.length + 1), dtype=torch.int32, pin_memory=True)
     hs = h_starts.numpy().view(np.uint32)
     hp = h_path.numpy().view(np.uint32)
-    csaw.walk(G, hs, wl.length, wl.bias, seed, wl.n2v_mult, path=hp, stream=stream)   # warm
+
+    def e2e_call():
+        csaw.walk(G, hs, wl.length, wl.bias, seed, wl.n2v_mult, path=hp, stream=stream, build_cdf=per_call)
+
+    e2e_call()   # warm
     e2e_steps = max(1, min(args.steps, 5))
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     for _ in range(e2e_steps):
-        csaw.walk(G, hs, wl.length, wl.bias, seed, wl.n2v_mult, path=hp, stream=stream)
+        e2e_call()
     e2e_s = (time.perf_counter() - t1) / e2e_steps
     e2e_ok = bool(np.array_equal(hp, path.cpu().numpy().view(np.uint32)))
     e2e = {"value": n_trans * world / e2e_s, "unit": "edges/s",
            "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * n * (wl.length + 1),
            "matches_device_run": e2e_ok}
 
-    tr = traffic_record("csaw_walk.cu", f"{args.workload}_s{args.scale}" + ("_cdf" if args.cdf else ""))
-    kname = "walk_kernel<NODE2VEC>" if wl.bias == "node2vec" else "walk_kernel<EDGE_WEIGHT>"
-    if args.cdf and wl.bias != "node2vec":
-        kname = "walk_cached_kernel<EDGE_WEIGHT>"
-        alg_bytes = cached_walk_bytes(torch, off_t, path, wl.length)
-    roofline = roofline_block(kname, tr, ms_per_step, alg_bytes,
-                              sector_bytes if (sector_bytes is not None and not args.cdf) else None)
+    wl_name = f"{args.workload}_s{args.scale}"
+    kernels = {}
+    if mode == "streaming":
+        kname = "walk_kernel<NODE2VEC>" if wl.bias == "node2vec" else "walk_kernel<EDGE_WEIGHT>"
+        roofline = roofline_block(kname, traffic_record("csaw_walk.cu", wl_name), ms_per_step, alg_bytes,
+                                  sector_bytes)
+    elif wl.bias == "node2vec":
+        roofline = roofline_block("walk_kernel<NODE2VEC>", traffic_record("csaw_walk.cu", wl_name + "_cdf"),
+                                  ms_per_step, alg_bytes)
+    else:
+        # the dominant kernel of the step is the walk over the array: timed
+        # alone over the graph's cached copy (identical paths), the rest of
+        # the step is the array's construction
+        cb = cached_walk_bytes(torch, off_t, path, wl.length)
+        ms_walk = ms_per_step
+        if mode == "build":
+            G.build_cdf(wl.bias)
+            path2 = torch.empty_like(path)
+            t_w = time_steps(torch, lambda: csaw.walk(G, starts, wl.length, wl.bias, seed, wl.n2v_mult,
+                                                      path=path2, stream=stream),
+                             args.steps, args.warmup, stream, flush)
+            ms_walk = sum(t_w) / len(t_w)
+            same = bool(torch.equal(path, path2))
+            G.drop_cdf(wl.bias)
+            ms_build = ms_per_step - ms_walk
+            kernels = {"walk_cached_kernel_ms": ms_walk,
+                       "cumulative_array_build_ms": ms_build,
+                       "build_basis": "step time minus the walk kernel timed alone over a prebuilt array",
+                       "build_algorithmic_bytes": 13 * g.E + 8 * (g.V + 1),
+                       "identical_paths_prebuilt_array": same}
+            recs = traffic_records("csaw_graph.cu", wl_name + "_build")
+            if recs and ms_build > 0:
+                peak, peak_kind = measured_peaks()
+                dram = sum(r["traffic_bytes_per_launch"] for r in recs)
+                kernels["build_dram_bytes"] = dram
+                kernels["build_dram_gbs"] = round(dram / (ms_build / 1e3) / 1e9, 1)
+                kernels["build_dram_frac"] = round(dram / (ms_build / 1e3) / 1e9 / peak, 4)
+                kernels["build_kernels"] = sorted(r["kernel"] for r in recs)
+        roofline = roofline_block("walk_cached_kernel<EDGE_WEIGHT>", traffic_record("csaw_walk.cu", wl_name + "_cdf"),
+                                  ms_walk, cb)
+    cum = {"build": "built over all rows inside every step (segmented scan over edge tiles, then each step a "
+                    "search of its summary and one or two 32-byte sectors)",
+           "cached": "cached per edge (built once per graph, before timing)",
+           "streaming": "computed per step (streamed over the row)"}[mode]
     result = {
         "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -348,47 +423,30 @@ def run_walk_bench(args, rank, world):
         "config": {"workload": walk_config(args, wl),
                    "parallelism": "replicas" if world > 1 else "1 GPU",
                    "l2": "flushed (512 MiB write) before every timed step",
-                   "cumulative_array": "cached per edge (built once per graph)" if args.cdf
-                   else "computed per step (streamed over the row)",
+                   "cumulative_array": cum,
                    "sampled_edges_per_step": n_trans},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * (4 if mode == "build" else 1),
         "roofline": roofline,
         "e2e": e2e,
     }
+    if kernels:
+        result["kernels"] = kernels
     if clk:
         result["clocks"] = clk
-    if not args.cdf and wl.bias != "node2vec" and not args.no_variant:
-        # The same walks over the cached per-edge cumulative array (built once
-        # per graph): identical paths, a binary search per step instead of a
-        # pass over the row.  Reported beside the per-step path, timed the same way.
-        t_b = time.perf_counter()
-        G.build_cdf(wl.bias)
-        build_ms = (time.perf_counter() - t_b) * 1e3
-        path2 = torch.empty_like(path)
-        def step2():
-            csaw.walk(G, starts, wl.length, wl.bias, seed, wl.n2v_mult, path=path2, stream=stream)
-        for _ in range(args.warmup):
-            step2()
-        ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.steps)]
-        torch.cuda.synchronize()
-        for i in range(args.steps):
-            flush.fill_(i)
-            ev2[i][0].record(stream)
-            step2()
-            ev2[i][1].record(stream)
-        torch.cuda.synchronize()
-        ms2 = sum(a.elapsed_time(b) for a, b in ev2) / args.steps
-        same = bool(torch.equal(path, path2))
-        result["variant_cached_cumulative_array"] = {
-            "value": n_trans * world / (ms2 / 1e3), "unit": "edges/s", "ms_per_step": ms2,
-            "kernel": "walk_cached_kernel", "build_ms_once_per_graph": build_ms,
-            "extra_device_bytes": 8 * (g.E + 16), "identical_paths": same,
-            "roofline": roofline_block("walk_cached_kernel<EDGE_WEIGHT>",
-                                       traffic_record("csaw_walk.cu", f"walk_s{args.scale}_cdf"), ms2,
-                                       cached_walk_bytes(torch, off_t, path2, wl.length))}
-        G.drop_cdf(wl.bias)
-        result["gpu_launches_variant"] = args.steps
+    if mode == "build" and not args.no_variant:
+        # The per-visit streaming walk (each step streams its row's biases):
+        # the same paths, timed the same way.
+        path3 = torch.empty_like(path)
+        t_s = time_steps(torch, lambda: csaw.walk(G, starts, wl.length, wl.bias, seed, wl.n2v_mult,
+                                                  path=path3, stream=stream),
+                         args.steps, args.warmup, stream, flush)
+        ms3 = sum(t_s) / len(t_s)
+        result["streaming_per_visit"] = {
+            "value": n_trans * world / (ms3 / 1e3), "unit": "edges/s", "ms_per_step": ms3,
+            "kernel": "walk_kernel", "identical_paths": bool(torch.equal(path, path3)),
+            "roofline": roofline_block("walk_kernel<EDGE_WEIGHT>", traffic_record("csaw_walk.cu", wl_name), ms3,
+                                       alg_bytes, sector_bytes)}
+        result["gpu_launches_streaming"] = args.steps
     G.close()
     return result, (g, wl, n_trans)
 
@@ -1177,7 +1235,9 @@ def main():
                              "attempts"])
     ap.add_argument("--autotune", action="store_true", help="sampling workloads: autotune first")
     ap.add_argument("--no-variant", action="store_true",
-                    help="walks: skip the cached-array variant measured after the main line")
+                    help="walks: skip the per-visit streaming walk measured after the main line")
+    ap.add_argument("--streaming", action="store_true",
+                    help="walks: the main line streams each step's row (no cumulative array)")
     ap.add_argument("--cdf", action="store_true",
                     help="build the cached per-edge cumulative array of the static bias first")
     ap.add_argument("--plain-instances", type=int, default=4096,

@@ -130,7 +130,8 @@ csaw_status csaw_graph_get_info(const csaw_graph* g, csaw_graph_info* out);
 /* Build the cached cumulative bias array of a static bias kind
  * (CSAW_BIAS_EDGE_WEIGHT or CSAW_BIAS_NEIGHBOR_DEGREE): per edge e of row v,
  * the inclusive uint64 prefix sum of the row's biases up to e -- the CTPS of
- * Sec. II-B computed once instead of at every selection (8 bytes per edge).
+ * Sec. II-B computed once instead of at every selection -- and a summary of
+ * every 8th sum (9 bytes per edge in all).
  * Afterwards csaw_walk, csaw_sample and plans created later use it for that
  * kind: a walk step or a draw is a binary search (O(log d)) instead of a pass
  * over the row.  Picks are identical (same prefix sums, same draws).  Graphs
@@ -196,8 +197,15 @@ csaw_status csaw_walk(csaw_graph* g, const uint32_t* starts, uint64_t n_walkers,
  * with no neighbour of positive bias teleports the same way instead of
  * stopping.  After a teleport a node2vec walk has no previous vertex (its
  * next step uses the weights alone).  Teleporting walks always stream the
- * biases (a cached cumulative array is not used).  Errors: those of
- * csaw_walk, and CSAW_ERR_INVALID for an unknown teleport mode. */
+ * biases (a cached cumulative array is not used).
+ * build_cdf = 1 (no teleport, static bias whose biases are all positive, no
+ * cached array of the kind on g): the call first builds the cumulative array
+ * of the kind over the whole graph, as csaw_graph_build_cdf does, into a
+ * temporary of 9 bytes per edge (stream-ordered, freed by the call), and
+ * every step is then a search of it instead of a pass over the row: the
+ * same paths, with the array's construction inside the call.  Ignored
+ * otherwise.  Errors: those of csaw_walk, and CSAW_ERR_INVALID for an
+ * unknown teleport mode. */
 #define CSAW_TELEPORT_NONE 0
 #define CSAW_TELEPORT_RESTART 1
 #define CSAW_TELEPORT_JUMP 2
@@ -205,6 +213,7 @@ csaw_status csaw_walk(csaw_graph* g, const uint32_t* starts, uint64_t n_walkers,
 typedef struct {
     int32_t teleport;        /* CSAW_TELEPORT_* */
     uint32_t teleport_q32;   /* teleport probability per step, in units of 2^-32 */
+    uint32_t build_cdf;      /* 1: see below */
 } csaw_walk_opts;
 
 csaw_status csaw_walk_ex(csaw_graph* g, const uint32_t* starts, uint64_t n_walkers, uint32_t length,
@@ -520,9 +529,11 @@ csaw_status csaw_autotune_select(csaw_graph* g, const uint32_t* seeds, const uin
  * other waiting requests of the same kind and bias that fit the budget; their
  * instances (sampling) or walkers (walks) run as one multi-instance launch
  * (the batched multi-instance sampling of Sec. V-B) and finish together.
- * Requests that can produce more than 2^18 sampled edges are large: at most
- * one large batch runs at a time, and small batches run beside it on
- * high-priority streams, so that neither waits behind the other's kernels.
+ * Batches that can produce more than 2^18 sampled edges run on low-priority
+ * streams and smaller ones on high-priority streams, so that a small batch's
+ * blocks are scheduled ahead of the waiting blocks of large ones; a batch
+ * holds only its own stream while it runs (its device memory is freed
+ * stream-ordered, without waiting for other slots' kernels).
  * Each request's draws depend only on its own arguments and seed, so its
  * result is bit-for-bit the one that csaw_sample / csaw_walk return for it
  * alone.  The paper has no serving layer: this runs its selection (Sec.

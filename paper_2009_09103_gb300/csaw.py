@@ -45,7 +45,7 @@ class Bias(ctypes.Structure):
 
 
 class WalkOpts(ctypes.Structure):
-    _fields_ = [("teleport", ctypes.c_int32), ("teleport_q32", ctypes.c_uint32)]
+    _fields_ = [("teleport", ctypes.c_int32), ("teleport_q32", ctypes.c_uint32), ("build_cdf", ctypes.c_uint32)]
 
 
 TELEPORT = {None: 0, "restart": 1, "jump": 2}
@@ -326,15 +326,19 @@ class Graph:
 
 
 def walk(g: Graph, starts, length: int, bias="edge_weight", seed: int = 0, mult=(1, 1, 1),
-         path=None, stream=None, teleport=None, teleport_q32: int = 0):
+         path=None, stream=None, teleport=None, teleport_q32: int = 0, build_cdf: bool = False):
     """csaw_walk (csaw_walk_ex with teleport = "restart" or "jump" and a
-    per-step probability teleport_q32 / 2^32).  Device call when `starts` is
-    a torch CUDA tensor (returns a torch int32 tensor [n, length+1] holding
-    uint32 vertex ids, asynchronous on `stream`); host call when `starts` is
-    a numpy array (returns numpy uint32)."""
+    per-step probability teleport_q32 / 2^32, or with build_cdf: the call
+    builds the kind's cumulative array for itself and walks over it).
+    Device call when `starts` is a torch CUDA tensor (returns a torch int32
+    tensor [n, length+1] holding uint32 vertex ids, asynchronous on
+    `stream`); host call when `starts` is a numpy array (returns numpy
+    uint32)."""
     L = lib()
     b = make_bias(bias, mult) if isinstance(bias, str) else bias
-    opts = WalkOpts(TELEPORT[teleport], teleport_q32) if teleport is not None else None
+    opts = None
+    if teleport is not None or build_cdf:
+        opts = WalkOpts(TELEPORT[teleport], teleport_q32, 1 if build_cdf else 0)
 
     def call(sp, pp, mem, st):
         if opts is None:

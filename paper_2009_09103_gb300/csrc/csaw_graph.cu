@@ -338,10 +338,21 @@ extern "C" csaw_status csaw_graph_get_info(const csaw_graph* g, csaw_graph_info*
 
 // ---------------------------------------------------------------------------
 // Cached cumulative bias arrays (the CTPS of Sec. II-B kept per edge for a
-// static bias).  One warp per row in rounds of 512 neighbours: each lane takes
-// four aligned groups of four, forms their inclusive sums, and a warp scan of
-// the lane totals gives every lane its offset; groups are written as two
-// 16-byte stores (partial groups at the row ends element by element).
+// static bias).  The array over all rows is one segmented inclusive scan of
+// the edge biases, segments being the rows, so the work is split by edges,
+// not rows: tiles of CB_TILE consecutive edges, CB_ITEMS per thread, each
+// thread reading its biases as two 16-byte loads.  Three launches, none of
+// which waits on another block:
+//   cdf_tile_sum_kernel   each tile's segmented total (whether a row starts
+//                         in it; the sum since its last row start)
+//   cdf_tile_carry_kernel one block: the running row sum entering each tile
+//   cdf_tile_scan_kernel  the tile's scan with that carry, written as 16-byte
+//                         stores, and the summary entries of its groups.
+// Row starts inside a tile come from the row offsets (two binary searches
+// for the rows holding its first and last edge, then one bit per row start
+// in shared memory).  The summary holds every 8th prefix sum (S[g] =
+// cdf[8g + 7]): a walk bisects it first and then reads one or two 32-byte
+// sectors of the array.
 
 namespace csaw {
 
@@ -353,60 +364,260 @@ bool cached_cdf_usable(const csaw_graph* g, int kind)
     return false;
 }
 
-template <int KIND>
-__global__ void build_cdf_kernel(const uint64_t* __restrict__ off, const uint32_t* __restrict__ col,
-                                 const uint32_t* __restrict__ w, const uint32_t* __restrict__ deg,
-                                 uint32_t V, uint64_t* __restrict__ cdf, unsigned long long* next_row)
+bool cdf_kind_positive(const csaw_graph* g, int kind)
 {
-    const int lane = threadIdx.x & 31;
-    while (true) {
-        unsigned long long v = 0;
-        if (lane == 0) v = atomicAdd(next_row, 1ull);
-        v = __shfl_sync(CSAW_FULL_MASK, v, 0);
-        if (v >= V) break;
-        const uint64_t beg = off[v], end = off[v + 1];
-        if (beg == end) continue;
-        const uint64_t abeg = beg & ~3ull;
-        uint64_t carry = 0;
-        for (uint64_t base = abeg; base < end; base += 512) {
+    if (kind == CSAW_BIAS_EDGE_WEIGHT) return g->w != nullptr && g->min_weight > 0;
+    if (kind == CSAW_BIAS_NEIGHBOR_DEGREE) return !g->zero_degree_target;
+    return false;
+}
+
+uint64_t cdf_words(uint64_t E) { return E + CSAW_EDGE_PAD + (E + 7) / 8 + 8; }
+
+constexpr int CB_THREADS = 256;
+constexpr int CB_ITEMS = 8;
+constexpr uint32_t CB_TILE = CB_THREADS * CB_ITEMS;   // 2048 edges per tile
+constexpr int CB_CARRY_THREADS = 1024;
+
+// A segmented sum: f = some row starts in the span, s = the sum of the
+// biases after its last row start (the whole span's if none starts in it).
+struct SegSum {
+    uint32_t f;
+    uint64_t s;
+};
+
+__device__ __forceinline__ SegSum seg_join(SegSum a, SegSum b)
+{
+    return SegSum{a.f | b.f, b.f ? b.s : a.s + b.s};
+}
+
+__device__ __forceinline__ SegSum warp_inclusive_seg(SegSum x, int lane)
+{
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const uint64_t g0 = base + 128ull * u + 4ull * lane;
-                uint32_t b[4] = {0u, 0u, 0u, 0u};
-                if (g0 < end) {
-                    if constexpr (KIND == CSAW_BIAS_EDGE_WEIGHT) {
-                        const uint4 q = __ldg(reinterpret_cast<const uint4*>(w + g0));
-                        b[0] = q.x; b[1] = q.y; b[2] = q.z; b[3] = q.w;
-                    } else {
-                        const uint4 q = __ldg(reinterpret_cast<const uint4*>(col + g0));
-                        b[0] = __ldg(deg + q.x);
-                        b[1] = q.y < V ? __ldg(deg + q.y) : 0u;
-                        b[2] = q.z < V ? __ldg(deg + q.z) : 0u;
-                        b[3] = q.w < V ? __ldg(deg + q.w) : 0u;
-                    }
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        if (g0 + j < beg || g0 + j >= end) b[j] = 0u;
-                }
-                const uint64_t i0 = b[0], i1 = i0 + b[1], i2 = i1 + b[2], i3 = i2 + b[3];
-                const uint64_t incl = warp_inclusive_scan_u64(i3, lane);
-                const uint64_t off0 = carry + incl - i3;
-                if (g0 < end) {
-                    const uint64_t e[4] = {off0 + i0, off0 + i1, off0 + i2, off0 + i3};
-                    if (g0 >= beg && g0 + 4 <= end) {
-                        ulonglong2* dst = reinterpret_cast<ulonglong2*>(cdf + g0);
-                        dst[0] = make_ulonglong2(e[0], e[1]);
-                        dst[1] = make_ulonglong2(e[2], e[3]);
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            if (g0 + j >= beg && g0 + j < end) cdf[g0 + j] = e[j];
-                    }
-                }
-                carry += __shfl_sync(CSAW_FULL_MASK, incl, 31);
-            }
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t yf = __shfl_up_sync(CSAW_FULL_MASK, x.f, o);
+        const uint64_t ys = __shfl_up_sync(CSAW_FULL_MASK, x.s, o);
+        if (lane >= o) {
+            if (!x.f) x.s += ys;
+            x.f |= yf;
         }
     }
+    return x;
+}
+
+// Smallest v in [1, V] with off[v] > p (p < off[V]).
+__device__ __forceinline__ uint32_t row_upper(const uint64_t* __restrict__ off, uint32_t V, uint64_t p)
+{
+    uint32_t lo = 0, hi = V;
+    while (lo < hi) {
+        const uint32_t mid = lo + ((hi - lo) >> 1);
+        if (__ldg(off + mid) > p) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+// Per-thread state of one tile: the thread's biases, its row-start bits and
+// its own segmented sums.
+template <int KIND>
+struct CdfTile {
+    uint32_t b[CB_ITEMS];
+    uint32_t starts;   // bit j: a row starts at the thread's j-th edge
+    uint64_t pb;       // the thread's first edge
+
+    __device__ void load(const uint64_t* __restrict__ off, const uint32_t* __restrict__ col,
+                         const uint32_t* __restrict__ w, const uint32_t* __restrict__ deg, uint32_t V,
+                         uint64_t E, uint64_t p0, uint32_t* s_bits, uint32_t* s_rows)
+    {
+        const int tid = threadIdx.x;
+        const uint64_t p1 = p0 + CB_TILE < E ? p0 + CB_TILE : E;
+        for (int i = tid; i < (int)(CB_TILE / 32); i += CB_THREADS) s_bits[i] = 0;
+        if (tid == 0) s_rows[0] = row_upper(off, V, p0) - 1;        // the row holding p0
+        if (tid == 32) s_rows[1] = row_upper(off, V, p1 - 1) - 1;   // the row holding p1 - 1
+        __syncthreads();
+        const uint32_t r0 = s_rows[0], r1 = s_rows[1];
+        if (tid == 0 && __ldg(off + r0) == p0) atomicOr(s_bits, 1u);
+        // rows r0+1 .. r1 start strictly inside the tile (empty rows share
+        // the start of the next row that has edges)
+        for (uint64_t r = (uint64_t)r0 + 1 + tid; r <= r1; r += CB_THREADS) {
+            const uint32_t q = (uint32_t)(__ldg(off + r) - p0);
+            atomicOr(s_bits + (q >> 5), 1u << (q & 31));
+        }
+        pb = p0 + (uint64_t)CB_ITEMS * tid;
+        if (pb + CB_ITEMS <= E) {
+            if constexpr (KIND == CSAW_BIAS_EDGE_WEIGHT) {
+                const uint4 u0 = __ldg(reinterpret_cast<const uint4*>(w + pb));
+                const uint4 u1 = __ldg(reinterpret_cast<const uint4*>(w + pb) + 1);
+                b[0] = u0.x; b[1] = u0.y; b[2] = u0.z; b[3] = u0.w;
+                b[4] = u1.x; b[5] = u1.y; b[6] = u1.z; b[7] = u1.w;
+            } else {
+                const uint4 u0 = __ldg(reinterpret_cast<const uint4*>(col + pb));
+                const uint4 u1 = __ldg(reinterpret_cast<const uint4*>(col + pb) + 1);
+                const uint32_t c[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+#pragma unroll
+                for (int j = 0; j < CB_ITEMS; ++j) b[j] = __ldg(deg + c[j]);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < CB_ITEMS; ++j) {
+                b[j] = 0u;
+                if (pb + j < E) {
+                    if constexpr (KIND == CSAW_BIAS_EDGE_WEIGHT) b[j] = __ldg(w + pb + j);
+                    else b[j] = __ldg(deg + __ldg(col + pb + j));
+                }
+            }
+        }
+        __syncthreads();
+        starts = (s_bits[(CB_ITEMS * tid) >> 5] >> ((CB_ITEMS * tid) & 31)) & 0xFFu;
+    }
+
+    // The thread's own segmented total.
+    __device__ SegSum total() const
+    {
+        uint64_t run = 0;
+#pragma unroll
+        for (int j = 0; j < CB_ITEMS; ++j) {
+            if ((starts >> j) & 1u) run = 0;
+            run += b[j];
+        }
+        return SegSum{starts != 0u, run};
+    }
+};
+
+// Block-wide exclusive segmented scan of the threads' totals (thread order);
+// the tile's total goes to *tile_total (every thread gets it).
+__device__ __forceinline__ SegSum block_exclusive_seg(SegSum mine, SegSum* s_warp, SegSum* tile_total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const SegSum incl = warp_inclusive_seg(mine, lane);
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    SegSum before{0u, 0ull};
+    for (int k = 0; k < wid; ++k) before = seg_join(before, s_warp[k]);
+    SegSum all = before;
+    for (int k = wid; k < CB_THREADS / 32; ++k) all = seg_join(all, s_warp[k]);
+    *tile_total = all;
+    SegSum prev{__shfl_up_sync(CSAW_FULL_MASK, incl.f, 1), __shfl_up_sync(CSAW_FULL_MASK, incl.s, 1)};
+    if (lane == 0) prev = SegSum{0u, 0ull};
+    return seg_join(before, prev);
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(CB_THREADS) cdf_tile_sum_kernel(const uint64_t* __restrict__ off,
+                                                                   const uint32_t* __restrict__ col,
+                                                                   const uint32_t* __restrict__ w,
+                                                                   const uint32_t* __restrict__ deg, uint32_t V,
+                                                                   uint64_t E, uint32_t* __restrict__ tile_f,
+                                                                   uint64_t* __restrict__ tile_s)
+{
+    __shared__ uint32_t s_bits[CB_TILE / 32];
+    __shared__ uint32_t s_rows[2];
+    __shared__ SegSum s_warp[CB_THREADS / 32];
+    const uint64_t t = blockIdx.x;
+    CdfTile<KIND> tl;
+    tl.load(off, col, w, deg, V, E, t * CB_TILE, s_bits, s_rows);
+    SegSum tot;
+    block_exclusive_seg(tl.total(), s_warp, &tot);
+    if (threadIdx.x == 0) {
+        tile_f[t] = tot.f;
+        tile_s[t] = tot.s;
+    }
+}
+
+// One block.  tile_s becomes the running row sum entering each tile (the
+// segmented sum of all earlier tiles; edge 0 always starts a row).
+__global__ void __launch_bounds__(CB_CARRY_THREADS) cdf_tile_carry_kernel(const uint32_t* __restrict__ tile_f,
+                                                                          uint64_t* __restrict__ tile_s,
+                                                                          uint64_t n_tiles)
+{
+    __shared__ SegSum s_warp[CB_CARRY_THREADS / 32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const uint64_t per = (n_tiles + CB_CARRY_THREADS - 1) / CB_CARRY_THREADS;
+    const uint64_t t0 = per * tid < n_tiles ? per * tid : n_tiles;
+    const uint64_t t1 = t0 + per < n_tiles ? t0 + per : n_tiles;
+    SegSum mine{0u, 0ull};
+    for (uint64_t t = t0; t < t1; ++t) mine = seg_join(mine, SegSum{tile_f[t], tile_s[t]});
+    const SegSum incl = warp_inclusive_seg(mine, lane);
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    SegSum acc{0u, 0ull};
+    for (int k = 0; k < wid; ++k) acc = seg_join(acc, s_warp[k]);
+    SegSum prev{__shfl_up_sync(CSAW_FULL_MASK, incl.f, 1), __shfl_up_sync(CSAW_FULL_MASK, incl.s, 1)};
+    if (lane == 0) prev = SegSum{0u, 0ull};
+    acc = seg_join(acc, prev);
+    for (uint64_t t = t0; t < t1; ++t) {
+        const SegSum here{tile_f[t], tile_s[t]};
+        tile_s[t] = acc.s;
+        acc = seg_join(acc, here);
+    }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(CB_THREADS) cdf_tile_scan_kernel(const uint64_t* __restrict__ off,
+                                                                    const uint32_t* __restrict__ col,
+                                                                    const uint32_t* __restrict__ w,
+                                                                    const uint32_t* __restrict__ deg, uint32_t V,
+                                                                    uint64_t E, const uint64_t* __restrict__ carry,
+                                                                    uint64_t* __restrict__ cdf,
+                                                                    uint64_t* __restrict__ sum)
+{
+    __shared__ uint32_t s_bits[CB_TILE / 32];
+    __shared__ uint32_t s_rows[2];
+    __shared__ SegSum s_warp[CB_THREADS / 32];
+    const uint64_t t = blockIdx.x;
+    CdfTile<KIND> tl;
+    tl.load(off, col, w, deg, V, E, t * CB_TILE, s_bits, s_rows);
+    SegSum tot;
+    const SegSum ex = seg_join(SegSum{0u, __ldg(carry + t)}, block_exclusive_seg(tl.total(), s_warp, &tot));
+    uint64_t out[CB_ITEMS];
+    uint64_t run = ex.s;
+#pragma unroll
+    for (int j = 0; j < CB_ITEMS; ++j) {
+        if ((tl.starts >> j) & 1u) run = 0;
+        run += tl.b[j];
+        out[j] = run;
+    }
+    const uint64_t pb = tl.pb;
+    if (pb + CB_ITEMS <= E) {
+        ulonglong2* dst = reinterpret_cast<ulonglong2*>(cdf + pb);
+#pragma unroll
+        for (int j = 0; j < CB_ITEMS / 2; ++j) dst[j] = make_ulonglong2(out[2 * j], out[2 * j + 1]);
+        sum[pb >> 3] = out[CB_ITEMS - 1];
+    } else {
+#pragma unroll
+        for (int j = 0; j < CB_ITEMS; ++j)
+            if (pb + j < E) cdf[pb + j] = out[j];
+    }
+}
+
+csaw_status enqueue_cdf_build(const csaw_graph* g, int kind, uint64_t* cdf, cudaStream_t s)
+{
+    if (g->E == 0) return CSAW_OK;
+    const uint64_t n_tiles = (g->E + CB_TILE - 1) / CB_TILE;
+    if (n_tiles > 0x7FFFFFFFull) return fail(CSAW_ERR_INVALID, "too many edges for the cumulative array");
+    void* tf = nullptr;
+    void* ts = nullptr;
+    CSAW_TRY(dalloc(&tf, sizeof(uint32_t) * n_tiles, s));
+    csaw_status st = dalloc(&ts, sizeof(uint64_t) * n_tiles, s);
+    if (st != CSAW_OK) { dfree(tf, s); return st; }
+    uint64_t* S = cdf_summary(cdf, g->E);
+    const unsigned grid = (unsigned)n_tiles;
+    if (kind == CSAW_BIAS_EDGE_WEIGHT) {
+        cdf_tile_sum_kernel<CSAW_BIAS_EDGE_WEIGHT><<<grid, CB_THREADS, 0, s>>>(
+            g->off, g->col, g->w, g->deg, g->V, g->E, (uint32_t*)tf, (uint64_t*)ts);
+        cdf_tile_carry_kernel<<<1, CB_CARRY_THREADS, 0, s>>>((const uint32_t*)tf, (uint64_t*)ts, n_tiles);
+        cdf_tile_scan_kernel<CSAW_BIAS_EDGE_WEIGHT><<<grid, CB_THREADS, 0, s>>>(
+            g->off, g->col, g->w, g->deg, g->V, g->E, (const uint64_t*)ts, cdf, S);
+    } else {
+        cdf_tile_sum_kernel<CSAW_BIAS_NEIGHBOR_DEGREE><<<grid, CB_THREADS, 0, s>>>(
+            g->off, g->col, g->w, g->deg, g->V, g->E, (uint32_t*)tf, (uint64_t*)ts);
+        cdf_tile_carry_kernel<<<1, CB_CARRY_THREADS, 0, s>>>((const uint32_t*)tf, (uint64_t*)ts, n_tiles);
+        cdf_tile_scan_kernel<CSAW_BIAS_NEIGHBOR_DEGREE><<<grid, CB_THREADS, 0, s>>>(
+            g->off, g->col, g->w, g->deg, g->V, g->E, (const uint64_t*)ts, cdf, S);
+    }
+    cudaError_t e = cudaGetLastError();
+    dfree(tf, s);
+    dfree(ts, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cumulative array launch");
+    return CSAW_OK;
 }
 
 }  // namespace csaw
@@ -422,28 +633,23 @@ extern "C" csaw_status csaw_graph_build_cdf(csaw_graph* g, int32_t bias_kind, vo
     if (g->cdf[bias_kind]) return CSAW_OK;
     cudaStream_t s = (cudaStream_t)stream;
     uint64_t* cdf = nullptr;
-    // padded like col/w so that 16-byte stores of a row's last group stay inside
-    CSAW_TRY(alloc_with(&g->allocator, (void**)&cdf, sizeof(uint64_t) * (g->E + CSAW_EDGE_PAD), s));
-    unsigned long long* ctr = nullptr;
-    cudaError_t e = cudaMalloc(&ctr, sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), s);
-    if (e == cudaSuccess) {
-        const unsigned blocks = (unsigned)g->sm_count * 8;
-        if (bias_kind == CSAW_BIAS_EDGE_WEIGHT)
-            build_cdf_kernel<CSAW_BIAS_EDGE_WEIGHT><<<blocks, 256, 0, s>>>(g->off, g->col, g->w, g->deg, g->V, cdf, ctr);
-        else
-            build_cdf_kernel<CSAW_BIAS_NEIGHBOR_DEGREE><<<blocks, 256, 0, s>>>(g->off, g->col, g->w, g->deg, g->V, cdf, ctr);
-        e = cudaGetLastError();
+    // padded like col/w so that a group's 16-byte loads and stores stay
+    // inside; the summary follows the padding
+    const size_t bytes = sizeof(uint64_t) * cdf_words(g->E);
+    CSAW_TRY(alloc_with(&g->allocator, (void**)&cdf, bytes, s));
+    csaw_status st = enqueue_cdf_build(g, bias_kind, cdf, s);
+    if (st == CSAW_OK) {
+        const cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_fail(e, "build cumulative array");
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    cudaFree(ctr);
-    if (e != cudaSuccess) {
+    if (st != CSAW_OK) {
+        cudaStreamSynchronize(s);
         free_with(g->allocator, cdf, s);
-        return cuda_fail(e, "build cumulative array");
+        return st;
     }
     g->cdf[bias_kind] = cdf;
     g->cdf_alloc[bias_kind] = g->allocator;
-    g->device_bytes += sizeof(uint64_t) * (g->E + CSAW_EDGE_PAD);
+    g->device_bytes += bytes;
     return CSAW_OK;
 }
 
@@ -469,7 +675,7 @@ extern "C" csaw_status csaw_graph_drop_cdf(csaw_graph* g, int32_t bias_kind)
         cudaDeviceSynchronize();   // no call may be running on the graph; its frees may still be queued
         free_with(g->cdf_alloc[bias_kind], g->cdf[bias_kind], nullptr);
         g->cdf[bias_kind] = nullptr;
-        g->device_bytes -= sizeof(uint64_t) * (g->E + CSAW_EDGE_PAD);
+        g->device_bytes -= sizeof(uint64_t) * cdf_words(g->E);
     }
     return CSAW_OK;
 }

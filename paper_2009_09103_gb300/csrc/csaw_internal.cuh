@@ -143,13 +143,32 @@ void launch_partition_check(uint32_t* col, uint32_t* w, uint64_t ne, uint32_t V,
 
 // Walks that read a cached cumulative array (or, for uniform bias, none):
 // one thread per walker.  Defined in csaw_walk.cu.
-csaw_status launch_walk_cached(const csaw_graph* g, int kind, const uint32_t* starts, uint64_t n,
-                               uint32_t length, uint64_t rng_seed, uint32_t* path, cudaStream_t s);
+// cdf: the kind's cumulative array (cdf_words(E) words; ignored for uniform).
+csaw_status launch_walk_cached(const csaw_graph* g, int kind, const uint64_t* cdf, const uint32_t* starts,
+                               uint64_t n, uint32_t length, uint64_t rng_seed, uint32_t* path, cudaStream_t s);
 
 // Whether selection/walks of this kind can use a cached cumulative array:
 // uniform always (implicit), edge weight / neighbour degree when built and
 // no bias of the kind is zero.
 bool cached_cdf_usable(const csaw_graph* g, int kind);
+
+// Whether every bias of a static kind is positive (the condition for walking
+// or selecting over its cumulative array).
+bool cdf_kind_positive(const csaw_graph* g, int kind);
+
+// The cumulative array of a static kind: cdf[e] for e < E, CSAW_EDGE_PAD
+// padding words, then the summary S[g] = cdf[8g + 7] for 8g + 7 < E;
+// cdf_words(E) words in all.
+uint64_t cdf_words(uint64_t E);
+__host__ __device__ inline uint64_t* cdf_summary(uint64_t* cdf, uint64_t E) { return cdf + E + CSAW_EDGE_PAD; }
+__host__ __device__ inline const uint64_t* cdf_summary(const uint64_t* cdf, uint64_t E)
+{
+    return cdf + E + CSAW_EDGE_PAD;
+}
+
+// Enqueues the build of the cumulative array (and its summary) of a static
+// kind into cdf (cdf_words(E) words) on s; temporaries are stream-ordered.
+csaw_status enqueue_cdf_build(const csaw_graph* g, int kind, uint64_t* cdf, cudaStream_t s);
 
 // Releases a result made by the request server (tagged "CSRV").
 void free_server_result(void* result);
@@ -168,6 +187,11 @@ struct SampleTables {
 csaw_status sample_batch(csaw_graph* g, const uint32_t* d_seeds, const uint64_t* d_inst_off, uint32_t n_inst,
                          uint64_t n_seeds, uint32_t depth, const uint32_t* fan_max, const SampleTables& t,
                          int kind, cudaStream_t s, csaw_sample_result** out);
+
+// Frees a result of sample_batch: its device edges stream-ordered on s (no
+// device-wide synchronisation, unlike csaw_result_free, whose caller's stream
+// may be gone), then the result.  For callers that own s.
+void free_sample_result_on(csaw_sample_result* R, cudaStream_t s);
 
 // Validation of a bias argument against a graph; fills the effective kind
 // (EDGE_WEIGHT on a graph without weights is UNIFORM).
@@ -281,6 +305,46 @@ __device__ __forceinline__ bool sorted_contains(const uint32_t* __restrict__ col
         if (c < u) beg = mid + 1; else end = mid;
     }
     return beg < row_end && __ldg(col + beg) == u;
+}
+
+// Smallest e in [beg, end) with cdf[e] > x, for x < cdf[end - 1].  Groups
+// are the aligned runs of 8 edges; every summary entry sum[g] with
+// beg/8 <= g < (end-1)/8 is a prefix sum of this row, so bisecting them
+// finds the group of the hit (the last group when none exceeds x).  In that
+// group the row's positions [a, b) are read as two 32-byte halves, the
+// second only when every row position of the first is <= x; the hit is the
+// half's first row position plus its count of positions <= x (the row's
+// sums do not decrease).  Reads stay below 8 * ((end-1)/8) + 8 <= E + 7,
+// inside the array's padding.
+__device__ __forceinline__ uint64_t cdf_search(const uint64_t* __restrict__ cdf, const uint64_t* __restrict__ sum,
+                                               uint64_t beg, uint64_t end, uint64_t x)
+{
+    uint64_t lo = beg >> 3, hi = (end - 1) >> 3;
+    while (lo < hi) {
+        const uint64_t mid = lo + ((hi - lo) >> 1);
+        if (__ldg(sum + mid) > x) hi = mid; else lo = mid + 1;
+    }
+    const uint64_t gb = lo << 3;
+    const uint64_t a = gb > beg ? gb : beg;
+    const uint64_t b = gb + 8 < end ? gb + 8 : end;
+    const ulonglong2* q = reinterpret_cast<const ulonglong2*>(cdf + gb);
+    const ulonglong2 u0 = __ldg(q), u1 = __ldg(q + 1);
+    const uint64_t h0[4] = {u0.x, u0.y, u1.x, u1.y};
+    uint32_t valid = 0, le = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const bool in = gb + j >= a && gb + j < b;
+        valid += in;
+        le += in && h0[j] <= x;
+    }
+    if (le < valid) return a + le;
+    const ulonglong2 u2 = __ldg(q + 2), u3 = __ldg(q + 3);
+    const uint64_t h1[4] = {u2.x, u2.y, u3.x, u3.y};
+    const uint64_t a1 = a > gb + 4 ? a : gb + 4;
+    uint32_t le1 = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) le1 += gb + 4 + j >= a1 && gb + 4 + j < b && h1[j] <= x;
+    return a1 + le1;
 }
 
 }  // namespace csaw

@@ -105,6 +105,7 @@ struct SelParams {
     const uint64_t* __restrict__ hub_off = nullptr;
     const uint64_t* __restrict__ hubS = nullptr;
     uint64_t hubS_cap = 0;                // entries of hubS
+    const uint64_t* __restrict__ cdf_sum = nullptr;   // the cached array's summary (sum[g] = cdf[8g + 7])
     uint32_t* err = nullptr;              // error flags (8: a hub range beyond hubS_cap)
     // instances of several requests in one run (null: one request): per
     // instance its Philox key, its index within its request (the draw
@@ -440,7 +441,7 @@ __global__ void __launch_bounds__(SEL_THREADS, 8) select_cdf_kernel(SelParams p)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint32_t* picks = s_picks[wid];
     const uint32_t lt = lanemask_lt();
-    const bool hub = p.hub_off != nullptr;
+    const bool hub = p.item_e != nullptr;   // hub items (vertex order): shared array or cached one
     const unsigned long long n_warp = hub ? p.n_items[2] : p.n_items[0];
     unsigned long long* counter = hub ? p.next + 2 : p.next;
     while (true) {
@@ -461,11 +462,11 @@ __global__ void __launch_bounds__(SEL_THREADS, 8) select_cdf_kernel(SelParams p)
             for (uint32_t j = lane; j < d; j += 32) emit(p, q0 + j, v, inst, __ldg(p.col + beg + j));
             continue;
         }
-        if (hub && p.hub_off[p.item_h[it]] + d > p.hubS_cap) {
+        if (hub && p.hubS && p.hub_off[p.item_h[it]] + d > p.hubS_cap) {
             if (lane == 0) atomicOr(p.err, 8u);   // never happens when the scratch is sized right
             continue;
         }
-        const uint64_t* row = hub ? p.hubS + p.hub_off[p.item_h[it]] : p.cdf ? p.cdf + beg : nullptr;
+        const uint64_t* row = hub && p.hubS ? p.hubS + p.hub_off[p.item_h[it]] : p.cdf ? p.cdf + beg : nullptr;
         const DrawKey dk = draw_key(p, inst);
         const uint64_t T = cdf_at(row, IMPLICIT, d - 1);
         uint32_t have = 0, a0 = 0;
@@ -479,6 +480,8 @@ __global__ void __launch_bounds__(SEL_THREADS, 8) select_cdf_kernel(SelParams p)
             if (!live) {
             } else if (IMPLICIT) {
                 i = (uint32_t)x;
+            } else if (p.cdf_sum && row == p.cdf + beg) {
+                i = (uint32_t)(cdf_search(p.cdf, p.cdf_sum, beg, beg + d, x) - beg);   // the cached array
             } else {
                 uint32_t lo = 0, hi = d - 1;
                 while (lo < hi) {
@@ -633,7 +636,7 @@ __global__ void count_kernel(CountParams p)
         const uint32_t c = min(k, npos);
         const bool take_all = npos <= k;
         const bool listed = e < n && c > 0 && v >= p.v_lo && v < p.v_hi;
-        const bool to_warp = listed && (take_all || (p.cached ? c <= PICK_MAX : d <= p.theta_w));
+        const bool to_warp = listed && (take_all || (p.cached && !p.hub_list ? c <= PICK_MAX : d <= p.theta_w));
         const bool to_hub = listed && !to_warp && p.hub_list != nullptr && c <= PICK_MAX;
         const bool to_cta = listed && !to_warp && !to_hub;
         if (e < n && p.write_cnt) p.cnt[e] = c;
@@ -695,6 +698,16 @@ __global__ void hub_flag_kernel(const uint64_t* __restrict__ sorted, const unsig
     for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
          q += (uint64_t)gridDim.x * blockDim.x)
         flag[q] = (q == 0 || ((sorted[q] ^ sorted[q - 1]) & vmask) != 0) ? 1u : 0u;
+}
+
+// item_e[q] = the entry of sorted key q (cached arrays: vertex order only).
+__global__ void hub_order_kernel(const uint64_t* __restrict__ sorted, const unsigned long long* n_dev,
+                                 uint32_t vshift, uint32_t* __restrict__ item_e)
+{
+    const uint64_t n = *n_dev;
+    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (uint64_t)gridDim.x * blockDim.x)
+        item_e[q] = (uint32_t)(sorted[q] >> vshift);
 }
 
 constexpr uint32_t HUB_WARP_DEG = 2048;   // hubs up to this degree: one warp builds each
@@ -1429,6 +1442,7 @@ struct Pipeline {
     uint32_t theta_w = WARP_MAX_DEG;
     bool cached = false;                 // selection over a cached cumulative array
     bool hub_path = false;               // shared hub arrays per layer (static bias, streamed)
+    bool hub_order = false;              // cached static bias: hub items visited in vertex order
     bool cta_slots = false;              // CTA items may exceed CTA_SMEM_DEG: global slots
     uint32_t attempt_cap = CSAW_ATTEMPT_CAP;
     uint32_t k0 = 0, k1 = 0;
@@ -1484,6 +1498,7 @@ struct Pipeline {
         select_shape(g, kind, &theta_w, &sel_blocks);
         cached = cached_cdf_usable(g, kind);
         hub_path = !cached && (kind == CSAW_BIAS_EDGE_WEIGHT || kind == CSAW_BIAS_NEIGHBOR_DEGREE);
+        hub_order = cached && (kind == CSAW_BIAS_EDGE_WEIGHT || kind == CSAW_BIAS_NEIGHBOR_DEGREE);
         // CTA items exist for picks above PICK_MAX (or, without the hub
         // path, any long row); only rows above CTA_SMEM_DEG need a slot
         bool big_k = false;
@@ -1546,6 +1561,24 @@ static csaw_status enqueue_hub_groups(Pipeline& P, uint32_t l, cudaStream_t s)
     return CSAW_OK;
 }
 
+// Cached arrays: the layer's hub items in vertex order (item_e), so that the
+// warps drawing from one hub's row run back to back and share its lines in L2.
+static csaw_status enqueue_hub_order(Pipeline& P, uint32_t l, cudaStream_t s)
+{
+    csaw_graph* g = P.g;
+    const uint64_t cap = P.L[l].f_cap;
+    const unsigned long long* n_hub = (const unsigned long long*)P.lc(l, L_ITEMS + 2);
+    const unsigned grid = grid_for(cap, 256, g->sm_count);
+    const uint32_t vshift = ((uint32_t)P.vbits + 7u) & ~7u;
+    hub_keys_kernel<<<grid, 256, 0, s>>>(P.hlist, n_hub, P.L[l].F, P.vmask, vshift, P.hkeys);
+    uint64_t* sorted = P.hkeys;
+    CSAW_TRY(radix_sort_u64(P.hkeys, P.halt, (const uint64_t*)n_hub, cap, (int)vshift, g->sm_count, P.sort_scr,
+                            s, &sorted));
+    hub_order_kernel<<<grid, 256, 0, s>>>(sorted, n_hub, vshift, P.item_e);
+    CSAW_CUDA(cudaGetLastError());
+    return CSAW_OK;
+}
+
 // Count/classify of layer l's entries (vertices in [v_lo, v_hi) listed;
 // write_cnt: store the counts).
 static csaw_status enqueue_classify(Pipeline& P, uint32_t l, uint32_t v_lo, uint32_t v_hi, bool write_cnt,
@@ -1559,7 +1592,7 @@ static csaw_status enqueue_classify(Pipeline& P, uint32_t l, uint32_t v_lo, uint
     cp.k = P.fanout[l]; cp.theta_w = P.theta_w; cp.cached = P.cached; cp.zero_bias = P.zero_bias;
     cp.cnt = B.cnt; cp.warp_list = B.wlist; cp.cta_list = B.clist;
     cp.n_items = (unsigned long long*)P.lc(l, L_ITEMS);
-    cp.hub_list = P.hub_path ? P.hlist : nullptr;
+    cp.hub_list = P.hub_path || P.hub_order ? P.hlist : nullptr;
     cp.inst_k = P.inst_fan ? P.inst_fan + (uint64_t)l * P.n_inst : nullptr;
     cp.vbits = (uint32_t)P.vbits;
     cp.v_lo = v_lo; cp.v_hi = v_hi; cp.write_cnt = write_cnt;
@@ -1580,6 +1613,7 @@ static csaw_status enqueue_count(Pipeline& P, uint32_t l, cudaStream_t s)
     CSAW_TRY(enqueue_classify(P, l, 0, 0xFFFFFFFFu, true, s));
     CSAW_TRY(scan_u32(B.cnt, B.pos, P.lc(l, L_N), B.f_cap, P.scan_scr, P.lc(l, L_TOTAL), s));
     if (P.hub_path && B.f_cap) CSAW_TRY(enqueue_hub_groups(P, l, s));
+    if (P.hub_order && B.f_cap) CSAW_TRY(enqueue_hub_order(P, l, s));
     return CSAW_OK;
 }
 
@@ -1599,6 +1633,7 @@ static csaw_status enqueue_select_items(Pipeline& P, uint32_t l, cudaStream_t s)
         sp.out_src = B.src; sp.out_dst = B.dst; sp.out_cand = (l + 1 < P.depth) ? B.cand : nullptr;
         sp.scratch_S = P.hub_S; sp.scratch_bits = P.hub_bits; sp.scratch_stride = g->max_degree;
         sp.cdf = P.cached && P.kind != CSAW_BIAS_UNIFORM ? g->cdf[P.kind] : nullptr;
+    sp.cdf_sum = sp.cdf ? cdf_summary(sp.cdf, g->E) : nullptr;
         sp.skip_warp_items = P.cached;
         sp.attempt_cap = P.attempt_cap;
         sp.inst_key = P.inst_key; sp.inst_id = P.inst_id;
@@ -1609,6 +1644,12 @@ static csaw_status enqueue_select_items(Pipeline& P, uint32_t l, cudaStream_t s)
             const int blocks = g->sm_count * 8;
             if (P.kind == CSAW_BIAS_UNIFORM) select_cdf_kernel<true><<<blocks, SEL_THREADS, 0, s>>>(sp);
             else select_cdf_kernel<false><<<blocks, SEL_THREADS, 0, s>>>(sp);
+            if (P.hub_order) {
+                // the hub items in vertex order, over the same array
+                SelParams hs = sp;
+                hs.item_e = P.item_e;
+                select_cdf_kernel<false><<<blocks, SEL_THREADS, 0, s>>>(hs);
+            }
             CSAW_CUDA(cudaGetLastError());
         }
         switch (P.kind) {
@@ -1781,6 +1822,7 @@ static LayerSelParams layer_params(const Pipeline& P, uint32_t l)
     sp.zero_bias = P.zero_bias; sp.pos = B.pos;
     sp.out_src = B.src; sp.out_dst = B.dst; sp.out_cand = (l + 1 < P.depth) ? B.cand : nullptr;
     sp.cdf = P.cached && P.kind != CSAW_BIAS_UNIFORM ? g->cdf[P.kind] : nullptr;
+    sp.cdf_sum = sp.cdf ? cdf_summary(sp.cdf, g->E) : nullptr;
     sp.attempt_cap = P.attempt_cap;
     lp.FO = B.FO;
     lp.n_inst = P.n_inst;
@@ -1867,7 +1909,7 @@ static csaw_status run_sample(csaw_graph* g, const uint32_t* seeds, const uint64
     R->src.assign(depth, nullptr);
     R->dst.assign(depth, nullptr);
     R->layer_edges.assign(depth, 0);
-    const bool hubs = P.hub_path && !layer_mode;
+    const bool hubs = (P.hub_path || P.hub_order) && !layer_mode;
     for (uint32_t l = 0; l < depth; ++l) {
         // the layer's hub grouping buffers and shared hub prefix sums live
         // until its selection is done
@@ -1882,11 +1924,12 @@ static csaw_status run_sample(csaw_graph* g, const uint32_t* seeds, const uint64
         uint64_t h[3] = {0, 0, 0};
         CSAW_CUDA(cudaMemcpyAsync(&h[0], P.ctr + CT_ERR, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
         CSAW_CUDA(cudaMemcpyAsync(&h[1], P.lc(l, L_TOTAL), sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
-        if (hubs) CSAW_CUDA(cudaMemcpyAsync(&h[2], P.lc(l, L_HUBE), sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+        const bool shared = hubs && P.hub_path;   // shared hub arrays (streamed biases)
+        if (shared) CSAW_CUDA(cudaMemcpyAsync(&h[2], P.lc(l, L_HUBE), sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
         CSAW_CUDA(cudaStreamSynchronize(s));
         CSAW_TRY(check_errors(h[0]));
         const uint64_t total = h[1];
-        if (hubs) {
+        if (shared) {
             P.hubS_cap = h[2];
             CSAW_TRY(get_layer((void**)&P.hubS, sizeof(uint64_t) * (h[2] ? h[2] : 1)));
         }
@@ -1952,6 +1995,20 @@ csaw_status sample_batch(csaw_graph* g, const uint32_t* d_seeds, const uint64_t*
     }
     *out = R;
     return CSAW_OK;
+}
+
+void free_sample_result_on(csaw_sample_result* R, cudaStream_t s)
+{
+    if (!R) return;
+    for (std::vector<uint32_t*>* arrs : {&R->src, &R->dst})
+        for (uint32_t*& p : *arrs) {
+            if (p) {
+                if (R->alloc.free) R->alloc.free(p, (void*)s, R->alloc.ctx);
+                else cudaFreeAsync(p, s);
+            }
+            p = nullptr;
+        }
+    delete R;
 }
 
 }  // namespace csaw
@@ -2172,6 +2229,7 @@ extern "C" csaw_status csaw_sample_plan_create_ex(csaw_graph* g, uint32_t n_inst
         if (st == CSAW_OK) st = alloc_edges(P, l, e, get, get);
         f = e < fmax ? e : fmax;
     }
+    if (st == CSAW_OK && P.hub_order) st = alloc_hub(P, f_max, get);   // vertex order of hub items
     if (st == CSAW_OK && P.hub_path) {
         // shared hub prefix sums: at most every edge of the rows above
         // theta_w, and at most max degree per hub item

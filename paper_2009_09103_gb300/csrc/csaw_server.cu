@@ -48,7 +48,7 @@ struct Request {
     std::vector<uint32_t> starts;
     uint32_t length = 0;
     uint64_t estimate = 0;
-    bool large = false;            // more than SMALL_BATCH_EDGES sampled edges possible
+    bool large = false;            // more than SMALL_BATCH_EDGES sampled edges possible: low priority
     enum { PENDING, RUNNING, DONE } state = PENDING;
     csaw_result* result = nullptr;
 };
@@ -389,21 +389,25 @@ static csaw_status execute_samples(csaw_graph* g, Lane& L, std::vector<Request*>
         e = cudaStreamSynchronize(L.s);
         if (e != cudaSuccess) st = cuda_fail(e, "sample batch");
     }
-    csaw_result_free(R);
+    free_sample_result_on(R, L.s);   // csaw_result_free would wait for every slot's kernels
     return st;
 }
 
 
-// Sampled edges a request produces at most (walk steps; sampling without
-// the visited filter).
-static uint64_t edge_bound(const Request* rq)
+// Sampled edges a request produces at most: walk steps; for sampling, per
+// layer the smaller of frontier x fanout and the degrees of the frontier's
+// largest possible rows (the visited filter is not counted).
+static uint64_t edge_bound(const csaw_graph* g, const DegreeTable& dt, const Request* rq)
 {
     if (rq->kind == CSAW_REQ_WALK) return (uint64_t)rq->starts.size() * rq->length;
+    const uint64_t f_max = (uint64_t)g->V * (rq->n_instances ? rq->n_instances : 1);
     uint64_t f = rq->seeds.size(), total = 0;
     for (uint32_t k : rq->fanout) {
-        const uint64_t e = f > (1ull << 40) / (k ? k : 1) ? (1ull << 40) : f * k;
+        uint64_t e = f > (1ull << 40) / (k ? k : 1) ? (1ull << 40) : f * k;
+        const uint64_t rows = dt.top_sum(f < g->V ? f : g->V) * (f / (g->V ? g->V : 1) + 1);
+        e = e < rows ? e : rows;
         total += e;
-        f = e;
+        f = e < f_max ? e : f_max;
     }
     return total;
 }
@@ -443,20 +447,16 @@ struct csaw_server {
     uint64_t next_ticket = 1;
     uint64_t in_use = 0;
     uint32_t running = 0;
-    uint32_t large_running = 0;    // large batches running (at most one)
     bool stop = false;
     std::vector<std::thread> workers;
     std::vector<Lane> lanes;
 
-    // Two classes: large requests (more than SMALL_BATCH_EDGES sampled edges
-    // possible) run one batch at a time, so that each sees the GPU nearly to
-    // itself; small ones run beside them on the high-priority streams.  The
-    // oldest waiting request that may start now: one whose estimate fits the
-    // budget, and small or with no large batch running.  Called with mu held.
+    // The oldest waiting request whose estimate fits the budget.  Called
+    // with mu held.
     std::deque<Request*>::iterator startable()
     {
         for (auto it = pending.begin(); it != pending.end(); ++it)
-            if (in_use + (*it)->estimate <= budget && (!(*it)->large || large_running == 0)) return it;
+            if (in_use + (*it)->estimate <= budget) return it;
         return pending.end();
     }
 
@@ -501,8 +501,6 @@ struct csaw_server {
             cv_work.wait(lk, [&] { return stop || startable() != pending.end(); });
             if (stop) break;   // pending requests are aborted by destroy
             take_batch(batch);
-            const bool large = batch[0]->large;
-            if (large) ++large_running;
             const int64_t t_admit = now_ns();
             for (Request* rq : batch) {
                 in_use += rq->estimate;
@@ -522,7 +520,6 @@ struct csaw_server {
                 --running;
                 rq->state = Request::DONE;
             }
-            if (large) --large_running;
             cv_done.notify_all();
             cv_work.notify_all();
         }
@@ -642,7 +639,7 @@ extern "C" csaw_status csaw_submit(csaw_server* sv, const csaw_request* r, uint6
     }
     if (st != CSAW_OK) { delete rq; return st; }
     rq->estimate = estimate_bytes(sv->g, sv->degrees, *rq);
-    rq->large = edge_bound(rq) > SMALL_BATCH_EDGES;
+    rq->large = edge_bound(sv->g, sv->degrees, rq) > SMALL_BATCH_EDGES;
     if (rq->estimate > sv->budget) {
         const uint64_t est = rq->estimate;
         delete rq;

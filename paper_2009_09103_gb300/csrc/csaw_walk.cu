@@ -924,6 +924,7 @@ struct WalkCdfParams {
     const uint64_t* __restrict__ off;
     const uint32_t* __restrict__ col;
     const uint64_t* __restrict__ cdf;   // null for uniform bias
+    const uint64_t* __restrict__ sum;   // its summary: sum[g] = cdf[8g + 7]
     uint32_t V;
     const uint32_t* __restrict__ starts;
     uint64_t n;
@@ -1019,13 +1020,7 @@ __global__ void __launch_bounds__(WC_THREADS) walk_cached_kernel(WalkCdfParams p
                         stop = T == 0;
                         if (!stop) {
                             const uint64_t x = scale_draw(r, T);
-                            // smallest e in [beg, end) with cdf[e] > x
-                            uint64_t lo = beg, hi = end - 1;
-                            while (lo < hi) {
-                                const uint64_t mid = lo + ((hi - lo) >> 1);
-                                if (__ldg(p.cdf + mid) > x) hi = mid; else lo = mid + 1;
-                            }
-                            i = lo - beg;
+                            i = cdf_search(p.cdf, p.sum, beg, end, x) - beg;
                         }
                     }
                 }
@@ -1074,11 +1069,12 @@ static csaw_status launch_walk_cached_k(const WalkCdfParams& p, int sm_count, cu
     return CSAW_OK;
 }
 
-csaw_status launch_walk_cached(const csaw_graph* g, int kind, const uint32_t* starts, uint64_t n,
-                               uint32_t length, uint64_t rng_seed, uint32_t* path, cudaStream_t s)
+csaw_status launch_walk_cached(const csaw_graph* g, int kind, const uint64_t* cdf, const uint32_t* starts,
+                               uint64_t n, uint32_t length, uint64_t rng_seed, uint32_t* path, cudaStream_t s)
 {
     WalkCdfParams p;
-    p.off = g->off; p.col = g->col; p.cdf = kind == CSAW_BIAS_UNIFORM ? nullptr : g->cdf[kind];
+    p.off = g->off; p.col = g->col; p.cdf = kind == CSAW_BIAS_UNIFORM ? nullptr : cdf;
+    p.sum = p.cdf ? cdf_summary(p.cdf, g->E) : nullptr;
     p.V = g->V; p.starts = starts; p.n = n; p.L = length; p.path = path;
     p.keys = philox_round_keys(rng_seed);
     p.seg = WalkSegments{};
@@ -1095,6 +1091,7 @@ csaw_status walk_batch(const csaw_graph* g, const csaw_bias* bias, const uint32_
     if (kind != CSAW_BIAS_NODE2VEC && cached_cdf_usable(g, kind)) {
         WalkCdfParams p;
         p.off = g->off; p.col = g->col; p.cdf = kind == CSAW_BIAS_UNIFORM ? nullptr : g->cdf[kind];
+        p.sum = p.cdf ? cdf_summary(p.cdf, g->E) : nullptr;
         p.V = g->V; p.starts = d_starts; p.n = n; p.L = max_len; p.path = d_path;
         p.keys = philox_round_keys(0);
         p.seg = seg;
@@ -1175,9 +1172,22 @@ extern "C" csaw_status csaw_walk_ex(csaw_graph* g, const uint32_t* starts, uint6
                                         cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) { dfree(a, s); dfree(b, s); return cuda_fail(e, "copy starts"); }
     }
-    if (tele == CSAW_TELEPORT_NONE && kind != CSAW_BIAS_NODE2VEC && cached_cdf_usable(g, kind)) {
-        // static bias with a cached cumulative array (or uniform): thread per walker
-        csaw_status st = launch_walk_cached(g, kind, d_starts, n_walkers, length, rng_seed, d_path, s);
+    // static bias with a positive cumulative array: the graph's cached one,
+    // or (build_cdf) one built for this call into a stream-ordered temporary
+    const bool cached = cached_cdf_usable(g, kind);
+    const bool build = !cached && opts && opts->build_cdf && cdf_kind_positive(g, kind);
+    if (tele == CSAW_TELEPORT_NONE && kind != CSAW_BIAS_NODE2VEC && (cached || build)) {
+        const uint64_t* cdf = kind == CSAW_BIAS_UNIFORM ? nullptr : g->cdf[kind];
+        void* tmp = nullptr;
+        csaw_status st = CSAW_OK;
+        if (build) {
+            st = dalloc(&tmp, sizeof(uint64_t) * cdf_words(g->E), s);
+            if (st == CSAW_OK) st = enqueue_cdf_build(g, kind, (uint64_t*)tmp, s);
+            cdf = (const uint64_t*)tmp;
+        }
+        // thread per walker
+        if (st == CSAW_OK) st = launch_walk_cached(g, kind, cdf, d_starts, n_walkers, length, rng_seed, d_path, s);
+        dfree(tmp, s);
         if (mem_kind == CSAW_MEM_HOST) {
             if (st == CSAW_OK) {
                 cudaError_t e = cudaMemcpyAsync(path, d_path, path_bytes, cudaMemcpyDeviceToHost, s);

@@ -29,7 +29,7 @@ def star(d, seed, wmax=1000):
 
 @pytest.mark.parametrize("bias", ["edge_weight", "neighbor_degree"])
 def test_cached_walks_match_oracle(csaw, bias):
-    for g in (inputs.rmat_csr(12, 16, 100, 12), inputs.rmat_csr(8, 8, 40, 1), star(70001, 3)):
+    for g in (inputs.rmat_csr(12, 16, 100, 12), inputs.rmat_csr(8, 8, 40, 1), star(70001, 3), ragged(3)):
         G = csaw.Graph(g.off, g.col, g.w)
         G.build_cdf(bias)
         starts = np.concatenate([np.arange(min(g.V, 5000), dtype=np.uint32),
@@ -37,6 +37,61 @@ def test_cached_walks_match_oracle(csaw, bias):
         got = csaw.walk(G, starts, 20, bias, 77)
         assert np.array_equal(got, oracle.walk(g, starts, 20, bias, 77))
         G.close()
+
+
+def ragged(seed, V=7000, wmax=2**20):
+    """Rows of degree 0, 1, a few and a few hundred, and rows that straddle
+    the 2048-edge scan tiles; the edge count is not a multiple of 8."""
+    rng = np.random.default_rng(seed)
+    kind = rng.integers(0, 10, size=V)
+    deg = np.where(kind < 3, 0, np.where(kind < 6, 1, np.where(kind < 9, rng.integers(2, 30, size=V),
+                                                               rng.integers(100, 700, size=V))))
+    deg[[5, 17, V - 100]] = [2047, 2049, min(6500, V - 1)]
+    if int(deg.sum()) % 8 == 0:
+        deg[6] += 1
+    cols = [np.sort(rng.choice(V, size=int(d), replace=False)) for d in deg]
+    off = np.concatenate([[0], np.cumsum(deg)]).astype(np.uint64)
+    col = np.concatenate(cols).astype(np.uint32)
+    w = rng.integers(1, wmax, size=len(col)).astype(np.uint32)
+    return inputs.CSRGraph(off, col, w)
+
+
+@pytest.mark.parametrize("bias", ["edge_weight", "neighbor_degree"])
+def test_walk_with_cumulative_array_built_per_call(csaw, bias):
+    """build_cdf: the call builds the kind's cumulative array and its summary
+    (segmented scan over edge tiles) and walks over it; paths equal the
+    oracle's and those of the streaming walk, on graphs with empty rows, rows
+    across tile boundaries, a 70,001-neighbour hub and tiny edge counts.
+    Neighbour degree with an edge into a vertex without neighbours keeps the
+    streaming path (the option is ignored) and stays exact."""
+    tiny = inputs.csr_from_edges(4, [(0, 1), (0, 2), (0, 3), (1, 0), (2, 0), (2, 3), (3, 2)],
+                                 [3, 1, 4, 1, 5, 9, 2])
+    for g in (ragged(1), ragged(2, V=3000, wmax=7), inputs.rmat_csr(12, 16, 100, 12), star(70001, 3), tiny):
+        G = csaw.Graph(g.off, g.col, g.w)
+        starts = np.concatenate([np.arange(min(g.V, 7000), dtype=np.uint32), inputs.uniform_vertices(500, g.V, 4)])
+        got = csaw.walk(G, starts, 24, bias, 31, build_cdf=True)
+        assert np.array_equal(got, oracle.walk(g, starts, 24, bias, 31)), (g.V, g.E)
+        assert np.array_equal(got, csaw.walk(G, starts, 24, bias, 31))
+        G.close()
+
+
+def test_walk_build_per_call_equals_cached_on_device(csaw):
+    """Device inputs: the per-call array gives the paths of the graph's
+    cached array, which the option then leaves in use."""
+    import torch
+    g = inputs.rmat_csr(14, 16, 255, 14)
+    G = csaw.Graph(g.off, g.col, g.w)
+    s = torch.from_numpy(np.arange(g.V, dtype=np.uint32).view(np.int32)).cuda()
+    a = csaw.walk(G, s, 40, "edge_weight", 9, build_cdf=True)
+    G.build_cdf("edge_weight")
+    b = csaw.walk(G, s, 40, "edge_weight", 9, build_cdf=True)
+    c = csaw.walk(G, s, 40, "edge_weight", 9)
+    torch.cuda.synchronize()
+    assert bool(torch.equal(a, b)) and bool(torch.equal(b, c))
+    pick = inputs.uniform_vertices(400, g.V, 2).astype(np.int64)
+    ref = oracle.walk(g, pick.astype(np.uint32), 40, "edge_weight", 9, walker_ids=pick.astype(np.uint64))
+    assert np.array_equal(a[torch.from_numpy(pick).cuda()].cpu().numpy().view(np.uint32), ref)
+    G.close()
 
 
 @pytest.mark.parametrize("bias", ["edge_weight", "uniform"])

@@ -240,6 +240,25 @@ def test_sample_plan_batched_s24_subset(csaw, s24):
     G.close()
 
 
+def test_sample_plan_batched_s24_cached_subset(csaw, s24):
+    """The batched plan over the cached cumulative array (hub items in
+    vertex order, summary searches) against the oracle on the stratified
+    instance subset."""
+    wl = s24
+    g = wl.graph
+    G = csaw.Graph(g.off, g.col, g.w)
+    G.build_cdf(wl.bias)
+    n = len(wl.inst_offsets) - 1
+    plan = csaw.SamplePlan(G, n, len(wl.seeds), wl.fanout, wl.bias)
+    plan.run(wl.seeds, wl.inst_offsets, wl.rng_seed)
+    res = plan.result()
+    plan.close()
+    pick = s24_pick(wl, g)
+    ref = instance_subset_oracle(g, wl.seeds, wl.inst_offsets, pick, wl.fanout, wl.bias, wl.rng_seed)
+    check_subset(res, ref, n, pick, 2)
+    G.close()
+
+
 def test_sample_shared_hub_arrays(csaw):
     """Hub vertices that recur in many instances' frontiers share one
     cumulative array per layer: degrees around the warp/CTA build split
@@ -282,4 +301,16 @@ def test_sample_shared_hub_arrays(csaw):
             check_equal(plan.result(), ref, n_inst, len(fan))
             plan.close()
             csaw.set_select_tuning(G, bias, 0, 0)
+        # the cached array: hub items drawn in vertex order from it
+        G.build_cdf(bias)
+        for fan in ([25, 10], [3, 40, 2]):
+            ref = oracle.sample(g, seeds, io, fan, bias, 5)
+            check_equal(csaw.sample(G, seeds, io, fan, bias, 5), ref, n_inst, len(fan))
+            csaw.set_select_tuning(G, bias, 32, 0)
+            plan = csaw.SamplePlan(G, n_inst, len(seeds), fan, bias)
+            plan.run(seeds, io, 5)
+            check_equal(plan.result(), ref, n_inst, len(fan))
+            plan.close()
+            csaw.set_select_tuning(G, bias, 0, 0)
+        G.drop_cdf(bias)
     G.close()
