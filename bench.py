@@ -61,6 +61,16 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def source_sha(kernel_src: str) -> str:
+    """The kernel's source as compiled: its translation unit and the shared
+    header every unit includes."""
+    h = hashlib.sha256()
+    for f in (kernel_src, "csaw_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2009_09103_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def traffic_records(kernel_src: str, workload: str):
     """The committed ncu DRAM records of this workload's kernels in one
     translation unit, if they were taken on its current source."""
@@ -69,8 +79,7 @@ def traffic_records(kernel_src: str, workload: str):
         return []
     with open(p) as f:
         recs = json.load(f)
-    src = open(os.path.join(ROOT, "paper_2009_09103_gb300", "csrc", kernel_src), "rb").read()
-    sha = hashlib.sha256(src).hexdigest()[:16]
+    sha = source_sha(kernel_src)
     return [r for r in recs if r.get("source") == kernel_src and r.get("source_sha") == sha
             and r.get("workload") == workload]
 
@@ -409,7 +418,7 @@ def run_walk_bench(args, rank, world):
                 kernels["build_dram_gbs"] = round(dram / (ms_build / 1e3) / 1e9, 1)
                 kernels["build_dram_frac"] = round(dram / (ms_build / 1e3) / 1e9 / peak, 4)
                 kernels["build_kernels"] = sorted(r["kernel"] for r in recs)
-        roofline = roofline_block("walk_cached_kernel<EDGE_WEIGHT>", traffic_record("csaw_walk.cu", wl_name + "_cdf"),
+        roofline = roofline_block("walk_cached_kernel<EDGE_WEIGHT>", traffic_record("csaw_walk_cdf.cu", wl_name + "_cdf"),
                                   ms_walk, cb)
     cum = {"build": "built over all rows inside every step (segmented scan over edge tiles, then each step a "
                     "search of its summary and one or two 32-byte sectors)",
@@ -1131,11 +1140,12 @@ def served_leg(csaw, G, reqs, loads, slots, budget):
         th = threading.Thread(target=submitter)
         th.start()
         th.join()
-        lat = []
+        lat, wait = [], []
         first_sub, last_fin = None, 0
         for i, r in enumerate(reqs):
             res = srv.poll(tickets[i])
             lat.append((res.t_finish_ns - res.t_submit_ns) / 1e9)
+            wait.append((res.t_start_ns - res.t_submit_ns) / 1e9)
             first_sub = res.t_submit_ns if first_sub is None else min(first_sub, res.t_submit_ns)
             last_fin = max(last_fin, res.t_finish_ns)
         srv.close()
@@ -1143,7 +1153,8 @@ def served_leg(csaw, G, reqs, loads, slots, budget):
         lat = np.array(lat)
         slow = np.argsort(-lat)[:3]
         worst = [{"kind": reqs[i][0], "size": int(len(reqs[i][1])), "edges": int(edges[i]),
-                  "latency_ms": 1e3 * float(lat[i]), "serial_service_ms": 1e3 * float(svc[i])} for i in slow]
+                  "latency_ms": 1e3 * float(lat[i]), "waited_ms": 1e3 * float(wait[i]),
+                  "serial_service_ms": 1e3 * float(svc[i])} for i in slow]
         pt = {"load_frac_of_serial_capacity": frac, "arrival_rate_per_s": lam,
               "served": {"seps": total_edges / span, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
                          "p99_ms": 1e3 * float(np.percentile(lat, 99)), "slowest": worst},

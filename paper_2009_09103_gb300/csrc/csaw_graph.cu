@@ -8,7 +8,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <vector>
 
 #include "csaw_internal.cuh"
 
@@ -73,12 +75,48 @@ void free_with(const DevAllocator& a, void* p, cudaStream_t s)
     else cudaFree(p);
 }
 
+// The library's own stream-ordered pool, one per device.  Freed blocks stay
+// in it (they are not returned at every synchronisation), and a block freed
+// on one stream is reused on another only once that free has completed: the
+// pool never makes an allocation wait for work queued on another stream, so
+// one server slot's buffers never wait for another slot's kernels.
+static cudaError_t lib_pool(cudaMemPool_t* out)
+{
+    static std::mutex mu;
+    static std::vector<cudaMemPool_t> pools;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    if ((size_t)dev < pools.size() && pools[dev]) {
+        *out = pools[dev];
+        return cudaSuccess;
+    }
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool;
+    e = cudaMemPoolCreate(&pool, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = UINT64_MAX;
+    int no = 0;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no);
+    if (pools.size() <= (size_t)dev) pools.resize(dev + 1, nullptr);
+    pools[dev] = pool;
+    *out = pool;
+    return cudaSuccess;
+}
+
 csaw_status dalloc(void** p, size_t bytes, cudaStream_t s)
 {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
     if (t_alloc) return alloc_with(t_alloc, p, bytes, s);
-    cudaError_t e = cudaMallocAsync(p, bytes, s);
+    cudaMemPool_t pool;
+    cudaError_t e = lib_pool(&pool);
+    if (e == cudaSuccess) e = cudaMallocFromPoolAsync(p, bytes, pool, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
@@ -244,15 +282,6 @@ extern "C" csaw_status csaw_graph_create(const uint64_t* row_offsets, uint32_t n
             return cuda_fail(e0, "device query");
         }
     }
-    {
-        // Keep freed stream-ordered allocations in the device's pool instead of
-        // returning them at every synchronisation: calls reuse their buffers.
-        cudaMemPool_t pool;
-        if (cudaDeviceGetDefaultMemPool(&pool, g->device) == cudaSuccess) {
-            uint64_t keep = UINT64_MAX;
-            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
-        }
-    }
     g->V = n_vertices;
     g->E = n_edges;
     const size_t off_b = sizeof(uint64_t) * ((size_t)n_vertices + 1);
@@ -348,11 +377,14 @@ extern "C" csaw_status csaw_graph_get_info(const csaw_graph* g, csaw_graph_info*
 //   cdf_tile_carry_kernel one block: the running row sum entering each tile
 //   cdf_tile_scan_kernel  the tile's scan with that carry, written as 16-byte
 //                         stores, and the summary entries of its groups.
-// Row starts inside a tile come from the row offsets (two binary searches
-// for the rows holding its first and last edge, then one bit per row start
-// in shared memory).  The summary holds every 8th prefix sum (S[g] =
-// cdf[8g + 7]): a walk bisects it first and then reads one or two 32-byte
-// sectors of the array.
+// Row starts inside a tile come from the row offsets: cdf_tile_rows_kernel
+// first records, for every tile, the row holding its first edge (one pass
+// over the rows), and a tile sets one shared-memory bit per row start
+// between its own row and the next tile's.  The scan also writes the
+// summaries s1 (every 8th sum) and s2 (every 64th), and cdf_records_kernel
+// the per-vertex records {row start, row end, row total}: a walk step reads
+// one record sector, bisects s2, then reads one or two sectors of s1 and of
+// the array.
 
 namespace csaw {
 
@@ -371,7 +403,7 @@ bool cdf_kind_positive(const csaw_graph* g, int kind)
     return false;
 }
 
-uint64_t cdf_words(uint64_t E) { return E + CSAW_EDGE_PAD + (E + 7) / 8 + 8; }
+uint64_t cdf_words(uint64_t E, uint64_t V) { return cdf_layout(E, V).words; }
 
 constexpr int CB_THREADS = 256;
 constexpr int CB_ITEMS = 8;
@@ -404,15 +436,15 @@ __device__ __forceinline__ SegSum warp_inclusive_seg(SegSum x, int lane)
     return x;
 }
 
-// Smallest v in [1, V] with off[v] > p (p < off[V]).
-__device__ __forceinline__ uint32_t row_upper(const uint64_t* __restrict__ off, uint32_t V, uint64_t p)
+// tile_row[t] = the row holding edge t * CB_TILE (each tile start lies in
+// exactly one row with edges).
+__global__ void cdf_tile_rows_kernel(const uint64_t* __restrict__ off, uint32_t V, uint32_t* __restrict__ tile_row)
 {
-    uint32_t lo = 0, hi = V;
-    while (lo < hi) {
-        const uint32_t mid = lo + ((hi - lo) >> 1);
-        if (__ldg(off + mid) > p) hi = mid; else lo = mid + 1;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V;
+         v += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t beg = __ldg(off + v), end = __ldg(off + v + 1);
+        for (uint64_t t = (beg + CB_TILE - 1) / CB_TILE; t * CB_TILE < end; ++t) tile_row[t] = (uint32_t)v;
     }
-    return lo;
 }
 
 // Per-thread state of one tile: the thread's biases, its row-start bits and
@@ -425,21 +457,23 @@ struct CdfTile {
 
     __device__ void load(const uint64_t* __restrict__ off, const uint32_t* __restrict__ col,
                          const uint32_t* __restrict__ w, const uint32_t* __restrict__ deg, uint32_t V,
-                         uint64_t E, uint64_t p0, uint32_t* s_bits, uint32_t* s_rows)
+                         uint64_t E, const uint32_t* __restrict__ tile_row, uint64_t n_tiles, uint64_t t,
+                         uint32_t* s_bits)
     {
         const int tid = threadIdx.x;
-        const uint64_t p1 = p0 + CB_TILE < E ? p0 + CB_TILE : E;
+        const uint64_t p0 = t * CB_TILE;
+        const uint32_t span = (uint32_t)((p0 + CB_TILE < E ? p0 + CB_TILE : E) - p0);
         for (int i = tid; i < (int)(CB_TILE / 32); i += CB_THREADS) s_bits[i] = 0;
-        if (tid == 0) s_rows[0] = row_upper(off, V, p0) - 1;        // the row holding p0
-        if (tid == 32) s_rows[1] = row_upper(off, V, p1 - 1) - 1;   // the row holding p1 - 1
+        // r0 holds the tile's first edge, r1 the next tile's (the last row
+        // for the last tile); the rows between start inside (p0, p0 + span]
+        // (empty rows share the start of the next row with edges)
+        const uint32_t r0 = __ldg(tile_row + t);
+        const uint32_t r1 = t + 1 < n_tiles ? __ldg(tile_row + t + 1) : V - 1;
         __syncthreads();
-        const uint32_t r0 = s_rows[0], r1 = s_rows[1];
         if (tid == 0 && __ldg(off + r0) == p0) atomicOr(s_bits, 1u);
-        // rows r0+1 .. r1 start strictly inside the tile (empty rows share
-        // the start of the next row that has edges)
         for (uint64_t r = (uint64_t)r0 + 1 + tid; r <= r1; r += CB_THREADS) {
-            const uint32_t q = (uint32_t)(__ldg(off + r) - p0);
-            atomicOr(s_bits + (q >> 5), 1u << (q & 31));
+            const uint64_t q = __ldg(off + r) - p0;
+            if (q < span) atomicOr(s_bits + (q >> 5), 1u << (q & 31));
         }
         pb = p0 + (uint64_t)CB_ITEMS * tid;
         if (pb + CB_ITEMS <= E) {
@@ -505,15 +539,15 @@ __global__ void __launch_bounds__(CB_THREADS) cdf_tile_sum_kernel(const uint64_t
                                                                    const uint32_t* __restrict__ col,
                                                                    const uint32_t* __restrict__ w,
                                                                    const uint32_t* __restrict__ deg, uint32_t V,
-                                                                   uint64_t E, uint32_t* __restrict__ tile_f,
+                                                                   uint64_t E, const uint32_t* __restrict__ tile_row,
+                                                                   uint64_t n_tiles, uint32_t* __restrict__ tile_f,
                                                                    uint64_t* __restrict__ tile_s)
 {
     __shared__ uint32_t s_bits[CB_TILE / 32];
-    __shared__ uint32_t s_rows[2];
     __shared__ SegSum s_warp[CB_THREADS / 32];
     const uint64_t t = blockIdx.x;
     CdfTile<KIND> tl;
-    tl.load(off, col, w, deg, V, E, t * CB_TILE, s_bits, s_rows);
+    tl.load(off, col, w, deg, V, E, tile_row, n_tiles, t, s_bits);
     SegSum tot;
     block_exclusive_seg(tl.total(), s_warp, &tot);
     if (threadIdx.x == 0) {
@@ -555,16 +589,16 @@ __global__ void __launch_bounds__(CB_THREADS) cdf_tile_scan_kernel(const uint64_
                                                                     const uint32_t* __restrict__ col,
                                                                     const uint32_t* __restrict__ w,
                                                                     const uint32_t* __restrict__ deg, uint32_t V,
-                                                                    uint64_t E, const uint64_t* __restrict__ carry,
-                                                                    uint64_t* __restrict__ cdf,
-                                                                    uint64_t* __restrict__ sum)
+                                                                    uint64_t E, const uint32_t* __restrict__ tile_row,
+                                                                    uint64_t n_tiles, const uint64_t* __restrict__ carry,
+                                                                    uint64_t* __restrict__ cdf, uint64_t* __restrict__ s1,
+                                                                    uint64_t* __restrict__ s2)
 {
     __shared__ uint32_t s_bits[CB_TILE / 32];
-    __shared__ uint32_t s_rows[2];
     __shared__ SegSum s_warp[CB_THREADS / 32];
     const uint64_t t = blockIdx.x;
     CdfTile<KIND> tl;
-    tl.load(off, col, w, deg, V, E, t * CB_TILE, s_bits, s_rows);
+    tl.load(off, col, w, deg, V, E, tile_row, n_tiles, t, s_bits);
     SegSum tot;
     const SegSum ex = seg_join(SegSum{0u, __ldg(carry + t)}, block_exclusive_seg(tl.total(), s_warp, &tot));
     uint64_t out[CB_ITEMS];
@@ -580,7 +614,8 @@ __global__ void __launch_bounds__(CB_THREADS) cdf_tile_scan_kernel(const uint64_
         ulonglong2* dst = reinterpret_cast<ulonglong2*>(cdf + pb);
 #pragma unroll
         for (int j = 0; j < CB_ITEMS / 2; ++j) dst[j] = make_ulonglong2(out[2 * j], out[2 * j + 1]);
-        sum[pb >> 3] = out[CB_ITEMS - 1];
+        s1[pb >> 3] = out[CB_ITEMS - 1];
+        if (((pb >> 3) & 7) == 7) s2[pb >> 6] = out[CB_ITEMS - 1];   // edge 64h + 63
     } else {
 #pragma unroll
         for (int j = 0; j < CB_ITEMS; ++j)
@@ -588,34 +623,63 @@ __global__ void __launch_bounds__(CB_THREADS) cdf_tile_scan_kernel(const uint64_
     }
 }
 
+// rec[v] = {off[v], off[v+1], row total, 0}, two 16-byte stores per vertex.
+__global__ void cdf_records_kernel(const uint64_t* __restrict__ off, uint32_t V, const uint64_t* __restrict__ cdf,
+                                   uint64_t* __restrict__ rec)
+{
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V;
+         v += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t beg = __ldg(off + v), end = __ldg(off + v + 1);
+        const uint64_t T = end > beg ? cdf[end - 1] : 0ull;
+        ulonglong2* r = reinterpret_cast<ulonglong2*>(rec + 4 * v);
+        r[0] = make_ulonglong2(beg, end);
+        r[1] = make_ulonglong2(T, 0ull);
+    }
+}
+
 csaw_status enqueue_cdf_build(const csaw_graph* g, int kind, uint64_t* cdf, cudaStream_t s)
 {
-    if (g->E == 0) return CSAW_OK;
+    const CdfLayout L = cdf_layout(g->E, g->V);
+    uint64_t vb = ((uint64_t)g->V + 255) / 256;
+    if (vb > (uint64_t)g->sm_count * 8) vb = (uint64_t)g->sm_count * 8;
+    const unsigned vgrid = (unsigned)(vb ? vb : 1);
+    if (g->E == 0) {
+        if (g->V) cdf_records_kernel<<<vgrid, 256, 0, s>>>(g->off, g->V, cdf, cdf + L.rec);
+        const cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? CSAW_OK : cuda_fail(e, "cumulative array launch");
+    }
     const uint64_t n_tiles = (g->E + CB_TILE - 1) / CB_TILE;
     if (n_tiles > 0x7FFFFFFFull) return fail(CSAW_ERR_INVALID, "too many edges for the cumulative array");
     void* tf = nullptr;
     void* ts = nullptr;
+    void* tr = nullptr;
     CSAW_TRY(dalloc(&tf, sizeof(uint32_t) * n_tiles, s));
     csaw_status st = dalloc(&ts, sizeof(uint64_t) * n_tiles, s);
-    if (st != CSAW_OK) { dfree(tf, s); return st; }
-    uint64_t* S = cdf_summary(cdf, g->E);
+    if (st == CSAW_OK) st = dalloc(&tr, sizeof(uint32_t) * n_tiles, s);
+    if (st != CSAW_OK) { dfree(tf, s); dfree(ts, s); return st; }
     const unsigned grid = (unsigned)n_tiles;
+    uint32_t* tile_row = (uint32_t*)tr;
+    cdf_tile_rows_kernel<<<vgrid, 256, 0, s>>>(g->off, g->V, tile_row);
     if (kind == CSAW_BIAS_EDGE_WEIGHT) {
         cdf_tile_sum_kernel<CSAW_BIAS_EDGE_WEIGHT><<<grid, CB_THREADS, 0, s>>>(
-            g->off, g->col, g->w, g->deg, g->V, g->E, (uint32_t*)tf, (uint64_t*)ts);
+            g->off, g->col, g->w, g->deg, g->V, g->E, tile_row, n_tiles, (uint32_t*)tf, (uint64_t*)ts);
         cdf_tile_carry_kernel<<<1, CB_CARRY_THREADS, 0, s>>>((const uint32_t*)tf, (uint64_t*)ts, n_tiles);
         cdf_tile_scan_kernel<CSAW_BIAS_EDGE_WEIGHT><<<grid, CB_THREADS, 0, s>>>(
-            g->off, g->col, g->w, g->deg, g->V, g->E, (const uint64_t*)ts, cdf, S);
+            g->off, g->col, g->w, g->deg, g->V, g->E, tile_row, n_tiles, (const uint64_t*)ts, cdf, cdf + L.s1,
+            cdf + L.s2);
     } else {
         cdf_tile_sum_kernel<CSAW_BIAS_NEIGHBOR_DEGREE><<<grid, CB_THREADS, 0, s>>>(
-            g->off, g->col, g->w, g->deg, g->V, g->E, (uint32_t*)tf, (uint64_t*)ts);
+            g->off, g->col, g->w, g->deg, g->V, g->E, tile_row, n_tiles, (uint32_t*)tf, (uint64_t*)ts);
         cdf_tile_carry_kernel<<<1, CB_CARRY_THREADS, 0, s>>>((const uint32_t*)tf, (uint64_t*)ts, n_tiles);
         cdf_tile_scan_kernel<CSAW_BIAS_NEIGHBOR_DEGREE><<<grid, CB_THREADS, 0, s>>>(
-            g->off, g->col, g->w, g->deg, g->V, g->E, (const uint64_t*)ts, cdf, S);
+            g->off, g->col, g->w, g->deg, g->V, g->E, tile_row, n_tiles, (const uint64_t*)ts, cdf, cdf + L.s1,
+            cdf + L.s2);
     }
+    cdf_records_kernel<<<vgrid, 256, 0, s>>>(g->off, g->V, cdf, cdf + L.rec);
     cudaError_t e = cudaGetLastError();
     dfree(tf, s);
     dfree(ts, s);
+    dfree(tr, s);
     if (e != cudaSuccess) return cuda_fail(e, "cumulative array launch");
     return CSAW_OK;
 }
@@ -635,7 +699,7 @@ extern "C" csaw_status csaw_graph_build_cdf(csaw_graph* g, int32_t bias_kind, vo
     uint64_t* cdf = nullptr;
     // padded like col/w so that a group's 16-byte loads and stores stay
     // inside; the summary follows the padding
-    const size_t bytes = sizeof(uint64_t) * cdf_words(g->E);
+    const size_t bytes = sizeof(uint64_t) * cdf_words(g->E, g->V);
     CSAW_TRY(alloc_with(&g->allocator, (void**)&cdf, bytes, s));
     csaw_status st = enqueue_cdf_build(g, bias_kind, cdf, s);
     if (st == CSAW_OK) {
@@ -675,7 +739,7 @@ extern "C" csaw_status csaw_graph_drop_cdf(csaw_graph* g, int32_t bias_kind)
         cudaDeviceSynchronize();   // no call may be running on the graph; its frees may still be queued
         free_with(g->cdf_alloc[bias_kind], g->cdf[bias_kind], nullptr);
         g->cdf[bias_kind] = nullptr;
-        g->device_bytes -= sizeof(uint64_t) * cdf_words(g->E);
+        g->device_bytes -= sizeof(uint64_t) * cdf_words(g->E, g->V);
     }
     return CSAW_OK;
 }

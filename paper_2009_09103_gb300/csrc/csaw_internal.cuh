@@ -119,6 +119,28 @@ struct WalkSegments {
     uint32_t warp_budget;
 };
 
+// Which segment walker w is in, and its place there.
+struct WalkerSlot {
+    uint32_t k0, k1, id, L;
+    uint64_t row0;
+};
+
+__device__ __forceinline__ WalkerSlot walker_slot(const WalkSegments& sg, uint64_t w)
+{
+    uint32_t lo = 0, hi = sg.n;   // last r with start[r] <= w
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(sg.start + mid) <= w) lo = mid; else hi = mid;
+    }
+    WalkerSlot ws;
+    ws.id = (uint32_t)(w - __ldg(sg.start + lo));
+    ws.L = __ldg(sg.len + lo);
+    ws.k0 = __ldg(sg.key + 2 * lo);
+    ws.k1 = __ldg(sg.key + 2 * lo + 1);
+    ws.row0 = __ldg(sg.row0 + lo) + (uint64_t)ws.id * ((uint64_t)ws.L + 1);
+    return ws;
+}
+
 // The walks of a batch of requests (same bias) in one launch: d_starts holds
 // the n walkers of all requests in segment order, max_len is the longest
 // length.  Results are those of csaw_walk for each request alone.  Defined
@@ -143,9 +165,21 @@ void launch_partition_check(uint32_t* col, uint32_t* w, uint64_t ne, uint32_t V,
 
 // Walks that read a cached cumulative array (or, for uniform bias, none):
 // one thread per walker.  Defined in csaw_walk.cu.
-// cdf: the kind's cumulative array (cdf_words(E) words; ignored for uniform).
+// cdf: the kind's cumulative array (cdf_words(E, V) words; ignored for uniform).
+// Walkers w0 .. w0+n-1 of the call: starts and path point at walker w0's
+// entries, and walker w0 + i draws as walker w0 + i.  Defined in csaw_walk_cdf.cu.
 csaw_status launch_walk_cached(const csaw_graph* g, int kind, const uint64_t* cdf, const uint32_t* starts,
-                               uint64_t n, uint32_t length, uint64_t rng_seed, uint32_t* path, cudaStream_t s);
+                               uint64_t w0, uint64_t n, uint32_t length, uint64_t rng_seed, uint32_t* path,
+                               cudaStream_t s);
+// The same walks with the path matrix copied to host memory h_path: the
+// walkers run in a few chunks on s, and each chunk's rows are copied out on
+// a second stream while the next chunk walks.  Returns after the copies.
+csaw_status walk_cached_to_host(const csaw_graph* g, int kind, const uint64_t* cdf, const uint32_t* d_starts,
+                                uint64_t n, uint32_t length, uint64_t rng_seed, uint32_t* d_path,
+                                uint32_t* h_path, cudaStream_t s);
+// The batched form (several requests, WalkSegments) over the graph's cached array.
+csaw_status walk_batch_cached(const csaw_graph* g, int kind, const uint32_t* d_starts, uint64_t n,
+                              const WalkSegments& seg, uint32_t max_len, uint32_t* d_path, cudaStream_t s);
 
 // Whether selection/walks of this kind can use a cached cumulative array:
 // uniform always (implicit), edge weight / neighbour degree when built and
@@ -156,18 +190,46 @@ bool cached_cdf_usable(const csaw_graph* g, int kind);
 // or selecting over its cumulative array).
 bool cdf_kind_positive(const csaw_graph* g, int kind);
 
-// The cumulative array of a static kind: cdf[e] for e < E, CSAW_EDGE_PAD
-// padding words, then the summary S[g] = cdf[8g + 7] for 8g + 7 < E;
-// cdf_words(E) words in all.
-uint64_t cdf_words(uint64_t E);
-__host__ __device__ inline uint64_t* cdf_summary(uint64_t* cdf, uint64_t E) { return cdf + E + CSAW_EDGE_PAD; }
-__host__ __device__ inline const uint64_t* cdf_summary(const uint64_t* cdf, uint64_t E)
+// The cumulative array of a static kind and its search aids, in one
+// allocation of cdf_layout(E, V).words words (each part 64-byte aligned):
+//   cdf[E + pad]        inclusive row prefix sums, cdf[e] = b(row start) + ... + b(e)
+//   s1[(E+7)/8 + 8]     s1[g] = cdf[8g + 7]      for 8g + 7 < E
+//   s2[(E+63)/64 + 8]   s2[h] = cdf[64h + 63]    for 64h + 63 < E
+//   rec[V][4]           rec[v] = {off[v], off[v+1], row total, 0}: one 32-byte sector
+struct CdfLayout {
+    uint64_t s1, s2, rec, words;   // word offsets and the total
+};
+__host__ __device__ inline CdfLayout cdf_layout(uint64_t E, uint64_t V)
 {
-    return cdf + E + CSAW_EDGE_PAD;
+    CdfLayout L;
+    L.s1 = (E + CSAW_EDGE_PAD + 7) & ~7ull;
+    L.s2 = (L.s1 + (E + 7) / 8 + 8 + 7) & ~7ull;
+    L.rec = (L.s2 + (E + 63) / 64 + 8 + 7) & ~7ull;
+    L.words = L.rec + 4 * V;
+    return L;
 }
+struct CdfView {
+    const uint64_t* cdf = nullptr;
+    const uint64_t* s1 = nullptr;
+    const uint64_t* s2 = nullptr;
+    const uint64_t* rec = nullptr;
+};
+__host__ __device__ inline CdfView cdf_view(const uint64_t* base, uint64_t E, uint64_t V)
+{
+    CdfView c;
+    if (!base) return c;
+    const CdfLayout L = cdf_layout(E, V);
+    c.cdf = base;
+    c.s1 = base + L.s1;
+    c.s2 = base + L.s2;
+    c.rec = base + L.rec;
+    return c;
+}
+uint64_t cdf_words(uint64_t E, uint64_t V);
 
-// Enqueues the build of the cumulative array (and its summary) of a static
-// kind into cdf (cdf_words(E) words) on s; temporaries are stream-ordered.
+// Enqueues the build of the cumulative array of a static kind and its
+// search aids into cdf (cdf_words(E, V) words) on s; temporaries are
+// stream-ordered.
 csaw_status enqueue_cdf_build(const csaw_graph* g, int kind, uint64_t* cdf, cudaStream_t s);
 
 // Releases a result made by the request server (tagged "CSRV").
@@ -307,44 +369,68 @@ __device__ __forceinline__ bool sorted_contains(const uint32_t* __restrict__ col
     return beg < row_end && __ldg(col + beg) == u;
 }
 
-// Smallest e in [beg, end) with cdf[e] > x, for x < cdf[end - 1].  Groups
-// are the aligned runs of 8 edges; every summary entry sum[g] with
-// beg/8 <= g < (end-1)/8 is a prefix sum of this row, so bisecting them
-// finds the group of the hit (the last group when none exceeds x).  In that
-// group the row's positions [a, b) are read as two 32-byte halves, the
-// second only when every row position of the first is <= x; the hit is the
-// half's first row position plus its count of positions <= x (the row's
-// sums do not decrease).  Reads stay below 8 * ((end-1)/8) + 8 <= E + 7,
-// inside the array's padding.
-__device__ __forceinline__ uint64_t cdf_search(const uint64_t* __restrict__ cdf, const uint64_t* __restrict__ sum,
-                                               uint64_t beg, uint64_t end, uint64_t x)
+// First i in [lo, hi) with a[i] > x (hi if none), where [lo, hi) lies in
+// one aligned run a[8q .. 8q+7] and a does not decrease over [lo, hi):
+// the run is read as two 32-byte halves, the second only when every entry
+// of [lo, hi) in the first is <= x.  Reads a[8q .. 8q+7].  STREAM: loads
+// marked evict-first (lines unlikely to be read again soon).
+template <bool STREAM = false>
+__device__ __forceinline__ ulonglong2 ld_pair(const ulonglong2* p)
 {
-    uint64_t lo = beg >> 3, hi = (end - 1) >> 3;
+    if constexpr (STREAM) return __ldcs(p);
+    else return __ldg(p);
+}
+
+template <bool STREAM = false>
+__device__ __forceinline__ uint64_t first_above8(const uint64_t* __restrict__ a, uint64_t lo, uint64_t hi,
+                                                 uint64_t x)
+{
+    if (lo >= hi) return hi;
+    const uint64_t q = lo & ~7ull, mid = q + 4;
+    const ulonglong2* p = reinterpret_cast<const ulonglong2*>(a + q);
+    if (lo < mid) {
+        const ulonglong2 u0 = ld_pair<STREAM>(p), u1 = ld_pair<STREAM>(p + 1);
+        const uint64_t v[4] = {u0.x, u0.y, u1.x, u1.y};
+        const uint64_t h = hi < mid ? hi : mid;
+        uint32_t le = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) le += q + j >= lo && q + j < h && v[j] <= x;
+        if (lo + le < h || hi <= mid) return lo + le;
+        lo = mid;
+    }
+    const ulonglong2 u2 = ld_pair<STREAM>(p + 2), u3 = ld_pair<STREAM>(p + 3);
+    const uint64_t v[4] = {u2.x, u2.y, u3.x, u3.y};
+    uint32_t le = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) le += mid + j >= lo && mid + j < hi && v[j] <= x;
+    return lo + le;
+}
+
+// Smallest e in [beg, end) with cdf[e] > x, for x < cdf[end - 1] (a row of
+// the cumulative array of c).  Every s2[h] with beg/64 <= h < (end-1)/64,
+// and every s1[g] with beg/8 <= g < (end-1)/8, is a prefix sum of this row.
+// Bisecting the row's s2 entries finds the 64-edge block of the hit (the
+// row's last block when none exceeds x); that block's s1 entries in the row
+// (at most 7, one aligned run) give its 8-edge group, and the group's
+// entries in the row the edge.  Each step after the bisection reads one or
+// two 32-byte sectors; all reads stay inside the arrays and their padding.
+// STREAM_LEAF: the array's own sectors are read evict-first, so that they
+// do not push the summaries out of L2.
+template <bool STREAM_LEAF = false>
+__device__ __forceinline__ uint64_t cdf_search(const CdfView& c, uint64_t beg, uint64_t end, uint64_t x)
+{
+    uint64_t lo = beg >> 6, hi = (end - 1) >> 6;
     while (lo < hi) {
         const uint64_t mid = lo + ((hi - lo) >> 1);
-        if (__ldg(sum + mid) > x) hi = mid; else lo = mid + 1;
+        if (__ldg(c.s2 + mid) > x) hi = mid; else lo = mid + 1;
     }
-    const uint64_t gb = lo << 3;
-    const uint64_t a = gb > beg ? gb : beg;
-    const uint64_t b = gb + 8 < end ? gb + 8 : end;
-    const ulonglong2* q = reinterpret_cast<const ulonglong2*>(cdf + gb);
-    const ulonglong2 u0 = __ldg(q), u1 = __ldg(q + 1);
-    const uint64_t h0[4] = {u0.x, u0.y, u1.x, u1.y};
-    uint32_t valid = 0, le = 0;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const bool in = gb + j >= a && gb + j < b;
-        valid += in;
-        le += in && h0[j] <= x;
-    }
-    if (le < valid) return a + le;
-    const ulonglong2 u2 = __ldg(q + 2), u3 = __ldg(q + 3);
-    const uint64_t h1[4] = {u2.x, u2.y, u3.x, u3.y};
-    const uint64_t a1 = a > gb + 4 ? a : gb + 4;
-    uint32_t le1 = 0;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) le1 += gb + 4 + j >= a1 && gb + 4 + j < b && h1[j] <= x;
-    return a1 + le1;
+    const uint64_t g_lo = (lo << 3) > (beg >> 3) ? (lo << 3) : (beg >> 3);
+    const uint64_t g_end = (end - 1) >> 3;
+    const uint64_t g_hi = (lo << 3) + 7 < g_end ? (lo << 3) + 7 : g_end;
+    const uint64_t g = first_above8(c.s1, g_lo, g_hi, x);
+    const uint64_t e_lo = (g << 3) > beg ? (g << 3) : beg;
+    const uint64_t e_hi = (g << 3) + 8 < end ? (g << 3) + 8 : end;
+    return first_above8<STREAM_LEAF>(c.cdf, e_lo, e_hi, x);
 }
 
 }  // namespace csaw

@@ -105,7 +105,7 @@ struct SelParams {
     const uint64_t* __restrict__ hub_off = nullptr;
     const uint64_t* __restrict__ hubS = nullptr;
     uint64_t hubS_cap = 0;                // entries of hubS
-    const uint64_t* __restrict__ cdf_sum = nullptr;   // the cached array's summary (sum[g] = cdf[8g + 7])
+    CdfView cv;                           // the cached array and its search aids (cv.cdf == cdf)
     uint32_t* err = nullptr;              // error flags (8: a hub range beyond hubS_cap)
     // instances of several requests in one run (null: one request): per
     // instance its Philox key, its index within its request (the draw
@@ -430,7 +430,9 @@ __device__ __forceinline__ uint64_t cdf_at(const uint64_t* __restrict__ row, boo
     return implicit ? (uint64_t)i + 1 : __ldg(row + i);
 }
 
-template <bool IMPLICIT>
+// CACHED: rows of the graph's cumulative array, searched through its
+// summaries (cdf_search); otherwise bisected directly (shared hub arrays).
+template <bool IMPLICIT, bool CACHED = false>
 __global__ void __launch_bounds__(SEL_THREADS, 8) select_cdf_kernel(SelParams p)
 {
     __shared__ uint32_t s_picks[SEL_WARPS][PICK_MAX];
@@ -480,8 +482,8 @@ __global__ void __launch_bounds__(SEL_THREADS, 8) select_cdf_kernel(SelParams p)
             if (!live) {
             } else if (IMPLICIT) {
                 i = (uint32_t)x;
-            } else if (p.cdf_sum && row == p.cdf + beg) {
-                i = (uint32_t)(cdf_search(p.cdf, p.cdf_sum, beg, beg + d, x) - beg);   // the cached array
+            } else if (CACHED) {
+                i = (uint32_t)(cdf_search(p.cv, beg, beg + d, x) - beg);   // the cached array
             } else {
                 uint32_t lo = 0, hi = d - 1;
                 while (lo < hi) {
@@ -1498,7 +1500,8 @@ struct Pipeline {
         select_shape(g, kind, &theta_w, &sel_blocks);
         cached = cached_cdf_usable(g, kind);
         hub_path = !cached && (kind == CSAW_BIAS_EDGE_WEIGHT || kind == CSAW_BIAS_NEIGHBOR_DEGREE);
-        hub_order = cached && (kind == CSAW_BIAS_EDGE_WEIGHT || kind == CSAW_BIAS_NEIGHBOR_DEGREE);
+        // vertex order pays only when several instances can hold the same hub
+        hub_order = cached && n_inst > 1 && (kind == CSAW_BIAS_EDGE_WEIGHT || kind == CSAW_BIAS_NEIGHBOR_DEGREE);
         // CTA items exist for picks above PICK_MAX (or, without the hub
         // path, any long row); only rows above CTA_SMEM_DEG need a slot
         bool big_k = false;
@@ -1633,7 +1636,7 @@ static csaw_status enqueue_select_items(Pipeline& P, uint32_t l, cudaStream_t s)
         sp.out_src = B.src; sp.out_dst = B.dst; sp.out_cand = (l + 1 < P.depth) ? B.cand : nullptr;
         sp.scratch_S = P.hub_S; sp.scratch_bits = P.hub_bits; sp.scratch_stride = g->max_degree;
         sp.cdf = P.cached && P.kind != CSAW_BIAS_UNIFORM ? g->cdf[P.kind] : nullptr;
-    sp.cdf_sum = sp.cdf ? cdf_summary(sp.cdf, g->E) : nullptr;
+    sp.cv = cdf_view(sp.cdf, g->E, g->V);
         sp.skip_warp_items = P.cached;
         sp.attempt_cap = P.attempt_cap;
         sp.inst_key = P.inst_key; sp.inst_id = P.inst_id;
@@ -1643,12 +1646,12 @@ static csaw_status enqueue_select_items(Pipeline& P, uint32_t l, cudaStream_t s)
             // picks) by the streaming kernel below
             const int blocks = g->sm_count * 8;
             if (P.kind == CSAW_BIAS_UNIFORM) select_cdf_kernel<true><<<blocks, SEL_THREADS, 0, s>>>(sp);
-            else select_cdf_kernel<false><<<blocks, SEL_THREADS, 0, s>>>(sp);
+            else select_cdf_kernel<false, true><<<blocks, SEL_THREADS, 0, s>>>(sp);
             if (P.hub_order) {
                 // the hub items in vertex order, over the same array
                 SelParams hs = sp;
                 hs.item_e = P.item_e;
-                select_cdf_kernel<false><<<blocks, SEL_THREADS, 0, s>>>(hs);
+                select_cdf_kernel<false, true><<<blocks, SEL_THREADS, 0, s>>>(hs);
             }
             CSAW_CUDA(cudaGetLastError());
         }
@@ -1822,7 +1825,7 @@ static LayerSelParams layer_params(const Pipeline& P, uint32_t l)
     sp.zero_bias = P.zero_bias; sp.pos = B.pos;
     sp.out_src = B.src; sp.out_dst = B.dst; sp.out_cand = (l + 1 < P.depth) ? B.cand : nullptr;
     sp.cdf = P.cached && P.kind != CSAW_BIAS_UNIFORM ? g->cdf[P.kind] : nullptr;
-    sp.cdf_sum = sp.cdf ? cdf_summary(sp.cdf, g->E) : nullptr;
+    sp.cv = cdf_view(sp.cdf, g->E, g->V);
     sp.attempt_cap = P.attempt_cap;
     lp.FO = B.FO;
     lp.n_inst = P.n_inst;

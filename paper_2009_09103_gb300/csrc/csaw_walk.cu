@@ -14,7 +14,8 @@
 // Rows that fit one round stay in registers and need one pass.
 //
 // Work distribution: a persistent grid; each warp takes the next walker from
-// a global counter and runs all its steps.  The path row is buffered one
+// a global counter and runs all its steps.  (Walks over a cached cumulative
+// array are in csaw_walk_cdf.cu.)  The path row is buffered one
 // 32-entry block per warp (lane j holds entry 32*blk + j) and written with
 // one coalesced store per block.
 #include <atomic>
@@ -36,28 +37,6 @@ constexpr uint32_t CHUNK_SLOTS = 256;       // chunk prefixes per warp (shared m
 #define CSAW_WALK_UNROLL 1
 #endif
 constexpr int PASS1_UNROLL = CSAW_WALK_UNROLL;   // rounds of pass 1 in flight
-
-// Which segment walker w is in, and its place there.
-struct WalkerSlot {
-    uint32_t k0, k1, id, L;
-    uint64_t row0;
-};
-
-__device__ __forceinline__ WalkerSlot walker_slot(const WalkSegments& sg, uint64_t w)
-{
-    uint32_t lo = 0, hi = sg.n;   // last r with start[r] <= w
-    while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (__ldg(sg.start + mid) <= w) lo = mid; else hi = mid;
-    }
-    WalkerSlot ws;
-    ws.id = (uint32_t)(w - __ldg(sg.start + lo));
-    ws.L = __ldg(sg.len + lo);
-    ws.k0 = __ldg(sg.key + 2 * lo);
-    ws.k1 = __ldg(sg.key + 2 * lo + 1);
-    ws.row0 = __ldg(sg.row0 + lo) + (uint64_t)ws.id * ((uint64_t)ws.L + 1);
-    return ws;
-}
 
 struct WalkParams {
     const uint64_t* __restrict__ off;
@@ -902,202 +881,14 @@ static csaw_status launch_walk_batch(int kind, uint64_t max_bias, const WalkPara
 }
 
 
-// ---------------------------------------------------------------------------
-// Walks over a cached cumulative array (static biases): one thread per
-// walker.  A step loads the row's total T = cdf[end-1], maps the draw to x
-// and binary-searches the row's prefix sums (uniform bias: the pick is x),
-// so its cost is O(log d) dependent loads instead of a stream over the row;
-// 32 walkers per warp keep many searches in flight.  The picks are those of
-// the streaming kernel: the same prefix sums and the same draws.
-//
-// Path stores: a warp's 32 walkers (consecutive rows) stage their next 16
-// path entries in a shared-memory tile, one tile row per walker; when the
-// tile is full (or the walk ends) the warp writes it out two walkers at a
-// time, each walker's entries as 64 consecutive bytes of its row.  Stores
-// from one thread per walker would put 32 different rows behind every warp
-// store, each sector written a few bytes at a time.
-constexpr int WC_THREADS = 256;
-constexpr int WC_WARPS = WC_THREADS / 32;
-constexpr int WC_TILE = 16;                  // path entries staged per walker
-
-struct WalkCdfParams {
-    const uint64_t* __restrict__ off;
-    const uint32_t* __restrict__ col;
-    const uint64_t* __restrict__ cdf;   // null for uniform bias
-    const uint64_t* __restrict__ sum;   // its summary: sum[g] = cdf[8g + 7]
-    uint32_t V;
-    const uint32_t* __restrict__ starts;
-    uint64_t n;
-    uint32_t L;
-    uint32_t* __restrict__ path;
-    PhiloxKeys keys;
-    WalkSegments seg;                    // batched kernel: several requests in one launch
-};
-
-// Writes the staged entries t in [t0, t_end) of the warp's walkers base ..
-// base + 31 (those below n): per iteration, lanes 0-15 store 16 consecutive
-// entries of one walker's row and lanes 16-31 those of the next walker.
-__device__ __forceinline__ void walk_tile_flush(const WalkCdfParams& p, uint32_t (*tile)[WC_TILE + 1],
-                                                uint64_t base, uint64_t row_len, uint64_t t0, uint64_t t_end,
-                                                int lane)
-{
-    __syncwarp();
-    const int half = lane >> 4, c = lane & 15;
-    const uint64_t t = t0 + (uint64_t)c;
-    uint64_t wk = base + (uint64_t)half;
-    uint32_t* out = p.path + wk * row_len + t;
-    const uint64_t step = 2 * row_len;
-#pragma unroll 2
-    for (int i = half; i < 32; i += 2) {
-        if (wk < p.n && t < t_end) *out = tile[i][c];
-        wk += 2;
-        out += step;
-    }
-    __syncwarp();
-}
-
-// The same for a batch, where each walker has its own row start (row0,
-// relative to path) and row length (rl, 0 for lanes without a walker).
-__device__ __forceinline__ void walk_tile_flush_rows(const WalkCdfParams& p, uint32_t (*tile)[WC_TILE + 1],
-                                                     uint64_t row0, uint64_t rl, uint64_t t0, int lane)
-{
-    __syncwarp();
-    const int half = lane >> 4, c = lane & 15;
-    const uint64_t t = t0 + (uint64_t)c;
-#pragma unroll 2
-    for (int i0 = 0; i0 < 32; i0 += 2) {
-        const int i = i0 + half;
-        const uint64_t r0 = __shfl_sync(CSAW_FULL_MASK, row0, i);
-        const uint64_t n = __shfl_sync(CSAW_FULL_MASK, rl, i);
-        if (t < n) p.path[r0 + t] = tile[i][c];
-    }
-    __syncwarp();
-}
-
-template <bool UNIFORM, bool BATCH = false>
-__global__ void __launch_bounds__(WC_THREADS) walk_cached_kernel(WalkCdfParams p)
-{
-    __shared__ uint32_t s_tile[WC_WARPS][32][WC_TILE + 1];   // +1: conflict-free column writes
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    uint32_t (*tile)[WC_TILE + 1] = s_tile[wid];
-    const uint64_t row_len = (uint64_t)p.L + 1;
-    const uint64_t n_warps = (uint64_t)gridDim.x * WC_WARPS;
-    for (uint64_t base = ((uint64_t)blockIdx.x * WC_WARPS + wid) * 32; base < p.n; base += n_warps * 32) {
-        const uint64_t wk = base + (uint64_t)lane;
-        // batch: this lane's request (key, index, length) and row; the warp
-        // runs to the longest length among its lanes
-        WalkerSlot ws{};
-        uint32_t L = p.L;
-        uint64_t rl = 0;
-        if constexpr (BATCH) {
-            if (wk < p.n) {
-                ws = walker_slot(p.seg, wk);
-                rl = (uint64_t)ws.L + 1;
-            }
-            L = __reduce_max_sync(CSAW_FULL_MASK, ws.L);
-        }
-        // alive: still walking; cur = CSAW_NONE once stopped (or never started)
-        uint32_t cur = wk < p.n ? __ldg(p.starts + wk) : CSAW_NONE;
-        if (cur >= p.V) cur = CSAW_NONE;
-        bool alive = cur != CSAW_NONE;
-        tile[lane][0] = cur;
-        uint64_t t0 = 0;                   // path position of tile column 0
-        for (uint32_t s = 0; s < L; ++s) {
-            if constexpr (BATCH) alive = alive && s < ws.L;
-            if (alive) {
-                const uint64_t beg = __ldg(p.off + cur);
-                const uint64_t end = __ldg(p.off + cur + 1);
-                bool stop = beg == end;
-                uint64_t i = 0;
-                if (!stop) {
-                    uint64_t r;
-                    if constexpr (BATCH) r = philox_draw(ws.k0, ws.k1, 0u, cur, s, ws.id);
-                    else r = philox_draw(p.keys, 0u, cur, s, (uint32_t)wk);
-                    if constexpr (UNIFORM) {
-                        i = scale_draw(r, end - beg);
-                    } else {
-                        const uint64_t T = __ldg(p.cdf + end - 1);
-                        stop = T == 0;
-                        if (!stop) {
-                            const uint64_t x = scale_draw(r, T);
-                            i = cdf_search(p.cdf, p.sum, beg, end, x) - beg;
-                        }
-                    }
-                }
-                if (stop) { alive = false; cur = CSAW_NONE; }
-                else cur = __ldg(p.col + beg + i);
-            }
-            const uint64_t t = (uint64_t)s + 1;      // path position of this step's vertex
-            tile[lane][t - t0] = cur;
-            if (t - t0 == WC_TILE - 1 || t == L) {
-                if constexpr (BATCH) walk_tile_flush_rows(p, tile, ws.row0, rl, t0, lane);
-                else walk_tile_flush(p, tile, base, row_len, t0, t + 1, lane);
-                t0 = t + 1;
-            }
-        }
-        if (L == 0) {
-            if constexpr (BATCH) walk_tile_flush_rows(p, tile, ws.row0, rl, 0, lane);
-            else walk_tile_flush(p, tile, base, row_len, 0, 1, lane);
-        }
-    }
-}
-
-template <bool UNIFORM, bool BATCH>
-static csaw_status launch_walk_cached_k(const WalkCdfParams& p, int sm_count, cudaStream_t s)
-{
-    static std::atomic<int> cached{0};
-    int per_sm = cached.load(std::memory_order_acquire);
-    if (per_sm == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_cached_kernel<UNIFORM, BATCH>,
-                                                                      WC_THREADS, 0);
-        if (e != cudaSuccess) return cuda_fail(e, "occupancy(walk_cached)");
-        if (per_sm < 1) per_sm = 1;
-        cached.store(per_sm, std::memory_order_release);
-    }
-    uint64_t blocks = (p.n + WC_THREADS - 1) / WC_THREADS;
-    uint64_t cap = (uint64_t)sm_count * per_sm;
-    if (BATCH && p.seg.warp_budget) {
-        // each warp walks at most warp_budget groups of 32 walkers
-        const uint64_t per_block = (uint64_t)WC_THREADS * p.seg.warp_budget;
-        cap = (p.n + per_block - 1) / per_block;
-    }
-    if (blocks > cap) blocks = cap;
-    if (blocks < 1) blocks = 1;
-    walk_cached_kernel<UNIFORM, BATCH><<<(unsigned)blocks, WC_THREADS, 0, s>>>(p);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "walk_cached_kernel launch");
-    return CSAW_OK;
-}
-
-csaw_status launch_walk_cached(const csaw_graph* g, int kind, const uint64_t* cdf, const uint32_t* starts,
-                               uint64_t n, uint32_t length, uint64_t rng_seed, uint32_t* path, cudaStream_t s)
-{
-    WalkCdfParams p;
-    p.off = g->off; p.col = g->col; p.cdf = kind == CSAW_BIAS_UNIFORM ? nullptr : cdf;
-    p.sum = p.cdf ? cdf_summary(p.cdf, g->E) : nullptr;
-    p.V = g->V; p.starts = starts; p.n = n; p.L = length; p.path = path;
-    p.keys = philox_round_keys(rng_seed);
-    p.seg = WalkSegments{};
-    return kind == CSAW_BIAS_UNIFORM ? launch_walk_cached_k<true, false>(p, g->sm_count, s)
-                                     : launch_walk_cached_k<false, false>(p, g->sm_count, s);
-}
-
 csaw_status walk_batch(const csaw_graph* g, const csaw_bias* bias, const uint32_t* d_starts, uint64_t n,
                        const WalkSegments& seg, uint32_t max_len, uint32_t* d_path, cudaStream_t s)
 {
     int kind;
     CSAW_TRY(check_bias(g, bias, true, &kind));
     if (n == 0) return CSAW_OK;
-    if (kind != CSAW_BIAS_NODE2VEC && cached_cdf_usable(g, kind)) {
-        WalkCdfParams p;
-        p.off = g->off; p.col = g->col; p.cdf = kind == CSAW_BIAS_UNIFORM ? nullptr : g->cdf[kind];
-        p.sum = p.cdf ? cdf_summary(p.cdf, g->E) : nullptr;
-        p.V = g->V; p.starts = d_starts; p.n = n; p.L = max_len; p.path = d_path;
-        p.keys = philox_round_keys(0);
-        p.seg = seg;
-        return kind == CSAW_BIAS_UNIFORM ? launch_walk_cached_k<true, true>(p, g->sm_count, s)
-                                         : launch_walk_cached_k<false, true>(p, g->sm_count, s);
-    }
+    if (kind != CSAW_BIAS_NODE2VEC && cached_cdf_usable(g, kind))
+        return walk_batch_cached(g, kind, d_starts, n, seg, max_len, d_path, s);
     void* counter = nullptr;
     CSAW_TRY(dalloc(&counter, sizeof(unsigned long long), s));
     csaw_status st = CSAW_OK;
@@ -1181,19 +972,21 @@ extern "C" csaw_status csaw_walk_ex(csaw_graph* g, const uint32_t* starts, uint6
         void* tmp = nullptr;
         csaw_status st = CSAW_OK;
         if (build) {
-            st = dalloc(&tmp, sizeof(uint64_t) * cdf_words(g->E), s);
+            st = dalloc(&tmp, sizeof(uint64_t) * cdf_words(g->E, g->V), s);
             if (st == CSAW_OK) st = enqueue_cdf_build(g, kind, (uint64_t*)tmp, s);
             cdf = (const uint64_t*)tmp;
         }
-        // thread per walker
-        if (st == CSAW_OK) st = launch_walk_cached(g, kind, cdf, d_starts, n_walkers, length, rng_seed, d_path, s);
+        // thread per walker; host paths come back chunk by chunk while the
+        // next chunk walks
+        if (st == CSAW_OK) {
+            if (mem_kind == CSAW_MEM_HOST)
+                st = walk_cached_to_host(g, kind, cdf, d_starts, n_walkers, length, rng_seed, d_path, path, s);
+            else
+                st = launch_walk_cached(g, kind, cdf, d_starts, 0, n_walkers, length, rng_seed, d_path, s);
+        }
         dfree(tmp, s);
         if (mem_kind == CSAW_MEM_HOST) {
-            if (st == CSAW_OK) {
-                cudaError_t e = cudaMemcpyAsync(path, d_path, path_bytes, cudaMemcpyDeviceToHost, s);
-                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-                if (e != cudaSuccess) st = cuda_fail(e, "copy path");
-            }
+            if (st != CSAW_OK) cudaStreamSynchronize(s);
             dfree((void*)d_starts, s);
             dfree(d_path, s);
         }

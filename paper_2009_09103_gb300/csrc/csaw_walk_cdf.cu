@@ -1,0 +1,270 @@
+// csaw_walk_cdf.cu -- random walks over a static bias's cumulative array
+// (Sec. II-A, II-B: the CTPS of every row built once, then searched).
+#include <atomic>
+
+#include "csaw_internal.cuh"
+
+namespace csaw {
+
+// ---------------------------------------------------------------------------
+// Walks over a cached cumulative array (static biases): one thread per
+// walker.  A step reads the vertex's record {row start, row end, row total}
+// (one 32-byte sector), maps the draw to x and searches the row's prefix
+// sums through their summaries (cdf_search; uniform bias: the pick is x),
+// so its cost is a few dependent loads instead of a stream over the row;
+// 32 walkers per warp keep many searches in flight.  The picks are those of
+// the streaming kernel: the same prefix sums and the same draws.
+//
+// Path stores: a warp's 32 walkers (consecutive rows) stage their next 16
+// path entries in a shared-memory tile, one tile row per walker; when the
+// tile is full (or the walk ends) the warp writes it out two walkers at a
+// time, each walker's entries as 64 consecutive bytes of its row.  Stores
+// from one thread per walker would put 32 different rows behind every warp
+// store, each sector written a few bytes at a time.
+//
+// L2 residency: the records and summaries (about 9 bytes per edge / 8 + 32
+// per vertex) are what walkers at the same hubs re-read; the array's own
+// sectors, the picked columns and the path rows are touched once.  Those are
+// read and written evict-first (ld/st .cs) so that they pass through L2
+// without pushing the summaries out.
+constexpr int WC_THREADS = 256;
+constexpr int WC_WARPS = WC_THREADS / 32;
+constexpr int WC_TILE = 16;                  // path entries staged per walker
+
+struct WalkCdfParams {
+    const uint64_t* __restrict__ off;
+    const uint32_t* __restrict__ col;
+    CdfView c;                           // the cumulative array (cdf null for uniform bias)
+    uint32_t V;
+    const uint32_t* __restrict__ starts;
+    uint64_t n;
+    uint32_t L;
+    uint32_t* __restrict__ path;
+    uint32_t w0;                         // the call's index of walker 0 of this launch (its draws)
+    PhiloxKeys keys;
+    WalkSegments seg;                    // batched kernel: several requests in one launch
+};
+
+// Writes the staged entries t in [t0, t_end) of the warp's walkers base ..
+// base + 31 (those below n): per iteration, lanes 0-15 store 16 consecutive
+// entries of one walker's row and lanes 16-31 those of the next walker.
+__device__ __forceinline__ void walk_tile_flush(const WalkCdfParams& p, uint32_t (*tile)[WC_TILE + 1],
+                                                uint64_t base, uint64_t row_len, uint64_t t0, uint64_t t_end,
+                                                int lane)
+{
+    __syncwarp();
+    const int half = lane >> 4, c = lane & 15;
+    const uint64_t t = t0 + (uint64_t)c;
+    uint64_t wk = base + (uint64_t)half;
+    uint32_t* out = p.path + wk * row_len + t;
+    const uint64_t step = 2 * row_len;
+#pragma unroll 2
+    for (int i = half; i < 32; i += 2) {
+        if (wk < p.n && t < t_end) __stcs(out, tile[i][c]);
+        wk += 2;
+        out += step;
+    }
+    __syncwarp();
+}
+
+// The same for a batch, where each walker has its own row start (row0,
+// relative to path) and row length (rl, 0 for lanes without a walker).
+__device__ __forceinline__ void walk_tile_flush_rows(const WalkCdfParams& p, uint32_t (*tile)[WC_TILE + 1],
+                                                     uint64_t row0, uint64_t rl, uint64_t t0, int lane)
+{
+    __syncwarp();
+    const int half = lane >> 4, c = lane & 15;
+    const uint64_t t = t0 + (uint64_t)c;
+#pragma unroll 2
+    for (int i0 = 0; i0 < 32; i0 += 2) {
+        const int i = i0 + half;
+        const uint64_t r0 = __shfl_sync(CSAW_FULL_MASK, row0, i);
+        const uint64_t n = __shfl_sync(CSAW_FULL_MASK, rl, i);
+        if (t < n) p.path[r0 + t] = tile[i][c];
+    }
+    __syncwarp();
+}
+
+template <bool UNIFORM, bool BATCH = false>
+__global__ void __launch_bounds__(WC_THREADS, 6) walk_cached_kernel(WalkCdfParams p)
+{
+    __shared__ uint32_t s_tile[WC_WARPS][32][WC_TILE + 1];   // +1: conflict-free column writes
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t (*tile)[WC_TILE + 1] = s_tile[wid];
+    const uint64_t row_len = (uint64_t)p.L + 1;
+    const uint64_t n_warps = (uint64_t)gridDim.x * WC_WARPS;
+    for (uint64_t base = ((uint64_t)blockIdx.x * WC_WARPS + wid) * 32; base < p.n; base += n_warps * 32) {
+        const uint64_t wk = base + (uint64_t)lane;
+        // batch: this lane's request (key, index, length) and row; the warp
+        // runs to the longest length among its lanes
+        WalkerSlot ws{};
+        uint32_t L = p.L;
+        uint64_t rl = 0;
+        if constexpr (BATCH) {
+            if (wk < p.n) {
+                ws = walker_slot(p.seg, wk);
+                rl = (uint64_t)ws.L + 1;
+            }
+            L = __reduce_max_sync(CSAW_FULL_MASK, ws.L);
+        }
+        // alive: still walking; cur = CSAW_NONE once stopped (or never started)
+        uint32_t cur = wk < p.n ? __ldg(p.starts + wk) : CSAW_NONE;
+        if (cur >= p.V) cur = CSAW_NONE;
+        bool alive = cur != CSAW_NONE;
+        tile[lane][0] = cur;
+        uint64_t t0 = 0;                   // path position of tile column 0
+        for (uint32_t s = 0; s < L; ++s) {
+            if constexpr (BATCH) alive = alive && s < ws.L;
+            if (alive) {
+                // the row: offsets (uniform) or the vertex's record {start, end, total}
+                uint64_t beg, end, T = 0;
+                if constexpr (UNIFORM) {
+                    beg = __ldg(p.off + cur);
+                    end = __ldg(p.off + cur + 1);
+                } else {
+                    const ulonglong2* rc = reinterpret_cast<const ulonglong2*>(p.c.rec + 4ull * cur);
+                    const ulonglong2 r0 = __ldg(rc), r1 = __ldg(rc + 1);
+                    beg = r0.x;
+                    end = r0.y;
+                    T = r1.x;
+                }
+                bool stop = beg == end;
+                uint64_t i = 0;
+                if (!stop) {
+                    uint64_t r;
+                    if constexpr (BATCH) r = philox_draw(ws.k0, ws.k1, 0u, cur, s, ws.id);
+                    else r = philox_draw(p.keys, 0u, cur, s, p.w0 + (uint32_t)wk);
+                    if constexpr (UNIFORM) {
+                        i = scale_draw(r, end - beg);
+                    } else {
+                        stop = T == 0;
+                        if (!stop) i = cdf_search<true>(p.c, beg, end, scale_draw(r, T)) - beg;
+                    }
+                }
+                if (stop) { alive = false; cur = CSAW_NONE; }
+                else cur = __ldcs(p.col + beg + i);
+            }
+            const uint64_t t = (uint64_t)s + 1;      // path position of this step's vertex
+            tile[lane][t - t0] = cur;
+            if (t - t0 == WC_TILE - 1 || t == L) {
+                if constexpr (BATCH) walk_tile_flush_rows(p, tile, ws.row0, rl, t0, lane);
+                else walk_tile_flush(p, tile, base, row_len, t0, t + 1, lane);
+                t0 = t + 1;
+            }
+        }
+        if (L == 0) {
+            if constexpr (BATCH) walk_tile_flush_rows(p, tile, ws.row0, rl, 0, lane);
+            else walk_tile_flush(p, tile, base, row_len, 0, 1, lane);
+        }
+    }
+}
+
+template <bool UNIFORM, bool BATCH>
+static csaw_status launch_walk_cached_k(const WalkCdfParams& p, int sm_count, cudaStream_t s)
+{
+    static std::atomic<int> cached{0};
+    int per_sm = cached.load(std::memory_order_acquire);
+    if (per_sm == 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_cached_kernel<UNIFORM, BATCH>,
+                                                                      WC_THREADS, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "occupancy(walk_cached)");
+        if (per_sm < 1) per_sm = 1;
+        cached.store(per_sm, std::memory_order_release);
+    }
+    uint64_t blocks = (p.n + WC_THREADS - 1) / WC_THREADS;
+    uint64_t cap = (uint64_t)sm_count * per_sm;
+    if (BATCH && p.seg.warp_budget) {
+        // each warp walks at most warp_budget groups of 32 walkers
+        const uint64_t per_block = (uint64_t)WC_THREADS * p.seg.warp_budget;
+        cap = (p.n + per_block - 1) / per_block;
+    }
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    walk_cached_kernel<UNIFORM, BATCH><<<(unsigned)blocks, WC_THREADS, 0, s>>>(p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "walk_cached_kernel launch");
+    return CSAW_OK;
+}
+
+csaw_status launch_walk_cached(const csaw_graph* g, int kind, const uint64_t* cdf, const uint32_t* starts,
+                               uint64_t w0, uint64_t n, uint32_t length, uint64_t rng_seed, uint32_t* path,
+                               cudaStream_t s)
+{
+    WalkCdfParams p;
+    p.off = g->off; p.col = g->col;
+    p.c = cdf_view(kind == CSAW_BIAS_UNIFORM ? nullptr : cdf, g->E, g->V);
+    p.V = g->V; p.starts = starts; p.n = n; p.L = length; p.path = path;
+    p.w0 = (uint32_t)w0;
+    p.keys = philox_round_keys(rng_seed);
+    p.seg = WalkSegments{};
+    return kind == CSAW_BIAS_UNIFORM ? launch_walk_cached_k<true, false>(p, g->sm_count, s)
+                                     : launch_walk_cached_k<false, false>(p, g->sm_count, s);
+}
+
+// Chunks of at least WC_CHUNK_MIN walkers keep the persistent grid full
+// (the kernel is latency-bound); at most WC_CHUNKS of them.
+constexpr uint64_t WC_CHUNK_MIN = 1ull << 18;
+constexpr uint64_t WC_CHUNKS = 4;
+
+csaw_status walk_cached_to_host(const csaw_graph* g, int kind, const uint64_t* cdf, const uint32_t* d_starts,
+                                uint64_t n, uint32_t length, uint64_t rng_seed, uint32_t* d_path,
+                                uint32_t* h_path, cudaStream_t s)
+{
+    const uint64_t row_len = (uint64_t)length + 1;
+    uint64_t k = n / WC_CHUNK_MIN;
+    k = k < 1 ? 1 : (k > WC_CHUNKS ? WC_CHUNKS : k);
+    const uint64_t chunk = ((n + k - 1) / k + 31) & ~31ull;
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev[WC_CHUNKS] = {};
+    csaw_status st = CSAW_OK;
+    cudaError_t e = cudaSuccess;
+    if (k > 1) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    for (uint64_t c = 0; e == cudaSuccess && c < k && k > 1; ++c) e = cudaEventCreateWithFlags(&ev[c], cudaEventDisableTiming);
+    if (e != cudaSuccess) st = cuda_fail(e, "copy stream");
+    // every chunk's walk first (the copies of pageable memory block the host)
+    uint64_t n_chunks = 0;
+    for (uint64_t w0 = 0; st == CSAW_OK && w0 < n; w0 += chunk, ++n_chunks) {
+        const uint64_t m = n - w0 < chunk ? n - w0 : chunk;
+        st = launch_walk_cached(g, kind, cdf, d_starts + w0, w0, m, length, rng_seed, d_path + w0 * row_len, s);
+        if (st == CSAW_OK && k > 1) {
+            e = cudaEventRecord(ev[n_chunks], s);
+            if (e != cudaSuccess) st = cuda_fail(e, "chunk event");
+        }
+    }
+    // then each chunk's rows, on the copy stream once the chunk is done
+    for (uint64_t c = 0, w0 = 0; st == CSAW_OK && w0 < n; w0 += chunk, ++c) {
+        const uint64_t m = n - w0 < chunk ? n - w0 : chunk;
+        cudaStream_t q = k > 1 ? cs : s;
+        if (k > 1) e = cudaStreamWaitEvent(cs, ev[c], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h_path + w0 * row_len, d_path + w0 * row_len, sizeof(uint32_t) * m * row_len,
+                                cudaMemcpyDeviceToHost, q);
+        if (e != cudaSuccess) st = cuda_fail(e, "copy path");
+    }
+    if (k > 1) {
+        e = cudaStreamSynchronize(cs);
+        if (e != cudaSuccess && st == CSAW_OK) st = cuda_fail(e, "copy path");
+    }
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess && st == CSAW_OK) st = cuda_fail(e, "walk");
+    for (uint64_t c = 0; c < k && k > 1; ++c)
+        if (ev[c]) cudaEventDestroy(ev[c]);
+    if (cs) cudaStreamDestroy(cs);
+    return st;
+}
+
+csaw_status walk_batch_cached(const csaw_graph* g, int kind, const uint32_t* d_starts, uint64_t n,
+                              const WalkSegments& seg, uint32_t max_len, uint32_t* d_path, cudaStream_t s)
+{
+    WalkCdfParams p;
+    p.off = g->off; p.col = g->col;
+    p.c = cdf_view(kind == CSAW_BIAS_UNIFORM ? nullptr : g->cdf[kind], g->E, g->V);
+    p.V = g->V; p.starts = d_starts; p.n = n; p.L = max_len; p.path = d_path;
+    p.w0 = 0;
+    p.keys = philox_round_keys(0);
+    p.seg = seg;
+    return kind == CSAW_BIAS_UNIFORM ? launch_walk_cached_k<true, true>(p, g->sm_count, s)
+                                     : launch_walk_cached_k<false, true>(p, g->sm_count, s);
+}
+
+}  // namespace csaw

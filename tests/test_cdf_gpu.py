@@ -94,6 +94,28 @@ def test_walk_build_per_call_equals_cached_on_device(csaw):
     G.close()
 
 
+@pytest.mark.parametrize("n,build", [(600_000, True), (1_100_003, False), (262_145, True)])
+def test_host_walk_in_chunks_with_overlapped_copies(csaw, n, build):
+    """Host inputs and outputs over a cumulative array: the walkers run in
+    chunks (each chunk's rows copied out while the next walks), every walker
+    keeping its own draws -- the paths equal the device call's and the
+    oracle's, ragged last chunk included."""
+    import torch
+    g = inputs.rmat_csr(14, 16, 255, 14)
+    G = csaw.Graph(g.off, g.col, g.w)
+    if not build:
+        G.build_cdf("edge_weight")
+    starts = inputs.uniform_vertices(n, g.V, 6)
+    host = csaw.walk(G, starts, 10, "edge_weight", 21, build_cdf=build)
+    dev = csaw.walk(G, torch.from_numpy(starts.view(np.int32)).cuda(), 10, "edge_weight", 21, build_cdf=build)
+    assert np.array_equal(host, dev.cpu().numpy().view(np.uint32))
+    pick = np.unique(np.concatenate([np.arange(0, n, 9973), [n - 1, n // 2, 262_143, 262_144]])).astype(np.int64)
+    pick = pick[pick < n]
+    ref = oracle.walk(g, starts[pick], 10, "edge_weight", 21, walker_ids=pick.astype(np.uint64))
+    assert np.array_equal(host[pick], ref)
+    G.close()
+
+
 @pytest.mark.parametrize("bias", ["edge_weight", "uniform"])
 def test_cached_walk_tile_boundaries_and_dead_ends(csaw, bias):
     """Path rows are staged 16 entries at a time per walker and written out
