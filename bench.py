@@ -231,21 +231,22 @@ def node2vec_bytes(torch, off_t, path):
 
 
 def cached_walk_bytes(torch, off_t, path, length):
-    """Algorithmic bytes of one walk launch over the cumulative array and its
-    summary: per step 16 (row offsets) + 8 (row total) + 8 per summary probe
-    (ceil(log2(G + 1)) probes over the row's G = (end-1)/8 - beg/8 summary
-    entries) + 32 (one half of the 8-entry group) + 4 (picked column) + 4
-    (path entry); per walker 4 (start) and 4 * (L + 1) (its path row)."""
+    """Algorithmic bytes of one walk launch over the cumulative array's
+    search aids: per step 32 (the vertex record) + 8 per s2 probe
+    (ceil(log2(G + 1)) over the row's G = (end-1)/64 - beg/64 entries) + 32
+    (one half of the s1 run) + 32 (the 8-edge group: its weights, or one half
+    of its leaf entries) + 4 (picked column) + 4 (path entry); per walker 4
+    (start) and 4 * (L + 1) (its path row)."""
     p = path.to(torch.int64) & 0xFFFFFFFF
     a, b = p[:, :-1], p[:, 1:]
     real = b != 0xFFFFFFFF
     n_trans = int(real.sum())
     av = a[real]
     beg, end = off_t[av], off_t[av + 1]
-    G = ((end - 1) >> 3) - (beg >> 3)
+    G = ((end - 1) >> 6) - (beg >> 6)
     probes = int(torch.ceil(torch.log2((G + 1).to(torch.float64))).sum())
     n = path.shape[0]
-    return (16 + 8 + 32 + 4 + 4) * n_trans + 8 * probes + 4 * n + 4 * n * (length + 1)
+    return (32 + 32 + 32 + 4 + 4) * n_trans + 8 * probes + 4 * n + 4 * n * (length + 1)
 
 
 def walk_workload(args):
@@ -390,26 +391,32 @@ def run_walk_bench(args, rank, world):
         roofline = roofline_block("walk_kernel<NODE2VEC>", traffic_record("csaw_walk.cu", wl_name + "_cdf"),
                                   ms_per_step, alg_bytes)
     else:
-        # the dominant kernel of the step is the walk over the array: timed
-        # alone over the graph's cached copy (identical paths), the rest of
-        # the step is the array's construction
+        # the step's phases timed by CUDA events on the step's stream inside
+        # the call (the array's construction, then the walk kernels); the
+        # paths checked against the graph's prebuilt array
         cb = cached_walk_bytes(torch, off_t, path, wl.length)
         ms_walk = ms_per_step
         if mode == "build":
+            ph = []
+            for i in range(args.steps):
+                flush.fill_(i)
+                p_ms = [0.0, 0.0]
+                csaw.walk(G, starts, wl.length, wl.bias, seed, wl.n2v_mult, path=path, stream=stream, build_cdf=True,
+                          phase_ms=p_ms)
+                ph.append(p_ms)
+            ms_build = float(np.mean([x[0] for x in ph]))
+            ms_walk = float(np.mean([x[1] for x in ph]))
             G.build_cdf(wl.bias)
             path2 = torch.empty_like(path)
-            t_w = time_steps(torch, lambda: csaw.walk(G, starts, wl.length, wl.bias, seed, wl.n2v_mult,
-                                                      path=path2, stream=stream),
-                             args.steps, args.warmup, stream, flush)
-            ms_walk = sum(t_w) / len(t_w)
+            csaw.walk(G, starts, wl.length, wl.bias, seed, wl.n2v_mult, path=path2, stream=stream)
+            torch.cuda.synchronize()
             same = bool(torch.equal(path, path2))
             G.drop_cdf(wl.bias)
-            ms_build = ms_per_step - ms_walk
             kernels = {"walk_cached_kernel_ms": ms_walk,
                        "cumulative_array_build_ms": ms_build,
-                       "build_basis": "step time minus the walk kernel timed alone over a prebuilt array",
-                       "build_algorithmic_bytes": 13 * g.E + 8 * (g.V + 1),
-                       "identical_paths_prebuilt_array": same}
+                       "basis": "CUDA events on the step's stream around each phase inside the call (phase_ms)",
+                       "build_algorithmic_bytes": 4 * g.E + 9 * g.E // 8 + 40 * g.V,
+                       "identical_paths_graph_array": same}
             recs = traffic_records("csaw_graph.cu", wl_name + "_build")
             if recs and ms_build > 0:
                 peak, peak_kind = measured_peaks()
@@ -418,10 +425,12 @@ def run_walk_bench(args, rank, world):
                 kernels["build_dram_gbs"] = round(dram / (ms_build / 1e3) / 1e9, 1)
                 kernels["build_dram_frac"] = round(dram / (ms_build / 1e3) / 1e9 / peak, 4)
                 kernels["build_kernels"] = sorted(r["kernel"] for r in recs)
-        roofline = roofline_block("walk_cached_kernel<EDGE_WEIGHT>", traffic_record("csaw_walk_cdf.cu", wl_name + "_cdf"),
+        kn = "walk_cached_kernel<WEIGHTS>" if mode == "build" else "walk_cached_kernel<LEAF>"
+        roofline = roofline_block(kn, traffic_record("csaw_walk_cdf.cu", wl_name + ("_build" if mode == "build" else "_cdf")),
                                   ms_walk, cb)
-    cum = {"build": "built over all rows inside every step (segmented scan over edge tiles, then each step a "
-                    "search of its summary and one or two 32-byte sectors)",
+    cum = {"build": "built over all rows inside every step (segmented scan over edge tiles into summaries of the "
+                    "prefix sums and per-vertex records; each step bisects the summaries and sums one 32-byte "
+                    "group of weights)",
            "cached": "cached per edge (built once per graph, before timing)",
            "streaming": "computed per step (streamed over the row)"}[mode]
     result = {
@@ -1009,6 +1018,14 @@ def run_oom_bench(args):
                                                         np.array_equal(res.edge_offsets, ref_s.edge_offsets)),
                          **st, "link_gbs": st["bytes_loaded"] / sec / 1e9}
         log(f"[bench] oom {name}: walk {walks[name]['seconds']:.3f}s, sample {samples[name]['seconds']:.3f}s")
+    # the host CSR read in place (coherent host access): no partition copies
+    sec, (path, st) = timed(lambda: csaw.walk_oom(g.off, g.col, g.w, starts, L, "edge_weight", 7,
+                                                  budget_bytes=budget, slots=2, direct=True), reps)
+    walks["direct"] = {"seconds": sec, "seps": walk_edges / sec,
+                       "identical_to_in_memory": bool(np.array_equal(path, ref_path)), **st,
+                       "host_reads": "summaries built on the device from the host weights; each step reads one "
+                                     "32-byte group of weights and the picked column from host memory"}
+    log(f"[bench] oom direct (mode {st['direct']}): walk {sec:.3f}s")
     best = min(walks.values(), key=lambda r: r["seconds"])
     return {
         "metric": METRIC, "value": best["seps"], "unit": "edges/s", "n_gpus": 1, "steps": reps,

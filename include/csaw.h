@@ -204,8 +204,16 @@ csaw_status csaw_walk(csaw_graph* g, const uint32_t* starts, uint64_t n_walkers,
  * temporary of 9 bytes per edge (stream-ordered, freed by the call), and
  * every step is then a search of it instead of a pass over the row: the
  * same paths, with the array's construction inside the call.  Ignored
- * otherwise.  Errors: those of csaw_walk, and CSAW_ERR_INVALID for an
- * unknown teleport mode. */
+ * otherwise.  For edge weights the temporary holds only the summaries of the
+ * prefix sums (every 8th and 64th) and per-vertex records {start, end,
+ * total}, about 1.14 bytes per edge + 32 per vertex, and a step forms its
+ * 8-edge group's sums from the weights; for neighbour degree it holds the
+ * whole array (9 bytes per edge + 32 per vertex).
+ * phase_ms (not NULL): the call records CUDA events on `stream` around its
+ * phases, waits for the stream, and stores the device time of the array's
+ * construction in phase_ms[0] (0 when nothing is built) and of the walk
+ * kernels in phase_ms[1].  Errors: those of csaw_walk, and CSAW_ERR_INVALID
+ * for an unknown teleport mode. */
 #define CSAW_TELEPORT_NONE 0
 #define CSAW_TELEPORT_RESTART 1
 #define CSAW_TELEPORT_JUMP 2
@@ -214,6 +222,7 @@ typedef struct {
     int32_t teleport;        /* CSAW_TELEPORT_* */
     uint32_t teleport_q32;   /* teleport probability per step, in units of 2^-32 */
     uint32_t build_cdf;      /* 1: see below */
+    float* phase_ms;         /* NULL, or float[2]: see below */
 } csaw_walk_opts;
 
 csaw_status csaw_walk_ex(csaw_graph* g, const uint32_t* starts, uint64_t n_walkers, uint32_t length,
@@ -243,6 +252,7 @@ typedef struct {
     uint64_t bytes_loaded;   /* host-to-device bytes of those uploads */
     uint64_t reuses;         /* rounds whose partition was still in a slot (no upload) */
     uint64_t pinned_bytes;   /* host bytes page-locked for the call (opts->pin_host) */
+    uint32_t direct;         /* 1: the walk read the host arrays in place (opts->direct) */
 } csaw_oom_stats;
 
 /* Options of the out-of-memory calls (NULL = defaults). */
@@ -253,6 +263,8 @@ typedef struct {
                                 duration of the call (cudaHostRegister), so that
                                 partition copies run behind the selection; a
                                 refused registration falls back to pageable copies */
+    uint32_t direct;         /* walks, 1: read the host CSR in place instead of
+                                copying partitions (see csaw_walk_oom_ex) */
 } csaw_oom_opts;
 
 /* The partitions csaw_walk_oom cuts a host CSR into for a device budget
@@ -279,7 +291,17 @@ csaw_status csaw_walk_oom(const uint64_t* row_offsets, const uint32_t* cols, con
  * slots, each round also loads the partition with the second most active
  * walkers into another slot, on a stream of its own, while the round runs
  * (Sec. V-B); a round whose partition is still in a slot loads nothing
- * (stats->reuses).  Paths are those of csaw_walk_oom and csaw_walk. */
+ * (stats->reuses).  Paths are those of csaw_walk_oom and csaw_walk.
+ * opts->direct = 1, on a device that reads pageable host memory coherently
+ * (cudaDevAttrPageableMemoryAccess, e.g. a Grace-attached GPU), with cols
+ * and weights 16-byte aligned: no partition is copied.  The device builds,
+ * from the host weights read in place, the summaries of their row prefix
+ * sums (every 8th and 64th) and per-vertex records {start, end, total}
+ * (about 1.14 bytes per edge + 32 per vertex, which must fit
+ * slots x device_budget_bytes), and each step reads one record, bisects the
+ * summaries and reads one 32-byte group of weights and the picked column
+ * from host memory.  Columns are checked on the device before the walk.
+ * stats->direct reports the mode; otherwise the call partitions as above. */
 csaw_status csaw_walk_oom_ex(const uint64_t* row_offsets, const uint32_t* cols, const uint32_t* weights,
                              uint32_t n_vertices, uint64_t n_edges, uint64_t device_budget_bytes,
                              const uint32_t* starts, uint64_t n_walkers, uint32_t length,

@@ -45,7 +45,8 @@ class Bias(ctypes.Structure):
 
 
 class WalkOpts(ctypes.Structure):
-    _fields_ = [("teleport", ctypes.c_int32), ("teleport_q32", ctypes.c_uint32), ("build_cdf", ctypes.c_uint32)]
+    _fields_ = [("teleport", ctypes.c_int32), ("teleport_q32", ctypes.c_uint32), ("build_cdf", ctypes.c_uint32),
+                ("phase_ms", ctypes.POINTER(ctypes.c_float))]
 
 
 TELEPORT = {None: 0, "restart": 1, "jump": 2}
@@ -53,11 +54,11 @@ TELEPORT = {None: 0, "restart": 1, "jump": 2}
 
 class OomStats(ctypes.Structure):
     _fields_ = [("partitions", ctypes.c_uint32), ("loads", ctypes.c_uint64), ("bytes_loaded", ctypes.c_uint64),
-                ("reuses", ctypes.c_uint64), ("pinned_bytes", ctypes.c_uint64)]
+                ("reuses", ctypes.c_uint64), ("pinned_bytes", ctypes.c_uint64), ("direct", ctypes.c_uint32)]
 
 
 class OomOpts(ctypes.Structure):
-    _fields_ = [("slots", ctypes.c_uint32), ("pin_host", ctypes.c_uint32)]
+    _fields_ = [("slots", ctypes.c_uint32), ("pin_host", ctypes.c_uint32), ("direct", ctypes.c_uint32)]
 
 
 class GraphInfo(ctypes.Structure):
@@ -326,7 +327,7 @@ class Graph:
 
 
 def walk(g: Graph, starts, length: int, bias="edge_weight", seed: int = 0, mult=(1, 1, 1),
-         path=None, stream=None, teleport=None, teleport_q32: int = 0, build_cdf: bool = False):
+         path=None, stream=None, teleport=None, teleport_q32: int = 0, build_cdf: bool = False, phase_ms=None):
     """csaw_walk (csaw_walk_ex with teleport = "restart" or "jump" and a
     per-step probability teleport_q32 / 2^32, or with build_cdf: the call
     builds the kind's cumulative array for itself and walks over it).
@@ -337,13 +338,21 @@ def walk(g: Graph, starts, length: int, bias="edge_weight", seed: int = 0, mult=
     L = lib()
     b = make_bias(bias, mult) if isinstance(bias, str) else bias
     opts = None
-    if teleport is not None or build_cdf:
+    if teleport is not None or build_cdf or phase_ms is not None:
+        # phase_ms: a list that receives [build ms, walk ms] (device time, the call waits)
         opts = WalkOpts(TELEPORT[teleport], teleport_q32, 1 if build_cdf else 0)
+        if phase_ms is not None:
+            ph = (ctypes.c_float * 2)()
+            opts.phase_ms = ph
 
     def call(sp, pp, mem, st):
         if opts is None:
             return L.csaw_walk(g.handle, sp, n, length, ctypes.byref(b), seed, pp, mem, st)
         return L.csaw_walk_ex(g.handle, sp, n, length, ctypes.byref(b), seed, pp, mem, st, ctypes.byref(opts))
+
+    def phases():
+        if phase_ms is not None:
+            phase_ms[:] = [float(ph[0]), float(ph[1])]
 
     if _is_torch(starts):
         import torch
@@ -351,6 +360,7 @@ def walk(g: Graph, starts, length: int, bias="edge_weight", seed: int = 0, mult=
         if path is None:
             path = torch.empty((n, length + 1), dtype=torch.int32, device=starts.device)
         _check(call(_ptr(starts), _ptr(path), MEM_DEVICE, _stream_handle(stream)))
+        phases()
         return path
     starts = np.ascontiguousarray(starts, dtype=np.uint32)
     n = len(starts)
@@ -358,6 +368,7 @@ def walk(g: Graph, starts, length: int, bias="edge_weight", seed: int = 0, mult=
         path = np.empty((n, length + 1), dtype=np.uint32)
     st = _stream_handle(stream) if stream is not None else None
     _check(call(_ptr(starts), _ptr(path), MEM_HOST, st))
+    phases()
     return path
 
 
@@ -376,14 +387,15 @@ def oom_plan(off, budget_bytes: int, weighted: bool = True) -> np.ndarray:
 
 def _oom_stats(st):
     return {"partitions": st.partitions, "loads": st.loads, "bytes_loaded": st.bytes_loaded, "reuses": st.reuses,
-            "pinned_bytes": st.pinned_bytes}
+            "pinned_bytes": st.pinned_bytes, "direct": st.direct}
 
 
 def walk_oom(off, col, w, starts, length: int, bias="edge_weight", seed: int = 0,
-             budget_bytes: int = 1 << 30, stream=None, slots=None, pin_host: bool = False):
+             budget_bytes: int = 1 << 30, stream=None, slots=None, pin_host: bool = False, direct: bool = False):
     """csaw_walk_oom (slots None) or csaw_walk_oom_ex: walks over a host CSR
     (numpy off uint64, col uint32, w uint32 or None) streamed through slots
-    of `budget_bytes` of device memory.  Returns (path uint32[n, length+1],
+    of `budget_bytes` of device memory, or (direct) read in place where the
+    device reads host memory coherently.  Returns (path uint32[n, length+1],
     stats dict)."""
     L = lib()
     off = np.ascontiguousarray(off, dtype=np.uint64)
@@ -394,11 +406,11 @@ def walk_oom(off, col, w, starts, length: int, bias="edge_weight", seed: int = 0
     path = np.empty((len(starts), length + 1), dtype=np.uint32)
     st = OomStats()
     sh = _stream_handle(stream) if stream is not None else None
-    if slots is None and not pin_host:
+    if slots is None and not pin_host and not direct:
         _check(L.csaw_walk_oom(_ptr(off), _ptr(col), _ptr(w), len(off) - 1, len(col), budget_bytes, _ptr(starts),
                                len(starts), length, ctypes.byref(b), seed, _ptr(path), ctypes.byref(st), sh))
     else:
-        o = OomOpts(slots or 0, int(pin_host))
+        o = OomOpts(slots or 0, int(pin_host), int(direct))
         _check(L.csaw_walk_oom_ex(_ptr(off), _ptr(col), _ptr(w), len(off) - 1, len(col), budget_bytes,
                                   _ptr(starts), len(starts), length, ctypes.byref(b), seed, _ptr(path),
                                   ctypes.byref(st), sh, ctypes.byref(o)))

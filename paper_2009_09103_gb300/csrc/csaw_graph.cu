@@ -611,12 +611,14 @@ __global__ void __launch_bounds__(CB_THREADS) cdf_tile_scan_kernel(const uint64_
     }
     const uint64_t pb = tl.pb;
     if (pb + CB_ITEMS <= E) {
-        ulonglong2* dst = reinterpret_cast<ulonglong2*>(cdf + pb);
+        if (cdf) {
+            ulonglong2* dst = reinterpret_cast<ulonglong2*>(cdf + pb);
 #pragma unroll
-        for (int j = 0; j < CB_ITEMS / 2; ++j) dst[j] = make_ulonglong2(out[2 * j], out[2 * j + 1]);
+            for (int j = 0; j < CB_ITEMS / 2; ++j) dst[j] = make_ulonglong2(out[2 * j], out[2 * j + 1]);
+        }
         s1[pb >> 3] = out[CB_ITEMS - 1];
         if (((pb >> 3) & 7) == 7) s2[pb >> 6] = out[CB_ITEMS - 1];   // edge 64h + 63
-    } else {
+    } else if (cdf) {
 #pragma unroll
         for (int j = 0; j < CB_ITEMS; ++j)
             if (pb + j < E) cdf[pb + j] = out[j];
@@ -624,31 +626,42 @@ __global__ void __launch_bounds__(CB_THREADS) cdf_tile_scan_kernel(const uint64_
 }
 
 // rec[v] = {off[v], off[v+1], row total, 0}, two 16-byte stores per vertex.
+// The total is cdf[end - 1], or without a leaf level the last summary entry
+// inside the row plus the weights after it (edge weights).
 __global__ void cdf_records_kernel(const uint64_t* __restrict__ off, uint32_t V, const uint64_t* __restrict__ cdf,
+                                   const uint64_t* __restrict__ s1, const uint32_t* __restrict__ w,
                                    uint64_t* __restrict__ rec)
 {
     for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V;
          v += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t beg = __ldg(off + v), end = __ldg(off + v + 1);
-        const uint64_t T = end > beg ? cdf[end - 1] : 0ull;
+        const uint64_t beg = off[v], end = off[v + 1];
+        uint64_t T = 0;
+        if (end > beg && cdf) {
+            T = cdf[end - 1];
+        } else if (end > beg) {
+            const uint64_t gb = ((end - 1) >> 3) << 3;
+            T = gb > beg ? s1[(gb >> 3) - 1] : 0ull;
+            for (uint64_t q = gb > beg ? gb : beg; q < end; ++q) T += w[q];
+        }
         ulonglong2* r = reinterpret_cast<ulonglong2*>(rec + 4 * v);
         r[0] = make_ulonglong2(beg, end);
         r[1] = make_ulonglong2(T, 0ull);
     }
 }
 
-csaw_status enqueue_cdf_build(const csaw_graph* g, int kind, uint64_t* cdf, cudaStream_t s)
+csaw_status enqueue_cdf_build_raw(const uint64_t* off, const uint32_t* col, const uint32_t* w, const uint32_t* deg,
+                                  uint32_t V, uint64_t E, int sm_count, int kind, uint64_t* leaf, uint64_t* s1,
+                                  uint64_t* s2, uint64_t* rec, cudaStream_t s)
 {
-    const CdfLayout L = cdf_layout(g->E, g->V);
-    uint64_t vb = ((uint64_t)g->V + 255) / 256;
-    if (vb > (uint64_t)g->sm_count * 8) vb = (uint64_t)g->sm_count * 8;
+    uint64_t vb = ((uint64_t)V + 255) / 256;
+    if (vb > (uint64_t)sm_count * 8) vb = (uint64_t)sm_count * 8;
     const unsigned vgrid = (unsigned)(vb ? vb : 1);
-    if (g->E == 0) {
-        if (g->V) cdf_records_kernel<<<vgrid, 256, 0, s>>>(g->off, g->V, cdf, cdf + L.rec);
+    if (E == 0) {
+        if (V) cdf_records_kernel<<<vgrid, 256, 0, s>>>(off, V, leaf, s1, w, rec);
         const cudaError_t e = cudaGetLastError();
         return e == cudaSuccess ? CSAW_OK : cuda_fail(e, "cumulative array launch");
     }
-    const uint64_t n_tiles = (g->E + CB_TILE - 1) / CB_TILE;
+    const uint64_t n_tiles = (E + CB_TILE - 1) / CB_TILE;
     if (n_tiles > 0x7FFFFFFFull) return fail(CSAW_ERR_INVALID, "too many edges for the cumulative array");
     void* tf = nullptr;
     void* ts = nullptr;
@@ -659,29 +672,34 @@ csaw_status enqueue_cdf_build(const csaw_graph* g, int kind, uint64_t* cdf, cuda
     if (st != CSAW_OK) { dfree(tf, s); dfree(ts, s); return st; }
     const unsigned grid = (unsigned)n_tiles;
     uint32_t* tile_row = (uint32_t*)tr;
-    cdf_tile_rows_kernel<<<vgrid, 256, 0, s>>>(g->off, g->V, tile_row);
+    cdf_tile_rows_kernel<<<vgrid, 256, 0, s>>>(off, V, tile_row);
     if (kind == CSAW_BIAS_EDGE_WEIGHT) {
         cdf_tile_sum_kernel<CSAW_BIAS_EDGE_WEIGHT><<<grid, CB_THREADS, 0, s>>>(
-            g->off, g->col, g->w, g->deg, g->V, g->E, tile_row, n_tiles, (uint32_t*)tf, (uint64_t*)ts);
+            off, col, w, deg, V, E, tile_row, n_tiles, (uint32_t*)tf, (uint64_t*)ts);
         cdf_tile_carry_kernel<<<1, CB_CARRY_THREADS, 0, s>>>((const uint32_t*)tf, (uint64_t*)ts, n_tiles);
         cdf_tile_scan_kernel<CSAW_BIAS_EDGE_WEIGHT><<<grid, CB_THREADS, 0, s>>>(
-            g->off, g->col, g->w, g->deg, g->V, g->E, tile_row, n_tiles, (const uint64_t*)ts, cdf, cdf + L.s1,
-            cdf + L.s2);
+            off, col, w, deg, V, E, tile_row, n_tiles, (const uint64_t*)ts, leaf, s1, s2);
     } else {
         cdf_tile_sum_kernel<CSAW_BIAS_NEIGHBOR_DEGREE><<<grid, CB_THREADS, 0, s>>>(
-            g->off, g->col, g->w, g->deg, g->V, g->E, tile_row, n_tiles, (uint32_t*)tf, (uint64_t*)ts);
+            off, col, w, deg, V, E, tile_row, n_tiles, (uint32_t*)tf, (uint64_t*)ts);
         cdf_tile_carry_kernel<<<1, CB_CARRY_THREADS, 0, s>>>((const uint32_t*)tf, (uint64_t*)ts, n_tiles);
         cdf_tile_scan_kernel<CSAW_BIAS_NEIGHBOR_DEGREE><<<grid, CB_THREADS, 0, s>>>(
-            g->off, g->col, g->w, g->deg, g->V, g->E, tile_row, n_tiles, (const uint64_t*)ts, cdf, cdf + L.s1,
-            cdf + L.s2);
+            off, col, w, deg, V, E, tile_row, n_tiles, (const uint64_t*)ts, leaf, s1, s2);
     }
-    cdf_records_kernel<<<vgrid, 256, 0, s>>>(g->off, g->V, cdf, cdf + L.rec);
+    cdf_records_kernel<<<vgrid, 256, 0, s>>>(off, V, leaf, s1, w, rec);
     cudaError_t e = cudaGetLastError();
     dfree(tf, s);
     dfree(ts, s);
     dfree(tr, s);
     if (e != cudaSuccess) return cuda_fail(e, "cumulative array launch");
     return CSAW_OK;
+}
+
+csaw_status enqueue_cdf_build(const csaw_graph* g, int kind, uint64_t* cdf, cudaStream_t s)
+{
+    const CdfLayout L = cdf_layout(g->E, g->V);
+    return enqueue_cdf_build_raw(g->off, g->col, g->w, g->deg, g->V, g->E, g->sm_count, kind, cdf, cdf + L.s1,
+                                 cdf + L.s2, cdf + L.rec, s);
 }
 
 }  // namespace csaw

@@ -165,18 +165,31 @@ void launch_partition_check(uint32_t* col, uint32_t* w, uint64_t ne, uint32_t V,
 
 // Walks that read a cached cumulative array (or, for uniform bias, none):
 // one thread per walker.  Defined in csaw_walk.cu.
-// cdf: the kind's cumulative array (cdf_words(E, V) words; ignored for uniform).
-// Walkers w0 .. w0+n-1 of the call: starts and path point at walker w0's
-// entries, and walker w0 + i draws as walker w0 + i.  Defined in csaw_walk_cdf.cu.
-csaw_status launch_walk_cached(const csaw_graph* g, int kind, const uint64_t* cdf, const uint32_t* starts,
-                               uint64_t w0, uint64_t n, uint32_t length, uint64_t rng_seed, uint32_t* path,
-                               cudaStream_t s);
+// cdf: the kind's cumulative array (cdf_words(E, V) words; ignored for
+// uniform); leaf = false: summaries and records only, the leaf level formed
+// from the edge weights (edge-weight bias).  Walkers w0 .. w0+n-1 of the
+// call: starts and path point at walker w0's entries, and walker w0 + i
+// draws as walker w0 + i.  Defined in csaw_walk_cdf.cu.
+csaw_status launch_walk_cached(const csaw_graph* g, int kind, const uint64_t* cdf, bool leaf,
+                               const uint32_t* starts, uint64_t w0, uint64_t n, uint32_t length, uint64_t rng_seed,
+                               uint32_t* path, cudaStream_t s);
 // The same walks with the path matrix copied to host memory h_path: the
 // walkers run in a few chunks on s, and each chunk's rows are copied out on
 // a second stream while the next chunk walks.  Returns after the copies.
-csaw_status walk_cached_to_host(const csaw_graph* g, int kind, const uint64_t* cdf, const uint32_t* d_starts,
-                                uint64_t n, uint32_t length, uint64_t rng_seed, uint32_t* d_path,
-                                uint32_t* h_path, cudaStream_t s);
+// The host starts h_starts (the source of d_starts) are checked while the
+// walks run: CSAW_ERR_INVALID for a start that is not a vertex.
+// walked (or null) is recorded on s after the last walk kernel.
+csaw_status walk_cached_to_host(const csaw_graph* g, int kind, const uint64_t* cdf, bool leaf,
+                                const uint32_t* h_starts, const uint32_t* d_starts, uint64_t n, uint32_t length,
+                                uint64_t rng_seed, uint32_t* d_path, uint32_t* h_path, cudaStream_t s,
+                                cudaEvent_t walked);
+// Walks over CSR arrays in host memory, read in place (coherent access to
+// host memory): off, col and w (null: uniform) are host arrays, c holds
+// device summaries and records of the weights (no leaf level).
+struct CdfView;
+csaw_status launch_walk_host(const CdfView& c, const uint64_t* off, const uint32_t* col, const uint32_t* w,
+                             uint32_t V, uint64_t E, int sm_count, const uint32_t* starts, uint64_t n,
+                             uint32_t length, uint64_t rng_seed, uint32_t* path, cudaStream_t s);
 // The batched form (several requests, WalkSegments) over the graph's cached array.
 csaw_status walk_batch_cached(const csaw_graph* g, int kind, const uint32_t* d_starts, uint64_t n,
                               const WalkSegments& seg, uint32_t max_len, uint32_t* d_path, cudaStream_t s);
@@ -208,6 +221,8 @@ __host__ __device__ inline CdfLayout cdf_layout(uint64_t E, uint64_t V)
     L.words = L.rec + 4 * V;
     return L;
 }
+// A summary-only array (edge weights: the leaf level is formed from the
+// weights by w_search) has the same layout with cdf unused.
 struct CdfView {
     const uint64_t* cdf = nullptr;
     const uint64_t* s1 = nullptr;
@@ -227,10 +242,39 @@ __host__ __device__ inline CdfView cdf_view(const uint64_t* base, uint64_t E, ui
 }
 uint64_t cdf_words(uint64_t E, uint64_t V);
 
+// Summaries and records alone (edge weights, no leaf level), in one
+// allocation of wsum_layout(E, V).words words with s1 at word 0.
+__host__ __device__ inline CdfLayout wsum_layout(uint64_t E, uint64_t V)
+{
+    CdfLayout L;
+    L.s1 = 0;
+    L.s2 = ((E + 7) / 8 + 8 + 7) & ~7ull;
+    L.rec = (L.s2 + (E + 63) / 64 + 8 + 7) & ~7ull;
+    L.words = L.rec + 4 * V;
+    return L;
+}
+__host__ __device__ inline CdfView wsum_view(const uint64_t* base, uint64_t E, uint64_t V)
+{
+    CdfView c;
+    if (!base) return c;
+    const CdfLayout L = wsum_layout(E, V);
+    c.s1 = base + L.s1;
+    c.s2 = base + L.s2;
+    c.rec = base + L.rec;
+    return c;
+}
+
 // Enqueues the build of the cumulative array of a static kind and its
 // search aids into cdf (cdf_words(E, V) words) on s; temporaries are
 // stream-ordered.
 csaw_status enqueue_cdf_build(const csaw_graph* g, int kind, uint64_t* cdf, cudaStream_t s);
+// The same from raw CSR pointers (device, or host arrays read in place, with
+// w 16-byte aligned), writing the leaf level to leaf (or, when leaf is null,
+// only the summaries and records: edge weights) and the search aids to
+// s1, s2, rec.
+csaw_status enqueue_cdf_build_raw(const uint64_t* off, const uint32_t* col, const uint32_t* w, const uint32_t* deg,
+                                  uint32_t V, uint64_t E, int sm_count, int kind, uint64_t* leaf, uint64_t* s1,
+                                  uint64_t* s2, uint64_t* rec, cudaStream_t s);
 
 // Releases a result made by the request server (tagged "CSRV").
 void free_server_result(void* result);
@@ -406,18 +450,14 @@ __device__ __forceinline__ uint64_t first_above8(const uint64_t* __restrict__ a,
     return lo + le;
 }
 
-// Smallest e in [beg, end) with cdf[e] > x, for x < cdf[end - 1] (a row of
-// the cumulative array of c).  Every s2[h] with beg/64 <= h < (end-1)/64,
-// and every s1[g] with beg/8 <= g < (end-1)/8, is a prefix sum of this row.
-// Bisecting the row's s2 entries finds the 64-edge block of the hit (the
-// row's last block when none exceeds x); that block's s1 entries in the row
-// (at most 7, one aligned run) give its 8-edge group, and the group's
-// entries in the row the edge.  Each step after the bisection reads one or
-// two 32-byte sectors; all reads stay inside the arrays and their padding.
-// STREAM_LEAF: the array's own sectors are read evict-first, so that they
-// do not push the summaries out of L2.
-template <bool STREAM_LEAF = false>
-__device__ __forceinline__ uint64_t cdf_search(const CdfView& c, uint64_t beg, uint64_t end, uint64_t x)
+// The 8-edge group of the hit: the group g of the smallest e in [beg, end)
+// with cdf[e] > x, for x below the row total (a row of the cumulative array
+// of c).  Every s2[h] with beg/64 <= h < (end-1)/64, and every s1[g] with
+// beg/8 <= g < (end-1)/8, is a prefix sum of this row.  Bisecting the row's
+// s2 entries finds the 64-edge block of the hit (the row's last block when
+// none exceeds x); that block's s1 entries in the row (at most 7, one
+// aligned run) give its group.  Reads stay inside s1, s2 and their padding.
+__device__ __forceinline__ uint64_t cdf_group(const CdfView& c, uint64_t beg, uint64_t end, uint64_t x)
 {
     uint64_t lo = beg >> 6, hi = (end - 1) >> 6;
     while (lo < hi) {
@@ -427,10 +467,61 @@ __device__ __forceinline__ uint64_t cdf_search(const CdfView& c, uint64_t beg, u
     const uint64_t g_lo = (lo << 3) > (beg >> 3) ? (lo << 3) : (beg >> 3);
     const uint64_t g_end = (end - 1) >> 3;
     const uint64_t g_hi = (lo << 3) + 7 < g_end ? (lo << 3) + 7 : g_end;
-    const uint64_t g = first_above8(c.s1, g_lo, g_hi, x);
+    return first_above8(c.s1, g_lo, g_hi, x);
+}
+
+// Smallest e in [beg, end) with cdf[e] > x: the group's entries in the row
+// (one or two 32-byte sectors of the array).  STREAM_LEAF: the array's own
+// sectors are read evict-first, so that they do not push the summaries out
+// of L2.
+template <bool STREAM_LEAF = false>
+__device__ __forceinline__ uint64_t cdf_search(const CdfView& c, uint64_t beg, uint64_t end, uint64_t x)
+{
+    const uint64_t g = cdf_group(c, beg, end, x);
     const uint64_t e_lo = (g << 3) > beg ? (g << 3) : beg;
     const uint64_t e_hi = (g << 3) + 8 < end ? (g << 3) + 8 : end;
     return first_above8<STREAM_LEAF>(c.cdf, e_lo, e_hi, x);
+}
+
+// The same search without the array's leaf level (summaries and records
+// only): the group's sums are formed from its biases w[8g .. 8g+7] (one
+// 32-byte sector), starting from the previous summary entry s1[g-1] =
+// cdf[8g-1] when that edge is in the row (else from 0 at the row start).
+// PADDED: w is a graph array, 16-byte aligned and readable to E + 7, read
+// as two 16-byte loads (evict-first); otherwise (arrays in host memory) the
+// group is read entry by entry below E.
+template <bool PADDED>
+__device__ __forceinline__ uint64_t w_search(const CdfView& c, const uint32_t* __restrict__ w, uint64_t E,
+                                             uint64_t beg, uint64_t end, uint64_t x)
+{
+    const uint64_t g = cdf_group(c, beg, end, x);
+    const uint64_t gb = g << 3;
+    const uint64_t e_lo = gb > beg ? gb : beg;
+    const uint64_t e_hi = gb + 8 < end ? gb + 8 : end;
+    uint64_t acc = gb > beg ? __ldg(c.s1 + g - 1) : 0ull;
+    uint32_t v[8];
+    if constexpr (PADDED) {
+        const uint4 a = __ldcs(reinterpret_cast<const uint4*>(w + gb));
+        const uint4 b = __ldcs(reinterpret_cast<const uint4*>(w + gb) + 1);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = gb + j < E ? w[gb + j] : 0u;
+    }
+    uint64_t hit = e_hi - 1;
+    bool found = false;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const uint64_t pos = gb + j;
+        const bool in = pos >= e_lo && pos < e_hi;
+        if (in) acc += v[j];
+        if (in && !found && acc > x) {
+            hit = pos;
+            found = true;
+        }
+    }
+    return hit;
 }
 
 }  // namespace csaw

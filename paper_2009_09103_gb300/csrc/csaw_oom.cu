@@ -155,6 +155,61 @@ bool host_register(void* p, size_t bytes)
     return false;
 }
 
+// Columns of a host CSR read in place: err |= 1 where one is not a vertex.
+__global__ void direct_check_kernel(const uint32_t* col, uint64_t ne, uint32_t V, uint32_t* err)
+{
+    uint32_t bad = 0;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (uint64_t)gridDim.x * blockDim.x)
+        bad |= col[e] >= V;
+    if (__any_sync(CSAW_FULL_MASK, bad) && (threadIdx.x & 31) == 0) atomicOr(err, 1u);
+}
+
+// Direct mode of csaw_walk_oom_ex: the GPU reads the host CSR in place
+// (coherent access to pageable host memory).  The device holds the walkers,
+// the path and, for edge weights, the summaries and vertex records of the
+// weights' prefix sums (built from the host weights by the segmented scan);
+// every step reads one record, bisects the summaries and then reads one
+// 32-byte group of weights and the picked column over the host link.
+static csaw_status walk_oom_direct(const uint64_t* off, const uint32_t* cols, const uint32_t* weights,
+                                   uint32_t V, uint64_t E, int sm_count, const uint32_t* starts, uint64_t n,
+                                   uint32_t length, uint64_t rng_seed, uint32_t* path, cudaStream_t s)
+{
+    const uint64_t row_len = (uint64_t)length + 1;
+    void *d_starts = nullptr, *d_path = nullptr, *d_err = nullptr, *d_sum = nullptr;
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(s);
+        for (void* p : {d_starts, d_path, d_err, d_sum}) dfree(p, s);
+    };
+    csaw_status st = dalloc(&d_starts, sizeof(uint32_t) * n, s);
+    if (st == CSAW_OK) st = dalloc(&d_path, sizeof(uint32_t) * n * row_len, s);
+    if (st == CSAW_OK) st = dalloc(&d_err, sizeof(uint32_t), s);
+    if (st == CSAW_OK && weights) st = dalloc(&d_sum, sizeof(uint64_t) * wsum_layout(E, V).words, s);
+    if (st != CSAW_OK) { cleanup(); return st; }
+    cudaError_t e = cudaMemsetAsync(d_err, 0, sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_starts, starts, sizeof(uint32_t) * n, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "copy starts"); }
+    if (E) direct_check_kernel<<<(unsigned)sm_count * 8, 256, 0, s>>>(cols, E, V, (uint32_t*)d_err);
+    const CdfView c = wsum_view((const uint64_t*)d_sum, E, V);
+    if (weights)
+        st = enqueue_cdf_build_raw(off, cols, weights, nullptr, V, E, sm_count, CSAW_BIAS_EDGE_WEIGHT, nullptr,
+                                   (uint64_t*)c.s1, (uint64_t*)c.s2, (uint64_t*)c.rec, s);
+    uint32_t err = 0;
+    e = cudaMemcpyAsync(&err, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess && st == CSAW_OK) st = cuda_fail(e, "column check");
+    if (st == CSAW_OK && err) st = fail(CSAW_ERR_INVALID, "a column is not a vertex");
+    if (st == CSAW_OK)
+        st = launch_walk_host(c, off, cols, weights, V, E, sm_count, (const uint32_t*)d_starts, n, length, rng_seed,
+                              (uint32_t*)d_path, s);
+    if (st == CSAW_OK) {
+        e = cudaMemcpyAsync(path, d_path, sizeof(uint32_t) * n * row_len, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_fail(e, "copy path");
+    }
+    cleanup();
+    return st;
+}
+
 void launch_partition_check(uint32_t* col, uint32_t* w, uint64_t ne, uint32_t V, const uint32_t* deg,
                             uint32_t* err, cudaStream_t s)
 {
@@ -238,6 +293,26 @@ extern "C" csaw_status csaw_walk_oom_ex(const uint64_t* row_offsets, const uint3
     // that is not a vertex is replaced, so that no walker leaves every
     // partition, and the call fails).
     cudaStream_t s = (cudaStream_t)stream;
+
+    // Direct mode, where the device reads host memory in place and the
+    // summaries and records fit the budget.
+    if (opts && opts->direct) {
+        int dev = 0, pageable = 0, sm_count = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return cuda_fail(e, "device query");
+        const uint64_t need = weighted ? sizeof(uint64_t) * wsum_layout(n_edges, n_vertices).words : 0;
+        const bool aligned = ((uintptr_t)cols % 16 == 0) && (!weighted || (uintptr_t)weights % 16 == 0);
+        if (pageable && aligned && need <= device_budget_bytes * n_slots) {
+            if (stats) {
+                stats->partitions = 1;
+                stats->direct = 1;
+            }
+            return walk_oom_direct(row_offsets, cols, weighted ? weights : nullptr, n_vertices, n_edges, sm_count,
+                                   starts, n_walkers, length, rng_seed, path, s);
+        }
+    }
 
     // Partitions: vertex ranges whose slot fits the budget.
     uint32_t np = 0;

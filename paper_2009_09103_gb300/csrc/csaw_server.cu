@@ -124,28 +124,106 @@ static uint64_t estimate_bytes(const csaw_graph* g, const DegreeTable& dt, const
     return b + hub;
 }
 
+// Page-locked host blocks for the arrays of request results, kept for reuse
+// for the life of the process in power-of-two classes from 64 KiB and carved
+// from slabs of at least 256 MiB (one cudaHostAlloc per slab): a result's
+// edges or path are copied from the device straight into one (DMA at the
+// link's rate, with no staging copy and no first-touch faults on the host),
+// and the block goes back to its class when the result is freed.
+struct PinnedPool {
+    static constexpr int MIN_CLASS = 16;
+    static constexpr size_t SLAB = (size_t)256 << 20;
+    std::mutex mu;
+    std::vector<std::vector<void*>> free_by_class = std::vector<std::vector<void*>>(64);
+    unsigned char* slab = nullptr;
+    size_t slab_left = 0;
+    // A block of at least `bytes` bytes and its class, or null (class -1)
+    // when page-locked memory is refused.
+    void* get(size_t bytes, int* cls)
+    {
+        int c = MIN_CLASS;
+        while (c < 62 && ((size_t)1 << c) < bytes) ++c;
+        const size_t size = (size_t)1 << c;
+        *cls = -1;
+        std::lock_guard<std::mutex> lk(mu);
+        auto& f = free_by_class[c];
+        if (!f.empty()) {
+            void* p = f.back();
+            f.pop_back();
+            *cls = c;
+            return p;
+        }
+        if (slab_left < size) {
+            void* p = nullptr;
+            const size_t n = size > SLAB ? size : SLAB;
+            if (cudaHostAlloc(&p, n, cudaHostAllocDefault) != cudaSuccess) {
+                cudaGetLastError();
+                return nullptr;
+            }
+            slab = (unsigned char*)p;   // the rest of the previous slab stays unused
+            slab_left = n;
+        }
+        void* p = slab;
+        slab += size;
+        slab_left -= size;
+        *cls = c;
+        return p;
+    }
+    void put(void* p, int cls)
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        free_by_class[cls].push_back(p);
+    }
+};
+
+static PinnedPool* result_pool()
+{
+    static PinnedPool* pool = new PinnedPool();   // never freed: results may outlive every server
+    return pool;
+}
+
+// A server result: the caller's view first, then where its arrays came from.
+struct ServerResult {
+    csaw_result pub;
+    int cls[5] = {-1, -1, -1, -1, -1};   // edge_offsets, frontier_sizes, src, dst, path (-1: new[])
+};
+
+// An array of n elements of T for result slot k: from the pool, or new[].
+template <class T>
+static T* result_array(ServerResult* r, int k, uint64_t n)
+{
+    int cls = -1;
+    void* p = result_pool()->get(sizeof(T) * (size_t)n, &cls);
+    r->cls[k] = cls;
+    if (p) return (T*)p;
+    return new (std::nothrow) T[n];
+}
+
 static csaw_result* new_result(const Request& r)
 {
-    csaw_result* res = new (std::nothrow) csaw_result();
+    ServerResult* res = new (std::nothrow) ServerResult();
     if (!res) return nullptr;
-    std::memset(res, 0, sizeof(*res));
-    res->tag = SERVER_RESULT_TAG;
-    res->kind = r.kind;
-    res->device_bytes_estimate = r.estimate;
-    return res;
+    std::memset(&res->pub, 0, sizeof(res->pub));
+    res->pub.tag = SERVER_RESULT_TAG;
+    res->pub.kind = r.kind;
+    res->pub.device_bytes_estimate = r.estimate;
+    return &res->pub;
 }
 
 void free_server_result(void* p)
 {
     csaw_result* r = (csaw_result*)p;
     if (!r || r->tag != SERVER_RESULT_TAG) return;
-    delete[] r->edge_offsets;
-    delete[] r->frontier_sizes;
-    delete[] r->src;
-    delete[] r->dst;
-    delete[] r->path;
+    ServerResult* sr = reinterpret_cast<ServerResult*>(r);
+    void* arrays[5] = {r->edge_offsets, r->frontier_sizes, r->src, r->dst, r->path};
+    for (int k = 0; k < 5; ++k) {
+        if (!arrays[k]) continue;
+        if (sr->cls[k] >= 0) result_pool()->put(arrays[k], sr->cls[k]);
+        else if (k < 2) delete[] (uint64_t*)arrays[k];
+        else delete[] (uint32_t*)arrays[k];
+    }
     r->tag = 0;
-    delete r;
+    delete sr;
 }
 
 // One slot: two streams and a pinned staging buffer (grown on demand).
@@ -254,7 +332,7 @@ static csaw_status execute_walks(csaw_graph* g, Lane& L, std::vector<Request*>& 
         const uint64_t cnt = (uint64_t)rq->starts.size() * ((uint64_t)rq->length + 1);
         res->n_walkers = rq->starts.size();
         res->length = rq->length;
-        res->path = new (std::nothrow) uint32_t[cnt + 1];
+        res->path = result_array<uint32_t>(reinterpret_cast<ServerResult*>(res), 4, cnt + 1);
         if (!res->path) {
             res->status = CSAW_ERR_NOMEM;
         } else {
@@ -354,10 +432,11 @@ static csaw_status execute_samples(csaw_graph* g, Lane& L, std::vector<Request*>
         res->depth = dep;
         res->n_instances = n;
         res->n_edges = total;
-        res->edge_offsets = new (std::nothrow) uint64_t[ng + 1];
-        res->frontier_sizes = new (std::nothrow) uint64_t[ng + 1];
-        res->src = new (std::nothrow) uint32_t[total + 1];
-        res->dst = new (std::nothrow) uint32_t[total + 1];
+        ServerResult* sr = reinterpret_cast<ServerResult*>(res);
+        res->edge_offsets = result_array<uint64_t>(sr, 0, ng + 1);
+        res->frontier_sizes = result_array<uint64_t>(sr, 1, ng + 1);
+        res->src = result_array<uint32_t>(sr, 2, total + 1);
+        res->dst = result_array<uint32_t>(sr, 3, total + 1);
         if (!res->edge_offsets || !res->frontier_sizes || !res->src || !res->dst) {
             res->status = CSAW_ERR_NOMEM;
         } else {

@@ -919,6 +919,37 @@ csaw_status walk_batch(const csaw_graph* g, const csaw_bias* bias, const uint32_
     return st;
 }
 
+// CUDA events around a call's phases, when the caller asks for their times:
+// [0] before the array's construction, [1] before the walk, [2] after it.
+struct PhaseTimer {
+    float* out = nullptr;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    bool ok = true;
+    PhaseTimer(float* o, cudaStream_t s) : out(o)
+    {
+        for (int i = 0; out && ok && i < 3; ++i) ok = cudaEventCreate(&ev[i]) == cudaSuccess;
+        mark(0, s);
+    }
+    void mark(int i, cudaStream_t s)
+    {
+        if (out && ok) ok = cudaEventRecord(ev[i], s) == cudaSuccess;
+    }
+    // Waits for the last mark and stores the two phase times.
+    csaw_status finish()
+    {
+        if (!out) return CSAW_OK;
+        cudaError_t e = ok ? cudaEventSynchronize(ev[2]) : cudaErrorUnknown;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&out[0], ev[0], ev[1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&out[1], ev[1], ev[2]);
+        return e == cudaSuccess ? CSAW_OK : cuda_fail(e, "phase times");
+    }
+    ~PhaseTimer()
+    {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+};
+
 }  // namespace csaw
 
 using namespace csaw;
@@ -947,8 +978,15 @@ extern "C" csaw_status csaw_walk_ex(csaw_graph* g, const uint32_t* starts, uint6
 
     const uint32_t* d_starts = starts;
     uint32_t* d_path = path;
+    // static bias with a positive cumulative array: the graph's cached one,
+    // or (build_cdf) one built for this call into a stream-ordered temporary
+    const bool cached = cached_cdf_usable(g, kind);
+    const bool build = !cached && opts && opts->build_cdf && cdf_kind_positive(g, kind);
+    const bool over_array = tele == CSAW_TELEPORT_NONE && kind != CSAW_BIAS_NODE2VEC && (cached || build);
     if (mem_kind == CSAW_MEM_HOST) {
-        for (uint64_t i = 0; i < n_walkers; ++i)
+        // (over the array, the host starts are checked while the walk runs:
+        // the kernels stop a walker whose start is not a vertex)
+        for (uint64_t i = 0; !over_array && i < n_walkers; ++i)
             if (starts[i] >= g->V)
                 return fail(CSAW_ERR_INVALID, "start %llu of walker %llu out of range",
                             (unsigned long long)starts[i], (unsigned long long)i);
@@ -963,27 +1001,39 @@ extern "C" csaw_status csaw_walk_ex(csaw_graph* g, const uint32_t* starts, uint6
                                         cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) { dfree(a, s); dfree(b, s); return cuda_fail(e, "copy starts"); }
     }
-    // static bias with a positive cumulative array: the graph's cached one,
-    // or (build_cdf) one built for this call into a stream-ordered temporary
-    const bool cached = cached_cdf_usable(g, kind);
-    const bool build = !cached && opts && opts->build_cdf && cdf_kind_positive(g, kind);
-    if (tele == CSAW_TELEPORT_NONE && kind != CSAW_BIAS_NODE2VEC && (cached || build)) {
+    PhaseTimer timer(opts ? opts->phase_ms : nullptr, s);
+    if (over_array) {
         const uint64_t* cdf = kind == CSAW_BIAS_UNIFORM ? nullptr : g->cdf[kind];
         void* tmp = nullptr;
         csaw_status st = CSAW_OK;
+        // built for the call: edge weights keep only the summaries and
+        // records (the leaf level is formed from the weights); neighbour
+        // degree keeps the whole array (its biases are gathers)
+        const bool leaf = !(build && kind == CSAW_BIAS_EDGE_WEIGHT);
         if (build) {
-            st = dalloc(&tmp, sizeof(uint64_t) * cdf_words(g->E, g->V), s);
-            if (st == CSAW_OK) st = enqueue_cdf_build(g, kind, (uint64_t*)tmp, s);
+            const uint64_t words = leaf ? cdf_words(g->E, g->V) : wsum_layout(g->E, g->V).words;
+            st = dalloc(&tmp, sizeof(uint64_t) * words, s);
+            if (st == CSAW_OK && leaf) st = enqueue_cdf_build(g, kind, (uint64_t*)tmp, s);
+            if (st == CSAW_OK && !leaf) {
+                const CdfView c = wsum_view((const uint64_t*)tmp, g->E, g->V);
+                st = enqueue_cdf_build_raw(g->off, g->col, g->w, g->deg, g->V, g->E, g->sm_count, kind, nullptr,
+                                           (uint64_t*)c.s1, (uint64_t*)c.s2, (uint64_t*)c.rec, s);
+            }
             cdf = (const uint64_t*)tmp;
         }
+        timer.mark(1, s);
         // thread per walker; host paths come back chunk by chunk while the
         // next chunk walks
         if (st == CSAW_OK) {
-            if (mem_kind == CSAW_MEM_HOST)
-                st = walk_cached_to_host(g, kind, cdf, d_starts, n_walkers, length, rng_seed, d_path, path, s);
-            else
-                st = launch_walk_cached(g, kind, cdf, d_starts, 0, n_walkers, length, rng_seed, d_path, s);
+            if (mem_kind == CSAW_MEM_HOST) {
+                st = walk_cached_to_host(g, kind, cdf, leaf, starts, d_starts, n_walkers, length, rng_seed, d_path,
+                                         path, s, timer.out && timer.ok ? timer.ev[2] : nullptr);
+            } else {
+                st = launch_walk_cached(g, kind, cdf, leaf, d_starts, 0, n_walkers, length, rng_seed, d_path, s);
+                timer.mark(2, s);
+            }
         }
+        if (st == CSAW_OK) st = timer.finish();
         dfree(tmp, s);
         if (mem_kind == CSAW_MEM_HOST) {
             if (st != CSAW_OK) cudaStreamSynchronize(s);
@@ -1017,9 +1067,12 @@ extern "C" csaw_status csaw_walk_ex(csaw_graph* g, const uint32_t* starts, uint6
             for (int i = 0; i < 3; ++i) m = bias->n2v_mult[i] > m ? bias->n2v_mult[i] : m;
             max_bias = (uint64_t)g->max_weight * m;
         }
+        timer.mark(1, s);
         st = launch_walk(kind, max_bias, p, g->sm_count, s);
+        timer.mark(2, s);
     }
     dfree(counter, s);
+    if (st == CSAW_OK) st = timer.finish();
     if (mem_kind == CSAW_MEM_HOST) {
         if (st == CSAW_OK) {
             cudaError_t e = cudaMemcpyAsync(path, d_path, path_bytes, cudaMemcpyDeviceToHost, s);

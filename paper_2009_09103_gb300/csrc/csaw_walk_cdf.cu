@@ -31,9 +31,15 @@ constexpr int WC_THREADS = 256;
 constexpr int WC_WARPS = WC_THREADS / 32;
 constexpr int WC_TILE = 16;                  // path entries staged per walker
 
+// How a step finds its pick: uniform (x itself), the array's leaf level, or
+// the summaries and the weights (w_search, no leaf level).
+constexpr int WC_UNIFORM = 0, WC_LEAF = 1, WC_WEIGHTS = 2;
+
 struct WalkCdfParams {
     const uint64_t* __restrict__ off;
     const uint32_t* __restrict__ col;
+    const uint32_t* __restrict__ w;      // weights (WC_WEIGHTS)
+    uint64_t E;
     CdfView c;                           // the cumulative array (cdf null for uniform bias)
     uint32_t V;
     const uint32_t* __restrict__ starts;
@@ -85,7 +91,17 @@ __device__ __forceinline__ void walk_tile_flush_rows(const WalkCdfParams& p, uin
     __syncwarp();
 }
 
-template <bool UNIFORM, bool BATCH = false>
+// Loads of the CSR arrays: read-only cache for graph arrays, plain loads for
+// arrays in host memory (HOST: read in place over the host link).
+template <bool HOST, class T>
+__device__ __forceinline__ T ld_graph(const T* p)
+{
+    if constexpr (HOST) return *p;
+    else return __ldg(p);
+}
+
+// HOST: off, col and w are host arrays (unpadded), read in place.
+template <int MODE, bool BATCH = false, bool HOST = false>
 __global__ void __launch_bounds__(WC_THREADS, 6) walk_cached_kernel(WalkCdfParams p)
 {
     __shared__ uint32_t s_tile[WC_WARPS][32][WC_TILE + 1];   // +1: conflict-free column writes
@@ -118,9 +134,9 @@ __global__ void __launch_bounds__(WC_THREADS, 6) walk_cached_kernel(WalkCdfParam
             if (alive) {
                 // the row: offsets (uniform) or the vertex's record {start, end, total}
                 uint64_t beg, end, T = 0;
-                if constexpr (UNIFORM) {
-                    beg = __ldg(p.off + cur);
-                    end = __ldg(p.off + cur + 1);
+                if constexpr (MODE == WC_UNIFORM) {
+                    beg = ld_graph<HOST>(p.off + cur);
+                    end = ld_graph<HOST>(p.off + cur + 1);
                 } else {
                     const ulonglong2* rc = reinterpret_cast<const ulonglong2*>(p.c.rec + 4ull * cur);
                     const ulonglong2 r0 = __ldg(rc), r1 = __ldg(rc + 1);
@@ -134,14 +150,19 @@ __global__ void __launch_bounds__(WC_THREADS, 6) walk_cached_kernel(WalkCdfParam
                     uint64_t r;
                     if constexpr (BATCH) r = philox_draw(ws.k0, ws.k1, 0u, cur, s, ws.id);
                     else r = philox_draw(p.keys, 0u, cur, s, p.w0 + (uint32_t)wk);
-                    if constexpr (UNIFORM) {
+                    if constexpr (MODE == WC_UNIFORM) {
                         i = scale_draw(r, end - beg);
                     } else {
                         stop = T == 0;
-                        if (!stop) i = cdf_search<true>(p.c, beg, end, scale_draw(r, T)) - beg;
+                        if (!stop) {
+                            const uint64_t x = scale_draw(r, T);
+                            if constexpr (MODE == WC_LEAF) i = cdf_search<true>(p.c, beg, end, x) - beg;
+                            else i = w_search<!HOST>(p.c, p.w, p.E, beg, end, x) - beg;
+                        }
                     }
                 }
                 if (stop) { alive = false; cur = CSAW_NONE; }
+                else if constexpr (HOST) cur = p.col[beg + i];
                 else cur = __ldcs(p.col + beg + i);
             }
             const uint64_t t = (uint64_t)s + 1;      // path position of this step's vertex
@@ -159,13 +180,13 @@ __global__ void __launch_bounds__(WC_THREADS, 6) walk_cached_kernel(WalkCdfParam
     }
 }
 
-template <bool UNIFORM, bool BATCH>
+template <int MODE, bool BATCH, bool HOST = false>
 static csaw_status launch_walk_cached_k(const WalkCdfParams& p, int sm_count, cudaStream_t s)
 {
     static std::atomic<int> cached{0};
     int per_sm = cached.load(std::memory_order_acquire);
     if (per_sm == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_cached_kernel<UNIFORM, BATCH>,
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_cached_kernel<MODE, BATCH, HOST>,
                                                                       WC_THREADS, 0);
         if (e != cudaSuccess) return cuda_fail(e, "occupancy(walk_cached)");
         if (per_sm < 1) per_sm = 1;
@@ -180,25 +201,42 @@ static csaw_status launch_walk_cached_k(const WalkCdfParams& p, int sm_count, cu
     }
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    walk_cached_kernel<UNIFORM, BATCH><<<(unsigned)blocks, WC_THREADS, 0, s>>>(p);
+    walk_cached_kernel<MODE, BATCH, HOST><<<(unsigned)blocks, WC_THREADS, 0, s>>>(p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "walk_cached_kernel launch");
     return CSAW_OK;
 }
 
-csaw_status launch_walk_cached(const csaw_graph* g, int kind, const uint64_t* cdf, const uint32_t* starts,
-                               uint64_t w0, uint64_t n, uint32_t length, uint64_t rng_seed, uint32_t* path,
-                               cudaStream_t s)
+csaw_status launch_walk_cached(const csaw_graph* g, int kind, const uint64_t* cdf, bool leaf,
+                               const uint32_t* starts, uint64_t w0, uint64_t n, uint32_t length, uint64_t rng_seed,
+                               uint32_t* path, cudaStream_t s)
 {
     WalkCdfParams p;
-    p.off = g->off; p.col = g->col;
-    p.c = cdf_view(kind == CSAW_BIAS_UNIFORM ? nullptr : cdf, g->E, g->V);
+    p.off = g->off; p.col = g->col; p.w = g->w; p.E = g->E;
+    const uint64_t* base = kind == CSAW_BIAS_UNIFORM ? nullptr : cdf;
+    p.c = leaf ? cdf_view(base, g->E, g->V) : wsum_view(base, g->E, g->V);
     p.V = g->V; p.starts = starts; p.n = n; p.L = length; p.path = path;
     p.w0 = (uint32_t)w0;
     p.keys = philox_round_keys(rng_seed);
     p.seg = WalkSegments{};
-    return kind == CSAW_BIAS_UNIFORM ? launch_walk_cached_k<true, false>(p, g->sm_count, s)
-                                     : launch_walk_cached_k<false, false>(p, g->sm_count, s);
+    if (kind == CSAW_BIAS_UNIFORM) return launch_walk_cached_k<WC_UNIFORM, false>(p, g->sm_count, s);
+    if (!leaf) return launch_walk_cached_k<WC_WEIGHTS, false>(p, g->sm_count, s);
+    return launch_walk_cached_k<WC_LEAF, false>(p, g->sm_count, s);
+}
+
+csaw_status launch_walk_host(const CdfView& c, const uint64_t* off, const uint32_t* col, const uint32_t* w,
+                             uint32_t V, uint64_t E, int sm_count, const uint32_t* starts, uint64_t n,
+                             uint32_t length, uint64_t rng_seed, uint32_t* path, cudaStream_t s)
+{
+    WalkCdfParams p;
+    p.off = off; p.col = col; p.w = w; p.E = E;
+    p.c = c;
+    p.V = V; p.starts = starts; p.n = n; p.L = length; p.path = path;
+    p.w0 = 0;
+    p.keys = philox_round_keys(rng_seed);
+    p.seg = WalkSegments{};
+    if (!w) return launch_walk_cached_k<WC_UNIFORM, false, true>(p, sm_count, s);
+    return launch_walk_cached_k<WC_WEIGHTS, false, true>(p, sm_count, s);
 }
 
 // Chunks of at least WC_CHUNK_MIN walkers keep the persistent grid full
@@ -206,9 +244,10 @@ csaw_status launch_walk_cached(const csaw_graph* g, int kind, const uint64_t* cd
 constexpr uint64_t WC_CHUNK_MIN = 1ull << 18;
 constexpr uint64_t WC_CHUNKS = 4;
 
-csaw_status walk_cached_to_host(const csaw_graph* g, int kind, const uint64_t* cdf, const uint32_t* d_starts,
-                                uint64_t n, uint32_t length, uint64_t rng_seed, uint32_t* d_path,
-                                uint32_t* h_path, cudaStream_t s)
+csaw_status walk_cached_to_host(const csaw_graph* g, int kind, const uint64_t* cdf, bool leaf,
+                                const uint32_t* h_starts, const uint32_t* d_starts, uint64_t n, uint32_t length,
+                                uint64_t rng_seed, uint32_t* d_path, uint32_t* h_path, cudaStream_t s,
+                                cudaEvent_t walked)
 {
     const uint64_t row_len = (uint64_t)length + 1;
     uint64_t k = n / WC_CHUNK_MIN;
@@ -225,12 +264,21 @@ csaw_status walk_cached_to_host(const csaw_graph* g, int kind, const uint64_t* c
     uint64_t n_chunks = 0;
     for (uint64_t w0 = 0; st == CSAW_OK && w0 < n; w0 += chunk, ++n_chunks) {
         const uint64_t m = n - w0 < chunk ? n - w0 : chunk;
-        st = launch_walk_cached(g, kind, cdf, d_starts + w0, w0, m, length, rng_seed, d_path + w0 * row_len, s);
+        st = launch_walk_cached(g, kind, cdf, leaf, d_starts + w0, w0, m, length, rng_seed, d_path + w0 * row_len, s);
         if (st == CSAW_OK && k > 1) {
             e = cudaEventRecord(ev[n_chunks], s);
             if (e != cudaSuccess) st = cuda_fail(e, "chunk event");
         }
     }
+    if (st == CSAW_OK && walked) {
+        e = cudaEventRecord(walked, s);
+        if (e != cudaSuccess) st = cuda_fail(e, "walk event");
+    }
+    // the host starts are checked while the walks run
+    for (uint64_t i = 0; st == CSAW_OK && i < n; ++i)
+        if (h_starts[i] >= g->V)
+            st = fail(CSAW_ERR_INVALID, "start %llu of walker %llu out of range", (unsigned long long)h_starts[i],
+                      (unsigned long long)i);
     // then each chunk's rows, on the copy stream once the chunk is done
     for (uint64_t c = 0, w0 = 0; st == CSAW_OK && w0 < n; w0 += chunk, ++c) {
         const uint64_t m = n - w0 < chunk ? n - w0 : chunk;
@@ -257,14 +305,14 @@ csaw_status walk_batch_cached(const csaw_graph* g, int kind, const uint32_t* d_s
                               const WalkSegments& seg, uint32_t max_len, uint32_t* d_path, cudaStream_t s)
 {
     WalkCdfParams p;
-    p.off = g->off; p.col = g->col;
+    p.off = g->off; p.col = g->col; p.w = g->w; p.E = g->E;
     p.c = cdf_view(kind == CSAW_BIAS_UNIFORM ? nullptr : g->cdf[kind], g->E, g->V);
     p.V = g->V; p.starts = d_starts; p.n = n; p.L = max_len; p.path = d_path;
     p.w0 = 0;
     p.keys = philox_round_keys(0);
     p.seg = seg;
-    return kind == CSAW_BIAS_UNIFORM ? launch_walk_cached_k<true, true>(p, g->sm_count, s)
-                                     : launch_walk_cached_k<false, true>(p, g->sm_count, s);
+    return kind == CSAW_BIAS_UNIFORM ? launch_walk_cached_k<WC_UNIFORM, true>(p, g->sm_count, s)
+                                     : launch_walk_cached_k<WC_LEAF, true>(p, g->sm_count, s);
 }
 
 }  // namespace csaw

@@ -113,6 +113,11 @@ def test_host_walk_in_chunks_with_overlapped_copies(csaw, n, build):
     pick = pick[pick < n]
     ref = oracle.walk(g, starts[pick], 10, "edge_weight", 21, walker_ids=pick.astype(np.uint64))
     assert np.array_equal(host[pick], ref)
+    bad = starts.copy()
+    bad[n // 3] = g.V   # checked on the host while the chunks walk
+    with pytest.raises(csaw.CsawError) as e:
+        csaw.walk(G, bad, 10, "edge_weight", 21, build_cdf=build)
+    assert e.value.status == csaw.ERR_INVALID
     G.close()
 
 

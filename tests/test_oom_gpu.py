@@ -73,6 +73,43 @@ def test_oom_walk_slots_and_prefetch(csaw, slots, pin):
         assert st["reuses"] > 0
 
 
+@pytest.mark.parametrize("bias", ["uniform", "edge_weight"])
+def test_oom_walk_direct_reads_host_arrays(csaw, bias):
+    """Direct mode: the device reads the host CSR in place (summaries and
+    records of the weights built on the device from the host weights); the
+    paths equal the oracle's, zero weights and dead ends included."""
+    g = inputs.rmat_csr(13, 16, 100, 13)
+    g.w[::7] = 0
+    starts = np.concatenate([np.arange(g.V, dtype=np.uint32), inputs.uniform_vertices(3000, g.V, 5)])
+    path, st = csaw.walk_oom(g.off, g.col, g.w, starts, 30, bias, 41, budget_bytes=1 << 26, direct=True)
+    assert np.array_equal(path, oracle.walk(g, starts, 30, bias, 41))
+    if st["direct"] == 0:
+        pytest.skip("this device does not read pageable host memory")
+    assert st["loads"] == 0 and st["bytes_loaded"] == 0
+    # summaries that do not fit the budget: the call partitions instead
+    path2, st2 = csaw.walk_oom(g.off, g.col, g.w, starts, 30, bias, 41, budget_bytes=16 * int(np.diff(g.off).max()) + 4096,
+                               slots=1, direct=True)
+    assert np.array_equal(path2, path)
+    if bias == "edge_weight":
+        assert st2["direct"] == 0 and st2["partitions"] > 1
+
+
+def test_oom_walk_direct_hub_and_bad_columns(csaw):
+    rng = np.random.default_rng(4)
+    d = 30000
+    edges = [(0, j + 1) for j in range(d)] + [(j + 1, 0) for j in range(d)]
+    w = list(rng.integers(1, 2**20, size=d)) + [1] * d
+    g = inputs.csr_from_edges(d + 1, edges, w)
+    starts = np.concatenate([np.zeros(64, dtype=np.uint32), inputs.uniform_vertices(64, g.V, 2)])
+    path, st = csaw.walk_oom(g.off, g.col, g.w, starts, 20, "edge_weight", 5, budget_bytes=1 << 24, direct=True)
+    assert np.array_equal(path, oracle.walk(g, starts, 20, "edge_weight", 5))
+    col = g.col.copy()
+    col[len(col) // 3] = g.V + 9
+    with pytest.raises(csaw.CsawError) as e:
+        csaw.walk_oom(g.off, col, g.w, starts, 5, "edge_weight", 5, budget_bytes=1 << 24, direct=True)
+    assert e.value.status == csaw.ERR_INVALID
+
+
 def _sample_cases():
     g = inputs.rmat_csr(12, 16, 100, 12)
     sizes = inputs.loguniform_sizes(30, 0.0, 7.0, 4)
