@@ -1,6 +1,7 @@
 // csaw_walk_cdf.cu -- random walks over a static bias's cumulative array
 // (Sec. II-A, II-B: the CTPS of every row built once, then searched).
 #include <atomic>
+#include <vector>
 
 #include "csaw_internal.cuh"
 
@@ -180,8 +181,9 @@ __global__ void __launch_bounds__(WC_THREADS, 6) walk_cached_kernel(WalkCdfParam
     }
 }
 
-template <int MODE, bool BATCH, bool HOST = false>
-static csaw_status launch_walk_cached_k(const WalkCdfParams& p, int sm_count, cudaStream_t s)
+// Resident blocks per SM of one instantiation (queried once).
+template <int MODE, bool BATCH, bool HOST>
+static csaw_status walk_cached_occupancy(int* per_sm_out)
 {
     static std::atomic<int> cached{0};
     int per_sm = cached.load(std::memory_order_acquire);
@@ -192,6 +194,15 @@ static csaw_status launch_walk_cached_k(const WalkCdfParams& p, int sm_count, cu
         if (per_sm < 1) per_sm = 1;
         cached.store(per_sm, std::memory_order_release);
     }
+    *per_sm_out = per_sm;
+    return CSAW_OK;
+}
+
+template <int MODE, bool BATCH, bool HOST = false>
+static csaw_status launch_walk_cached_k(const WalkCdfParams& p, int sm_count, cudaStream_t s)
+{
+    int per_sm = 0;
+    CSAW_TRY((walk_cached_occupancy<MODE, BATCH, HOST>(&per_sm)));
     uint64_t blocks = (p.n + WC_THREADS - 1) / WC_THREADS;
     uint64_t cap = (uint64_t)sm_count * per_sm;
     if (BATCH && p.seg.warp_budget) {
@@ -239,10 +250,13 @@ csaw_status launch_walk_host(const CdfView& c, const uint64_t* off, const uint32
     return launch_walk_cached_k<WC_WEIGHTS, false, true>(p, sm_count, s);
 }
 
-// Chunks of at least WC_CHUNK_MIN walkers keep the persistent grid full
-// (the kernel is latency-bound); at most WC_CHUNKS of them.
-constexpr uint64_t WC_CHUNK_MIN = 1ull << 18;
-constexpr uint64_t WC_CHUNKS = 4;
+// With host outputs the walkers run in chunks of whole resident waves (the
+// walkers the persistent grid holds at once: a thread walks one walker's
+// whole path, so a launch takes as many path-lengths as it has waves, the
+// last one partial), at most WC_MAX_CHUNKS of them: each chunk's rows are
+// copied out while the next chunk walks, and only the last, partial wave's
+// copy is left after the walk.
+constexpr uint64_t WC_MAX_CHUNKS = 64;
 
 csaw_status walk_cached_to_host(const csaw_graph* g, int kind, const uint64_t* cdf, bool leaf,
                                 const uint32_t* h_starts, const uint32_t* d_starts, uint64_t n, uint32_t length,
@@ -250,23 +264,28 @@ csaw_status walk_cached_to_host(const csaw_graph* g, int kind, const uint64_t* c
                                 cudaEvent_t walked)
 {
     const uint64_t row_len = (uint64_t)length + 1;
-    uint64_t k = n / WC_CHUNK_MIN;
-    k = k < 1 ? 1 : (k > WC_CHUNKS ? WC_CHUNKS : k);
-    const uint64_t chunk = ((n + k - 1) / k + 31) & ~31ull;
+    int per_sm = 0;
+    if (kind == CSAW_BIAS_UNIFORM) CSAW_TRY((walk_cached_occupancy<WC_UNIFORM, false, false>(&per_sm)));
+    else if (!leaf) CSAW_TRY((walk_cached_occupancy<WC_WEIGHTS, false, false>(&per_sm)));
+    else CSAW_TRY((walk_cached_occupancy<WC_LEAF, false, false>(&per_sm)));
+    const uint64_t wave = (uint64_t)g->sm_count * (uint64_t)per_sm * WC_THREADS;
+    const uint64_t waves = (n + wave - 1) / wave;
+    const uint64_t per_chunk = (waves + WC_MAX_CHUNKS - 1) / WC_MAX_CHUNKS;
+    const uint64_t chunk = wave * per_chunk;
+    const uint64_t k = (n + chunk - 1) / chunk;
     cudaStream_t cs = nullptr;
-    cudaEvent_t ev[WC_CHUNKS] = {};
+    std::vector<cudaEvent_t> ev(k > 1 ? k : 0, nullptr);
     csaw_status st = CSAW_OK;
     cudaError_t e = cudaSuccess;
     if (k > 1) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-    for (uint64_t c = 0; e == cudaSuccess && c < k && k > 1; ++c) e = cudaEventCreateWithFlags(&ev[c], cudaEventDisableTiming);
+    for (uint64_t c = 0; e == cudaSuccess && c < ev.size(); ++c) e = cudaEventCreateWithFlags(&ev[c], cudaEventDisableTiming);
     if (e != cudaSuccess) st = cuda_fail(e, "copy stream");
     // every chunk's walk first (the copies of pageable memory block the host)
-    uint64_t n_chunks = 0;
-    for (uint64_t w0 = 0; st == CSAW_OK && w0 < n; w0 += chunk, ++n_chunks) {
+    for (uint64_t c = 0, w0 = 0; st == CSAW_OK && w0 < n; w0 += chunk, ++c) {
         const uint64_t m = n - w0 < chunk ? n - w0 : chunk;
         st = launch_walk_cached(g, kind, cdf, leaf, d_starts + w0, w0, m, length, rng_seed, d_path + w0 * row_len, s);
         if (st == CSAW_OK && k > 1) {
-            e = cudaEventRecord(ev[n_chunks], s);
+            e = cudaEventRecord(ev[c], s);
             if (e != cudaSuccess) st = cuda_fail(e, "chunk event");
         }
     }
@@ -295,8 +314,8 @@ csaw_status walk_cached_to_host(const csaw_graph* g, int kind, const uint64_t* c
     }
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess && st == CSAW_OK) st = cuda_fail(e, "walk");
-    for (uint64_t c = 0; c < k && k > 1; ++c)
-        if (ev[c]) cudaEventDestroy(ev[c]);
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
     if (cs) cudaStreamDestroy(cs);
     return st;
 }
