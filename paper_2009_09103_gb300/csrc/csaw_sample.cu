@@ -46,6 +46,9 @@ constexpr uint32_t WARP_MAX_DEG = 256;     // warp items: degree <= this
 constexpr uint32_t CTA_SMEM_DEG = 8192;    // CTA items keep S in shared memory up to this
 constexpr uint32_t WARP_SLOT = WARP_MAX_DEG * 8 + (WARP_MAX_DEG / 32) * 4;   // bytes per warp
 constexpr size_t SEL_DYN_SMEM = (size_t)CTA_SMEM_DEG * 8 + (CTA_SMEM_DEG / 32) * 4;
+// Warp items alone use only the warps' slots: a launch that can hold no CTA
+// item takes this much, and more blocks fit an SM.
+constexpr size_t SEL_WARP_SMEM = (size_t)(SEL_THREADS / 32) * WARP_SLOT;
 constexpr uint32_t PICK_MAX = 256;         // picks a cached-array warp item may hold
 
 static_assert(SEL_WARPS * WARP_SLOT <= SEL_DYN_SMEM, "warp slots reuse the CTA region");
@@ -371,7 +374,7 @@ __device__ void cta_item(const SelParams& p, uint32_t e, uint64_t* S, uint32_t* 
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(SEL_THREADS) select_kernel(SelParams p)
+__global__ void __launch_bounds__(SEL_THREADS, 5) select_kernel(SelParams p)
 {
     if (p.key_dev) {
         p.k0 = p.key_dev[0];
@@ -1070,9 +1073,9 @@ struct Temps {
 };
 
 template <int KIND>
-static csaw_status launch_select(const SelParams& p, int blocks, cudaStream_t s)
+static csaw_status launch_select(const SelParams& p, int blocks, cudaStream_t s, size_t smem = SEL_DYN_SMEM)
 {
-    select_kernel<KIND><<<blocks, SEL_THREADS, SEL_DYN_SMEM, s>>>(p);
+    select_kernel<KIND><<<blocks, SEL_THREADS, smem, s>>>(p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "select_kernel");
     return CSAW_OK;
@@ -1122,6 +1125,30 @@ static int select_occupancy(int kind)
 static int select_blocks(int kind, int sm_count)
 {
     return sm_count * select_occupancy(kind);
+}
+
+// Resident blocks per SM of a launch with warp items only (SEL_WARP_SMEM).
+static int select_occupancy_warp(int kind)
+{
+    static std::atomic<int> cached[4];
+    const int have = cached[kind].load(std::memory_order_acquire);
+    if (have) return have;
+    int per_sm = 1;
+    cudaError_t e = cudaSuccess;
+    switch (kind) {
+    case CSAW_BIAS_UNIFORM:
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, select_kernel<CSAW_BIAS_UNIFORM>, SEL_THREADS, SEL_WARP_SMEM);
+        break;
+    case CSAW_BIAS_EDGE_WEIGHT:
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, select_kernel<CSAW_BIAS_EDGE_WEIGHT>, SEL_THREADS, SEL_WARP_SMEM);
+        break;
+    default:
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, select_kernel<CSAW_BIAS_NEIGHBOR_DEGREE>, SEL_THREADS, SEL_WARP_SMEM);
+        break;
+    }
+    if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+    cached[kind].store(per_sm, std::memory_order_release);
+    return per_sm;
 }
 
 // Launch shape of the selection kernel for this graph and kind: the tuned
@@ -1655,10 +1682,22 @@ static csaw_status enqueue_select_items(Pipeline& P, uint32_t l, cudaStream_t s)
             }
             CSAW_CUDA(cudaGetLastError());
         }
+        // with shared hub arrays a CTA item needs more than PICK_MAX picks: a
+        // layer whose fanout is at most that holds warp items only, launched
+        // with their slots alone (more resident blocks hide the gathers)
+        const bool warp_only = P.hub_path && P.fanout[l] <= PICK_MAX;
+        int blocks = P.sel_blocks;
+        size_t smem = SEL_DYN_SMEM;
+        if (warp_only) {
+            const int occ = select_occupancy_warp(P.kind);
+            const int per = (int)g->tune_blocks_per_sm[P.kind];
+            blocks = g->sm_count * (per > 0 && per < occ ? per : occ);
+            smem = SEL_WARP_SMEM;
+        }
         switch (P.kind) {
-        case CSAW_BIAS_UNIFORM: CSAW_TRY(launch_select<CSAW_BIAS_UNIFORM>(sp, P.sel_blocks, s)); break;
-        case CSAW_BIAS_EDGE_WEIGHT: CSAW_TRY(launch_select<CSAW_BIAS_EDGE_WEIGHT>(sp, P.sel_blocks, s)); break;
-        default: CSAW_TRY(launch_select<CSAW_BIAS_NEIGHBOR_DEGREE>(sp, P.sel_blocks, s)); break;
+        case CSAW_BIAS_UNIFORM: CSAW_TRY(launch_select<CSAW_BIAS_UNIFORM>(sp, blocks, s, smem)); break;
+        case CSAW_BIAS_EDGE_WEIGHT: CSAW_TRY(launch_select<CSAW_BIAS_EDGE_WEIGHT>(sp, blocks, s, smem)); break;
+        default: CSAW_TRY(launch_select<CSAW_BIAS_NEIGHBOR_DEGREE>(sp, blocks, s, smem)); break;
         }
         if (P.hub_path) {
             // the layer's distinct hubs: prefix sums built once each, then
