@@ -374,7 +374,7 @@ __device__ void cta_item(const SelParams& p, uint32_t e, uint64_t* S, uint32_t* 
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(SEL_THREADS, 5) select_kernel(SelParams p)
+__global__ void __launch_bounds__(SEL_THREADS, 6) select_kernel(SelParams p)
 {
     if (p.key_dev) {
         p.k0 = p.key_dev[0];
@@ -436,7 +436,7 @@ __device__ __forceinline__ uint64_t cdf_at(const uint64_t* __restrict__ row, boo
 // CACHED: rows of the graph's cumulative array, searched through its
 // summaries (cdf_search); otherwise bisected directly (shared hub arrays).
 template <bool IMPLICIT, bool CACHED = false>
-__global__ void __launch_bounds__(SEL_THREADS, 8) select_cdf_kernel(SelParams p)
+__global__ void __launch_bounds__(SEL_THREADS, CACHED ? 6 : 8) select_cdf_kernel(SelParams p)
 {
     __shared__ uint32_t s_picks[SEL_WARPS][PICK_MAX];
     if (p.key_dev) {

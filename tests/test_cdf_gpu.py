@@ -121,6 +121,26 @@ def test_host_walk_in_chunks_with_overlapped_copies(csaw, n, build):
     G.close()
 
 
+def test_walk_phase_times(csaw):
+    """phase_ms: device times of the array's construction and of the walk,
+    measured by events inside the call; the paths are unchanged."""
+    import torch
+    g = inputs.rmat_csr(14, 16, 255, 14)
+    G = csaw.Graph(g.off, g.col, g.w)
+    s = torch.from_numpy(np.arange(g.V, dtype=np.uint32).view(np.int32)).cuda()
+    ref = csaw.walk(G, s, 30, "edge_weight", 4, build_cdf=True)
+    ph = [0.0, 0.0]
+    got = csaw.walk(G, s, 30, "edge_weight", 4, build_cdf=True, phase_ms=ph)
+    assert bool(torch.equal(got, ref)) and ph[0] > 0 and ph[1] > 0
+    host_ph = [0.0, 0.0]
+    host = csaw.walk(G, np.arange(g.V, dtype=np.uint32), 30, "edge_weight", 4, build_cdf=True, phase_ms=host_ph)
+    assert np.array_equal(host, ref.cpu().numpy().view(np.uint32)) and host_ph[0] > 0 and host_ph[1] > 0
+    st_ph = [0.0, 0.0]   # streaming: nothing is built
+    csaw.walk(G, s, 30, "edge_weight", 4, phase_ms=st_ph)
+    assert st_ph[0] < ph[0] and st_ph[1] > 0
+    G.close()
+
+
 @pytest.mark.parametrize("bias", ["edge_weight", "uniform"])
 def test_cached_walk_tile_boundaries_and_dead_ends(csaw, bias):
     """Path rows are staged 16 entries at a time per walker and written out
