@@ -1526,7 +1526,10 @@ struct Pipeline {
                     (kind == CSAW_BIAS_NEIGHBOR_DEGREE && g->zero_degree_target);
         select_shape(g, kind, &theta_w, &sel_blocks);
         cached = cached_cdf_usable(g, kind);
-        hub_path = !cached && (kind == CSAW_BIAS_EDGE_WEIGHT || kind == CSAW_BIAS_NEIGHBOR_DEGREE);
+        // shared hub arrays pay when several instances can reach the same
+        // hub; a single instance's frontier holds each vertex once, and its
+        // long rows take the CTA path without the grouping kernels
+        hub_path = !cached && n_inst > 1 && (kind == CSAW_BIAS_EDGE_WEIGHT || kind == CSAW_BIAS_NEIGHBOR_DEGREE);
         // vertex order pays only when several instances can hold the same hub
         hub_order = cached && n_inst > 1 && (kind == CSAW_BIAS_EDGE_WEIGHT || kind == CSAW_BIAS_NEIGHBOR_DEGREE);
         // CTA items exist for picks above PICK_MAX (or, without the hub
