@@ -264,27 +264,6 @@ csaw_status walk_cached_to_host(const csaw_graph* g, int kind, const uint64_t* c
                                 cudaEvent_t walked)
 {
     const uint64_t row_len = (uint64_t)length + 1;
-    // Page-locked host rows: the kernel writes the path straight into them
-    // (the device addresses page-locked host memory), so no copy is left
-    // after the walk.
-    cudaPointerAttributes pa{};
-    if (cudaPointerGetAttributes(&pa, h_path) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer) {
-        csaw_status st = launch_walk_cached(g, kind, cdf, leaf, d_starts, 0, n, length, rng_seed,
-                                            (uint32_t*)pa.devicePointer, s);
-        cudaError_t e = cudaSuccess;
-        if (st == CSAW_OK && walked) {
-            e = cudaEventRecord(walked, s);
-            if (e != cudaSuccess) st = cuda_fail(e, "walk event");
-        }
-        for (uint64_t i = 0; st == CSAW_OK && i < n; ++i)
-            if (h_starts[i] >= g->V)
-                st = fail(CSAW_ERR_INVALID, "start %llu of walker %llu out of range",
-                          (unsigned long long)h_starts[i], (unsigned long long)i);
-        e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess && st == CSAW_OK) st = cuda_fail(e, "walk");
-        return st;
-    }
-    cudaGetLastError();   // pageable rows: copied out below
     int per_sm = 0;
     if (kind == CSAW_BIAS_UNIFORM) CSAW_TRY((walk_cached_occupancy<WC_UNIFORM, false, false>(&per_sm)));
     else if (!leaf) CSAW_TRY((walk_cached_occupancy<WC_WEIGHTS, false, false>(&per_sm)));

@@ -113,7 +113,7 @@ def test_host_walk_in_chunks_with_overlapped_copies(csaw, n, build):
     pick = pick[pick < n]
     ref = oracle.walk(g, starts[pick], 10, "edge_weight", 21, walker_ids=pick.astype(np.uint64))
     assert np.array_equal(host[pick], ref)
-    # page-locked host rows: written by the kernel in place
+    # page-locked host rows
     pinned = torch.empty((n, 11), dtype=torch.int32, pin_memory=True)
     got = csaw.walk(G, starts, 10, "edge_weight", 21, build_cdf=build, path=pinned.numpy().view(np.uint32))
     assert np.array_equal(got, host)
