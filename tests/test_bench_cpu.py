@@ -43,6 +43,7 @@ def test_walk_byte_models_match_a_direct_count():
     NONE = 0xFFFFFFFF
     rng = np.random.default_rng(3)
     deg = rng.integers(0, 9, size=40)
+    deg[[5, 17, 23]] = [300, 1000, 65]   # rows spanning several 64-edge blocks
     off = np.zeros(41, dtype=np.int64)
     off[1:] = np.cumsum(deg)
     n, L = 30, 7
@@ -77,6 +78,21 @@ def test_walk_byte_models_match_a_direct_count():
     path_t = torch.from_numpy(path.view(np.int32))
     assert bench.walk_bytes(torch, off_t, path_t) == (n_trans, ew)
     assert bench.node2vec_bytes(torch, off_t, path_t) == (n_trans, n2v)
+
+    # the summary search: per step 32 (record) + 8 per s2 probe over the row's
+    # G = (end-1)/64 - beg/64 entries + 32 + 32 + 4 + 4, per walker 4 + 4 (L + 1)
+    import math
+    cw = 0
+    for i in range(n):
+        cw += 4 + 4 * (L + 1)
+        for t in range(L):
+            a, b = path[i, t], path[i, t + 1]
+            if a == NONE or b == NONE:
+                break
+            beg, end = int(off[a]), int(off[a + 1])
+            G = ((end - 1) >> 6) - (beg >> 6)
+            cw += 32 + 8 * math.ceil(math.log2(G + 1)) + 32 + 32 + 4 + 4
+    assert bench.cached_walk_bytes(torch, off_t, path_t, L) == cw
 
 
 def test_walk_sector_bytes_match_a_direct_count():
