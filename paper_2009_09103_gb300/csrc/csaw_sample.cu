@@ -435,24 +435,31 @@ __device__ __forceinline__ uint64_t cdf_at(const uint64_t* __restrict__ row, boo
 
 // CACHED: rows of the graph's cumulative array, searched through its
 // summaries (cdf_search); otherwise bisected directly (shared hub arrays).
-template <bool IMPLICIT, bool CACHED = false>
+// G: lanes per item -- 32, or 16 (two items per warp, rounds of 16
+// attempts; for layers whose fanout is at most 16, where a hub row's first
+// round nearly always holds the picks).  Attempts are taken in the same
+// order either way, so the picks do not depend on G.
+template <bool IMPLICIT, bool CACHED = false, int G = 32>
 __global__ void __launch_bounds__(SEL_THREADS, CACHED ? 6 : 8) select_cdf_kernel(SelParams p)
 {
+    static_assert(G == 32 || G == 16, "16 or 32 lanes per item");
     __shared__ uint32_t s_picks[SEL_WARPS][PICK_MAX];
     if (p.key_dev) {
         p.k0 = p.key_dev[0];
         p.k1 = p.key_dev[1];
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    uint32_t* picks = s_picks[wid];
-    const uint32_t lt = lanemask_lt();
+    const int gb = lane & ~(G - 1), gl = lane & (G - 1);   // the group's first lane; this lane in it
+    const uint32_t gmask = G == 32 ? CSAW_FULL_MASK : (0xFFFFu << gb);
+    uint32_t* picks = s_picks[wid] + gb * (PICK_MAX / 32);     // PICK_MAX * G / 32 entries per group
+    const uint32_t lt = (1u << gl) - 1u;                   // group lanes before this one
     const bool hub = p.item_e != nullptr;   // hub items (vertex order): shared array or cached one
     const unsigned long long n_warp = hub ? p.n_items[2] : p.n_items[0];
     unsigned long long* counter = hub ? p.next + 2 : p.next;
     while (true) {
         unsigned long long it = 0;
-        if (lane == 0) it = atomicAdd(counter, 1ull);
-        it = __shfl_sync(CSAW_FULL_MASK, it, 0);
+        if (gl == 0) it = atomicAdd(counter, 1ull);
+        it = __shfl_sync(gmask, it, gb);
         if (it >= n_warp) break;
         const uint32_t e = hub ? p.item_e[it] : p.warp_list[it];
         const uint64_t key = p.fkeys[e];
@@ -464,11 +471,11 @@ __global__ void __launch_bounds__(SEL_THREADS, CACHED ? 6 : 8) select_cdf_kernel
         const uint32_t cnt = (uint32_t)(p.pos[e + 1] - q0);
         if (cnt >= d) {
             // every neighbour (all biases are positive here), CSR order
-            for (uint32_t j = lane; j < d; j += 32) emit(p, q0 + j, v, inst, __ldg(p.col + beg + j));
+            for (uint32_t j = gl; j < d; j += G) emit(p, q0 + j, v, inst, __ldg(p.col + beg + j));
             continue;
         }
         if (hub && p.hubS && p.hub_off[p.item_h[it]] + d > p.hubS_cap) {
-            if (lane == 0) atomicOr(p.err, 8u);   // never happens when the scratch is sized right
+            if (gl == 0) atomicOr(p.err, 8u);   // never happens when the scratch is sized right
             continue;
         }
         const uint64_t* row = hub && p.hubS ? p.hubS + p.hub_off[p.item_h[it]] : p.cdf ? p.cdf + beg : nullptr;
@@ -479,8 +486,8 @@ __global__ void __launch_bounds__(SEL_THREADS, CACHED ? 6 : 8) select_cdf_kernel
         (void)used;
         (void)rounds;
         while (have < cnt && a0 < p.attempt_cap) {
-            const bool live = a0 + lane < p.attempt_cap;   // the last round may be partial
-            const uint64_t x = scale_draw(philox_draw(dk.k0, dk.k1, a0 + lane, v, p.layer, dk.id), T);
+            const bool live = a0 + gl < p.attempt_cap;   // the last round may be partial
+            const uint64_t x = scale_draw(philox_draw(dk.k0, dk.k1, a0 + gl, v, p.layer, dk.id), T);
             uint32_t i = 0xFFFFFFFFu;
             if (!live) {
             } else if (IMPLICIT) {
@@ -497,9 +504,9 @@ __global__ void __launch_bounds__(SEL_THREADS, CACHED ? 6 : 8) select_cdf_kernel
             }
             bool chosen = false;
             for (uint32_t j = 0; j < have; ++j) chosen |= picks[j] == i;
-            const uint32_t peers = __match_any_sync(CSAW_FULL_MASK, i);
+            const uint32_t peers = __match_any_sync(gmask, i);
             const bool fresh = live && !chosen && lane == __ffs(peers) - 1;
-            const uint32_t bal = __ballot_sync(CSAW_FULL_MASK, fresh);
+            const uint32_t bal = (__ballot_sync(gmask, fresh) & gmask) >> gb;   // the group's lanes, from bit 0
             const uint32_t rank = __popc(bal & lt);
             const uint32_t need = cnt - have;
             if (fresh && rank < need) {
@@ -507,23 +514,23 @@ __global__ void __launch_bounds__(SEL_THREADS, CACHED ? 6 : 8) select_cdf_kernel
                 emit(p, q0 + have + rank, v, inst, __ldg(p.col + beg + i));
             }
 #ifdef CSAW_STATS
-            used = (uint32_t)__popc(bal) >= need ? a0 + nth_set_bit(bal, need) + 1 : min(a0 + 32, p.attempt_cap);
+            used = (uint32_t)__popc(bal) >= need ? a0 + nth_set_bit(bal, need) + 1 : min(a0 + G, p.attempt_cap);
             ++rounds;
 #endif
             have += min((uint32_t)__popc(bal), need);
-            a0 += 32;
-            __syncwarp();
+            a0 += G;
+            __syncwarp(gmask);
         }
-        if (lane == 0) {
+        if (gl == 0) {
             // draws consumed: to the last pick's attempt, or every repeated
             // attempt and then one per updated-sampling pick
             const uint32_t f = cnt - have;
             CSAW_STAT_ADD(0, f ? p.attempt_cap + f : used);
             CSAW_STAT_ADD(1, cnt);
-            CSAW_STAT_ADD(2, 32u * rounds + f);
+            CSAW_STAT_ADD(2, (uint32_t)G * rounds + f);
             CSAW_STAT_ADD(3, f);
         }
-        if (have < cnt && lane == 0) {
+        if (have < cnt && gl == 0) {
             // Updated sampling (attempts attempt_cap, ...): picks sorted
             // ascending, the draw scaled to the unpicked total and moved past
             // every picked interval that starts at or below it.
@@ -560,7 +567,7 @@ __global__ void __launch_bounds__(SEL_THREADS, CACHED ? 6 : 8) select_cdf_kernel
                 ++have;
             }
         }
-        __syncwarp();
+        __syncwarp(gmask);
     }
 }
 
@@ -1681,7 +1688,8 @@ static csaw_status enqueue_select_items(Pipeline& P, uint32_t l, cudaStream_t s)
                 // the hub items in vertex order, over the same array
                 SelParams hs = sp;
                 hs.item_e = P.item_e;
-                select_cdf_kernel<false, true><<<blocks, SEL_THREADS, 0, s>>>(hs);
+                if (P.fanout[l] <= 16) select_cdf_kernel<false, true, 16><<<blocks, SEL_THREADS, 0, s>>>(hs);
+                else select_cdf_kernel<false, true><<<blocks, SEL_THREADS, 0, s>>>(hs);
             }
             CSAW_CUDA(cudaGetLastError());
         }
@@ -1719,7 +1727,9 @@ static csaw_status enqueue_select_items(Pipeline& P, uint32_t l, cudaStream_t s)
             hs.cdf = nullptr;
             hs.item_e = P.item_e; hs.item_h = P.item_h; hs.hub_off = P.hub_off; hs.hubS = P.hubS;
             hs.hubS_cap = P.hubS_cap; hs.err = (uint32_t*)(P.ctr + CT_ERR);
-            select_cdf_kernel<false><<<g->sm_count * 8, SEL_THREADS, 0, s>>>(hs);
+            // hub rows are long, so with at most 16 picks two items share a warp
+            if (P.fanout[l] <= 16) select_cdf_kernel<false, false, 16><<<g->sm_count * 8, SEL_THREADS, 0, s>>>(hs);
+            else select_cdf_kernel<false><<<g->sm_count * 8, SEL_THREADS, 0, s>>>(hs);
             CSAW_CUDA(cudaGetLastError());
         }
     }
