@@ -1275,7 +1275,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="default run: skip the batched block")
     ap.add_argument("--no-served", action="store_true", help="default run: skip the served block")
     ap.add_argument("--instances", type=int, default=4096, help="batched_s24 at another --scale")
-    ap.add_argument("--requests", type=int, default=200, help="serve: requests per load point")
+    ap.add_argument("--requests", type=int, default=400, help="serve: requests per load point")
     ap.add_argument("--slots", type=int, default=8, help="serve: server slots")
     ap.add_argument("--loads", type=float, nargs="+", default=[0.25, 0.5, 1.0, 1.5, 3.0],
                     help="serve: arrival rates as multiples of the serial capacity")
