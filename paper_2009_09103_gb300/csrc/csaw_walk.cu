@@ -690,12 +690,16 @@ __device__ __forceinline__ bool walk_pick(const WalkParams& p, const Row& row, c
 #define CSAW_WALK_EW_BLOCKS 6   // edge-weight, 32-bit sums (swept: 5 -> 42.9 ms, 6 -> 39.9 ms, 7 -> 43.8 ms at s20)
 #endif
 
-template <int KIND, bool WIDE>
+#ifndef CSAW_WALK_N2V_BLOCKS
+#define CSAW_WALK_N2V_BLOCKS 4   // node2vec, plain walks (64 registers; 3 blocks: 80 registers)
+#endif
+
+template <int KIND, bool WIDE, bool TELE, bool BATCH>
 constexpr int walk_min_blocks()
 {
     return KIND == CSAW_BIAS_UNIFORM ? 5
            : (KIND == CSAW_BIAS_EDGE_WEIGHT && !WIDE) ? CSAW_WALK_EW_BLOCKS
-           : KIND == CSAW_BIAS_NODE2VEC ? 3 : 4;
+           : KIND == CSAW_BIAS_NODE2VEC ? (TELE || BATCH ? 3 : CSAW_WALK_N2V_BLOCKS) : 4;
 }
 
 // TELE: random walk with restart or with jump (Sec. II-A; an Update, Eq. 4,
@@ -707,7 +711,7 @@ constexpr int walk_min_blocks()
 // BATCH: walkers of several requests (WalkSegments), each with its own
 // seed, walker index and length; the draws are those of its request alone.
 template <int KIND, bool WIDE, bool TELE, bool BATCH = false>
-__global__ void __launch_bounds__(WALK_THREADS, (walk_min_blocks<KIND, WIDE>())) walk_kernel(WalkParams p)
+__global__ void __launch_bounds__(WALK_THREADS, (walk_min_blocks<KIND, WIDE, TELE, BATCH>())) walk_kernel(WalkParams p)
 {
     static_assert(!(TELE && BATCH), "teleporting walks are not batched");
     // Per warp: the chunk prefix table, then (node2vec) the N(prev) window.
